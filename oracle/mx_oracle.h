@@ -1,0 +1,152 @@
+/*
+ * mx_oracle.h -- plain FP64 CPU oracle for the hybrid symplectic hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
+ * bench.py's CPU-baseline leg (and its --impl reference arm) may load this
+ * library.  It shares no code, header, table or constant with the CUDA path
+ * in paper_2601_16791_gb300/csrc; both are written from the paper
+ * (arXiv 2601.16791, "Mercury-Arxes") independently.
+ *
+ * Units: AU, day, solar mass.  Masses enter as G-scaled mu = G*m
+ * (the paper's Sec. 2.1.3 force loop multiplies by m(i) with no G).
+ * Arrays are structure-of-arrays: a "6xN" buffer holds x[N], y[N], z[N],
+ * vx[N], vy[N], vz[N] back to back.  Big (massive) bodies come first.
+ * In the democratic-heliocentric (DH) coordinates that the step works in,
+ * x is heliocentric position and v is barycentric velocity.
+ *
+ * Every function returns 0 on success or a positive ORC_ERR_* code.
+ */
+#ifndef MX_ORACLE_H
+#define MX_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ORC_OK = 0,
+  ORC_ERR_ARG = 1,
+  ORC_ERR_KEPLER_NOCONV = 2,
+  ORC_ERR_BS_NOCONV = 3,
+  ORC_ERR_PAIR_OVERFLOW = 4,
+  ORC_ERR_NONFINITE = 5
+};
+
+typedef struct {
+  double sigma1_gcm2;   /* surface density at 1 AU [g/cm^2] (Eq. 1 normalised at 1 AU) */
+  double gamma;         /* surface-density slope (Eq. 1) */
+  double r_c_au;        /* characteristic radius R_C [AU]; +inf = pure power law */
+  double r_in_au;       /* inner edge R_in [AU]: no gas inward (Sec. 3.1) */
+  double hr_1au;        /* aspect ratio H/r at 1 AU */
+  double flare;         /* H/r grows as r^flare; temperature slope beta = 1 - 2*flare */
+  double gamma_c;       /* ratio of specific heats, 7/5 (Eq. 6) */
+  double mu_mol;        /* mean molecular weight, for the mean free path */
+  double sigma_mol_cm2; /* molecular cross-section [cm^2] */
+  double cd_scale;      /* multiplies C_D (differentiable drag-coefficient factor) */
+  int enabled;          /* 0 = no gas drag */
+  int cd_mode;          /* 0: bracket of Eq. 7 to the power -1; 1: power -2 as printed */
+} orc_gas;
+
+typedef struct {
+  double G;             /* gravitational constant [AU^3 Msun^-1 d^-2] */
+  double m_star;        /* central mass [Msun] */
+  double dt;            /* step h [d] */
+  double rcrit_hill;    /* changeover radius in Hill radii */
+  double bs_tol;        /* Bulirsch-Stoer relative tolerance */
+  int kepler_max_iter;  /* iteration cap of the universal Kepler solve */
+  int bs_max_sub;       /* cap on BS macro sub-steps per group and step */
+  int pair_cap;         /* capacity of the encounter pair list */
+  orc_gas gas;
+} orc_params;
+
+void orc_set_threads(int n);
+
+/* Changeover function K(s) for changeover radius rc (Sec. 2.1.3 listing). */
+double orc_changeover(double s, double rc);
+/* K(s)/s^3 written in terms of s^2, the factor the kick multiplies by mu*dx. */
+double orc_k_over_s3(double s2, double rc);
+
+/* Heliocentric (x, v_h) -> DH (x, v_b); mu = G*m; rcrit = rcrit_hill * R_Hill. */
+int orc_init(const orc_params* p, int nbig, int nsmall, const double* m_big,
+             const double* xv_helio, double* xv_dh, double* mu, double* rcrit);
+/* DH -> heliocentric. */
+int orc_readout(const orc_params* p, int nbig, int nsmall, const double* mu,
+                const double* xv_dh, double* xv_helio);
+
+/* K-weighted gravity on every body from the big bodies, acc is 3xN.
+ * triangular=0: the paper's rectangular gather loop; 1: its serial
+ * triangular loop with Newton's third law. */
+int orc_accel_grav(int nbig, int n, const double* xv, const double* mu,
+                   const double* rcrit, double* acc, int triangular);
+/* P = sum over massive bodies of mu_i v_i (G-scaled momentum). */
+int orc_momentum(int nbig, int n, const double* xv, const double* mu, double* P3);
+
+/* Gas-drag acceleration on every small body (3 x nsmall), Eqs. 1, 3-7. */
+int orc_gas_drag(const orc_params* p, int nbig, int nsmall, const double* xv,
+                 const double* mu, const double* rp_km, const double* rhop,
+                 double* acc_small);
+/* Disk quantities at cylindrical radius R [AU]:
+ * out = {Sigma [g/cm^2], rho_g [g/cm^3], H [AU], c_s [AU/d], v_k [AU/d],
+ *        eta, v_g [AU/d], H/r}. */
+int orc_gas_state(const orc_params* p, double R, double* out8);
+/* Drag coefficient of Eq. 7 (k = 0.4 below Re = 1e5, 0.2 from 1e5 up). */
+double orc_drag_cd(double Re, double Ma, int cd_mode);
+/* Drag acceleration of one small body with given heliocentric x and v_h. */
+int orc_drag_one(const orc_params* p, const double* x3, const double* vh3,
+                 double rp_km, double rhop, double* acc3, double* re_ma2);
+
+/* Stumpff functions c0..c3 at z. */
+void orc_stumpff(double z, double* c4);
+/* Kepler drift of n bodies by h about mu0 = G*m_star (universal variables).
+ * iters_max receives the largest iteration count used. */
+int orc_drift(const orc_params* p, int n, double* xv, double h, int* iters_max);
+
+/* Minimum over [0,1] of the cubic Hermite interpolant of the squared
+ * distance (endpoint values d0, d1, time slopes d0t, d1t over step h);
+ * +inf unless the separation shrinks at the start and grows at the end. */
+double orc_hermite_d2min(double d0, double d1, double d0t, double d1t, double h);
+/* Encounter detection over big x body pairs between the pre-drift (xv0) and
+ * post-drift (xv1) states.  flags[n] = 1 for bodies in a flagged pair;
+ * pairs = (i, j) int pairs sorted by (i, j), at most cap. */
+int orc_detect(const orc_params* p, int nbig, int n, const double* xv0,
+               const double* xv1, const double* rcrit, unsigned char* flags,
+               int* pairs, int cap, int* npairs);
+
+/* Bulirsch-Stoer integration over h of a group of nb bodies (6 x nb SoA
+ * state, modified in place) under the star plus (1-K)-weighted pair forces
+ * from the group's massive members. nsub receives the macro sub-steps. */
+int orc_bs_group(const orc_params* p, int nb, const double* mu,
+                 const double* rcrit, double* xv, double h, int* nsub);
+
+/* nsteps hybrid steps of the full system, in place (DH state).
+ * ever_flag[n] (may be NULL) is OR-ed with 1 for every body flagged in any
+ * step.  pair_log (may be NULL) receives (step, i, j) triples, up to
+ * log_cap of them; log_count receives how many were found in total.
+ * stats (may be NULL) receives {pairs, groups, max BS sub-steps,
+ * max Kepler iterations}. */
+int orc_step(const orc_params* p, int nbig, int nsmall, double* xv,
+             const double* mu, const double* rcrit, const double* rp_km,
+             const double* rhop, int nsteps, unsigned char* ever_flag,
+             int* pair_log, int log_cap, int* log_count, long long* stats);
+
+/* Energy (M_sun AU^2 d^-2) and angular momentum of the massive bodies. */
+int orc_energy(const orc_params* p, int nbig, int n, const double* xv,
+               const double* mu, double* E, double* L3);
+
+/* Semimajor axes from heliocentric states (vis-viva, gm = G*m_star for
+ * small bodies, G*(m_star + m) for big ones). */
+int orc_semimajor(const orc_params* p, int nbig, int n, const double* mu,
+                  const double* xv_helio, double* a);
+
+/* Forward-mode reference derivative of the loss
+ *   L = sum_j w[j] * (a_final_j - a_initial_j)^2   (small bodies j)
+ * after nsteps steps from the heliocentric input state, along the direction
+ * (dxv [6xN], dpar = {d sigma1, d gamma, d cd_scale}).  Returns L and dL. */
+int orc_jvp_loss(const orc_params* p, int nbig, int nsmall, const double* m_big,
+                 const double* xv_helio, const double* rp_km, const double* rhop,
+                 const double* w, int nsteps, const double* dxv,
+                 const double* dpar, double* L, double* dL);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
