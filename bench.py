@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Throughput of the hybrid symplectic step (FP64 particle-steps/s).
+
+Workload (one GPU): 4 giant cores (10-30 Earth masses, a in [3, 10] AU) and
+100,000 gas-dragged planetesimals (a in [1, 15] AU, radius 1-100 km), power-law
+gas disk Sigma = 1700 (r/AU)^-1 g/cm^2, H/r = 0.05 (r/AU)^0.25, dt = 10 days;
+seeded synthetic inputs (paper_2601_16791_gb300.workloads.gas_4core_100k).
+
+A timed step is one full hybrid step (half kick with drag, jump, Kepler drift,
+encounter detection, Bulirsch-Stoer of the flagged groups, jump, half kick),
+run kernel by kernel with CUDA events on the system's stream
+(mx_step_profiled).  L2 is flushed (256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank integrates its own disk (seed offset by rank; weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 particle-steps/s at N=100k (plain vs batched), % FP64 peak; adjoint/fwd cost"
+UNIT = "particle-steps/s"
+WORKLOAD = "gas_4core_100k"
+WORKLOAD_TEXT = ("4 giant cores + 100,000 gas-dragged planetesimals, Sigma=1700 (r/AU)^-1 g/cm^2, "
+                 "H/r=0.05 (r/AU)^0.25, dt=10 d")
+
+# Algorithmic FP64 work per unit (flops; FMA = 2, sqrt/div/transcendental = 1):
+FLOPS_PAIR_KICK = 20       # K-weighted pair force, per (target, big) pair
+FLOPS_DRAG = 88            # drag of one planetesimal: ~80 + pow, exp, 3 sqrt, 3 div
+FLOPS_KICK_UPDATE = 9      # v += (h/2)(a_grav + a_drag)
+FLOPS_JUMP = 3             # x += (h/2) P/m0
+FLOPS_DRIFT = 340          # universal-variable solve: ~60 x 5 iterations + Stumpff ~40
+FLOPS_DETECT_PAIR = 30     # endpoint distances and slopes, per (target, big) pair
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mx", choices=["mx", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- baselines
+def oracle_rate(workload, target_s, warm_steps=1):
+    """Oracle particle-steps/s on the host cores over a bounded sample of the
+    workload: every big body plus a prefix of the planetesimals."""
+    import oracle as orc
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    w = workload
+
+    def sample(ns):
+        cols = np.concatenate([np.arange(w.nbig), w.nbig + np.arange(ns)])
+        return cols
+
+    # size the sample so that one step takes ~0.5 s
+    ns = min(w.nsmall, 2000)
+    p = orc.make_params(w.params)
+    while True:
+        cols = sample(ns)
+        xv, mu, rc = orc.init(p, w.nbig, ns, w.m_big, w.xv_helio[:, cols])
+        t0 = time.perf_counter()
+        orc.step(p, w.nbig, xv, mu, rc, w.rp_km[:ns], w.rhop[:ns], 1)
+        dt = time.perf_counter() - t0
+        if dt > 0.3 or ns >= w.nsmall:
+            break
+        ns = min(w.nsmall, ns * 4)
+    nsteps = max(1, int(target_s / max(dt, 1e-6)))
+    for _ in range(warm_steps):
+        xv, _, _, _ = orc.step(p, w.nbig, xv, mu, rc, w.rp_km[:ns], w.rhop[:ns], 1)
+    t0 = time.perf_counter()
+    xv, _, _, _ = orc.step(p, w.nbig, xv, mu, rc, w.rp_km[:ns], w.rhop[:ns], nsteps)
+    el = time.perf_counter() - t0
+    n = w.nbig + ns
+    return {"value": n * nsteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{w.nbig} cores + first {ns} of {w.nsmall} planetesimals, {nsteps} steps "
+                      f"({el:.1f} s wall)"}, n, el / nsteps
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2601_16791_gb300 import workloads as W
+    import oracle as orc
+    w = W.make(WORKLOAD)
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    # bound the sample so W + K steps take about two minutes
+    budget_s = 120.0
+    per_step_target = budget_s / max(1, args.steps + args.warmup)
+    ns = 256
+    p = orc.make_params(w.params)
+    while True:
+        cols = np.concatenate([np.arange(w.nbig), w.nbig + np.arange(ns)])
+        xv, mu, rc = orc.init(p, w.nbig, ns, w.m_big, w.xv_helio[:, cols])
+        t0 = time.perf_counter()
+        orc.step(p, w.nbig, xv, mu, rc, w.rp_km[:ns], w.rhop[:ns], 1)
+        dt = time.perf_counter() - t0
+        if dt * 2 > per_step_target or ns >= w.nsmall:
+            break
+        ns = min(w.nsmall, ns * 2)
+    xv, _, _, _ = orc.step(p, w.nbig, xv, mu, rc, w.rp_km[:ns], w.rhop[:ns], args.warmup)
+    t0 = time.perf_counter()
+    xv, _, _, _ = orc.step(p, w.nbig, xv, mu, rc, w.rp_km[:ns], w.rhop[:ns], args.steps)
+    el = time.perf_counter() - t0
+    n = w.nbig + ns
+    value = n * args.steps / el
+    sample = f"{w.nbig} cores + first {ns} of {w.nsmall} planetesimals per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "n_bodies": w.n,
+                       "reference": "CPU FP64 oracle (oracle/mx_oracle.cpp), OpenMP over targets"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- roofline
+def kernel_flops(kname, w, launches, nsteps):
+    """Algorithmic FP64 flops of all launches of one kernel in the timed region."""
+    nb, ns, n = w.nbig, w.nsmall, w.n
+    if kname == "k_jump_kick":
+        per = (ns * (nb * FLOPS_PAIR_KICK + FLOPS_DRAG * (1 if w.params["gas"]["enabled"] else 0)
+                     + FLOPS_KICK_UPDATE) + nb * ((nb - 1) * FLOPS_PAIR_KICK + FLOPS_KICK_UPDATE))
+        return per * launches + FLOPS_JUMP * n * nsteps
+    if kname == "k_jump_drift":
+        return (FLOPS_DRIFT + FLOPS_JUMP) * n * launches
+    if kname == "k_detect":
+        return FLOPS_DETECT_PAIR * (ns * nb + nb * (nb - 1) // 2) * launches
+    return None
+
+
+def source_hash(names):
+    h = hashlib.sha256()
+    for nm in names:
+        h.update(open(os.path.join(ROOT, "paper_2601_16791_gb300", "csrc", nm), "rb").read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {"k_jump_kick": ["k_kick.cu", "mx_common.cuh"],
+                  "k_jump_drift": ["k_drift.cu", "mx_common.cuh"],
+                  "k_detect": ["k_detect.cu", "mx_common.cuh"]}
+
+
+def dram_traffic(kname):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
+    source still matches the one that was profiled."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path) or kname not in KERNEL_SOURCES:
+        return None
+    rec = json.load(open(path)).get(kname)
+    if not rec or rec.get("source_sha") != source_hash(KERNEL_SOURCES[kname]):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------- main
+def run_mx(args):
+    import torch
+    from paper_2601_16791_gb300 import mx, workloads as W
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    st = torch.cuda.current_stream()
+    w = W.make(WORKLOAD, seed=1 + rank)
+    sysm = mx.System(w, stream=st.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    peak = mx.mx_fp64_peak(st.cuda_stream, 200.0)
+    for _ in range(args.warmup):
+        flush.zero_()
+        mx.mx_step_profiled(sysm.h, 1)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    kms = {k: 0.0 for k in mx.KERNELS}
+    kcnt = {k: 0 for k in mx.KERNELS}
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        ms, cnt, tot = mx.mx_step_profiled(sysm.h, 1)
+        for k in mx.KERNELS:
+            kms[k] += ms[k]
+            kcnt[k] += cnt[k]
+        total_ms += tot
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    units = world * w.n * args.steps
+    value = units / (t_max * 1e-3)
+
+    # end to end through the public API with host buffers: per step the state
+    # goes host->device from pinned memory, one step runs, the state comes back
+    L = mx.load()
+    pin_in = torch.empty((6, w.n), dtype=torch.float64, pin_memory=True)
+    pin_out = torch.empty((6, w.n), dtype=torch.float64, pin_memory=True)
+    pin_in.copy_(torch.from_numpy(sysm.state(mx.MX_COORD_DH)))
+    stepc = ctypes.c_longlong(0)
+    ne = max(1, args.e2e_steps)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        mx._check(L.mx_set_state(sysm.h, ctypes.c_void_p(pin_in.data_ptr()), mx.MX_COORD_DH, 0),
+                  "mx_set_state")
+        mx._check(L.mx_step(sysm.h, 1), "mx_step")
+        mx._check(L.mx_get_state(sysm.h, ctypes.c_void_p(pin_out.data_ptr()), mx.MX_COORD_DH,
+                                 ctypes.byref(stepc)), "mx_get_state")
+        pin_in.copy_(pin_out)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * w.n * ne / e2e_s
+
+    if rank != 0:
+        sysm.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    # dominant kernel and its roofline
+    dom = max(kms, key=lambda k: kms[k])
+    flops = kernel_flops(dom, w, kcnt[dom], args.steps)
+    avg_ms = kms[dom] / max(1, kcnt[dom])
+    achieved = (flops / kcnt[dom]) / (avg_ms * 1e-3) / 1e12 if flops else None
+    traffic = dram_traffic(dom)
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "peak_source": "FP64 FMA-chain probe (mx_fp64_peak, all SMs) in this run",
+            "avg_launch_ms": avg_ms,
+            "share_of_step": kms[dom] / max(1e-12, sum(kms.values()))}
+    per_kernel = {k: {"ms_per_step": kms[k] / args.steps, "launches": kcnt[k]} for k in mx.KERNELS}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "n_bodies": w.n,
+                       "per_rank_seed": "1 + rank",
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "path": "mx_step_profiled, one step per call"},
+            "roofline": roof, "kernels": per_kernel, "clocks": clk,
+            "gpu_launches": int(sum(kcnt.values())),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 48 * w.n,
+                    "d2h_bytes_per_step": 48 * w.n, "steps": ne,
+                    "api": "mx_set_state + mx_step + mx_get_state (pinned host buffers)"}}
+    sysm.close()
+    if not args.no_cpu_baseline:
+        cb, _, _ = oracle_rate(w, 12.0)
+        line["cpu_baseline"] = cb
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mx(args)
+
+
+if __name__ == "__main__":
+    main()

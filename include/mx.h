@@ -1,0 +1,205 @@
+/*
+ * mx.h -- C ABI of the GB300 (sm_103a) hybrid symplectic hot path.
+ *
+ * The library advances planetary systems with the hybrid symplectic step that
+ * Mercury+ parallelises (arXiv 2601.16791, Sec. 2): a kick with forces from the
+ * massive ("big") bodies weighted by the changeover function K (Sec. 2.1.3,
+ * mfo_drct listing) plus gas drag on the planetesimals (Sec. 3.1, Eqs. 1-7),
+ * a jump of all heliocentric positions by the massive bodies' momentum
+ * (Sec. 2.1.3, the massive-body momentum loops), a Kepler drift of every body
+ * (Sec. 2: the WHFast Kepler part, here universal variables), detection of
+ * close encounters (Sec. 2.1.2, mce_snif listing), and Bulirsch-Stoer
+ * integration of the encounter groups (Sec. 2: mdt_bs2).
+ *
+ * Conventions shared by every entry point:
+ *  - Units: AU, day, solar mass.  Gravity enters as mu = G*m.
+ *  - "6xN" buffers are structure-of-arrays float64: x[N], y[N], z[N], vx[N],
+ *    vy[N], vz[N] back to back; big (massive) bodies come first.
+ *  - dev_* arguments are device pointers owned by the caller (for instance
+ *    torch tensors on the system's device); host_* or unprefixed pointers are
+ *    host memory owned by the caller.  The library never frees caller memory.
+ *  - Every call is ordered on the CUDA stream given to mx_init_system.  Calls
+ *    that return host values synchronise that stream before returning.
+ *  - No call aborts, traps or waits without a bound.  Device-side failures set
+ *    bits of a status word that the next synchronising call turns into the
+ *    returned mx_status.  On MX_ERR_ARG nothing was changed.
+ *  - mx_last_error() gives a one-line description of the last failure on the
+ *    calling thread.
+ */
+#ifndef MX_H
+#define MX_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MX_OK = 0,
+  MX_ERR_ARG = 1,                 /* bad argument; state unchanged */
+  MX_ERR_CUDA = 2,                /* a CUDA runtime call failed */
+  MX_ERR_OOM = 3,                 /* device allocation failed */
+  MX_ERR_KEPLER_NOCONV = 4,       /* Kepler solve hit its iteration cap */
+  MX_ERR_BS_NOCONV = 5,           /* Bulirsch-Stoer hit its sub-step cap */
+  MX_ERR_PAIR_OVERFLOW = 6,       /* more encounter pairs than pair_cap */
+  MX_ERR_NONFINITE = 7,           /* a non-finite position or velocity */
+  MX_ERR_BARRIER_TIMEOUT = 8,     /* a bounded device-side wait gave up */
+  MX_ERR_ENCOUNTER_IN_ADJOINT = 9,/* the adjoint met a big-big encounter */
+  MX_ERR_GROUP_TOO_LARGE = 10     /* an encounter group exceeds MX_MAX_GROUP */
+} mx_status;
+
+#define MX_MAX_GROUP 16           /* bodies per Bulirsch-Stoer group */
+
+typedef struct mx_system mx_system;   /* opaque; owns its device memory */
+
+/* Gas disk (Sec. 3.1).  Sigma(R) = sigma1 (R/1AU)^-gamma exp[-(R/r_c)^(2-gamma)]
+ * (Eq. 1 normalised at 1 AU), zero inside r_in; H/r = hr_1au (R/1AU)^flare;
+ * temperature slope beta = 1 - 2 flare (Eq. 2 through c_s^2 ~ T). */
+typedef struct {
+  double sigma1_gcm2;   /* g/cm^2 at 1 AU */
+  double gamma;         /* surface-density slope */
+  double r_c_au;        /* characteristic radius; +inf for a pure power law */
+  double r_in_au;       /* inner edge */
+  double hr_1au;        /* aspect ratio at 1 AU */
+  double flare;         /* aspect-ratio exponent */
+  double gamma_c;       /* ratio of specific heats (Eq. 6), 7/5 */
+  double mu_mol;        /* mean molecular weight (mean free path) */
+  double sigma_mol_cm2; /* molecular cross-section */
+  double cd_scale;      /* factor on C_D */
+  int enabled;          /* 0: no drag */
+  int cd_mode;          /* 0: Eq. 7 bracket to the power -1; 1: power -2 as printed */
+} mx_gas;
+
+typedef struct {
+  double G;             /* AU^3 Msun^-1 d^-2 */
+  double m_star;        /* Msun */
+  double dt;            /* step h, days (may be negative) */
+  double rcrit_hill;    /* changeover radius in Hill radii (3) */
+  double bs_tol;        /* Bulirsch-Stoer tolerance (1e-12) */
+  int kepler_max_iter;  /* Kepler iteration cap */
+  int bs_max_sub;       /* Bulirsch-Stoer macro sub-step cap per group and step */
+  int pair_cap;         /* encounter pair capacity */
+  mx_gas gas;
+} mx_params;
+
+/* Coordinates of mx_get_state / mx_set_state. */
+#define MX_COORD_HELIO 0  /* heliocentric x and v */
+#define MX_COORD_DH 1     /* heliocentric x, barycentric v (what the step works in) */
+
+/*
+ * mx_init_system -- copy one system to the device and prepare it.
+ *  p          parameters (copied).
+ *  n_big      massive bodies (>= 0); n_small massless planetesimals (>= 0).
+ *  m_big      [n_big] masses in Msun (host).
+ *  xv_helio   6xN heliocentric state (host), N = n_big + n_small.
+ *  rp_km, rho_gcm3  [n_small] radius and density of each planetesimal (host);
+ *             may be NULL when p->gas.enabled == 0.
+ *  cuda_stream a cudaStream_t (NULL: the legacy default stream).
+ *  out        receives the system.
+ * Converts to democratic-heliocentric coordinates (barycentric velocities)
+ * and sets each big body's changeover radius to rcrit_hill Hill radii from its
+ * osculating semimajor axis (Sec. 2.1.3 mce_hill; Sec. 3.5 for gm).
+ * Errors: MX_ERR_ARG, MX_ERR_OOM, MX_ERR_CUDA.
+ */
+mx_status mx_init_system(const mx_params* p, int n_big, int n_small, const double* m_big,
+                         const double* xv_helio, const double* rp_km, const double* rho_gcm3,
+                         void* cuda_stream, mx_system** out);
+
+/* Frees the system's device memory and graphs.  NULL is ignored. */
+void mx_destroy(mx_system* s);
+
+/*
+ * mx_step -- advance n_steps hybrid steps (Sec. 2; step order: half kick,
+ * half jump, drift, detection, Bulirsch-Stoer of encounter groups, half jump,
+ * half kick).  Runs as CUDA graphs on the system's stream and synchronises
+ * once at the end to read the status word.  n_steps >= 0.
+ */
+mx_status mx_step(mx_system* s, int n_steps);
+
+/* Kernels of one step, in launch order, for mx_step_profiled. */
+#define MX_NKERN 7
+#define MX_K_PREP 0       /* momentum + staged big positions */
+#define MX_K_JUMP_KICK 1  /* jump + half kick(s): gravity and drag */
+#define MX_K_JUMP_DRIFT 2 /* jump + Kepler drift */
+#define MX_K_DETECT 3     /* encounter detection + compaction */
+#define MX_K_SORT 4       /* pair-key sort */
+#define MX_K_GROUPS 5     /* encounter groups */
+#define MX_K_BS 6         /* Bulirsch-Stoer of the groups */
+
+/*
+ * mx_step_profiled -- the same n_steps as mx_step, launched kernel by kernel
+ * (no graph) with CUDA events around every launch on the system's stream.
+ *  kernel_ms [MX_NKERN]  summed device time per kernel (host, may be NULL)
+ *  launches  [MX_NKERN]  launches per kernel (host, may be NULL)
+ *  total_ms              device time from before the first launch to after
+ *                        the last (host, may be NULL)
+ * Synchronises once at the end.
+ */
+mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* launches,
+                           double* total_ms);
+
+/* Encounter pairs found by the last step (sorted by (i, j), i big, body
+ * indices), copied to host_pairs [2*cap]; *n_pairs gets the full count. */
+mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pairs);
+
+/*
+ * mx_accel -- kick acceleration at the current state into dev_acc (3xN):
+ * the K-weighted gravity of the big bodies (Sec. 2.1.3, rectangular loop)
+ * plus, on planetesimals, the gas drag of mx_gas_drag.
+ */
+mx_status mx_accel(mx_system* s, double* dev_acc);
+
+/*
+ * mx_gas_drag -- gas-drag acceleration of every planetesimal at the current
+ * state into dev_acc (3 x n_small): Eq. 3 with C_D from Eq. 7, rho_g from
+ * Eq. 4, sub-Keplerian gas speed from Eqs. 5-6, relative to the body's
+ * heliocentric velocity.  Zeros when the gas is disabled.
+ */
+mx_status mx_gas_drag(mx_system* s, double* dev_acc);
+
+/*
+ * mx_detect_encounters -- close-encounter test (Sec. 2.1.2, mce_snif) between
+ * the states dev_xv0 (start of the step) and dev_xv1 (end), both 6xN DH
+ * device buffers.  A pair (big i, body j) is flagged when the smallest of the
+ * squared separations at the two ends and the minimum of their cubic Hermite
+ * interpolant over the step is at most max(rcrit_i, rcrit_j)^2.
+ *  dev_flags  [N] bytes, 1 for bodies in a flagged pair (may be NULL).
+ *  dev_pairs  [2*cap] ints, (i, j) pairs sorted by (i, j) (may be NULL).
+ *  n_pairs    host; receives the number of flagged pairs (also when > cap,
+ *             which returns MX_ERR_PAIR_OVERFLOW).
+ */
+mx_status mx_detect_encounters(mx_system* s, const double* dev_xv0, const double* dev_xv1,
+                               unsigned char* dev_flags, int* dev_pairs, int cap, int* n_pairs);
+
+/* mx_kepler_drift -- Kepler drift by h of the N bodies of dev_xv (6xN, in
+ * place) about mu0 = G m_star, universal variables (Sec. 2). */
+mx_status mx_kepler_drift(mx_system* s, double* dev_xv, double h);
+
+/* mx_energy -- energy and angular momentum of the massive bodies, DH form
+ * (kinetic sum_i |p_i|^2/2m_i + |sum p|^2/2m0, full Newtonian potential;
+ * Sec. 2.1.3: the energy loop runs over massive bodies only).  Host outputs. */
+mx_status mx_energy(mx_system* s, double* E, double* L3);
+
+/* State transfer.  coords: MX_COORD_HELIO or MX_COORD_DH.  step: the number
+ * of steps taken so far (may be NULL on get). */
+mx_status mx_get_state(mx_system* s, double* xv_host, int coords, long long* step);
+mx_status mx_set_state(mx_system* s, const double* xv_host, int coords, long long step);
+/* Device-to-device copies of the DH state (6xN), ordered on the stream. */
+mx_status mx_get_state_device(mx_system* s, double* dev_xv);
+mx_status mx_set_state_device(mx_system* s, const double* dev_xv);
+
+/* Sizes of the system. */
+mx_status mx_sizes(mx_system* s, int* n_big, int* n_small);
+
+/* One-line description of the last error on this thread ("" if none). */
+const char* mx_last_error(void);
+
+/*
+ * mx_fp64_peak -- measures this GPU's FP64 fused-multiply-add rate: every SM
+ * runs independent FMA chains for about ms_target milliseconds; *tflops gets
+ * 2 * FMAs / second / 1e12.  Used for the roofline denominator.
+ */
+mx_status mx_fp64_peak(void* cuda_stream, double ms_target, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

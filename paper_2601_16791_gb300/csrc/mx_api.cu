@@ -1,0 +1,615 @@
+// mx_api.cu -- the C ABI (include/mx.h): owns the device buffers of one or
+// more systems, records the step as CUDA graphs, and maps device status bits to
+// mx_status.  All arithmetic on bodies runs in the kernels; the host only
+// folds parameters into per-system constants and lays out the buffers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mx.h"
+#include "mx_common.cuh"
+#include "mx_kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mx_status fail(mx_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kAuCm = 1.495978707e13;
+constexpr double kHydrogenG = 1.6735575e-24;
+
+#define MX_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? MX_ERR_OOM : MX_ERR_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+mx_status status_to_code(unsigned st) {
+  if (st & mx::ST_NONFINITE) return fail(MX_ERR_NONFINITE, "non-finite position or velocity");
+  if (st & mx::ST_KEPLER) return fail(MX_ERR_KEPLER_NOCONV, "Kepler solve hit its iteration cap");
+  if (st & mx::ST_PAIR_OVF) return fail(MX_ERR_PAIR_OVERFLOW, "more encounter pairs than pair_cap");
+  if (st & mx::ST_GROUP)
+    return fail(MX_ERR_GROUP_TOO_LARGE, "encounter group larger than MX_MAX_GROUP bodies");
+  if (st & mx::ST_WORK_OVF) return fail(MX_ERR_PAIR_OVERFLOW, "encounter work list overflow");
+  if (st & mx::ST_BS) return fail(MX_ERR_BS_NOCONV, "Bulirsch-Stoer hit its sub-step cap");
+  if (st & mx::ST_BARRIER) return fail(MX_ERR_BARRIER_TIMEOUT, "device wait gave up");
+  if (st & mx::ST_ADJ_ENC)
+    return fail(MX_ERR_ENCOUNTER_IN_ADJOINT, "big-big encounter inside the adjoint");
+  return MX_OK;
+}
+
+bool valid_params(const mx_params* p) {
+  return p && std::isfinite(p->G) && p->G > 0 && p->m_star > 0 && std::isfinite(p->dt) &&
+         p->rcrit_hill >= 0 && p->bs_tol > 0 && p->kepler_max_iter > 0 && p->bs_max_sub > 0 &&
+         p->pair_cap > 0 && p->pair_cap <= (1 << 26);
+}
+
+// Per-system constants folded from the parameters.
+mx::SysDev make_sysdev(const mx_params& p, int off, int nbig, int n, int boff) {
+  mx::SysDev s;
+  std::memset(&s, 0, sizeof(s));
+  s.off = off;
+  s.nbig = nbig;
+  s.n = n;
+  s.boff = boff;
+  s.mu0 = p.G * p.m_star;
+  s.inv_mu0 = 1.0 / s.mu0;
+  s.sqrt_mu0 = std::sqrt(s.mu0);
+  s.h = p.dt;
+  const mx_gas& g = p.gas;
+  s.gas_on = g.enabled ? 1 : 0;
+  s.cd_mode = g.cd_mode;
+  s.gamma_one = (g.gamma == 1.0) ? 1 : 0;
+  s.flare_quarter = (g.flare == 0.25) ? 1 : 0;
+  s.rc_inf = std::isinf(g.r_c_au) ? 1 : 0;
+  s.sigma1 = g.sigma1_gcm2;
+  s.gamma = g.gamma;
+  s.inv_rc = s.rc_inf ? 0.0 : 1.0 / g.r_c_au;
+  s.r_in = g.r_in_au;
+  s.hr1 = g.hr_1au;
+  s.flare = g.flare;
+  s.cd_scale = g.cd_scale;
+  s.c_rho = 1.0 / (std::sqrt(2.0 * kPi) * kAuCm * g.hr_1au);
+  s.c_cs = g.hr_1au * s.sqrt_mu0;
+  s.inv_c_cs = 1.0 / s.c_cs;
+  const double beta_T = 1.0 - 2.0 * g.flare;
+  s.c_eta = g.hr_1au * g.hr_1au * (g.gamma + beta_T / 2.0 + 1.5) / (2.0 * g.gamma_c);
+  const double c_lam = g.mu_mol * kHydrogenG / g.sigma_mol_cm2;
+  s.c_re = 4.0 / (std::sqrt(8.0 / kPi) * c_lam);
+  return s;
+}
+
+}  // namespace
+
+struct mx_system {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  cudaStream_t cap_st = nullptr;
+  std::vector<mx_params> params;   // per system
+  std::vector<int> nbig, nsmall;
+  int N = 0, NB = 0;
+  mx::Dev d{};
+  mx::SysDev* d_sys = nullptr;
+  mx::Tile* d_tiles = nullptr;
+  double* d_tmp = nullptr;        // 6 x N scratch for readout / set_state
+  double* d_energy = nullptr;
+  double* d_sink = nullptr;
+  unsigned* h_status = nullptr;   // pinned
+  int* h_count = nullptr;         // pinned
+  std::vector<void*> allocs;
+  cudaGraphExec_t g_head = nullptr, g_mid = nullptr, g_last = nullptr;
+  long long step = 0;
+  int bs_blocks = 0;
+};
+
+namespace {
+
+template <class T>
+mx_status dalloc(mx_system* s, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return fail(MX_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  s->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return MX_OK;
+}
+
+#define MX_TRY(x)                 \
+  do {                            \
+    mx_status r_ = (x);           \
+    if (r_ != MX_OK) return r_;   \
+  } while (0)
+
+mx_status set_device(mx_system* s) {
+  int cur = -1;
+  MX_CUDA(cudaGetDevice(&cur));
+  if (cur != s->device) MX_CUDA(cudaSetDevice(s->device));
+  return MX_OK;
+}
+
+mx_status sync_status(mx_system* s) {
+  MX_CUDA(cudaMemcpyAsync(s->h_status, s->d.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  MX_CUDA(cudaGetLastError());
+  const unsigned st = *s->h_status;
+  if (st) {
+    MX_CUDA(cudaMemsetAsync(s->d.status, 0, sizeof(unsigned), s->st));
+    MX_CUDA(cudaStreamSynchronize(s->st));
+    return status_to_code(st);
+  }
+  return MX_OK;
+}
+
+// The device work of one interior step, or the last step of a call
+// (one half kick at its end), or the leading half kick.
+void enqueue_head(mx_system* s, cudaStream_t st) {
+  const double h = s->params[0].dt;
+  mx::launch_prep(s->d, 0.0, st);
+  mx::launch_jump_kick(s->d, 0.0, 0.5 * h, 1, st);
+}
+
+void enqueue_step(mx_system* s, int last, cudaStream_t st) {
+  const double h = s->params[0].dt;
+  mx::launch_jump_drift(s->d, 0.5 * h, st);
+  mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count,
+                    s->d.pair_cap, st);
+  mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st);
+  mx::launch_groups(s->d, st);
+  mx::launch_bs(s->d, s->bs_blocks, st);
+  mx::launch_prep(s->d, 0.5 * h, st);
+  mx::launch_jump_kick(s->d, 0.5 * h, 0.5 * h, last ? 1 : 2, st);
+}
+
+mx_status capture(mx_system* s, int which, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  MX_CUDA(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
+  if (which == 0) enqueue_head(s, s->cap_st);
+  else enqueue_step(s, which == 2, s->cap_st);
+  cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
+  if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  return MX_OK;
+}
+
+mx_status ensure_graphs(mx_system* s) {
+  if (s->g_head) return MX_OK;
+  MX_TRY(capture(s, 0, &s->g_head));
+  MX_TRY(capture(s, 1, &s->g_mid));
+  MX_TRY(capture(s, 2, &s->g_last));
+  return MX_OK;
+}
+
+// Builds the device side of a batch of systems (one system = batch of one).
+mx_status build(mx_system* s, const std::vector<const double*>& m_big,
+                const std::vector<const double*>& xv_helio, const std::vector<const double*>& rp,
+                const std::vector<const double*>& rho) {
+  const int nsys = (int)s->params.size();
+  std::vector<mx::SysDev> sys(nsys);
+  std::vector<mx::Tile> tiles;
+  int off = 0, boff = 0;
+  for (int k = 0; k < nsys; ++k) {
+    const int n = s->nbig[k] + s->nsmall[k];
+    sys[k] = make_sysdev(s->params[k], off, s->nbig[k], n, boff);
+    for (int t = 0; t < n; t += mx::kThreads) tiles.push_back({k, off + t, std::min(mx::kThreads, n - t), 0});
+    off += n;
+    boff += s->nbig[k];
+  }
+  s->N = off;
+  s->NB = boff;
+  const int N = s->N, NB = s->NB;
+  if (N <= 0) return fail(MX_ERR_ARG, "empty system");
+  mx::Dev& d = s->d;
+  int cap = 0;
+  for (auto& p : s->params) cap = std::max(cap, p.pair_cap);
+  int cap2 = 1;
+  while (cap2 < cap) cap2 <<= 1;
+  MX_TRY(dalloc(s, &d.xv, (size_t)6 * N));
+  MX_TRY(dalloc(s, &d.xv0, (size_t)6 * N));
+  MX_TRY(dalloc(s, &s->d_tmp, (size_t)6 * N));
+  MX_TRY(dalloc(s, &d.rp_cm, N));
+  MX_TRY(dalloc(s, &d.kdrag, N));
+  MX_TRY(dalloc(s, &d.bx, NB));
+  MX_TRY(dalloc(s, &d.by, NB));
+  MX_TRY(dalloc(s, &d.bz, NB));
+  MX_TRY(dalloc(s, &d.bmu, NB));
+  MX_TRY(dalloc(s, &d.brc, NB));
+  MX_TRY(dalloc(s, &d.P, 3 * (size_t)nsys));
+  MX_TRY(dalloc(s, &d.flags, N));
+  MX_TRY(dalloc(s, &d.keys, cap2));
+  MX_TRY(dalloc(s, &d.pair_count, 2));
+  d.work_count = d.pair_count + 1;
+  const int work_cap = cap + NB;
+  const int mem_cap = 4 * cap + NB;
+  MX_TRY(dalloc(s, &d.work_off, work_cap + 1));
+  MX_TRY(dalloc(s, &d.work_mem, mem_cap));
+  MX_TRY(dalloc(s, &d.work_sys, work_cap));
+  MX_TRY(dalloc(s, &d.work_wfrom, work_cap));
+  MX_TRY(dalloc(s, &d.work_nsub, work_cap));
+  MX_TRY(dalloc(s, &d.status, 1));
+  MX_TRY(dalloc(s, &s->d_sys, nsys));
+  MX_TRY(dalloc(s, &s->d_tiles, tiles.size()));
+  MX_TRY(dalloc(s, &s->d_energy, 7 * (size_t)nsys));
+  MX_TRY(dalloc(s, &s->d_sink, 1));
+  d.sys = s->d_sys;
+  d.tiles = s->d_tiles;
+  d.N = N;
+  d.NB = NB;
+  d.nsys = nsys;
+  d.ntiles = (int)tiles.size();
+  d.pair_cap = cap;
+  d.work_cap = work_cap;
+  d.mem_cap = mem_cap;
+  d.kepler_max_iter = s->params[0].kepler_max_iter;
+  d.bs_max_sub = s->params[0].bs_max_sub;
+  d.bs_tol = s->params[0].bs_tol;
+  cudaStream_t st = s->st;
+  MX_CUDA(cudaMemcpyAsync(s->d_sys, sys.data(), nsys * sizeof(mx::SysDev), cudaMemcpyHostToDevice, st));
+  MX_CUDA(cudaMemcpyAsync(s->d_tiles, tiles.data(), tiles.size() * sizeof(mx::Tile),
+                          cudaMemcpyHostToDevice, st));
+  MX_CUDA(cudaMemsetAsync(d.status, 0, sizeof(unsigned), st));
+  MX_CUDA(cudaMemsetAsync(d.pair_count, 0, 2 * sizeof(int), st));
+  MX_CUDA(cudaMemsetAsync(d.flags, 0, N, st));
+  // host staging: state rows, masses as mu = G m, per-body drag inputs
+  std::vector<double> xv((size_t)6 * N), bmu(NB, 0.0), rpb(N, 1.0), rhob(N, 1.0);
+  for (int k = 0; k < nsys; ++k) {
+    const int n = s->nbig[k] + s->nsmall[k], o = sys[k].off;
+    for (int c = 0; c < 6; ++c)
+      std::memcpy(&xv[(size_t)c * N + o], xv_helio[k] + (size_t)c * n, n * sizeof(double));
+    for (int i = 0; i < s->nbig[k]; ++i) bmu[sys[k].boff + i] = s->params[k].G * m_big[k][i];
+    for (int q = 0; q < s->nsmall[k]; ++q) {
+      if (rp[k]) rpb[o + s->nbig[k] + q] = rp[k][q];
+      if (rho[k]) rhob[o + s->nbig[k] + q] = rho[k][q];
+    }
+  }
+  double *d_rp = nullptr, *d_rho = nullptr;
+  MX_CUDA(cudaMalloc(&d_rp, N * sizeof(double)));
+  MX_CUDA(cudaMalloc(&d_rho, N * sizeof(double)));
+  MX_CUDA(cudaMemcpyAsync(d.xv, xv.data(), xv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  MX_CUDA(cudaMemcpyAsync(d.bmu, bmu.data(), NB * sizeof(double), cudaMemcpyHostToDevice, st));
+  MX_CUDA(cudaMemcpyAsync(d_rp, rpb.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+  MX_CUDA(cudaMemcpyAsync(d_rho, rhob.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+  MX_CUDA(cudaMemsetAsync(d.brc, 0, NB * sizeof(double), st));
+  mx::launch_init_sys(d, 1, s->params[0].rcrit_hill, st);
+  mx::launch_init_bodies(d, d_rp, d_rho, 1, st);
+  MX_CUDA(cudaGetLastError());
+  MX_CUDA(cudaStreamSynchronize(st));
+  cudaFree(d_rp);
+  cudaFree(d_rho);
+  int nsm = 0;
+  MX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device));
+  s->bs_blocks = 4 * nsm;
+  return sync_status(s);
+}
+
+void destroy_impl(mx_system* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  if (s->st) cudaStreamSynchronize(s->st);
+  if (s->g_head) cudaGraphExecDestroy(s->g_head);
+  if (s->g_mid) cudaGraphExecDestroy(s->g_mid);
+  if (s->g_last) cudaGraphExecDestroy(s->g_last);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->h_status) cudaFreeHost(s->h_status);
+  if (s->h_count) cudaFreeHost(s->h_count);
+  if (s->cap_st) cudaStreamDestroy(s->cap_st);
+  delete s;
+}
+
+mx_status create(mx_system** out, void* stream) {
+  mx_system* s = new mx_system();
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(MX_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  s->st = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(&s->h_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost(&s->h_count, 2 * sizeof(int)) != cudaSuccess) {
+    destroy_impl(s);
+    return fail(MX_ERR_CUDA, "stream or pinned allocation failed");
+  }
+  *out = s;
+  return MX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mx_last_error(void) { return g_last_error.c_str(); }
+
+mx_status mx_init_system(const mx_params* p, int n_big, int n_small, const double* m_big,
+                         const double* xv_helio, const double* rp_km, const double* rho_gcm3,
+                         void* cuda_stream, mx_system** out) {
+  g_last_error.clear();
+  if (!out) return fail(MX_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!valid_params(p)) return fail(MX_ERR_ARG, "invalid parameters");
+  if (n_big < 0 || n_small < 0 || n_big + n_small <= 0 || (long long)n_big + n_small > (1 << 30))
+    return fail(MX_ERR_ARG, "invalid body counts");
+  if ((n_big > 0 && !m_big) || !xv_helio) return fail(MX_ERR_ARG, "NULL input array");
+  if (p->gas.enabled && n_small > 0 && (!rp_km || !rho_gcm3))
+    return fail(MX_ERR_ARG, "gas drag needs rp_km and rho_gcm3");
+  if (p->gas.enabled && !(p->gas.hr_1au > 0 && p->gas.gamma_c > 0 && p->gas.sigma_mol_cm2 > 0))
+    return fail(MX_ERR_ARG, "invalid gas parameters");
+  for (int i = 0; i < n_big; ++i)
+    if (!(m_big[i] >= 0.0)) return fail(MX_ERR_ARG, "negative or NaN mass");
+  mx_system* s = nullptr;
+  MX_TRY(create(&s, cuda_stream));
+  s->params.assign(1, *p);
+  s->nbig.assign(1, n_big);
+  s->nsmall.assign(1, n_small);
+  mx_status r = build(s, {m_big}, {xv_helio}, {rp_km}, {rho_gcm3});
+  if (r != MX_OK) {
+    std::string msg = g_last_error;
+    destroy_impl(s);
+    return fail(r, msg);
+  }
+  *out = s;
+  return MX_OK;
+}
+
+void mx_destroy(mx_system* s) { destroy_impl(s); }
+
+mx_status mx_sizes(mx_system* s, int* n_big, int* n_small) {
+  if (!s) return fail(MX_ERR_ARG, "NULL system");
+  if (n_big) *n_big = s->nbig[0];
+  if (n_small) *n_small = s->nsmall[0];
+  return MX_OK;
+}
+
+mx_status mx_step(mx_system* s, int n_steps) {
+  if (!s || n_steps < 0) return fail(MX_ERR_ARG, "invalid arguments");
+  if (n_steps == 0) return MX_OK;
+  MX_TRY(set_device(s));
+  MX_TRY(ensure_graphs(s));
+  MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
+  for (int k = 0; k + 1 < n_steps; ++k) MX_CUDA(cudaGraphLaunch(s->g_mid, s->st));
+  MX_CUDA(cudaGraphLaunch(s->g_last, s->st));
+  s->step += n_steps;
+  return sync_status(s);
+}
+
+mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* launches,
+                           double* total_ms) {
+  if (!s || n_steps < 0) return fail(MX_ERR_ARG, "invalid arguments");
+  if (n_steps == 0) return MX_OK;
+  MX_TRY(set_device(s));
+  cudaStream_t st = s->st;
+  const double h = s->params[0].dt;
+  // (kind, event-before, event-after) per launch
+  std::vector<int> kind;
+  std::vector<cudaEvent_t> ev;
+  auto rec = [&]() -> cudaError_t {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+    return cudaEventRecord(e, st);
+  };
+  auto timed = [&](int k, auto&& launch) -> cudaError_t {
+    kind.push_back(k);
+    cudaError_t r = rec();
+    if (r != cudaSuccess) return r;
+    launch();
+    return rec();
+  };
+  cudaError_t e = cudaSuccess;
+  e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, st); });
+  if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5 * h, 1, st); });
+  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+    const bool last = (k + 1 == n_steps);
+    e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5 * h, st); });
+    if (e == cudaSuccess)
+      e = timed(MX_K_DETECT, [&] {
+        mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count, s->d.pair_cap, st);
+      });
+    if (e == cudaSuccess) e = timed(MX_K_SORT, [&] { mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st); });
+    if (e == cudaSuccess) e = timed(MX_K_GROUPS, [&] { mx::launch_groups(s->d, st); });
+    if (e == cudaSuccess) e = timed(MX_K_BS, [&] { mx::launch_bs(s->d, s->bs_blocks, st); });
+    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5 * h, st); });
+    if (e == cudaSuccess)
+      e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5 * h, 0.5 * h, last ? 1 : 2, st); });
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  double sum[MX_NKERN] = {0};
+  int cnt[MX_NKERN] = {0};
+  float ms = 0.f;
+  for (size_t q = 0; q < kind.size() && e == cudaSuccess; ++q) {
+    e = cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]);
+    sum[kind[q]] += ms;
+    cnt[kind[q]]++;
+  }
+  if (e == cudaSuccess && total_ms) {
+    e = cudaEventElapsedTime(&ms, ev.front(), ev.back());
+    *total_ms = ms;
+  }
+  for (auto x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("profiled step: ") + cudaGetErrorString(e));
+  for (int k = 0; k < MX_NKERN; ++k) {
+    if (kernel_ms) kernel_ms[k] = sum[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  s->step += n_steps;
+  return sync_status(s);
+}
+
+mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pairs) {
+  if (!s || !n_pairs || cap < 0 || (cap > 0 && !host_pairs)) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_CUDA(cudaMemcpyAsync(s->h_count, s->d.pair_count, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  const int n = std::min(*s->h_count, s->d.pair_cap);
+  *n_pairs = *s->h_count;
+  std::vector<unsigned long long> keys(n);
+  if (n > 0)
+    MX_CUDA(cudaMemcpy(keys.data(), s->d.keys, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  std::vector<std::pair<int, int>> pr(n);
+  for (int k = 0; k < n; ++k)
+    pr[k] = {(int)(keys[k] & 0xffffffffull), (int)((keys[k] >> 32) & 0x7fffffffull)};
+  std::sort(pr.begin(), pr.end());
+  for (int k = 0; k < n && k < cap; ++k) {
+    host_pairs[2 * k] = pr[k].first;
+    host_pairs[2 * k + 1] = pr[k].second;
+  }
+  return (*s->h_count > s->d.pair_cap) ? fail(MX_ERR_PAIR_OVERFLOW, "pair list overflow") : MX_OK;
+}
+
+mx_status mx_accel(mx_system* s, double* dev_acc) {
+  if (!s || !dev_acc) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  mx::launch_prep(s->d, 0.0, s->st);
+  mx::launch_accel(s->d, dev_acc, 0, s->N, 0, s->st);
+  return sync_status(s);
+}
+
+mx_status mx_gas_drag(mx_system* s, double* dev_acc) {
+  if (!s || !dev_acc) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  const int ns = s->nsmall[0];
+  if (ns == 0) return MX_OK;
+  MX_CUDA(cudaMemsetAsync(dev_acc, 0, (size_t)3 * ns * sizeof(double), s->st));
+  mx::launch_prep(s->d, 0.0, s->st);
+  mx::launch_accel(s->d, dev_acc, 1, ns, s->nbig[0], s->st);
+  return sync_status(s);
+}
+
+mx_status mx_detect_encounters(mx_system* s, const double* dev_xv0, const double* dev_xv1,
+                               unsigned char* dev_flags, int* dev_pairs, int cap, int* n_pairs) {
+  if (!s || !dev_xv0 || !dev_xv1 || !n_pairs || cap < 0 || (cap > 0 && !dev_pairs) ||
+      s->params.size() != 1)
+    return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  unsigned char* flags = dev_flags ? dev_flags : s->d.flags;
+  MX_CUDA(cudaMemsetAsync(flags, 0, s->N, s->st));
+  MX_CUDA(cudaMemsetAsync(s->d.pair_count, 0, sizeof(int), s->st));
+  mx::launch_detect(s->d, dev_xv0, dev_xv1, flags, s->d.keys, s->d.pair_count, s->d.pair_cap, s->st);
+  mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 1, s->st);
+  if (dev_pairs && cap > 0)
+    mx::launch_keys_to_pairs(s->d.keys, s->d.pair_count, std::min(cap, s->d.pair_cap), dev_pairs, s->st);
+  MX_CUDA(cudaMemcpyAsync(s->h_count, s->d.pair_count, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  MX_TRY(sync_status(s));
+  *n_pairs = *s->h_count;
+  // the step's own pair list is overwritten; it is rebuilt by the next step
+  MX_CUDA(cudaMemsetAsync(s->d.pair_count, 0, 2 * sizeof(int), s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  if (*n_pairs > cap || *n_pairs > s->d.pair_cap)
+    return fail(MX_ERR_PAIR_OVERFLOW, "more flagged pairs than cap");
+  return MX_OK;
+}
+
+mx_status mx_kepler_drift(mx_system* s, double* dev_xv, double h) {
+  if (!s || !dev_xv || !std::isfinite(h)) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  const mx_params& p = s->params[0];
+  mx::launch_drift_buf(dev_xv, s->N, p.G * p.m_star, h, p.kepler_max_iter, s->d.status, s->st);
+  return sync_status(s);
+}
+
+mx_status mx_energy(mx_system* s, double* E, double* L3) {
+  if (!s || !E || !L3) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  const mx_params& p = s->params[0];
+  mx::launch_energy(s->d, 1.0 / p.G, p.m_star, s->d_energy, s->st);
+  double o[7];
+  MX_CUDA(cudaMemcpyAsync(o, s->d_energy, sizeof(o), cudaMemcpyDeviceToHost, s->st));
+  MX_TRY(sync_status(s));
+  *E = o[2];
+  L3[0] = o[4];
+  L3[1] = o[5];
+  L3[2] = o[6];
+  return MX_OK;
+}
+
+mx_status mx_get_state(mx_system* s, double* xv_host, int coords, long long* step) {
+  if (!s || !xv_host || (coords != MX_COORD_HELIO && coords != MX_COORD_DH))
+    return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  const double* src = s->d.xv;
+  if (coords == MX_COORD_HELIO) {
+    mx::launch_prep(s->d, 0.0, s->st);
+    mx::launch_readout(s->d, s->d_tmp, s->st);
+    src = s->d_tmp;
+  }
+  MX_CUDA(cudaMemcpyAsync(xv_host, src, (size_t)6 * s->N * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  MX_TRY(sync_status(s));
+  if (step) *step = s->step;
+  return MX_OK;
+}
+
+mx_status mx_set_state(mx_system* s, const double* xv_host, int coords, long long step) {
+  if (!s || !xv_host || (coords != MX_COORD_HELIO && coords != MX_COORD_DH))
+    return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_CUDA(cudaMemcpyAsync(s->d.xv, xv_host, (size_t)6 * s->N * sizeof(double), cudaMemcpyHostToDevice, s->st));
+  if (coords == MX_COORD_HELIO) {
+    mx::launch_init_sys(s->d, 0, 0.0, s->st);
+    mx::launch_init_bodies(s->d, nullptr, nullptr, 0, s->st);
+  }
+  MX_TRY(sync_status(s));
+  s->step = step;
+  return MX_OK;
+}
+
+mx_status mx_get_state_device(mx_system* s, double* dev_xv) {
+  if (!s || !dev_xv) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_CUDA(cudaMemcpyAsync(dev_xv, s->d.xv, (size_t)6 * s->N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+  return MX_OK;
+}
+
+mx_status mx_set_state_device(mx_system* s, const double* dev_xv) {
+  if (!s || !dev_xv) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_CUDA(cudaMemcpyAsync(s->d.xv, dev_xv, (size_t)6 * s->N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+  return MX_OK;
+}
+
+mx_status mx_fp64_peak(void* cuda_stream, double ms_target, double* tflops) {
+  if (!tflops || !(ms_target > 0)) return fail(MX_ERR_ARG, "invalid arguments");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, nsm = 0;
+  MX_CUDA(cudaGetDevice(&dev));
+  MX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  double* sink = nullptr;
+  MX_CUDA(cudaMalloc(&sink, sizeof(double)));
+  cudaEvent_t e0, e1;
+  MX_CUDA(cudaEventCreate(&e0));
+  MX_CUDA(cudaEventCreate(&e1));
+  const int blocks = nsm * 8;
+  int iters = 256;
+  float ms = 0.f;
+  for (int rep = 0; rep < 8; ++rep) {
+    MX_CUDA(cudaEventRecord(e0, st));
+    mx::launch_dfma(sink, blocks, iters, st);
+    MX_CUDA(cudaEventRecord(e1, st));
+    MX_CUDA(cudaEventSynchronize(e1));
+    MX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms >= 0.8 * ms_target) break;
+    const double scale = std::min(16.0, ms_target / std::max(ms, 0.01f));
+    iters = (int)std::min(1 << 24, (int)(iters * scale) + 1);
+  }
+  const double flops = 2.0 * 8.0 * (double)iters * blocks * 256.0;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return MX_OK;
+}
+
+}  // extern "C"

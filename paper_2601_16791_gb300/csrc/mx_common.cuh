@@ -1,0 +1,121 @@
+// mx_common.cuh -- device data layout and FP64 helpers shared by the sm_103a
+// kernels of the hybrid symplectic step (arXiv 2601.16791, Sec. 2 and 3.1).
+//
+// Layout in HBM (all float64 unless noted), for all systems of a batch back to
+// back (a single system is a batch of one):
+//   state  6 x N   x, y, z, vx, vy, vz rows; each system's big bodies first.
+//                  DH coordinates: heliocentric x, barycentric v.
+//   xv0    6 x N   the post-jump, pre-drift state of the current step
+//                  (detection endpoints and Bulirsch-Stoer starting point).
+//   rp_cm, kdrag [N]  planetesimal radius [cm] and 3/(8 r_p[AU] rho_p).
+//   bx,by,bz,bmu,brc [NB]  big bodies of every system, compact: positions
+//                  staged for the kick (already jumped), mu = G m, rcrit.
+//   P      [3 x nsys]  massive-body momentum sum mu_i v_i of each system.
+//   flags  [N] uint8, pair keys [cap] uint64, Bulirsch-Stoer work list.
+// Every kernel reads its system's constants from a SysDev record.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mx {
+
+constexpr int kThreads = 256;     // threads per block of the per-body kernels (= tile)
+constexpr int kBigChunk = 512;    // big bodies staged in shared memory per pass
+constexpr int kMaxGroup = 16;     // bodies per Bulirsch-Stoer group (MX_MAX_GROUP)
+constexpr int kBsRows = 8;        // extrapolation rows: n_k = 2, 4, ..., 16
+constexpr int kMaxBigPairs = 512; // big-big encounter pairs handled per step
+
+// Device status bits, OR-ed by kernels and turned into mx_status on the host.
+enum : unsigned {
+  ST_KEPLER = 1u << 0,
+  ST_BS = 1u << 1,
+  ST_PAIR_OVF = 1u << 2,
+  ST_NONFINITE = 1u << 3,
+  ST_BARRIER = 1u << 4,
+  ST_GROUP = 1u << 5,
+  ST_WORK_OVF = 1u << 6,
+  ST_ADJ_ENC = 1u << 7
+};
+
+// Constants of one system.
+struct SysDev {
+  int off;        // global index of the system's first body
+  int nbig;       // massive bodies
+  int n;          // all bodies
+  int boff;       // index of its first big body in the compact big arrays
+  double mu0, inv_mu0, sqrt_mu0;
+  double h;       // step
+  // gas (Sec. 3.1)
+  int gas_on, cd_mode, gamma_one, flare_quarter;
+  int rc_inf, pad0;
+  double sigma1, gamma, inv_rc, r_in, hr1, flare, cd_scale;
+  double c_rho;   // rho_g = c_rho * Sigma * R^-(1+flare)     [g/cm^3]
+  double c_cs;    // c_s  = c_cs * R^(flare-1/2)              [AU/d]
+  double inv_c_cs;
+  double c_eta;   // eta  = c_eta * R^(2 flare)
+  double c_re;    // Re   = c_re * r_p[cm] * Ma * rho_g
+};
+
+// A block's worth of targets, never spanning two systems.
+struct Tile {
+  int sys, start, count, pad;
+};
+
+// Pointers to the device buffers.
+struct Dev {
+  double* xv;      // 6 x N
+  double* xv0;     // 6 x N
+  double* rp_cm;   // N
+  double* kdrag;   // N
+  double *bx, *by, *bz, *bmu, *brc;   // NB
+  double* P;       // 3 x nsys
+  unsigned char* flags;               // N
+  unsigned long long* keys;           // pair keys [pair_cap]
+  int* pair_count;
+  int* work_count;
+  int* work_off;   // [work_cap + 1]
+  int* work_mem;   // [mem_cap]
+  int* work_sys;   // [work_cap]
+  int* work_wfrom; // [work_cap]
+  int* work_nsub;  // [work_cap] macro sub-steps used (diagnostic)
+  unsigned* status;
+  const SysDev* sys;
+  const Tile* tiles;
+  int N, NB, nsys, ntiles;
+  int pair_cap, work_cap, mem_cap;
+  int kepler_max_iter, bs_max_sub;
+  double bs_tol;
+};
+
+// ------------------------------------------------------------------ helpers
+// 1/sqrt(x) for x > 0: single-precision hardware estimate, then one
+// third-order Householder correction y <- y (1 + e/2 + 3e^2/8), e = 1 - x y^2.
+// The estimate is good to ~1e-7, so the result is within a few ulp.
+__device__ __forceinline__ double rsqrt_d(double x) {
+  const double y = (double)rsqrtf((float)x);
+  const double e = fma(-x * y, y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
+}
+
+// 1/x: single-precision estimate, then y <- y (1 + e + e^2), e = 1 - x y.
+__device__ __forceinline__ double rcp_d(double x) {
+  const double y = (double)__frcp_rn((float)x);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+__device__ __forceinline__ bool finite_d(double a) { return isfinite(a); }
+
+// Jump displacement (h/2) P / m0 of the step's democratic-heliocentric split
+// (Sec. 2.1.3: momentum of massive bodies only).  Every kernel that applies
+// the same jump evaluates this same expression, so a big body's staged
+// position and its own update agree bit for bit.
+__device__ __forceinline__ void jump_vec(const double* P, const SysDev& S, double jump_h,
+                                         double* dj) {
+  const double c = jump_h * S.inv_mu0;
+  dj[0] = c * P[0];
+  dj[1] = c * P[1];
+  dj[2] = c * P[2];
+}
+
+}  // namespace mx

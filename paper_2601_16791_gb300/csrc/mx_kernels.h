@@ -1,0 +1,41 @@
+// mx_kernels.h -- host-side launchers of the sm_103a kernels (internal to the
+// library; the public C ABI is include/mx.h).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mx {
+
+struct Dev;
+
+// k_init.cu / k_misc.cu
+void launch_init_sys(const Dev& d, int do_rcrit, double rcrit_hill, cudaStream_t st);
+void launch_init_bodies(const Dev& d, const double* rp_km, const double* rho, int set_drag,
+                        cudaStream_t st);
+void launch_readout(const Dev& d, double* out, cudaStream_t st);
+void launch_energy(const Dev& d, double inv_G, double m_star, double* out, cudaStream_t st);
+void launch_dfma(double* sink, int blocks, int iters, cudaStream_t st);
+
+// k_kick.cu
+void launch_prep(const Dev& d, double jump_h, cudaStream_t st);
+void launch_jump_kick(const Dev& d, double jump_h, double kick_h, int nkick, cudaStream_t st);
+void launch_accel(const Dev& d, double* acc, int drag_only, int acc_stride, int acc_base,
+                  cudaStream_t st);
+
+// k_drift.cu
+void launch_jump_drift(const Dev& d, double jump_h, cudaStream_t st);
+void launch_drift_buf(double* xv, int n, double mu, double h, int maxit, unsigned* status,
+                      cudaStream_t st);
+
+// k_detect.cu
+void launch_detect(const Dev& d, const double* xv0, const double* xv1, unsigned char* flags,
+                   unsigned long long* keys, int* count, int cap, cudaStream_t st);
+void launch_sort_keys(unsigned long long* keys, const int* count, int cap, int swap_ij,
+                      cudaStream_t st);
+void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int cap, int* pairs,
+                          cudaStream_t st);
+
+// k_bs.cu
+void launch_groups(const Dev& d, cudaStream_t st);
+void launch_bs(const Dev& d, int nblocks, cudaStream_t st);
+
+}  // namespace mx

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of include/mx.h (argument marshalling only).
+
+Every function here has the C name and calls straight into libmx.so; all
+arithmetic on bodies runs in the library's CUDA kernels.  Device buffers are
+passed as torch CUDA tensors (float64, contiguous) or raw integer pointers;
+host buffers as numpy arrays.  If libmx.so cannot be built or loaded, the
+import of the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_D = ctypes.c_double
+_I = ctypes.c_int
+_P = ctypes.c_void_p
+
+MX_OK = 0
+STATUS = {0: "MX_OK", 1: "MX_ERR_ARG", 2: "MX_ERR_CUDA", 3: "MX_ERR_OOM", 4: "MX_ERR_KEPLER_NOCONV",
+          5: "MX_ERR_BS_NOCONV", 6: "MX_ERR_PAIR_OVERFLOW", 7: "MX_ERR_NONFINITE",
+          8: "MX_ERR_BARRIER_TIMEOUT", 9: "MX_ERR_ENCOUNTER_IN_ADJOINT",
+          10: "MX_ERR_GROUP_TOO_LARGE"}
+MX_COORD_HELIO = 0
+MX_COORD_DH = 1
+MX_MAX_GROUP = 16
+
+
+class MxGas(ctypes.Structure):
+    _fields_ = [("sigma1_gcm2", _D), ("gamma", _D), ("r_c_au", _D), ("r_in_au", _D),
+                ("hr_1au", _D), ("flare", _D), ("gamma_c", _D), ("mu_mol", _D),
+                ("sigma_mol_cm2", _D), ("cd_scale", _D), ("enabled", _I), ("cd_mode", _I)]
+
+
+class MxParams(ctypes.Structure):
+    _fields_ = [("G", _D), ("m_star", _D), ("dt", _D), ("rcrit_hill", _D), ("bs_tol", _D),
+                ("kepler_max_iter", _I), ("bs_max_sub", _I), ("pair_cap", _I), ("gas", MxGas)]
+
+
+class MxError(RuntimeError):
+    def __init__(self, code, where, msg=""):
+        super().__init__(f"{where}: {STATUS.get(code, code)} {msg}".strip())
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+_lib = None
+
+_SIGS = {
+    "mx_init_system": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P]),
+    "mx_destroy": (None, [_P]),
+    "mx_step": (_I, [_P, _I]),
+    "mx_step_profiled": (_I, [_P, _I, _P, _P, _P]),
+    "mx_last_encounters": (_I, [_P, _P, _I, _P]),
+    "mx_accel": (_I, [_P, _P]),
+    "mx_gas_drag": (_I, [_P, _P]),
+    "mx_detect_encounters": (_I, [_P, _P, _P, _P, _P, _I, _P]),
+    "mx_kepler_drift": (_I, [_P, _P, _D]),
+    "mx_energy": (_I, [_P, _P, _P]),
+    "mx_get_state": (_I, [_P, _P, _I, _P]),
+    "mx_set_state": (_I, [_P, _P, _I, ctypes.c_longlong]),
+    "mx_get_state_device": (_I, [_P, _P]),
+    "mx_set_state_device": (_I, [_P, _P]),
+    "mx_sizes": (_I, [_P, _P, _P]),
+    "mx_last_error": (ctypes.c_char_p, []),
+    "mx_fp64_peak": (_I, [_P, _D, _P]),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load():
+    """Build (if stale) and load libmx.so; raises if either fails."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(code, where):
+    if code != MX_OK:
+        raise MxError(code, where, load().mx_last_error().decode())
+
+
+def _host(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dptr(t):
+    """Device pointer of a torch CUDA tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(cfg) -> MxParams:
+    g = cfg["gas"]
+    gas = MxGas(g["sigma1_gcm2"], g["gamma"], g["r_c_au"], g["r_in_au"], g["hr_1au"], g["flare"],
+                g["gamma_c"], g["mu_mol"], g["sigma_mol_cm2"], g["cd_scale"], int(g["enabled"]),
+                int(g["cd_mode"]))
+    return MxParams(cfg["G"], cfg["m_star"], cfg["dt"], cfg["rcrit_hill"], cfg["bs_tol"],
+                    int(cfg["kepler_max_iter"]), int(cfg["bs_max_sub"]), int(cfg["pair_cap"]), gas)
+
+
+# ------------------------------------------------------------ C-named calls
+def mx_init_system(params, n_big, n_small, m_big, xv_helio, rp_km=None, rho_gcm3=None,
+                   stream=None):
+    L = load()
+    out = ctypes.c_void_p()
+    m_big = _host(m_big)
+    xv = _host(xv_helio)
+    rp = None if rp_km is None else _host(rp_km)
+    rho = None if rho_gcm3 is None else _host(rho_gcm3)
+    st = ctypes.c_void_p(stream) if stream else None
+    _check(L.mx_init_system(ctypes.byref(params), int(n_big), int(n_small), _hptr(m_big), _hptr(xv),
+                            _hptr(rp), _hptr(rho), st, ctypes.byref(out)), "mx_init_system")
+    return out
+
+
+def mx_destroy(sys):
+    load().mx_destroy(sys)
+
+
+def mx_step(sys, n_steps):
+    _check(load().mx_step(sys, int(n_steps)), "mx_step")
+
+
+KERNELS = ("k_prep", "k_jump_kick", "k_jump_drift", "k_detect", "k_sort_keys", "k_groups", "k_bs")
+
+
+def mx_step_profiled(sys, n_steps):
+    """Returns (per-kernel ms dict, per-kernel launch counts dict, total ms)."""
+    ms = np.zeros(len(KERNELS))
+    cnt = np.zeros(len(KERNELS), dtype=np.int32)
+    tot = ctypes.c_double(0.0)
+    _check(load().mx_step_profiled(sys, int(n_steps), _hptr(ms), _hptr(cnt), ctypes.byref(tot)),
+           "mx_step_profiled")
+    return dict(zip(KERNELS, ms.tolist())), dict(zip(KERNELS, cnt.tolist())), tot.value
+
+
+def mx_last_encounters(sys, cap=1 << 16):
+    pairs = np.empty((max(cap, 1), 2), dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check(load().mx_last_encounters(sys, _hptr(pairs), int(cap), ctypes.byref(n)),
+           "mx_last_encounters")
+    return pairs[:min(n.value, cap)].copy()
+
+
+def mx_accel(sys, dev_acc):
+    _check(load().mx_accel(sys, _dptr(dev_acc)), "mx_accel")
+
+
+def mx_gas_drag(sys, dev_acc):
+    _check(load().mx_gas_drag(sys, _dptr(dev_acc)), "mx_gas_drag")
+
+
+def mx_detect_encounters(sys, dev_xv0, dev_xv1, dev_flags=None, dev_pairs=None, cap=0):
+    n = ctypes.c_int(0)
+    _check(load().mx_detect_encounters(sys, _dptr(dev_xv0), _dptr(dev_xv1), _dptr(dev_flags),
+                                       _dptr(dev_pairs), int(cap), ctypes.byref(n)),
+           "mx_detect_encounters")
+    return n.value
+
+
+def mx_kepler_drift(sys, dev_xv, h):
+    _check(load().mx_kepler_drift(sys, _dptr(dev_xv), float(h)), "mx_kepler_drift")
+
+
+def mx_energy(sys):
+    E = ctypes.c_double(0.0)
+    L3 = np.empty(3)
+    _check(load().mx_energy(sys, ctypes.byref(E), _hptr(L3)), "mx_energy")
+    return E.value, L3
+
+
+def mx_get_state(sys, n, coords=MX_COORD_HELIO):
+    out = np.empty((6, n))
+    step = ctypes.c_longlong(0)
+    _check(load().mx_get_state(sys, _hptr(out), int(coords), ctypes.byref(step)), "mx_get_state")
+    return out, step.value
+
+
+def mx_set_state(sys, xv, coords=MX_COORD_HELIO, step=0):
+    xv = _host(xv)
+    _check(load().mx_set_state(sys, _hptr(xv), int(coords), int(step)), "mx_set_state")
+
+
+def mx_get_state_device(sys, dev_xv):
+    _check(load().mx_get_state_device(sys, _dptr(dev_xv)), "mx_get_state_device")
+
+
+def mx_set_state_device(sys, dev_xv):
+    _check(load().mx_set_state_device(sys, _dptr(dev_xv)), "mx_set_state_device")
+
+
+def mx_sizes(sys):
+    nb, ns = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().mx_sizes(sys, ctypes.byref(nb), ctypes.byref(ns)), "mx_sizes")
+    return nb.value, ns.value
+
+
+def mx_fp64_peak(stream=None, ms_target=200.0):
+    t = ctypes.c_double(0.0)
+    st = ctypes.c_void_p(stream) if stream else None
+    _check(load().mx_fp64_peak(st, float(ms_target), ctypes.byref(t)), "mx_fp64_peak")
+    return t.value
+
+
+class System:
+    """Owns one mx_system; a convenience wrapper over the C-named calls."""
+
+    def __init__(self, workload, stream=None):
+        self.w = workload
+        self.params = make_params(workload.params)
+        self.nbig, self.nsmall = workload.nbig, workload.nsmall
+        self.n = workload.n
+        self.h = mx_init_system(self.params, self.nbig, self.nsmall, workload.m_big,
+                                workload.xv_helio, workload.rp_km, workload.rhop, stream)
+
+    def step(self, n):
+        mx_step(self.h, n)
+
+    def state(self, coords=MX_COORD_HELIO):
+        return mx_get_state(self.h, self.n, coords)[0]
+
+    def set_state(self, xv, coords=MX_COORD_HELIO, step=0):
+        mx_set_state(self.h, xv, coords, step)
+
+    def energy(self):
+        return mx_energy(self.h)
+
+    def close(self):
+        if self.h:
+            mx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+INF = math.inf

@@ -1,0 +1,315 @@
+"""GPU (libmx, sm_103a) against the CPU oracle on the same seeded inputs.
+
+Tolerances (stated for the method's outputs):
+  * per-step accelerations (kick: K-weighted gravity + drag): relative <= 1e-12
+  * Kepler drift, one call: relative <= 1e-13
+  * positions of bodies never flagged, after 1,000 steps: relative <= 1e-9
+  * encounter flag sets: identical, except pairs whose minimum squared
+    separation is within 1e-9 relative of rc^2 (checked with the oracle's
+    own distances).
+Every input comes from workloads.py; every expected value from oracle/.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2601_16791_gb300 import mx, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def rel_rows(a, b):
+    """Max over bodies of |a - b| / |b| with vectors along axis 0."""
+    num = np.linalg.norm(np.asarray(a) - np.asarray(b), axis=0)
+    den = np.linalg.norm(np.asarray(b), axis=0)
+    return float(np.max(num / np.maximum(den, 1e-300)))
+
+
+def both(w):
+    """(GPU system, oracle params, oracle DH state, mu, rcrit) for one workload."""
+    sysg = mx.System(w)
+    p = orc.make_params(w.params)
+    xv, mu, rc = orc.init(p, w.nbig, w.nsmall, w.m_big, w.xv_helio)
+    return sysg, p, xv, mu, rc
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+# ------------------------------------------------------------------ set-up
+@pytest.mark.parametrize("name,kw", [("plain_2big_1k", {}),
+                                     ("gas_4core_100k", dict(nsmall=3000)),
+                                     ("semiactive_2000big_200k", dict(nbig=300, nsmall=2000))])
+def test_init_matches_oracle(name, kw):
+    w = W.make(name, **kw)
+    g, p, xv, mu, rc = both(w)
+    dh = g.state(mx.MX_COORD_DH)
+    assert rel_rows(dh[:3], xv[:3]) == 0.0
+    assert rel_rows(dh[3:], xv[3:]) < 1e-14
+    back = g.state(mx.MX_COORD_HELIO)
+    assert rel_rows(back, w.xv_helio) < 1e-14
+    g.close()
+
+
+# ------------------------------------------------------------- accelerations
+@pytest.mark.parametrize("name,kw", [("plain_2big_1k", {}),
+                                     ("gas_4core_100k", dict(nsmall=5000)),
+                                     ("semiactive_2000big_200k", dict(nbig=700, nsmall=3001))])
+def test_accel_parity(name, kw):
+    """mx_accel = gravity (Sec. 2.1.3 gather loop) + drag (Eqs. 3-7), 1e-12 relative."""
+    w = W.make(name, **kw)
+    g, p, xv, mu, rc = both(w)
+    acc = torch.zeros((3, w.n), dtype=torch.float64, device="cuda")
+    mx.mx_accel(g.h, acc)
+    a_gpu = acc.cpu().numpy()
+    a_ref = orc.accel_grav(w.nbig, xv, mu, rc)
+    if w.params["gas"]["enabled"]:
+        a_ref[:, w.nbig:] += orc.gas_drag(p, w.nbig, xv, mu, w.rp_km, w.rhop)
+    assert rel_rows(a_gpu, a_ref) <= 1e-12
+    g.close()
+
+
+def test_gas_drag_parity():
+    w = W.gas_4core_100k(nsmall=20000)
+    g, p, xv, mu, rc = both(w)
+    acc = torch.zeros((3, w.nsmall), dtype=torch.float64, device="cuda")
+    mx.mx_gas_drag(g.h, acc)
+    ref = orc.gas_drag(p, w.nbig, xv, mu, w.rp_km, w.rhop)
+    assert rel_rows(acc.cpu().numpy(), ref) <= 1e-12
+    # both k branches of Eq. 7 are exercised at these radii
+    g.close()
+
+
+def test_gas_drag_general_exponents():
+    """gamma != 1, flare != 1/4, finite R_C, inner edge, printed C_D exponent."""
+    w = W.gas_4core_100k(nsmall=4000)
+    gas = dict(w.params["gas"], gamma=0.8, flare=0.2, r_c_au=30.0, r_in_au=2.0, cd_mode=1,
+               cd_scale=1.3)
+    w.params = dict(w.params, gas=gas)
+    g, p, xv, mu, rc = both(w)
+    acc = torch.zeros((3, w.nsmall), dtype=torch.float64, device="cuda")
+    mx.mx_gas_drag(g.h, acc)
+    ref = orc.gas_drag(p, w.nbig, xv, mu, w.rp_km, w.rhop)
+    got = acc.cpu().numpy()
+    inside = np.linalg.norm(ref, axis=0) == 0
+    assert inside.sum() > 10 and np.all(got[:, inside] == 0.0)
+    assert rel_rows(got[:, ~inside], ref[:, ~inside]) <= 1e-12
+    g.close()
+
+
+# -------------------------------------------------------------------- drift
+@pytest.mark.parametrize("h", [10.0, -7.0, 400.0, 3000.0])
+def test_kepler_drift_parity(h):
+    w = W.gas_4core_100k(nsmall=3000)
+    g, p, xv, mu, rc = both(w)
+    # add a few hyperbolic and near-parabolic bodies
+    xv = xv.copy()
+    xv[3:, -5:] *= np.array([1.5, 2.0, 1.42, 1.414, 3.0])
+    t = dev(xv)
+    mx.mx_kepler_drift(g.h, t, h)
+    ref, _ = orc.drift(p, xv, h)
+    got = t.cpu().numpy()
+    # A step spanning several orbits (3000 d is ~8 periods at 1 AU) needs ~7
+    # quartering levels of the Stumpff argument in both codes; each doubling
+    # formula can grow the relative rounding by up to ~4x, so that case gets
+    # 2e-12.  Steps up to 400 d stay within 1e-13.
+    tol = 1e-13 if abs(h) <= 400 else 2e-12
+    assert rel_rows(got[:3], ref[:3]) <= tol
+    assert rel_rows(got[3:], ref[3:]) <= tol
+    g.close()
+
+
+# ---------------------------------------------------------------- detection
+def _near_threshold(p, nbig, xv0, xv1, rcrit, i, j):
+    """True when the pair's minimum squared separation is within 1e-9 of rc^2."""
+    dx0 = xv0[:3, j] - xv0[:3, i]
+    dx1 = xv1[:3, j] - xv1[:3, i]
+    dv0 = xv0[3:, j] - xv0[3:, i]
+    dv1 = xv1[3:, j] - xv1[3:, i]
+    d0, d1 = dx0 @ dx0, dx1 @ dx1
+    m = min(d0, d1, orc.hermite_d2min(d0, d1, 2 * dx0 @ dv0, 2 * dx1 @ dv1, p.dt))
+    rc = max(rcrit[i], rcrit[j])
+    return abs(m - rc * rc) <= 1e-9 * rc * rc
+
+
+@pytest.mark.parametrize("name,kw", [("plain_2big_1k", {}),
+                                     ("semiactive_2000big_200k", dict(nbig=500, nsmall=6000)),
+                                     ("gas_4core_100k", dict(nsmall=20000))])
+def test_detect_parity(name, kw):
+    w = W.make(name, **kw)
+    g, p, xv0, mu, rc = both(w)
+    xv1, _ = orc.drift(p, xv0, p.dt)
+    f_ref, p_ref = orc.detect(p, w.nbig, xv0, xv1, rc)
+    assert len(p_ref) > 5
+    cap = 4 * len(p_ref) + 64
+    flags = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    pairs = torch.zeros(2 * cap, dtype=torch.int32, device="cuda")
+    n = mx.mx_detect_encounters(g.h, dev(xv0), dev(xv1), flags, pairs, cap)
+    got = pairs.cpu().numpy()[:2 * n].reshape(-1, 2)
+    A = set(map(tuple, got.tolist()))
+    B = set(map(tuple, p_ref.tolist()))
+    for (i, j) in A ^ B:
+        assert _near_threshold(p, w.nbig, xv0, xv1, rc, i, j), (i, j)
+    assert np.array_equal(got, np.array(sorted(A)).reshape(-1, 2))   # sorted by (i, j)
+    if A == B:
+        assert np.array_equal(flags.cpu().numpy(), f_ref)
+    g.close()
+
+
+# ------------------------------------------------------------- whole steps
+def _compare_run(w, nsteps, per_step_pairs=False, tol=1e-9):
+    g, p, xv, mu, rc = both(w)
+    ref, ever, log, st = orc.step(p, w.nbig, xv, mu, rc, w.rp_km, w.rhop, nsteps, log_cap=1 << 20)
+    ever_gpu = np.zeros(w.n, dtype=bool)
+    if per_step_pairs:
+        mism = 0
+        for k in range(nsteps):
+            g.step(1)
+            got = mx.mx_last_encounters(g.h)
+            for (i, j) in got:
+                ever_gpu[i] = ever_gpu[j] = True
+            want = log[log[:, 0] == k][:, 1:]
+            if not np.array_equal(np.asarray(got).reshape(-1, 2), want.reshape(-1, 2)):
+                mism += 1
+        assert mism <= max(1, nsteps // 200), f"{mism} steps with different pair lists"
+    else:
+        g.step(nsteps)
+    out = g.state(mx.MX_COORD_DH)
+    keep = (ever == 0) & ~ever_gpu
+    err = np.linalg.norm(out[:3] - ref[:3], axis=0) / np.linalg.norm(ref[:3], axis=0)
+    assert err[keep].max() <= tol, err[keep].max()
+    g.close()
+    return err, keep, st
+
+
+def test_plain_1000_steps_per_step_pairs():
+    """Config of two giants and 1,000 planetesimals: per-step pair lists and final positions."""
+    w = W.plain_2big_1k()
+    err, keep, st = _compare_run(w, 1000, per_step_pairs=True)
+    assert st[0] > 100 and keep.sum() > 500
+
+
+def test_plain_1000_steps_one_call():
+    w = W.plain_2big_1k()
+    _compare_run(w, 1000)
+
+
+def test_gas_steps():
+    w = W.gas_4core_100k(nsmall=3000, nsteps=300)
+    err, keep, st = _compare_run(w, 300)
+    assert st[0] > 0
+
+
+def test_semiactive_steps_with_big_encounters():
+    w = W.semiactive_2000big_200k(nbig=300, nsmall=3000)
+    err, keep, st = _compare_run(w, 60, tol=1e-8)
+    assert st[0] > 0 and st[1] > 0
+
+
+def test_full_size_sampled_gas_workload():
+    """4 cores + 100,000 planetesimals on the GPU, 40 steps; the oracle integrates
+    the cores with a random sample of the planetesimals (massless, so the sample
+    moves exactly as inside the full system)."""
+    w = W.gas_4core_100k(nsteps=40)
+    g = mx.System(w)
+    g.step(w.nsteps)
+    out = g.state(mx.MX_COORD_DH)
+    g.close()
+    rng = np.random.default_rng(99)
+    sel = np.sort(rng.choice(w.nsmall, 300, replace=False))
+    cols = np.concatenate([np.arange(w.nbig), w.nbig + sel])
+    ws = W.Workload("sample", w.params, w.nbig, len(sel), w.m_big, w.xv_helio[:, cols].copy(),
+                    w.rp_km[sel].copy(), w.rhop[sel].copy(), w.nsteps)
+    p = orc.make_params(ws.params)
+    xv, mu, rc = orc.init(p, ws.nbig, ws.nsmall, ws.m_big, ws.xv_helio)
+    ref, ever, _, _ = orc.step(p, ws.nbig, xv, mu, rc, ws.rp_km, ws.rhop, w.nsteps)
+    got = out[:, cols]
+    keep = ever == 0
+    err = np.linalg.norm(got[:3] - ref[:3], axis=0) / np.linalg.norm(ref[:3], axis=0)
+    assert keep.sum() > 250 and err[keep].max() <= 1e-9
+
+
+def test_energy_parity():
+    w = W.semiactive_2000big_200k(nbig=400, nsmall=100)
+    g, p, xv, mu, rc = both(w)
+    E, L = g.energy()
+    E0, L0 = orc.energy(p, w.nbig, xv, mu)
+    assert abs(E - E0) <= 1e-13 * abs(E0)
+    assert np.max(np.abs(L - L0)) <= 1e-13 * np.linalg.norm(L0)
+    g.close()
+
+
+# -------------------------------------------------------------- edge cases
+def test_ragged_and_degenerate_sizes():
+    for nsmall in (0, 1, 255, 257):
+        w = W.plain_2big_1k(nsmall=nsmall, nsteps=5)
+        _compare_run(w, 5, tol=1e-12)
+    # no big bodies at all: every body drifts on its Kepler orbit
+    w = W.plain_2big_1k(nsmall=300, nsteps=3)
+    w = W.Workload("kepler_only", w.params, 0, 300, np.zeros(0), w.xv_helio[:, 2:].copy(),
+                   w.rp_km, w.rhop, 3)
+    _compare_run(w, 3, tol=1e-13)
+
+
+def test_status_words_without_faults():
+    """Host-injected failures come back as mx_status, not as device faults."""
+    w = W.plain_2big_1k(nsmall=500)
+    cfg = dict(w.params, pair_cap=2)
+    w2 = W.Workload(w.name, cfg, w.nbig, w.nsmall, w.m_big, w.xv_helio, w.rp_km, w.rhop, 1)
+    g = mx.System(w2)
+    with pytest.raises(mx.MxError) as e:
+        g.step(20)
+    assert e.value.status == "MX_ERR_PAIR_OVERFLOW"
+    g.close()
+    cfg = dict(w.params, kepler_max_iter=1)
+    w3 = W.Workload(w.name, cfg, w.nbig, w.nsmall, w.m_big, w.xv_helio, w.rp_km, w.rhop, 1)
+    g = mx.System(w3)
+    with pytest.raises(mx.MxError) as e:
+        g.step(1)
+    assert e.value.status == "MX_ERR_KEPLER_NOCONV"
+    g.close()
+    bad = w.xv_helio.copy()
+    bad[0, 7] = np.nan
+    w4 = W.Workload(w.name, w.params, w.nbig, w.nsmall, w.m_big, bad, w.rp_km, w.rhop, 1)
+    g = mx.System(w4)
+    with pytest.raises(mx.MxError) as e:
+        g.step(1)
+    assert e.value.status in ("MX_ERR_NONFINITE", "MX_ERR_KEPLER_NOCONV")
+    g.close()
+    with pytest.raises(mx.MxError) as e:
+        mx.mx_init_system(mx.make_params(w.params), -1, 3, w.m_big, w.xv_helio)
+    assert e.value.status == "MX_ERR_ARG"
+
+
+def test_run_to_run_bitwise():
+    w = W.semiactive_2000big_200k(nbig=200, nsmall=3000)
+    outs = []
+    for _ in range(2):
+        g = mx.System(w)
+        g.step(30)
+        outs.append(g.state(mx.MX_COORD_DH))
+        g.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_checkpoint_resume_bitwise():
+    w = W.gas_4core_100k(nsmall=2000)
+    g = mx.System(w)
+    g.step(40)
+    a = g.state(mx.MX_COORD_DH)
+    g.close()
+    g = mx.System(w)
+    g.step(20)
+    mid = g.state(mx.MX_COORD_DH)
+    g.close()
+    g = mx.System(w)
+    g.set_state(mid, mx.MX_COORD_DH, 20)
+    g.step(20)
+    b = g.state(mx.MX_COORD_DH)
+    g.close()
+    assert np.array_equal(a, b)
