@@ -169,6 +169,40 @@ mx_status mx_gas_drag(mx_system* s, double* dev_acc);
 mx_status mx_detect_encounters(mx_system* s, const double* dev_xv0, const double* dev_xv1,
                                unsigned char* dev_flags, int* dev_pairs, int cap, int* n_pairs);
 
+/*
+ * mx_detect_encounters_noalloc -- the encounter test of mx_detect_encounters
+ * for callers that cannot allocate device memory (the paper has no
+ * counterpart; it is a library-usage variant).  Some callers cannot call
+ * cudaMalloc -- a host application that owns all of the GPU's memory through
+ * its own pool, or a latency-critical loop that cannot take the device-wide
+ * synchronisation an allocation may cause -- so this call needs no mx_system
+ * and allocates nothing: its working memory is a fixed array in the
+ * library's static device memory (about 0.7 MB, held on every GPU that loads
+ * the library until the process exits).
+ *  p          parameters; only G, m_star and dt are used.
+ *  n_big, n   big bodies and all bodies (n <= MX_NOALLOC_MAX_BODIES).
+ *  dev_rcrit  [n] changeover radius per body (0 for planetesimals), device.
+ *  dev_xv0, dev_xv1  6xn DH states at the start and end of the step, device.
+ *  dev_flags  [n] bytes, set to 1 for bodies in a flagged pair (required).
+ *  dev_pairs  [2*cap] ints, (i, j) sorted by (i, j) (may be NULL if cap = 0).
+ *  n_pairs    host; receives the number of flagged pairs.
+ *  cuda_stream  stream to run on (NULL: legacy default stream).
+ * The first call on a device, made with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call shares the one array, which keeps the last
+ * call's contents; the call clears what must start at zero.  Calls that
+ * overlap on the GPU (other threads or streams) race on the array.
+ * Errors: MX_ERR_ARG (including n above the limit), MX_ERR_CUDA,
+ * MX_ERR_PAIR_OVERFLOW when more than cap or MX_NOALLOC_MAX_PAIRS pairs.
+ * Synchronises the stream before returning.
+ */
+#define MX_NOALLOC_MAX_BODIES (1 << 21)
+#define MX_NOALLOC_MAX_PAIRS (1 << 16)
+mx_status mx_detect_encounters_noalloc(const mx_params* p, int n_big, int n,
+                                       const double* dev_rcrit, const double* dev_xv0,
+                                       const double* dev_xv1, unsigned char* dev_flags,
+                                       int* dev_pairs, int cap, int* n_pairs, void* cuda_stream);
+
 /* mx_kepler_drift -- Kepler drift by h of the N bodies of dev_xv (6xN, in
  * place) about mu0 = G m_star, universal variables (Sec. 2). */
 mx_status mx_kepler_drift(mx_system* s, double* dev_xv, double h);

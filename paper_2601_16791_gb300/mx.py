@@ -68,6 +68,7 @@ _SIGS = {
     "mx_sizes": (_I, [_P, _P, _P]),
     "mx_last_error": (ctypes.c_char_p, []),
     "mx_fp64_peak": (_I, [_P, _D, _P]),
+    "mx_detect_encounters_noalloc": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P, _P]),
 }
 
 
