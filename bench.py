@@ -237,6 +237,28 @@ def dram_traffic(kname):
     return rec.get("bytes_per_launch")
 
 
+# ------------------------------------------------------------ multi-rank
+def rank_seed(rank):
+    """Each rank integrates its own disk: same workload, seed offset by rank."""
+    return 1 + rank
+
+
+def reduce_max(x, device):
+    """Max over ranks of a host float (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(bodies_per_rank, steps, world, t_max_s):
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * bodies_per_rank * steps / t_max_s
+
+
 # ------------------------------------------------------------------- main
 def run_mx(args):
     import torch
@@ -248,7 +270,7 @@ def run_mx(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     st = torch.cuda.current_stream()
-    w = W.make(WORKLOAD, seed=1 + rank)
+    w = W.make(WORKLOAD, seed=rank_seed(rank))
     sysm = mx.System(w, stream=st.cuda_stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
 
@@ -277,13 +299,8 @@ def run_mx(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    units = world * w.n * args.steps
-    value = units / (t_max * 1e-3)
+    t_max = reduce_max(total_ms, "cuda")
+    value = whole_job_rate(w.n, args.steps, world, t_max * 1e-3)
 
     # end to end through the public API with host buffers: per step the state
     # goes host->device from pinned memory, one step runs, the state comes back
@@ -302,12 +319,8 @@ def run_mx(args):
         mx._check(L.mx_get_state(sysm.h, ctypes.c_void_p(pin_out.data_ptr()), mx.MX_COORD_DH,
                                  ctypes.byref(stepc)), "mx_get_state")
         pin_in.copy_(pin_out)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * w.n * ne / e2e_s
+    e2e_s = reduce_max(time.perf_counter() - t0, "cuda")
+    e2e_value = whole_job_rate(w.n, ne, world, e2e_s)
 
     if rank != 0:
         sysm.close()

@@ -385,13 +385,225 @@ __device__ bool bs_integrate(const GroupState& G, double mu0, double h, double t
   return true;
 }
 
-// One thread per work item, grid-stride.
+// ------------------------------------------------- warp-cooperative groups
+// Groups of up to kLaneMaxNB bodies run on 8 lanes each (4 groups per warp):
+// lane r of a group integrates extrapolation row r (n = 2(r+1) Stoermer
+// sub-steps), so the 8 rows of one macro sub-step advance side by side instead
+// of one after another.  The Aitken-Neville table is then built as a wavefront
+// across the 8 lanes (row r takes row r-1's column j-1 by a shuffle), each lane
+// checks its own row's error, and the lowest converged row is taken -- the
+// same choice as evaluating the rows in order and stopping at the first one
+// that converges.
+constexpr int kLaneMaxNB = 4;
+
+template <int NB>
+__device__ __forceinline__ void acc_nb(double mu0, const double* mu, const double* rc,
+                                       const double (&X)[3][NB], double (&A)[3][NB]) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const double x = X[0][b], y = X[1][b], z = X[2][b];
+    const double ir = rsqrt_d(fma(x, x, fma(y, y, z * z)));
+    const double f = mu0 * ir * ir * ir;
+    double ax = -f * x, ay = -f * y, az = -f * z;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      if (i == b || mu[i] == 0.0) continue;
+      const double dx = x - X[0][i], dy = y - X[1][i], dz = z - X[2][i];
+      const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
+      const double r = fmax(rc[b], rc[i]);
+      const double r2 = r * r;
+      if (s2 >= r2) continue;
+      const double yy = rsqrt_d(s2);
+      double wgt = yy * yy * yy;
+      if (s2 > 0.01 * r2) {
+        const double q = (s2 * yy - 0.1 * r) * (1.0 / (0.9 * r));
+        wgt *= 1.0 - q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
+      }
+      wgt *= mu[i];
+      ax = fma(-wgt, dx, ax);
+      ay = fma(-wgt, dy, ay);
+      az = fma(-wgt, dz, az);
+    }
+    A[0][b] = ax;
+    A[1][b] = ay;
+    A[2][b] = az;
+  }
+}
+
+// One group on the 8 lanes of `mask` (lane r = row r).  Y is the group state
+// (identical in all 8 lanes); returns false when the sub-step cap is hit.
+template <int NB>
+__device__ bool bs_lanes(unsigned mask, int row, double mu0, const double* mu, const double* rc,
+                         double h, double tol, int max_sub, double (&Y)[6][NB], int* nsub_out) {
+  const double tol2 = tol * tol;
+  // 1 / ((n_row / n_{row-j})^2 - 1) for j = 1..row
+  double inv_den[kBsRows];
+#pragma unroll
+  for (int j = 1; j < kBsRows; ++j) {
+    const double r = (double)(row + 1) / (double)(row - j + 1);
+    inv_den[j] = (j <= row) ? 1.0 / (r * r - 1.0) : 0.0;
+  }
+  const int n = 2 * (row + 1);
+  double rem = h, H = h;
+  int nsub = 0;
+  while (rem != 0.0) {
+    if (nsub >= max_sub) {
+      *nsub_out = nsub;
+      return false;
+    }
+    ++nsub;
+    if (fabs(H) > fabs(rem)) H = rem;
+    double xscal[NB], vscal[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      xscal[b] = 1.0 / fma(Y[0][b], Y[0][b], fma(Y[1][b], Y[1][b], Y[2][b] * Y[2][b]));
+      vscal[b] = 1.0 / fma(Y[3][b], Y[3][b], fma(Y[4][b], Y[4][b], Y[5][b] * Y[5][b]));
+    }
+    // this lane's Stoermer row
+    double X[3][NB], A[3][NB], D[3][NB];
+    const double dd = H / n;
+    const double d2 = dd * dd;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) X[c][b] = Y[c][b];
+    acc_nb<NB>(mu0, mu, rc, X, A);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        D[c][b] = dd * fma(0.5 * dd, A[c][b], Y[3 + c][b]);
+        X[c][b] += D[c][b];
+      }
+    for (int s = 1; s < n; ++s) {
+      acc_nb<NB>(mu0, mu, rc, X, A);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          D[c][b] = fma(d2, A[c][b], D[c][b]);
+          X[c][b] += D[c][b];
+        }
+    }
+    acc_nb<NB>(mu0, mu, rc, X, A);
+    double T[6][NB], Tp[6][NB];
+    const double idd = (double)n / H;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        T[c][b] = X[c][b];
+        T[3 + c][b] = fma(D[c][b], idd, 0.5 * dd * A[c][b]);
+        Tp[c][b] = T[c][b];
+        Tp[3 + c][b] = T[3 + c][b];
+      }
+    __syncwarp(mask);
+    // Aitken-Neville wavefront: after step j, lane r >= j holds T[r][j]
+#pragma unroll
+    for (int j = 1; j < kBsRows; ++j) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const double up = __shfl_up_sync(mask, T[c][b], 1, 8);
+          if (row >= j) {
+            if (row == j) Tp[c][b] = T[c][b];
+            T[c][b] = fma(T[c][b] - up, inv_den[j], T[c][b]);
+          }
+        }
+    }
+    bool ok = false;
+    if (row >= 1) {
+      double err = 0.0;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        double ex = 0.0, ev = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double dx = T[c][b] - Tp[c][b];
+          const double dv = T[3 + c][b] - Tp[3 + c][b];
+          ex = fma(dx, dx, ex);
+          ev = fma(dv, dv, ev);
+        }
+        err = fmax(err, fmax(ex * xscal[b], ev * vscal[b]));
+      }
+      ok = err <= tol2;
+    }
+    const unsigned vote = __ballot_sync(mask, ok) & mask;
+    if (vote) {
+      const int lead = __ffs(vote) - 1;          // lowest converged row (warp lane)
+      const int src = lead & 7;
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) Y[c][b] = __shfl_sync(mask, T[c][b], src, 8);
+      rem -= H;
+      H *= 1.3;
+    } else {
+      H *= 0.5;
+    }
+  }
+  *nsub_out = nsub;
+  return true;
+}
+
+template <int NB>
+__device__ void bs_slot_group(const Dev& d, int w, unsigned mask, int row) {
+  const int N = d.N;
+  const int o0 = d.work_off[w];
+  const SysDev& S = d.sys[d.work_sys[w]];
+  double mu[NB], rc[NB], Y[6][NB];
+#pragma unroll
+  for (int m = 0; m < NB; ++m) {
+    const int g = d.work_mem[o0 + m];
+    const int l = g - S.off;
+    mu[m] = (l < S.nbig) ? d.bmu[S.boff + l] : 0.0;
+    rc[m] = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) Y[c][m] = d.xv0[(size_t)c * N + g];
+  }
+  int nsub = 0;
+  const bool ok = bs_lanes<NB>(mask, row, S.mu0, mu, rc, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub);
+  if (row == 0) {
+    if (!ok) atomicOr(d.status, ST_BS);
+    d.work_nsub[w] = nsub;
+    for (int m = d.work_wfrom[w]; m < NB; ++m) {
+      const int g = d.work_mem[o0 + m];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) d.xv[(size_t)c * N + g] = Y[c][m];
+    }
+  }
+}
+
+// 4 groups per warp, 8 lanes each; groups of more than kLaneMaxNB bodies are
+// left to k_bs.
+__global__ void __launch_bounds__(128) k_bs_lanes(Dev d) {
+  const int W = *d.work_count;
+  const int lane = threadIdx.x & 31;
+  const int slot = lane >> 3, row = lane & 7;
+  const unsigned mask = 0xffu << (8 * slot);
+  const int gslot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4 + slot;
+  const int nslots = (gridDim.x * blockDim.x >> 5) * 4;
+  for (int w = gslot; w < W; w += nslots) {
+    const int nb = d.work_off[w + 1] - d.work_off[w];
+    switch (nb) {
+      case 1: bs_slot_group<1>(d, w, mask, row); break;
+      case 2: bs_slot_group<2>(d, w, mask, row); break;
+      case 3: bs_slot_group<3>(d, w, mask, row); break;
+      case 4: bs_slot_group<4>(d, w, mask, row); break;
+      default: break;
+    }
+  }
+}
+
+// One thread per work item with more than kLaneMaxNB bodies, grid-stride.
 __global__ void __launch_bounds__(32) k_bs(Dev d) {
   const int W = *d.work_count;
   const int N = d.N;
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x) {
     const int o0 = d.work_off[w];
     const int nb = min(d.work_off[w + 1] - o0, kMaxGroup);   // the builder caps groups
+    if (nb <= kLaneMaxNB) continue;
     GroupState G;
     G.nb = nb;
     const SysDev& S = d.sys[d.work_sys[w]];
@@ -417,6 +629,7 @@ __global__ void __launch_bounds__(32) k_bs(Dev d) {
 void launch_groups(const Dev& d, cudaStream_t st) { k_groups<<<1, 1024, 0, st>>>(d); }
 
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
+  k_bs_lanes<<<nblocks, 128, 0, st>>>(d);
   k_bs<<<nblocks, 32, 0, st>>>(d);
 }
 

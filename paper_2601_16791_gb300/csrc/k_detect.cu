@@ -55,6 +55,7 @@ struct DetSmem {
   double s[12][kThreads];   // x0 y0 z0 u0 v0 w0 x1 y1 z1 u1 v1 w1
   float f[12][kThreads];
   double rc[kThreads];
+  float rcf[kThreads];
 };
 
 // xv0, xv1: 6 x N endpoint states; keys/count/cap: pair output.
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
     af[6 + k] = (float)a1[k];
   }
   if (act && jbig) rcj = d.brc[S.boff + jl];
+  const float rcjf = (float)rcj;
   for (int c0 = 0; c0 < S.nbig; c0 += kThreads) {
     const int cn = min(kThreads, S.nbig - c0);
     __syncthreads();
@@ -95,7 +97,9 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
         sm.f[k][threadIdx.x] = (float)p0;
         sm.f[6 + k][threadIdx.x] = (float)p1;
       }
-      sm.rc[threadIdx.x] = d.brc[S.boff + c0 + threadIdx.x];
+      const double rcb = d.brc[S.boff + c0 + threadIdx.x];
+      sm.rc[threadIdx.x] = rcb;
+      sm.rcf[threadIdx.x] = (float)rcb;
     }
     __syncthreads();
     for (int k = 0; k < cn; ++k) {
@@ -104,8 +108,8 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
       bool ok = act && (!jbig || il < jl);
       bool hit = false;
       if (ok) {
-        const double rc = fmax(sm.rc[k], rcj);
-        const double rc2 = rc * rc;
+        const float rcf = fmaxf(sm.rcf[k], rcjf);
+        const float rc2f = rcf * rcf;
         const float dx0 = af[0] - sm.f[0][k], dy0 = af[1] - sm.f[1][k], dz0 = af[2] - sm.f[2][k];
         const float du0 = af[3] - sm.f[3][k], dv0 = af[4] - sm.f[4][k], dw0 = af[5] - sm.f[5][k];
         const float dx1 = af[6] - sm.f[6][k], dy1 = af[7] - sm.f[7][k], dz1 = af[8] - sm.f[8][k];
@@ -115,8 +119,9 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
         const float D0 = fabsf(2.0f * hf * fmaf(dx0, du0, fmaf(dy0, dv0, dz0 * dw0)));
         const float D1 = fabsf(2.0f * hf * fmaf(dx1, du1, fmaf(dy1, dv1, dz1 * dw1)));
         const float lb = fminf(d0, d1) - (4.0f / 27.0f) * (D0 + D1);
-        const float rc2f = (float)rc2;
         if (lb <= 1.1f * rc2f + 1e-3f * (d0 + d1 + D0 + D1)) {
+          const double rc = fmax(sm.rc[k], rcj);
+          const double rc2 = rc * rc;
           double b0[6], b1[6];
           for (int q = 0; q < 6; ++q) {
             b0[q] = sm.s[q][k];

@@ -88,18 +88,40 @@ struct Dev {
 };
 
 // ------------------------------------------------------------------ helpers
-// 1/sqrt(x) for x > 0: single-precision hardware estimate, then one
-// third-order Householder correction y <- y (1 + e/2 + 3e^2/8), e = 1 - x y^2.
-// The estimate is good to ~1e-7, so the result is within a few ulp.
+// On this part FP64 instructions (conversions included) issue at ~1/60 of the
+// FP32 rate with ~67-cycle dependent latency, so seeds are built with integer
+// and FP32 instructions only.
+//
+// |x| as a float, read off the binary64 bit pattern: the exponent is rebased
+// from bias 1023 to 127 and the top 20 mantissa bits are kept (truncation,
+// relative error < 2^-20).  Valid for 2^-126 <= |x| < 2^128.
+__device__ __forceinline__ float abs_to_float_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+  return __uint_as_float((hi - ((1023u - 127u) << 20)) << 3);
+}
+
+// A positive normal float as a double, exactly, by moving its bits.
+__device__ __forceinline__ double float_to_double_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  return __hiloint2double((int)((u >> 3) + ((1023u - 127u) << 20)), (int)(u << 29));
+}
+
+// 1/sqrt(x) for x > 0 (in the range above): single-precision hardware
+// estimate of the truncated argument (~1e-6), then one third-order Householder
+// correction y <- y (1 + e/2 + 3e^2/8), e = 1 - x y^2 (error ~ e^3, below the
+// FP64 rounding).
 __device__ __forceinline__ double rsqrt_d(double x) {
-  const double y = (double)rsqrtf((float)x);
+  const double y = float_to_double_bits(rsqrtf(abs_to_float_bits(x)));
   const double e = fma(-x * y, y, 1.0);
   return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
-// 1/x: single-precision estimate, then y <- y (1 + e + e^2), e = 1 - x y.
+// 1/x for |x| in the range above: estimate from the truncated |x|, sign put
+// back by bits, then y <- y (1 + e + e^2), e = 1 - x y.
 __device__ __forceinline__ double rcp_d(double x) {
-  const double y = (double)__frcp_rn((float)x);
+  const double a = float_to_double_bits(__frcp_rn(abs_to_float_bits(x)));
+  const double y = __hiloint2double(__double2hiint(a) | (__double2hiint(x) & (int)0x80000000),
+                                    __double2loint(a));
   const double e = fma(-x, y, 1.0);
   return fma(y, fma(e, e, e), y);
 }

@@ -234,6 +234,31 @@ def test_full_size_sampled_gas_workload():
     assert keep.sum() > 250 and err[keep].max() <= 1e-9
 
 
+@pytest.mark.parametrize("name,kw,steps", [("gas_4core_100k", dict(nsmall=20000), 4),
+                                           ("semiactive_2000big_200k", dict(nbig=300, nsmall=3000), 3)])
+def test_bs_groups_parity(name, kw, steps):
+    """Bodies that went through Bulirsch-Stoer, step by step: the GPU's lane-parallel
+    rows and the oracle's sequential rows take the same steps and agree to ~tol."""
+    w = W.make(name, **kw)
+    g, p, xv, mu, rc = both(w)
+    worst = 0.0
+    nflag = 0
+    for k in range(steps):
+        ref, ever, _, st = orc.step(p, w.nbig, xv, mu, rc, w.rp_km, w.rhop, 1)
+        mx.mx_set_state(g.h, xv, mx.MX_COORD_DH, k)
+        g.step(1)
+        got = g.state(mx.MX_COORD_DH)
+        fl = ever.astype(bool)
+        nflag += int(fl.sum())
+        err = np.linalg.norm(got[:3] - ref[:3], axis=0) / np.linalg.norm(ref[:3], axis=0)
+        worst = max(worst, float(err[fl].max()) if fl.any() else 0.0)
+        assert err[~fl].max() <= 1e-13
+        xv = ref
+    assert nflag > 10
+    assert worst <= 1e-10, worst
+    g.close()
+
+
 def test_energy_parity():
     w = W.semiactive_2000big_200k(nbig=400, nsmall=100)
     g, p, xv, mu, rc = both(w)
