@@ -103,6 +103,35 @@ mx_status mx_init_system(const mx_params* p, int n_big, int n_small, const doubl
                          const double* xv_helio, const double* rp_km, const double* rho_gcm3,
                          void* cuda_stream, mx_system** out);
 
+/*
+ * mx_init_batch -- n_sys independent systems of uneven size in one mx_system
+ * (the batched ensemble).  Arrays of n_sys entries: params[k], n_big[k],
+ * n_small[k], and per-system host pointers m_big[k], xv_helio[k], rp_km[k],
+ * rho_gcm3[k] with the layout of mx_init_system (rp_km / rho_gcm3 may be NULL
+ * when no system has gas).  Every kernel of mx_step then runs once over all
+ * systems: targets are cut into tiles that never span two systems, and the
+ * step is replayed as CUDA graphs.  The integrator caps (kepler_max_iter,
+ * bs_max_sub, bs_tol) and the pair capacity are taken from params[0]; dt,
+ * masses and gas may differ per system.  The state of system k occupies
+ * columns [off[k], off[k+1]) of the 6xN state (mx_batch_offsets).  Tile size
+ * and order are autotuned per size bucket at set-up and cached
+ * ($MX_AUTOTUNE_CACHE, default ~/.cache/mx/autotune.json; MX_AUTOTUNE=0 keeps
+ * tiles of 256 in system order); the choice does not change any result.
+ */
+mx_status mx_init_batch(int n_sys, const mx_params* params, const int* n_big, const int* n_small,
+                        const double* const* m_big, const double* const* xv_helio,
+                        const double* const* rp_km, const double* const* rho_gcm3,
+                        void* cuda_stream, mx_system** out);
+/* offsets [n_sys + 1]: first body of each system in the 6xN state. */
+mx_status mx_batch_offsets(mx_system* s, int* offsets);
+mx_status mx_batch_size(mx_system* s, int* n_sys, int* n_total);
+/* Energy and angular momentum of every system: E [n_sys], L3 [3 n_sys]. */
+mx_status mx_energy_batch(mx_system* s, double* E, double* L3);
+/* Tile size (64, 128 or 256 targets per block) and order (0: system order,
+ * 1: costliest tiles first) in use; mx_set_tiling overrides the autotuner. */
+mx_status mx_tiling(mx_system* s, int* tile, int* order);
+mx_status mx_set_tiling(mx_system* s, int tile, int order);
+
 /* Frees the system's device memory and graphs.  NULL is ignored. */
 void mx_destroy(mx_system* s);
 

@@ -12,10 +12,14 @@
 // one block from the sorted pair keys, so it is the same on every run.
 //
 // Integrator: Stoermer's rule for x'' = a(x) with n_k = 2k sub-steps
-// (k = 1..8), Aitken-Neville extrapolation in (H/n)^2 kept as one in-place
-// row, error = max over bodies of max(|dx|^2 xscal, |dv|^2 vscal) <= tol^2;
-// accepted sub-steps grow by 1.3 (capped by what remains), failed ones halve.
-// One thread per group; groups are independent.
+// (k = 1..8), Aitken-Neville extrapolation in (H/n)^2, error = max over
+// bodies of max(|dx|^2 xscal, |dv|^2 vscal) <= tol^2; accepted sub-steps grow
+// by 1.3 (capped by what remains), failed ones halve.  Groups of up to four
+// bodies run on lanes (k_bs_pack, then k_bs_spread for the long ones); larger
+// groups run one per thread (k_bs).  On this part an FP64 instruction has
+// ~67-cycle latency and costs the same for 1 or 32 active lanes, so a group's
+// serial chain, not its arithmetic, sets the time: the rows and step
+// candidates of a macro sub-step go on separate lanes to shorten it.
 #include "mx_common.cuh"
 #include "mx_kernels.h"
 
@@ -386,40 +390,53 @@ __device__ bool bs_integrate(const GroupState& G, double mu0, double h, double t
 }
 
 // ------------------------------------------------- warp-cooperative groups
-// Groups of up to kLaneMaxNB bodies run on 8 lanes each (4 groups per warp):
-// lane r of a group integrates extrapolation row r (n = 2(r+1) Stoermer
-// sub-steps), so the 8 rows of one macro sub-step advance side by side instead
-// of one after another.  The Aitken-Neville table is then built as a wavefront
-// across the 8 lanes (row r takes row r-1's column j-1 by a shuffle), each lane
-// checks its own row's error, and the lowest converged row is taken -- the
-// same choice as evaluating the rows in order and stopping at the first one
-// that converges.
+// Groups of up to kLaneMaxNB bodies run on lanes: lane 8c + r of a group
+// integrates extrapolation row r (n = 2(r+1) Stoermer sub-steps) with the
+// candidate step H/2^c.  The rows of a macro sub-step advance side by side;
+// the Aitken-Neville table of each candidate is a wavefront across its 8
+// lanes (row r takes row r-1's column j-1 by a shuffle); every lane checks its
+// own row's error, and the lowest converged lane of the group's vote (smallest
+// c, then smallest r) is accepted -- exactly what trying H, then H/2 after a
+// failure, and so on, with the rows in order, would accept.
+//
+// Two phases.  k_bs_pack runs four groups per warp with one candidate (8
+// lanes each) for at most kPackRounds macro sub-steps: cheap in FP64 issue
+// slots, which cost the same for 1 or 32 active lanes.  Groups still running
+// are saved to a continuation list, and k_bs_spread finishes them one per
+// warp with four candidates on a grid of one warp per SM, so the few long
+// chains (deep fly-bys) neither wait behind failed attempts nor share an
+// SM's FP64 pipe.
 constexpr int kLaneMaxNB = 4;
+constexpr int kPackRounds = 3;
+
+// Changeover constants of one member: rc^2, 0.01 rc^2, 0.1 rc, 1/(0.9 rc).
+struct MemberK {
+  double rc, rc2, rc2lo, rc01, i09;
+};
 
 template <int NB>
-__device__ __forceinline__ void acc_nb(double mu0, const double* mu, const double* rc,
+__device__ __forceinline__ void acc_nb(double mu0, const double* mu, const MemberK* K,
                                        const double (&X)[3][NB], double (&A)[3][NB]) {
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const double x = X[0][b], y = X[1][b], z = X[2][b];
     const double ir = rsqrt_d(fma(x, x, fma(y, y, z * z)));
-    const double f = mu0 * ir * ir * ir;
+    const double f = mu0 * (ir * ir) * ir;
     double ax = -f * x, ay = -f * y, az = -f * z;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       if (i == b || mu[i] == 0.0) continue;
       const double dx = x - X[0][i], dy = y - X[1][i], dz = z - X[2][i];
       const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
-      const double r = fmax(rc[b], rc[i]);
-      const double r2 = r * r;
-      if (s2 >= r2) continue;
+      // rc = max(rcrit_b, rcrit_i): the constants of the member with the larger radius
+      const MemberK& k = (K[b].rc > K[i].rc) ? K[b] : K[i];
+      if (s2 >= k.rc2) continue;
       const double yy = rsqrt_d(s2);
-      double wgt = yy * yy * yy;
-      if (s2 > 0.01 * r2) {
-        const double q = (s2 * yy - 0.1 * r) * (1.0 / (0.9 * r));
-        wgt *= 1.0 - q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
+      double wgt = (yy * yy) * (yy * mu[i]);
+      if (s2 > k.rc2lo) {
+        const double q = fma(s2, yy, -k.rc01) * k.i09;
+        wgt *= fma(-q * q * q, fma(q, fma(6.0, q, -15.0), 10.0), 1.0);
       }
-      wgt *= mu[i];
       ax = fma(-wgt, dx, ax);
       ay = fma(-wgt, dy, ay);
       az = fma(-wgt, dz, az);
@@ -430,13 +447,24 @@ __device__ __forceinline__ void acc_nb(double mu0, const double* mu, const doubl
   }
 }
 
-// One group on the 8 lanes of `mask` (lane r = row r).  Y is the group state
-// (identical in all 8 lanes); returns false when the sub-step cap is hit.
+// Integration state of one group between macro sub-steps.
 template <int NB>
-__device__ bool bs_lanes(unsigned mask, int row, double mu0, const double* mu, const double* rc,
-                         double h, double tol, int max_sub, double (&Y)[6][NB], int* nsub_out) {
+struct GroupRun {
+  double Y[6][NB];
+  double rem, H;
+  int nsub;
+};
+
+// Up to max_rounds macro sub-steps of one group on the lanes of `gmask`
+// (8 * NCAND lanes starting at warp lane `base`; this lane is base + 8c + r).
+// Returns 1 when the step is done, 0 when rounds ran out, -1 at the cap.
+template <int NB, int NCAND>
+__device__ int bs_rounds(unsigned gmask, int base, int lane, double mu0, const double* mu,
+                         const MemberK* K, double tol, int max_sub, int max_rounds,
+                         GroupRun<NB>& g) {
+  const int rel = lane - base;
+  const int row = rel & 7, cand = rel >> 3;
   const double tol2 = tol * tol;
-  // 1 / ((n_row / n_{row-j})^2 - 1) for j = 1..row
   double inv_den[kBsRows];
 #pragma unroll
   for (int j = 1; j < kBsRows; ++j) {
@@ -444,39 +472,36 @@ __device__ bool bs_lanes(unsigned mask, int row, double mu0, const double* mu, c
     inv_den[j] = (j <= row) ? 1.0 / (r * r - 1.0) : 0.0;
   }
   const int n = 2 * (row + 1);
-  double rem = h, H = h;
-  int nsub = 0;
-  while (rem != 0.0) {
-    if (nsub >= max_sub) {
-      *nsub_out = nsub;
-      return false;
-    }
-    ++nsub;
-    if (fabs(H) > fabs(rem)) H = rem;
+  const double inv_n = 1.0 / n;
+  const double cscale = 1.0 / (double)(1 << cand);
+  for (int round = 0; round < max_rounds; ++round) {
+    if (g.rem == 0.0) return 1;
+    if (g.nsub >= max_sub) return -1;
+    if (fabs(g.H) > fabs(g.rem)) g.H = g.rem;
+    const double Hc = g.H * cscale;
     double xscal[NB], vscal[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      xscal[b] = 1.0 / fma(Y[0][b], Y[0][b], fma(Y[1][b], Y[1][b], Y[2][b] * Y[2][b]));
-      vscal[b] = 1.0 / fma(Y[3][b], Y[3][b], fma(Y[4][b], Y[4][b], Y[5][b] * Y[5][b]));
+      xscal[b] = rcp_d(fma(g.Y[0][b], g.Y[0][b], fma(g.Y[1][b], g.Y[1][b], g.Y[2][b] * g.Y[2][b])));
+      vscal[b] = rcp_d(fma(g.Y[3][b], g.Y[3][b], fma(g.Y[4][b], g.Y[4][b], g.Y[5][b] * g.Y[5][b])));
     }
-    // this lane's Stoermer row
     double X[3][NB], A[3][NB], D[3][NB];
-    const double dd = H / n;
+    const double dd = Hc * inv_n;
     const double d2 = dd * dd;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int b = 0; b < NB; ++b) X[c][b] = Y[c][b];
-    acc_nb<NB>(mu0, mu, rc, X, A);
+      for (int b = 0; b < NB; ++b) X[c][b] = g.Y[c][b];
+    acc_nb<NB>(mu0, mu, K, X, A);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        D[c][b] = dd * fma(0.5 * dd, A[c][b], Y[3 + c][b]);
+        D[c][b] = dd * fma(0.5 * dd, A[c][b], g.Y[3 + c][b]);
         X[c][b] += D[c][b];
       }
     for (int s = 1; s < n; ++s) {
-      acc_nb<NB>(mu0, mu, rc, X, A);
+      acc_nb<NB>(mu0, mu, K, X, A);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -485,9 +510,9 @@ __device__ bool bs_lanes(unsigned mask, int row, double mu0, const double* mu, c
           X[c][b] += D[c][b];
         }
     }
-    acc_nb<NB>(mu0, mu, rc, X, A);
+    acc_nb<NB>(mu0, mu, K, X, A);
     double T[6][NB], Tp[6][NB];
-    const double idd = (double)n / H;
+    const double idd = n * rcp_d(Hc);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -497,15 +522,14 @@ __device__ bool bs_lanes(unsigned mask, int row, double mu0, const double* mu, c
         Tp[c][b] = T[c][b];
         Tp[3 + c][b] = T[3 + c][b];
       }
-    __syncwarp(mask);
-    // Aitken-Neville wavefront: after step j, lane r >= j holds T[r][j]
+    __syncwarp(gmask);
 #pragma unroll
     for (int j = 1; j < kBsRows; ++j) {
 #pragma unroll
       for (int c = 0; c < 6; ++c)
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          const double up = __shfl_up_sync(mask, T[c][b], 1, 8);
+          const double up = __shfl_up_sync(gmask, T[c][b], 1, 8);
           if (row >= j) {
             if (row == j) Tp[c][b] = T[c][b];
             T[c][b] = fma(T[c][b] - up, inv_den[j], T[c][b]);
@@ -529,70 +553,174 @@ __device__ bool bs_lanes(unsigned mask, int row, double mu0, const double* mu, c
       }
       ok = err <= tol2;
     }
-    const unsigned vote = __ballot_sync(mask, ok) & mask;
+    const unsigned vote = __ballot_sync(gmask, ok) & gmask;
     if (vote) {
-      const int lead = __ffs(vote) - 1;          // lowest converged row (warp lane)
-      const int src = lead & 7;
+      const int src = __ffs(vote) - 1;
+      const int c_acc = (src - base) >> 3;
+      g.nsub += c_acc + 1;                   // attempts a one-at-a-time search makes
+      if (g.nsub > max_sub) return -1;
 #pragma unroll
       for (int c = 0; c < 6; ++c)
 #pragma unroll
-        for (int b = 0; b < NB; ++b) Y[c][b] = __shfl_sync(mask, T[c][b], src, 8);
-      rem -= H;
-      H *= 1.3;
+        for (int b = 0; b < NB; ++b) g.Y[c][b] = __shfl_sync(gmask, T[c][b], src);
+      const double Hacc = g.H / (double)(1 << c_acc);
+      g.rem -= Hacc;
+      g.H = 1.3 * Hacc;
     } else {
-      H *= 0.5;
+      g.nsub += NCAND;
+      g.H *= 1.0 / (double)(1 << NCAND);
     }
   }
-  *nsub_out = nsub;
-  return true;
+  return (g.rem == 0.0) ? 1 : 0;
 }
 
 template <int NB>
-__device__ void bs_slot_group(const Dev& d, int w, unsigned mask, int row) {
-  const int N = d.N;
-  const int o0 = d.work_off[w];
-  const SysDev& S = d.sys[d.work_sys[w]];
-  double mu[NB], rc[NB], Y[6][NB];
+__device__ __forceinline__ void load_members(const Dev& d, const SysDev& S, int o0, double* mu,
+                                             MemberK* K) {
 #pragma unroll
   for (int m = 0; m < NB; ++m) {
     const int g = d.work_mem[o0 + m];
     const int l = g - S.off;
+    const double rc = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
     mu[m] = (l < S.nbig) ? d.bmu[S.boff + l] : 0.0;
-    rc[m] = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) Y[c][m] = d.xv0[(size_t)c * N + g];
+    K[m].rc = rc;
+    K[m].rc2 = rc * rc;
+    K[m].rc2lo = 0.01 * (rc * rc);
+    K[m].rc01 = 0.1 * rc;
+    K[m].i09 = (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
   }
-  int nsub = 0;
-  const bool ok = bs_lanes<NB>(mask, row, S.mu0, mu, rc, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub);
-  if (row == 0) {
-    if (!ok) atomicOr(d.status, ST_BS);
-    d.work_nsub[w] = nsub;
-    for (int m = d.work_wfrom[w]; m < NB; ++m) {
-      const int g = d.work_mem[o0 + m];
+}
+
+template <int NB>
+__device__ __forceinline__ void write_members(const Dev& d, int w, int o0, int lane_rel,
+                                              const GroupRun<NB>& g) {
+  const int wf = d.work_wfrom[w];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) d.xv[(size_t)c * N + g] = Y[c][m];
+  for (int m = 0; m < NB; ++m) {
+    if (lane_rel == m && m >= wf) {
+      const int gi = d.work_mem[o0 + m];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) d.xv[(size_t)c * d.N + gi] = g.Y[c][m];
     }
   }
 }
 
-// 4 groups per warp, 8 lanes each; groups of more than kLaneMaxNB bodies are
-// left to k_bs.
-__global__ void __launch_bounds__(128) k_bs_lanes(Dev d) {
+// Continuation record: rem, H, nsub, then Y.
+constexpr int kContDoubles = 3 + 6 * kLaneMaxNB;
+
+template <int NB>
+__device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int lane) {
+  const int o0 = d.work_off[w];
+  const SysDev& S = d.sys[d.work_sys[w]];
+  double mu[NB];
+  MemberK K[NB];
+  load_members<NB>(d, S, o0, mu, K);
+  GroupRun<NB> g;
+#pragma unroll
+  for (int m = 0; m < NB; ++m)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g.Y[c][m] = d.xv0[(size_t)c * d.N + d.work_mem[o0 + m]];
+  g.rem = S.h;
+  g.H = S.h;
+  g.nsub = 0;
+  const int r = bs_rounds<NB, 1>(gmask, base, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub,
+                                 kPackRounds, g);
+  if (r != 0) {
+    if (lane == base) {
+      if (r < 0) atomicOr(d.status, ST_BS);
+      d.work_nsub[w] = g.nsub;
+    }
+    write_members<NB>(d, w, o0, lane - base, g);
+    return;
+  }
+  // still running: hand over to k_bs_spread
+  int slot = 0;
+  if (lane == base) slot = atomicAdd(d.cont_count, 1);
+  slot = __shfl_sync(gmask, slot, base);
+  if (slot >= d.cont_cap) {   // list full: finish here
+    const int r2 = bs_rounds<NB, 1>(gmask, base, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub,
+                                    1 << 30, g);
+    if (lane == base) {
+      if (r2 < 0) atomicOr(d.status, ST_BS);
+      d.work_nsub[w] = g.nsub;
+    }
+    write_members<NB>(d, w, o0, lane - base, g);
+    return;
+  }
+  if (lane == base) {
+    double* c = d.cont_state + (size_t)slot * kContDoubles;
+    d.cont_item[slot] = w;
+    c[0] = g.rem;
+    c[1] = g.H;
+    c[2] = (double)g.nsub;
+#pragma unroll
+    for (int m = 0; m < NB; ++m)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) c[3 + 6 * m + q] = g.Y[q][m];
+  }
+}
+
+// Four groups of LO..HI bodies per warp, 8 lanes each (separate kernels keep
+// the common two-body case free of the larger cases' register pressure).
+template <int LO, int HI>
+__global__ void __launch_bounds__(128) k_bs_pack(Dev d) {
   const int W = *d.work_count;
   const int lane = threadIdx.x & 31;
-  const int slot = lane >> 3, row = lane & 7;
-  const unsigned mask = 0xffu << (8 * slot);
+  const int slot = lane >> 3;
+  const int base = slot * 8;
+  const unsigned gmask = 0xffu << base;
   const int gslot = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4 + slot;
   const int nslots = (gridDim.x * blockDim.x >> 5) * 4;
   for (int w = gslot; w < W; w += nslots) {
     const int nb = d.work_off[w + 1] - d.work_off[w];
-    switch (nb) {
-      case 1: bs_slot_group<1>(d, w, mask, row); break;
-      case 2: bs_slot_group<2>(d, w, mask, row); break;
-      case 3: bs_slot_group<3>(d, w, mask, row); break;
-      case 4: bs_slot_group<4>(d, w, mask, row); break;
-      default: break;
-    }
+    if (nb < LO || nb > HI) continue;
+    if (LO <= 1 && nb == 1) pack_group<(LO <= 1 ? 1 : LO)>(d, w, gmask, base, lane);
+    else if (LO <= 2 && HI >= 2 && nb == 2) pack_group<2>(d, w, gmask, base, lane);
+    else if (LO <= 3 && HI >= 3 && nb == 3) pack_group<(HI >= 3 ? 3 : 2)>(d, w, gmask, base, lane);
+    else if (HI >= 4 && nb == 4) pack_group<(HI >= 4 ? 4 : 2)>(d, w, gmask, base, lane);
+  }
+}
+
+template <int NB>
+__device__ void spread_group(const Dev& d, int slot, int lane) {
+  const int w = d.cont_item[slot];
+  const int o0 = d.work_off[w];
+  const SysDev& S = d.sys[d.work_sys[w]];
+  double mu[NB];
+  MemberK K[NB];
+  load_members<NB>(d, S, o0, mu, K);
+  GroupRun<NB> g;
+  const double* c = d.cont_state + (size_t)slot * kContDoubles;
+  g.rem = c[0];
+  g.H = c[1];
+  g.nsub = (int)c[2];
+#pragma unroll
+  for (int m = 0; m < NB; ++m)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) g.Y[q][m] = c[3 + 6 * m + q];
+  const int r = bs_rounds<NB, 4>(0xffffffffu, 0, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub,
+                                 1 << 30, g);
+  if (lane == 0) {
+    if (r < 0) atomicOr(d.status, ST_BS);
+    d.work_nsub[w] = g.nsub;
+  }
+  write_members<NB>(d, w, o0, lane, g);
+}
+
+// The continued groups of LO..HI bodies, one per warp, four step candidates
+// x eight rows.
+template <int LO, int HI>
+__global__ void __launch_bounds__(32) k_bs_spread(Dev d) {
+  const int C = min(*d.cont_count, d.cont_cap);
+  const int lane = threadIdx.x & 31;
+  for (int slot = blockIdx.x; slot < C; slot += gridDim.x) {
+    const int w = d.cont_item[slot];
+    const int nb = d.work_off[w + 1] - d.work_off[w];
+    if (nb < LO || nb > HI) continue;
+    if (LO <= 1 && nb == 1) spread_group<(LO <= 1 ? 1 : LO)>(d, slot, lane);
+    else if (LO <= 2 && HI >= 2 && nb == 2) spread_group<2>(d, slot, lane);
+    else if (LO <= 3 && HI >= 3 && nb == 3) spread_group<(HI >= 3 ? 3 : 2)>(d, slot, lane);
+    else if (HI >= 4 && nb == 4) spread_group<(HI >= 4 ? 4 : 2)>(d, slot, lane);
   }
 }
 
@@ -629,8 +757,13 @@ __global__ void __launch_bounds__(32) k_bs(Dev d) {
 void launch_groups(const Dev& d, cudaStream_t st) { k_groups<<<1, 1024, 0, st>>>(d); }
 
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
-  k_bs_lanes<<<nblocks, 128, 0, st>>>(d);
+  // (a group has at least two members: one big body and the body it meets)
+  cudaMemsetAsync(d.cont_count, 0, sizeof(int), st);
+  k_bs_pack<2, 2><<<nblocks, 128, 0, st>>>(d);
+  k_bs_pack<3, 4><<<nblocks, 128, 0, st>>>(d);
   k_bs<<<nblocks, 32, 0, st>>>(d);
+  k_bs_spread<2, 2><<<nblocks / 4, 32, 0, st>>>(d);
+  k_bs_spread<3, 4><<<nblocks / 4, 32, 0, st>>>(d);
 }
 
 }  // namespace mx

@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
   }
   if (act && jbig) rcj = d.brc[S.boff + jl];
   const float rcjf = (float)rcj;
-  for (int c0 = 0; c0 < S.nbig; c0 += kThreads) {
-    const int cn = min(kThreads, S.nbig - c0);
+  for (int c0 = 0; c0 < S.nbig; c0 += blockDim.x) {
+    const int cn = min((int)blockDim.x, S.nbig - c0);
     __syncthreads();
     if (threadIdx.x < cn) {
       const int g = S.off + c0 + threadIdx.x;
@@ -215,7 +215,7 @@ void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int 
 
 void launch_detect(const Dev& d, const double* xv0, const double* xv1, unsigned char* flags,
                    unsigned long long* keys, int* count, int cap, cudaStream_t st) {
-  k_detect<<<d.ntiles, kThreads, 0, st>>>(d, xv0, xv1, flags, keys, count, cap);
+  k_detect<<<d.ntiles, d.tile, 0, st>>>(d, xv0, xv1, flags, keys, count, cap);
 }
 
 void launch_sort_keys(unsigned long long* keys, const int* count, int cap, int swap_ij,

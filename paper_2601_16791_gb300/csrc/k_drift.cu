@@ -122,8 +122,8 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, int maxit, dou
   return true;
 }
 
-// Jump by (jump_h) P/m0, save the pre-drift state, drift by the system's h.
-__global__ void __launch_bounds__(kThreads) k_jump_drift(Dev d, double jump_h) {
+// Jump by (jump_frac h) P/m0, save the pre-drift state, drift by the system's h.
+__global__ void __launch_bounds__(kThreads) k_jump_drift(Dev d, double jump_frac) {
   const Tile t = d.tiles[blockIdx.x];
   const SysDev& S = d.sys[t.sys];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_jump_drift(Dev d, double jump_h) {
   const int N = d.N;
   const int j = t.start + threadIdx.x;
   double dj[3];
-  jump_vec(d.P + 3 * t.sys, S, jump_h, dj);
+  jump_vec(d.P + 3 * t.sys, S, jump_frac, dj);
   double x = d.xv[j] + dj[0];
   double y = d.xv[(size_t)N + j] + dj[1];
   double z = d.xv[2 * (size_t)N + j] + dj[2];
@@ -174,8 +174,8 @@ __global__ void __launch_bounds__(kThreads) k_drift_buf(double* xv, int n, doubl
   xv[5 * (size_t)n + j] = w;
 }
 
-void launch_jump_drift(const Dev& d, double jump_h, cudaStream_t st) {
-  k_jump_drift<<<d.ntiles, kThreads, 0, st>>>(d, jump_h);
+void launch_jump_drift(const Dev& d, double jump_frac, cudaStream_t st) {
+  k_jump_drift<<<d.ntiles, d.tile, 0, st>>>(d, jump_frac);
 }
 
 void launch_drift_buf(double* xv, int n, double mu, double h, int maxit, unsigned* status,

@@ -87,11 +87,11 @@ void launch_init_sys(const Dev& d, int do_rcrit, double rcrit_hill, cudaStream_t
 
 void launch_init_bodies(const Dev& d, const double* rp_km, const double* rho, int set_drag,
                         cudaStream_t st) {
-  k_init_bodies<<<d.ntiles, kThreads, 0, st>>>(d, rp_km, rho, set_drag);
+  k_init_bodies<<<d.ntiles, d.tile, 0, st>>>(d, rp_km, rho, set_drag);
 }
 
 void launch_readout(const Dev& d, double* out, cudaStream_t st) {
-  k_readout<<<d.ntiles, kThreads, 0, st>>>(d, out);
+  k_readout<<<d.ntiles, d.tile, 0, st>>>(d, out);
 }
 
 }  // namespace mx

@@ -145,7 +145,7 @@ __device__ __forceinline__ void gravity_all(const Dev& d, const SysDev& S, BigSm
 
 // Momentum of each system's massive bodies and the staged big positions.
 // One block per system; a fixed partition and tree keep the sum deterministic.
-__global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_h) {
+__global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac) {
   const SysDev& S = d.sys[blockIdx.x];
   __shared__ double red[3][kThreads];
   const int N = d.N;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_h) {
     for (int c = 0; c < 3; ++c) P[c] = red[c][0];
   double Ps[3] = {red[0][0], red[1][0], red[2][0]};
   double dj[3];
-  jump_vec(Ps, S, jump_h, dj);
+  jump_vec(Ps, S, jump_frac, dj);
   for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
     const int g = S.off + i;
     d.bx[S.boff + i] = d.xv[g] + dj[0];
@@ -178,20 +178,21 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_h) {
   }
 }
 
-// Jump then kick (nkick half kicks of kick_h each, gravity evaluated once; the
+// Jump then kick (nkick half kicks of kick_frac * h each, gravity evaluated once; the
 // drag is re-evaluated before each with the updated velocity).  The momentum
 // P read here is the one k_prep just computed; it stays valid across the
 // kicks because the K-weighted pair forces are antisymmetric and the drag acts
 // on massless bodies only.
 template <int NKICK>
-__global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_h, double kick_h) {
+__global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac, double kick_frac) {
   __shared__ BigSmem sb;
   const Tile t = d.tiles[blockIdx.x];
   const SysDev& S = d.sys[t.sys];
   const double* P = d.P + 3 * t.sys;
   const int N = d.N;
   double dj[3];
-  jump_vec(P, S, jump_h, dj);
+  jump_vec(P, S, jump_frac, dj);
+  const double kick_h = kick_frac * S.h;
   const bool act = threadIdx.x < t.count;
   const int j = t.start + threadIdx.x;
   const int jl = j - S.off;
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_h, do
   double ax = 0, ay = 0, az = 0;
   gravity_all(d, S, sb, act, jl, rcj, x, y, z, ax, ay, az);
   if (!act) return;
-  if (jump_h != 0.0) {
+  if (jump_frac != 0.0) {
     d.xv[j] = x;
     d.xv[(size_t)N + j] = y;
     d.xv[2 * (size_t)N + j] = z;
@@ -274,18 +275,19 @@ __global__ void __launch_bounds__(kThreads) k_accel(Dev d, double* acc, int drag
   }
 }
 
-void launch_prep(const Dev& d, double jump_h, cudaStream_t st) {
-  k_prep<<<d.nsys, kThreads, 0, st>>>(d, jump_h);
+void launch_prep(const Dev& d, double jump_frac, cudaStream_t st) {
+  k_prep<<<d.nsys, kThreads, 0, st>>>(d, jump_frac);
 }
 
-void launch_jump_kick(const Dev& d, double jump_h, double kick_h, int nkick, cudaStream_t st) {
-  if (nkick == 2) k_jump_kick<2><<<d.ntiles, kThreads, 0, st>>>(d, jump_h, kick_h);
-  else k_jump_kick<1><<<d.ntiles, kThreads, 0, st>>>(d, jump_h, kick_h);
+void launch_jump_kick(const Dev& d, double jump_frac, double kick_frac, int nkick,
+                      cudaStream_t st) {
+  if (nkick == 2) k_jump_kick<2><<<d.ntiles, d.tile, 0, st>>>(d, jump_frac, kick_frac);
+  else k_jump_kick<1><<<d.ntiles, d.tile, 0, st>>>(d, jump_frac, kick_frac);
 }
 
 void launch_accel(const Dev& d, double* acc, int drag_only, int acc_stride, int acc_base,
                   cudaStream_t st) {
-  k_accel<<<d.ntiles, kThreads, 0, st>>>(d, acc, drag_only, acc_stride, acc_base);
+  k_accel<<<d.ntiles, d.tile, 0, st>>>(d, acc, drag_only, acc_stride, acc_base);
 }
 
 }  // namespace mx

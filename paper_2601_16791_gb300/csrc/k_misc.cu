@@ -10,9 +10,9 @@
 
 namespace mx {
 
-__global__ void __launch_bounds__(kThreads) k_energy(Dev d, double inv_G, double m_star,
-                                                     double* out /* 7 per system */) {
+__global__ void __launch_bounds__(kThreads) k_energy(Dev d, double* out /* 7 per system */) {
   const SysDev& S = d.sys[blockIdx.x];
+  const double inv_G = S.inv_G, m_star = S.m_star;
   const int N = d.N;
   __shared__ double red[8][kThreads];
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // ke, pe, Px, Py, Pz, Lx, Ly, Lz
@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(kThreads) k_energy(Dev d, double inv_G, double
   }
 }
 
-void launch_energy(const Dev& d, double inv_G, double m_star, double* out, cudaStream_t st) {
-  k_energy<<<d.nsys, kThreads, 0, st>>>(d, inv_G, m_star, out);
+void launch_energy(const Dev& d, double* out, cudaStream_t st) {
+  k_energy<<<d.nsys, kThreads, 0, st>>>(d, out);
 }
 
 // Independent FMA chains, eight per thread, so the FP64 pipe is the limit.

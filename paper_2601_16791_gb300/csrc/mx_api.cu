@@ -4,9 +4,13 @@
 // folds parameters into per-system constants and lays out the buffers.
 #include <cuda_runtime.h>
 
+#include <sys/stat.h>
+#include <unistd.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -68,6 +72,8 @@ mx::SysDev make_sysdev(const mx_params& p, int off, int nbig, int n, int boff) {
   s.inv_mu0 = 1.0 / s.mu0;
   s.sqrt_mu0 = std::sqrt(s.mu0);
   s.h = p.dt;
+  s.inv_G = 1.0 / p.G;
+  s.m_star = p.m_star;
   const mx_gas& g = p.gas;
   s.gas_on = g.enabled ? 1 : 0;
   s.cd_mode = g.cd_mode;
@@ -112,6 +118,10 @@ struct mx_system {
   cudaGraphExec_t g_head = nullptr, g_mid = nullptr, g_last = nullptr;
   long long step = 0;
   int bs_blocks = 0;
+  int tile = mx::kThreads;        // targets per tile (autotuned)
+  int order = 0;                  // 0: tiles in system order; 1: costliest first
+  int tiles_cap = 0;
+  std::vector<mx::SysDev> h_sys;
 };
 
 namespace {
@@ -155,21 +165,19 @@ mx_status sync_status(mx_system* s) {
 // The device work of one interior step, or the last step of a call
 // (one half kick at its end), or the leading half kick.
 void enqueue_head(mx_system* s, cudaStream_t st) {
-  const double h = s->params[0].dt;
   mx::launch_prep(s->d, 0.0, st);
-  mx::launch_jump_kick(s->d, 0.0, 0.5 * h, 1, st);
+  mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st);
 }
 
 void enqueue_step(mx_system* s, int last, cudaStream_t st) {
-  const double h = s->params[0].dt;
-  mx::launch_jump_drift(s->d, 0.5 * h, st);
+  mx::launch_jump_drift(s->d, 0.5, st);
   mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count,
                     s->d.pair_cap, st);
   mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st);
   mx::launch_groups(s->d, st);
   mx::launch_bs(s->d, s->bs_blocks, st);
-  mx::launch_prep(s->d, 0.5 * h, st);
-  mx::launch_jump_kick(s->d, 0.5 * h, 0.5 * h, last ? 1 : 2, st);
+  mx::launch_prep(s->d, 0.5, st);
+  mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st);
 }
 
 mx_status capture(mx_system* s, int which, cudaGraphExec_t* out) {
@@ -193,6 +201,179 @@ mx_status ensure_graphs(mx_system* s) {
   return MX_OK;
 }
 
+constexpr int kMinTile = 64;
+
+// Tiles of `tile` targets per system; order 1 puts the costliest first (work
+// per target grows with the system's big bodies and with gas drag), so the
+// block scheduler starts the long blocks early and the tail is short.
+std::vector<mx::Tile> make_tiles(const std::vector<mx::SysDev>& sys, int tile, int order) {
+  std::vector<mx::Tile> tiles;
+  std::vector<double> cost;
+  for (int k = 0; k < (int)sys.size(); ++k) {
+    for (int t = 0; t < sys[k].n; t += tile) {
+      const int cnt = std::min(tile, sys[k].n - t);
+      tiles.push_back({k, sys[k].off + t, cnt, 0});
+      cost.push_back((double)cnt * (sys[k].nbig + 1 + (sys[k].gas_on ? 4 : 0)));
+    }
+  }
+  if (order == 1) {
+    std::vector<int> idx(tiles.size());
+    for (size_t q = 0; q < idx.size(); ++q) idx[q] = (int)q;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<mx::Tile> sorted;
+    for (int q : idx) sorted.push_back(tiles[q]);
+    tiles.swap(sorted);
+  }
+  return tiles;
+}
+
+void drop_graphs(mx_system* s) {
+  if (s->g_head) cudaGraphExecDestroy(s->g_head);
+  if (s->g_mid) cudaGraphExecDestroy(s->g_mid);
+  if (s->g_last) cudaGraphExecDestroy(s->g_last);
+  s->g_head = s->g_mid = s->g_last = nullptr;
+}
+
+mx_status set_tiling(mx_system* s, int tile, int order) {
+  std::vector<mx::Tile> tiles = make_tiles(s->h_sys, tile, order);
+  if ((int)tiles.size() > s->tiles_cap) return fail(MX_ERR_ARG, "tile size below the minimum");
+  MX_CUDA(cudaMemcpyAsync(s->d_tiles, tiles.data(), tiles.size() * sizeof(mx::Tile),
+                          cudaMemcpyHostToDevice, s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  s->tile = tile;
+  s->order = order;
+  s->d.tile = tile;
+  s->d.ntiles = (int)tiles.size();
+  drop_graphs(s);
+  return MX_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Picks the tile size (targets per block) and the tile order for a size
+// bucket by timing one plain step per candidate, state saved and restored
+// (results do not depend on the choice: every target sums its sources in
+// the same order and the pair keys are sorted).  Choices are kept in a
+// small JSON file ($MX_AUTOTUNE_CACHE, else ~/.cache/mx/autotune.json);
+// MX_AUTOTUNE=0 keeps the defaults.
+std::string tune_key(const mx_system* s) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, s->device);
+  auto bucket = [](double x) { return x <= 0 ? 0 : (int)std::lround(4.0 * std::log2(x)); };
+  bool gas = false;
+  for (auto& p : s->params) gas |= (p.gas.enabled != 0);
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s/%d|nsys%d|N%d|NB%d|gas%d", prop.name, prop.multiProcessorCount,
+                bucket(s->params.size()), bucket(s->N), bucket(s->NB), gas ? 1 : 0);
+  return buf;
+}
+
+std::string tune_path() {
+  const char* p = std::getenv("MX_AUTOTUNE_CACHE");
+  if (p && *p) return p;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/mx/autotune.json";
+}
+
+// Flat {"key": [tile, order], ...} file.
+std::vector<std::pair<std::string, std::pair<int, int>>> tune_load() {
+  std::vector<std::pair<std::string, std::pair<int, int>>> out;
+  FILE* f = std::fopen(tune_path().c_str(), "r");
+  if (!f) return out;
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+  std::fclose(f);
+  size_t pos = 0;
+  while ((pos = txt.find('"', pos)) != std::string::npos) {
+    const size_t end = txt.find('"', pos + 1);
+    if (end == std::string::npos) break;
+    std::string key = txt.substr(pos + 1, end - pos - 1);
+    int a = 0, b = 0;
+    if (std::sscanf(txt.c_str() + end + 1, " : [ %d , %d ]", &a, &b) == 2) out.push_back({key, {a, b}});
+    pos = end + 1;
+  }
+  return out;
+}
+
+void tune_store(const std::string& key, int tile, int order) {
+  auto all = tune_load();
+  bool found = false;
+  for (auto& kv : all)
+    if (kv.first == key) { kv.second = {tile, order}; found = true; }
+  if (!found) all.push_back({key, {tile, order}});
+  const std::string path = tune_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {
+    std::string dir = path.substr(0, slash), cur;
+    for (size_t q = 1; q <= dir.size(); ++q)
+      if (q == dir.size() || dir[q] == '/') { cur = dir.substr(0, q); mkdir(cur.c_str(), 0755); }
+  }
+  const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\n");
+  for (size_t q = 0; q < all.size(); ++q)
+    std::fprintf(f, "  \"%s\": [%d, %d]%s\n", all[q].first.c_str(), all[q].second.first,
+                 all[q].second.second, q + 1 < all.size() ? "," : "");
+  std::fprintf(f, "}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+void enqueue_head(mx_system* s, cudaStream_t st);
+void enqueue_step(mx_system* s, int last, cudaStream_t st);
+
+mx_status trial_ms(mx_system* s, double* ms) {
+  const size_t bytes = (size_t)6 * s->N * sizeof(double);
+  MX_CUDA(cudaMemcpyAsync(s->d_tmp, s->d.xv, bytes, cudaMemcpyDeviceToDevice, s->st));
+  cudaEvent_t e0, e1;
+  MX_CUDA(cudaEventCreate(&e0));
+  MX_CUDA(cudaEventCreate(&e1));
+  enqueue_head(s, s->st);          // warm-up step
+  enqueue_step(s, 1, s->st);
+  MX_CUDA(cudaEventRecord(e0, s->st));
+  enqueue_head(s, s->st);
+  enqueue_step(s, 1, s->st);
+  MX_CUDA(cudaEventRecord(e1, s->st));
+  MX_CUDA(cudaEventSynchronize(e1));
+  float t = 0.f;
+  MX_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MX_CUDA(cudaMemcpyAsync(s->d.xv, s->d_tmp, bytes, cudaMemcpyDeviceToDevice, s->st));
+  MX_CUDA(cudaMemsetAsync(s->d.status, 0, sizeof(unsigned), s->st));
+  MX_CUDA(cudaMemsetAsync(s->d.pair_count, 0, 2 * sizeof(int), s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  *ms = t;
+  return MX_OK;
+}
+
+mx_status autotune(mx_system* s) {
+  const char* env = std::getenv("MX_AUTOTUNE");
+  if (env && std::strcmp(env, "0") == 0) return MX_OK;
+  const std::string key = tune_key(s);
+  for (auto& kv : tune_load())
+    if (kv.first == key) {
+      const int tile = kv.second.first, order = kv.second.second;
+      if ((tile == 64 || tile == 128 || tile == 256) && (order == 0 || order == 1))
+        return set_tiling(s, tile, order);
+    }
+  double best = 1e300;
+  int bt = s->tile, bo = s->order;
+  for (int tile : {64, 128, 256})
+    for (int order : {0, 1}) {
+      if (order == 1 && s->params.size() == 1) continue;   // one system: order is moot
+      MX_TRY(set_tiling(s, tile, order));
+      double ms = 0.0;
+      MX_TRY(trial_ms(s, &ms));
+      if (ms < best) { best = ms; bt = tile; bo = order; }
+    }
+  MX_TRY(set_tiling(s, bt, bo));
+  tune_store(key, bt, bo);
+  return MX_OK;
+}
+
 // Builds the device side of a batch of systems (one system = batch of one).
 mx_status build(mx_system* s, const std::vector<const double*>& m_big,
                 const std::vector<const double*>& xv_helio, const std::vector<const double*>& rp,
@@ -200,14 +381,17 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   const int nsys = (int)s->params.size();
   std::vector<mx::SysDev> sys(nsys);
   std::vector<mx::Tile> tiles;
-  int off = 0, boff = 0;
+  int off = 0, boff = 0, tiles_cap = 0;
   for (int k = 0; k < nsys; ++k) {
     const int n = s->nbig[k] + s->nsmall[k];
     sys[k] = make_sysdev(s->params[k], off, s->nbig[k], n, boff);
-    for (int t = 0; t < n; t += mx::kThreads) tiles.push_back({k, off + t, std::min(mx::kThreads, n - t), 0});
+    tiles_cap += (n + kMinTile - 1) / kMinTile;
     off += n;
     boff += s->nbig[k];
   }
+  s->h_sys = sys;
+  s->tiles_cap = tiles_cap;
+  tiles = make_tiles(sys, s->tile, s->order);
   s->N = off;
   s->NB = boff;
   const int N = s->N, NB = s->NB;
@@ -239,9 +423,13 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_TRY(dalloc(s, &d.work_sys, work_cap));
   MX_TRY(dalloc(s, &d.work_wfrom, work_cap));
   MX_TRY(dalloc(s, &d.work_nsub, work_cap));
+  d.cont_cap = std::min(work_cap, 1 << 14);
+  MX_TRY(dalloc(s, &d.cont_count, 1));
+  MX_TRY(dalloc(s, &d.cont_item, d.cont_cap));
+  MX_TRY(dalloc(s, &d.cont_state, (size_t)d.cont_cap * 27));
   MX_TRY(dalloc(s, &d.status, 1));
   MX_TRY(dalloc(s, &s->d_sys, nsys));
-  MX_TRY(dalloc(s, &s->d_tiles, tiles.size()));
+  MX_TRY(dalloc(s, &s->d_tiles, tiles_cap));
   MX_TRY(dalloc(s, &s->d_energy, 7 * (size_t)nsys));
   MX_TRY(dalloc(s, &s->d_sink, 1));
   d.sys = s->d_sys;
@@ -250,6 +438,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   d.NB = NB;
   d.nsys = nsys;
   d.ntiles = (int)tiles.size();
+  d.tile = s->tile;
   d.pair_cap = cap;
   d.work_cap = work_cap;
   d.mem_cap = mem_cap;
@@ -299,9 +488,7 @@ void destroy_impl(mx_system* s) {
   if (!s) return;
   cudaSetDevice(s->device);
   if (s->st) cudaStreamSynchronize(s->st);
-  if (s->g_head) cudaGraphExecDestroy(s->g_head);
-  if (s->g_mid) cudaGraphExecDestroy(s->g_mid);
-  if (s->g_last) cudaGraphExecDestroy(s->g_last);
+  drop_graphs(s);
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_status) cudaFreeHost(s->h_status);
   if (s->h_count) cudaFreeHost(s->h_count);
@@ -355,12 +542,101 @@ mx_status mx_init_system(const mx_params* p, int n_big, int n_small, const doubl
   s->nbig.assign(1, n_big);
   s->nsmall.assign(1, n_small);
   mx_status r = build(s, {m_big}, {xv_helio}, {rp_km}, {rho_gcm3});
+  if (r == MX_OK) r = autotune(s);
   if (r != MX_OK) {
     std::string msg = g_last_error;
     destroy_impl(s);
     return fail(r, msg);
   }
   *out = s;
+  return MX_OK;
+}
+
+mx_status mx_init_batch(int n_sys, const mx_params* params, const int* n_big, const int* n_small,
+                        const double* const* m_big, const double* const* xv_helio,
+                        const double* const* rp_km, const double* const* rho_gcm3,
+                        void* cuda_stream, mx_system** out) {
+  g_last_error.clear();
+  if (!out) return fail(MX_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_sys <= 0 || !params || !n_big || !n_small || !m_big || !xv_helio)
+    return fail(MX_ERR_ARG, "invalid batch arguments");
+  long long total = 0;
+  for (int k = 0; k < n_sys; ++k) {
+    const mx_params* p = &params[k];
+    if (!valid_params(p)) return fail(MX_ERR_ARG, "invalid parameters of system " + std::to_string(k));
+    if (n_big[k] < 0 || n_small[k] < 0 || n_big[k] + n_small[k] <= 0)
+      return fail(MX_ERR_ARG, "invalid body counts of system " + std::to_string(k));
+    if ((n_big[k] > 0 && !m_big[k]) || !xv_helio[k]) return fail(MX_ERR_ARG, "NULL input array");
+    if (p->gas.enabled && n_small[k] > 0 && (!rp_km || !rho_gcm3 || !rp_km[k] || !rho_gcm3[k]))
+      return fail(MX_ERR_ARG, "gas drag needs rp_km and rho_gcm3");
+    for (int i = 0; i < n_big[k]; ++i)
+      if (!(m_big[k][i] >= 0.0)) return fail(MX_ERR_ARG, "negative or NaN mass");
+    total += n_big[k] + n_small[k];
+  }
+  if (total > (1LL << 30)) return fail(MX_ERR_ARG, "too many bodies");
+  mx_system* s = nullptr;
+  MX_TRY(create(&s, cuda_stream));
+  s->params.assign(params, params + n_sys);
+  s->nbig.assign(n_big, n_big + n_sys);
+  s->nsmall.assign(n_small, n_small + n_sys);
+  std::vector<const double*> mb(m_big, m_big + n_sys), xv(xv_helio, xv_helio + n_sys);
+  std::vector<const double*> rp(n_sys, nullptr), rh(n_sys, nullptr);
+  for (int k = 0; k < n_sys; ++k) {
+    if (rp_km) rp[k] = rp_km[k];
+    if (rho_gcm3) rh[k] = rho_gcm3[k];
+  }
+  mx_status r = build(s, mb, xv, rp, rh);
+  if (r == MX_OK) r = autotune(s);
+  if (r != MX_OK) {
+    std::string msg = g_last_error;
+    destroy_impl(s);
+    return fail(r, msg);
+  }
+  *out = s;
+  return MX_OK;
+}
+
+mx_status mx_batch_offsets(mx_system* s, int* offsets) {
+  if (!s || !offsets) return fail(MX_ERR_ARG, "invalid arguments");
+  for (size_t k = 0; k < s->h_sys.size(); ++k) offsets[k] = s->h_sys[k].off;
+  offsets[s->h_sys.size()] = s->N;
+  return MX_OK;
+}
+
+mx_status mx_batch_size(mx_system* s, int* n_sys, int* n_total) {
+  if (!s) return fail(MX_ERR_ARG, "NULL system");
+  if (n_sys) *n_sys = (int)s->h_sys.size();
+  if (n_total) *n_total = s->N;
+  return MX_OK;
+}
+
+mx_status mx_tiling(mx_system* s, int* tile, int* order) {
+  if (!s) return fail(MX_ERR_ARG, "NULL system");
+  if (tile) *tile = s->tile;
+  if (order) *order = s->order;
+  return MX_OK;
+}
+
+mx_status mx_set_tiling(mx_system* s, int tile, int order) {
+  if (!s || !(tile == 64 || tile == 128 || tile == 256) || !(order == 0 || order == 1))
+    return fail(MX_ERR_ARG, "tile must be 64, 128 or 256 and order 0 or 1");
+  MX_TRY(set_device(s));
+  return set_tiling(s, tile, order);
+}
+
+mx_status mx_energy_batch(mx_system* s, double* E, double* L3) {
+  if (!s || !E || !L3) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  const int nsys = (int)s->h_sys.size();
+  mx::launch_energy(s->d, s->d_energy, s->st);
+  std::vector<double> o(7 * (size_t)nsys);
+  MX_CUDA(cudaMemcpyAsync(o.data(), s->d_energy, o.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  MX_TRY(sync_status(s));
+  for (int k = 0; k < nsys; ++k) {
+    E[k] = o[7 * k + 2];
+    for (int c = 0; c < 3; ++c) L3[3 * k + c] = o[7 * k + 4 + c];
+  }
   return MX_OK;
 }
 
@@ -391,7 +667,6 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
   if (n_steps == 0) return MX_OK;
   MX_TRY(set_device(s));
   cudaStream_t st = s->st;
-  const double h = s->params[0].dt;
   // (kind, event-before, event-after) per launch
   std::vector<int> kind;
   std::vector<cudaEvent_t> ev;
@@ -411,10 +686,10 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
   };
   cudaError_t e = cudaSuccess;
   e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, st); });
-  if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5 * h, 1, st); });
+  if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
     const bool last = (k + 1 == n_steps);
-    e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5 * h, st); });
+    e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5, st); });
     if (e == cudaSuccess)
       e = timed(MX_K_DETECT, [&] {
         mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count, s->d.pair_cap, st);
@@ -422,9 +697,9 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     if (e == cudaSuccess) e = timed(MX_K_SORT, [&] { mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st); });
     if (e == cudaSuccess) e = timed(MX_K_GROUPS, [&] { mx::launch_groups(s->d, st); });
     if (e == cudaSuccess) e = timed(MX_K_BS, [&] { mx::launch_bs(s->d, s->bs_blocks, st); });
-    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5 * h, st); });
+    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, st); });
     if (e == cudaSuccess)
-      e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5 * h, 0.5 * h, last ? 1 : 2, st); });
+      e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st); });
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   double sum[MX_NKERN] = {0};
@@ -524,8 +799,7 @@ mx_status mx_kepler_drift(mx_system* s, double* dev_xv, double h) {
 mx_status mx_energy(mx_system* s, double* E, double* L3) {
   if (!s || !E || !L3) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
-  const mx_params& p = s->params[0];
-  mx::launch_energy(s->d, 1.0 / p.G, p.m_star, s->d_energy, s->st);
+  mx::launch_energy(s->d, s->d_energy, s->st);
   double o[7];
   MX_CUDA(cudaMemcpyAsync(o, s->d_energy, sizeof(o), cudaMemcpyDeviceToHost, s->st));
   MX_TRY(sync_status(s));

@@ -45,6 +45,7 @@ struct SysDev {
   int boff;       // index of its first big body in the compact big arrays
   double mu0, inv_mu0, sqrt_mu0;
   double h;       // step
+  double inv_G, m_star;
   // gas (Sec. 3.1)
   int gas_on, cd_mode, gamma_one, flare_quarter;
   int rc_inf, pad0;
@@ -78,10 +79,15 @@ struct Dev {
   int* work_sys;   // [work_cap]
   int* work_wfrom; // [work_cap]
   int* work_nsub;  // [work_cap] macro sub-steps used (diagnostic)
+  int* cont_count; // groups handed from the packed to the spread BS phase
+  int* cont_item;  // [cont_cap] their work items
+  double* cont_state; // [cont_cap x (3 + 6 x 4)] their integration state
+  int cont_cap;
   unsigned* status;
   const SysDev* sys;
   const Tile* tiles;
   int N, NB, nsys, ntiles;
+  int tile;        // targets per tile = threads per block of the per-body kernels
   int pair_cap, work_cap, mem_cap;
   int kepler_max_iter, bs_max_sub;
   double bs_tol;
@@ -132,9 +138,10 @@ __device__ __forceinline__ bool finite_d(double a) { return isfinite(a); }
 // (Sec. 2.1.3: momentum of massive bodies only).  Every kernel that applies
 // the same jump evaluates this same expression, so a big body's staged
 // position and its own update agree bit for bit.
-__device__ __forceinline__ void jump_vec(const double* P, const SysDev& S, double jump_h,
+// jump_frac is the jump's length in units of the system's step h.
+__device__ __forceinline__ void jump_vec(const double* P, const SysDev& S, double jump_frac,
                                          double* dj) {
-  const double c = jump_h * S.inv_mu0;
+  const double c = (jump_frac * S.h) * S.inv_mu0;
   dj[0] = c * P[0];
   dj[1] = c * P[1];
   dj[2] = c * P[2];

@@ -12,17 +12,17 @@ void launch_init_sys(const Dev& d, int do_rcrit, double rcrit_hill, cudaStream_t
 void launch_init_bodies(const Dev& d, const double* rp_km, const double* rho, int set_drag,
                         cudaStream_t st);
 void launch_readout(const Dev& d, double* out, cudaStream_t st);
-void launch_energy(const Dev& d, double inv_G, double m_star, double* out, cudaStream_t st);
+void launch_energy(const Dev& d, double* out, cudaStream_t st);
 void launch_dfma(double* sink, int blocks, int iters, cudaStream_t st);
 
 // k_kick.cu
-void launch_prep(const Dev& d, double jump_h, cudaStream_t st);
-void launch_jump_kick(const Dev& d, double jump_h, double kick_h, int nkick, cudaStream_t st);
+void launch_prep(const Dev& d, double jump_frac, cudaStream_t st);
+void launch_jump_kick(const Dev& d, double jump_frac, double kick_frac, int nkick, cudaStream_t st);
 void launch_accel(const Dev& d, double* acc, int drag_only, int acc_stride, int acc_base,
                   cudaStream_t st);
 
 // k_drift.cu
-void launch_jump_drift(const Dev& d, double jump_h, cudaStream_t st);
+void launch_jump_drift(const Dev& d, double jump_frac, cudaStream_t st);
 void launch_drift_buf(double* xv, int n, double mu, double h, int maxit, unsigned* status,
                       cudaStream_t st);
 

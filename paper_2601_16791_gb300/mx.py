@@ -69,6 +69,12 @@ _SIGS = {
     "mx_last_error": (ctypes.c_char_p, []),
     "mx_fp64_peak": (_I, [_P, _D, _P]),
     "mx_detect_encounters_noalloc": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P, _P]),
+    "mx_init_batch": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "mx_batch_offsets": (_I, [_P, _P]),
+    "mx_batch_size": (_I, [_P, _P, _P]),
+    "mx_energy_batch": (_I, [_P, _P, _P]),
+    "mx_tiling": (_I, [_P, _P, _P]),
+    "mx_set_tiling": (_I, [_P, _I, _I]),
 }
 
 
@@ -229,6 +235,87 @@ def mx_fp64_peak(stream=None, ms_target=200.0):
     st = ctypes.c_void_p(stream) if stream else None
     _check(load().mx_fp64_peak(st, float(ms_target), ctypes.byref(t)), "mx_fp64_peak")
     return t.value
+
+
+def mx_init_batch(workloads, stream=None):
+    """One mx_system holding every workload of the list (the batched ensemble)."""
+    L = load()
+    k = len(workloads)
+    params = (MxParams * k)(*[make_params(w.params) for w in workloads])
+    nb = (ctypes.c_int * k)(*[w.nbig for w in workloads])
+    ns = (ctypes.c_int * k)(*[w.nsmall for w in workloads])
+    keep = []
+
+    def ptrs(arrs):
+        arr = (ctypes.c_void_p * k)()
+        for q, a in enumerate(arrs):
+            a = _host(a)
+            keep.append(a)
+            arr[q] = a.ctypes.data
+        return arr
+    m = ptrs([w.m_big for w in workloads])
+    xv = ptrs([w.xv_helio for w in workloads])
+    rp = ptrs([w.rp_km for w in workloads])
+    rh = ptrs([w.rhop for w in workloads])
+    out = ctypes.c_void_p()
+    st = ctypes.c_void_p(stream) if stream else None
+    _check(L.mx_init_batch(k, params, nb, ns, m, xv, rp, rh, st, ctypes.byref(out)),
+           "mx_init_batch")
+    return out
+
+
+def mx_batch_offsets(sys, n_sys):
+    off = np.empty(n_sys + 1, dtype=np.int32)
+    _check(load().mx_batch_offsets(sys, _hptr(off)), "mx_batch_offsets")
+    return off
+
+
+def mx_energy_batch(sys, n_sys):
+    E = np.empty(n_sys)
+    L3 = np.empty((n_sys, 3))
+    _check(load().mx_energy_batch(sys, _hptr(E), _hptr(L3)), "mx_energy_batch")
+    return E, L3
+
+
+def mx_tiling(sys):
+    t, o = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().mx_tiling(sys, ctypes.byref(t), ctypes.byref(o)), "mx_tiling")
+    return t.value, o.value
+
+
+def mx_set_tiling(sys, tile, order):
+    _check(load().mx_set_tiling(sys, int(tile), int(order)), "mx_set_tiling")
+
+
+class Batch:
+    """Owns one mx_system with many systems (mx_init_batch)."""
+
+    def __init__(self, workloads, stream=None):
+        self.ws = list(workloads)
+        self.h = mx_init_batch(self.ws, stream)
+        self.offsets = mx_batch_offsets(self.h, len(self.ws))
+        self.n = int(self.offsets[-1])
+
+    def step(self, n):
+        mx_step(self.h, n)
+
+    def state(self, coords=MX_COORD_HELIO):
+        return mx_get_state(self.h, self.n, coords)[0]
+
+    def system_state(self, k, coords=MX_COORD_HELIO):
+        xv = self.state(coords)
+        return xv[:, self.offsets[k]:self.offsets[k + 1]]
+
+    def close(self):
+        if self.h:
+            mx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class System:
