@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--impl", default="mx", choices=["mx", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and adjoint legs")
+    ap.add_argument("--ensemble-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -259,6 +261,95 @@ def whole_job_rate(bodies_per_rank, steps, world, t_max_s):
     return world * bodies_per_rank * steps / t_max_s
 
 
+# ------------------------------------------------- ensemble and adjoint legs
+def ensemble_leg(steps, nsys=256):
+    """256 systems (2-50 embryos, 1e3-2e5 planetesimals each, gas with Sigma
+    x U[0.3, 3]): one batched mx_system vs a host loop calling mx_step on one
+    mx_system per system.  Both advance every system by `steps` steps."""
+    import torch
+    from paper_2601_16791_gb300 import mx, workloads as W
+    ws = W.ensemble_256(nsys=nsys)
+    n_tot = sum(w.n for w in ws)
+    st = torch.cuda.current_stream()
+    b = mx.Batch(ws, stream=st.cuda_stream)
+    tile, order = mx.mx_tiling(b.h)
+    b.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    b.close()
+    systems = [mx.System(w, stream=st.cuda_stream) for w in ws]
+    for s in systems:
+        s.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for s in systems:
+            s.step(1)
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    for s in systems:
+        s.close()
+    return {"workload": "ensemble_256: 256 systems, 2-50 embryos and 1e3-2e5 planetesimals each, "
+                        "gas Sigma x U[0.3,3], dt=10 d",
+            "n_systems": nsys, "n_bodies": n_tot, "steps": steps,
+            "batched_value": n_tot * steps / t_batch, "loop_value": n_tot * steps / t_loop,
+            "unit": UNIT, "speedup": t_loop / t_batch, "tile": tile, "tile_order": order,
+            "timing": "host wall clock around mx_step with device synchronisation"}
+
+
+def adjoint_leg(nsteps=200, every=50):
+    """Cost of one hand-written adjoint step against one forward step on the
+    adjoint workload (4 cores + 50,000 planetesimals with gas)."""
+    import torch
+    from paper_2601_16791_gb300 import mx, workloads as W
+    from paper_2601_16791_gb300.autograd import Trajectory, semimajor_loss
+    w = W.adjoint_4core_50k(nsteps=nsteps, checkpoint_every=every)
+    traj = Trajectory(w, stream=torch.cuda.current_stream().cuda_stream)
+    g = w.params["gas"]
+    xv0 = torch.tensor(w.xv_helio, dtype=torch.float64, device="cuda", requires_grad=True)
+    gas = torch.tensor([g["sigma1_gcm2"], g["gamma"], g["cd_scale"]], dtype=torch.float64,
+                       device="cuda", requires_grad=True)
+    wts = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    wts[w.nbig:] = 1.0 / w.nsmall
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = semimajor_loss(traj, xv0, gas, wts, nsteps, every)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    # one forward step and one adjoint step, same state, CUDA events
+    z = torch.empty((6, w.n), dtype=torch.float64, device="cuda")
+    mx.mx_get_state_device(traj.h, z)
+    lam = torch.randn((6, w.n), dtype=torch.float64, device="cuda")
+    dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    reps = 20
+    mx.mx_step(traj.h, 1)
+    e[0].record()
+    for _ in range(reps):
+        mx.mx_set_state_device(traj.h, z)
+        mx.mx_step(traj.h, 1)
+    e[1].record()
+    e[2].record()
+    for _ in range(reps):
+        mx.mx_adjoint_step(traj.h, z, 0, lam, dpar)
+    e[3].record()
+    torch.cuda.synchronize()
+    f_ms = e[0].elapsed_time(e[1]) / reps
+    a_ms = e[2].elapsed_time(e[3]) / reps
+    traj.close()
+    return {"workload": "adjoint_4core_50k: 4 cores + 50,000 planetesimals, gas, loss on final a",
+            "steps": nsteps, "checkpoint_every": every, "forward_s": t_fwd, "backward_s": t_bwd,
+            "backward_over_forward": t_bwd / t_fwd, "adjoint_step_ms": a_ms,
+            "forward_step_ms": f_ms, "adjoint_over_forward_step": a_ms / f_ms}
+
+
 # ------------------------------------------------------------------- main
 def run_mx(args):
     import torch
@@ -352,6 +443,15 @@ def run_mx(args):
                     "d2h_bytes_per_step": 48 * w.n, "steps": ne,
                     "api": "mx_set_state + mx_step + mx_get_state (pinned host buffers)"}}
     sysm.close()
+    if not args.no_extra:
+        try:
+            line["batched"] = ensemble_leg(args.ensemble_steps)
+        except Exception as exc:  # reported, not hidden
+            line["batched"] = {"error": str(exc)[:300]}
+        try:
+            line["adjoint"] = adjoint_leg()
+        except Exception as exc:
+            line["adjoint"] = {"error": str(exc)[:300]}
     if not args.no_cpu_baseline:
         cb, _, _ = oracle_rate(w, 12.0)
         line["cpu_baseline"] = cb

@@ -249,6 +249,61 @@ mx_status mx_set_state(mx_system* s, const double* xv_host, int coords, long lon
 mx_status mx_get_state_device(mx_system* s, double* dev_xv);
 mx_status mx_set_state_device(mx_system* s, const double* dev_xv);
 
+/* ------------------------------------------------------------------------
+ * Differentiation: a hand-written adjoint (reverse mode) of the hybrid step.
+ * The spec loss is the squared change of the planetesimals' semimajor
+ * axes; its gradient is taken with respect to the initial heliocentric state
+ * and to the gas parameters (Sigma normalisation, Sigma slope, C_D factor).
+ * Bodies that met an encounter are massless and are left out of the loss
+ * (weight 0), so Bulirsch-Stoer is never differentiated; an encounter
+ * between two big bodies makes the adjoint inapplicable (the caller checks
+ * mx_encounter_log).  The Python layer (paper_2601_16791_gb300.autograd)
+ * drives checkpointing: the state is stored every k steps and each segment is
+ * recomputed before its reverse sweep.
+ * ------------------------------------------------------------------------ */
+
+/* Gas parameters of system k (Sec. 3.1): Sigma at 1 AU, slope gamma (Eq. 1),
+ * and the factor on C_D (Eq. 7).  Takes effect at the next launch. */
+mx_status mx_set_gas_params(mx_system* s, int k, double sigma1_gcm2, double gamma,
+                            double cd_scale);
+
+/* The k switch of Eq. 7 (k = 0.4 below Re = 1e5, 0.2 above) is a jump; for
+ * finite differences and for the adjoint's recomputation the branch taken at
+ * each (half kick, planetesimal) can be recorded and replayed.
+ * mode 0: off; 1: record (clears, room for max_kicks half kicks, counted from
+ * step 0 as 2 per step); 2: replay the recording. */
+mx_status mx_kick_branches(mx_system* s, int mode, long long max_kicks);
+
+/* Encounter log since the last reset: dev_ever [N] bytes (device, may be
+ * NULL) = 1 for every body flagged in any step; *n_big_big = flagged big-big
+ * pairs summed over steps.  reset != 0 clears the log afterwards. */
+mx_status mx_encounter_log(mx_system* s, unsigned char* dev_ever, long long* n_big_big,
+                           int reset);
+
+/* Sets the step counter (used to index recorded branches). */
+mx_status mx_set_step_index(mx_system* s, long long step);
+
+/* Loss at the current state against the initial heliocentric state
+ * dev_xv_helio0 (6xN, device): L[k] = sum over bodies j of system k of
+ * w[j] (a_final,j - a_initial,j)^2, a = 1/(2/r - v^2/gm) (gm = G m0 for
+ * planetesimals, G (m0 + m) for big bodies; Sec. 3.5).  dev_w [N] device.
+ * Writes L [n_sys] (host), dev_seed_final (6xN device: dL/d of the current DH
+ * state) and dev_seed_init (6xN device: dL/d of the initial heliocentric
+ * state through a_initial). */
+mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const double* dev_w,
+                            double* L, double* dev_seed_final, double* dev_seed_init);
+
+/* Reverse of one hybrid step.  dev_state_k: 6xN DH state at the start of
+ * step step_k (device); dev_lambda: 6xN cotangent of the state at the end of
+ * the step, replaced by the cotangent at its start; dev_dparams [3 n_sys]
+ * (device) accumulates d/d(sigma1, gamma, cd_scale) of each system. */
+mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long step_k,
+                          double* dev_lambda, double* dev_dparams);
+
+/* Reverse of the set-up transform: cotangent of the initial DH state ->
+ * cotangent of the initial heliocentric state (6xN device buffers). */
+mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_grad_helio);
+
 /* Sizes of the system. */
 mx_status mx_sizes(mx_system* s, int* n_big, int* n_small);
 

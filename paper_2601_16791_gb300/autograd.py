@@ -1,0 +1,119 @@
+"""Differentiable runs of the hybrid step: a torch.autograd.Function whose
+backward is the library's hand-written adjoint (mx_adjoint_step), with the
+state checkpointed every k steps and each segment recomputed before its
+reverse sweep.
+
+The loss is the weighted squared change of semimajor axes,
+    L = sum_j w_j (a_final,j - a_initial,j)^2,
+with a from the heliocentric state (mx_loss_semimajor).  Bodies flagged for an
+encounter in any step of the forward run get weight 0 (they are massless, so
+nothing else depends on them, and their Bulirsch-Stoer steps are not
+differentiated).  An encounter between two big bodies makes the backward
+raise MX_ERR_ENCOUNTER_IN_ADJOINT.  The k switch of the drag coefficient is
+recorded in the forward run and replayed in the recomputation, so the
+reverse sweep sees the branches the forward run took.
+
+Inputs: the initial heliocentric state (6 x N float64 CUDA tensor) and the
+gas parameters (sigma1 [g/cm^2], gamma, cd_scale) as a 3-vector.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import mx
+
+
+def _dev(t):
+    return t.contiguous()
+
+
+class Trajectory:
+    """An mx_system kept for differentiable runs of one workload."""
+
+    def __init__(self, workload, stream=None):
+        self.w = workload
+        self.sys = mx.System(workload, stream)
+        self.h = self.sys.h
+        self.n = workload.n
+
+    def run(self, xv_helio0, gas, nsteps, every, record=True, replay=False, keep=True):
+        """Forward run from xv_helio0 with gas parameters; returns the
+        checkpoints [(step, state)] and the encounter mask (N bytes)."""
+        mx.mx_set_gas_params(self.h, 0, float(gas[0]), float(gas[1]), float(gas[2]))
+        mx.mx_set_state(self.h, xv_helio0.detach().cpu().numpy(), mx.MX_COORD_HELIO, 0)
+        mx.mx_encounter_log(self.h, None, reset=True)
+        if record:
+            mx.mx_kick_branches(self.h, 1, 2 * nsteps + 2)
+        elif replay:
+            mx.mx_kick_branches(self.h, 2)
+        ckpts = []
+        for start in range(0, nsteps, every):
+            if keep:
+                ck = torch.empty((6, self.n), dtype=torch.float64, device="cuda")
+                mx.mx_get_state_device(self.h, ck)
+                ckpts.append((start, ck))
+            mx.mx_step(self.h, min(every, nsteps - start))
+        ever = torch.zeros(self.n, dtype=torch.uint8, device="cuda")
+        nbb = mx.mx_encounter_log(self.h, ever, reset=False)
+        return ckpts, ever, nbb
+
+    def loss(self, xv_helio0, w_eff):
+        """Loss at the current state and its seeds (final DH, initial helio)."""
+        seed_f = torch.empty((6, self.n), dtype=torch.float64, device="cuda")
+        seed_i = torch.empty((6, self.n), dtype=torch.float64, device="cuda")
+        L = mx.mx_loss_semimajor(self.h, _dev(xv_helio0), _dev(w_eff), seed_f, seed_i)
+        return float(L[0]), seed_f, seed_i
+
+    def loss_at(self, xv_helio0, gas, w_eff, nsteps, every):
+        """Loss of a run that replays the recorded branches (finite differences)."""
+        self.run(xv_helio0, gas, nsteps, every, record=False, replay=True, keep=False)
+        return self.loss(xv_helio0, w_eff)[0]
+
+    def close(self):
+        self.sys.close()
+
+
+class SemimajorLoss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xv_helio0, gas, traj, w, nsteps, every):
+        ckpts, ever, nbb = traj.run(xv_helio0, gas, nsteps, every, record=True)
+        w_eff = w * (1.0 - ever.to(torch.float64))
+        L, seed_f, seed_i = traj.loss(xv_helio0, w_eff)
+        ctx.traj, ctx.nsteps, ctx.every, ctx.nbb = traj, nsteps, every, nbb
+        ctx.ckpts = ckpts
+        ctx.save_for_backward(seed_f, seed_i)
+        ctx.w_eff = w_eff
+        return torch.tensor(L, dtype=torch.float64, device=xv_helio0.device)
+
+    @staticmethod
+    def backward(ctx, gL):
+        traj = ctx.traj
+        if ctx.nbb > 0:
+            raise mx.MxError(9, "SemimajorLoss.backward",
+                             f"{ctx.nbb} big-big encounter pairs in the forward run")
+        seed_f, seed_i = ctx.saved_tensors
+        g = float(gL)
+        h = traj.h
+        mx.mx_kick_branches(h, 2)
+        lam = (seed_f * g).contiguous()
+        dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
+        seg = torch.empty((ctx.every, 6, traj.n), dtype=torch.float64, device="cuda")
+        for start, ck in reversed(ctx.ckpts):
+            length = min(ctx.every, ctx.nsteps - start)
+            mx.mx_set_state_device(h, ck)
+            mx.mx_set_step_index(h, start)
+            for k in range(length):
+                mx.mx_get_state_device(h, seg[k])
+                if k + 1 < length:
+                    mx.mx_step(h, 1)
+            for k in reversed(range(length)):
+                mx.mx_adjoint_step(h, seg[k], start + k, lam, dpar)
+        grad0 = torch.empty((6, traj.n), dtype=torch.float64, device="cuda")
+        mx.mx_adjoint_init(h, lam, grad0)
+        grad0 += g * seed_i
+        return grad0, dpar, None, None, None, None
+
+
+def semimajor_loss(traj, xv_helio0, gas, w, nsteps, every):
+    """Differentiable loss of a run of nsteps steps checkpointed every `every`."""
+    return SemimajorLoss.apply(xv_helio0, gas, traj, w, int(nsteps), int(every))

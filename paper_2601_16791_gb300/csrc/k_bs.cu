@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
     }
     s_nnodes = nn;
     s_ncomp = nc;
+    if (d.bb_count && nbb > 0) atomicAdd(d.bb_count, (unsigned long long)nbb);
     s_bw = nc;
     s_bm = m;
   }

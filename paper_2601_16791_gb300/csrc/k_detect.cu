@@ -144,6 +144,10 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
                         ((unsigned long long)(unsigned)j << 32) | (unsigned)gi;
           flags[gi] = 1;
           flags[j] = 1;
+          if (d.ever) {
+            d.ever[gi] = 1;
+            d.ever[j] = 1;
+          }
         }
       }
     }

@@ -9,95 +9,9 @@
 // parallel loop), so results do not depend on the launch shape.
 #include "mx_common.cuh"
 #include "mx_kernels.h"
+#include "mx_physics.cuh"
 
 namespace mx {
-
-// Drag acceleration (Eq. 3) of one planetesimal at heliocentric position
-// (x, y, z) moving with heliocentric velocity (u, v, w).  Quantities follow
-// Sec. 3.1: Sigma (Eq. 1, normalised at 1 AU), rho_g (Eq. 4) at the midplane,
-// v_g = v_k sqrt(1 - 2 eta) (Eqs. 5, 6), C_D (Eq. 7) from Re and Ma.
-// kd = 3 / (8 r_p[AU] rho_p); rp_cm = r_p in cm.
-__device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, double z, double u,
-                                         double v, double w, double rp_cm, double kd, double* a) {
-  a[0] = a[1] = a[2] = 0.0;
-  const double R2 = fma(x, x, y * y);
-  const double iR = rsqrt_d(R2);             // 1/R
-  const double R = R2 * iR;
-  if (R < S.r_in) return;                    // no gas inside the inner edge (Sec. 3.1.1)
-  double sigma, rmh, rcs, reta, inv_cs;      // Sigma, R^-(1+f), R^(f-1/2), R^(2f), 1/c_s
-  const double ih = rsqrt_d(R);              // R^-1/2
-  if (S.flare_quarter) {
-    const double q = rsqrt_d(ih);            // R^1/4
-    rcs = q * ih;                            // R^-1/4
-    rmh = iR * rcs;                          // R^-5/4
-    reta = R * ih;                           // R^1/2
-    inv_cs = q * S.inv_c_cs;
-  } else {
-    const double lr = log(R);
-    rcs = exp((S.flare - 0.5) * lr);
-    rmh = exp(-(1.0 + S.flare) * lr);
-    reta = exp(2.0 * S.flare * lr);
-    inv_cs = rcp_d(S.c_cs * rcs);
-  }
-  if (S.gamma_one) sigma = S.sigma1 * iR;
-  else sigma = S.sigma1 * exp(-S.gamma * log(R));
-  if (!S.rc_inf) sigma *= exp(-pow(R * S.inv_rc, 2.0 - S.gamma));
-  const double rho = S.c_rho * sigma * rmh;
-  const double vk = S.sqrt_mu0 * ih;
-  const double t = fma(-2.0 * S.c_eta, reta, 1.0);   // 1 - 2 eta
-  const double vg = vk * (t * rsqrt_d(t));
-  const double g = vg * iR;                  // gas velocity = g * (-y, x, 0)
-  const double du = fma(g, y, u);
-  const double dv = fma(-g, x, v);
-  const double dw = w;
-  const double dv2 = fma(du, du, fma(dv, dv, dw * dw));
-  if (dv2 == 0.0) return;
-  const double dvm = dv2 * rsqrt_d(dv2);
-  const double Ma = dvm * inv_cs;
-  const double Re = S.c_re * rp_cm * Ma * rho;
-  const double k = (Re < 1e5) ? 0.4 : 0.2;
-  // Eq. 7 with one reciprocal: [(24/Re + 40/(10+Re))^-1 + 0.23 Ma]^-1 = D/den1
-  // where D = 240 + 64 Re and den1 = Re (10 + Re) + 0.23 Ma D.
-  const double D = fma(64.0, Re, 240.0);
-  const double den1 = fma(0.23 * Ma, D, Re * (10.0 + Re));
-  const double A = 1.6 + Ma;
-  const double r = rcp_d(den1 * A);
-  const double first = D * A * r;           // = D / den1
-  const double second = fma(2.0, Ma, 1.6 * k) * den1 * r;
-  const double cd = (S.cd_mode == 1) ? fma(first, first, second) : first + second;
-  const double coef = S.cd_scale * cd * kd * rho * dvm;
-  a[0] = -coef * du;
-  a[1] = -coef * dv;
-  a[2] = -coef * dw;
-}
-
-// K(s)/s^3 times mu for one pair, accumulated into (ax, ay, az) as -f * d
-// (Sec. 2.1.3: K = 1 for s^2 >= rc^2, 0 for s^2 <= 0.01 rc^2, quintic between).
-__device__ __forceinline__ void pair_acc(double dx, double dy, double dz, double mu, double rc2,
-                                         double rc2lo, double rc01, double i09rc, double& ax,
-                                         double& ay, double& az) {
-  const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
-  const double yy = rsqrt_d(s2);
-  double f = yy * yy * yy;
-  if (s2 < rc2) {
-    if (s2 <= rc2lo) {
-      f = 0.0;
-    } else {
-      const double q = (s2 * yy - rc01) * i09rc;
-      f *= q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
-    }
-  }
-  f *= mu;
-  ax = fma(-f, dx, ax);
-  ay = fma(-f, dy, ay);
-  az = fma(-f, dz, az);
-}
-
-// Shared-memory staging of one chunk of big bodies.
-struct BigSmem {
-  double x[kBigChunk], y[kBigChunk], z[kBigChunk], mu[kBigChunk];
-  double rc[kBigChunk], rc2[kBigChunk], rc2lo[kBigChunk], rc01[kBigChunk], i09rc[kBigChunk];
-};
 
 __device__ __forceinline__ void stage_bigs(const Dev& d, const SysDev& S, int c0, int cn,
                                            BigSmem& sb) {
@@ -145,8 +59,14 @@ __device__ __forceinline__ void gravity_all(const Dev& d, const SysDev& S, BigSm
 
 // Momentum of each system's massive bodies and the staged big positions.
 // One block per system; a fixed partition and tree keep the sum deterministic.
-__global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac) {
+// nkick > 0: the kernel that follows makes nkick half kicks; the kick counter
+// (for recording or replaying the k branch of Eq. 7) advances here.
+__global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int nkick) {
   const SysDev& S = d.sys[blockIdx.x];
+  if (nkick > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    d.kick_ctr[1] = d.kick_ctr[0];
+    d.kick_ctr[0] += nkick;
+  }
   __shared__ double red[3][kThreads];
   const int N = d.N;
   double p[3] = {0.0, 0.0, 0.0};
@@ -217,10 +137,19 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
   const bool drag = S.gas_on && jl >= S.nbig;
   const double hp0 = P[0] * S.inv_mu0, hp1 = P[1] * S.inv_mu0, hp2 = P[2] * S.inv_mu0;
   const double rp = drag ? d.rp_cm[j] : 0.0, kd = drag ? d.kdrag[j] : 0.0;
+  const int kbase = d.kmode ? d.kick_ctr[1] : 0;
 #pragma unroll
   for (int kk = 0; kk < NKICK; ++kk) {
     double a[3] = {0.0, 0.0, 0.0};
-    if (drag) gas_drag(S, x, y, z, u + hp0, v + hp1, w + hp2, rp, kd, a);
+    if (drag) {
+      const int kidx = kbase + kk;
+      const bool kuse = d.kmode != 0 && kidx < d.kcap;
+      const size_t word = (size_t)kidx * d.kwords + (j >> 5);
+      int kin = -1, kout = 0;
+      if (kuse && d.kmode == 2) kin = (d.kbits[word] >> (j & 31)) & 1u;
+      gas_drag(S, x, y, z, u + hp0, v + hp1, w + hp2, rp, kd, a, kin, &kout);
+      if (kuse && d.kmode == 1 && kout) atomicOr(&d.kbits[word], 1u << (j & 31));
+    }
     u = fma(kick_h, ax + a[0], u);
     v = fma(kick_h, ay + a[1], v);
     w = fma(kick_h, az + a[2], w);
@@ -259,8 +188,9 @@ __global__ void __launch_bounds__(kThreads) k_accel(Dev d, double* acc, int drag
   const bool drag = S.gas_on && jl >= S.nbig;
   double a[3] = {0.0, 0.0, 0.0};
   if (drag) {
+    int kout = 0;
     gas_drag(S, x, y, z, u + P[0] * S.inv_mu0, v + P[1] * S.inv_mu0, w + P[2] * S.inv_mu0,
-             d.rp_cm[j], d.kdrag[j], a);
+             d.rp_cm[j], d.kdrag[j], a, -1, &kout);
   }
   if (drag_only) {
     if (jl < S.nbig) return;
@@ -275,8 +205,8 @@ __global__ void __launch_bounds__(kThreads) k_accel(Dev d, double* acc, int drag
   }
 }
 
-void launch_prep(const Dev& d, double jump_frac, cudaStream_t st) {
-  k_prep<<<d.nsys, kThreads, 0, st>>>(d, jump_frac);
+void launch_prep(const Dev& d, double jump_frac, int nkick, cudaStream_t st) {
+  k_prep<<<d.nsys, kThreads, 0, st>>>(d, jump_frac, nkick);
 }
 
 void launch_jump_kick(const Dev& d, double jump_frac, double kick_frac, int nkick,

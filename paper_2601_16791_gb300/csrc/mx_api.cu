@@ -92,6 +92,7 @@ mx::SysDev make_sysdev(const mx_params& p, int off, int nbig, int n, int boff) {
   s.inv_c_cs = 1.0 / s.c_cs;
   const double beta_T = 1.0 - 2.0 * g.flare;
   s.c_eta = g.hr_1au * g.hr_1au * (g.gamma + beta_T / 2.0 + 1.5) / (2.0 * g.gamma_c);
+  s.deta_dgamma = g.hr_1au * g.hr_1au / (2.0 * g.gamma_c);
   const double c_lam = g.mu_mol * kHydrogenG / g.sigma_mol_cm2;
   s.c_re = 4.0 / (std::sqrt(8.0 / kPi) * c_lam);
   return s;
@@ -122,6 +123,14 @@ struct mx_system {
   int order = 0;                  // 0: tiles in system order; 1: costliest first
   int tiles_cap = 0;
   std::vector<mx::SysDev> h_sys;
+  // adjoint scratch (allocated on first use)
+  double *a_v1 = nullptr, *a_x2 = nullptr, *a_xv3 = nullptr, *a_x4 = nullptr;
+  double *a_part = nullptr, *a_P = nullptr, *a_L = nullptr;
+  int* a_poff = nullptr;
+  size_t a_part_cap = 0;
+  int a_poff_tiles = -1;          // tile count a_poff was built for
+  int a_poff_tile = -1, a_poff_order = -1;
+  long long kbits_cap = 0;
 };
 
 namespace {
@@ -165,7 +174,7 @@ mx_status sync_status(mx_system* s) {
 // The device work of one interior step, or the last step of a call
 // (one half kick at its end), or the leading half kick.
 void enqueue_head(mx_system* s, cudaStream_t st) {
-  mx::launch_prep(s->d, 0.0, st);
+  mx::launch_prep(s->d, 0.0, 1, st);
   mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st);
 }
 
@@ -176,7 +185,7 @@ void enqueue_step(mx_system* s, int last, cudaStream_t st) {
   mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st);
   mx::launch_groups(s->d, st);
   mx::launch_bs(s->d, s->bs_blocks, st);
-  mx::launch_prep(s->d, 0.5, st);
+  mx::launch_prep(s->d, 0.5, last ? 1 : 2, st);
   mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st);
 }
 
@@ -425,6 +434,13 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_TRY(dalloc(s, &d.work_nsub, work_cap));
   d.cont_cap = std::min(work_cap, 1 << 14);
   MX_TRY(dalloc(s, &d.cont_count, 1));
+  MX_TRY(dalloc(s, &d.ever, N));
+  MX_TRY(dalloc(s, &d.bb_count, 1));
+  MX_TRY(dalloc(s, &d.kick_ctr, 2));
+  d.kbits = nullptr;
+  d.kmode = 0;
+  d.kwords = (N + 31) / 32;
+  d.kcap = 0;
   MX_TRY(dalloc(s, &d.cont_item, d.cont_cap));
   MX_TRY(dalloc(s, &d.cont_state, (size_t)d.cont_cap * 27));
   MX_TRY(dalloc(s, &d.status, 1));
@@ -452,6 +468,9 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemsetAsync(d.status, 0, sizeof(unsigned), st));
   MX_CUDA(cudaMemsetAsync(d.pair_count, 0, 2 * sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.flags, 0, N, st));
+  MX_CUDA(cudaMemsetAsync(d.ever, 0, N, st));
+  MX_CUDA(cudaMemsetAsync(d.bb_count, 0, sizeof(unsigned long long), st));
+  MX_CUDA(cudaMemsetAsync(d.kick_ctr, 0, 2 * sizeof(int), st));
   // host staging: state rows, masses as mu = G m, per-body drag inputs
   std::vector<double> xv((size_t)6 * N), bmu(NB, 0.0), rpb(N, 1.0), rhob(N, 1.0);
   for (int k = 0; k < nsys; ++k) {
@@ -685,7 +704,7 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     return rec();
   };
   cudaError_t e = cudaSuccess;
-  e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, st); });
+  e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
   if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
     const bool last = (k + 1 == n_steps);
@@ -697,7 +716,7 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     if (e == cudaSuccess) e = timed(MX_K_SORT, [&] { mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st); });
     if (e == cudaSuccess) e = timed(MX_K_GROUPS, [&] { mx::launch_groups(s->d, st); });
     if (e == cudaSuccess) e = timed(MX_K_BS, [&] { mx::launch_bs(s->d, s->bs_blocks, st); });
-    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, st); });
+    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, last ? 1 : 2, st); });
     if (e == cudaSuccess)
       e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st); });
   }
@@ -748,7 +767,7 @@ mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pair
 mx_status mx_accel(mx_system* s, double* dev_acc) {
   if (!s || !dev_acc) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
-  mx::launch_prep(s->d, 0.0, s->st);
+  mx::launch_prep(s->d, 0.0, 0, s->st);
   mx::launch_accel(s->d, dev_acc, 0, s->N, 0, s->st);
   return sync_status(s);
 }
@@ -759,7 +778,7 @@ mx_status mx_gas_drag(mx_system* s, double* dev_acc) {
   const int ns = s->nsmall[0];
   if (ns == 0) return MX_OK;
   MX_CUDA(cudaMemsetAsync(dev_acc, 0, (size_t)3 * ns * sizeof(double), s->st));
-  mx::launch_prep(s->d, 0.0, s->st);
+  mx::launch_prep(s->d, 0.0, 0, s->st);
   mx::launch_accel(s->d, dev_acc, 1, ns, s->nbig[0], s->st);
   return sync_status(s);
 }
@@ -773,7 +792,10 @@ mx_status mx_detect_encounters(mx_system* s, const double* dev_xv0, const double
   unsigned char* flags = dev_flags ? dev_flags : s->d.flags;
   MX_CUDA(cudaMemsetAsync(flags, 0, s->N, s->st));
   MX_CUDA(cudaMemsetAsync(s->d.pair_count, 0, sizeof(int), s->st));
-  mx::launch_detect(s->d, dev_xv0, dev_xv1, flags, s->d.keys, s->d.pair_count, s->d.pair_cap, s->st);
+  mx::Dev dd = s->d;
+  dd.ever = nullptr;        // caller-supplied states do not enter the encounter log
+  dd.bb_count = nullptr;
+  mx::launch_detect(dd, dev_xv0, dev_xv1, flags, s->d.keys, s->d.pair_count, s->d.pair_cap, s->st);
   mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 1, s->st);
   if (dev_pairs && cap > 0)
     mx::launch_keys_to_pairs(s->d.keys, s->d.pair_count, std::min(cap, s->d.pair_cap), dev_pairs, s->st);
@@ -816,7 +838,7 @@ mx_status mx_get_state(mx_system* s, double* xv_host, int coords, long long* ste
   MX_TRY(set_device(s));
   const double* src = s->d.xv;
   if (coords == MX_COORD_HELIO) {
-    mx::launch_prep(s->d, 0.0, s->st);
+    mx::launch_prep(s->d, 0.0, 0, s->st);
     mx::launch_readout(s->d, s->d_tmp, s->st);
     src = s->d_tmp;
   }
@@ -835,6 +857,8 @@ mx_status mx_set_state(mx_system* s, const double* xv_host, int coords, long lon
     mx::launch_init_sys(s->d, 0, 0.0, s->st);
     mx::launch_init_bodies(s->d, nullptr, nullptr, 0, s->st);
   }
+  const int ctr[2] = {(int)(2 * step), (int)(2 * step)};
+  MX_CUDA(cudaMemcpyAsync(s->d.kick_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s->st));
   MX_TRY(sync_status(s));
   s->step = step;
   return MX_OK;
@@ -884,6 +908,165 @@ mx_status mx_fp64_peak(void* cuda_stream, double ms_target, double* tflops) {
   cudaEventDestroy(e1);
   cudaFree(sink);
   return MX_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ adjoint
+namespace {
+
+// Per-tile partial records for the adjoint and the loss: 3 doubles per big
+// body of the tile's system plus 9.
+mx_status ensure_adjoint(mx_system* s) {
+  const int N = s->N;
+  if (!s->a_v1) {
+    MX_TRY(dalloc(s, &s->a_v1, (size_t)3 * N));
+    MX_TRY(dalloc(s, &s->a_x2, (size_t)3 * N));
+    MX_TRY(dalloc(s, &s->a_xv3, (size_t)6 * N));
+    MX_TRY(dalloc(s, &s->a_x4, (size_t)3 * N));
+    MX_TRY(dalloc(s, &s->a_P, 9 * s->h_sys.size()));
+    MX_TRY(dalloc(s, &s->a_L, s->h_sys.size()));
+    MX_TRY(dalloc(s, &s->a_poff, s->tiles_cap));
+  }
+  if (s->a_poff_tile == s->tile && s->a_poff_order == s->order) return MX_OK;
+  std::vector<mx::Tile> tiles = make_tiles(s->h_sys, s->tile, s->order);
+  std::vector<int> poff(tiles.size());
+  size_t off = 0;
+  for (size_t t = 0; t < tiles.size(); ++t) {
+    poff[t] = (int)off;
+    off += 3 * (size_t)s->h_sys[tiles[t].sys].nbig + 9;
+  }
+  if (off > (size_t)INT32_MAX) return fail(MX_ERR_ARG, "adjoint partials too large");
+  if (off > s->a_part_cap) {
+    MX_TRY(dalloc(s, &s->a_part, off));
+    s->a_part_cap = off;
+  }
+  MX_CUDA(cudaMemcpyAsync(s->a_poff, poff.data(), poff.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  s->a_poff_tile = s->tile;
+  s->a_poff_order = s->order;
+  return MX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mx_status mx_set_gas_params(mx_system* s, int k, double sigma1, double gamma, double cd_scale) {
+  if (!s || k < 0 || k >= (int)s->h_sys.size() || !std::isfinite(sigma1) || !std::isfinite(gamma) ||
+      !std::isfinite(cd_scale))
+    return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  mx_params& p = s->params[k];
+  p.gas.sigma1_gcm2 = sigma1;
+  p.gas.gamma = gamma;
+  p.gas.cd_scale = cd_scale;
+  const mx::SysDev old = s->h_sys[k];
+  mx::SysDev nw = make_sysdev(p, old.off, old.nbig, old.n, old.boff);
+  s->h_sys[k] = nw;
+  MX_CUDA(cudaMemcpyAsync(s->d_sys + k, &s->h_sys[k], sizeof(mx::SysDev), cudaMemcpyHostToDevice, s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  return MX_OK;
+}
+
+mx_status mx_kick_branches(mx_system* s, int mode, long long max_kicks) {
+  if (!s || mode < 0 || mode > 2 || max_kicks < 0 || max_kicks > (1LL << 30))
+    return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  if (mode == 0) {
+    s->d.kmode = 0;
+    drop_graphs(s);
+    return MX_OK;
+  }
+  if (mode == 1) {
+    const size_t words = (size_t)max_kicks * s->d.kwords;
+    if (max_kicks > s->kbits_cap) {
+      if (s->d.kbits) {
+        cudaFree(s->d.kbits);
+        s->allocs.erase(std::remove(s->allocs.begin(), s->allocs.end(), (void*)s->d.kbits), s->allocs.end());
+        s->d.kbits = nullptr;
+      }
+      MX_TRY(dalloc(s, &s->d.kbits, words));
+      s->kbits_cap = max_kicks;
+    }
+    MX_CUDA(cudaMemsetAsync(s->d.kbits, 0, words * sizeof(unsigned), s->st));
+    s->d.kcap = (int)max_kicks;
+  } else if (!s->d.kbits) {
+    return fail(MX_ERR_ARG, "no recorded branches to replay");
+  }
+  s->d.kmode = mode;
+  drop_graphs(s);
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  return MX_OK;
+}
+
+mx_status mx_encounter_log(mx_system* s, unsigned char* dev_ever, long long* n_big_big, int reset) {
+  if (!s) return fail(MX_ERR_ARG, "NULL system");
+  MX_TRY(set_device(s));
+  if (dev_ever) MX_CUDA(cudaMemcpyAsync(dev_ever, s->d.ever, s->N, cudaMemcpyDeviceToDevice, s->st));
+  unsigned long long bb = 0;
+  MX_CUDA(cudaMemcpyAsync(&bb, s->d.bb_count, sizeof(bb), cudaMemcpyDeviceToHost, s->st));
+  if (reset) {
+    MX_CUDA(cudaMemsetAsync(s->d.ever, 0, s->N, s->st));
+    MX_CUDA(cudaMemsetAsync(s->d.bb_count, 0, sizeof(unsigned long long), s->st));
+  }
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  if (n_big_big) *n_big_big = (long long)bb;
+  return MX_OK;
+}
+
+mx_status mx_set_step_index(mx_system* s, long long step) {
+  if (!s || step < 0 || step > (1LL << 29)) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  const int ctr[2] = {(int)(2 * step), (int)(2 * step)};
+  MX_CUDA(cudaMemcpyAsync(s->d.kick_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  s->step = step;
+  return MX_OK;
+}
+
+mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const double* dev_w,
+                            double* L, double* dev_seed_final, double* dev_seed_init) {
+  if (!s || !dev_xv_helio0 || !dev_w || !L || !dev_seed_final || !dev_seed_init)
+    return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_TRY(ensure_adjoint(s));
+  mx::launch_prep(s->d, 0.0, 0, s->st);
+  mx::launch_loss(s->d, dev_xv_helio0, dev_w, dev_seed_final, dev_seed_init, s->a_part, s->a_poff,
+                  s->a_L, s->st);
+  MX_CUDA(cudaMemcpyAsync(L, s->a_L, s->h_sys.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  return sync_status(s);
+}
+
+mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_grad_helio) {
+  if (!s || !dev_lambda || !dev_grad_helio) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  mx::launch_init_vjp(s->d, dev_lambda, dev_grad_helio, s->st);
+  return sync_status(s);
+}
+
+mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long step_k,
+                          double* dev_lambda, double* dev_dparams) {
+  if (!s || !dev_state_k || !dev_lambda || !dev_dparams || step_k < 0 || step_k > (1LL << 29))
+    return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_TRY(ensure_adjoint(s));
+  const size_t N = s->N;
+  mx::Adj a;
+  a.z0 = dev_state_k;
+  a.v1 = s->a_v1;
+  a.x2 = s->a_x2;
+  a.xv3 = s->a_xv3;
+  a.x4 = s->a_x4;
+  a.lam = dev_lambda;
+  a.part = s->a_part;
+  a.poff = s->a_poff;
+  a.P = s->a_P;
+  a.dpar = dev_dparams;
+  a.step = (int)step_k;
+  (void)N;
+  mx::launch_adjoint_step(s->d, a, s->st);
+  return sync_status(s);
 }
 
 }  // extern "C"

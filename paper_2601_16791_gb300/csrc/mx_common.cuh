@@ -54,6 +54,7 @@ struct SysDev {
   double c_cs;    // c_s  = c_cs * R^(flare-1/2)              [AU/d]
   double inv_c_cs;
   double c_eta;   // eta  = c_eta * R^(2 flare)
+  double deta_dgamma;  // d c_eta / d gamma
   double c_re;    // Re   = c_re * r_p[cm] * Ma * rho_g
 };
 
@@ -83,6 +84,13 @@ struct Dev {
   int* cont_item;  // [cont_cap] their work items
   double* cont_state; // [cont_cap x (3 + 6 x 4)] their integration state
   int cont_cap;
+  unsigned char* ever;          // [N] bodies flagged since the log was reset
+  unsigned long long* bb_count; // big-big pairs flagged since the log was reset
+  int* kick_ctr;   // [0]: half kicks made so far, [1]: index of the next launch's first
+  unsigned* kbits; // recorded k branch of Eq. 7, one bit per (half kick, body)
+  int kmode;       // 0: compute k from Re, 1: record, 2: replay
+  int kwords;      // 32-bit words per half kick
+  int kcap;        // half kicks the bit array holds
   unsigned* status;
   const SysDev* sys;
   const Tile* tiles;
@@ -91,6 +99,21 @@ struct Dev {
   int pair_cap, work_cap, mem_cap;
   int kepler_max_iter, bs_max_sub;
   double bs_tol;
+};
+
+// Buffers of one adjoint step (k_adjoint.cu).
+struct Adj {
+  const double* z0;   // 6 x N state at the start of the step
+  double* v1;         // 3 x N after kick 1
+  double* x2;         // 3 x N after jump 1
+  double* xv3;        // 6 x N after the drift
+  double* x4;         // 3 x N after jump 2
+  double* lam;        // 6 x N cotangent, in/out
+  double* part;       // per-tile partial sums
+  const int* poff;    // [ntiles] offset of each tile's partial record
+  double* P;          // 9 per system: P0, P1, P3
+  double* dpar;       // 3 per system, accumulated
+  int step;           // index of the step (recorded k branches)
 };
 
 // ------------------------------------------------------------------ helpers

@@ -1,0 +1,115 @@
+// mx_kepler.cuh -- universal-variable Kepler drift (arXiv 2601.16791, Sec. 2:
+// the Keplerian part of the hybrid step), shared by the drift kernels and the
+// adjoint.  See k_drift.cu for the method.
+#pragma once
+#include "mx_common.cuh"
+
+namespace mx {
+
+// c2(z) = sum_k (-z)^k/(2k+2)!, c3(z) = sum_k (-z)^k/(2k+3)!, eight terms,
+// accurate to FP64 for |z| <= 0.3.
+__device__ __forceinline__ void stumpff_series(double z, double& c2, double& c3) {
+  c2 = 1.0 / 20922789888000.0;      // 1/16!
+  c3 = 1.0 / 355687428096000.0;     // 1/17!
+  c2 = fma(-z, c2, 1.0 / 87178291200.0);
+  c3 = fma(-z, c3, 1.0 / 1307674368000.0);
+  c2 = fma(-z, c2, 1.0 / 479001600.0);
+  c3 = fma(-z, c3, 1.0 / 6227020800.0);
+  c2 = fma(-z, c2, 1.0 / 3628800.0);
+  c3 = fma(-z, c3, 1.0 / 39916800.0);
+  c2 = fma(-z, c2, 1.0 / 40320.0);
+  c3 = fma(-z, c3, 1.0 / 362880.0);
+  c2 = fma(-z, c2, 1.0 / 720.0);
+  c3 = fma(-z, c3, 1.0 / 5040.0);
+  c2 = fma(-z, c2, 1.0 / 24.0);
+  c3 = fma(-z, c3, 1.0 / 120.0);
+  c2 = fma(-z, c2, 0.5);
+  c3 = fma(-z, c3, 1.0 / 6.0);
+}
+
+// c0..c3 for any z: quarter the argument into the series range, then apply
+// c0(4z) = 2c0^2 - 1, c1(4z) = c0 c1, c2(4z) = c1^2/2, c3(4z) = (c2 + c0 c3)/4.
+static __device__ __noinline__ void stumpff_reduced(double z, double& c0, double& c1, double& c2,
+                                             double& c3) {
+  int m = 0;
+  while (fabs(z) > 0.3 && m < 60) {
+    z *= 0.25;
+    ++m;
+  }
+  stumpff_series(z, c2, c3);
+  c1 = fma(-z, c3, 1.0);
+  c0 = fma(-z, c2, 1.0);
+  for (; m > 0; --m) {
+    c3 = 0.25 * fma(c0, c3, c2);
+    c2 = 0.5 * c1 * c1;
+    c1 = c0 * c1;
+    c0 = fma(2.0 * c0, c0, -1.0);
+  }
+}
+
+// G0..G3 at s for beta.
+__device__ __forceinline__ void gfuns(double s, double beta, double* G) {
+  const double s2 = s * s;
+  const double z = beta * s2;
+  double c2, c3;
+  if (fabs(z) <= 0.3) {
+    stumpff_series(z, c2, c3);
+  } else {
+    double c0, c1;
+    stumpff_reduced(z, c0, c1, c2, c3);
+  }
+  G[2] = s2 * c2;
+  G[3] = s2 * s * c3;
+  G[1] = fma(-beta, G[3], s);
+  G[0] = fma(-beta, G[2], 1.0);
+}
+
+// Returns false when the iteration cap is reached.
+__device__ __forceinline__ bool kepler_drift(double mu, double h, int maxit, double& x, double& y,
+                                             double& z, double& u, double& v, double& w) {
+  if (h == 0.0) return true;
+  const double r02 = fma(x, x, fma(y, y, z * z));
+  const double ir0 = rsqrt_d(r02);
+  const double r0 = r02 * ir0;
+  const double v2 = fma(u, u, fma(v, v, w * w));
+  const double eta = fma(x, u, fma(y, v, z * w));
+  const double beta = fma(2.0 * mu, ir0, -v2);
+  const double zeta = fma(-beta, r0, mu);
+  // second-order guess s = (h/r0)(1 - eta h / (2 r0^2))
+  double s = h * ir0 * fma(-0.5 * eta * h, ir0 * ir0, 1.0);
+  double G[4];
+  bool done = false;
+  double ds = 0.0;
+  for (int it = 0; it < maxit; ++it) {
+    gfuns(s, beta, G);
+    const double F = fma(r0, s, fma(eta, G[2], fma(zeta, G[3], -h)));
+    const double Fp = fma(eta, G[1], fma(zeta, G[2], r0));
+    const double Fpp = fma(eta, G[0], zeta * G[1]);
+    ds = -F * Fp * rcp_d(fma(Fp, Fp, -0.5 * F * Fpp));
+    s += ds;
+    if (fabs(ds) <= 1e-7 * fabs(s)) {
+      done = true;
+      break;
+    }
+  }
+  if (!done) return false;
+  // carry G to the stepped s: G_k(s0 + ds) = G_k + ds G_{k-1} + ds^2/2 G_{k-2},
+  // with G_{-1} = -beta G1 and G_{-2} = -beta G0.
+  // (f and g need only G1 and G2.)
+  const double hd = 0.5 * ds;
+  const double g2 = fma(ds, fma(hd, G[0], G[1]), G[2]);
+  const double g1 = fma(ds, fma(-hd * beta, G[1], G[0]), G[1]);
+  const double r = fma(eta, g1, fma(zeta, g2, r0));
+  const double ir = rcp_d(r);
+  const double f = fma(-mu * g2, ir0, 1.0);
+  const double g = fma(r0, g1, eta * g2);
+  const double fd = -mu * g1 * ir * ir0;
+  const double gd = fma(-mu * g2, ir, 1.0);
+  const double xn = fma(f, x, g * u), yn = fma(f, y, g * v), zn = fma(f, z, g * w);
+  const double un = fma(fd, x, gd * u), vn = fma(fd, y, gd * v), wn = fma(fd, z, gd * w);
+  x = xn; y = yn; z = zn;
+  u = un; v = vn; w = wn;
+  return true;
+}
+
+}  // namespace mx

@@ -16,7 +16,7 @@ void launch_energy(const Dev& d, double* out, cudaStream_t st);
 void launch_dfma(double* sink, int blocks, int iters, cudaStream_t st);
 
 // k_kick.cu
-void launch_prep(const Dev& d, double jump_frac, cudaStream_t st);
+void launch_prep(const Dev& d, double jump_frac, int nkick, cudaStream_t st);
 void launch_jump_kick(const Dev& d, double jump_frac, double kick_frac, int nkick, cudaStream_t st);
 void launch_accel(const Dev& d, double* acc, int drag_only, int acc_stride, int acc_base,
                   cudaStream_t st);
@@ -37,5 +37,12 @@ void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int 
 // k_bs.cu
 void launch_groups(const Dev& d, cudaStream_t st);
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st);
+
+
+// k_adjoint.cu
+void launch_adjoint_step(const Dev& d, const Adj& a, cudaStream_t st);
+void launch_loss(const Dev& d, const double* xvh0, const double* w, double* seed_f, double* seed_i,
+                 double* part, const int* poff, double* Lsys, cudaStream_t st);
+void launch_init_vjp(const Dev& d, const double* lam, double* grad, cudaStream_t st);
 
 }  // namespace mx

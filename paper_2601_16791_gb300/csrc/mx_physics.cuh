@@ -1,0 +1,102 @@
+// mx_physics.cuh -- per-pair gravity with the changeover weight and the gas
+// drag of one planetesimal (arXiv 2601.16791, Sec. 2.1.3 and Sec. 3.1),
+// shared by the forward kick and the adjoint's recomputation.
+#pragma once
+#include "mx_common.cuh"
+
+namespace mx {
+
+// Drag acceleration (Eq. 3) of one planetesimal at heliocentric position
+// (x, y, z) moving with heliocentric velocity (u, v, w).  Quantities follow
+// Sec. 3.1: Sigma (Eq. 1, normalised at 1 AU), rho_g (Eq. 4) at the midplane,
+// v_g = v_k sqrt(1 - 2 eta) (Eqs. 5, 6), C_D (Eq. 7) from Re and Ma.
+// kd = 3 / (8 r_p[AU] rho_p); rp_cm = r_p in cm.
+// kb_in: -1 takes the k of Eq. 7 from Re; 0 or 1 forces k = 0.4 or 0.2 (a
+// recorded branch being replayed).  *kb_out receives the branch used.
+__device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, double z, double u,
+                                         double v, double w, double rp_cm, double kd, double* a,
+                                         int kb_in, int* kb_out) {
+  a[0] = a[1] = a[2] = 0.0;
+  *kb_out = 0;
+  const double R2 = fma(x, x, y * y);
+  const double iR = rsqrt_d(R2);             // 1/R
+  const double R = R2 * iR;
+  if (R < S.r_in) return;                    // no gas inside the inner edge (Sec. 3.1.1)
+  double sigma, rmh, rcs, reta, inv_cs;      // Sigma, R^-(1+f), R^(f-1/2), R^(2f), 1/c_s
+  const double ih = rsqrt_d(R);              // R^-1/2
+  if (S.flare_quarter) {
+    const double q = rsqrt_d(ih);            // R^1/4
+    rcs = q * ih;                            // R^-1/4
+    rmh = iR * rcs;                          // R^-5/4
+    reta = R * ih;                           // R^1/2
+    inv_cs = q * S.inv_c_cs;
+  } else {
+    const double lr = log(R);
+    rcs = exp((S.flare - 0.5) * lr);
+    rmh = exp(-(1.0 + S.flare) * lr);
+    reta = exp(2.0 * S.flare * lr);
+    inv_cs = rcp_d(S.c_cs * rcs);
+  }
+  if (S.gamma_one) sigma = S.sigma1 * iR;
+  else sigma = S.sigma1 * exp(-S.gamma * log(R));
+  if (!S.rc_inf) sigma *= exp(-pow(R * S.inv_rc, 2.0 - S.gamma));
+  const double rho = S.c_rho * sigma * rmh;
+  const double vk = S.sqrt_mu0 * ih;
+  const double t = fma(-2.0 * S.c_eta, reta, 1.0);   // 1 - 2 eta
+  const double vg = vk * (t * rsqrt_d(t));
+  const double g = vg * iR;                  // gas velocity = g * (-y, x, 0)
+  const double du = fma(g, y, u);
+  const double dv = fma(-g, x, v);
+  const double dw = w;
+  const double dv2 = fma(du, du, fma(dv, dv, dw * dw));
+  if (dv2 == 0.0) return;
+  const double dvm = dv2 * rsqrt_d(dv2);
+  const double Ma = dvm * inv_cs;
+  const double Re = S.c_re * rp_cm * Ma * rho;
+  const int kb = (kb_in >= 0) ? kb_in : (Re < 1e5 ? 0 : 1);
+  *kb_out = kb;
+  const double k = kb ? 0.2 : 0.4;
+  // Eq. 7 with one reciprocal: [(24/Re + 40/(10+Re))^-1 + 0.23 Ma]^-1 = D/den1
+  // where D = 240 + 64 Re and den1 = Re (10 + Re) + 0.23 Ma D.
+  const double D = fma(64.0, Re, 240.0);
+  const double den1 = fma(0.23 * Ma, D, Re * (10.0 + Re));
+  const double A = 1.6 + Ma;
+  const double r = rcp_d(den1 * A);
+  const double first = D * A * r;           // = D / den1
+  const double second = fma(2.0, Ma, 1.6 * k) * den1 * r;
+  const double cd = (S.cd_mode == 1) ? fma(first, first, second) : first + second;
+  const double coef = S.cd_scale * cd * kd * rho * dvm;
+  a[0] = -coef * du;
+  a[1] = -coef * dv;
+  a[2] = -coef * dw;
+}
+
+// K(s)/s^3 times mu for one pair, accumulated into (ax, ay, az) as -f * d
+// (Sec. 2.1.3: K = 1 for s^2 >= rc^2, 0 for s^2 <= 0.01 rc^2, quintic between).
+__device__ __forceinline__ void pair_acc(double dx, double dy, double dz, double mu, double rc2,
+                                         double rc2lo, double rc01, double i09rc, double& ax,
+                                         double& ay, double& az) {
+  const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
+  const double yy = rsqrt_d(s2);
+  double f = yy * yy * yy;
+  if (s2 < rc2) {
+    if (s2 <= rc2lo) {
+      f = 0.0;
+    } else {
+      const double q = (s2 * yy - rc01) * i09rc;
+      f *= q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
+    }
+  }
+  f *= mu;
+  ax = fma(-f, dx, ax);
+  ay = fma(-f, dy, ay);
+  az = fma(-f, dz, az);
+}
+
+// Shared-memory staging of one chunk of big bodies.
+struct BigSmem {
+  double x[kBigChunk], y[kBigChunk], z[kBigChunk], mu[kBigChunk];
+  double rc[kBigChunk], rc2[kBigChunk], rc2lo[kBigChunk], rc01[kBigChunk], i09rc[kBigChunk];
+};
+
+}  // namespace mx

@@ -75,6 +75,13 @@ _SIGS = {
     "mx_energy_batch": (_I, [_P, _P, _P]),
     "mx_tiling": (_I, [_P, _P, _P]),
     "mx_set_tiling": (_I, [_P, _I, _I]),
+    "mx_set_gas_params": (_I, [_P, _I, _D, _D, _D]),
+    "mx_kick_branches": (_I, [_P, _I, ctypes.c_longlong]),
+    "mx_encounter_log": (_I, [_P, _P, _P, _I]),
+    "mx_set_step_index": (_I, [_P, ctypes.c_longlong]),
+    "mx_loss_semimajor": (_I, [_P, _P, _P, _P, _P, _P]),
+    "mx_adjoint_step": (_I, [_P, _P, ctypes.c_longlong, _P, _P]),
+    "mx_adjoint_init": (_I, [_P, _P, _P]),
 }
 
 
@@ -354,3 +361,42 @@ class System:
 
 
 INF = math.inf
+
+
+# ----------------------------------------------------------- differentiation
+def mx_set_gas_params(sys, k, sigma1, gamma, cd_scale):
+    _check(load().mx_set_gas_params(sys, int(k), float(sigma1), float(gamma), float(cd_scale)),
+           "mx_set_gas_params")
+
+
+def mx_kick_branches(sys, mode, max_kicks=0):
+    _check(load().mx_kick_branches(sys, int(mode), int(max_kicks)), "mx_kick_branches")
+
+
+def mx_encounter_log(sys, dev_ever=None, reset=False):
+    nbb = ctypes.c_longlong(0)
+    _check(load().mx_encounter_log(sys, _dptr(dev_ever), ctypes.byref(nbb), int(bool(reset))),
+           "mx_encounter_log")
+    return nbb.value
+
+
+def mx_set_step_index(sys, step):
+    _check(load().mx_set_step_index(sys, int(step)), "mx_set_step_index")
+
+
+def mx_loss_semimajor(sys, dev_xv_helio0, dev_w, dev_seed_final, dev_seed_init, n_sys=1):
+    L = np.zeros(n_sys)
+    _check(load().mx_loss_semimajor(sys, _dptr(dev_xv_helio0), _dptr(dev_w), _hptr(L),
+                                    _dptr(dev_seed_final), _dptr(dev_seed_init)),
+           "mx_loss_semimajor")
+    return L
+
+
+def mx_adjoint_step(sys, dev_state_k, step_k, dev_lambda, dev_dparams):
+    _check(load().mx_adjoint_step(sys, _dptr(dev_state_k), int(step_k), _dptr(dev_lambda),
+                                  _dptr(dev_dparams)), "mx_adjoint_step")
+
+
+def mx_adjoint_init(sys, dev_lambda, dev_grad_helio):
+    _check(load().mx_adjoint_init(sys, _dptr(dev_lambda), _dptr(dev_grad_helio)),
+           "mx_adjoint_init")

@@ -1,0 +1,106 @@
+"""Hand-written adjoint (mx_adjoint_step behind torch.autograd) against the
+oracle's forward-mode reference derivative and against central differences.
+
+Loss: weighted squared change of the planetesimals' semimajor axes after a
+checkpointed run (4 giant cores + planetesimals with gas drag, the shape of
+the adjoint workload).  Gradients w.r.t. the initial heliocentric state and
+(Sigma1, gamma, C_D factor) are checked along random directions:
+  * against the oracle's dual-number JVP: relative error <= 1e-8;
+  * against central differences of the GPU loss (recorded C_D branches
+    replayed): relative error <= 1e-5 at a step on the plateau.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2601_16791_gb300 import mx, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2601_16791_gb300.autograd import Trajectory, semimajor_loss  # noqa: E402
+
+
+def _setup(nsmall=300, nsteps=40, every=10, seed=4):
+    w = W.adjoint_4core_50k(seed=seed, nsmall=nsmall, nsteps=nsteps, checkpoint_every=every)
+    traj = Trajectory(w)
+    g = w.params["gas"]
+    xv0 = torch.tensor(w.xv_helio, dtype=torch.float64, device="cuda")
+    gas = torch.tensor([g["sigma1_gcm2"], g["gamma"], g["cd_scale"]], dtype=torch.float64,
+                       device="cuda")
+    wts = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    wts[w.nbig:] = 1.0 / w.nsmall
+    return w, traj, xv0, gas, wts
+
+
+def _directions(w, k, rng):
+    out = []
+    for _ in range(k):
+        dxv = np.zeros((6, w.n))
+        dxv[:3] = rng.normal(0, 1e-4, (3, w.n))
+        dxv[3:] = rng.normal(0, 1e-6, (3, w.n))
+        dpar = np.array([17.0, 0.01, 0.01]) * rng.normal(0, 1, 3)
+        out.append((dxv, dpar))
+    return out
+
+
+def _grad(traj, xv0, gas, wts, nsteps, every):
+    x = xv0.clone().requires_grad_(True)
+    p = gas.clone().requires_grad_(True)
+    L = semimajor_loss(traj, x, p, wts, nsteps, every)
+    L.backward()
+    return float(L.detach()), x.grad.detach().cpu().numpy(), p.grad.detach().cpu().numpy()
+
+
+def test_adjoint_vs_oracle_jvp():
+    w, traj, xv0, gas, wts = _setup()
+    L, gx, gp = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every)
+    ever_gpu = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(traj.h, ever_gpu)
+    # the oracle's own encounter mask
+    p = orc.make_params(w.params)
+    xvd, mu, rc = orc.init(p, w.nbig, w.nsmall, w.m_big, w.xv_helio)
+    _, ever_o, _, _ = orc.step(p, w.nbig, xvd, mu, rc, w.rp_km, w.rhop, w.nsteps)
+    assert np.array_equal(ever_o[w.nbig:], ever_gpu.cpu().numpy()[w.nbig:])
+    w_small = (1.0 / w.nsmall) * (1 - ever_o[w.nbig:].astype(float))
+    assert ever_o[w.nbig:].sum() > 0 and w_small.sum() > 0
+    rng = np.random.default_rng(12)
+    for dxv, dpar in _directions(w, 4, rng):
+        Lo, jvp = orc.jvp_loss(p, w.nbig, w.m_big, w.xv_helio, w.rp_km, w.rhop, w_small,
+                               w.nsteps, dxv, dpar)
+        ours = float((gx * dxv).sum() + (gp * dpar).sum())
+        assert abs(Lo - L) <= 1e-9 * abs(Lo)
+        assert abs(ours - jvp) <= 1e-8 * abs(jvp), (ours, jvp)
+    traj.close()
+
+
+def test_adjoint_vs_central_differences():
+    w, traj, xv0, gas, wts = _setup(nsmall=200, nsteps=30)
+    L, gx, gp = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every)
+    ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(traj.h, ever)
+    w_eff = wts * (1.0 - ever.to(torch.float64))
+    rng = np.random.default_rng(5)
+    for dxv, dpar in _directions(w, 3, rng):
+        ours = float((gx * dxv).sum() + (gp * dpar).sum())
+        best = np.inf
+        for t in (1e-1, 3e-2, 1e-2, 3e-3):
+            dx_t = torch.tensor(dxv, dtype=torch.float64, device="cuda")
+            dp_t = torch.tensor(dpar, dtype=torch.float64, device="cuda")
+            Lp = traj.loss_at(xv0 + t * dx_t, gas + t * dp_t, w_eff, w.nsteps, w.checkpoint_every)
+            Lm = traj.loss_at(xv0 - t * dx_t, gas - t * dp_t, w_eff, w.nsteps, w.checkpoint_every)
+            fd = (Lp - Lm) / (2 * t)
+            best = min(best, abs(fd - ours) / abs(ours))
+        assert best <= 1e-5, best
+    traj.close()
+
+
+def test_adjoint_is_deterministic():
+    w, traj, xv0, gas, wts = _setup(nsmall=150, nsteps=20)
+    a = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every)
+    b = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    traj.close()
