@@ -132,6 +132,34 @@ mx_status mx_energy_batch(mx_system* s, double* E, double* L3);
 mx_status mx_tiling(mx_system* s, int* tile, int* order);
 mx_status mx_set_tiling(mx_system* s, int tile, int order);
 
+/*
+ * Deferred planetesimals (an execution choice of this library; the paper has
+ * no counterpart).  A planetesimal is massless (Sec. 3.4), so its own close
+ * encounter changes no other body.  When its Bulirsch-Stoer group needs more
+ * than a few macro sub-steps, the body leaves the step and the other bodies go
+ * on.  One catch-up launch later replays its remaining steps from the big
+ * bodies' recorded states with the same device arithmetic.  That happens when
+ * `window` history slots have been recorded (a slot is a step, or the leading
+ * half kick of an mx_step / mx_step_profiled call, so a window may span calls),
+ * or earlier, before any call that reads or replaces the state, changes the
+ * gas parameters or the branch mode, or reads the encounter log or pair list.
+ * The state every such call sees is the one the direct path gives, bit for
+ * bit.  Big-body groups are never deferred.  Recording or replaying drag
+ * branches (mx_kick_branches) turns deferral off.  A catch-up's device errors
+ * are reported by the call that launched it.
+ *
+ * mx_set_defer_window: window = 0 keeps every body on the direct path;
+ * 1 <= window <= the history length (*max_window of mx_defer_stats, at most
+ * 64) sets the slots per catch-up.  Default: min(32, history length).
+ * MX_ERR_ARG for a window outside that range.
+ * mx_defer_stats: window in effect (0 when off), history length, bodies
+ * deferred since creation, catch-up launches made (host pointers, each may
+ * be NULL).
+ */
+mx_status mx_set_defer_window(mx_system* s, int window);
+mx_status mx_defer_stats(mx_system* s, int* window, int* max_window, long long* deferred,
+                         long long* catchups);
+
 /* Frees the system's device memory and graphs.  NULL is ignored. */
 void mx_destroy(mx_system* s);
 
@@ -139,12 +167,13 @@ void mx_destroy(mx_system* s);
  * mx_step -- advance n_steps hybrid steps (Sec. 2; step order: half kick,
  * half jump, drift, detection, Bulirsch-Stoer of encounter groups, half jump,
  * half kick).  Runs as CUDA graphs on the system's stream and synchronises
- * once at the end to read the status word.  n_steps >= 0.
+ * once at the end to read the status word.  n_steps >= 0; n_steps = 0 only
+ * brings deferred planetesimals up to date (see mx_set_defer_window).
  */
 mx_status mx_step(mx_system* s, int n_steps);
 
 /* Kernels of one step, in launch order, for mx_step_profiled. */
-#define MX_NKERN 7
+#define MX_NKERN 8
 #define MX_K_PREP 0       /* momentum + staged big positions */
 #define MX_K_JUMP_KICK 1  /* jump + half kick(s): gravity and drag */
 #define MX_K_JUMP_DRIFT 2 /* jump + Kepler drift */
@@ -152,6 +181,7 @@ mx_status mx_step(mx_system* s, int n_steps);
 #define MX_K_SORT 4       /* pair-key sort */
 #define MX_K_GROUPS 5     /* encounter groups */
 #define MX_K_BS 6         /* Bulirsch-Stoer of the groups */
+#define MX_K_CATCHUP 7    /* deferred planetesimals brought to the end of the window */
 
 /*
  * mx_step_profiled -- the same n_steps as mx_step, launched kernel by kernel
@@ -160,7 +190,8 @@ mx_status mx_step(mx_system* s, int n_steps);
  *  launches  [MX_NKERN]  launches per kernel (host, may be NULL)
  *  total_ms              device time from before the first launch to after
  *                        the last (host, may be NULL)
- * Synchronises once at the end.
+ * Synchronises once at the end.  n_steps = 0 only runs (and times) the
+ * pending catch-up of deferred planetesimals, if any.
  */
 mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* launches,
                            double* total_ms);

@@ -21,7 +21,10 @@
 // serial chain, not its arithmetic, sets the time: the rows and step
 // candidates of a macro sub-step go on separate lanes to shorten it.
 #include "mx_common.cuh"
+#include "mx_encounter.cuh"
+#include "mx_kepler.cuh"
 #include "mx_kernels.h"
+#include "mx_physics.cuh"
 
 namespace mx {
 
@@ -194,6 +197,13 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
       d.work_wfrom[c] = 0;
       for (int b = comp_start[c]; b < comp_start[c + 1]; ++b) d.work_mem[m++] = nodes[comp_nodes[b]];
     }
+    // big groups of this step, for the catch-up of deferred planetesimals
+    const int slot = d.defer ? *d.hstep : 0;
+    if (d.defer && slot < d.hist_cap)
+      for (int e = 0; e < nn; ++e) {
+        const SysDev& Sg = d.sys[sys_of(d, nodes[e])];
+        d.h_comp[(size_t)slot * d.NB + Sg.boff + (nodes[e] - Sg.off)] = comp_of[e];
+      }
     s_nnodes = nn;
     s_ncomp = nc;
     if (d.bb_count && nbb > 0) atomicAdd(d.bb_count, (unsigned long long)nbb);
@@ -634,7 +644,38 @@ __device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int la
     write_members<NB>(d, w, o0, lane - base, g);
     return;
   }
-  // still running: hand over to k_bs_spread
+  // still running.  A test-particle group (only the planetesimal's state is
+  // kept) leaves the step: the body is deferred to the window's catch-up.
+  if (d.defer && d.work_wfrom[w] == NB - 1) {
+    const int hs = *d.hstep;
+    int r = d.dcap;
+    if (lane == base && hs < d.hist_cap) r = atomicAdd(&d.hstep[1], 1);
+    r = __shfl_sync(gmask, r, base);
+    if (r < d.dcap) {
+      if (lane == base) {
+        const int j = d.work_mem[o0 + NB - 1];
+        int* R = d.d_rec + (size_t)r * kDeferInts;
+        R[0] = j;
+        R[1] = hs;
+        R[2] = NB;
+#pragma unroll
+        for (int m = 0; m < NB; ++m) R[3 + m] = d.work_mem[o0 + m];
+        double* c = d.d_state + (size_t)r * kContDoubles;
+        c[0] = g.rem;
+        c[1] = g.H;
+        c[2] = (double)g.nsub;
+#pragma unroll
+        for (int m = 0; m < NB; ++m)
+#pragma unroll
+          for (int q = 0; q < 6; ++q) c[3 + 6 * m + q] = g.Y[q][m];
+        d.work_nsub[w] = g.nsub;
+        d.lag[j] = 1;
+        atomicAdd(d.defer_total, 1ull);
+      }
+      return;
+    }
+  }
+  // hand over to k_bs_spread
   int slot = 0;
   if (lane == base) slot = atomicAdd(d.cont_count, 1);
   slot = __shfl_sync(gmask, slot, base);
@@ -662,9 +703,12 @@ __device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int la
 }
 
 // Four groups of LO..HI bodies per warp, 8 lanes each (separate kernels keep
-// the common two-body case free of the larger cases' register pressure).
+// the common two-body case free of the larger cases' register pressure).  One
+// warp per block: consecutive blocks land on different SMs, so the groups
+// spread over all SMs' FP64 pipes instead of filling a few SMs' worth of
+// four-warp blocks.
 template <int LO, int HI>
-__global__ void __launch_bounds__(128) k_bs_pack(Dev d) {
+__global__ void __launch_bounds__(32) k_bs_pack(Dev d) {
   const int W = *d.work_count;
   const int lane = threadIdx.x & 31;
   const int slot = lane >> 3;
@@ -755,16 +799,302 @@ __global__ void __launch_bounds__(32) k_bs(Dev d) {
   }
 }
 
+// ----------------------------------------------- deferred planetesimals
+// k_catchup takes every planetesimal deferred in the window (one warp each)
+// from the middle of its deferral step to the end of the window.  A window's
+// history slots are whole steps and the leading half kicks of calls.  Each step
+// is the direct path's own arithmetic on the big bodies' recorded history:
+// jump (P of jump 1), Kepler drift, the encounter test against every big body
+// (same screen and FP64 test as k_detect), Bulirsch-Stoer of its
+// test-particle group from the pre-drift states (same lane integrator as the
+// packed and spread phases, which accept the same sub-steps), jump (P of jump
+// 2), gravity of the staged big positions in ascending order and the half
+// kick(s) with drag.  So a deferred body ends where the direct path would
+// have put it, bit for bit.  Lanes split only the encounter test; every other
+// part is the same on all 32 lanes (an FP64 instruction costs the same for
+// one lane or 32).
+
+template <int NB>
+__device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, const int* gid,
+                                               double* mu, MemberK* K) {
+#pragma unroll
+  for (int m = 0; m < NB; ++m) {
+    const int l = gid[m] - S.off;
+    const double rc = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
+    mu[m] = (l < S.nbig) ? d.bmu[S.boff + l] : 0.0;
+    K[m].rc = rc;
+    K[m].rc2 = rc * rc;
+    K[m].rc2lo = 0.01 * (rc * rc);
+    K[m].rc01 = 0.1 * rc;
+    K[m].i09 = (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
+  }
+}
+
+// Runs the group (members gid, state Y, progress rem/H/nsub) to the end of
+// the step on the whole warp; the last member's state goes to s6.
+template <int NB>
+__device__ int catch_bs(const Dev& d, const SysDev& S, const int* gid,
+                        const double (&Y)[6][kLaneMaxNB], double rem, double H, int nsub,
+                        int lane, double* s6) {
+  double mu[NB];
+  MemberK K[NB];
+  load_members_g<NB>(d, S, gid, mu, K);
+  GroupRun<NB> g;
+#pragma unroll
+  for (int m = 0; m < NB; ++m)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) g.Y[q][m] = Y[q][m];
+  g.rem = rem;
+  g.H = H;
+  g.nsub = nsub;
+  const int r = bs_rounds<NB, 4>(0xffffffffu, 0, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub,
+                                 1 << 30, g);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) s6[q] = g.Y[q][NB - 1];
+  return r;
+}
+
+__device__ int catch_bs_any(const Dev& d, const SysDev& S, const int* gid, int nb,
+                            const double (&Y)[6][kLaneMaxNB], double rem, double H, int nsub,
+                            int lane, double* s6) {
+  switch (nb) {
+    case 2: return catch_bs<2>(d, S, gid, Y, rem, H, nsub, lane, s6);
+    case 3: return catch_bs<3>(d, S, gid, Y, rem, H, nsub, lane, s6);
+    default: return catch_bs<4>(d, S, gid, Y, rem, H, nsub, lane, s6);
+  }
+}
+
+// Jump 1, drift, encounter test and (if flagged) Bulirsch-Stoer of step t.
+__device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t, bool last,
+                            int lane, double* s6) {
+  const size_t NBs = (size_t)d.NB;
+  double dj[3];
+  jump_vec(d.h_P + (size_t)t * 6 * d.nsys + 3 * sys, S, 0.5, dj);
+  double x = s6[0] + dj[0], y = s6[1] + dj[1], z = s6[2] + dj[2];
+  double u = s6[3], v = s6[4], w = s6[5];
+  const double a0[6] = {x, y, z, u, v, w};
+  if (!kepler_drift(S.mu0, S.h, d.kepler_max_iter, x, y, z, u, v, w) && lane == 0)
+    atomicOr(d.status, ST_KEPLER);
+  const double a1[6] = {x, y, z, u, v, w};
+  float af[12];
+  for (int k = 0; k < 6; ++k) {
+    af[k] = (float)a0[k];
+    af[6 + k] = (float)a1[k];
+  }
+  const double* B0 = d.h_b0 + (size_t)t * 6 * NBs + S.boff;
+  const double* B1 = d.h_b1 + (size_t)t * 6 * NBs + S.boff;
+  const float hf = (float)S.h;
+  // flagged big bodies, ascending
+  int fl[kMaxGroup];
+  int nf = 0;
+  bool over = false;
+  for (int c0 = 0; c0 < S.nbig; c0 += 32) {
+    const int l = c0 + lane;
+    bool hit = false;
+    if (l < S.nbig) {
+      const double rcb = d.brc[S.boff + l];
+      const float rcf = fmaxf((float)rcb, (float)0.0);
+      float bf[12];
+      double b0[6], b1[6];
+      for (int q = 0; q < 6; ++q) {
+        b0[q] = B0[(size_t)q * NBs + l];
+        b1[q] = B1[(size_t)q * NBs + l];
+        bf[q] = (float)b0[q];
+        bf[6 + q] = (float)b1[q];
+      }
+      if (encounter_screen(af, bf, rcf * rcf, hf)) {
+        const double rc = fmax(rcb, 0.0);
+        hit = encounter_fp64(a0, b0, a1, b1, S.h, rc * rc);
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      const int gi = S.off + l;
+      if (d.ever) {
+        d.ever[gi] = 1;
+        d.ever[j] = 1;
+      }
+      if (last) {
+        d.flags[gi] = 1;
+        const int pos = atomicAdd(d.pair_count, 1);
+        if (pos < d.pair_cap)
+          d.keys[pos] = (1ull << 63) | ((unsigned long long)(unsigned)j << 32) | (unsigned)gi;
+      }
+    }
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      if (nf < kMaxGroup) fl[nf++] = c0 + b;
+      else over = true;
+    }
+  }
+  if (last && lane == 0) d.flags[j] = nf > 0 ? 1 : 0;
+  if (nf == 0) {
+    for (int q = 0; q < 6; ++q) s6[q] = a1[q];
+    return;
+  }
+  // members: the big groups of the flagged bodies (ascending), then j
+  const int* comp = d.h_comp + (size_t)t * NBs + S.boff;
+  int mem[kMaxGroup];
+  int cnt = 0;
+  bool bad = over;
+  for (int e = 0; e < nf && !bad; ++e) {
+    const int ce = comp[fl[e]];
+    const int b0 = (ce >= 0) ? 0 : fl[e];
+    const int b1 = (ce >= 0) ? S.nbig : fl[e] + 1;
+    for (int b = b0; b < b1 && !bad; ++b) {
+      if (ce >= 0 && comp[b] != ce) continue;
+      bool seen = false;
+      for (int q = 0; q < cnt; ++q) seen |= (mem[q] == b);
+      if (seen) continue;
+      if (cnt >= kMaxGroup - 1) {
+        bad = true;
+        break;
+      }
+      int q = cnt;
+      while (q > 0 && mem[q - 1] > b) {
+        mem[q] = mem[q - 1];
+        --q;
+      }
+      mem[q] = b;
+      ++cnt;
+    }
+  }
+  if (bad) {   // the direct path skips the step's Bulirsch-Stoer and reports it
+    if (lane == 0) atomicOr(d.status, ST_GROUP);
+    for (int q = 0; q < 6; ++q) s6[q] = a1[q];
+    return;
+  }
+  const int nb = cnt + 1;
+  if (nb <= kLaneMaxNB) {
+    int gid[kLaneMaxNB];
+    double Y[6][kLaneMaxNB];
+    for (int m = 0; m < kLaneMaxNB; ++m) {
+      const bool big = m < cnt;
+      gid[m] = big ? S.off + mem[m] : j;
+      for (int q = 0; q < 6; ++q) Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
+    }
+    const int r = catch_bs_any(d, S, gid, nb, Y, S.h, S.h, 0, lane, s6);
+    if (r < 0 && lane == 0) atomicOr(d.status, ST_BS);
+    return;
+  }
+  // more than four bodies: the thread integrator of k_bs, on lane 0
+  double out[6];
+  if (lane == 0) {
+    GroupState G;
+    G.nb = nb;
+    double Y[6][kMaxGroup];
+    for (int m = 0; m < nb; ++m) {
+      const bool big = m < cnt;
+      G.mu[m] = big ? d.bmu[S.boff + mem[m]] : 0.0;
+      G.rc[m] = big ? d.brc[S.boff + mem[m]] : 0.0;
+      for (int q = 0; q < 6; ++q) Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
+    }
+    int nsub = 0;
+    if (!bs_integrate(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub)) atomicOr(d.status, ST_BS);
+    for (int q = 0; q < 6; ++q) out[q] = Y[q][nb - 1];
+  }
+  for (int q = 0; q < 6; ++q) s6[q] = __shfl_sync(0xffffffffu, out[q], 0);
+}
+
+// Jump 2 and the half kick(s) that end step t, or (head) the leading half
+// kick of a call, which has no jump and keeps the positions as they are.
+__device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t, int lane,
+                           double* s6) {
+  const double* P2 = d.h_P + (size_t)t * 6 * d.nsys + 3 * d.nsys + 3 * sys;
+  const int hk = d.h_nkick[t];
+  const bool head = hk < 0;
+  double dj[3];
+  jump_vec(P2, S, head ? 0.0 : 0.5, dj);
+  const double x = s6[0] + dj[0], y = s6[1] + dj[1], z = s6[2] + dj[2];
+  double u = s6[3], v = s6[4], w = s6[5];
+  const double* BX = d.h_bx + (size_t)t * 3 * d.NB + S.boff;
+  double ax = 0, ay = 0, az = 0;
+  for (int l = 0; l < S.nbig; ++l) {
+    const double rc = d.brc[S.boff + l];
+    pair_acc(x - BX[l], y - BX[d.NB + l], z - BX[2 * (size_t)d.NB + l], d.bmu[S.boff + l],
+             rc * rc, 0.01 * (rc * rc), 0.1 * rc, (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0, ax, ay, az);
+  }
+  const int nk = head ? -hk : hk;
+  const double kick_h = 0.5 * S.h;
+  const double hp0 = P2[0] * S.inv_mu0, hp1 = P2[1] * S.inv_mu0, hp2 = P2[2] * S.inv_mu0;
+  const double rp = S.gas_on ? d.rp_cm[j] : 0.0, kd = S.gas_on ? d.kdrag[j] : 0.0;
+  for (int kk = 0; kk < nk; ++kk) {
+    double a[3] = {0.0, 0.0, 0.0};
+    if (S.gas_on) {
+      int kout = 0;
+      gas_drag(S, x, y, z, u + hp0, v + hp1, w + hp2, rp, kd, a, -1, &kout);
+    }
+    u = fma(kick_h, ax + a[0], u);
+    v = fma(kick_h, ay + a[1], v);
+    w = fma(kick_h, az + a[2], w);
+  }
+  if (!(finite_d(x) && finite_d(y) && finite_d(z) && finite_d(u) && finite_d(v) && finite_d(w)) &&
+      lane == 0)
+    atomicOr(d.status, ST_NONFINITE);
+  if (!head) {
+    s6[0] = x;
+    s6[1] = y;
+    s6[2] = z;
+  }
+  s6[3] = u;
+  s6[4] = v;
+  s6[5] = w;
+}
+
+__global__ void __launch_bounds__(32) k_catchup(Dev d) {
+  const int T = d.hstep[0];
+  const int C = min(d.hstep[1], d.dcap);
+  const int lane = threadIdx.x;
+  if (T > d.hist_cap) {   // a window longer than the history: nothing is replayed
+    if (C > 0 && blockIdx.x == 0 && lane == 0) atomicOr(d.status, ST_WINDOW);
+    return;
+  }
+  const size_t N = d.N;
+  int tl = T - 1;   // the window's last step (not a leading half kick)
+  while (tl >= 0 && d.h_nkick[tl] < 0) --tl;
+  for (int r = blockIdx.x; r < C; r += gridDim.x) {
+    const int* R = d.d_rec + (size_t)r * kDeferInts;
+    const int j = R[0], t0 = R[1], nb = R[2];
+    const int sys = sys_of(d, j);
+    const SysDev& S = d.sys[sys];
+    int gid[kLaneMaxNB];
+    double Y[6][kLaneMaxNB];
+    const double* c = d.d_state + (size_t)r * kContDoubles;
+    for (int m = 0; m < kLaneMaxNB; ++m) {
+      gid[m] = (m < nb) ? R[3 + m] : j;
+      for (int q = 0; q < 6; ++q) Y[q][m] = (m < nb) ? c[3 + 6 * m + q] : 0.0;
+    }
+    double s6[6];
+    const int res = catch_bs_any(d, S, gid, nb, Y, c[0], c[1], (int)c[2], lane, s6);
+    if (res < 0 && lane == 0) atomicOr(d.status, ST_BS);
+    for (int t = t0; t < T; ++t) {
+      if (t > t0 && d.h_nkick[t] > 0) catch_front(d, S, sys, j, t, t == tl, lane, s6);
+      catch_back(d, S, sys, j, t, lane, s6);
+    }
+    if (lane == 0) {
+      for (int q = 0; q < 6; ++q) d.xv[q * N + j] = s6[q];
+      if (t0 == tl) d.flags[j] = 1;
+      d.lag[j] = 0;
+    }
+  }
+}
+
 void launch_groups(const Dev& d, cudaStream_t st) { k_groups<<<1, 1024, 0, st>>>(d); }
 
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
   // (a group has at least two members: one big body and the body it meets)
   cudaMemsetAsync(d.cont_count, 0, sizeof(int), st);
-  k_bs_pack<2, 2><<<nblocks, 128, 0, st>>>(d);
-  k_bs_pack<3, 4><<<nblocks, 128, 0, st>>>(d);
+  k_bs_pack<2, 2><<<4 * nblocks, 32, 0, st>>>(d);
+  k_bs_pack<3, 4><<<4 * nblocks, 32, 0, st>>>(d);
   k_bs<<<nblocks, 32, 0, st>>>(d);
   k_bs_spread<2, 2><<<nblocks / 4, 32, 0, st>>>(d);
   k_bs_spread<3, 4><<<nblocks / 4, 32, 0, st>>>(d);
+}
+
+void launch_catchup(const Dev& d, int nblocks, cudaStream_t st) {
+  k_catchup<<<nblocks, 32, 0, st>>>(d);
+  cudaMemsetAsync(d.hstep, 0, 2 * sizeof(int), st);
 }
 
 }  // namespace mx

@@ -25,9 +25,14 @@ __global__ void __launch_bounds__(kThreads) k_jump_drift(Dev d, double jump_frac
     *d.pair_count = 0;
     *d.work_count = 0;
   }
+  const int slot = d.defer ? *d.hstep : 0;
+  const bool rec = d.defer && slot < d.hist_cap;
+  if (rec && t.start == S.off && threadIdx.x == 0)
+    for (int c = 0; c < 3; ++c) d.h_P[(size_t)slot * 6 * d.nsys + 3 * t.sys + c] = d.P[3 * t.sys + c];
   if (threadIdx.x >= t.count) return;
   const int N = d.N;
   const int j = t.start + threadIdx.x;
+  if (d.defer && d.lag[j]) return;   // waits for the window's catch-up
   double dj[3];
   jump_vec(d.P + 3 * t.sys, S, jump_frac, dj);
   double x = d.xv[j] + dj[0];
@@ -51,6 +56,18 @@ __global__ void __launch_bounds__(kThreads) k_jump_drift(Dev d, double jump_frac
   d.xv[4 * (size_t)N + j] = v;
   d.xv[5 * (size_t)N + j] = w;
   d.flags[j] = 0;
+  const int jl = j - S.off;
+  if (rec && jl < S.nbig) {   // the big body's endpoints, for deferred planetesimals
+    const size_t b = S.boff + jl, o0 = (size_t)slot * 6 * d.NB;
+    const double e0[6] = {d.xv0[j], d.xv0[(size_t)N + j], d.xv0[2 * (size_t)N + j], d.xv0[3 * (size_t)N + j],
+                          d.xv0[4 * (size_t)N + j], d.xv0[5 * (size_t)N + j]};
+    const double e1[6] = {x, y, z, u, v, w};
+    for (int c = 0; c < 6; ++c) {
+      d.h_b0[o0 + (size_t)c * d.NB + b] = e0[c];
+      d.h_b1[o0 + (size_t)c * d.NB + b] = e1[c];
+    }
+    d.h_comp[(size_t)slot * d.NB + b] = -1;
+  }
 }
 
 // Drift n bodies of a caller buffer (6 x n) by h about mu.

@@ -90,11 +90,28 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int 
   double Ps[3] = {red[0][0], red[1][0], red[2][0]};
   double dj[3];
   jump_vec(Ps, S, jump_frac, dj);
+  // the kicks of a history slot (the end of a step, or the leading half kick
+  // of a call, recorded as -1) enter the history deferred planetesimals replay
+  const int slot = d.defer ? *d.hstep : 0;
+  const bool rec = d.defer && nkick > 0 && slot < d.hist_cap;
+  if (rec && threadIdx.x == 0) {
+    for (int c = 0; c < 3; ++c) d.h_P[(size_t)slot * 6 * d.nsys + 3 * d.nsys + 3 * blockIdx.x + c] = Ps[c];
+    if (blockIdx.x == 0) d.h_nkick[slot] = (jump_frac != 0.0) ? nkick : -nkick;
+  }
   for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
     const int g = S.off + i;
-    d.bx[S.boff + i] = d.xv[g] + dj[0];
-    d.by[S.boff + i] = d.xv[(size_t)N + g] + dj[1];
-    d.bz[S.boff + i] = d.xv[2 * (size_t)N + g] + dj[2];
+    const double bx = d.xv[g] + dj[0];
+    const double by = d.xv[(size_t)N + g] + dj[1];
+    const double bz = d.xv[2 * (size_t)N + g] + dj[2];
+    d.bx[S.boff + i] = bx;
+    d.by[S.boff + i] = by;
+    d.bz[S.boff + i] = bz;
+    if (rec) {
+      const size_t o = (size_t)slot * 3 * d.NB + S.boff + i;
+      d.h_bx[o] = bx;
+      d.h_bx[o + d.NB] = by;
+      d.h_bx[o + 2 * (size_t)d.NB] = bz;
+    }
   }
 }
 
@@ -113,8 +130,11 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
   double dj[3];
   jump_vec(P, S, jump_frac, dj);
   const double kick_h = kick_frac * S.h;
-  const bool act = threadIdx.x < t.count;
   const int j = t.start + threadIdx.x;
+  // a deferred planetesimal is kicked by the window's catch-up instead
+  const bool act = threadIdx.x < t.count && !(d.defer && d.lag[j]);
+  // the last kernel of a history slot moves on to the next one
+  if (d.defer && blockIdx.x == 0 && threadIdx.x == 0) *d.hstep += 1;
   const int jl = j - S.off;
   double x = 0, y = 0, z = 0, u = 0, v = 0, w = 0, rcj = 0.0;
   if (act) {

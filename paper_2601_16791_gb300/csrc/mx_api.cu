@@ -51,6 +51,7 @@ mx_status status_to_code(unsigned st) {
   if (st & mx::ST_BARRIER) return fail(MX_ERR_BARRIER_TIMEOUT, "device wait gave up");
   if (st & mx::ST_ADJ_ENC)
     return fail(MX_ERR_ENCOUNTER_IN_ADJOINT, "big-big encounter inside the adjoint");
+  if (st & mx::ST_WINDOW) return fail(MX_ERR_CUDA, "deferral window longer than its history");
   return MX_OK;
 }
 
@@ -116,9 +117,13 @@ struct mx_system {
   unsigned* h_status = nullptr;   // pinned
   int* h_count = nullptr;         // pinned
   std::vector<void*> allocs;
-  cudaGraphExec_t g_head = nullptr, g_mid = nullptr, g_last = nullptr;
+  cudaGraphExec_t g_head = nullptr, g_mid = nullptr, g_last = nullptr, g_catch = nullptr;
   long long step = 0;
   int bs_blocks = 0;
+  int catch_blocks = 0;
+  int window = 0;                 // history slots per catch-up of deferred planetesimals (0: off)
+  int pending = 0;                // slots recorded since the last catch-up
+  long long catchups = 0;
   int tile = mx::kThreads;        // targets per tile (autotuned)
   int order = 0;                  // 0: tiles in system order; 1: costliest first
   int tiles_cap = 0;
@@ -189,10 +194,41 @@ void enqueue_step(mx_system* s, int last, cudaStream_t st) {
   mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st);
 }
 
+// The end of a window: deferred planetesimals catch up with the rest.
+void enqueue_catchup(mx_system* s, cudaStream_t st) { mx::launch_catchup(s->d, s->catch_blocks, st); }
+
+// Deferral is on for forward runs with a window; recording or replaying the
+// drag branches (kmode != 0) keeps every body on the direct path.
+void update_defer(mx_system* s) { s->d.defer = (s->window > 0 && s->d.kmode == 0) ? 1 : 0; }
+
+// A history slot (a step, or the leading half kick of a call) has been
+// enqueued; a full window is caught up at once.  `catch_up` enqueues it.
+template <class F>
+cudaError_t slot_done(mx_system* s, F&& catch_up) {
+  if (!s->d.defer) return cudaSuccess;
+  if (++s->pending < s->window) return cudaSuccess;
+  s->pending = 0;
+  ++s->catchups;
+  return catch_up();
+}
+
+// Brings deferred planetesimals up to date before the state is read,
+// replaced, or the parameters they were recorded under change.
+mx_status settle(mx_system* s) {
+  if (s->pending == 0) return MX_OK;
+  s->pending = 0;
+  ++s->catchups;
+  if (s->g_catch) MX_CUDA(cudaGraphLaunch(s->g_catch, s->st));
+  else enqueue_catchup(s, s->st);
+  MX_CUDA(cudaGetLastError());
+  return MX_OK;
+}
+
 mx_status capture(mx_system* s, int which, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   MX_CUDA(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
   if (which == 0) enqueue_head(s, s->cap_st);
+  else if (which == 3) enqueue_catchup(s, s->cap_st);
   else enqueue_step(s, which == 2, s->cap_st);
   cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
   if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
@@ -207,10 +243,14 @@ mx_status ensure_graphs(mx_system* s) {
   MX_TRY(capture(s, 0, &s->g_head));
   MX_TRY(capture(s, 1, &s->g_mid));
   MX_TRY(capture(s, 2, &s->g_last));
+  MX_TRY(capture(s, 3, &s->g_catch));
   return MX_OK;
 }
 
 constexpr int kMinTile = 64;
+constexpr int kMaxWindow = 64;       // steps of big-body history kept for deferred planetesimals
+constexpr int kDefaultWindow = 32;
+constexpr size_t kHistBudget = 256ull << 20;   // bytes the history may take
 
 // Tiles of `tile` targets per system; order 1 puts the costliest first (work
 // per target grows with the system's big bodies and with gas drag), so the
@@ -240,7 +280,8 @@ void drop_graphs(mx_system* s) {
   if (s->g_head) cudaGraphExecDestroy(s->g_head);
   if (s->g_mid) cudaGraphExecDestroy(s->g_mid);
   if (s->g_last) cudaGraphExecDestroy(s->g_last);
-  s->g_head = s->g_mid = s->g_last = nullptr;
+  if (s->g_catch) cudaGraphExecDestroy(s->g_catch);
+  s->g_head = s->g_mid = s->g_last = s->g_catch = nullptr;
 }
 
 mx_status set_tiling(mx_system* s, int tile, int order) {
@@ -341,9 +382,11 @@ mx_status trial_ms(mx_system* s, double* ms) {
   MX_CUDA(cudaEventCreate(&e1));
   enqueue_head(s, s->st);          // warm-up step
   enqueue_step(s, 1, s->st);
+  if (s->d.defer) enqueue_catchup(s, s->st);
   MX_CUDA(cudaEventRecord(e0, s->st));
   enqueue_head(s, s->st);
   enqueue_step(s, 1, s->st);
+  if (s->d.defer) enqueue_catchup(s, s->st);
   MX_CUDA(cudaEventRecord(e1, s->st));
   MX_CUDA(cudaEventSynchronize(e1));
   float t = 0.f;
@@ -353,6 +396,11 @@ mx_status trial_ms(mx_system* s, double* ms) {
   MX_CUDA(cudaMemcpyAsync(s->d.xv, s->d_tmp, bytes, cudaMemcpyDeviceToDevice, s->st));
   MX_CUDA(cudaMemsetAsync(s->d.status, 0, sizeof(unsigned), s->st));
   MX_CUDA(cudaMemsetAsync(s->d.pair_count, 0, 2 * sizeof(int), s->st));
+  // trials run at creation: the encounter log and the counters start empty
+  MX_CUDA(cudaMemsetAsync(s->d.ever, 0, s->N, s->st));
+  MX_CUDA(cudaMemsetAsync(s->d.bb_count, 0, sizeof(unsigned long long), s->st));
+  MX_CUDA(cudaMemsetAsync(s->d.defer_total, 0, sizeof(unsigned long long), s->st));
+  MX_CUDA(cudaMemsetAsync(s->d.kick_ctr, 0, 2 * sizeof(int), s->st));
   MX_CUDA(cudaStreamSynchronize(s->st));
   *ms = t;
   return MX_OK;
@@ -443,6 +491,27 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   d.kcap = 0;
   MX_TRY(dalloc(s, &d.cont_item, d.cont_cap));
   MX_TRY(dalloc(s, &d.cont_state, (size_t)d.cont_cap * 27));
+  // deferred planetesimals: per-step history of the big bodies, records
+  {
+    const size_t per_step = (size_t)15 * NB * sizeof(double) + (size_t)NB * sizeof(int) +
+                            (size_t)6 * nsys * sizeof(double) + sizeof(int);
+    int hc = kMaxWindow;
+    while (hc > 1 && (size_t)hc * per_step > kHistBudget) hc >>= 1;
+    d.hist_cap = hc;
+    d.dcap = 1 << 14;
+    MX_TRY(dalloc(s, &d.lag, N));
+    MX_TRY(dalloc(s, &d.hstep, 2));
+    MX_TRY(dalloc(s, &d.defer_total, 1));
+    MX_TRY(dalloc(s, &d.h_P, (size_t)hc * 6 * nsys));
+    MX_TRY(dalloc(s, &d.h_b0, (size_t)hc * 6 * NB));
+    MX_TRY(dalloc(s, &d.h_b1, (size_t)hc * 6 * NB));
+    MX_TRY(dalloc(s, &d.h_bx, (size_t)hc * 3 * NB));
+    MX_TRY(dalloc(s, &d.h_comp, (size_t)hc * NB));
+    MX_TRY(dalloc(s, &d.h_nkick, hc));
+    MX_TRY(dalloc(s, &d.d_rec, (size_t)d.dcap * mx::kDeferInts));
+    MX_TRY(dalloc(s, &d.d_state, (size_t)d.dcap * 27));
+    s->window = std::min(kDefaultWindow, hc);
+  }
   MX_TRY(dalloc(s, &d.status, 1));
   MX_TRY(dalloc(s, &s->d_sys, nsys));
   MX_TRY(dalloc(s, &s->d_tiles, tiles_cap));
@@ -471,6 +540,10 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemsetAsync(d.ever, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.bb_count, 0, sizeof(unsigned long long), st));
   MX_CUDA(cudaMemsetAsync(d.kick_ctr, 0, 2 * sizeof(int), st));
+  MX_CUDA(cudaMemsetAsync(d.lag, 0, N, st));
+  MX_CUDA(cudaMemsetAsync(d.hstep, 0, 2 * sizeof(int), st));
+  MX_CUDA(cudaMemsetAsync(d.defer_total, 0, sizeof(unsigned long long), st));
+  update_defer(s);
   // host staging: state rows, masses as mu = G m, per-body drag inputs
   std::vector<double> xv((size_t)6 * N), bmu(NB, 0.0), rpb(N, 1.0), rhob(N, 1.0);
   for (int k = 0; k < nsys; ++k) {
@@ -500,6 +573,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   int nsm = 0;
   MX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device));
   s->bs_blocks = 4 * nsm;
+  s->catch_blocks = 8 * nsm;
   return sync_status(s);
 }
 
@@ -644,9 +718,36 @@ mx_status mx_set_tiling(mx_system* s, int tile, int order) {
   return set_tiling(s, tile, order);
 }
 
+mx_status mx_set_defer_window(mx_system* s, int window) {
+  if (!s || window < 0) return fail(MX_ERR_ARG, "invalid arguments");
+  if (window > s->d.hist_cap)
+    return fail(MX_ERR_ARG, "window longer than the history (" + std::to_string(s->d.hist_cap) + " steps)");
+  MX_TRY(set_device(s));
+  MX_TRY(settle(s));
+  s->window = window;
+  update_defer(s);
+  drop_graphs(s);
+  return MX_OK;
+}
+
+mx_status mx_defer_stats(mx_system* s, int* window, int* max_window, long long* deferred,
+                         long long* catchups) {
+  if (!s) return fail(MX_ERR_ARG, "NULL system");
+  MX_TRY(set_device(s));
+  unsigned long long n = 0;
+  MX_CUDA(cudaMemcpyAsync(&n, s->d.defer_total, sizeof(n), cudaMemcpyDeviceToHost, s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  if (window) *window = s->d.defer ? s->window : 0;
+  if (max_window) *max_window = s->d.hist_cap;
+  if (deferred) *deferred = (long long)n;
+  if (catchups) *catchups = s->catchups;
+  return MX_OK;
+}
+
 mx_status mx_energy_batch(mx_system* s, double* E, double* L3) {
   if (!s || !E || !L3) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   const int nsys = (int)s->h_sys.size();
   mx::launch_energy(s->d, s->d_energy, s->st);
   std::vector<double> o(7 * (size_t)nsys);
@@ -670,12 +771,19 @@ mx_status mx_sizes(mx_system* s, int* n_big, int* n_small) {
 
 mx_status mx_step(mx_system* s, int n_steps) {
   if (!s || n_steps < 0) return fail(MX_ERR_ARG, "invalid arguments");
-  if (n_steps == 0) return MX_OK;
   MX_TRY(set_device(s));
+  if (n_steps == 0) {
+    MX_TRY(settle(s));
+    return sync_status(s);
+  }
   MX_TRY(ensure_graphs(s));
+  auto catch_up = [&] { return cudaGraphLaunch(s->g_catch, s->st); };
   MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
-  for (int k = 0; k + 1 < n_steps; ++k) MX_CUDA(cudaGraphLaunch(s->g_mid, s->st));
-  MX_CUDA(cudaGraphLaunch(s->g_last, s->st));
+  MX_CUDA(slot_done(s, catch_up));
+  for (int k = 0; k < n_steps; ++k) {
+    MX_CUDA(cudaGraphLaunch(k + 1 == n_steps ? s->g_last : s->g_mid, s->st));
+    MX_CUDA(slot_done(s, catch_up));
+  }
   s->step += n_steps;
   return sync_status(s);
 }
@@ -683,7 +791,6 @@ mx_status mx_step(mx_system* s, int n_steps) {
 mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* launches,
                            double* total_ms) {
   if (!s || n_steps < 0) return fail(MX_ERR_ARG, "invalid arguments");
-  if (n_steps == 0) return MX_OK;
   MX_TRY(set_device(s));
   cudaStream_t st = s->st;
   // (kind, event-before, event-after) per launch
@@ -704,8 +811,18 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     return rec();
   };
   cudaError_t e = cudaSuccess;
-  e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
-  if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
+  auto catch_up = [&] { return timed(MX_K_CATCHUP, [&] { enqueue_catchup(s, st); }); };
+  if (n_steps == 0) {   // only the pending catch-up, timed
+    if (s->pending > 0) {
+      s->pending = 0;
+      ++s->catchups;
+      e = catch_up();
+    }
+  } else {
+    e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
+    if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
+    if (e == cudaSuccess) e = slot_done(s, catch_up);
+  }
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
     const bool last = (k + 1 == n_steps);
     e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5, st); });
@@ -719,6 +836,7 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, last ? 1 : 2, st); });
     if (e == cudaSuccess)
       e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st); });
+    if (e == cudaSuccess) e = slot_done(s, catch_up);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   double sum[MX_NKERN] = {0};
@@ -730,7 +848,8 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     cnt[kind[q]]++;
   }
   if (e == cudaSuccess && total_ms) {
-    e = cudaEventElapsedTime(&ms, ev.front(), ev.back());
+    ms = 0.f;
+    if (!ev.empty()) e = cudaEventElapsedTime(&ms, ev.front(), ev.back());
     *total_ms = ms;
   }
   for (auto x : ev) cudaEventDestroy(x);
@@ -746,6 +865,7 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
 mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pairs) {
   if (!s || !n_pairs || cap < 0 || (cap > 0 && !host_pairs)) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   MX_CUDA(cudaMemcpyAsync(s->h_count, s->d.pair_count, sizeof(int), cudaMemcpyDeviceToHost, s->st));
   MX_CUDA(cudaStreamSynchronize(s->st));
   const int n = std::min(*s->h_count, s->d.pair_cap);
@@ -767,6 +887,7 @@ mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pair
 mx_status mx_accel(mx_system* s, double* dev_acc) {
   if (!s || !dev_acc) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   mx::launch_prep(s->d, 0.0, 0, s->st);
   mx::launch_accel(s->d, dev_acc, 0, s->N, 0, s->st);
   return sync_status(s);
@@ -775,6 +896,7 @@ mx_status mx_accel(mx_system* s, double* dev_acc) {
 mx_status mx_gas_drag(mx_system* s, double* dev_acc) {
   if (!s || !dev_acc) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   const int ns = s->nsmall[0];
   if (ns == 0) return MX_OK;
   MX_CUDA(cudaMemsetAsync(dev_acc, 0, (size_t)3 * ns * sizeof(double), s->st));
@@ -789,12 +911,14 @@ mx_status mx_detect_encounters(mx_system* s, const double* dev_xv0, const double
       s->params.size() != 1)
     return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   unsigned char* flags = dev_flags ? dev_flags : s->d.flags;
   MX_CUDA(cudaMemsetAsync(flags, 0, s->N, s->st));
   MX_CUDA(cudaMemsetAsync(s->d.pair_count, 0, sizeof(int), s->st));
   mx::Dev dd = s->d;
   dd.ever = nullptr;        // caller-supplied states do not enter the encounter log
   dd.bb_count = nullptr;
+  dd.defer = 0;
   mx::launch_detect(dd, dev_xv0, dev_xv1, flags, s->d.keys, s->d.pair_count, s->d.pair_cap, s->st);
   mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 1, s->st);
   if (dev_pairs && cap > 0)
@@ -821,6 +945,7 @@ mx_status mx_kepler_drift(mx_system* s, double* dev_xv, double h) {
 mx_status mx_energy(mx_system* s, double* E, double* L3) {
   if (!s || !E || !L3) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   mx::launch_energy(s->d, s->d_energy, s->st);
   double o[7];
   MX_CUDA(cudaMemcpyAsync(o, s->d_energy, sizeof(o), cudaMemcpyDeviceToHost, s->st));
@@ -836,6 +961,7 @@ mx_status mx_get_state(mx_system* s, double* xv_host, int coords, long long* ste
   if (!s || !xv_host || (coords != MX_COORD_HELIO && coords != MX_COORD_DH))
     return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   const double* src = s->d.xv;
   if (coords == MX_COORD_HELIO) {
     mx::launch_prep(s->d, 0.0, 0, s->st);
@@ -852,6 +978,7 @@ mx_status mx_set_state(mx_system* s, const double* xv_host, int coords, long lon
   if (!s || !xv_host || (coords != MX_COORD_HELIO && coords != MX_COORD_DH))
     return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   MX_CUDA(cudaMemcpyAsync(s->d.xv, xv_host, (size_t)6 * s->N * sizeof(double), cudaMemcpyHostToDevice, s->st));
   if (coords == MX_COORD_HELIO) {
     mx::launch_init_sys(s->d, 0, 0.0, s->st);
@@ -867,6 +994,7 @@ mx_status mx_set_state(mx_system* s, const double* xv_host, int coords, long lon
 mx_status mx_get_state_device(mx_system* s, double* dev_xv) {
   if (!s || !dev_xv) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   MX_CUDA(cudaMemcpyAsync(dev_xv, s->d.xv, (size_t)6 * s->N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
   return MX_OK;
 }
@@ -874,6 +1002,7 @@ mx_status mx_get_state_device(mx_system* s, double* dev_xv) {
 mx_status mx_set_state_device(mx_system* s, const double* dev_xv) {
   if (!s || !dev_xv) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   MX_CUDA(cudaMemcpyAsync(s->d.xv, dev_xv, (size_t)6 * s->N * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
   return MX_OK;
 }
@@ -957,6 +1086,7 @@ mx_status mx_set_gas_params(mx_system* s, int k, double sigma1, double gamma, do
       !std::isfinite(cd_scale))
     return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   mx_params& p = s->params[k];
   p.gas.sigma1_gcm2 = sigma1;
   p.gas.gamma = gamma;
@@ -973,8 +1103,10 @@ mx_status mx_kick_branches(mx_system* s, int mode, long long max_kicks) {
   if (!s || mode < 0 || mode > 2 || max_kicks < 0 || max_kicks > (1LL << 30))
     return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   if (mode == 0) {
     s->d.kmode = 0;
+    update_defer(s);
     drop_graphs(s);
     return MX_OK;
   }
@@ -995,6 +1127,7 @@ mx_status mx_kick_branches(mx_system* s, int mode, long long max_kicks) {
     return fail(MX_ERR_ARG, "no recorded branches to replay");
   }
   s->d.kmode = mode;
+  update_defer(s);
   drop_graphs(s);
   MX_CUDA(cudaStreamSynchronize(s->st));
   return MX_OK;
@@ -1003,6 +1136,7 @@ mx_status mx_kick_branches(mx_system* s, int mode, long long max_kicks) {
 mx_status mx_encounter_log(mx_system* s, unsigned char* dev_ever, long long* n_big_big, int reset) {
   if (!s) return fail(MX_ERR_ARG, "NULL system");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   if (dev_ever) MX_CUDA(cudaMemcpyAsync(dev_ever, s->d.ever, s->N, cudaMemcpyDeviceToDevice, s->st));
   unsigned long long bb = 0;
   MX_CUDA(cudaMemcpyAsync(&bb, s->d.bb_count, sizeof(bb), cudaMemcpyDeviceToHost, s->st));
@@ -1030,6 +1164,7 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
   if (!s || !dev_xv_helio0 || !dev_w || !L || !dev_seed_final || !dev_seed_init)
     return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   MX_TRY(ensure_adjoint(s));
   mx::launch_prep(s->d, 0.0, 0, s->st);
   mx::launch_loss(s->d, dev_xv_helio0, dev_w, dev_seed_final, dev_seed_init, s->a_part, s->a_poff,
@@ -1041,6 +1176,7 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
 mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_grad_helio) {
   if (!s || !dev_lambda || !dev_grad_helio) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   mx::launch_init_vjp(s->d, dev_lambda, dev_grad_helio, s->st);
   return sync_status(s);
 }
@@ -1050,6 +1186,7 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   if (!s || !dev_state_k || !dev_lambda || !dev_dparams || step_k < 0 || step_k > (1LL << 29))
     return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
+  MX_TRY(settle(s));
   MX_TRY(ensure_adjoint(s));
   const size_t N = s->N;
   mx::Adj a;

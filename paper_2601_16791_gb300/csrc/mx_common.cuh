@@ -34,7 +34,8 @@ enum : unsigned {
   ST_BARRIER = 1u << 4,
   ST_GROUP = 1u << 5,
   ST_WORK_OVF = 1u << 6,
-  ST_ADJ_ENC = 1u << 7
+  ST_ADJ_ENC = 1u << 7,
+  ST_WINDOW = 1u << 8
 };
 
 // Constants of one system.
@@ -99,7 +100,31 @@ struct Dev {
   int pair_cap, work_cap, mem_cap;
   int kepler_max_iter, bs_max_sub;
   double bs_tol;
+  // Deferred planetesimals.  A planetesimal is massless, so its own close
+  // encounter changes no other body: when its Bulirsch-Stoer group outlasts
+  // the packed phase, the rest of its steps wait for the end of the window,
+  // where k_catchup replays them from the big bodies' recorded history with
+  // the same device functions (so the result is the one the direct path
+  // gives, bit for bit).  defer = 0 leaves every step on the direct path.
+  int defer;
+  int hist_cap;        // steps of history (the longest window)
+  int dcap;            // deferred records
+  unsigned char* lag;  // [N] 1 while the body waits for the catch-up
+  int* hstep;          // [0] slot of the current step in the window, [1] deferred records
+  unsigned long long* defer_total;  // bodies deferred since creation
+  double* h_P;         // [hist_cap][2][3 nsys] P of jump 1, P of jump 2 and the kicks
+  double* h_b0;        // [hist_cap][6][NB] big bodies after jump 1 (pre-drift)
+  double* h_b1;        // [hist_cap][6][NB] big bodies after the drift (detection endpoint)
+  double* h_bx;        // [hist_cap][3][NB] big positions after jump 2 (kick sources)
+  int* h_comp;         // [hist_cap][NB] big group of each big body, -1 for none
+  int* h_nkick;        // [hist_cap] half kicks at the end of the step
+  int* d_rec;          // [dcap][kDeferInts] body, window slot, member count, members
+  double* d_state;     // [dcap][3 + 6 x 4] Bulirsch-Stoer state handed over
 };
+
+// Deferred record: body, window slot, member count, up to four members
+// (global indices, bigs ascending, the body last), one spare.
+constexpr int kDeferInts = 8;
 
 // Buffers of one adjoint step (k_adjoint.cu).
 struct Adj {

@@ -37,6 +37,7 @@ void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int 
 // k_bs.cu
 void launch_groups(const Dev& d, cudaStream_t st);
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st);
+void launch_catchup(const Dev& d, int nblocks, cudaStream_t st);
 
 
 // k_adjoint.cu

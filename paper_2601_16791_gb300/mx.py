@@ -75,6 +75,8 @@ _SIGS = {
     "mx_energy_batch": (_I, [_P, _P, _P]),
     "mx_tiling": (_I, [_P, _P, _P]),
     "mx_set_tiling": (_I, [_P, _I, _I]),
+    "mx_set_defer_window": (_I, [_P, _I]),
+    "mx_defer_stats": (_I, [_P, _P, _P, _P, _P]),
     "mx_set_gas_params": (_I, [_P, _I, _D, _D, _D]),
     "mx_kick_branches": (_I, [_P, _I, ctypes.c_longlong]),
     "mx_encounter_log": (_I, [_P, _P, _P, _I]),
@@ -163,7 +165,8 @@ def mx_step(sys, n_steps):
     _check(load().mx_step(sys, int(n_steps)), "mx_step")
 
 
-KERNELS = ("k_prep", "k_jump_kick", "k_jump_drift", "k_detect", "k_sort_keys", "k_groups", "k_bs")
+KERNELS = ("k_prep", "k_jump_kick", "k_jump_drift", "k_detect", "k_sort_keys", "k_groups", "k_bs",
+           "k_catchup")
 
 
 def mx_step_profiled(sys, n_steps):
@@ -292,6 +295,20 @@ def mx_tiling(sys):
 
 def mx_set_tiling(sys, tile, order):
     _check(load().mx_set_tiling(sys, int(tile), int(order)), "mx_set_tiling")
+
+
+def mx_set_defer_window(sys, window):
+    """Steps per catch-up of deferred planetesimals (0: every body on the direct path)."""
+    _check(load().mx_set_defer_window(sys, int(window)), "mx_set_defer_window")
+
+
+def mx_defer_stats(sys):
+    """(window in effect, history length, bodies deferred so far, catch-up launches)."""
+    w, mw = ctypes.c_int(0), ctypes.c_int(0)
+    n, c = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _check(load().mx_defer_stats(sys, ctypes.byref(w), ctypes.byref(mw), ctypes.byref(n),
+                                 ctypes.byref(c)), "mx_defer_stats")
+    return w.value, mw.value, n.value, c.value
 
 
 class Batch:
