@@ -616,26 +616,252 @@ __device__ __forceinline__ void write_members(const Dev& d, int w, int o0, int l
   }
 }
 
+
+// ----------------------------------------- two-body groups, one term per lane
+// A group of two bodies (a big body and a planetesimal, or two big bodies)
+// runs one step candidate per warp.  Lane 4r + q holds extrapolation row r
+// and one force term q: 0 the star on body 0, 1 the star on body 1, 2 body 1
+// on body 0, 3 body 0 on body 1.  Every lane evaluates its term with the same
+// instructions (the star is a source without changeover), the two terms of a
+// body are added with one shuffle, and each lane advances only its own body
+// (q & 1).  One warp scheduler issues an FP64 instruction about every 70
+// cycles on this part, so a macro sub-step costs the FP64 instructions of one
+// lane: about 30 per Stoermer sub-step here, against about 70 when one lane
+// carries both bodies and all their terms.  The four candidates of the spread
+// phase and of the catch-up are four warps, one per scheduler.  The Neville
+// values of a row are split over its lanes: positions of body q & 1 on q < 2,
+// velocities on q >= 2.  Rows are checked as they complete, after rows 2, 3, 5
+// and 7: the round ends at the first check where candidate 0 (the largest
+// step) has a converged row.  The search still accepts what trying H, then
+// H/2 after a failure, with the rows in order, would accept.
+constexpr unsigned kBs2Checks = (1u << 2) | (1u << 3) | (1u << 5) | (1u << 7);
+
+constexpr double bs_inv_den_c(int r, int j) {
+  return (j < 1 || j > r) ? 0.0
+                          : 1.0 / (((double)(r + 1) / (double)(r - j + 1)) *
+                                       ((double)(r + 1) / (double)(r - j + 1)) - 1.0);
+}
+#define MX_DEN_ROW(r)                                                                       \
+  { bs_inv_den_c(r, 0), bs_inv_den_c(r, 1), bs_inv_den_c(r, 2), bs_inv_den_c(r, 3),          \
+    bs_inv_den_c(r, 4), bs_inv_den_c(r, 5), bs_inv_den_c(r, 6), bs_inv_den_c(r, 7) }
+// 1 / ((n_r / n_{r-j})^2 - 1) and 1 / n_r for n_r = 2(r+1)
+__constant__ double c_bs_inv_den[kBsRows][kBsRows] = {
+    MX_DEN_ROW(0), MX_DEN_ROW(1), MX_DEN_ROW(2), MX_DEN_ROW(3),
+    MX_DEN_ROW(4), MX_DEN_ROW(5), MX_DEN_ROW(6), MX_DEN_ROW(7)};
+#undef MX_DEN_ROW
+__constant__ double c_bs_inv_n[kBsRows] = {1.0 / 2, 1.0 / 4, 1.0 / 6, 1.0 / 8,
+                                           1.0 / 10, 1.0 / 12, 1.0 / 14, 1.0 / 16};
+
+// The force term of one lane: source mu and the changeover of the pair
+// (rc = max of the two rcrit; the star's term has rc = infinity).
+struct Bs2Term {
+  double musrc, rc2, rc2lo, rc01, i09;
+  bool pair;
+};
+
+__device__ __forceinline__ Bs2Term bs2_term(int q, double mu0, const double* mu, const MemberK* K) {
+  Bs2Term t;
+  t.pair = q >= 2;
+  const int ob = q & 1;
+  if (!t.pair) {
+    t.musrc = mu0;
+    t.rc2 = t.rc2lo = INFINITY;
+    t.rc01 = t.i09 = 0.0;
+  } else {
+    const MemberK& k = (K[0].rc > K[1].rc) ? K[0] : K[1];
+    t.musrc = mu[1 - ob];
+    t.rc2 = k.rc2;
+    t.rc2lo = k.rc2lo;
+    t.rc01 = k.rc01;
+    t.i09 = k.i09;
+  }
+  return t;
+}
+
+// Acceleration of this lane's body (its two terms summed) at positions X.
+__device__ __forceinline__ void bs2_accel(const Bs2Term& t, const double (&X)[3], double (&A)[3]) {
+  double dv[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double xo = __shfl_xor_sync(0xffffffffu, X[c], 1);
+    dv[c] = X[c] - (t.pair ? xo : 0.0);
+  }
+  const double s2 = fma(dv[0], dv[0], fma(dv[1], dv[1], dv[2] * dv[2]));
+  const double yy = rsqrt_d(s2);
+  double wgt = (yy * yy) * (yy * t.musrc);
+  if (s2 >= t.rc2) {
+    wgt = 0.0;
+  } else if (s2 > t.rc2lo) {
+    const double q = fma(s2, yy, -t.rc01) * t.i09;
+    wgt *= fma(-q * q * q, fma(q, fma(6.0, q, -15.0), 10.0), 1.0);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double a = -wgt * dv[c];
+    A[c] = a + __shfl_xor_sync(0xffffffffu, a, 2);
+  }
+}
+
+// Neville table of rows 0..K from the raw row values; returns the lowest row
+// r in 1..K whose error max(|dx|^2 xscal, |dv|^2 vscal) over both bodies is
+// within tol2, or -1.  T keeps the extrapolated values of each lane's row.
+__device__ __forceinline__ int bs2_check(int K, int row, double sc, double tol2,
+                                         const double (&Traw)[3], double (&T)[3]) {
+  double Tp[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) T[c] = Tp[c] = Traw[c];
+#pragma unroll
+  for (int j = 1; j < kBsRows; ++j) {
+    if (j > K) break;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double up = __shfl_up_sync(0xffffffffu, T[c], 4);
+      if (row >= j && row <= K) {
+        if (row == j) Tp[c] = T[c];
+        T[c] = fma(T[c] - up, c_bs_inv_den[row][j], T[c]);
+      }
+    }
+  }
+  double e = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double dx = T[c] - Tp[c];
+    e = fma(dx, dx, e);
+  }
+  e *= sc;
+  e = fmax(e, __shfl_xor_sync(0xffffffffu, e, 1));
+  e = fmax(e, __shfl_xor_sync(0xffffffffu, e, 2));
+  const bool conv = row >= 1 && row <= K && e <= tol2;
+  const unsigned v = __ballot_sync(0xffffffffu, conv);
+  return v ? ((__ffs(v) - 1) >> 2) : -1;
+}
+
+// Up to max_rounds macro sub-steps of a two-body group; this warp runs step
+// candidate `cand` of NCAND (NCAND warps of the block, s_row[NCAND] and
+// s_y[12] in shared memory when NCAND > 1).  Returns 1 when the step is done,
+// 0 when rounds ran out, -1 at the sub-step cap.  g is the same on every lane
+// and warp before and after.
+template <int NCAND>
+__device__ int bs2_rounds(int cand, int lane, const Bs2Term& t, double tol, int max_sub,
+                          int max_rounds, GroupRun<2>& g, int* s_row, double* s_y) {
+  const int row = lane >> 2, q = lane & 3, ob = q & 1;
+  const bool vel = q >= 2;
+  const int n = 2 * (row + 1);
+  const double tol2 = tol * tol;
+  const double cscale = 1.0 / (double)(1 << cand);
+  for (int round = 0; round < max_rounds; ++round) {
+    if (g.rem == 0.0) return 1;
+    if (g.nsub >= max_sub) return -1;
+    if (fabs(g.H) > fabs(g.rem)) g.H = g.rem;
+    const double Hc = g.H * cscale;
+    double X[3], V[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      X[c] = ob ? g.Y[c][1] : g.Y[c][0];
+      V[c] = ob ? g.Y[3 + c][1] : g.Y[3 + c][0];
+    }
+    const double s0 = vel ? V[0] : X[0], s1 = vel ? V[1] : X[1], s2v = vel ? V[2] : X[2];
+    const double sc = rcp_d(fma(s0, s0, fma(s1, s1, s2v * s2v)));
+    const double dd = Hc * c_bs_inv_n[row];
+    const double d2 = dd * dd;
+    double A[3], D[3], Traw[3] = {0.0, 0.0, 0.0}, T[3];
+    bs2_accel(t, X, A);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      D[c] = dd * fma(0.5 * dd, A[c], V[c]);
+      X[c] += D[c];
+    }
+    int acc_c = -1, acc_r = -1;
+    bool decided = false;
+    for (int s = 1; s <= 2 * kBsRows && !decided; ++s) {
+      bs2_accel(t, X, A);
+      if (s < n) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          D[c] = fma(d2, A[c], D[c]);
+          X[c] += D[c];
+        }
+      } else if (s == n) {
+        const double idd = n * rcp_d(Hc);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Traw[c] = vel ? fma(D[c], idd, 0.5 * dd * A[c]) : X[c];
+      }
+      const int K = (s >> 1) - 1;   // the row that completed at this sub-step
+      if ((s & 1) || !((kBs2Checks >> K) & 1u)) continue;
+      const int r = bs2_check(K, row, sc, tol2, Traw, T);
+      if (NCAND == 1) {
+        if (r >= 0) {
+          acc_c = 0;
+          acc_r = r;
+          decided = true;
+        } else if (K == kBsRows - 1) {
+          decided = true;
+        }
+      } else {
+        if (lane == 0) s_row[cand] = r;
+        __syncthreads();
+        if (s_row[0] >= 0) {
+          acc_c = 0;
+          acc_r = s_row[0];
+          decided = true;
+        } else if (K == kBsRows - 1) {
+          for (int c = 1; c < NCAND && acc_c < 0; ++c)
+            if (s_row[c] >= 0) {
+              acc_c = c;
+              acc_r = s_row[c];
+            }
+          decided = true;
+        }
+        __syncthreads();
+      }
+    }
+    if (acc_c >= 0) {
+      // the accepted row's lanes hold x0, x1 (q = 0, 1) and v0, v1 (q = 2, 3)
+      if (NCAND == 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          g.Y[c][0] = __shfl_sync(0xffffffffu, T[c], 4 * acc_r + 0);
+          g.Y[c][1] = __shfl_sync(0xffffffffu, T[c], 4 * acc_r + 1);
+          g.Y[3 + c][0] = __shfl_sync(0xffffffffu, T[c], 4 * acc_r + 2);
+          g.Y[3 + c][1] = __shfl_sync(0xffffffffu, T[c], 4 * acc_r + 3);
+        }
+      } else {
+        if (cand == acc_c && row == acc_r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) s_y[3 * q + c] = T[c];
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          g.Y[c][0] = s_y[c];
+          g.Y[c][1] = s_y[3 + c];
+          g.Y[3 + c][0] = s_y[6 + c];
+          g.Y[3 + c][1] = s_y[9 + c];
+        }
+        __syncthreads();
+      }
+      g.nsub += acc_c + 1;                   // attempts a one-at-a-time search makes
+      if (g.nsub > max_sub) return -1;
+      const double Hacc = g.H * (1.0 / (double)(1 << acc_c));
+      g.rem -= Hacc;
+      g.H = 1.3 * Hacc;
+    } else {
+      g.nsub += NCAND;
+      g.H *= 1.0 / (double)(1 << NCAND);
+    }
+  }
+  return (g.rem == 0.0) ? 1 : 0;
+}
+
 // Continuation record: rem, H, nsub, then Y.
 constexpr int kContDoubles = 3 + 6 * kLaneMaxNB;
 
-template <int NB>
-__device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int lane) {
-  const int o0 = d.work_off[w];
-  const SysDev& S = d.sys[d.work_sys[w]];
-  double mu[NB];
-  MemberK K[NB];
-  load_members<NB>(d, S, o0, mu, K);
-  GroupRun<NB> g;
-#pragma unroll
-  for (int m = 0; m < NB; ++m)
-#pragma unroll
-    for (int c = 0; c < 6; ++c) g.Y[c][m] = d.xv0[(size_t)c * d.N + d.work_mem[o0 + m]];
-  g.rem = S.h;
-  g.H = S.h;
-  g.nsub = 0;
-  const int r = bs_rounds<NB, 1>(gmask, base, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub,
-                                 kPackRounds, g);
+// After the packed rounds (result r of the round function): finished groups
+// are written; a test-particle group still running is deferred to the
+// window's catch-up when deferral is on; anything else goes to the spread
+// phase, or, with its list full, is finished here by `finish_here`.
+template <int NB, class Finish>
+__device__ void pack_tail(const Dev& d, int w, unsigned gmask, int base, int lane, int o0, int r,
+                          GroupRun<NB>& g, Finish&& finish_here) {
   if (r != 0) {
     if (lane == base) {
       if (r < 0) atomicOr(d.status, ST_BS);
@@ -648,19 +874,19 @@ __device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int la
   // kept) leaves the step: the body is deferred to the window's catch-up.
   if (d.defer && d.work_wfrom[w] == NB - 1) {
     const int hs = *d.hstep;
-    int r = d.dcap;
-    if (lane == base && hs < d.hist_cap) r = atomicAdd(&d.hstep[1], 1);
-    r = __shfl_sync(gmask, r, base);
-    if (r < d.dcap) {
+    int rr = d.dcap;
+    if (lane == base && hs < d.hist_cap) rr = atomicAdd(&d.hstep[1], 1);
+    rr = __shfl_sync(gmask, rr, base);
+    if (rr < d.dcap) {
       if (lane == base) {
         const int j = d.work_mem[o0 + NB - 1];
-        int* R = d.d_rec + (size_t)r * kDeferInts;
+        int* R = d.d_rec + (size_t)rr * kDeferInts;
         R[0] = j;
         R[1] = hs;
         R[2] = NB;
 #pragma unroll
         for (int m = 0; m < NB; ++m) R[3 + m] = d.work_mem[o0 + m];
-        double* c = d.d_state + (size_t)r * kContDoubles;
+        double* c = d.d_state + (size_t)rr * kContDoubles;
         c[0] = g.rem;
         c[1] = g.H;
         c[2] = (double)g.nsub;
@@ -675,13 +901,12 @@ __device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int la
       return;
     }
   }
-  // hand over to k_bs_spread
+  // hand over to the spread phase
   int slot = 0;
   if (lane == base) slot = atomicAdd(d.cont_count, 1);
   slot = __shfl_sync(gmask, slot, base);
   if (slot >= d.cont_cap) {   // list full: finish here
-    const int r2 = bs_rounds<NB, 1>(gmask, base, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub,
-                                    1 << 30, g);
+    const int r2 = finish_here(g);
     if (lane == base) {
       if (r2 < 0) atomicOr(d.status, ST_BS);
       d.work_nsub[w] = g.nsub;
@@ -699,6 +924,93 @@ __device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int la
     for (int m = 0; m < NB; ++m)
 #pragma unroll
       for (int q = 0; q < 6; ++q) c[3 + 6 * m + q] = g.Y[q][m];
+  }
+}
+
+template <int NB>
+__device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int lane) {
+  const int o0 = d.work_off[w];
+  const SysDev& S = d.sys[d.work_sys[w]];
+  double mu[NB];
+  MemberK K[NB];
+  load_members<NB>(d, S, o0, mu, K);
+  GroupRun<NB> g;
+#pragma unroll
+  for (int m = 0; m < NB; ++m)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g.Y[c][m] = d.xv0[(size_t)c * d.N + d.work_mem[o0 + m]];
+  g.rem = S.h;
+  g.H = S.h;
+  g.nsub = 0;
+  // with deferral on, a group that needs a second round leaves the step at once
+  const int r = bs_rounds<NB, 1>(gmask, base, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub,
+                                 d.defer ? 1 : kPackRounds, g);
+  pack_tail<NB>(d, w, gmask, base, lane, o0, r, g, [&](GroupRun<NB>& gg) {
+    return bs_rounds<NB, 1>(gmask, base, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub, 1 << 30, gg);
+  });
+}
+
+// Two-body groups, one per warp (term lanes, one candidate).
+__global__ void __launch_bounds__(32) k_bs_pack2(Dev d) {
+  const int W = *d.work_count;
+  const int lane = threadIdx.x;
+  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+    const int o0 = d.work_off[w];
+    if (d.work_off[w + 1] - o0 != 2) continue;
+    const SysDev& S = d.sys[d.work_sys[w]];
+    double mu[2];
+    MemberK K[2];
+    load_members<2>(d, S, o0, mu, K);
+    const Bs2Term t = bs2_term(lane & 3, S.mu0, mu, K);
+    GroupRun<2> g;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) g.Y[c][m] = d.xv0[(size_t)c * d.N + d.work_mem[o0 + m]];
+    g.rem = S.h;
+    g.H = S.h;
+    g.nsub = 0;
+    const int r = bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, d.defer ? 1 : kPackRounds, g,
+                                nullptr, nullptr);
+    pack_tail<2>(d, w, 0xffffffffu, 0, lane, o0, r, g, [&](GroupRun<2>& gg) {
+      return bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, 1 << 30, gg, nullptr, nullptr);
+    });
+  }
+}
+
+// Two-body groups handed over by k_bs_pack2: one per block of four warps,
+// one step candidate per warp.
+__global__ void __launch_bounds__(128) k_bs_spread2(Dev d) {
+  __shared__ int s_row[4];
+  __shared__ double s_y[12];
+  const int C = min(*d.cont_count, d.cont_cap);
+  const int lane = threadIdx.x & 31, cand = threadIdx.x >> 5;
+  for (int slot = blockIdx.x; slot < C; slot += gridDim.x) {
+    const int w = d.cont_item[slot];
+    const int o0 = d.work_off[w];
+    if (d.work_off[w + 1] - o0 != 2) continue;
+    const SysDev& S = d.sys[d.work_sys[w]];
+    double mu[2];
+    MemberK K[2];
+    load_members<2>(d, S, o0, mu, K);
+    const Bs2Term t = bs2_term(lane & 3, S.mu0, mu, K);
+    GroupRun<2> g;
+    const double* c = d.cont_state + (size_t)slot * kContDoubles;
+    g.rem = c[0];
+    g.H = c[1];
+    g.nsub = (int)c[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) g.Y[q][m] = c[3 + 6 * m + q];
+    const int r = bs2_rounds<4>(cand, lane, t, d.bs_tol, d.bs_max_sub, 1 << 30, g, s_row, s_y);
+    if (cand == 0) {
+      if (lane == 0) {
+        if (r < 0) atomicOr(d.status, ST_BS);
+        d.work_nsub[w] = g.nsub;
+      }
+      write_members<2>(d, w, o0, lane, g);
+    }
   }
 }
 
@@ -830,10 +1142,23 @@ __device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, co
   }
 }
 
+// The catch-up block: four warps that take the same path through a body's
+// steps (each warp on its own scheduler, so the repeated work costs no time);
+// they differ only in the step candidate of a two-body Bulirsch-Stoer group,
+// and only warp 0 writes results.
+struct CatchBlk {
+  int lane, wq;
+  int* s_row;     // [4]
+  double* s_y;    // [12]
+  double* s_bc;   // [6] broadcast of a body state
+  int* s_r;       // [1] broadcast of a result code
+};
+
 // Runs the group (members gid, state Y, progress rem/H/nsub) to the end of
-// the step on the whole warp; the last member's state goes to s6.
+// the step on one warp (four candidates x eight rows on its lanes); the last
+// member's state goes to s6.
 template <int NB>
-__device__ int catch_bs(const Dev& d, const SysDev& S, const int* gid,
+__device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const int* gid,
                         const double (&Y)[6][kLaneMaxNB], double rem, double H, int nsub,
                         int lane, double* s6) {
   double mu[NB];
@@ -854,26 +1179,78 @@ __device__ int catch_bs(const Dev& d, const SysDev& S, const int* gid,
   return r;
 }
 
+// Two bodies: term lanes, one candidate per warp of the block (k_bs_spread2's
+// integrator).  Three or four: warp 0 runs the lane integrator of
+// k_bs_spread, and the result is broadcast.
 __device__ int catch_bs_any(const Dev& d, const SysDev& S, const int* gid, int nb,
                             const double (&Y)[6][kLaneMaxNB], double rem, double H, int nsub,
-                            int lane, double* s6) {
-  switch (nb) {
-    case 2: return catch_bs<2>(d, S, gid, Y, rem, H, nsub, lane, s6);
-    case 3: return catch_bs<3>(d, S, gid, Y, rem, H, nsub, lane, s6);
-    default: return catch_bs<4>(d, S, gid, Y, rem, H, nsub, lane, s6);
+                            const CatchBlk& B, double* s6) {
+  if (nb == 2) {
+    double mu[2];
+    MemberK K[2];
+    load_members_g<2>(d, S, gid, mu, K);
+    const Bs2Term t = bs2_term(B.lane & 3, S.mu0, mu, K);
+    GroupRun<2> g;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) g.Y[q][m] = Y[q][m];
+    g.rem = rem;
+    g.H = H;
+    g.nsub = nsub;
+    const int r = bs2_rounds<4>(B.wq, B.lane, t, d.bs_tol, d.bs_max_sub, 1 << 30, g, B.s_row, B.s_y);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s6[q] = g.Y[q][1];
+    return r;
   }
+  if (B.wq == 0) {
+    const int r = (nb == 3) ? catch_bs<3>(d, S, gid, Y, rem, H, nsub, B.lane, s6)
+                            : catch_bs<4>(d, S, gid, Y, rem, H, nsub, B.lane, s6);
+    if (B.lane == 0) {
+      for (int q = 0; q < 6; ++q) B.s_bc[q] = s6[q];
+      *B.s_r = r;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < 6; ++q) s6[q] = B.s_bc[q];
+  const int r = *B.s_r;
+  __syncthreads();
+  return r;
+}
+
+// The thread integrator of k_bs for a group of more than four bodies
+// (cnt big bodies mem[], then the planetesimal with pre-drift state a0).
+__device__ __noinline__ void catch_bs_thread(const Dev& d, const SysDev& S, const int* mem, int cnt,
+                                             const double* a0, int t, double* out) {
+  const size_t NBs = (size_t)d.NB;
+  const double* B0 = d.h_b0 + (size_t)t * 6 * NBs + S.boff;
+  const int nb = cnt + 1;
+  GroupState G;
+  G.nb = nb;
+  double Y[6][kMaxGroup];
+  for (int m = 0; m < nb; ++m) {
+    const bool big = m < cnt;
+    G.mu[m] = big ? d.bmu[S.boff + mem[m]] : 0.0;
+    G.rc[m] = big ? d.brc[S.boff + mem[m]] : 0.0;
+    for (int q = 0; q < 6; ++q) Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
+  }
+  int nsub = 0;
+  if (!bs_integrate(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub)) atomicOr(d.status, ST_BS);
+  for (int q = 0; q < 6; ++q) out[q] = Y[q][nb - 1];
 }
 
 // Jump 1, drift, encounter test and (if flagged) Bulirsch-Stoer of step t.
 __device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t, bool last,
-                            int lane, double* s6) {
+                            const CatchBlk& B, double* s6) {
+  const int lane = B.lane;
+  const bool w0 = B.wq == 0;
   const size_t NBs = (size_t)d.NB;
   double dj[3];
   jump_vec(d.h_P + (size_t)t * 6 * d.nsys + 3 * sys, S, 0.5, dj);
   double x = s6[0] + dj[0], y = s6[1] + dj[1], z = s6[2] + dj[2];
   double u = s6[3], v = s6[4], w = s6[5];
   const double a0[6] = {x, y, z, u, v, w};
-  if (!kepler_drift(S.mu0, S.h, d.kepler_max_iter, x, y, z, u, v, w) && lane == 0)
+  if (!kepler_drift(S.mu0, S.h, d.kepler_max_iter, x, y, z, u, v, w) && w0 && lane == 0)
     atomicOr(d.status, ST_KEPLER);
   const double a1[6] = {x, y, z, u, v, w};
   float af[12];
@@ -908,7 +1285,7 @@ __device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t
       }
     }
     unsigned m = __ballot_sync(0xffffffffu, hit);
-    if (hit) {
+    if (hit && w0) {
       const int gi = S.off + l;
       if (d.ever) {
         d.ever[gi] = 1;
@@ -928,7 +1305,7 @@ __device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t
       else over = true;
     }
   }
-  if (last && lane == 0) d.flags[j] = nf > 0 ? 1 : 0;
+  if (last && w0 && lane == 0) d.flags[j] = nf > 0 ? 1 : 0;
   if (nf == 0) {
     for (int q = 0; q < 6; ++q) s6[q] = a1[q];
     return;
@@ -961,7 +1338,7 @@ __device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t
     }
   }
   if (bad) {   // the direct path skips the step's Bulirsch-Stoer and reports it
-    if (lane == 0) atomicOr(d.status, ST_GROUP);
+    if (w0 && lane == 0) atomicOr(d.status, ST_GROUP);
     for (int q = 0; q < 6; ++q) s6[q] = a1[q];
     return;
   }
@@ -974,32 +1351,20 @@ __device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t
       gid[m] = big ? S.off + mem[m] : j;
       for (int q = 0; q < 6; ++q) Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
     }
-    const int r = catch_bs_any(d, S, gid, nb, Y, S.h, S.h, 0, lane, s6);
-    if (r < 0 && lane == 0) atomicOr(d.status, ST_BS);
+    const int r = catch_bs_any(d, S, gid, nb, Y, S.h, S.h, 0, B, s6);
+    if (r < 0 && w0 && lane == 0) atomicOr(d.status, ST_BS);
     return;
   }
-  // more than four bodies: the thread integrator of k_bs, on lane 0
-  double out[6];
-  if (lane == 0) {
-    GroupState G;
-    G.nb = nb;
-    double Y[6][kMaxGroup];
-    for (int m = 0; m < nb; ++m) {
-      const bool big = m < cnt;
-      G.mu[m] = big ? d.bmu[S.boff + mem[m]] : 0.0;
-      G.rc[m] = big ? d.brc[S.boff + mem[m]] : 0.0;
-      for (int q = 0; q < 6; ++q) Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
-    }
-    int nsub = 0;
-    if (!bs_integrate(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub)) atomicOr(d.status, ST_BS);
-    for (int q = 0; q < 6; ++q) out[q] = Y[q][nb - 1];
-  }
-  for (int q = 0; q < 6; ++q) s6[q] = __shfl_sync(0xffffffffu, out[q], 0);
+  // more than four bodies: the thread integrator of k_bs, on one thread
+  if (w0 && lane == 0) catch_bs_thread(d, S, mem, cnt, a0, t, B.s_bc);
+  __syncthreads();
+  for (int q = 0; q < 6; ++q) s6[q] = B.s_bc[q];
+  __syncthreads();
 }
 
 // Jump 2 and the half kick(s) that end step t, or (head) the leading half
 // kick of a call, which has no jump and keeps the positions as they are.
-__device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t, int lane,
+__device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t, bool lead,
                            double* s6) {
   const double* P2 = d.h_P + (size_t)t * 6 * d.nsys + 3 * d.nsys + 3 * sys;
   const int hk = d.h_nkick[t];
@@ -1030,7 +1395,7 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
     w = fma(kick_h, az + a[2], w);
   }
   if (!(finite_d(x) && finite_d(y) && finite_d(z) && finite_d(u) && finite_d(v) && finite_d(w)) &&
-      lane == 0)
+      lead)
     atomicOr(d.status, ST_NONFINITE);
   if (!head) {
     s6[0] = x;
@@ -1042,12 +1407,15 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
   s6[5] = w;
 }
 
-__global__ void __launch_bounds__(32) k_catchup(Dev d) {
+__global__ void __launch_bounds__(128) k_catchup(Dev d) {
+  __shared__ int s_row[4], s_r;
+  __shared__ double s_y[12], s_bc[6];
   const int T = d.hstep[0];
   const int C = min(d.hstep[1], d.dcap);
-  const int lane = threadIdx.x;
+  const CatchBlk B{(int)(threadIdx.x & 31), (int)(threadIdx.x >> 5), s_row, s_y, s_bc, &s_r};
+  const bool lead = threadIdx.x == 0;
   if (T > d.hist_cap) {   // a window longer than the history: nothing is replayed
-    if (C > 0 && blockIdx.x == 0 && lane == 0) atomicOr(d.status, ST_WINDOW);
+    if (C > 0 && blockIdx.x == 0 && lead) atomicOr(d.status, ST_WINDOW);
     return;
   }
   const size_t N = d.N;
@@ -1066,13 +1434,13 @@ __global__ void __launch_bounds__(32) k_catchup(Dev d) {
       for (int q = 0; q < 6; ++q) Y[q][m] = (m < nb) ? c[3 + 6 * m + q] : 0.0;
     }
     double s6[6];
-    const int res = catch_bs_any(d, S, gid, nb, Y, c[0], c[1], (int)c[2], lane, s6);
-    if (res < 0 && lane == 0) atomicOr(d.status, ST_BS);
+    const int res = catch_bs_any(d, S, gid, nb, Y, c[0], c[1], (int)c[2], B, s6);
+    if (res < 0 && lead) atomicOr(d.status, ST_BS);
     for (int t = t0; t < T; ++t) {
-      if (t > t0 && d.h_nkick[t] > 0) catch_front(d, S, sys, j, t, t == tl, lane, s6);
-      catch_back(d, S, sys, j, t, lane, s6);
+      if (t > t0 && d.h_nkick[t] > 0) catch_front(d, S, sys, j, t, t == tl, B, s6);
+      catch_back(d, S, sys, j, t, lead, s6);
     }
-    if (lane == 0) {
+    if (lead) {
       for (int q = 0; q < 6; ++q) d.xv[q * N + j] = s6[q];
       if (t0 == tl) d.flags[j] = 1;
       d.lag[j] = 0;
@@ -1085,15 +1453,15 @@ void launch_groups(const Dev& d, cudaStream_t st) { k_groups<<<1, 1024, 0, st>>>
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
   // (a group has at least two members: one big body and the body it meets)
   cudaMemsetAsync(d.cont_count, 0, sizeof(int), st);
-  k_bs_pack<2, 2><<<4 * nblocks, 32, 0, st>>>(d);
+  k_bs_pack2<<<4 * nblocks, 32, 0, st>>>(d);
   k_bs_pack<3, 4><<<4 * nblocks, 32, 0, st>>>(d);
   k_bs<<<nblocks, 32, 0, st>>>(d);
-  k_bs_spread<2, 2><<<nblocks / 4, 32, 0, st>>>(d);
+  k_bs_spread2<<<nblocks / 4, 128, 0, st>>>(d);
   k_bs_spread<3, 4><<<nblocks / 4, 32, 0, st>>>(d);
 }
 
 void launch_catchup(const Dev& d, int nblocks, cudaStream_t st) {
-  k_catchup<<<nblocks, 32, 0, st>>>(d);
+  k_catchup<<<nblocks, 128, 0, st>>>(d);
   cudaMemsetAsync(d.hstep, 0, 2 * sizeof(int), st);
 }
 

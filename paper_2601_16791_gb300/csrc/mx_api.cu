@@ -573,7 +573,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   int nsm = 0;
   MX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device));
   s->bs_blocks = 4 * nsm;
-  s->catch_blocks = 8 * nsm;
+  s->catch_blocks = 4 * nsm;
   return sync_status(s);
 }
 
