@@ -875,18 +875,20 @@ __device__ void pack_tail(const Dev& d, int w, unsigned gmask, int base, int lan
   if (d.defer && d.work_wfrom[w] == NB - 1) {
     const int hs = *d.hstep;
     int rr = d.dcap;
-    if (lane == base && hs < d.hist_cap) rr = atomicAdd(&d.hstep[1], 1);
+    if (lane == base && hs < d.hist_cap) rr = atomicAdd(&d.rcount[0], 1);
     rr = __shfl_sync(gmask, rr, base);
     if (rr < d.dcap) {
       if (lane == base) {
         const int j = d.work_mem[o0 + NB - 1];
-        int* R = d.d_rec + (size_t)rr * kDeferInts;
+        int* R = d.d_rec + (size_t)rr * kRecInts;   // bank 0: deferred in this window
         R[0] = j;
         R[1] = hs;
         R[2] = NB;
 #pragma unroll
-        for (int m = 0; m < NB; ++m) R[3 + m] = d.work_mem[o0 + m];
-        double* c = d.d_state + (size_t)rr * kContDoubles;
+        for (int m = 0; m < kLaneMaxNB; ++m) R[3 + m] = (m < NB) ? d.work_mem[o0 + m] : j;
+        R[7] = -1;
+        R[8] = 0;
+        double* c = d.d_state + (size_t)rr * kRecDoubles;
         c[0] = g.rem;
         c[1] = g.H;
         c[2] = (double)g.nsub;
@@ -1112,19 +1114,40 @@ __global__ void __launch_bounds__(32) k_bs(Dev d) {
 }
 
 // ----------------------------------------------- deferred planetesimals
-// k_catchup takes every planetesimal deferred in the window (one warp each)
-// from the middle of its deferral step to the end of the window.  A window's
-// history slots are whole steps and the leading half kicks of calls.  Each step
-// is the direct path's own arithmetic on the big bodies' recorded history:
-// jump (P of jump 1), Kepler drift, the encounter test against every big body
-// (same screen and FP64 test as k_detect), Bulirsch-Stoer of its
-// test-particle group from the pre-drift states (same lane integrator as the
-// packed and spread phases, which accept the same sub-steps), jump (P of jump
-// 2), gravity of the staged big positions in ascending order and the half
-// kick(s) with drag.  So a deferred body ends where the direct path would
-// have put it, bit for bit.  Lanes split only the encounter test; every other
-// part is the same on all 32 lanes (an FP64 instruction costs the same for
-// one lane or 32).
+// k_catchup replays the steps of deferred planetesimals (one body per block
+// of four warps).  A window's history slots are whole steps and the leading
+// half kicks of calls.  Each step is the direct path's own arithmetic on the
+// big bodies' recorded history: jump (P of jump 1), Kepler drift, the
+// encounter test against every big body (same screen and FP64 test as
+// k_detect), Bulirsch-Stoer of its test-particle group from the pre-drift
+// states (the integrators of the packed and spread phases, which accept the
+// same sub-steps), jump (P of jump 2), gravity of the staged big positions in
+// ascending order and the half kick(s) with drag.  So a deferred body ends
+// where the direct path would have put it, bit for bit.  The four warps take
+// the same path (each on its own scheduler, so the repeated work costs no
+// time); they differ only in the step candidate of a two-body group, and only
+// warp 0 writes.
+//
+// Modes (CatchArgs::mode):
+//  0  window end, main stream: every body deferred in the window and every
+//     body carried from the last one is replayed to the window's end with at
+//     most kCatchBudget macro sub-steps per two-body group; bodies that get
+//     there rejoin the step, the others are carried (copied to bank_out).
+//  1  side stream, while the main stream runs the next window: the carried
+//     bodies are replayed to the window's end without a budget (in place).
+//     This mode writes no state, lag flag or pair list, only the records.
+//  2  settle: everything is replayed to the end and rejoins the step.
+constexpr int kCatchBudget = 2;
+
+struct CatchArgs {
+  int mode;
+  int bank_a, bank_b;   // input banks (-1: none)
+  int bank_out;         // mode 0: bank of the carried bodies
+  int t_end;            // replay slots up to (not including) t_end
+  int tl;               // the range's last whole-step slot (pair list), -1 none
+  int next_slot;        // the history slot of the next step (modes 0 and 2, else -1)
+  int t_next;           // where the next range starts: a body that reached t_end is kept there
+};
 
 template <int NB>
 __device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, const int* gid,
@@ -1142,10 +1165,6 @@ __device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, co
   }
 }
 
-// The catch-up block: four warps that take the same path through a body's
-// steps (each warp on its own scheduler, so the repeated work costs no time);
-// they differ only in the step candidate of a two-body Bulirsch-Stoer group,
-// and only warp 0 writes results.
 struct CatchBlk {
   int lane, wq;
   int* s_row;     // [4]
@@ -1154,24 +1173,31 @@ struct CatchBlk {
   int* s_r;       // [1] broadcast of a result code
 };
 
-// Runs the group (members gid, state Y, progress rem/H/nsub) to the end of
-// the step on one warp (four candidates x eight rows on its lanes); the last
-// member's state goes to s6.
+// A test-particle group in progress: members, integration state.
+struct CatchGroup {
+  int nb;
+  int gid[kLaneMaxNB];
+  double rem, H;
+  int nsub;
+  double Y[6][kLaneMaxNB];
+};
+
+// Three or four bodies: the lane integrator of k_bs_spread on one warp, run
+// to the end of the step.
 template <int NB>
-__device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const int* gid,
-                        const double (&Y)[6][kLaneMaxNB], double rem, double H, int nsub,
-                        int lane, double* s6) {
+__device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const CatchGroup& G, int lane,
+                                     double* s6) {
   double mu[NB];
   MemberK K[NB];
-  load_members_g<NB>(d, S, gid, mu, K);
+  load_members_g<NB>(d, S, G.gid, mu, K);
   GroupRun<NB> g;
 #pragma unroll
   for (int m = 0; m < NB; ++m)
 #pragma unroll
-    for (int q = 0; q < 6; ++q) g.Y[q][m] = Y[q][m];
-  g.rem = rem;
-  g.H = H;
-  g.nsub = nsub;
+    for (int q = 0; q < 6; ++q) g.Y[q][m] = G.Y[q][m];
+  g.rem = G.rem;
+  g.H = G.H;
+  g.nsub = G.nsub;
   const int r = bs_rounds<NB, 4>(0xffffffffu, 0, lane, S.mu0, mu, K, d.bs_tol, d.bs_max_sub,
                                  1 << 30, g);
 #pragma unroll
@@ -1179,33 +1205,40 @@ __device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const int* g
   return r;
 }
 
-// Two bodies: term lanes, one candidate per warp of the block (k_bs_spread2's
-// integrator).  Three or four: warp 0 runs the lane integrator of
-// k_bs_spread, and the result is broadcast.
-__device__ int catch_bs_any(const Dev& d, const SysDev& S, const int* gid, int nb,
-                            const double (&Y)[6][kLaneMaxNB], double rem, double H, int nsub,
+// Runs the group for at most max_rounds macro sub-steps (two bodies: term
+// lanes, one candidate per warp; three or four: to the end of the step on
+// warp 0, then broadcast).  Returns 1 (done, body state in s6), 0 (rounds ran
+// out, G updated) or -1 (sub-step cap).
+__device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, int max_rounds,
                             const CatchBlk& B, double* s6) {
-  if (nb == 2) {
+  if (G.nb == 2) {
     double mu[2];
     MemberK K[2];
-    load_members_g<2>(d, S, gid, mu, K);
+    load_members_g<2>(d, S, G.gid, mu, K);
     const Bs2Term t = bs2_term(B.lane & 3, S.mu0, mu, K);
     GroupRun<2> g;
 #pragma unroll
     for (int m = 0; m < 2; ++m)
 #pragma unroll
-      for (int q = 0; q < 6; ++q) g.Y[q][m] = Y[q][m];
-    g.rem = rem;
-    g.H = H;
-    g.nsub = nsub;
-    const int r = bs2_rounds<4>(B.wq, B.lane, t, d.bs_tol, d.bs_max_sub, 1 << 30, g, B.s_row, B.s_y);
+      for (int q = 0; q < 6; ++q) g.Y[q][m] = G.Y[q][m];
+    g.rem = G.rem;
+    g.H = G.H;
+    g.nsub = G.nsub;
+    const int r = bs2_rounds<4>(B.wq, B.lane, t, d.bs_tol, d.bs_max_sub, max_rounds, g, B.s_row,
+                                B.s_y);
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) G.Y[q][m] = g.Y[q][m];
+    G.rem = g.rem;
+    G.H = g.H;
+    G.nsub = g.nsub;
 #pragma unroll
     for (int q = 0; q < 6; ++q) s6[q] = g.Y[q][1];
     return r;
   }
   if (B.wq == 0) {
-    const int r = (nb == 3) ? catch_bs<3>(d, S, gid, Y, rem, H, nsub, B.lane, s6)
-                            : catch_bs<4>(d, S, gid, Y, rem, H, nsub, B.lane, s6);
+    const int r = (G.nb == 3) ? catch_bs<3>(d, S, G, B.lane, s6) : catch_bs<4>(d, S, G, B.lane, s6);
     if (B.lane == 0) {
       for (int q = 0; q < 6; ++q) B.s_bc[q] = s6[q];
       *B.s_r = r;
@@ -1239,9 +1272,14 @@ __device__ __noinline__ void catch_bs_thread(const Dev& d, const SysDev& S, cons
   for (int q = 0; q < 6; ++q) out[q] = Y[q][nb - 1];
 }
 
-// Jump 1, drift, encounter test and (if flagged) Bulirsch-Stoer of step t.
-__device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t, bool last,
-                            const CatchBlk& B, double* s6) {
+// Jump 1, drift and the encounter test of step t.  No encounter: returns 0
+// with the drifted state in s6.  A group of up to four bodies: returns its
+// size with the group set up in G (pre-drift states, a fresh step).  Larger
+// groups are integrated here (returns 0).  keys: 0 ignore, 1 append the
+// pairs to the pair list (the last step of a range on the main stream), 2
+// keep them in *kn / kl for the record (the side stream).
+__device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t, int keys,
+                           const CatchBlk& B, double* s6, CatchGroup& G, int* kn, int* kl) {
   const int lane = B.lane;
   const bool w0 = B.wq == 0;
   const size_t NBs = (size_t)d.NB;
@@ -1291,7 +1329,7 @@ __device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t
         d.ever[gi] = 1;
         d.ever[j] = 1;
       }
-      if (last) {
+      if (keys == 1) {
         d.flags[gi] = 1;
         const int pos = atomicAdd(d.pair_count, 1);
         if (pos < d.pair_cap)
@@ -1305,11 +1343,13 @@ __device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t
       else over = true;
     }
   }
-  if (last && w0 && lane == 0) d.flags[j] = nf > 0 ? 1 : 0;
-  if (nf == 0) {
-    for (int q = 0; q < 6; ++q) s6[q] = a1[q];
-    return;
+  if (keys == 1 && w0 && lane == 0) d.flags[j] = nf > 0 ? 1 : 0;
+  if (keys == 2) {
+    *kn = nf;
+    for (int e = 0; e < nf; ++e) kl[e] = fl[e];
   }
+  for (int q = 0; q < 6; ++q) s6[q] = a1[q];
+  if (nf == 0) return 0;
   // members: the big groups of the flagged bodies (ascending), then j
   const int* comp = d.h_comp + (size_t)t * NBs + S.boff;
   int mem[kMaxGroup];
@@ -1339,27 +1379,27 @@ __device__ void catch_front(const Dev& d, const SysDev& S, int sys, int j, int t
   }
   if (bad) {   // the direct path skips the step's Bulirsch-Stoer and reports it
     if (w0 && lane == 0) atomicOr(d.status, ST_GROUP);
-    for (int q = 0; q < 6; ++q) s6[q] = a1[q];
-    return;
+    return 0;
   }
   const int nb = cnt + 1;
   if (nb <= kLaneMaxNB) {
-    int gid[kLaneMaxNB];
-    double Y[6][kLaneMaxNB];
+    G.nb = nb;
     for (int m = 0; m < kLaneMaxNB; ++m) {
       const bool big = m < cnt;
-      gid[m] = big ? S.off + mem[m] : j;
-      for (int q = 0; q < 6; ++q) Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
+      G.gid[m] = big ? S.off + mem[m] : j;
+      for (int q = 0; q < 6; ++q) G.Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
     }
-    const int r = catch_bs_any(d, S, gid, nb, Y, S.h, S.h, 0, B, s6);
-    if (r < 0 && w0 && lane == 0) atomicOr(d.status, ST_BS);
-    return;
+    G.rem = S.h;
+    G.H = S.h;
+    G.nsub = 0;
+    return nb;
   }
   // more than four bodies: the thread integrator of k_bs, on one thread
   if (w0 && lane == 0) catch_bs_thread(d, S, mem, cnt, a0, t, B.s_bc);
   __syncthreads();
   for (int q = 0; q < 6; ++q) s6[q] = B.s_bc[q];
   __syncthreads();
+  return 0;
 }
 
 // Jump 2 and the half kick(s) that end step t, or (head) the leading half
@@ -1407,44 +1447,133 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
   s6[5] = w;
 }
 
-__global__ void __launch_bounds__(128) k_catchup(Dev d) {
-  __shared__ int s_row[4], s_r;
-  __shared__ double s_y[12], s_bc[6];
-  const int T = d.hstep[0];
-  const int C = min(d.hstep[1], d.dcap);
-  const CatchBlk B{(int)(threadIdx.x & 31), (int)(threadIdx.x >> 5), s_row, s_y, s_bc, &s_r};
+__device__ __forceinline__ int* rec_ints(const Dev& d, int bank, int idx) {
+  return d.d_rec + ((size_t)bank * d.dcap + idx) * kRecInts;
+}
+__device__ __forceinline__ double* rec_state(const Dev& d, int bank, int idx) {
+  return d.d_state + ((size_t)bank * d.dcap + idx) * kRecDoubles;
+}
+
+// One record from the start of its progress to a.t_end (or, mode 0, until a
+// group outruns the budget).
+__device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx,
+                             const CatchBlk& B) {
   const bool lead = threadIdx.x == 0;
-  if (T > d.hist_cap) {   // a window longer than the history: nothing is replayed
-    if (C > 0 && blockIdx.x == 0 && lead) atomicOr(d.status, ST_WINDOW);
-    return;
+  const int* R = rec_ints(d, bank, idx);
+  const double* Cs = rec_state(d, bank, idx);
+  const int j = R[0];
+  int t = R[1];
+  int kslot = R[7], kn = R[8];
+  int kl[kMaxGroup];
+  for (int e = 0; e < kMaxGroup; ++e) kl[e] = (e < kn) ? R[9 + e] : 0;
+  const int sys = sys_of(d, j);
+  const SysDev& S = d.sys[sys];
+  // settle: pairs the side stream found at the range's last step
+  if (a.mode == 2 && kslot >= 0 && kslot == a.tl && lead) {
+    for (int e = 0; e < kn; ++e) {
+      const int gi = S.off + kl[e];
+      d.flags[gi] = 1;
+      const int pos = atomicAdd(d.pair_count, 1);
+      if (pos < d.pair_cap)
+        d.keys[pos] = (1ull << 63) | ((unsigned long long)(unsigned)j << 32) | (unsigned)gi;
+    }
+    d.flags[j] = kn > 0 ? 1 : 0;
   }
-  const size_t N = d.N;
-  int tl = T - 1;   // the window's last step (not a leading half kick)
-  while (tl >= 0 && d.h_nkick[tl] < 0) --tl;
-  for (int r = blockIdx.x; r < C; r += gridDim.x) {
-    const int* R = d.d_rec + (size_t)r * kDeferInts;
-    const int j = R[0], t0 = R[1], nb = R[2];
-    const int sys = sys_of(d, j);
-    const SysDev& S = d.sys[sys];
-    int gid[kLaneMaxNB];
-    double Y[6][kLaneMaxNB];
-    const double* c = d.d_state + (size_t)r * kContDoubles;
+  // stored pairs are valid only until the next pass over the record (slots are reused)
+  kslot = -1;
+  kn = 0;
+  CatchGroup G;
+  G.nb = R[2];
+  double s6[6];
+  for (int q = 0; q < 6; ++q) s6[q] = 0.0;
+  if (G.nb >= 2) {
     for (int m = 0; m < kLaneMaxNB; ++m) {
-      gid[m] = (m < nb) ? R[3 + m] : j;
-      for (int q = 0; q < 6; ++q) Y[q][m] = (m < nb) ? c[3 + 6 * m + q] : 0.0;
+      G.gid[m] = (m < G.nb) ? R[3 + m] : j;
+      for (int q = 0; q < 6; ++q) G.Y[q][m] = (m < G.nb) ? Cs[3 + 6 * m + q] : 0.0;
     }
-    double s6[6];
-    const int res = catch_bs_any(d, S, gid, nb, Y, c[0], c[1], (int)c[2], B, s6);
-    if (res < 0 && lead) atomicOr(d.status, ST_BS);
-    for (int t = t0; t < T; ++t) {
-      if (t > t0 && d.h_nkick[t] > 0) catch_front(d, S, sys, j, t, t == tl, B, s6);
+    G.rem = Cs[0];
+    G.H = Cs[1];
+    G.nsub = (int)Cs[2];
+  } else {
+    for (int q = 0; q < 6; ++q) s6[q] = Cs[3 + q];
+  }
+  const int budget = (a.mode == 0) ? kCatchBudget : (1 << 30);
+  bool carried = false;
+  for (;;) {
+    if (G.nb >= 2) {
+      const int r = catch_bs_any(d, S, G, budget, B, s6);
+      if (r == 0) {
+        carried = true;
+        break;
+      }
+      if (r < 0 && lead) atomicOr(d.status, ST_BS);
+      G.nb = 0;
       catch_back(d, S, sys, j, t, lead, s6);
+      ++t;
     }
+    if (t >= a.t_end) break;
+    if (d.h_nkick[t] > 0) {
+      const int km = (t == a.tl) ? (a.mode == 1 ? 2 : 1) : 0;
+      int kn2 = 0;
+      const int nb = catch_front(d, S, sys, j, t, km, B, s6, G, &kn2, kl);
+      if (km == 2) {
+        kslot = t;
+        kn = kn2;
+      }
+      if (nb >= 2) continue;   // the group runs at the top of the loop
+    }
+    catch_back(d, S, sys, j, t, lead, s6);
+    ++t;
+  }
+  if (a.mode != 1 && !carried) {   // up to date: the body rejoins the step
     if (lead) {
-      for (int q = 0; q < 6; ++q) d.xv[q * N + j] = s6[q];
-      if (t0 == tl) d.flags[j] = 1;
+      for (int q = 0; q < 6; ++q) d.xv[q * (size_t)d.N + j] = s6[q];
       d.lag[j] = 0;
     }
+    return;
+  }
+  // carried: mode 0 copies the record to bank_out, mode 1 updates it in place
+  __shared__ int s_slot;
+  if (lead) s_slot = (a.mode == 0) ? atomicAdd(&d.rcount[a.bank_out], 1) : idx;
+  __syncthreads();
+  const int ob = (a.mode == 0) ? a.bank_out : bank;
+  const int oi = s_slot;
+  __syncthreads();
+  if (!lead || oi >= d.dcap) {
+    if (lead && oi >= d.dcap) atomicOr(d.status, ST_WORK_OVF);
+    return;
+  }
+  int* O = rec_ints(d, ob, oi);
+  double* Os = rec_state(d, ob, oi);
+  O[0] = j;
+  O[1] = (t >= a.t_end) ? a.t_next : t;
+  O[2] = carried ? G.nb : 0;
+  for (int m = 0; m < kLaneMaxNB; ++m) O[3 + m] = carried ? G.gid[m] : 0;
+  O[7] = kslot;
+  O[8] = kn;
+  for (int e = 0; e < kMaxGroup; ++e) O[9 + e] = kl[e];
+  if (carried) {
+    Os[0] = G.rem;
+    Os[1] = G.H;
+    Os[2] = (double)G.nsub;
+    for (int m = 0; m < kLaneMaxNB; ++m)
+      for (int q = 0; q < 6; ++q) Os[3 + 6 * m + q] = G.Y[q][m];
+  } else {
+    for (int q = 0; q < 6; ++q) Os[3 + q] = s6[q];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_catchup(Dev d, CatchArgs a) {
+  __shared__ int s_row[4], s_r;
+  __shared__ double s_y[12], s_bc[6];
+  const CatchBlk B{(int)(threadIdx.x & 31), (int)(threadIdx.x >> 5), s_row, s_y, s_bc, &s_r};
+  const int na = (a.bank_a >= 0) ? min(d.rcount[a.bank_a], d.dcap) : 0;
+  const int nb = (a.bank_b >= 0) ? min(d.rcount[a.bank_b], d.dcap) : 0;
+  if (a.next_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) d.hstep[0] = a.next_slot;
+  for (int r = blockIdx.x; r < na + nb; r += gridDim.x) {
+    if (r < na) catch_record(d, a, a.bank_a, r, B);
+    else catch_record(d, a, a.bank_b, r - na, B);
+    __syncthreads();
   }
 }
 
@@ -1460,9 +1589,10 @@ void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
   k_bs_spread<3, 4><<<nblocks / 4, 32, 0, st>>>(d);
 }
 
-void launch_catchup(const Dev& d, int nblocks, cudaStream_t st) {
-  k_catchup<<<nblocks, 128, 0, st>>>(d);
-  cudaMemsetAsync(d.hstep, 0, 2 * sizeof(int), st);
+void launch_catchup(const Dev& d, int nblocks, int mode, int bank_a, int bank_b, int bank_out,
+                    int t_end, int tl, int next_slot, int t_next, cudaStream_t st) {
+  const CatchArgs a{mode, bank_a, bank_b, bank_out, t_end, tl, next_slot, t_next};
+  k_catchup<<<nblocks, 128, 0, st>>>(d, a);
 }
 
 }  // namespace mx

@@ -117,13 +117,25 @@ struct mx_system {
   unsigned* h_status = nullptr;   // pinned
   int* h_count = nullptr;         // pinned
   std::vector<void*> allocs;
-  cudaGraphExec_t g_head = nullptr, g_mid = nullptr, g_last = nullptr, g_catch = nullptr;
+  cudaGraphExec_t g_head = nullptr, g_mid = nullptr, g_last = nullptr;
   long long step = 0;
   int bs_blocks = 0;
   int catch_blocks = 0;
   int window = 0;                 // history slots per catch-up of deferred planetesimals (0: off)
-  int pending = 0;                // slots recorded since the last catch-up
+  int pending = 0;                // slots recorded in the current window
+  int wbase = 0;                  // first history slot of the current window (0 or window)
+  int last_full = -1;             // history slot of the last whole step, -1 none
+  int carried = 1;                // bank of the bodies carried from the last window (1 or 2)
+  bool side_busy = false;         // a side-stream pass is in flight
+  cudaStream_t side_st = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_side = nullptr;
   long long catchups = 0;
+  // side-stream launches timed by mx_step_profiled, read once they complete
+  struct Span {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Span> side_spans;
   int tile = mx::kThreads;        // targets per tile (autotuned)
   int order = 0;                  // 0: tiles in system order; 1: costliest first
   int tiles_cap = 0;
@@ -194,33 +206,87 @@ void enqueue_step(mx_system* s, int last, cudaStream_t st) {
   mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st);
 }
 
-// The end of a window: deferred planetesimals catch up with the rest.
-void enqueue_catchup(mx_system* s, cudaStream_t st) { mx::launch_catchup(s->d, s->catch_blocks, st); }
-
 // Deferral is on for forward runs with a window; recording or replaying the
 // drag branches (kmode != 0) keeps every body on the direct path.
 void update_defer(mx_system* s) { s->d.defer = (s->window > 0 && s->d.kmode == 0) ? 1 : 0; }
 
-// A history slot (a step, or the leading half kick of a call) has been
-// enqueued; a full window is caught up at once.  `catch_up` enqueues it.
-template <class F>
-cudaError_t slot_done(mx_system* s, F&& catch_up) {
-  if (!s->d.defer) return cudaSuccess;
-  if (++s->pending < s->window) return cudaSuccess;
+// The end of a window of history slots [wbase, wbase + window).  On the main
+// stream, after the side stream's pass over the last window: bodies deferred
+// in this window and bodies carried from the last one are replayed with a
+// round budget; those that reach the end rejoin the step, the rest are
+// carried.  Then, on the side stream, the carried bodies are replayed to the
+// window's end while the main stream goes on with the next window (it writes
+// the other half of the history ring).  `timed(kind, stream, launch)` wraps
+// each launch (event timing in mx_step_profiled).
+template <class Timed>
+cudaError_t window_end(mx_system* s, Timed&& timed) {
+  const int out = 3 - s->carried;
+  const int t_end = s->wbase + s->window;
+  const int next = (s->wbase == 0) ? s->window : 0;
+  const int tl = (s->last_full >= s->wbase && s->last_full < t_end) ? s->last_full : -1;
+  cudaError_t e = cudaSuccess;
+  if (s->side_busy) e = cudaStreamWaitEvent(s->st, s->ev_side, 0);
+  if (e == cudaSuccess)
+    e = timed(MX_K_CATCHUP, s->st, [&] {
+      mx::launch_catchup(s->d, s->catch_blocks, 0, s->carried, 0, out, t_end, tl, next, next, s->st);
+      cudaMemsetAsync(s->d.rcount + s->carried, 0, sizeof(int), s->st);
+      cudaMemsetAsync(s->d.rcount, 0, sizeof(int), s->st);
+    });
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_main, s->st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side_st, s->ev_main, 0);
+  if (e == cudaSuccess)
+    e = timed(MX_K_CATCHUP, s->side_st, [&] {
+      mx::launch_catchup(s->d, s->catch_blocks, 1, out, -1, out, t_end, tl, -1, next, s->side_st);
+    });
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_side, s->side_st);
+  s->side_busy = true;
+  s->carried = out;
+  s->wbase = next;
   s->pending = 0;
   ++s->catchups;
-  return catch_up();
+  return e;
 }
 
-// Brings deferred planetesimals up to date before the state is read,
-// replaced, or the parameters they were recorded under change.
-mx_status settle(mx_system* s) {
-  if (s->pending == 0) return MX_OK;
+// A history slot (a whole step, or the leading half kick of a call) has been
+// enqueued on the main stream.
+template <class Timed>
+cudaError_t slot_done(mx_system* s, bool full, Timed&& timed) {
+  if (!s->d.defer) return cudaSuccess;
+  if (full) s->last_full = s->wbase + s->pending;
+  if (++s->pending < s->window) return cudaSuccess;
+  return window_end(s, timed);
+}
+
+auto untimed = [](int, cudaStream_t, auto&& launch) -> cudaError_t {
+  launch();
+  return cudaGetLastError();
+};
+
+// Brings every deferred planetesimal up to date (the main stream waits for
+// the side stream, then replays what is left of the current window with no
+// budget) before the state is read or replaced, or the parameters the history
+// was recorded under change.  The history ring starts again at slot 0.
+template <class Timed>
+cudaError_t settle_with(mx_system* s, Timed&& timed) {
+  if (!s->d.defer || (s->pending == 0 && !s->side_busy)) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (s->side_busy) e = cudaStreamWaitEvent(s->st, s->ev_side, 0);
+  if (e == cudaSuccess)
+    e = timed(MX_K_CATCHUP, s->st, [&] {
+      mx::launch_catchup(s->d, s->catch_blocks, 2, s->carried, 0, -1, s->wbase + s->pending,
+                         s->last_full, 0, 0, s->st);
+      cudaMemsetAsync(s->d.rcount, 0, 3 * sizeof(int), s->st);
+    });
+  s->side_busy = false;
   s->pending = 0;
+  s->wbase = 0;
+  s->last_full = -1;
   ++s->catchups;
-  if (s->g_catch) MX_CUDA(cudaGraphLaunch(s->g_catch, s->st));
-  else enqueue_catchup(s, s->st);
-  MX_CUDA(cudaGetLastError());
+  return e;
+}
+
+mx_status settle(mx_system* s) {
+  MX_CUDA(settle_with(s, untimed));
   return MX_OK;
 }
 
@@ -228,7 +294,6 @@ mx_status capture(mx_system* s, int which, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   MX_CUDA(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
   if (which == 0) enqueue_head(s, s->cap_st);
-  else if (which == 3) enqueue_catchup(s, s->cap_st);
   else enqueue_step(s, which == 2, s->cap_st);
   cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
   if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
@@ -243,7 +308,6 @@ mx_status ensure_graphs(mx_system* s) {
   MX_TRY(capture(s, 0, &s->g_head));
   MX_TRY(capture(s, 1, &s->g_mid));
   MX_TRY(capture(s, 2, &s->g_last));
-  MX_TRY(capture(s, 3, &s->g_catch));
   return MX_OK;
 }
 
@@ -280,8 +344,7 @@ void drop_graphs(mx_system* s) {
   if (s->g_head) cudaGraphExecDestroy(s->g_head);
   if (s->g_mid) cudaGraphExecDestroy(s->g_mid);
   if (s->g_last) cudaGraphExecDestroy(s->g_last);
-  if (s->g_catch) cudaGraphExecDestroy(s->g_catch);
-  s->g_head = s->g_mid = s->g_last = s->g_catch = nullptr;
+  s->g_head = s->g_mid = s->g_last = nullptr;
 }
 
 mx_status set_tiling(mx_system* s, int tile, int order) {
@@ -380,13 +443,14 @@ mx_status trial_ms(mx_system* s, double* ms) {
   cudaEvent_t e0, e1;
   MX_CUDA(cudaEventCreate(&e0));
   MX_CUDA(cudaEventCreate(&e1));
-  enqueue_head(s, s->st);          // warm-up step
-  enqueue_step(s, 1, s->st);
-  if (s->d.defer) enqueue_catchup(s, s->st);
-  MX_CUDA(cudaEventRecord(e0, s->st));
-  enqueue_head(s, s->st);
-  enqueue_step(s, 1, s->st);
-  if (s->d.defer) enqueue_catchup(s, s->st);
+  for (int rep = 0; rep < 2; ++rep) {   // a warm-up step, then the timed one
+    if (rep == 1) MX_CUDA(cudaEventRecord(e0, s->st));
+    enqueue_head(s, s->st);
+    MX_CUDA(slot_done(s, false, untimed));
+    enqueue_step(s, 1, s->st);
+    MX_CUDA(slot_done(s, true, untimed));
+    MX_CUDA(settle_with(s, untimed));
+  }
   MX_CUDA(cudaEventRecord(e1, s->st));
   MX_CUDA(cudaEventSynchronize(e1));
   float t = 0.f;
@@ -500,7 +564,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
     d.hist_cap = hc;
     d.dcap = 1 << 14;
     MX_TRY(dalloc(s, &d.lag, N));
-    MX_TRY(dalloc(s, &d.hstep, 2));
+    MX_TRY(dalloc(s, &d.hstep, 1));
+    MX_TRY(dalloc(s, &d.rcount, 3));
     MX_TRY(dalloc(s, &d.defer_total, 1));
     MX_TRY(dalloc(s, &d.h_P, (size_t)hc * 6 * nsys));
     MX_TRY(dalloc(s, &d.h_b0, (size_t)hc * 6 * NB));
@@ -508,9 +573,9 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
     MX_TRY(dalloc(s, &d.h_bx, (size_t)hc * 3 * NB));
     MX_TRY(dalloc(s, &d.h_comp, (size_t)hc * NB));
     MX_TRY(dalloc(s, &d.h_nkick, hc));
-    MX_TRY(dalloc(s, &d.d_rec, (size_t)d.dcap * mx::kDeferInts));
-    MX_TRY(dalloc(s, &d.d_state, (size_t)d.dcap * 27));
-    s->window = std::min(kDefaultWindow, hc);
+    MX_TRY(dalloc(s, &d.d_rec, (size_t)3 * d.dcap * mx::kRecInts));
+    MX_TRY(dalloc(s, &d.d_state, (size_t)3 * d.dcap * mx::kRecDoubles));
+    s->window = std::min(kDefaultWindow, hc / 2);
   }
   MX_TRY(dalloc(s, &d.status, 1));
   MX_TRY(dalloc(s, &s->d_sys, nsys));
@@ -541,7 +606,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemsetAsync(d.bb_count, 0, sizeof(unsigned long long), st));
   MX_CUDA(cudaMemsetAsync(d.kick_ctr, 0, 2 * sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.lag, 0, N, st));
-  MX_CUDA(cudaMemsetAsync(d.hstep, 0, 2 * sizeof(int), st));
+  MX_CUDA(cudaMemsetAsync(d.hstep, 0, sizeof(int), st));
+  MX_CUDA(cudaMemsetAsync(d.rcount, 0, 3 * sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.defer_total, 0, sizeof(unsigned long long), st));
   update_defer(s);
   // host staging: state rows, masses as mu = G m, per-body drag inputs
@@ -585,6 +651,16 @@ void destroy_impl(mx_system* s) {
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_status) cudaFreeHost(s->h_status);
   if (s->h_count) cudaFreeHost(s->h_count);
+  if (s->side_st) {
+    cudaStreamSynchronize(s->side_st);
+    cudaStreamDestroy(s->side_st);
+  }
+  for (auto& sp : s->side_spans) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  if (s->ev_main) cudaEventDestroy(s->ev_main);
+  if (s->ev_side) cudaEventDestroy(s->ev_side);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
   delete s;
 }
@@ -598,6 +674,9 @@ mx_status create(mx_system** out, void* stream) {
   }
   s->st = (cudaStream_t)stream;
   if (cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_main, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_side, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost(&s->h_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&s->h_count, 2 * sizeof(int)) != cudaSuccess) {
     destroy_impl(s);
@@ -720,8 +799,8 @@ mx_status mx_set_tiling(mx_system* s, int tile, int order) {
 
 mx_status mx_set_defer_window(mx_system* s, int window) {
   if (!s || window < 0) return fail(MX_ERR_ARG, "invalid arguments");
-  if (window > s->d.hist_cap)
-    return fail(MX_ERR_ARG, "window longer than the history (" + std::to_string(s->d.hist_cap) + " steps)");
+  if (2 * window > s->d.hist_cap)
+    return fail(MX_ERR_ARG, "window longer than half the history (" + std::to_string(s->d.hist_cap / 2) + " slots)");
   MX_TRY(set_device(s));
   MX_TRY(settle(s));
   s->window = window;
@@ -738,7 +817,7 @@ mx_status mx_defer_stats(mx_system* s, int* window, int* max_window, long long* 
   MX_CUDA(cudaMemcpyAsync(&n, s->d.defer_total, sizeof(n), cudaMemcpyDeviceToHost, s->st));
   MX_CUDA(cudaStreamSynchronize(s->st));
   if (window) *window = s->d.defer ? s->window : 0;
-  if (max_window) *max_window = s->d.hist_cap;
+  if (max_window) *max_window = s->d.hist_cap / 2;
   if (deferred) *deferred = (long long)n;
   if (catchups) *catchups = s->catchups;
   return MX_OK;
@@ -777,12 +856,11 @@ mx_status mx_step(mx_system* s, int n_steps) {
     return sync_status(s);
   }
   MX_TRY(ensure_graphs(s));
-  auto catch_up = [&] { return cudaGraphLaunch(s->g_catch, s->st); };
   MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
-  MX_CUDA(slot_done(s, catch_up));
+  MX_CUDA(slot_done(s, false, untimed));
   for (int k = 0; k < n_steps; ++k) {
     MX_CUDA(cudaGraphLaunch(k + 1 == n_steps ? s->g_last : s->g_mid, s->st));
-    MX_CUDA(slot_done(s, catch_up));
+    MX_CUDA(slot_done(s, true, untimed));
   }
   s->step += n_steps;
   return sync_status(s);
@@ -794,37 +872,39 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
   MX_TRY(set_device(s));
   cudaStream_t st = s->st;
   // (kind, event-before, event-after) per launch
-  std::vector<int> kind;
-  std::vector<cudaEvent_t> ev;
-  auto rec = [&]() -> cudaError_t {
-    cudaEvent_t e;
-    cudaError_t r = cudaEventCreate(&e);
-    if (r != cudaSuccess) return r;
-    ev.push_back(e);
-    return cudaEventRecord(e, st);
+  std::vector<mx_system::Span> spans;
+  cudaEvent_t first = nullptr, last = nullptr;   // on the main stream
+  auto mk = [&](cudaStream_t sm, cudaEvent_t* ev) -> cudaError_t {
+    cudaError_t r = cudaEventCreate(ev);
+    return (r != cudaSuccess) ? r : cudaEventRecord(*ev, sm);
   };
-  auto timed = [&](int k, auto&& launch) -> cudaError_t {
-    kind.push_back(k);
-    cudaError_t r = rec();
+  auto timed3 = [&](int k, cudaStream_t sm, auto&& launch) -> cudaError_t {
+    mx_system::Span sp{k, nullptr, nullptr};
+    cudaError_t r = mk(sm, &sp.a);
     if (r != cudaSuccess) return r;
     launch();
-    return rec();
-  };
-  cudaError_t e = cudaSuccess;
-  auto catch_up = [&] { return timed(MX_K_CATCHUP, [&] { enqueue_catchup(s, st); }); };
-  if (n_steps == 0) {   // only the pending catch-up, timed
-    if (s->pending > 0) {
-      s->pending = 0;
-      ++s->catchups;
-      e = catch_up();
+    r = mk(sm, &sp.b);
+    if (r != cudaSuccess) return r;
+    if (sm == st) {
+      if (!first) first = sp.a;
+      last = sp.b;
+      spans.push_back(sp);
+    } else {
+      s->side_spans.push_back(sp);
     }
+    return cudaGetLastError();
+  };
+  auto timed = [&](int k, auto&& launch) { return timed3(k, st, launch); };
+  cudaError_t e = cudaSuccess;
+  if (n_steps == 0) {   // only the pending catch-up, timed
+    e = settle_with(s, timed3);
   } else {
     e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
     if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
-    if (e == cudaSuccess) e = slot_done(s, catch_up);
+    if (e == cudaSuccess) e = slot_done(s, false, timed3);
   }
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
-    const bool last = (k + 1 == n_steps);
+    const bool last_step = (k + 1 == n_steps);
     e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5, st); });
     if (e == cudaSuccess)
       e = timed(MX_K_DETECT, [&] {
@@ -833,26 +913,43 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     if (e == cudaSuccess) e = timed(MX_K_SORT, [&] { mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st); });
     if (e == cudaSuccess) e = timed(MX_K_GROUPS, [&] { mx::launch_groups(s->d, st); });
     if (e == cudaSuccess) e = timed(MX_K_BS, [&] { mx::launch_bs(s->d, s->bs_blocks, st); });
-    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, last ? 1 : 2, st); });
+    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, last_step ? 1 : 2, st); });
     if (e == cudaSuccess)
-      e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st); });
-    if (e == cudaSuccess) e = slot_done(s, catch_up);
+      e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last_step ? 1 : 2, st); });
+    if (e == cudaSuccess) e = slot_done(s, true, timed3);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   double sum[MX_NKERN] = {0};
   int cnt[MX_NKERN] = {0};
   float ms = 0.f;
-  for (size_t q = 0; q < kind.size() && e == cudaSuccess; ++q) {
-    e = cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]);
-    sum[kind[q]] += ms;
-    cnt[kind[q]]++;
+  for (auto& sp : spans) {
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, sp.a, sp.b);
+    sum[sp.kind] += ms;
+    cnt[sp.kind]++;
   }
+  // side-stream launches: those that have completed (all of them after a settle)
+  std::vector<mx_system::Span> keep;
+  for (auto& sp : s->side_spans) {
+    if (e == cudaSuccess && cudaEventQuery(sp.b) == cudaSuccess) {
+      e = cudaEventElapsedTime(&ms, sp.a, sp.b);
+      sum[sp.kind] += ms;
+      cnt[sp.kind]++;
+      cudaEventDestroy(sp.a);
+      cudaEventDestroy(sp.b);
+    } else {
+      keep.push_back(sp);
+    }
+  }
+  s->side_spans.swap(keep);
   if (e == cudaSuccess && total_ms) {
     ms = 0.f;
-    if (!ev.empty()) e = cudaEventElapsedTime(&ms, ev.front(), ev.back());
+    if (first) e = cudaEventElapsedTime(&ms, first, last);
     *total_ms = ms;
   }
-  for (auto x : ev) cudaEventDestroy(x);
+  for (auto& sp : spans) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
   if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("profiled step: ") + cudaGetErrorString(e));
   for (int k = 0; k < MX_NKERN; ++k) {
     if (kernel_ms) kernel_ms[k] = sum[k];

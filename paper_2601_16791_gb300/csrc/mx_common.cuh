@@ -107,24 +107,30 @@ struct Dev {
   // the same device functions (so the result is the one the direct path
   // gives, bit for bit).  defer = 0 leaves every step on the direct path.
   int defer;
-  int hist_cap;        // steps of history (the longest window)
-  int dcap;            // deferred records
-  unsigned char* lag;  // [N] 1 while the body waits for the catch-up
-  int* hstep;          // [0] slot of the current step in the window, [1] deferred records
+  int hist_cap;        // history slots (two windows)
+  int dcap;            // records per bank
+  unsigned char* lag;  // [N] 1 while the body waits for a catch-up
+  int* hstep;          // [0] history slot of the current step
+  int* rcount;         // [3] records in each bank
   unsigned long long* defer_total;  // bodies deferred since creation
   double* h_P;         // [hist_cap][2][3 nsys] P of jump 1, P of jump 2 and the kicks
   double* h_b0;        // [hist_cap][6][NB] big bodies after jump 1 (pre-drift)
   double* h_b1;        // [hist_cap][6][NB] big bodies after the drift (detection endpoint)
   double* h_bx;        // [hist_cap][3][NB] big positions after jump 2 (kick sources)
   int* h_comp;         // [hist_cap][NB] big group of each big body, -1 for none
-  int* h_nkick;        // [hist_cap] half kicks at the end of the step
-  int* d_rec;          // [dcap][kDeferInts] body, window slot, member count, members
-  double* d_state;     // [dcap][3 + 6 x 4] Bulirsch-Stoer state handed over
+  int* h_nkick;        // [hist_cap] half kicks ending the slot; -1: a call's leading half kick
+  int* d_rec;          // [3][dcap][kRecInts] records: bank 0 deferred in this window,
+                       // banks 1 and 2 carried between windows
+  double* d_state;     // [3][dcap][kRecDoubles]
 };
 
-// Deferred record: body, window slot, member count, up to four members
-// (global indices, bigs ascending, the body last), one spare.
-constexpr int kDeferInts = 8;
+// Record of a deferred body.  Ints: body, history slot t, group size (0: at
+// the start of slot t with the body's state in doubles 3..8; >= 2: in the
+// middle of slot t's Bulirsch-Stoer group), four member indices, the slot and
+// count of pairs found at the last step of a side-stream pass, their big
+// bodies (local indices).  Doubles: rem, H, nsub, 6 x 4 group state.
+constexpr int kRecInts = 32;
+constexpr int kRecDoubles = 3 + 6 * 4;
 
 // Buffers of one adjoint step (k_adjoint.cu).
 struct Adj {

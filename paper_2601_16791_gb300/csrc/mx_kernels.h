@@ -37,7 +37,11 @@ void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int 
 // k_bs.cu
 void launch_groups(const Dev& d, cudaStream_t st);
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st);
-void launch_catchup(const Dev& d, int nblocks, cudaStream_t st);
+// mode 0: window end (budgeted, carried bodies to bank_out); 1: side stream
+// (bank_a in place); 2: settle (everything rejoins).  Slots up to t_end; a
+// body kept at t_end is stored at slot t_next (the next range's start).
+void launch_catchup(const Dev& d, int nblocks, int mode, int bank_a, int bank_b, int bank_out,
+                    int t_end, int tl, int next_slot, int t_next, cudaStream_t st);
 
 
 // k_adjoint.cu
