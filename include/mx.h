@@ -173,7 +173,7 @@ void mx_destroy(mx_system* s);
 mx_status mx_step(mx_system* s, int n_steps);
 
 /* Kernels of one step, in launch order, for mx_step_profiled. */
-#define MX_NKERN 8
+#define MX_NKERN 9
 #define MX_K_PREP 0       /* momentum + staged big positions */
 #define MX_K_JUMP_KICK 1  /* jump + half kick(s): gravity and drag */
 #define MX_K_JUMP_DRIFT 2 /* jump + Kepler drift */
@@ -181,20 +181,33 @@ mx_status mx_step(mx_system* s, int n_steps);
 #define MX_K_SORT 4       /* pair-key sort */
 #define MX_K_GROUPS 5     /* encounter groups */
 #define MX_K_BS 6         /* Bulirsch-Stoer of the groups */
-#define MX_K_CATCHUP 7    /* deferred planetesimals brought to the end of the window */
+#define MX_K_CATCHUP 7    /* deferred planetesimals: window-end and settling catch-ups */
+#define MX_K_CATCHUP_SIDE 8 /* carried planetesimals on the side stream (overlaps the steps) */
 
 /*
  * mx_step_profiled -- the same n_steps as mx_step, launched kernel by kernel
  * (no graph) with CUDA events around every launch on the system's stream.
  *  kernel_ms [MX_NKERN]  summed device time per kernel (host, may be NULL)
  *  launches  [MX_NKERN]  launches per kernel (host, may be NULL)
- *  total_ms              device time from before the first launch to after
- *                        the last (host, may be NULL)
+ *  total_ms              sum over the steps of each step's device time, from
+ *                        before its first launch to after its last (a
+ *                        window-end catch-up belongs to the step that ends
+ *                        the window) (host, may be NULL)
  * Synchronises once at the end.  n_steps = 0 only runs (and times) the
- * pending catch-up of deferred planetesimals, if any.
+ * pending catch-up of deferred planetesimals, if any.  Side-stream launches
+ * (MX_K_CATCHUP_SIDE) are counted in the call during which they complete.
  */
 mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* launches,
                            double* total_ms);
+
+/*
+ * mx_step_timed -- mx_step_profiled with a cache flush: before every step the
+ * device buffer dev_flush (flush_bytes bytes, e.g. more than the L2 cache;
+ * caller-owned) is overwritten on the system's stream, outside the steps'
+ * timed spans.  flush_bytes = 0 means no flush.
+ */
+mx_status mx_step_timed(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
+                        double* kernel_ms, int* launches, double* total_ms);
 
 /* Encounter pairs found by the last step (sorted by (i, j), i big, body
  * indices), copied to host_pairs [2*cap]; *n_pairs gets the full count. */

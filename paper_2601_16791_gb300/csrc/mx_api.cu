@@ -235,7 +235,7 @@ cudaError_t window_end(mx_system* s, Timed&& timed) {
   if (e == cudaSuccess) e = cudaEventRecord(s->ev_main, s->st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side_st, s->ev_main, 0);
   if (e == cudaSuccess)
-    e = timed(MX_K_CATCHUP, s->side_st, [&] {
+    e = timed(MX_K_CATCHUP_SIDE, s->side_st, [&] {
       mx::launch_catchup(s->d, s->catch_blocks, 1, out, -1, out, t_end, tl, -1, next, s->side_st);
     });
   if (e == cudaSuccess) e = cudaEventRecord(s->ev_side, s->side_st);
@@ -866,14 +866,22 @@ mx_status mx_step(mx_system* s, int n_steps) {
   return sync_status(s);
 }
 
-mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* launches,
-                           double* total_ms) {
-  if (!s || n_steps < 0) return fail(MX_ERR_ARG, "invalid arguments");
+}  // extern "C"
+
+namespace {
+
+// mx_step_profiled / mx_step_timed: launch by launch with events.  total_ms
+// sums each step's span (its first launch to its last, a window-end
+// catch-up included); with a flush buffer, the buffer is overwritten before
+// every step, outside the spans.
+mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_bytes,
+                       double* kernel_ms, int* launches, double* total_ms) {
+  if (!s || n_steps < 0 || (flush_bytes > 0 && !flush)) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
   cudaStream_t st = s->st;
   // (kind, event-before, event-after) per launch
   std::vector<mx_system::Span> spans;
-  cudaEvent_t first = nullptr, last = nullptr;   // on the main stream
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> steps;   // per-step spans, main stream
   auto mk = [&](cudaStream_t sm, cudaEvent_t* ev) -> cudaError_t {
     cudaError_t r = cudaEventCreate(ev);
     return (r != cudaSuccess) ? r : cudaEventRecord(*ev, sm);
@@ -886,8 +894,6 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     r = mk(sm, &sp.b);
     if (r != cudaSuccess) return r;
     if (sm == st) {
-      if (!first) first = sp.a;
-      last = sp.b;
       spans.push_back(sp);
     } else {
       s->side_spans.push_back(sp);
@@ -895,17 +901,28 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     return cudaGetLastError();
   };
   auto timed = [&](int k, auto&& launch) { return timed3(k, st, launch); };
+  auto step_open = [&](int k) -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    if (flush_bytes > 0) r = cudaMemsetAsync(flush, k & 0xff, flush_bytes, st);
+    steps.push_back({nullptr, nullptr});
+    return (r != cudaSuccess) ? r : mk(st, &steps.back().first);
+  };
+  auto step_close = [&]() -> cudaError_t { return mk(st, &steps.back().second); };
   cudaError_t e = cudaSuccess;
   if (n_steps == 0) {   // only the pending catch-up, timed
-    e = settle_with(s, timed3);
+    e = step_open(0);
+    if (e == cudaSuccess) e = settle_with(s, timed3);
+    if (e == cudaSuccess) e = step_close();
   } else {
-    e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
+    e = step_open(0);
+    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
     if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
     if (e == cudaSuccess) e = slot_done(s, false, timed3);
   }
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
     const bool last_step = (k + 1 == n_steps);
-    e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5, st); });
+    if (k > 0) e = step_open(k);
+    if (e == cudaSuccess) e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5, st); });
     if (e == cudaSuccess)
       e = timed(MX_K_DETECT, [&] {
         mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count, s->d.pair_cap, st);
@@ -917,6 +934,7 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     if (e == cudaSuccess)
       e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last_step ? 1 : 2, st); });
     if (e == cudaSuccess) e = slot_done(s, true, timed3);
+    if (e == cudaSuccess) e = step_close();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   double sum[MX_NKERN] = {0};
@@ -941,14 +959,21 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
     }
   }
   s->side_spans.swap(keep);
-  if (e == cudaSuccess && total_ms) {
-    ms = 0.f;
-    if (first) e = cudaEventElapsedTime(&ms, first, last);
-    *total_ms = ms;
+  double tot = 0.0;
+  for (auto& sp : steps) {
+    if (e == cudaSuccess && sp.first && sp.second) {
+      e = cudaEventElapsedTime(&ms, sp.first, sp.second);
+      tot += ms;
+    }
   }
+  if (total_ms) *total_ms = tot;
   for (auto& sp : spans) {
     cudaEventDestroy(sp.a);
     cudaEventDestroy(sp.b);
+  }
+  for (auto& sp : steps) {
+    if (sp.first) cudaEventDestroy(sp.first);
+    if (sp.second) cudaEventDestroy(sp.second);
   }
   if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("profiled step: ") + cudaGetErrorString(e));
   for (int k = 0; k < MX_NKERN; ++k) {
@@ -957,6 +982,20 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
   }
   s->step += n_steps;
   return sync_status(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* launches,
+                           double* total_ms) {
+  return profiled_run(s, n_steps, nullptr, 0, kernel_ms, launches, total_ms);
+}
+
+mx_status mx_step_timed(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
+                        double* kernel_ms, int* launches, double* total_ms) {
+  return profiled_run(s, n_steps, dev_flush, flush_bytes, kernel_ms, launches, total_ms);
 }
 
 mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pairs) {

@@ -55,6 +55,7 @@ _SIGS = {
     "mx_destroy": (None, [_P]),
     "mx_step": (_I, [_P, _I]),
     "mx_step_profiled": (_I, [_P, _I, _P, _P, _P]),
+    "mx_step_timed": (_I, [_P, _I, _P, ctypes.c_size_t, _P, _P, _P]),
     "mx_last_encounters": (_I, [_P, _P, _I, _P]),
     "mx_accel": (_I, [_P, _P]),
     "mx_gas_drag": (_I, [_P, _P]),
@@ -166,7 +167,7 @@ def mx_step(sys, n_steps):
 
 
 KERNELS = ("k_prep", "k_jump_kick", "k_jump_drift", "k_detect", "k_sort_keys", "k_groups", "k_bs",
-           "k_catchup")
+           "k_catchup", "k_catchup_side")
 
 
 def mx_step_profiled(sys, n_steps):
@@ -176,6 +177,18 @@ def mx_step_profiled(sys, n_steps):
     tot = ctypes.c_double(0.0)
     _check(load().mx_step_profiled(sys, int(n_steps), _hptr(ms), _hptr(cnt), ctypes.byref(tot)),
            "mx_step_profiled")
+    return dict(zip(KERNELS, ms.tolist())), dict(zip(KERNELS, cnt.tolist())), tot.value
+
+
+def mx_step_timed(sys, n_steps, dev_flush=None):
+    """mx_step_profiled with dev_flush (a CUDA tensor, e.g. larger than L2)
+    overwritten before every step, outside the timed spans."""
+    ms = np.zeros(len(KERNELS))
+    cnt = np.zeros(len(KERNELS), dtype=np.int32)
+    tot = ctypes.c_double(0.0)
+    nbytes = 0 if dev_flush is None else dev_flush.numel() * dev_flush.element_size()
+    _check(load().mx_step_timed(sys, int(n_steps), _dptr(dev_flush), nbytes, _hptr(ms), _hptr(cnt),
+                                ctypes.byref(tot)), "mx_step_timed")
     return dict(zip(KERNELS, ms.tolist())), dict(zip(KERNELS, cnt.tolist())), tot.value
 
 

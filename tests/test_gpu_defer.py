@@ -104,9 +104,10 @@ def test_profiled_path_defers_too():
     # side-stream launch each), the last 5 slots wait for a reader; side
     # launches are counted once they have completed, at the latest by the
     # settling call
-    assert cnt["k_jump_drift"] == 20 and 2 <= cnt["k_catchup"] <= 4
+    assert cnt["k_jump_drift"] == 20 and cnt["k_catchup"] == 2
     ms0, cnt0, _ = mx.mx_step_profiled(s.h, 0)
-    assert cnt["k_catchup"] + cnt0["k_catchup"] == 5 and cnt0["k_jump_drift"] == 0
+    assert cnt0["k_catchup"] == 1 and cnt0["k_jump_drift"] == 0
+    assert cnt["k_catchup_side"] + cnt0["k_catchup_side"] == 2
     a = s.state(mx.MX_COORD_DH)
     s.close()
     ref = _run(w, 0, [20])
@@ -136,3 +137,15 @@ def test_window_limits():
     mx.mx_set_defer_window(s.h, max_window)
     s.step(max_window + 3)
     s.close()
+
+
+def test_timed_path_with_flush_matches_step():
+    w = W.gas_4core_100k(nsmall=30_000)
+    flush = torch.empty(8 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    s = mx.System(w)
+    ms, cnt, tot = mx.mx_step_timed(s.h, 25, flush)
+    ms0, cnt0, tot0 = mx.mx_step_timed(s.h, 0, flush)
+    a = s.state(mx.MX_COORD_DH)
+    s.close()
+    assert tot > 0 and cnt["k_jump_drift"] == 25 and cnt["k_jump_kick"] == 26
+    assert np.array_equal(a, _run(w, 32, [25])[0])
