@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and adjoint legs")
     ap.add_argument("--ensemble-steps", type=int, default=10)
+    ap.add_argument("--tiling", default=None,
+                    help="tile,order to override the autotuner (order 2: tiles per SM)")
     return ap.parse_args()
 
 
@@ -372,6 +374,8 @@ def run_mx(args):
     st = torch.cuda.current_stream()
     w = W.make(WORKLOAD, seed=rank_seed(rank))
     sysm = mx.System(w, stream=st.cuda_stream)
+    if args.tiling:
+        mx.mx_set_tiling(sysm.h, *[int(v) for v in args.tiling.split(",")])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
 
     def barrier():
@@ -399,6 +403,7 @@ def run_mx(args):
         total_ms += tot
     torch.cuda.synchronize()
     dwin, dmax, _, _ = mx.mx_defer_stats(sysm.h)
+    tiling = mx.mx_tiling(sysm.h)
     barrier()
     clk = clocks.stop()
     t_max = reduce_max(total_ms, "cuda")
@@ -457,6 +462,8 @@ def run_mx(args):
                        "l2": "flushed before every timed step (256 MiB write, outside the step spans)",
                        "path": "mx_step_timed: all steps in one call, launch by launch with CUDA events",
                        "defer_window": dwin,
+                       "tiling": {"tile": tiling[0], "order": tiling[1],
+                                  "meaning": "order 2: tiles per SM (balanced); else targets per block"},
                        "deferred": ("planetesimals whose encounter outlasts one Bulirsch-Stoer macro "
                                     "sub-step are replayed by k_catchup at the end of each window of "
                                     f"{dwin} steps; bodies still in a long encounter continue on a "

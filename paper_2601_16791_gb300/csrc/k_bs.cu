@@ -903,11 +903,14 @@ __device__ void pack_tail(const Dev& d, int w, unsigned gmask, int base, int lan
       return;
     }
   }
-  // hand over to the spread phase
-  int slot = 0;
-  if (lane == base) slot = atomicAdd(d.cont_count, 1);
-  slot = __shfl_sync(gmask, slot, base);
-  if (slot >= d.cont_cap) {   // list full: finish here
+  // hand over to the spread phase; with deferral on (no spread launches) a
+  // big-body group, or a group the record banks had no room for, finishes here
+  int slot = d.cont_cap;
+  if (!d.defer) {
+    if (lane == base) slot = atomicAdd(d.cont_count, 1);
+    slot = __shfl_sync(gmask, slot, base);
+  }
+  if (slot >= d.cont_cap) {   // list full or no spread phase: finish here
     const int r2 = finish_here(g);
     if (lane == base) {
       if (r2 < 0) atomicOr(d.status, ST_BS);
@@ -930,7 +933,7 @@ __device__ void pack_tail(const Dev& d, int w, unsigned gmask, int base, int lan
 }
 
 template <int NB>
-__device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int lane) {
+__device__ __noinline__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int lane) {
   const int o0 = d.work_off[w];
   const SysDev& S = d.sys[d.work_sys[w]];
   double mu[NB];
@@ -952,32 +955,52 @@ __device__ void pack_group(const Dev& d, int w, unsigned gmask, int base, int la
   });
 }
 
+__device__ void pack_two(const Dev& d, int w, int lane);
+__device__ __noinline__ void thread_group(const Dev& d, int w);
+
 // Two-body groups, one per warp (term lanes, one candidate).
 __global__ void __launch_bounds__(32) k_bs_pack2(Dev d) {
   const int W = *d.work_count;
+  for (int w = blockIdx.x; w < W; w += gridDim.x)
+    if (d.work_off[w + 1] - d.work_off[w] == 2) pack_two(d, w, threadIdx.x);
+}
+
+// Every group, one per warp, in one launch: two bodies on term lanes, three
+// or four on the lane integrator (eight lanes), more on one thread.  Used
+// with deferral on, where nothing is handed to a spread phase.
+__global__ void __launch_bounds__(32) k_bs_all(Dev d) {
+  const int W = *d.work_count;
   const int lane = threadIdx.x;
   for (int w = blockIdx.x; w < W; w += gridDim.x) {
-    const int o0 = d.work_off[w];
-    if (d.work_off[w + 1] - o0 != 2) continue;
-    const SysDev& S = d.sys[d.work_sys[w]];
-    double mu[2];
-    MemberK K[2];
-    load_members<2>(d, S, o0, mu, K);
-    const Bs2Term t = bs2_term(lane & 3, S.mu0, mu, K);
-    GroupRun<2> g;
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-      for (int c = 0; c < 6; ++c) g.Y[c][m] = d.xv0[(size_t)c * d.N + d.work_mem[o0 + m]];
-    g.rem = S.h;
-    g.H = S.h;
-    g.nsub = 0;
-    const int r = bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, d.defer ? 1 : kPackRounds, g,
-                                nullptr, nullptr);
-    pack_tail<2>(d, w, 0xffffffffu, 0, lane, o0, r, g, [&](GroupRun<2>& gg) {
-      return bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, 1 << 30, gg, nullptr, nullptr);
-    });
+    const int nb = d.work_off[w + 1] - d.work_off[w];
+    if (nb == 2) pack_two(d, w, lane);
+    else if (nb == 3) { if (lane < 8) pack_group<3>(d, w, 0xffu, 0, lane); }
+    else if (nb == 4) { if (lane < 8) pack_group<4>(d, w, 0xffu, 0, lane); }
+    else if (nb > kLaneMaxNB && lane == 0) thread_group(d, w);
+    __syncwarp();
   }
+}
+
+__device__ void pack_two(const Dev& d, int w, int lane) {
+  const int o0 = d.work_off[w];
+  const SysDev& S = d.sys[d.work_sys[w]];
+  double mu[2];
+  MemberK K[2];
+  load_members<2>(d, S, o0, mu, K);
+  const Bs2Term t = bs2_term(lane & 3, S.mu0, mu, K);
+  GroupRun<2> g;
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g.Y[c][m] = d.xv0[(size_t)c * d.N + d.work_mem[o0 + m]];
+  g.rem = S.h;
+  g.H = S.h;
+  g.nsub = 0;
+  const int r = bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, d.defer ? 1 : kPackRounds, g,
+                              nullptr, nullptr);
+  pack_tail<2>(d, w, 0xffffffffu, 0, lane, o0, r, g, [&](GroupRun<2>& gg) {
+    return bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, 1 << 30, gg, nullptr, nullptr);
+  });
 }
 
 // Two-body groups handed over by k_bs_pack2: one per block of four warps,
@@ -1083,34 +1106,36 @@ __global__ void __launch_bounds__(32) k_bs_spread(Dev d) {
   }
 }
 
+// A group of more than kLaneMaxNB bodies on one thread.
+__device__ __noinline__ void thread_group(const Dev& d, int w) {
+  const int N = d.N;
+  const int o0 = d.work_off[w];
+  const int nb = min(d.work_off[w + 1] - o0, kMaxGroup);   // the builder caps groups
+  GroupState G;
+  G.nb = nb;
+  const SysDev& S = d.sys[d.work_sys[w]];
+  double Y[6][kMaxGroup];
+  for (int m = 0; m < nb; ++m) {
+    const int g = d.work_mem[o0 + m];
+    const int l = g - S.off;
+    G.mu[m] = (l < S.nbig) ? d.bmu[S.boff + l] : 0.0;
+    G.rc[m] = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
+    for (int c = 0; c < 6; ++c) Y[c][m] = d.xv0[(size_t)c * N + g];
+  }
+  int nsub = 0;
+  if (!bs_integrate(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub)) atomicOr(d.status, ST_BS);
+  d.work_nsub[w] = nsub;
+  for (int m = d.work_wfrom[w]; m < nb; ++m) {
+    const int g = d.work_mem[o0 + m];
+    for (int c = 0; c < 6; ++c) d.xv[(size_t)c * N + g] = Y[c][m];
+  }
+}
+
 // One thread per work item with more than kLaneMaxNB bodies, grid-stride.
 __global__ void __launch_bounds__(32) k_bs(Dev d) {
   const int W = *d.work_count;
-  const int N = d.N;
-  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x) {
-    const int o0 = d.work_off[w];
-    const int nb = min(d.work_off[w + 1] - o0, kMaxGroup);   // the builder caps groups
-    if (nb <= kLaneMaxNB) continue;
-    GroupState G;
-    G.nb = nb;
-    const SysDev& S = d.sys[d.work_sys[w]];
-    double Y[6][kMaxGroup];
-    for (int m = 0; m < nb; ++m) {
-      const int g = d.work_mem[o0 + m];
-      const int l = g - S.off;
-      G.mu[m] = (l < S.nbig) ? d.bmu[S.boff + l] : 0.0;
-      G.rc[m] = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
-      for (int c = 0; c < 6; ++c) Y[c][m] = d.xv0[(size_t)c * N + g];
-    }
-    int nsub = 0;
-    if (!bs_integrate(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub))
-      atomicOr(d.status, ST_BS);
-    d.work_nsub[w] = nsub;
-    for (int m = d.work_wfrom[w]; m < nb; ++m) {
-      const int g = d.work_mem[o0 + m];
-      for (int c = 0; c < 6; ++c) d.xv[(size_t)c * N + g] = Y[c][m];
-    }
-  }
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x)
+    if (d.work_off[w + 1] - d.work_off[w] > kLaneMaxNB) thread_group(d, w);
 }
 
 // ----------------------------------------------- deferred planetesimals
@@ -1424,11 +1449,12 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
   const double kick_h = 0.5 * S.h;
   const double hp0 = P2[0] * S.inv_mu0, hp1 = P2[1] * S.inv_mu0, hp2 = P2[2] * S.inv_mu0;
   const double rp = S.gas_on ? d.rp_cm[j] : 0.0, kd = S.gas_on ? d.kdrag[j] : 0.0;
+  const GasAt gq = S.gas_on ? gas_at(S, x, y) : GasAt{false, 0.0, 0.0, 0.0};
   for (int kk = 0; kk < nk; ++kk) {
     double a[3] = {0.0, 0.0, 0.0};
     if (S.gas_on) {
       int kout = 0;
-      gas_drag(S, x, y, z, u + hp0, v + hp1, w + hp2, rp, kd, a, -1, &kout);
+      gas_drag_at(S, gq, x, y, u + hp0, v + hp1, w + hp2, rp, kd, a, -1, &kout);
     }
     u = fma(kick_h, ax + a[0], u);
     v = fma(kick_h, ay + a[1], v);
@@ -1581,6 +1607,10 @@ void launch_groups(const Dev& d, cudaStream_t st) { k_groups<<<1, 1024, 0, st>>>
 
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
   // (a group has at least two members: one big body and the body it meets)
+  if (d.defer) {   // no spread phase: one launch
+    k_bs_all<<<4 * nblocks, 32, 0, st>>>(d);
+    return;
+  }
   cudaMemsetAsync(d.cont_count, 0, sizeof(int), st);
   k_bs_pack2<<<4 * nblocks, 32, 0, st>>>(d);
   k_bs_pack<3, 4><<<4 * nblocks, 32, 0, st>>>(d);

@@ -158,6 +158,8 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
   const double hp0 = P[0] * S.inv_mu0, hp1 = P[1] * S.inv_mu0, hp2 = P[2] * S.inv_mu0;
   const double rp = drag ? d.rp_cm[j] : 0.0, kd = drag ? d.kdrag[j] : 0.0;
   const int kbase = d.kmode ? d.kick_ctr[1] : 0;
+  // the gas at the (fixed) position, shared by the launch's half kicks
+  const GasAt gq = drag ? gas_at(S, x, y) : GasAt{false, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int kk = 0; kk < NKICK; ++kk) {
     double a[3] = {0.0, 0.0, 0.0};
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
       const size_t word = (size_t)kidx * d.kwords + (j >> 5);
       int kin = -1, kout = 0;
       if (kuse && d.kmode == 2) kin = (d.kbits[word] >> (j & 31)) & 1u;
-      gas_drag(S, x, y, z, u + hp0, v + hp1, w + hp2, rp, kd, a, kin, &kout);
+      gas_drag_at(S, gq, x, y, u + hp0, v + hp1, w + hp2, rp, kd, a, kin, &kout);
       if (kuse && d.kmode == 1 && kout) atomicOr(&d.kbits[word], 1u << (j & 31));
     }
     u = fma(kick_h, ax + a[0], u);

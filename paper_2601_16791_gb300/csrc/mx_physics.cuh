@@ -6,30 +6,32 @@
 
 namespace mx {
 
-// Drag acceleration (Eq. 3) of one planetesimal at heliocentric position
-// (x, y, z) moving with heliocentric velocity (u, v, w).  Quantities follow
-// Sec. 3.1: Sigma (Eq. 1, normalised at 1 AU), rho_g (Eq. 4) at the midplane,
-// v_g = v_k sqrt(1 - 2 eta) (Eqs. 5, 6), C_D (Eq. 7) from Re and Ma.
-// kd = 3 / (8 r_p[AU] rho_p); rp_cm = r_p in cm.
-// kb_in: -1 takes the k of Eq. 7 from Re; 0 or 1 forces k = 0.4 or 0.2 (a
-// recorded branch being replayed).  *kb_out receives the branch used.
-__device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, double z, double u,
-                                         double v, double w, double rp_cm, double kd, double* a,
-                                         int kb_in, int* kb_out) {
-  a[0] = a[1] = a[2] = 0.0;
-  *kb_out = 0;
+// The gas at a planetesimal's heliocentric position (Sec. 3.1): rho_g
+// (Eq. 4, midplane), 1/c_s and the gas velocity factor g (v_gas = g (-y, x, 0),
+// v_g = v_k sqrt(1 - 2 eta), Eqs. 5, 6).  in_gas = false inside the inner
+// edge (Sec. 3.1.1).  It depends on the position only, so the two half kicks
+// of one launch share it.
+struct GasAt {
+  bool in_gas;
+  double rho, inv_cs, g;
+};
+
+__device__ __forceinline__ GasAt gas_at(const SysDev& S, double x, double y) {
+  GasAt q;
+  q.in_gas = false;
+  q.rho = q.inv_cs = q.g = 0.0;
   const double R2 = fma(x, x, y * y);
   const double iR = rsqrt_d(R2);             // 1/R
   const double R = R2 * iR;
-  if (R < S.r_in) return;                    // no gas inside the inner edge (Sec. 3.1.1)
+  if (R < S.r_in) return q;                  // no gas inside the inner edge (Sec. 3.1.1)
   double sigma, rmh, rcs, reta, inv_cs;      // Sigma, R^-(1+f), R^(f-1/2), R^(2f), 1/c_s
   const double ih = rsqrt_d(R);              // R^-1/2
   if (S.flare_quarter) {
-    const double q = rsqrt_d(ih);            // R^1/4
-    rcs = q * ih;                            // R^-1/4
+    const double qq = rsqrt_d(ih);           // R^1/4
+    rcs = qq * ih;                           // R^-1/4
     rmh = iR * rcs;                          // R^-5/4
     reta = R * ih;                           // R^1/2
-    inv_cs = q * S.inv_c_cs;
+    inv_cs = qq * S.inv_c_cs;
   } else {
     const double lr = log(R);
     rcs = exp((S.flare - 0.5) * lr);
@@ -40,19 +42,36 @@ __device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, do
   if (S.gamma_one) sigma = S.sigma1 * iR;
   else sigma = S.sigma1 * exp(-S.gamma * log(R));
   if (!S.rc_inf) sigma *= exp(-pow(R * S.inv_rc, 2.0 - S.gamma));
-  const double rho = S.c_rho * sigma * rmh;
+  q.rho = S.c_rho * sigma * rmh;
   const double vk = S.sqrt_mu0 * ih;
   const double t = fma(-2.0 * S.c_eta, reta, 1.0);   // 1 - 2 eta
   const double vg = vk * (t * rsqrt_d(t));
-  const double g = vg * iR;                  // gas velocity = g * (-y, x, 0)
-  const double du = fma(g, y, u);
-  const double dv = fma(-g, x, v);
+  q.g = vg * iR;                             // gas velocity = g * (-y, x, 0)
+  q.inv_cs = inv_cs;
+  q.in_gas = true;
+  return q;
+}
+
+// Drag acceleration (Eq. 3) of one planetesimal at heliocentric position
+// (x, y, .) with the gas there (gas_at), moving with heliocentric velocity
+// (u, v, w).  C_D (Eq. 7) from Re and Ma.
+// kd = 3 / (8 r_p[AU] rho_p); rp_cm = r_p in cm.
+// kb_in: -1 takes the k of Eq. 7 from Re; 0 or 1 forces k = 0.4 or 0.2 (a
+// recorded branch being replayed).  *kb_out receives the branch used.
+__device__ __forceinline__ void gas_drag_at(const SysDev& S, const GasAt& q, double x, double y,
+                                            double u, double v, double w, double rp_cm, double kd,
+                                            double* a, int kb_in, int* kb_out) {
+  a[0] = a[1] = a[2] = 0.0;
+  *kb_out = 0;
+  if (!q.in_gas) return;
+  const double du = fma(q.g, y, u);
+  const double dv = fma(-q.g, x, v);
   const double dw = w;
   const double dv2 = fma(du, du, fma(dv, dv, dw * dw));
   if (dv2 == 0.0) return;
   const double dvm = dv2 * rsqrt_d(dv2);
-  const double Ma = dvm * inv_cs;
-  const double Re = S.c_re * rp_cm * Ma * rho;
+  const double Ma = dvm * q.inv_cs;
+  const double Re = S.c_re * rp_cm * Ma * q.rho;
   const int kb = (kb_in >= 0) ? kb_in : (Re < 1e5 ? 0 : 1);
   *kb_out = kb;
   const double k = kb ? 0.2 : 0.4;
@@ -65,10 +84,22 @@ __device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, do
   const double first = D * A * r;           // = D / den1
   const double second = fma(2.0, Ma, 1.6 * k) * den1 * r;
   const double cd = (S.cd_mode == 1) ? fma(first, first, second) : first + second;
-  const double coef = S.cd_scale * cd * kd * rho * dvm;
+  const double coef = S.cd_scale * cd * kd * q.rho * dvm;
   a[0] = -coef * du;
   a[1] = -coef * dv;
   a[2] = -coef * dw;
+}
+
+// Drag acceleration (Eq. 3) of one planetesimal at heliocentric position
+// (x, y, z) moving with heliocentric velocity (u, v, w): gas_at, then
+// gas_drag_at.  Quantities follow Sec. 3.1: Sigma (Eq. 1, normalised at
+// 1 AU), rho_g (Eq. 4) at the midplane, v_g (Eqs. 5, 6), C_D (Eq. 7).
+__device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, double z, double u,
+                                         double v, double w, double rp_cm, double kd, double* a,
+                                         int kb_in, int* kb_out) {
+  (void)z;
+  const GasAt q = gas_at(S, x, y);
+  gas_drag_at(S, q, x, y, u, v, w, rp_cm, kd, a, kb_in, kb_out);
 }
 
 // K(s)/s^3 times mu for one pair, accumulated into (ax, ay, az) as -f * d
