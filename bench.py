@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and adjoint legs")
     ap.add_argument("--ensemble-steps", type=int, default=10)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="another named workload (informational; the metric is quoted on the default)")
     ap.add_argument("--tiling", default=None,
                     help="tile,order to override the autotuner (order 2: tiles per SM)")
     return ap.parse_args()
@@ -372,7 +374,7 @@ def run_mx(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     st = torch.cuda.current_stream()
-    w = W.make(WORKLOAD, seed=rank_seed(rank))
+    w = W.make(args.workload, seed=rank_seed(rank))
     sysm = mx.System(w, stream=st.cuda_stream)
     if args.tiling:
         mx.mx_set_tiling(sysm.h, *[int(v) for v in args.tiling.split(",")])
@@ -457,7 +459,9 @@ def run_mx(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "n_bodies": w.n,
+            "config": {"workload": args.workload,
+                       "description": WORKLOAD_TEXT if args.workload == WORKLOAD else args.workload,
+                       "n_bodies": w.n,
                        "per_rank_seed": "1 + rank",
                        "l2": "flushed before every timed step (256 MiB write, outside the step spans)",
                        "path": "mx_step_timed: all steps in one call, launch by launch with CUDA events",

@@ -144,7 +144,9 @@ mx_status mx_set_tiling(mx_system* s, int tile, int order);
  * or earlier, before any call that reads or replaces the state, changes the
  * gas parameters or the branch mode, or reads the encounter log or pair list.
  * The state every such call sees is the one the direct path gives, bit for
- * bit.  Big-body groups are never deferred.  Recording or replaying drag
+ * bit.  Big-body groups are never deferred, nor are planetesimals of systems
+ * with more than 64 big bodies (a replay sums every big body's gravity on one
+ * lane, in the direct path's order).  Recording or replaying drag
  * branches (mx_kick_branches) turns deferral off.  A catch-up's device errors
  * are reported by the call that launched it.
  *

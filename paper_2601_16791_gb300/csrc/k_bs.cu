@@ -9,7 +9,9 @@
 // planetesimal forms a test-particle group with the big groups of the bigs it
 // meets and only its own state is taken from it (it has no mass, so the big
 // copies follow the same motion as in their own group).  The list is built by
-// one block from the sorted pair keys, so it is the same on every run.
+// one block from the pair keys, which come as one contiguous run per target
+// with the big bodies ascending; the runs' order varies, but no group's
+// members or arithmetic depend on it.
 //
 // Integrator: Stoermer's rule for x'' = a(x) with n_k = 2k sub-steps
 // (k = 1..8), Aitken-Neville extrapolation in (H/n)^2, error = max over
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
   __shared__ int comp_nodes[2 * kMaxBigPairs];
   __shared__ int sa[1024], sb[1024];
   __shared__ int s_nbb, s_nnodes, s_ncomp, s_bw, s_bm, s_bad;
+  __shared__ unsigned long long bbk[kMaxBigPairs];   // the big-big pairs
   const int count = *d.pair_count;
   if (count > d.pair_cap) {
     if (threadIdx.x == 0) atomicOr(d.status, ST_PAIR_OVF);
@@ -118,12 +121,17 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
   if (n == 0) return;
   const unsigned long long* keys = d.keys;
   if (threadIdx.x == 0) {
-    s_nbb = n;
+    s_nbb = 0;
     s_bad = 0;
   }
   __syncthreads();
-  for (int p = threadIdx.x; p < n; p += blockDim.x)
-    if (key_small(keys[p]) && (p == 0 || !key_small(keys[p - 1]))) s_nbb = p;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const unsigned long long k = keys[p];
+    if (!key_small(k)) {
+      const int q = atomicAdd(&s_nbb, 1);
+      if (q < kMaxBigPairs) bbk[q] = k;
+    }
+  }
   __syncthreads();
   const int nbb = s_nbb;
   if (nbb > kMaxBigPairs) {
@@ -134,7 +142,7 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
   if (threadIdx.x == 0) {
     int nn = 0;
     for (int p = 0; p < nbb; ++p) {
-      const int ab[2] = {key_i(keys[p]), key_j(keys[p])};
+      const int ab[2] = {key_i(bbk[p]), key_j(bbk[p])};
       for (int q = 0; q < 2; ++q) {
         const int g = ab[q];
         int e = nn;
@@ -164,8 +172,8 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
       return e;
     };
     for (int p = 0; p < nbb; ++p) {
-      const int a = root(find_idx(key_i(keys[p])));
-      const int b = root(find_idx(key_j(keys[p])));
+      const int a = root(find_idx(key_i(bbk[p])));
+      const int b = root(find_idx(key_j(bbk[p])));
       if (a != b) parent[max(a, b)] = min(a, b);
     }
     // components numbered in order of their smallest member
@@ -216,9 +224,9 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
     return;
   }
   // ---- test-particle groups: one per run of pairs with the same small body
-  for (int cs = nbb; cs < n; cs += blockDim.x) {
+  for (int cs = 0; cs < n; cs += blockDim.x) {
     const int p = cs + threadIdx.x;
-    const bool start = p < n && (p == nbb || key_j(keys[p]) != key_j(keys[p - 1]));
+    const bool start = p < n && key_small(keys[p]) && (p == 0 || key_j(keys[p]) != key_j(keys[p - 1]));
     int mem[kMaxGroup];
     int mc = 0;
     if (start) {
@@ -872,7 +880,7 @@ __device__ void pack_tail(const Dev& d, int w, unsigned gmask, int base, int lan
   }
   // still running.  A test-particle group (only the planetesimal's state is
   // kept) leaves the step: the body is deferred to the window's catch-up.
-  if (d.defer && d.work_wfrom[w] == NB - 1) {
+  if (d.defer && d.work_wfrom[w] == NB - 1 && d.sys[d.work_sys[w]].nbig <= kDeferMaxBig) {
     const int hs = *d.hstep;
     int rr = d.dcap;
     if (lane == base && hs < d.hist_cap) rr = atomicAdd(&d.rcount[0], 1);

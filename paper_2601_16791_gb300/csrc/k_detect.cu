@@ -7,8 +7,10 @@
 // conservative FP32 screen discards far pairs (mx_encounter.cuh); surviving
 // pairs are decided in FP64 with the closed-form minimum of the cubic Hermite
 // interpolant of the squared separation.
-// Flagged pairs are appended with one atomic per warp (ballot compaction);
-// the pair order is then fixed by sorting the 64-bit keys.
+// Each target keeps its flagged big bodies (ascending) and writes them as one
+// contiguous run, with one atomic per warp; runs of different targets come in
+// any order.  The step groups runs as they are; callers that want the pairs
+// in order sort the keys (k_sort_keys).
 #include "mx_common.cuh"
 #include "mx_encounter.cuh"
 #include "mx_kernels.h"
@@ -23,10 +25,12 @@ struct DetSmem {
 };
 
 // xv0, xv1: 6 x N endpoint states; keys/count/cap: pair output.
+// runs = 1 (the step): a target with more than kMaxGroup flagged big bodies
+// would make a group larger than kMaxGroup, reported as ST_GROUP.
 __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, const double* xv1,
                                                      unsigned char* flags,
                                                      unsigned long long* keys, int* count,
-                                                     int cap) {
+                                                     int cap, int runs) {
   __shared__ DetSmem sm;
   const Tile t = d.tiles[blockIdx.x];
   const SysDev& S = d.sys[t.sys];
@@ -50,6 +54,30 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
   }
   if (act && jbig) rcj = d.brc[S.boff + jl];
   const float rcjf = (float)rcj;
+  int hits[kMaxGroup];
+  int nh = 0;
+  const unsigned long long tag = ((unsigned long long)(jbig ? 0u : 1u) << 63) |
+                                 ((unsigned long long)(unsigned)j << 32);
+  // writes the buffered hits of the lanes with `mine` set, each lane's as one
+  // run (the warp takes its space with one atomic); every lane calls it
+  auto flush = [&](bool mine) {
+    const int own = mine ? nh : 0;
+    int inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    if (total == 0) return;
+    int base = 0;
+    if (lane == 31) base = atomicAdd(count, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    const int start = base + inc - own;
+    for (int e = 0; e < own; ++e)
+      if (start + e < cap) keys[start + e] = tag | (unsigned)(S.off + hits[e]);
+    if (mine) nh = 0;
+  };
   for (int c0 = 0; c0 < S.nbig; c0 += blockDim.x) {
     const int cn = min((int)blockDim.x, S.nbig - c0);
     __syncthreads();
@@ -88,28 +116,31 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
           hit = encounter_fp64(a0, b0, a1, b1, h, rc2);
         }
       }
-      const unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(count, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (hit) {
-          const int pos = base + __popc(m & ((1u << lane) - 1u));
-          const int gi = S.off + il;
-          if (pos < cap)
-            keys[pos] = ((unsigned long long)(jbig ? 0u : 1u) << 63) |
-                        ((unsigned long long)(unsigned)j << 32) | (unsigned)gi;
-          flags[gi] = 1;
-          flags[j] = 1;
-          if (d.ever) {
-            d.ever[gi] = 1;
-            d.ever[j] = 1;
-          }
+      if (hit) {
+        const int gi = S.off + il;
+        flags[gi] = 1;
+        flags[j] = 1;
+        if (d.ever) {
+          d.ever[gi] = 1;
+          d.ever[j] = 1;
         }
+        if (nh == kMaxGroup) {   // a run split in two: only past the group limit
+          if (runs) atomicOr(d.status, ST_GROUP);
+          nh = -1;               // marks the flush below as due
+        } else {
+          hits[nh++] = il;
+        }
+      }
+      // a full buffer is written out (every lane of the warp takes part)
+      if (__any_sync(0xffffffffu, nh < 0)) {
+        const bool redo = nh < 0;
+        if (redo) nh = kMaxGroup;
+        flush(redo);
+        if (redo) hits[nh++] = il;
       }
     }
   }
+  flush(true);
 }
 
 // Sorts min(*count, cap) keys ascending in one block (bitonic; shared memory
@@ -176,8 +207,8 @@ void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int 
 }
 
 void launch_detect(const Dev& d, const double* xv0, const double* xv1, unsigned char* flags,
-                   unsigned long long* keys, int* count, int cap, cudaStream_t st) {
-  k_detect<<<d.ntiles, d.tile, 0, st>>>(d, xv0, xv1, flags, keys, count, cap);
+                   unsigned long long* keys, int* count, int cap, int runs, cudaStream_t st) {
+  k_detect<<<d.ntiles, d.tile, 0, st>>>(d, xv0, xv1, flags, keys, count, cap, runs);
 }
 
 void launch_sort_keys(unsigned long long* keys, const int* count, int cap, int swap_ij,

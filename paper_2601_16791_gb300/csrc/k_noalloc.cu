@@ -105,7 +105,7 @@ extern "C" mx_status mx_detect_encounters_noalloc(const mx_params* p, int n_big,
   int* count = reinterpret_cast<int*>(scratch + kOffCount);
   if (cudaMemsetAsync(dev_flags, 0, (size_t)n, st) != cudaSuccess) return MX_ERR_CUDA;
   k_noalloc_setup<<<32, 256, 0, st>>>(scratch, sys, n);
-  mx::launch_detect(d, dev_xv0, dev_xv1, dev_flags, keys, count, MX_NOALLOC_MAX_PAIRS, st);
+  mx::launch_detect(d, dev_xv0, dev_xv1, dev_flags, keys, count, MX_NOALLOC_MAX_PAIRS, 0, st);
   mx::launch_sort_keys(keys, count, MX_NOALLOC_MAX_PAIRS, 1, st);
   if (cap > 0) mx::launch_keys_to_pairs(keys, count, cap < MX_NOALLOC_MAX_PAIRS ? cap : MX_NOALLOC_MAX_PAIRS, dev_pairs, st);
   int found = 0;

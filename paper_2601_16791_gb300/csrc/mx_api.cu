@@ -198,8 +198,7 @@ void enqueue_head(mx_system* s, cudaStream_t st) {
 void enqueue_step(mx_system* s, int last, cudaStream_t st) {
   mx::launch_jump_drift(s->d, 0.5, st);
   mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count,
-                    s->d.pair_cap, st);
-  mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st);
+                    s->d.pair_cap, 1, st);
   mx::launch_groups(s->d, st);
   mx::launch_bs(s->d, s->bs_blocks, st);
   mx::launch_prep(s->d, 0.5, last ? 1 : 2, st);
@@ -929,9 +928,8 @@ mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_byte
     if (e == cudaSuccess) e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5, st); });
     if (e == cudaSuccess)
       e = timed(MX_K_DETECT, [&] {
-        mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count, s->d.pair_cap, st);
+        mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count, s->d.pair_cap, 1, st);
       });
-    if (e == cudaSuccess) e = timed(MX_K_SORT, [&] { mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 0, st); });
     if (e == cudaSuccess) e = timed(MX_K_GROUPS, [&] { mx::launch_groups(s->d, st); });
     if (e == cudaSuccess) e = timed(MX_K_BS, [&] { mx::launch_bs(s->d, s->bs_blocks, st); });
     if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, last_step ? 1 : 2, st); });
@@ -1059,7 +1057,7 @@ mx_status mx_detect_encounters(mx_system* s, const double* dev_xv0, const double
   dd.ever = nullptr;        // caller-supplied states do not enter the encounter log
   dd.bb_count = nullptr;
   dd.defer = 0;
-  mx::launch_detect(dd, dev_xv0, dev_xv1, flags, s->d.keys, s->d.pair_count, s->d.pair_cap, s->st);
+  mx::launch_detect(dd, dev_xv0, dev_xv1, flags, s->d.keys, s->d.pair_count, s->d.pair_cap, 0, s->st);
   mx::launch_sort_keys(s->d.keys, s->d.pair_count, s->d.pair_cap, 1, s->st);
   if (dev_pairs && cap > 0)
     mx::launch_keys_to_pairs(s->d.keys, s->d.pair_count, std::min(cap, s->d.pair_cap), dev_pairs, s->st);

@@ -24,6 +24,11 @@ constexpr int kBigChunk = 512;    // big bodies staged in shared memory per pass
 constexpr int kMaxGroup = 16;     // bodies per Bulirsch-Stoer group (MX_MAX_GROUP)
 constexpr int kBsRows = 8;        // extrapolation rows: n_k = 2, 4, ..., 16
 constexpr int kMaxBigPairs = 512; // big-big encounter pairs handled per step
+// Planetesimals are deferred only in systems with at most this many big
+// bodies: a replayed step sums the gravity of every big body on one lane (in
+// the direct path's order), so with many big bodies a replay costs more than
+// the encounter it moves off the step.
+constexpr int kDeferMaxBig = 64;
 
 // Device status bits, OR-ed by kernels and turned into mx_status on the host.
 enum : unsigned {

@@ -28,7 +28,7 @@ void launch_drift_buf(double* xv, int n, double mu, double h, int maxit, unsigne
 
 // k_detect.cu
 void launch_detect(const Dev& d, const double* xv0, const double* xv1, unsigned char* flags,
-                   unsigned long long* keys, int* count, int cap, cudaStream_t st);
+                   unsigned long long* keys, int* count, int cap, int runs, cudaStream_t st);
 void launch_sort_keys(unsigned long long* keys, const int* count, int cap, int swap_ij,
                       cudaStream_t st);
 void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int cap, int* pairs,

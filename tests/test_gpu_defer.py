@@ -71,11 +71,20 @@ def test_windows_and_call_boundaries(window):
 
 
 def test_many_big_bodies():
-    # 200 massive embryos + massless planetesimals (the semi-active layout),
-    # so the replayed kick and detection loop over many sources
+    # 40 giant cores (up to 64 big bodies defer), so the replayed kick and
+    # detection loop over many sources and groups often have several bigs
+    w = W.gas_4core_100k(nbig=40, nsmall=60_000)
+    direct = _run(w, 0, [30])
+    deferred = _run(w, 8, [30])
+    assert deferred[5][2] > 0
+    _same(direct, deferred)
+
+
+def test_no_deferral_beyond_64_big_bodies():
     w = W.semiactive_2000big_200k(nbig=200, nsmall=20_000)
     direct = _run(w, 0, [30])
     deferred = _run(w, 8, [30])
+    assert deferred[5][2] == 0
     _same(direct, deferred)
 
 
