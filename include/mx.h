@@ -203,10 +203,13 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
                            double* total_ms);
 
 /*
- * mx_step_timed -- mx_step_profiled with a cache flush: before every step the
- * device buffer dev_flush (flush_bytes bytes, e.g. more than the L2 cache;
+ * mx_step_timed -- the CUDA graphs of mx_step, in variants with an event
+ * between kernels, one step at a time, with a cache flush: before every step
+ * the device buffer dev_flush (flush_bytes bytes, e.g. more than the L2 cache;
  * caller-owned) is overwritten on the system's stream, outside the steps'
- * timed spans.  flush_bytes = 0 means no flush.
+ * timed spans; after every step the host waits for it and reads its events.
+ * Outputs as mx_step_profiled.  flush_bytes = 0 means no flush; n_steps = 0
+ * runs the pending catch-up, timed.
  */
 mx_status mx_step_timed(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
                         double* kernel_ms, int* launches, double* total_ms);

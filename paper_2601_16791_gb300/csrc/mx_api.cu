@@ -118,6 +118,9 @@ struct mx_system {
   int* h_count = nullptr;         // pinned
   std::vector<void*> allocs;
   cudaGraphExec_t g_head = nullptr, g_mid = nullptr, g_last = nullptr;
+  cudaGraphExec_t gt_head = nullptr, gt_mid = nullptr, gt_last = nullptr;   // timed variants
+  cudaEvent_t mk_head[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t mk_step[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   long long step = 0;
   int bs_blocks = 0;
   int catch_blocks = 0;
@@ -190,20 +193,42 @@ mx_status sync_status(mx_system* s) {
 
 // The device work of one interior step, or the last step of a call
 // (one half kick at its end), or the leading half kick.
-void enqueue_head(mx_system* s, cudaStream_t st) {
+// With `marks` (the timed graphs of mx_step_timed), an event is recorded
+// before the first launch and after each one (as graph nodes: external
+// records, so that launching the graph records them).
+void mark_event(cudaEvent_t e, cudaStream_t st) { cudaEventRecordWithFlags(e, st, cudaEventRecordExternal); }
+
+void enqueue_head(mx_system* s, cudaStream_t st, cudaEvent_t* marks) {
+  if (marks) mark_event(marks[0], st);
   mx::launch_prep(s->d, 0.0, 1, st);
+  if (marks) mark_event(marks[1], st);
   mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st);
+  if (marks) mark_event(marks[2], st);
 }
 
-void enqueue_step(mx_system* s, int last, cudaStream_t st) {
+void enqueue_step(mx_system* s, int last, cudaStream_t st, cudaEvent_t* marks) {
+  int m = 0;
+  auto mark = [&] {
+    if (marks) mark_event(marks[m++], st);
+  };
+  mark();
   mx::launch_jump_drift(s->d, 0.5, st);
+  mark();
   mx::launch_detect(s->d, s->d.xv0, s->d.xv, s->d.flags, s->d.keys, s->d.pair_count,
                     s->d.pair_cap, 1, st);
+  mark();
   mx::launch_groups(s->d, st);
+  mark();
   mx::launch_bs(s->d, s->bs_blocks, st);
+  mark();
   mx::launch_prep(s->d, 0.5, last ? 1 : 2, st);
+  mark();
   mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st);
+  mark();
 }
+
+void enqueue_head(mx_system* s, cudaStream_t st) { enqueue_head(s, st, nullptr); }
+void enqueue_step(mx_system* s, int last, cudaStream_t st) { enqueue_step(s, last, st, nullptr); }
 
 // Deferral is on for forward runs with a window; recording or replaying the
 // drag branches (kmode != 0) keeps every body on the direct path.
@@ -289,11 +314,11 @@ mx_status settle(mx_system* s) {
   return MX_OK;
 }
 
-mx_status capture(mx_system* s, int which, cudaGraphExec_t* out) {
+mx_status capture(mx_system* s, int which, cudaGraphExec_t* out, cudaEvent_t* marks = nullptr) {
   cudaGraph_t g = nullptr;
   MX_CUDA(cudaStreamBeginCapture(s->cap_st, cudaStreamCaptureModeThreadLocal));
-  if (which == 0) enqueue_head(s, s->cap_st);
-  else enqueue_step(s, which == 2, s->cap_st);
+  if (which == 0) enqueue_head(s, s->cap_st, marks);
+  else enqueue_step(s, which == 2, s->cap_st, marks);
   cudaError_t e = cudaStreamEndCapture(s->cap_st, &g);
   if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
   e = cudaGraphInstantiate(out, g, 0);
@@ -307,6 +332,19 @@ mx_status ensure_graphs(mx_system* s) {
   MX_TRY(capture(s, 0, &s->g_head));
   MX_TRY(capture(s, 1, &s->g_mid));
   MX_TRY(capture(s, 2, &s->g_last));
+  return MX_OK;
+}
+
+// The step graphs with event nodes between the kernels (mx_step_timed).
+mx_status ensure_timed_graphs(mx_system* s) {
+  if (s->gt_head) return MX_OK;
+  for (auto& e : s->mk_head)
+    if (!e) MX_CUDA(cudaEventCreate(&e));
+  for (auto& e : s->mk_step)
+    if (!e) MX_CUDA(cudaEventCreate(&e));
+  MX_TRY(capture(s, 0, &s->gt_head, s->mk_head));
+  MX_TRY(capture(s, 1, &s->gt_mid, s->mk_step));
+  MX_TRY(capture(s, 2, &s->gt_last, s->mk_step));
   return MX_OK;
 }
 
@@ -343,7 +381,11 @@ void drop_graphs(mx_system* s) {
   if (s->g_head) cudaGraphExecDestroy(s->g_head);
   if (s->g_mid) cudaGraphExecDestroy(s->g_mid);
   if (s->g_last) cudaGraphExecDestroy(s->g_last);
+  if (s->gt_head) cudaGraphExecDestroy(s->gt_head);
+  if (s->gt_mid) cudaGraphExecDestroy(s->gt_mid);
+  if (s->gt_last) cudaGraphExecDestroy(s->gt_last);
   s->g_head = s->g_mid = s->g_last = nullptr;
+  s->gt_head = s->gt_mid = s->gt_last = nullptr;
 }
 
 mx_status set_tiling(mx_system* s, int tile, int order) {
@@ -643,6 +685,10 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device));
   s->bs_blocks = 4 * nsm;
   s->catch_blocks = 4 * nsm;
+  mx::configure_drift();
+  mx::configure_detect();
+  mx::configure_kick();
+  mx::configure_bs();
   return sync_status(s);
 }
 
@@ -662,6 +708,10 @@ void destroy_impl(mx_system* s) {
     cudaEventDestroy(sp.a);
     cudaEventDestroy(sp.b);
   }
+  for (auto e : s->mk_head)
+    if (e) cudaEventDestroy(e);
+  for (auto e : s->mk_step)
+    if (e) cudaEventDestroy(e);
   if (s->ev_main) cudaEventDestroy(s->ev_main);
   if (s->ev_side) cudaEventDestroy(s->ev_side);
   if (s->cap_st) cudaStreamDestroy(s->cap_st);
@@ -986,6 +1036,106 @@ mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_byte
   return sync_status(s);
 }
 
+// mx_step_timed: the step graphs of mx_step, in their timed variants (an
+// event node between kernels), one step at a time.  Before every step the
+// flush buffer is overwritten; after it the host waits for the step's end and
+// reads its events.  A step's span runs from its first event to its end (a
+// window-end catch-up included).  Deferral's side-stream launches are timed
+// as in profiled_run.
+mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_bytes,
+                          double* kernel_ms, int* launches, double* total_ms) {
+  if (!s || n_steps < 0 || (flush_bytes > 0 && !flush)) return fail(MX_ERR_ARG, "invalid arguments");
+  if (n_steps == 0) return profiled_run(s, 0, flush, flush_bytes, kernel_ms, launches, total_ms);
+  MX_TRY(set_device(s));
+  MX_TRY(ensure_graphs(s));
+  MX_TRY(ensure_timed_graphs(s));
+  cudaStream_t st = s->st;
+  double sum[MX_NKERN] = {0};
+  int cnt[MX_NKERN] = {0};
+  std::vector<mx_system::Span> spans;   // window-end launches on the main stream
+  auto timed3 = [&](int k, cudaStream_t sm, auto&& launch) -> cudaError_t {
+    mx_system::Span sp{k, nullptr, nullptr};
+    cudaError_t r = cudaEventCreate(&sp.a);
+    if (r == cudaSuccess) r = cudaEventRecord(sp.a, sm);
+    if (r != cudaSuccess) return r;
+    launch();
+    r = cudaEventCreate(&sp.b);
+    if (r == cudaSuccess) r = cudaEventRecord(sp.b, sm);
+    if (r != cudaSuccess) return r;
+    if (sm == st) spans.push_back(sp);
+    else s->side_spans.push_back(sp);
+    return cudaGetLastError();
+  };
+  static const int kHeadKind[2] = {MX_K_PREP, MX_K_JUMP_KICK};
+  static const int kStepKind[6] = {MX_K_JUMP_DRIFT, MX_K_DETECT, MX_K_GROUPS, MX_K_BS, MX_K_PREP,
+                                   MX_K_JUMP_KICK};
+  cudaEvent_t e_end = nullptr;
+  MX_CUDA(cudaEventCreate(&e_end));
+  double tot = 0.0;
+  float ms = 0.f;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+    if (flush_bytes > 0) e = cudaMemsetAsync(flush, k & 0xff, flush_bytes, st);
+    if (e == cudaSuccess && k == 0) {
+      e = cudaGraphLaunch(s->gt_head, st);
+      if (e == cudaSuccess) e = slot_done(s, false, timed3);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(k + 1 == n_steps ? s->gt_last : s->gt_mid, st);
+    if (e == cudaSuccess) e = slot_done(s, true, timed3);
+    if (e == cudaSuccess) e = cudaEventRecord(e_end, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e_end);
+    if (e != cudaSuccess) break;
+    if (k == 0)
+      for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        e = cudaEventElapsedTime(&ms, s->mk_head[q], s->mk_head[q + 1]);
+        sum[kHeadKind[q]] += ms;
+        cnt[kHeadKind[q]]++;
+      }
+    for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
+      e = cudaEventElapsedTime(&ms, s->mk_step[q], s->mk_step[q + 1]);
+      sum[kStepKind[q]] += ms;
+      cnt[kStepKind[q]]++;
+    }
+    for (auto& sp : spans) {
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, sp.a, sp.b);
+      sum[sp.kind] += ms;
+      cnt[sp.kind]++;
+      cudaEventDestroy(sp.a);
+      cudaEventDestroy(sp.b);
+    }
+    spans.clear();
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, k == 0 ? s->mk_head[0] : s->mk_step[0], e_end);
+    tot += ms;
+  }
+  for (auto& sp : spans) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  cudaEventDestroy(e_end);
+  // side-stream launches that have completed
+  std::vector<mx_system::Span> keep;
+  for (auto& sp : s->side_spans) {
+    if (e == cudaSuccess && cudaEventQuery(sp.b) == cudaSuccess) {
+      e = cudaEventElapsedTime(&ms, sp.a, sp.b);
+      sum[sp.kind] += ms;
+      cnt[sp.kind]++;
+      cudaEventDestroy(sp.a);
+      cudaEventDestroy(sp.b);
+    } else {
+      keep.push_back(sp);
+    }
+  }
+  s->side_spans.swap(keep);
+  if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("timed step: ") + cudaGetErrorString(e));
+  for (int q = 0; q < MX_NKERN; ++q) {
+    if (kernel_ms) kernel_ms[q] = sum[q];
+    if (launches) launches[q] = cnt[q];
+  }
+  if (total_ms) *total_ms = tot;
+  s->step += n_steps;
+  return sync_status(s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -997,7 +1147,7 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
 
 mx_status mx_step_timed(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
                         double* kernel_ms, int* launches, double* total_ms) {
-  return profiled_run(s, n_steps, dev_flush, flush_bytes, kernel_ms, launches, total_ms);
+  return timed_graph_run(s, n_steps, dev_flush, flush_bytes, kernel_ms, launches, total_ms);
 }
 
 mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pairs) {

@@ -7,6 +7,12 @@ namespace mx {
 
 struct Dev;
 
+// One shared-memory carveout for all kernels of a step (set once per system).
+void configure_drift();
+void configure_detect();
+void configure_kick();
+void configure_bs();
+
 // k_init.cu / k_misc.cu
 void launch_init_sys(const Dev& d, int do_rcrit, double rcrit_hill, cudaStream_t st);
 void launch_init_bodies(const Dev& d, const double* rp_km, const double* rho, int set_drag,
