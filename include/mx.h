@@ -66,6 +66,12 @@ typedef struct {
   double cd_scale;      /* factor on C_D */
   int enabled;          /* 0: no drag */
   int cd_mode;          /* 0: Eq. 7 bracket to the power -1; 1: power -2 as printed */
+  int disk_gravity;     /* 1: the disk's gravity on planetesimals (Eqs. 10-12): a radial
+                           force per unit mass 2 pi G Sigma(R) S(gamma) (gamma != 1) or
+                           2 pi G Sigma(R) r_in / R (gamma = 1), outward positive, along the
+                           cylindrical radius, where R >= r_in; not differentiated by the
+                           adjoint (MX_ERR_ARG there) */
+  int reserved;         /* 0 */
 } mx_gas;
 
 typedef struct {

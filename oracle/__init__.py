@@ -24,7 +24,8 @@ _P = ctypes.c_void_p
 class OrcGas(ctypes.Structure):
     _fields_ = [("sigma1_gcm2", _D), ("gamma", _D), ("r_c_au", _D), ("r_in_au", _D),
                 ("hr_1au", _D), ("flare", _D), ("gamma_c", _D), ("mu_mol", _D),
-                ("sigma_mol_cm2", _D), ("cd_scale", _D), ("enabled", _I), ("cd_mode", _I)]
+                ("sigma_mol_cm2", _D), ("cd_scale", _D), ("enabled", _I), ("cd_mode", _I),
+                ("disk_gravity", _I), ("reserved", _I)]
 
 
 class OrcParams(ctypes.Structure):
@@ -61,6 +62,8 @@ def lib():
             "orc_gas_drag": (_I, [_P, _I, _I, _P, _P, _P, _P, _P]),
             "orc_gas_state": (_I, [_P, _D, _P]),
             "orc_drag_cd": (_D, [_D, _D, _I]),
+            "orc_dg_series": (_D, [_D]),
+            "orc_disk_gravity": (_I, [_P, _P, _P]),
             "orc_drag_one": (_I, [_P, _P, _P, _D, _D, _P, _P]),
             "orc_stumpff": (None, [_D, _P]),
             "orc_drift": (_I, [_P, _I, _P, _D, _P]),
@@ -98,7 +101,7 @@ def make_params(cfg):
     g = cfg["gas"]
     gas = OrcGas(g["sigma1_gcm2"], g["gamma"], g["r_c_au"], g["r_in_au"], g["hr_1au"], g["flare"],
                  g["gamma_c"], g["mu_mol"], g["sigma_mol_cm2"], g["cd_scale"], int(g["enabled"]),
-                 int(g["cd_mode"]))
+                 int(g["cd_mode"]), int(g.get("disk_gravity", False)), 0)
     return OrcParams(cfg["G"], cfg["m_star"], cfg["dt"], cfg["rcrit_hill"], cfg["bs_tol"],
                      int(cfg["kepler_max_iter"]), int(cfg["bs_max_sub"]), int(cfg["pair_cap"]), gas)
 
@@ -173,6 +176,18 @@ def gas_state(p, R):
 
 def drag_cd(Re, Ma, mode=0):
     return lib().orc_drag_cd(float(Re), float(Ma), int(mode))
+
+
+def dg_series(gamma):
+    """S(gamma) of Eq. 10: F_DG = 2 pi G Sigma(r) S(gamma) for gamma != 1."""
+    return lib().orc_dg_series(float(gamma))
+
+
+def disk_gravity(p, x3):
+    x3 = _f64(x3)
+    acc = np.empty(3)
+    _check(lib().orc_disk_gravity(ctypes.byref(p), _ptr(x3), _ptr(acc)), "disk_gravity")
+    return acc
 
 
 def drag_one(p, x3, vh3, rp_km, rhop):

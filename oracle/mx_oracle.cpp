@@ -36,6 +36,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kAuCm = 1.495978707e13;     // astronomical unit [cm] (IAU 2012)
 constexpr double kAuKm = 1.495978707e8;      // astronomical unit [km]
 constexpr double kHydrogenG = 1.6735575e-24; // mass of a hydrogen atom [g]
+constexpr double kMsunG = 1.98847e33;        // solar mass [g]
 constexpr double kEps = std::numeric_limits<double>::epsilon();
 
 // ------------------------------------------------------------ dual numbers
@@ -104,6 +105,7 @@ struct Bodies {
 template <class T>
 struct GasT {
   orc_gas raw;
+  double G = 0.0;             // gravitational constant (disk gravity)
   T sigma1, gamma, cd_scale;  // the three differentiable disk/drag parameters
 };
 
@@ -290,8 +292,64 @@ void drag_one(const GasT<T>& g, double mu0, const T* x, const T* vh, double rp_k
   if (re_ma) { re_ma[0] = val(Re); re_ma[1] = val(Ma); }
 }
 
-// Drag on every small body.  The body's heliocentric velocity is its DH
-// (barycentric) velocity plus P/m0, P the massive-body momentum at kick time.
+// ------------------------------------------- disk gravity (Sec. 3.1.2)
+// The leading term of the axisymmetric thin-disk force (Eq. 10):
+//   F_DG = 2 pi G Sigma(r) S(gamma),
+//   S(gamma) = sum_n A_n (1 - gamma)(4n + 1) / ((2n + 2 - gamma)(2n - 1 + gamma)),
+//   A_n = [(2n)! / (2^(2n) (n!)^2)]^2,
+// and for gamma = 1 the leading edge term, F_DG = 2 pi G Sigma(r) R_in / r
+// (Eq. 12).  The terms of S fall off as (1 - gamma)/(pi n^2), so the partial
+// sums S_N approach S as S + c1/N + c2/N^2 + ...; S is taken from the
+// compensated partial sums at N = 256 * 2^k by Richardson extrapolation in 1/N
+// (eight levels).  Reading: F_DG is the signed radial force per unit mass in the
+// midplane (positive outward), applied along the cylindrical radius; it acts
+// on planetesimals only, where there is gas (r >= R_in).
+double dg_series(double gamma) {
+  const int levels = 8;
+  double S[levels];
+  double sum = 0.0, comp = 0.0;      // compensated (Kahan) sum of the terms
+  double An_root = 1.0;              // A_n = An_root^2, An_root = (2n)!/(4^n (n!)^2)
+  int n = 0;
+  for (int k = 0; k < levels; ++k) {
+    const int N = 256 << k;
+    for (; n < N; ++n) {
+      if (n > 0) An_root *= (2.0 * n - 1.0) / (2.0 * n);
+      const double An = An_root * An_root;
+      const double t = An * (1.0 - gamma) * (4.0 * n + 1.0) /
+                       ((2.0 * n + 2.0 - gamma) * (2.0 * n - 1.0 + gamma));
+      const double y = t - comp;
+      const double nxt = sum + y;
+      comp = (nxt - sum) - y;
+      sum = nxt;
+    }
+    S[k] = sum;
+  }
+  // Richardson: each level removes the next 1/N^m term (N doubles between entries)
+  for (int m = 1; m < levels; ++m)
+    for (int k = levels - 1; k >= m; --k) {
+      const double f = std::ldexp(1.0, m);
+      S[k] = (f * S[k] - S[k - 1]) / (f - 1.0);
+    }
+  return S[levels - 1];
+}
+
+template <class T>
+void disk_gravity_one(const GasT<T>& g, double mu0, const T* x, T* acc) {
+  if (!g.raw.enabled || !g.raw.disk_gravity) return;
+  T R = sqrt(x[0] * x[0] + x[1] * x[1]);
+  if (val(R) < g.raw.r_in_au || val(R) == 0.0) return;
+  DiskAt<T> d = disk_at(g, mu0, R);
+  const double to_code = kAuCm * kAuCm / kMsunG;   // g/cm^2 -> Msun/AU^2
+  T F = T(2.0 * kPi * g.G * to_code) * d.sigma;
+  if (g.raw.gamma == 1.0) F = F * (g.raw.r_in_au / R);
+  else F = F * dg_series(g.raw.gamma);
+  acc[0] = acc[0] + F * x[0] / R;
+  acc[1] = acc[1] + F * x[1] / R;
+}
+
+// Drag on every small body, plus the disk's gravity when enabled.  The body's
+// heliocentric velocity is its DH (barycentric) velocity plus P/m0, P the
+// massive-body momentum at kick time.
 template <class T>
 void accel_drag(const GasT<T>& g, const Bodies& b, const State<T>& s, const T P[3],
                 std::vector<T>* a) {
@@ -303,6 +361,7 @@ void accel_drag(const GasT<T>& g, const Bodies& b, const State<T>& s, const T P[
     for (int k = 0; k < 3; ++k) vh[k] = s.q[3 + k][j] + P[k] / b.mu0;
     T acc[3];
     drag_one(g, b.mu0, x, vh, b.rp_km[j - nb], b.rhop[j - nb], acc, nullptr);
+    disk_gravity_one(g, b.mu0, x, acc);
     for (int k = 0; k < 3; ++k) a[k][j] = acc[k];
   }
 }
@@ -808,9 +867,10 @@ bool make_bodies(const orc_params* p, int nbig, int nsmall, const double* mu, co
 }
 
 template <class T>
-GasT<T> make_gas(const orc_gas& raw) {
+GasT<T> make_gas(const orc_gas& raw, double G) {
   GasT<T> g;
   g.raw = raw;
+  g.G = G;
   g.sigma1 = T(raw.sigma1_gcm2);
   g.gamma = T(raw.gamma);
   g.cd_scale = T(raw.cd_scale);
@@ -918,7 +978,7 @@ int orc_momentum(int nbig, int n, const double* xv, const double* mu, double* P3
 
 int orc_gas_state(const orc_params* p, double R, double* out8) {
   if (!p || !out8 || !(R > 0.0)) return ORC_ERR_ARG;
-  GasT<double> g = make_gas<double>(p->gas);
+  GasT<double> g = make_gas<double>(p->gas, p->G);
   DiskAt<double> d = disk_at(g, p->G * p->m_star, R);
   out8[0] = d.sigma; out8[1] = d.rho_g; out8[2] = d.H_au; out8[3] = d.cs;
   out8[4] = d.vk; out8[5] = d.eta; out8[6] = d.vg; out8[7] = d.hr;
@@ -927,10 +987,20 @@ int orc_gas_state(const orc_params* p, double R, double* out8) {
 
 double orc_drag_cd(double Re, double Ma, int cd_mode) { return drag_cd(Re, Ma, cd_mode); }
 
+double orc_dg_series(double gamma) { return dg_series(gamma); }
+
+int orc_disk_gravity(const orc_params* p, const double* x3, double* acc3) {
+  if (!p || !x3 || !acc3) return ORC_ERR_ARG;
+  GasT<double> g = make_gas<double>(p->gas, p->G);
+  acc3[0] = acc3[1] = acc3[2] = 0.0;
+  disk_gravity_one(g, p->G * p->m_star, x3, acc3);
+  return ORC_OK;
+}
+
 int orc_drag_one(const orc_params* p, const double* x3, const double* vh3, double rp_km,
                  double rhop, double* acc3, double* re_ma2) {
   if (!p || !x3 || !vh3 || !acc3) return ORC_ERR_ARG;
-  GasT<double> g = make_gas<double>(p->gas);
+  GasT<double> g = make_gas<double>(p->gas, p->G);
   drag_one(g, p->G * p->m_star, x3, vh3, rp_km, rhop, acc3, re_ma2);
   return ORC_OK;
 }
@@ -944,7 +1014,7 @@ int orc_gas_drag(const orc_params* p, int nbig, int nsmall, const double* xv, co
   make_bodies(p, nbig, nsmall, mu, zero.data(), rp_km, rhop, b);
   State<double> s;
   load_state(s, n, xv);
-  GasT<double> g = make_gas<double>(p->gas);
+  GasT<double> g = make_gas<double>(p->gas, p->G);
   double P[3];
   momentum(b, s, P);
   std::vector<double> a[3];
@@ -1012,7 +1082,7 @@ int orc_step(const orc_params* p, int nbig, int nsmall, double* xv, const double
   if (p->gas.enabled && nsmall > 0 && (!rp_km || !rhop)) return ORC_ERR_ARG;
   State<double> s;
   load_state(s, b.n, xv);
-  GasT<double> g = make_gas<double>(p->gas);
+  GasT<double> g = make_gas<double>(p->gas, p->G);
   StepStats st;
   int lc = 0;
   int err = ORC_OK;
@@ -1102,6 +1172,7 @@ int orc_jvp_loss(const orc_params* p, int nbig, int nsmall, const double* m_big,
   }
   GasT<Dual> g;
   g.raw = p->gas;
+  g.G = p->G;
   g.sigma1 = Dual(p->gas.sigma1_gcm2, dpar[0]);
   g.gamma = Dual(p->gas.gamma, dpar[1]);
   g.cd_scale = Dual(p->gas.cd_scale, dpar[2]);

@@ -44,6 +44,8 @@ typedef struct {
   double cd_scale;      /* multiplies C_D (differentiable drag-coefficient factor) */
   int enabled;          /* 0 = no gas drag */
   int cd_mode;          /* 0: bracket of Eq. 7 to the power -1; 1: power -2 as printed */
+  int disk_gravity;     /* 1: add the disk's gravity on planetesimals (Eqs. 10-12) */
+  int reserved;
 } orc_gas;
 
 typedef struct {
@@ -88,6 +90,10 @@ int orc_gas_drag(const orc_params* p, int nbig, int nsmall, const double* xv,
  * out = {Sigma [g/cm^2], rho_g [g/cm^3], H [AU], c_s [AU/d], v_k [AU/d],
  *        eta, v_g [AU/d], H/r}. */
 int orc_gas_state(const orc_params* p, double R, double* out8);
+/* The series S(gamma) of Eq. 10 (gamma != 1): F_DG = 2 pi G Sigma(r) S(gamma). */
+double orc_dg_series(double gamma);
+/* Disk-gravity acceleration (Eqs. 10-12) on a planetesimal at x3 (AU/d^2). */
+int orc_disk_gravity(const orc_params* p, const double* x3, double* acc3);
 /* Drag coefficient of Eq. 7 (k = 0.4 below Re = 1e5, 0.2 from 1e5 up). */
 double orc_drag_cd(double Re, double Ma, int cd_mode);
 /* Drag acceleration of one small body with given heliocentric x and v_h. */

@@ -1462,6 +1462,10 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
   const double hp0 = P2[0] * S.inv_mu0, hp1 = P2[1] * S.inv_mu0, hp2 = P2[2] * S.inv_mu0;
   const double rp = S.gas_on ? d.rp_cm[j] : 0.0, kd = S.gas_on ? d.kdrag[j] : 0.0;
   const GasAt gq = S.gas_on ? gas_at(S, x, y) : GasAt{false, 0.0, 0.0, 0.0};
+  if (S.gas_on && S.dg_on) {   // as in k_jump_kick
+    ax += gq.adg[0];
+    ay += gq.adg[1];
+  }
   for (int kk = 0; kk < nk; ++kk) {
     double a[3] = {0.0, 0.0, 0.0};
     if (S.gas_on) {

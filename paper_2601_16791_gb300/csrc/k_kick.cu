@@ -160,6 +160,10 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
   const int kbase = d.kmode ? d.kick_ctr[1] : 0;
   // the gas at the (fixed) position, shared by the launch's half kicks
   const GasAt gq = drag ? gas_at(S, x, y) : GasAt{false, 0.0, 0.0, 0.0};
+  if (drag && S.dg_on) {   // disk gravity: fixed over the launch, like the big bodies' gravity
+    ax += gq.adg[0];
+    ay += gq.adg[1];
+  }
 #pragma unroll
   for (int kk = 0; kk < NKICK; ++kk) {
     double a[3] = {0.0, 0.0, 0.0};

@@ -31,6 +31,34 @@ mx_status fail(mx_status code, const std::string& msg) {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kAuCm = 1.495978707e13;
 constexpr double kHydrogenG = 1.6735575e-24;
+constexpr double kMsunG = 1.98847e33;   // solar mass [g]
+
+// S(gamma) = sum_n A_n (1-gamma)(4n+1)/((2n+2-gamma)(2n-1+gamma)),
+// A_n = [(2n)!/(2^(2n) (n!)^2)]^2 (Eq. 10, gamma != 1).  The first 2^20 terms
+// are summed with compensation; the rest is the tail of the terms' expansion
+// t_n = (1-gamma)/(pi n^2) (1 - 1/(2n)) + O(n^-4), i.e.
+// (1-gamma)/pi (1/N + 1/(4N^2)) + O(N^-3).  Cached per gamma.
+double disk_gravity_series(double gamma) {
+  static std::vector<std::pair<double, double>> cache;
+  for (auto& kv : cache)
+    if (kv.first == gamma) return kv.second;
+  const int N = 1 << 20;
+  double sum = 0.0, comp = 0.0, b = 1.0;   // b = (2n)!/(4^n (n!)^2), A_n = b^2
+  for (int n = 0; n < N; ++n) {
+    if (n > 0) b *= (2.0 * n - 1.0) / (2.0 * n);
+    const double t = b * b * (1.0 - gamma) * (4.0 * n + 1.0) /
+                     ((2.0 * n + 2.0 - gamma) * (2.0 * n - 1.0 + gamma));
+    const double y = t - comp;
+    const double nx = sum + y;
+    comp = (nx - sum) - y;
+    sum = nx;
+  }
+  const double Nd = (double)N;
+  const double tail = (1.0 - gamma) / kPi * (1.0 / Nd + 0.25 / (Nd * Nd));
+  const double S = sum + tail;
+  cache.push_back({gamma, S});
+  return S;
+}
 
 #define MX_CUDA(call)                                                                     \
   do {                                                                                    \
@@ -96,6 +124,11 @@ mx::SysDev make_sysdev(const mx_params& p, int off, int nbig, int n, int boff) {
   s.deta_dgamma = g.hr_1au * g.hr_1au / (2.0 * g.gamma_c);
   const double c_lam = g.mu_mol * kHydrogenG / g.sigma_mol_cm2;
   s.c_re = 4.0 / (std::sqrt(8.0 / kPi) * c_lam);
+  // disk gravity: 2 pi G Sigma [Msun/AU^2] times S(gamma), or r_in / R at gamma = 1
+  s.dg_on = (g.enabled && g.disk_gravity) ? 1 : 0;
+  s.dg_edge = (g.gamma == 1.0) ? 1 : 0;
+  const double two_pi_g = 2.0 * kPi * p.G * (kAuCm * kAuCm / kMsunG);
+  s.c_dg = s.dg_on ? two_pi_g * (s.dg_edge ? g.r_in_au : disk_gravity_series(g.gamma)) : 0.0;
   return s;
 }
 
@@ -130,7 +163,8 @@ struct mx_system {
   int last_full = -1;             // history slot of the last whole step, -1 none
   int carried = 1;                // bank of the bodies carried from the last window (1 or 2)
   bool side_busy = false;         // a side-stream pass is in flight
-  cudaStream_t side_st = nullptr;
+  cudaStream_t side_st = nullptr; // highest priority: its blocks take SMs as soon as they free up
+  int prio_low = 0, prio_high = 0;
   cudaEvent_t ev_main = nullptr, ev_side = nullptr;
   long long catchups = 0;
   // side-stream launches timed by mx_step_profiled, read once they complete
@@ -727,7 +761,8 @@ mx_status create(mx_system** out, void* stream) {
   }
   s->st = (cudaStream_t)stream;
   if (cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&s->prio_low, &s->prio_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&s->side_st, cudaStreamNonBlocking, s->prio_high) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_main, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_side, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost(&s->h_status, sizeof(unsigned)) != cudaSuccess ||
@@ -1473,6 +1508,8 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
                           double* dev_lambda, double* dev_dparams) {
   if (!s || !dev_state_k || !dev_lambda || !dev_dparams || step_k < 0 || step_k > (1LL << 29))
     return fail(MX_ERR_ARG, "invalid arguments");
+  for (auto& y : s->h_sys)
+    if (y.dg_on) return fail(MX_ERR_ARG, "disk gravity is not differentiated by the adjoint");
   MX_TRY(set_device(s));
   MX_TRY(settle(s));
   MX_TRY(ensure_adjoint(s));

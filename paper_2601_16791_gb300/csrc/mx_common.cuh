@@ -62,6 +62,10 @@ struct SysDev {
   double c_eta;   // eta  = c_eta * R^(2 flare)
   double deta_dgamma;  // d c_eta / d gamma
   double c_re;    // Re   = c_re * r_p[cm] * Ma * rho_g
+  // disk gravity (Eqs. 10-12): radial force per unit mass c_dg * Sigma[g/cm^2],
+  // times 1/R for gamma = 1 (dg_edge), outward positive
+  int dg_on, dg_edge;
+  double c_dg;
 };
 
 // A block's worth of targets, never spanning two systems.

@@ -8,18 +8,21 @@ namespace mx {
 
 // The gas at a planetesimal's heliocentric position (Sec. 3.1): rho_g
 // (Eq. 4, midplane), 1/c_s and the gas velocity factor g (v_gas = g (-y, x, 0),
-// v_g = v_k sqrt(1 - 2 eta), Eqs. 5, 6).  in_gas = false inside the inner
-// edge (Sec. 3.1.1).  It depends on the position only, so the two half kicks
-// of one launch share it.
+// v_g = v_k sqrt(1 - 2 eta), Eqs. 5, 6), and, when enabled, the disk's
+// gravity (Eqs. 10-12) along the cylindrical radius.  in_gas = false inside
+// the inner edge (Sec. 3.1.1).  It depends on the position only, so the two
+// half kicks of one launch share it.
 struct GasAt {
   bool in_gas;
   double rho, inv_cs, g;
+  double adg[2];   // disk gravity (x, y), zero unless enabled
 };
 
 __device__ __forceinline__ GasAt gas_at(const SysDev& S, double x, double y) {
   GasAt q;
   q.in_gas = false;
   q.rho = q.inv_cs = q.g = 0.0;
+  q.adg[0] = q.adg[1] = 0.0;
   const double R2 = fma(x, x, y * y);
   const double iR = rsqrt_d(R2);             // 1/R
   const double R = R2 * iR;
@@ -49,6 +52,11 @@ __device__ __forceinline__ GasAt gas_at(const SysDev& S, double x, double y) {
   q.g = vg * iR;                             // gas velocity = g * (-y, x, 0)
   q.inv_cs = inv_cs;
   q.in_gas = true;
+  if (S.dg_on) {   // Eqs. 10-12: 2 pi G Sigma S(gamma), or 2 pi G Sigma r_in / R
+    const double F = S.c_dg * sigma * (S.dg_edge ? iR : 1.0);
+    q.adg[0] = F * iR * x;
+    q.adg[1] = F * iR * y;
+  }
   return q;
 }
 
@@ -90,16 +98,19 @@ __device__ __forceinline__ void gas_drag_at(const SysDev& S, const GasAt& q, dou
   a[2] = -coef * dw;
 }
 
-// Drag acceleration (Eq. 3) of one planetesimal at heliocentric position
-// (x, y, z) moving with heliocentric velocity (u, v, w): gas_at, then
-// gas_drag_at.  Quantities follow Sec. 3.1: Sigma (Eq. 1, normalised at
-// 1 AU), rho_g (Eq. 4) at the midplane, v_g (Eqs. 5, 6), C_D (Eq. 7).
+// The gas's acceleration on one planetesimal at heliocentric position
+// (x, y, z) moving with heliocentric velocity (u, v, w): the drag (gas_at,
+// then gas_drag_at) plus, when enabled, the disk's gravity.  Quantities follow
+// Sec. 3.1: Sigma (Eq. 1, normalised at 1 AU), rho_g (Eq. 4) at the midplane,
+// v_g (Eqs. 5, 6), C_D (Eq. 7).
 __device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, double z, double u,
                                          double v, double w, double rp_cm, double kd, double* a,
                                          int kb_in, int* kb_out) {
   (void)z;
   const GasAt q = gas_at(S, x, y);
   gas_drag_at(S, q, x, y, u, v, w, rp_cm, kd, a, kb_in, kb_out);
+  a[0] += q.adg[0];
+  a[1] += q.adg[1];
 }
 
 // K(s)/s^3 times mu for one pair, accumulated into (ax, ay, az) as -f * d

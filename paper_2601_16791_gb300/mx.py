@@ -33,7 +33,8 @@ MX_MAX_GROUP = 16
 class MxGas(ctypes.Structure):
     _fields_ = [("sigma1_gcm2", _D), ("gamma", _D), ("r_c_au", _D), ("r_in_au", _D),
                 ("hr_1au", _D), ("flare", _D), ("gamma_c", _D), ("mu_mol", _D),
-                ("sigma_mol_cm2", _D), ("cd_scale", _D), ("enabled", _I), ("cd_mode", _I)]
+                ("sigma_mol_cm2", _D), ("cd_scale", _D), ("enabled", _I), ("cd_mode", _I),
+                ("disk_gravity", _I), ("reserved", _I)]
 
 
 class MxParams(ctypes.Structure):
@@ -138,7 +139,7 @@ def make_params(cfg) -> MxParams:
     g = cfg["gas"]
     gas = MxGas(g["sigma1_gcm2"], g["gamma"], g["r_c_au"], g["r_in_au"], g["hr_1au"], g["flare"],
                 g["gamma_c"], g["mu_mol"], g["sigma_mol_cm2"], g["cd_scale"], int(g["enabled"]),
-                int(g["cd_mode"]))
+                int(g["cd_mode"]), int(g.get("disk_gravity", False)), 0)
     return MxParams(cfg["G"], cfg["m_star"], cfg["dt"], cfg["rcrit_hill"], cfg["bs_tol"],
                     int(cfg["kepler_max_iter"]), int(cfg["bs_max_sub"]), int(cfg["pair_cap"]), gas)
 

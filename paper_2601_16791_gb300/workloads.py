@@ -47,10 +47,10 @@ M_MOON = 3.69e-8                     # lunar mass [Msun]
 M_MARS = 3.23e-7                     # Mars mass [Msun]
 
 
-def default_gas(enabled=False, sigma1=1700.0, gamma=1.0):
+def default_gas(enabled=False, sigma1=1700.0, gamma=1.0, disk_gravity=False):
     return dict(sigma1_gcm2=sigma1, gamma=gamma, r_c_au=math.inf, r_in_au=0.0, hr_1au=0.05,
                 flare=0.25, gamma_c=1.4, mu_mol=2.34, sigma_mol_cm2=2e-15, cd_scale=1.0,
-                enabled=bool(enabled), cd_mode=0)
+                enabled=bool(enabled), cd_mode=0, disk_gravity=bool(disk_gravity))
 
 
 def default_params(dt, gas=None, pair_cap=1 << 20):

@@ -30,6 +30,58 @@ def params(dt=8.0, gas=False, **kw):
     return orc.make_params(p)
 
 
+# ------------------------------------------------------- disk gravity (Eqs. 10-12)
+def _dg_params(gamma=1.0, r_in=0.5, sigma1=1700.0, enabled=True):
+    g = W.default_gas(True, sigma1=sigma1, gamma=gamma, disk_gravity=enabled)
+    g["r_in_au"] = r_in
+    return orc.make_params(W.default_params(10.0, g))
+
+
+@pytest.mark.parametrize("gamma", [0.3, 0.5, 0.8, 1.2, 1.5, 1.9])
+def test_disk_gravity_series_vs_mpmath(gamma):
+    """Eq. 10's series S(gamma), summed by mpmath's own convergence acceleration."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    g = mp.mpf(gamma)
+    term = lambda n: ((mp.binomial(2 * n, n) / mp.mpf(4) ** n) ** 2 * (1 - g) * (4 * n + 1)
+                      / ((2 * n + 2 - g) * (2 * n - 1 + g)))
+    ref = float(mp.nsum(term, [0, mp.inf]))
+    assert abs(orc.dg_series(gamma) - ref) <= 2e-15 * abs(ref)
+
+
+def test_disk_gravity_units_against_cgs():
+    """2 pi G Sigma for Sigma = 1700 g/cm^2 at 1 AU, gamma = 1.5 (force = that x S),
+    computed in CGS (G = 6.6743e-8) and converted to AU/day^2: the Gaussian units
+    and the solar mass agree with CGS to ~1e-4."""
+    p = _dg_params(gamma=1.5, r_in=0.0)
+    a = orc.disk_gravity(p, [1.0, 0.0, 0.0])
+    cgs = 2 * math.pi * 6.6743e-8 * 1700.0 * orc.dg_series(1.5)          # cm/s^2
+    ref = cgs * 86400.0 ** 2 / 1.495978707e13                              # AU/d^2
+    assert abs(a[0] - ref) <= 2e-4 * abs(ref) and a[1] == 0.0 and a[2] == 0.0
+
+
+def test_disk_gravity_geometry_and_scalings():
+    """Radial in the plane, zero inside R_in and when off, independent of z,
+    outward for the gamma = 1 edge term (Eq. 12) and inward for gamma != 1
+    (S < 0), proportional to Sigma1, and for gamma = 1 to R_in / R^2."""
+    p = _dg_params(gamma=1.0, r_in=0.5)
+    a1 = orc.disk_gravity(p, [3.0, 4.0, 0.0])           # R = 5
+    assert a1[2] == 0.0 and a1[0] > 0 and abs(a1[0] / a1[1] - 0.75) < 1e-15
+    assert np.allclose(orc.disk_gravity(p, [3.0, 4.0, 0.3]), a1, rtol=1e-15, atol=0)
+    assert np.all(orc.disk_gravity(p, [0.3, 0.1, 0.0]) == 0.0)              # R < R_in
+    assert np.all(orc.disk_gravity(_dg_params(enabled=False), [3.0, 4.0, 0.0]) == 0.0)
+    a2 = orc.disk_gravity(p, [6.0, 8.0, 0.0])           # R = 10
+    assert abs(np.linalg.norm(a1) / np.linalg.norm(a2) - 4.0) < 1e-13
+    a3 = orc.disk_gravity(_dg_params(gamma=1.0, r_in=1.0), [3.0, 4.0, 0.0])
+    assert abs(np.linalg.norm(a3) / np.linalg.norm(a1) - 2.0) < 1e-13
+    a4 = orc.disk_gravity(_dg_params(gamma=1.0, r_in=0.5, sigma1=850.0), [3.0, 4.0, 0.0])
+    assert abs(np.linalg.norm(a1) / np.linalg.norm(a4) - 2.0) < 1e-13
+    b = orc.disk_gravity(_dg_params(gamma=1.5, r_in=0.5), [3.0, 4.0, 0.0])
+    assert b[0] < 0 and b[1] < 0
+    b2 = orc.disk_gravity(_dg_params(gamma=1.5, r_in=0.5), [6.0, 8.0, 0.0])
+    assert abs(np.linalg.norm(b) / np.linalg.norm(b2) - 2.0 ** 1.5) < 1e-13    # Sigma ~ R^-1.5
+
+
 # ------------------------------------------------------------ changeover K(r)
 def test_changeover_endpoints_midpoint_symmetry():
     """Sec. 2.1.3 listing: K=1 for s >= rc, K=0 for s <= 0.1 rc, smooth between."""
