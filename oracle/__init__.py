@@ -30,7 +30,8 @@ class OrcGas(ctypes.Structure):
 
 class OrcParams(ctypes.Structure):
     _fields_ = [("G", _D), ("m_star", _D), ("dt", _D), ("rcrit_hill", _D), ("bs_tol", _D),
-                ("kepler_max_iter", _I), ("bs_max_sub", _I), ("pair_cap", _I), ("gas", OrcGas)]
+                ("kepler_max_iter", _I), ("bs_max_sub", _I), ("pair_cap", _I),
+                ("eject_every", _I), ("gas", OrcGas)]
 
 
 ERRORS = {0: "ok", 1: "bad argument", 2: "Kepler solve did not converge",
@@ -71,6 +72,10 @@ def lib():
             "orc_detect": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P]),
             "orc_bs_group": (_I, [_P, _I, _P, _P, _P, _D, _P]),
             "orc_step": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _P, _P]),
+            "orc_step_ex": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, ctypes.c_longlong, _P, _P,
+                                 _P]),
+            "orc_eject": (_I, [_P, _I, _I, _P, _P, _P, _P]),
+            "orc_elements": (_I, [_I, _P, _P, _P]),
             "orc_energy": (_I, [_P, _I, _I, _P, _P, _P, _P]),
             "orc_semimajor": (_I, [_P, _I, _I, _P, _P, _P]),
             "orc_jvp_loss": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P]),
@@ -103,7 +108,8 @@ def make_params(cfg):
                  g["gamma_c"], g["mu_mol"], g["sigma_mol_cm2"], g["cd_scale"], int(g["enabled"]),
                  int(g["cd_mode"]), int(g.get("disk_gravity", False)), 0)
     return OrcParams(cfg["G"], cfg["m_star"], cfg["dt"], cfg["rcrit_hill"], cfg["bs_tol"],
-                     int(cfg["kepler_max_iter"]), int(cfg["bs_max_sub"]), int(cfg["pair_cap"]), gas)
+                     int(cfg["kepler_max_iter"]), int(cfg["bs_max_sub"]), int(cfg["pair_cap"]),
+                     int(cfg.get("eject_every", 0)), gas)
 
 
 def set_threads(n):
@@ -254,6 +260,48 @@ def step(p, nbig, xv, mu, rcrit, rp_km, rhop, nsteps, log_cap=0):
                           _ptr(log) if log_cap > 0 else None, int(log_cap), ctypes.byref(lc),
                           _ptr(stats)), "step")
     return xv, ever, log[:min(lc.value, log_cap)].copy(), stats
+
+
+def step_ex(p, nbig, xv, mu, rcrit, rp_km, rhop, nsteps, stat=None, step0=0):
+    """nsteps hybrid steps with the ejection test of Sec. 3.5 on the schedule
+    p.eject_every, from global step index step0.  Returns (xv, mu, stat, ever):
+    stat is int8, 0 for bodies in the integration and -3 for removed ones;
+    removed massive bodies have mu 0."""
+    xv = _f64(xv).copy()
+    n = xv.shape[1]
+    mu = _f64(mu).copy()
+    rcrit = _f64(rcrit)
+    stat = np.zeros(n, dtype=np.int8) if stat is None else np.ascontiguousarray(stat, np.int8).copy()
+    rp = None if rp_km is None else _f64(rp_km)
+    rh = None if rhop is None else _f64(rhop)
+    ever = np.zeros(n, dtype=np.uint8)
+    _check(lib().orc_step_ex(ctypes.byref(p), nbig, n - nbig, _ptr(xv), _ptr(mu), _ptr(rcrit),
+                             _ptr(rp), _ptr(rh), int(nsteps), int(step0), _ptr(stat), _ptr(ever),
+                             None), "step_ex")
+    return xv, mu, stat, ever
+
+
+def eject(p, nbig, xv, mu, stat=None):
+    """The ejection test on a DH state.  Returns (mu, stat, removed)."""
+    xv = _f64(xv)
+    n = xv.shape[1]
+    mu = _f64(mu).copy()
+    stat = np.zeros(n, dtype=np.int8) if stat is None else np.ascontiguousarray(stat, np.int8).copy()
+    k = ctypes.c_int(0)
+    _check(lib().orc_eject(ctypes.byref(p), nbig, n, _ptr(xv), _ptr(mu), _ptr(stat),
+                           ctypes.byref(k)), "eject")
+    return mu, stat, k.value
+
+
+def elements(gm, xv_helio):
+    """Osculating elements (6 x n rows q, e, i, varpi, Omega, M) of heliocentric
+    states about gm (scalar or per body)."""
+    xv_helio = _f64(xv_helio)
+    n = xv_helio.shape[1]
+    gm = _f64(np.broadcast_to(np.asarray(gm, dtype=np.float64), (n,)))
+    out = np.empty((6, n))
+    _check(lib().orc_elements(n, _ptr(gm), _ptr(xv_helio), _ptr(out)), "elements")
+    return out
 
 
 def energy(p, nbig, xv, mu):

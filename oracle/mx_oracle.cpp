@@ -100,6 +100,11 @@ struct Bodies {
   double mu0 = 0.0;                 // G * m_star
   std::vector<double> mu, rcrit;    // per body; zero for small bodies
   std::vector<double> rp_km, rhop;  // per small body
+  // per body: 0 in the integration, -3 removed as ejected (Sec. 3.5); empty:
+  // every body is in.  A removed body keeps its state and takes no part in
+  // the kick, jump, drift or encounter search; a removed massive body has mu 0.
+  std::vector<signed char> stat;
+  bool gone(int j) const { return !stat.empty() && stat[j] != 0; }
 };
 
 template <class T>
@@ -167,7 +172,7 @@ void accel_grav(const Bodies& b, const State<T>& s, std::vector<T>* a) {
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < b.n; ++j) {
     T ax(0.0), ay(0.0), az(0.0);
-    for (int i = 0; i < b.nbig; ++i) {
+    for (int i = 0; i < b.nbig && !b.gone(j); ++i) {
       if (i == j) continue;
       T dx = s.q[0][j] - s.q[0][i];
       T dy = s.q[1][j] - s.q[1][i];
@@ -356,6 +361,10 @@ void accel_drag(const GasT<T>& g, const Bodies& b, const State<T>& s, const T P[
   const int nb = b.nbig;
 #pragma omp parallel for schedule(static)
   for (int j = nb; j < b.n; ++j) {
+    if (b.gone(j)) {
+      for (int k = 0; k < 3; ++k) a[k][j] = T(0.0);
+      continue;
+    }
     T x[3] = {s.q[0][j], s.q[1][j], s.q[2][j]};
     T vh[3];
     for (int k = 0; k < 3; ++k) vh[k] = s.q[3 + k][j] + P[k] / b.mu0;
@@ -485,10 +494,12 @@ int drift_one(double mu, double h, T* x, T* v, int maxit, int* iters) {
 }
 
 template <class T>
-int drift_all(double mu0, double h, int maxit, State<T>& s, int* itmax) {
+int drift_all(double mu0, double h, int maxit, State<T>& s, int* itmax,
+              const Bodies* b = nullptr) {
   int err = ORC_OK, imax = 0;
 #pragma omp parallel for schedule(static) reduction(max : err, imax)
   for (int j = 0; j < s.n; ++j) {
+    if (b && b->gone(j)) continue;
     T x[3] = {s.q[0][j], s.q[1][j], s.q[2][j]};
     T v[3] = {s.q[3][j], s.q[4][j], s.q[5][j]};
     int it = 0;
@@ -538,7 +549,7 @@ void detect(const Bodies& b, const double* xv0, const double* xv1, double h,
 #pragma omp parallel for schedule(dynamic)
   for (int i = 0; i < b.nbig; ++i) {
     for (int j = 0; j < n; ++j) {
-      if (j == i || (j < b.nbig && j < i)) continue;
+      if (j == i || (j < b.nbig && j < i) || b.gone(i) || b.gone(j)) continue;
       double dx0[3], dv0[3], dx1[3], dv1[3];
       for (int k = 0; k < 3; ++k) {
         dx0[k] = xv0[(size_t)k * n + j] - xv0[(size_t)k * n + i];
@@ -767,20 +778,22 @@ int hybrid_step(const orc_params& p, const GasT<T>& g, const Bodies& b, State<T>
     for (int k = 0; k < 3; ++k) std::fill(ad[k].begin(), ad[k].end(), T(0.0));
     accel_drag(g, b, s, P, ad);
     for (int k = 0; k < 3; ++k)
-      for (int j = 0; j < n; ++j) s.q[3 + k][j] = s.q[3 + k][j] + T(0.5 * h) * (a[k][j] + ad[k][j]);
+      for (int j = 0; j < n; ++j)
+        if (!b.gone(j)) s.q[3 + k][j] = s.q[3 + k][j] + T(0.5 * h) * (a[k][j] + ad[k][j]);
   };
   auto jump = [&]() {
     momentum(b, s, P);
     for (int k = 0; k < 3; ++k) {
       T dx = T(0.5 * h) * P[k] / b.mu0;
-      for (int j = 0; j < n; ++j) s.q[k][j] = s.q[k][j] + dx;
+      for (int j = 0; j < n; ++j)
+        if (!b.gone(j)) s.q[k][j] = s.q[k][j] + dx;
     }
   };
   kick();
   jump();
   State<T> s0 = s;
   int itmax = 0;
-  int err = drift_all(b.mu0, h, p.kepler_max_iter, s, &itmax);
+  int err = drift_all(b.mu0, h, p.kepler_max_iter, s, &itmax, &b);
   st.max_kep_iter = std::max<long long>(st.max_kep_iter, itmax);
   if (err) return err;
   std::vector<double> xv0((size_t)6 * n), xv1((size_t)6 * n);
@@ -834,6 +847,96 @@ int hybrid_step(const orc_params& p, const GasT<T>& g, const Bodies& b, State<T>
     for (int j = 0; j < n; ++j)
       if (!std::isfinite(val(s.q[k][j]))) return ORC_ERR_NONFINITE;
   return ORC_OK;
+}
+
+// ------------------------------------- orbital elements and ejection (Sec. 3.5)
+// Osculating elements of one body about gm (G(m0 + m) for a massive body,
+// G m0 for a planetesimal, Sec. 3.5), from the two-body relations (Murray &
+// Dermott 1999, Sec. 2.8):
+//   angular momentum h = x cross v, semilatus rectum p = |h|^2/gm;
+//   eccentricity vector (v cross h)/gm - x/r, e its length;
+//   q = p/(1 + e); cos i = h_z/|h|; node Omega = atan2(h_x, -h_y);
+//   argument of latitude u = angle of x from the node line in the orbit plane;
+//   true anomaly f from e cos f = p/r - 1, e sin f = |h| (x.v)/(gm r);
+//   longitude of pericentre varpi = Omega + u - f;
+//   mean anomaly from the eccentric anomaly E (e < 1, M = E - e sin E), the
+//   hyperbolic anomaly F (e > 1, M = e sinh F - F) or, for e = 1, Barker's
+//   D + D^3/3 with D = tan(f/2).
+// Conventions for the degenerate cases: Omega = 0 when the orbit lies in the
+// reference plane, f = 0 when e = 0.  Angles Omega, varpi and the elliptic M
+// are reduced to [0, 2 pi).
+struct Elements {
+  double q, e, i, varpi, node, M;
+};
+
+double wrap_2pi(double a) {
+  a = std::fmod(a, 2.0 * kPi);
+  return a < 0.0 ? a + 2.0 * kPi : a;
+}
+
+Elements x2el(double gm, const double* x, const double* v) {
+  Elements el;
+  const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  const double hx = x[1] * v[2] - x[2] * v[1];
+  const double hy = x[2] * v[0] - x[0] * v[2];
+  const double hz = x[0] * v[1] - x[1] * v[0];
+  const double hxy = std::sqrt(hx * hx + hy * hy);
+  const double h = std::sqrt(hx * hx + hy * hy + hz * hz);
+  const double p = h * h / gm;
+  const double ex = (v[1] * hz - v[2] * hy) / gm - x[0] / r;
+  const double ey = (v[2] * hx - v[0] * hz) / gm - x[1] / r;
+  const double ez = (v[0] * hy - v[1] * hx) / gm - x[2] / r;
+  const double e = std::sqrt(ex * ex + ey * ey + ez * ez);
+  el.e = e;
+  el.q = p / (1.0 + e);
+  el.i = std::atan2(hxy, hz);
+  const double node = (hxy > 0.0) ? std::atan2(hx, -hy) : 0.0;
+  el.node = wrap_2pi(node);
+  const double cn = std::cos(node), sn = std::sin(node);
+  const double ci = (h > 0.0) ? hz / h : 1.0, si = (h > 0.0) ? hxy / h : 0.0;
+  // in-plane axes: the node line and the direction 90 degrees ahead of it
+  const double along = x[0] * cn + x[1] * sn;
+  const double ahead = (-x[0] * sn + x[1] * cn) * ci + x[2] * si;
+  const double u = std::atan2(ahead, along);
+  const double rv = x[0] * v[0] + x[1] * v[1] + x[2] * v[2];
+  const double ecf = p / r - 1.0, esf = h * rv / (gm * r);
+  const double f = (e > 0.0) ? std::atan2(esf, ecf) : 0.0;
+  el.varpi = wrap_2pi(node + u - f);
+  if (e < 1.0) {
+    const double E = std::atan2(std::sqrt(1.0 - e * e) * std::sin(f), e + std::cos(f));
+    el.M = wrap_2pi(E - e * std::sin(E));
+  } else if (e > 1.0) {
+    const double F = std::asinh(std::sqrt(e * e - 1.0) * std::sin(f) / (1.0 + e * std::cos(f)));
+    el.M = e * std::sinh(F) - F;
+  } else {
+    const double D = std::tan(0.5 * f);
+    el.M = D + D * D * D / 3.0;
+  }
+  return el;
+}
+
+// The ejection test of Sec. 3.5: a body still in the integration whose
+// osculating heliocentric eccentricity is 1 or more is flagged (stat -3) and
+// a massive one loses its mass (mu 0).  Heliocentric velocities are
+// v_b + P/m0 with the massive-body momentum P of the state as given, taken
+// once for all bodies.
+int eject_check(Bodies& b, const State<double>& s) {
+  double P[3];
+  momentum(b, s, P);
+  int removed = 0;
+  for (int j = 0; j < b.n; ++j) {
+    if (b.gone(j)) continue;
+    const double x[3] = {s.q[0][j], s.q[1][j], s.q[2][j]};
+    double vh[3];
+    for (int k = 0; k < 3; ++k) vh[k] = s.q[3 + k][j] + P[k] / b.mu0;
+    const double gm = (j < b.nbig) ? b.mu0 + b.mu[j] : b.mu0;
+    if (x2el(gm, x, vh).e >= 1.0) {
+      b.stat[j] = -3;
+      if (j < b.nbig) b.mu[j] = 0.0;
+      ++removed;
+    }
+  }
+  return removed;
 }
 
 // ------------------------------------------------------ set-up and readout
@@ -1086,14 +1189,79 @@ int orc_step(const orc_params* p, int nbig, int nsmall, double* xv, const double
   StepStats st;
   int lc = 0;
   int err = ORC_OK;
-  for (int k = 0; k < nsteps && !err; ++k)
+  if (p->eject_every > 0) b.stat.assign(b.n, 0);   // removals stay local (see orc_step_ex)
+  for (int k = 0; k < nsteps && !err; ++k) {
     err = hybrid_step(*p, g, b, s, ever_flag, k, pair_log, log_cap, &lc, st);
+    if (!err && p->eject_every > 0 && (k + 1) % p->eject_every == 0) eject_check(b, s);
+  }
   store_state(s, xv);
   if (log_count) *log_count = lc;
   if (stats) {
     stats[0] = st.pairs; stats[1] = st.groups; stats[2] = st.max_bs_sub; stats[3] = st.max_kep_iter;
   }
   return err;
+}
+
+int orc_step_ex(const orc_params* p, int nbig, int nsmall, double* xv, double* mu,
+                const double* rcrit, const double* rp_km, const double* rhop, int nsteps,
+                long long step0, signed char* stat, unsigned char* ever_flag, long long* stats) {
+  Bodies b;
+  if (!xv || !mu || !rcrit || !stat || nsteps < 0 || step0 < 0 || p->eject_every < 0 ||
+      !make_bodies(p, nbig, nsmall, mu, rcrit, rp_km, rhop, b))
+    return ORC_ERR_ARG;
+  if (p->gas.enabled && nsmall > 0 && (!rp_km || !rhop)) return ORC_ERR_ARG;
+  b.stat.assign(stat, stat + b.n);
+  State<double> s;
+  load_state(s, b.n, xv);
+  GasT<double> g = make_gas<double>(p->gas, p->G);
+  StepStats st;
+  int lc = 0;
+  int err = ORC_OK;
+  for (int k = 0; k < nsteps && !err; ++k) {
+    err = hybrid_step(*p, g, b, s, ever_flag, k, nullptr, 0, &lc, st);
+    if (!err && p->eject_every > 0 && (step0 + k + 1) % p->eject_every == 0) eject_check(b, s);
+  }
+  store_state(s, xv);
+  std::copy(b.mu.begin(), b.mu.end(), mu);
+  std::copy(b.stat.begin(), b.stat.end(), stat);
+  if (stats) {
+    stats[0] = st.pairs; stats[1] = st.groups; stats[2] = st.max_bs_sub; stats[3] = st.max_kep_iter;
+  }
+  return err;
+}
+
+int orc_eject(const orc_params* p, int nbig, int n, const double* xv, double* mu,
+              signed char* stat, int* n_new) {
+  Bodies b;
+  if (!p || !xv || !mu || !stat || nbig < 0 || n < nbig) return ORC_ERR_ARG;
+  b.nbig = nbig;
+  b.nsmall = n - nbig;
+  b.n = n;
+  b.mu0 = p->G * p->m_star;
+  b.mu.assign(mu, mu + n);
+  b.stat.assign(stat, stat + n);
+  State<double> s;
+  load_state(s, n, xv);
+  const int k = eject_check(b, s);
+  std::copy(b.mu.begin(), b.mu.end(), mu);
+  std::copy(b.stat.begin(), b.stat.end(), stat);
+  if (n_new) *n_new = k;
+  return ORC_OK;
+}
+
+int orc_elements(int n, const double* gm, const double* xv, double* out) {
+  if (n < 0 || !gm || !xv || !out) return ORC_ERR_ARG;
+  for (int j = 0; j < n; ++j) {
+    double x[3], v[3];
+    for (int k = 0; k < 3; ++k) {
+      x[k] = xv[(size_t)k * n + j];
+      v[k] = xv[(size_t)(3 + k) * n + j];
+    }
+    const Elements el = x2el(gm[j], x, v);
+    const double o[6] = {el.q, el.e, el.i, el.varpi, el.node, el.M};
+    for (int k = 0; k < 6; ++k) out[(size_t)k * n + j] = o[k];
+  }
+  return ORC_OK;
 }
 
 int orc_energy(const orc_params* p, int nbig, int n, const double* xv, const double* mu, double* E,

@@ -57,6 +57,8 @@ typedef struct {
   int kepler_max_iter;  /* iteration cap of the universal Kepler solve */
   int bs_max_sub;       /* cap on BS macro sub-steps per group and step */
   int pair_cap;         /* capacity of the encounter pair list */
+  int eject_every;      /* ejection test (Sec. 3.5) after every step whose global index
+                           k + 1 is a multiple of this; 0: never */
   orc_gas gas;
 } orc_params;
 
@@ -123,7 +125,9 @@ int orc_detect(const orc_params* p, int nbig, int n, const double* xv0,
 int orc_bs_group(const orc_params* p, int nb, const double* mu,
                  const double* rcrit, double* xv, double h, int* nsub);
 
-/* nsteps hybrid steps of the full system, in place (DH state).
+/* nsteps hybrid steps of the full system, in place (DH state), the first
+ * one with global index 0 (with p->eject_every > 0 the ejection test of
+ * orc_step_ex runs on its schedule; removals are not returned).
  * ever_flag[n] (may be NULL) is OR-ed with 1 for every body flagged in any
  * step.  pair_log (may be NULL) receives (step, i, j) triples, up to
  * log_cap of them; log_count receives how many were found in total.
@@ -133,6 +137,30 @@ int orc_step(const orc_params* p, int nbig, int nsmall, double* xv,
              const double* mu, const double* rcrit, const double* rp_km,
              const double* rhop, int nsteps, unsigned char* ever_flag,
              int* pair_log, int log_cap, int* log_count, long long* stats);
+
+/* As orc_step, with bodies that can be removed (Sec. 3.5).  stat[n] (in/out):
+ * 0 for a body in the integration, -3 for one removed as ejected; a removed
+ * body keeps its state and takes no further part in the step.  mu[n] (in/out):
+ * an ejected massive body's mu becomes 0.  step0 is the global index of the
+ * first step (the ejection test follows steps with (step0 + k + 1) a multiple
+ * of p->eject_every). */
+int orc_step_ex(const orc_params* p, int nbig, int nsmall, double* xv, double* mu,
+                const double* rcrit, const double* rp_km, const double* rhop, int nsteps,
+                long long step0, signed char* stat, unsigned char* ever_flag, long long* stats);
+
+/* The ejection test of Sec. 3.5 on a DH state: every body still in the
+ * integration whose heliocentric osculating eccentricity (gm = G(m0 + m) for
+ * massive bodies, G m0 for planetesimals) is >= 1 gets stat -3 and mu 0.
+ * Returns the number of bodies removed in *n_new. */
+int orc_eject(const orc_params* p, int nbig, int n, const double* xv, double* mu,
+              signed char* stat, int* n_new);
+
+/* Osculating heliocentric elements of n bodies about gm[j] from the
+ * heliocentric state xv (6 x n): out (6 x n) rows q [AU], e, i [rad],
+ * varpi = longitude of pericentre, Omega = longitude of the node, M = mean
+ * anomaly (e < 1: in [0, 2 pi); e > 1: e sinh F - F; e = 1: Barker's
+ * D + D^3/3 with D = tan(f/2)). */
+int orc_elements(int n, const double* gm, const double* xv, double* out);
 
 /* Energy (M_sun AU^2 d^-2) and angular momentum of the massive bodies. */
 int orc_energy(const orc_params* p, int nbig, int n, const double* xv,

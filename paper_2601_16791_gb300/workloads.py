@@ -55,7 +55,7 @@ def default_gas(enabled=False, sigma1=1700.0, gamma=1.0, disk_gravity=False):
 
 def default_params(dt, gas=None, pair_cap=1 << 20):
     return dict(G=G, m_star=1.0, dt=float(dt), rcrit_hill=3.0, bs_tol=1e-12,
-                kepler_max_iter=64, bs_max_sub=4096, pair_cap=int(pair_cap),
+                kepler_max_iter=64, bs_max_sub=4096, pair_cap=int(pair_cap), eject_every=0,
                 gas=gas if gas is not None else default_gas(False))
 
 
@@ -102,6 +102,37 @@ def elements_to_xv(gm, a, e, inc, node, peri, M):
     r31 = sw * si
     r32 = cw * si
     out = np.empty((6,) + a.shape)
+    out[0] = r11 * xo + r12 * yo
+    out[1] = r21 * xo + r22 * yo
+    out[2] = r31 * xo + r32 * yo
+    out[3] = r11 * vxo + r12 * vyo
+    out[4] = r21 * vxo + r22 * vyo
+    out[5] = r31 * vxo + r32 * vyo
+    return out
+
+
+def pericentre_to_xv(gm, q, e, inc, node, peri):
+    """Heliocentric state at pericentre from (q, e, inc, node, peri), for any
+    e >= 0 (elliptic, parabolic or hyperbolic orbits)."""
+    gm, q, e, inc, node, peri = (np.asarray(v, dtype=np.float64) for v in
+                                 np.broadcast_arrays(gm, q, e, inc, node, peri))
+    zero = np.zeros_like(q)
+    return elements_rotate(q, zero, zero, np.sqrt(gm * (1.0 + e) / q), inc, node, peri)
+
+
+def elements_rotate(xo, yo, vxo, vyo, inc, node, peri):
+    """Orbit-plane position and velocity (pericentre along x) rotated by
+    R_z(node) R_x(inc) R_z(peri) into the reference frame."""
+    cO, sO = np.cos(node), np.sin(node)
+    cw, sw = np.cos(peri), np.sin(peri)
+    ci, si = np.cos(inc), np.sin(inc)
+    r11 = cO * cw - sO * sw * ci
+    r12 = -cO * sw - sO * cw * ci
+    r21 = sO * cw + cO * sw * ci
+    r22 = -sO * sw + cO * cw * ci
+    r31 = sw * si
+    r32 = cw * si
+    out = np.empty((6,) + np.shape(xo))
     out[0] = r11 * xo + r12 * yo
     out[1] = r21 * xo + r22 * yo
     out[2] = r31 * xo + r32 * yo
@@ -183,6 +214,39 @@ def semiactive_2000big_200k(seed=2, nbig=2000, nsmall=200_000, nsteps=2000):
     return _assemble("semiactive_2000big_200k", default_params(6.0), m, xb, xs, rp, rho, nsteps)
 
 
+def scatter_2giant(seed=5, nsmall=4000, nsteps=500, eject_every=10):
+    """Two giants (Jupiter and Saturn masses at 5.2 and 9.5 AU) scattering a
+    planetesimal swarm on giant-crossing orbits, with the ejection test of
+    Sec. 3.5 every `eject_every` steps: half the planetesimals elliptic with
+    a ~ U[4, 12] AU and e ~ U[0.3, 0.95], a quarter near-parabolic (e ~
+    U[0.97, 1.03]) and a quarter hyperbolic (e ~ U[1.05, 1.5]), the last two
+    started at pericentre q ~ U[3, 8] AU.  No gas; dt = 8 d."""
+    rng = np.random.default_rng(seed)
+    m = np.array([M_JUP, 0.3 * M_JUP])
+    node, peri, M = _angles(rng, 2)
+    xb = elements_to_xv(G * (1.0 + m), np.array([5.2, 9.5]), 0.05, math.radians(1.0), node, peri,
+                        M)
+    k1 = nsmall // 2
+    k2 = nsmall // 4
+    k3 = nsmall - k1 - k2
+    a = rng.uniform(4.0, 12.0, k1)
+    e = rng.uniform(0.3, 0.95, k1)
+    inc = rng.rayleigh(0.02, k1)
+    node, peri, M = _angles(rng, k1)
+    x1 = elements_to_xv(G, a, e, inc, node, peri, M)
+    parts = [x1]
+    for k, lo, hi in ((k2, 0.97, 1.03), (k3, 1.05, 1.5)):
+        node, peri, _ = _angles(rng, k)
+        parts.append(pericentre_to_xv(G, rng.uniform(3.0, 8.0, k), rng.uniform(lo, hi, k),
+                                      rng.rayleigh(0.02, k), node, peri))
+    xs = np.concatenate(parts, axis=1)
+    params = default_params(8.0)
+    params["eject_every"] = int(eject_every)
+    rp = np.full(nsmall, 1.0)
+    rho = np.full(nsmall, 1.0)
+    return _assemble("scatter_2giant", params, m, xb, xs, rp, rho, nsteps)
+
+
 def adjoint_4core_50k(seed=4, nbig=4, nsmall=50_000, nsteps=2000, checkpoint_every=50):
     rng = np.random.default_rng(seed)
     m, xb = _cores(rng, nbig)
@@ -215,6 +279,7 @@ WORKLOADS = {
     "gas_4core_100k": gas_4core_100k,
     "semiactive_2000big_200k": semiactive_2000big_200k,
     "adjoint_4core_50k": adjoint_4core_50k,
+    "scatter_2giant": scatter_2giant,
 }
 
 
