@@ -83,6 +83,9 @@ typedef struct {
   int kepler_max_iter;  /* Kepler iteration cap */
   int bs_max_sub;       /* Bulirsch-Stoer macro sub-step cap per group and step */
   int pair_cap;         /* encounter pair capacity */
+  int eject_every;      /* ejection test (Sec. 3.5, see mx_check_ejections) after every step
+                           whose global index (steps taken, counting it) is a multiple of
+                           this; 0: never.  The same for every system of a batch. */
   mx_gas gas;
 } mx_params;
 
@@ -176,12 +179,15 @@ void mx_destroy(mx_system* s);
  * half jump, drift, detection, Bulirsch-Stoer of encounter groups, half jump,
  * half kick).  Runs as CUDA graphs on the system's stream and synchronises
  * once at the end to read the status word.  n_steps >= 0; n_steps = 0 only
- * brings deferred planetesimals up to date (see mx_set_defer_window).
+ * brings deferred planetesimals up to date (see mx_set_defer_window).  With
+ * eject_every > 0 the ejection test of mx_check_ejections follows every step
+ * on that schedule (the step then ends with its own half kick, and the next
+ * one starts with a fresh half kick).
  */
 mx_status mx_step(mx_system* s, int n_steps);
 
 /* Kernels of one step, in launch order, for mx_step_profiled. */
-#define MX_NKERN 9
+#define MX_NKERN 10
 #define MX_K_PREP 0       /* momentum + staged big positions */
 #define MX_K_JUMP_KICK 1  /* jump + half kick(s): gravity and drag */
 #define MX_K_JUMP_DRIFT 2 /* jump + Kepler drift */
@@ -191,6 +197,7 @@ mx_status mx_step(mx_system* s, int n_steps);
 #define MX_K_BS 6         /* Bulirsch-Stoer of the groups */
 #define MX_K_CATCHUP 7    /* deferred planetesimals: window-end and settling catch-ups */
 #define MX_K_CATCHUP_SIDE 8 /* carried planetesimals on the side stream (overlaps the steps) */
+#define MX_K_EJECT 9      /* ejection test (steps on the eject_every schedule) */
 
 /*
  * mx_step_profiled -- the same n_steps as mx_step, launched kernel by kernel
@@ -358,6 +365,37 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
 /* Reverse of the set-up transform: cotangent of the initial DH state ->
  * cotangent of the initial heliocentric state (6xN device buffers). */
 mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_grad_helio);
+
+/* ------------------------------------------------------------------------
+ * Ejection and orbital elements (Sec. 3.5).  A body is ejected when its
+ * osculating heliocentric orbit is unbound, e >= 1, with gm = G (m0 + m) for
+ * a massive body and G m0 for a planetesimal.  An ejected body is removed
+ * from the integration (its status becomes MX_STAT_EJECTED): it keeps the
+ * state it had at the test and takes no further part in the kick, the jump,
+ * the drift or the encounter search; a massive one also loses its mass
+ * (mu = 0), so it no longer pulls on the others and drops out of the momentum
+ * P and of mx_energy.  mx_accel gives it zero acceleration.  Systems with
+ * removed bodies, or with eject_every > 0, have no adjoint (MX_ERR_ARG).
+ * ------------------------------------------------------------------------ */
+#define MX_STAT_EJECTED (-3)
+
+/* Runs the ejection test now on the current state (heliocentric velocities
+ * v_b + P/m0 with P the momentum of that state); *n_removed (host, may be
+ * NULL) gets the number of bodies it removed, over all systems. */
+mx_status mx_check_ejections(mx_system* s, int* n_removed);
+
+/* host_stat [N] (host, may be NULL): 0 for a body in the integration,
+ * MX_STAT_EJECTED for a removed one.  n_removed [n_sys] (host, may be NULL):
+ * removed bodies of each system (the count of status < 0 over its bodies). */
+mx_status mx_body_status(mx_system* s, signed char* host_stat, int* n_removed);
+
+/* Osculating heliocentric elements of every body (removed ones: of the state
+ * they keep) into dev_el (6xN device buffer, caller-owned), rows: q [AU], e,
+ * i [rad], longitude of pericentre, longitude of the node, mean anomaly
+ * (e < 1: in [0, 2 pi); e > 1: e sinh F - F; e = 1: D + D^3/3 with D the
+ * tangent of half the true anomaly).  Node 0 for an orbit in the reference
+ * plane; angles in [0, 2 pi). */
+mx_status mx_elements(mx_system* s, double* dev_el);
 
 /* Sizes of the system. */
 mx_status mx_sizes(mx_system* s, int* n_big, int* n_small);

@@ -26,6 +26,7 @@
 #include "mx_encounter.cuh"
 #include "mx_kepler.cuh"
 #include "mx_kernels.h"
+#include "mx_orbit.cuh"
 #include "mx_physics.cuh"
 
 namespace mx {
@@ -1175,6 +1176,9 @@ __global__ void __launch_bounds__(32) k_bs(Dev d) {
 // budgets of 1, 2 and 4 sub-steps made the main-stream pass (which the step
 // waits for) 2.2-2.5x longer and the step about 6% slower.
 constexpr int kCatchBudget = 0;
+// Group-size field of a record whose body the ejection test removed during a
+// side-stream pass (the state in the record is the one it keeps).
+constexpr int kRecEjected = -3;
 
 struct CatchArgs {
   int mode;
@@ -1186,14 +1190,16 @@ struct CatchArgs {
   int t_next;           // where the next range starts: a body that reached t_end is kept there
 };
 
+// hmu: the system's big-body mu during the group's slot (the history's,
+// as a big body can be removed after the slot).
 template <int NB>
 __device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, const int* gid,
-                                               double* mu, MemberK* K) {
+                                               const double* hmu, double* mu, MemberK* K) {
 #pragma unroll
   for (int m = 0; m < NB; ++m) {
     const int l = gid[m] - S.off;
     const double rc = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
-    mu[m] = (l < S.nbig) ? d.bmu[S.boff + l] : 0.0;
+    mu[m] = (l < S.nbig) ? hmu[l] : 0.0;
     K[m].rc = rc;
     K[m].rc2 = rc * rc;
     K[m].rc2lo = 0.01 * (rc * rc);
@@ -1222,11 +1228,11 @@ struct CatchGroup {
 // Three or four bodies: the lane integrator of k_bs_spread on one warp, run
 // to the end of the step.
 template <int NB>
-__device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const CatchGroup& G, int lane,
-                                     double* s6) {
+__device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const CatchGroup& G,
+                                     const double* hmu, int lane, double* s6) {
   double mu[NB];
   MemberK K[NB];
-  load_members_g<NB>(d, S, G.gid, mu, K);
+  load_members_g<NB>(d, S, G.gid, hmu, mu, K);
   GroupRun<NB> g;
 #pragma unroll
   for (int m = 0; m < NB; ++m)
@@ -1246,12 +1252,12 @@ __device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const CatchG
 // lanes, one candidate per warp; three or four: to the end of the step on
 // warp 0, then broadcast).  Returns 1 (done, body state in s6), 0 (rounds ran
 // out, G updated) or -1 (sub-step cap).
-__device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, int max_rounds,
-                            const CatchBlk& B, double* s6) {
+__device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, const double* hmu,
+                            int max_rounds, const CatchBlk& B, double* s6) {
   if (G.nb == 2) {
     double mu[2];
     MemberK K[2];
-    load_members_g<2>(d, S, G.gid, mu, K);
+    load_members_g<2>(d, S, G.gid, hmu, mu, K);
     const Bs2Term t = bs2_term(B.lane & 3, S.mu0, mu, K);
     GroupRun<2> g;
 #pragma unroll
@@ -1275,7 +1281,8 @@ __device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, int ma
     return r;
   }
   if (B.wq == 0) {
-    const int r = (G.nb == 3) ? catch_bs<3>(d, S, G, B.lane, s6) : catch_bs<4>(d, S, G, B.lane, s6);
+    const int r = (G.nb == 3) ? catch_bs<3>(d, S, G, hmu, B.lane, s6)
+                              : catch_bs<4>(d, S, G, hmu, B.lane, s6);
     if (B.lane == 0) {
       for (int q = 0; q < 6; ++q) B.s_bc[q] = s6[q];
       *B.s_r = r;
@@ -1295,12 +1302,13 @@ __device__ __noinline__ void catch_bs_thread(const Dev& d, const SysDev& S, cons
   const size_t NBs = (size_t)d.NB;
   const double* B0 = d.h_b0 + (size_t)t * 6 * NBs + S.boff;
   const int nb = cnt + 1;
+  const double* hmu = d.h_mu + (size_t)t * NBs + S.boff;
   GroupState G;
   G.nb = nb;
   double Y[6][kMaxGroup];
   for (int m = 0; m < nb; ++m) {
     const bool big = m < cnt;
-    G.mu[m] = big ? d.bmu[S.boff + mem[m]] : 0.0;
+    G.mu[m] = big ? hmu[mem[m]] : 0.0;
     G.rc[m] = big ? d.brc[S.boff + mem[m]] : 0.0;
     for (int q = 0; q < 6; ++q) Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
   }
@@ -1335,6 +1343,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
   }
   const double* B0 = d.h_b0 + (size_t)t * 6 * NBs + S.boff;
   const double* B1 = d.h_b1 + (size_t)t * 6 * NBs + S.boff;
+  const double* hmu = d.h_mu + (size_t)t * NBs + S.boff;
   const float hf = (float)S.h;
   // flagged big bodies, ascending
   int fl[kMaxGroup];
@@ -1343,7 +1352,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
   for (int c0 = 0; c0 < S.nbig; c0 += 32) {
     const int l = c0 + lane;
     bool hit = false;
-    if (l < S.nbig) {
+    if (l < S.nbig && hmu[l] >= 0.0) {   // a body removed by then meets nothing
       const double rcb = d.brc[S.boff + l];
       const float rcf = fmaxf((float)rcb, (float)0.0);
       float bf[12];
@@ -1451,10 +1460,11 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
   const double x = s6[0] + dj[0], y = s6[1] + dj[1], z = s6[2] + dj[2];
   double u = s6[3], v = s6[4], w = s6[5];
   const double* BX = d.h_bx + (size_t)t * 3 * d.NB + S.boff;
+  const double* hmu = d.h_mu + (size_t)t * d.NB + S.boff;
   double ax = 0, ay = 0, az = 0;
   for (int l = 0; l < S.nbig; ++l) {
     const double rc = d.brc[S.boff + l];
-    pair_acc(x - BX[l], y - BX[d.NB + l], z - BX[2 * (size_t)d.NB + l], d.bmu[S.boff + l],
+    pair_acc(x - BX[l], y - BX[d.NB + l], z - BX[2 * (size_t)d.NB + l], fmax(hmu[l], 0.0),
              rc * rc, 0.01 * (rc * rc), 0.1 * rc, (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0, ax, ay, az);
   }
   const int nk = head ? -hk : hk;
@@ -1521,6 +1531,15 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
     }
     d.flags[j] = kn > 0 ? 1 : 0;
   }
+  if (R[2] == kRecEjected) {   // removed during a side-stream pass: the main stream finishes it
+    if (a.mode != 1 && lead) {
+      for (int q = 0; q < 6; ++q) d.xv[q * (size_t)d.N + j] = Cs[3 + q];
+      d.stat[j] = kStatEjected;
+      atomicAdd(d.ej_new, 1);
+      d.lag[j] = 0;
+    }
+    return;
+  }
   // stored pairs are valid only until the next pass over the record (slots are reused)
   kslot = -1;
   kn = 0;
@@ -1540,10 +1559,17 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
     for (int q = 0; q < 6; ++q) s6[q] = Cs[3 + q];
   }
   const int budget = (a.mode == 0) ? kCatchBudget : (1 << 30);
-  bool carried = false;
+  bool carried = false, ejected = false;
+  // the ejection test that follows slot tt, as k_eject runs it (planetesimal:
+  // gm = mu0; P of the slot's kicks)
+  auto eject_after = [&](int tt) {
+    if (!d.h_ej[tt]) return false;
+    const double* P2 = d.h_P + (size_t)tt * 6 * d.nsys + 3 * d.nsys + 3 * sys;
+    return dh_unbound(S.mu0, S.inv_mu0, P2, s6[0], s6[1], s6[2], s6[3], s6[4], s6[5]);
+  };
   for (;;) {
     if (G.nb >= 2) {
-      const int r = catch_bs_any(d, S, G, budget, B, s6);
+      const int r = catch_bs_any(d, S, G, d.h_mu + (size_t)t * d.NB + S.boff, budget, B, s6);
       if (r == 0) {
         carried = true;
         break;
@@ -1551,7 +1577,9 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
       if (r < 0 && lead) atomicOr(d.status, ST_BS);
       G.nb = 0;
       catch_back(d, S, sys, j, t, lead, s6);
+      ejected = eject_after(t);
       ++t;
+      if (ejected) break;
     }
     if (t >= a.t_end) break;
     if (d.h_nkick[t] > 0) {
@@ -1565,7 +1593,18 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
       if (nb >= 2) continue;   // the group runs at the top of the loop
     }
     catch_back(d, S, sys, j, t, lead, s6);
+    ejected = eject_after(t);
     ++t;
+    if (ejected) break;
+  }
+  if (ejected && a.mode != 1) {   // removed (Sec. 3.5), with the state it has now
+    if (lead) {
+      for (int q = 0; q < 6; ++q) d.xv[q * (size_t)d.N + j] = s6[q];
+      d.stat[j] = kStatEjected;
+      atomicAdd(d.ej_new, 1);
+      d.lag[j] = 0;
+    }
+    return;
   }
   if (a.mode != 1 && !carried) {   // up to date: the body rejoins the step
     if (lead) {
@@ -1589,7 +1628,7 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
   double* Os = rec_state(d, ob, oi);
   O[0] = j;
   O[1] = (t >= a.t_end) ? a.t_next : t;
-  O[2] = carried ? G.nb : 0;
+  O[2] = ejected ? kRecEjected : (carried ? G.nb : 0);
   for (int m = 0; m < kLaneMaxNB; ++m) O[3 + m] = carried ? G.gid[m] : 0;
   O[7] = kslot;
   O[8] = kn;

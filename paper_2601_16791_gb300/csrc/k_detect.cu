@@ -22,6 +22,7 @@ struct DetSmem {
   float f[12][kThreads];
   double rc[kThreads];
   float rcf[kThreads];
+  unsigned char out[kThreads];   // big body removed from the integration (Sec. 3.5)
 };
 
 // xv0, xv1: 6 x N endpoint states; keys/count/cap: pair output.
@@ -36,8 +37,9 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
   const SysDev& S = d.sys[t.sys];
   const int N = d.N;
   const int j = t.start + threadIdx.x;
-  // a deferred planetesimal is tested by the window's catch-up instead
-  const bool act = threadIdx.x < t.count && !(d.defer && d.lag[j]);
+  // a deferred planetesimal is tested by the window's catch-up instead; a
+  // removed body meets nothing
+  const bool act = threadIdx.x < t.count && !(d.defer && d.lag[j]) && !removed(d, j);
   const int jl = j - S.off;
   const bool jbig = jl < S.nbig;
   const int lane = threadIdx.x & 31;
@@ -93,12 +95,13 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
       const double rcb = d.brc[S.boff + c0 + threadIdx.x];
       sm.rc[threadIdx.x] = rcb;
       sm.rcf[threadIdx.x] = (float)rcb;
+      sm.out[threadIdx.x] = removed(d, g);
     }
     __syncthreads();
     for (int k = 0; k < cn; ++k) {
       const int il = c0 + k;
       // big-big pairs are tested once, with the lower index as the big one
-      bool ok = act && (!jbig || il < jl);
+      bool ok = act && (!jbig || il < jl) && !sm.out[k];
       bool hit = false;
       if (ok) {
         const float rcf = fmaxf(sm.rcf[k], rcjf);

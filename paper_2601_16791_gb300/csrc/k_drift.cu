@@ -33,6 +33,20 @@ __global__ void __launch_bounds__(kThreads) k_jump_drift(Dev d, double jump_frac
   const int N = d.N;
   const int j = t.start + threadIdx.x;
   if (d.defer && d.lag[j]) return;   // waits for the window's catch-up
+  const int jl = j - S.off;
+  if (removed(d, j)) {   // removed: stays where it is
+    d.flags[j] = 0;
+    if (rec && jl < S.nbig) {   // a history that deferred planetesimals never match
+      const size_t b = S.boff + jl, o0 = (size_t)slot * 6 * d.NB;
+      for (int c = 0; c < 6; ++c) {
+        const double q = d.xv[(size_t)c * N + j];
+        d.h_b0[o0 + (size_t)c * d.NB + b] = q;
+        d.h_b1[o0 + (size_t)c * d.NB + b] = q;
+      }
+      d.h_comp[(size_t)slot * d.NB + b] = -1;
+    }
+    return;
+  }
   double dj[3];
   jump_vec(d.P + 3 * t.sys, S, jump_frac, dj);
   double x = d.xv[j] + dj[0];
@@ -56,7 +70,6 @@ __global__ void __launch_bounds__(kThreads) k_jump_drift(Dev d, double jump_frac
   d.xv[4 * (size_t)N + j] = v;
   d.xv[5 * (size_t)N + j] = w;
   d.flags[j] = 0;
-  const int jl = j - S.off;
   if (rec && jl < S.nbig) {   // the big body's endpoints, for deferred planetesimals
     const size_t b = S.boff + jl, o0 = (size_t)slot * 6 * d.NB;
     const double e0[6] = {d.xv0[j], d.xv0[(size_t)N + j], d.xv0[2 * (size_t)N + j], d.xv0[3 * (size_t)N + j],

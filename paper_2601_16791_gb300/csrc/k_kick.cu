@@ -96,7 +96,10 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int 
   const bool rec = d.defer && nkick > 0 && slot < d.hist_cap;
   if (rec && threadIdx.x == 0) {
     for (int c = 0; c < 3; ++c) d.h_P[(size_t)slot * 6 * d.nsys + 3 * d.nsys + 3 * blockIdx.x + c] = Ps[c];
-    if (blockIdx.x == 0) d.h_nkick[slot] = (jump_frac != 0.0) ? nkick : -nkick;
+    if (blockIdx.x == 0) {
+      d.h_nkick[slot] = (jump_frac != 0.0) ? nkick : -nkick;
+      d.h_ej[slot] = 0;   // k_eject marks the slots an ejection test follows
+    }
   }
   for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
     const int g = S.off + i;
@@ -111,6 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int 
       d.h_bx[o] = bx;
       d.h_bx[o + d.NB] = by;
       d.h_bx[o + 2 * (size_t)d.NB] = bz;
+      d.h_mu[(size_t)slot * d.NB + S.boff + i] = removed(d, g) ? -1.0 : d.bmu[S.boff + i];
     }
   }
 }
@@ -131,8 +135,9 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
   jump_vec(P, S, jump_frac, dj);
   const double kick_h = kick_frac * S.h;
   const int j = t.start + threadIdx.x;
-  // a deferred planetesimal is kicked by the window's catch-up instead
-  const bool act = threadIdx.x < t.count && !(d.defer && d.lag[j]);
+  // a deferred planetesimal is kicked by the window's catch-up instead; a
+  // removed body is not kicked
+  const bool act = threadIdx.x < t.count && !(d.defer && d.lag[j]) && !removed(d, j);
   // the last kernel of a history slot moves on to the next one
   if (d.defer && blockIdx.x == 0 && threadIdx.x == 0) *d.hstep += 1;
   const int jl = j - S.off;
@@ -195,8 +200,9 @@ __global__ void __launch_bounds__(kThreads) k_accel(Dev d, double* acc, int drag
   const SysDev& S = d.sys[t.sys];
   const double* P = d.P + 3 * t.sys;
   const int N = d.N;
-  const bool act = threadIdx.x < t.count;
+  const bool valid = threadIdx.x < t.count;
   const int j = t.start + threadIdx.x;
+  const bool act = valid && !removed(d, j);   // a removed body gets zero
   const int jl = j - S.off;
   double x = 0, y = 0, z = 0, u = 0, v = 0, w = 0, rcj = 0.0;
   if (act) {
@@ -210,8 +216,8 @@ __global__ void __launch_bounds__(kThreads) k_accel(Dev d, double* acc, int drag
   }
   double ax = 0, ay = 0, az = 0;
   if (!drag_only) gravity_all(d, S, sb, act, jl, rcj, x, y, z, ax, ay, az);
-  if (!act) return;
-  const bool drag = S.gas_on && jl >= S.nbig;
+  if (!valid) return;
+  const bool drag = act && S.gas_on && jl >= S.nbig;
   double a[3] = {0.0, 0.0, 0.0};
   if (drag) {
     int kout = 0;

@@ -86,7 +86,7 @@ mx_status status_to_code(unsigned st) {
 bool valid_params(const mx_params* p) {
   return p && std::isfinite(p->G) && p->G > 0 && p->m_star > 0 && std::isfinite(p->dt) &&
          p->rcrit_hill >= 0 && p->bs_tol > 0 && p->kepler_max_iter > 0 && p->bs_max_sub > 0 &&
-         p->pair_cap > 0 && p->pair_cap <= (1 << 26);
+         p->pair_cap > 0 && p->pair_cap <= (1 << 26) && p->eject_every >= 0;
 }
 
 // Per-system constants folded from the parameters.
@@ -155,6 +155,9 @@ struct mx_system {
   cudaEvent_t mk_head[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t mk_step[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   long long step = 0;
+  int eject_every = 0;            // ejection test schedule (Sec. 3.5), 0: none
+  bool removed_any = false;       // a test outside the schedule removed bodies
+  int* d_counts = nullptr;        // [nsys] removed bodies per system
   int bs_blocks = 0;
   int catch_blocks = 0;
   int window = 0;                 // history slots per catch-up of deferred planetesimals (0: off)
@@ -263,6 +266,14 @@ void enqueue_step(mx_system* s, int last, cudaStream_t st, cudaEvent_t* marks) {
 
 void enqueue_head(mx_system* s, cudaStream_t st) { enqueue_head(s, st, nullptr); }
 void enqueue_step(mx_system* s, int last, cudaStream_t st) { enqueue_step(s, last, st, nullptr); }
+
+// The ejection test (Sec. 3.5) follows step number gstep (1-based, global)
+// when it is a multiple of eject_every.  Such a step ends with its own half
+// kick (the last-step form), so that the test sees the state at the step's
+// end and a removed massive body no longer acts in the next step's kick.
+bool eject_after(const mx_system* s, long long gstep) {
+  return s->eject_every > 0 && gstep % s->eject_every == 0;
+}
 
 // Deferral is on for forward runs with a window; recording or replaying the
 // drag branches (kmode != 0) keeps every body on the direct path.
@@ -636,8 +647,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_TRY(dalloc(s, &d.cont_state, (size_t)d.cont_cap * 27));
   // deferred planetesimals: per-step history of the big bodies, records
   {
-    const size_t per_step = (size_t)15 * NB * sizeof(double) + (size_t)NB * sizeof(int) +
-                            (size_t)6 * nsys * sizeof(double) + sizeof(int);
+    const size_t per_step = (size_t)16 * NB * sizeof(double) + (size_t)NB * sizeof(int) +
+                            (size_t)6 * nsys * sizeof(double) + 2 * sizeof(int);
     int hc = kMaxWindow;
     while (hc > 1 && (size_t)hc * per_step > kHistBudget) hc >>= 1;
     d.hist_cap = hc;
@@ -650,6 +661,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
     MX_TRY(dalloc(s, &d.h_b0, (size_t)hc * 6 * NB));
     MX_TRY(dalloc(s, &d.h_b1, (size_t)hc * 6 * NB));
     MX_TRY(dalloc(s, &d.h_bx, (size_t)hc * 3 * NB));
+    MX_TRY(dalloc(s, &d.h_mu, (size_t)hc * NB));
+    MX_TRY(dalloc(s, &d.h_ej, hc));
     MX_TRY(dalloc(s, &d.h_comp, (size_t)hc * NB));
     MX_TRY(dalloc(s, &d.h_nkick, hc));
     MX_TRY(dalloc(s, &d.d_rec, (size_t)3 * d.dcap * mx::kRecInts));
@@ -657,6 +670,9 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
     s->window = std::min(kDefaultWindow, hc / 2);
   }
   MX_TRY(dalloc(s, &d.status, 1));
+  MX_TRY(dalloc(s, &d.stat, N));
+  MX_TRY(dalloc(s, &d.ej_new, 1));
+  MX_TRY(dalloc(s, &s->d_counts, nsys));
   MX_TRY(dalloc(s, &s->d_sys, nsys));
   MX_TRY(dalloc(s, &s->d_tiles, tiles_cap));
   MX_TRY(dalloc(s, &s->d_energy, 7 * (size_t)nsys));
@@ -681,6 +697,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemsetAsync(d.status, 0, sizeof(unsigned), st));
   MX_CUDA(cudaMemsetAsync(d.pair_count, 0, 2 * sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.flags, 0, N, st));
+  MX_CUDA(cudaMemsetAsync(d.stat, 0, N, st));
+  MX_CUDA(cudaMemsetAsync(d.ej_new, 0, sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.ever, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.bb_count, 0, sizeof(unsigned long long), st));
   MX_CUDA(cudaMemsetAsync(d.kick_ctr, 0, 2 * sizeof(int), st));
@@ -723,6 +741,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   mx::configure_detect();
   mx::configure_kick();
   mx::configure_bs();
+  mx::configure_orbit();
+  s->eject_every = s->params[0].eject_every;
   return sync_status(s);
 }
 
@@ -832,6 +852,8 @@ mx_status mx_init_batch(int n_sys, const mx_params* params, const int* n_big, co
       return fail(MX_ERR_ARG, "gas drag needs rp_km and rho_gcm3");
     for (int i = 0; i < n_big[k]; ++i)
       if (!(m_big[k][i] >= 0.0)) return fail(MX_ERR_ARG, "negative or NaN mass");
+    if (p->eject_every != params[0].eject_every)
+      return fail(MX_ERR_ARG, "eject_every differs between systems");
     total += n_big[k] + n_small[k];
   }
   if (total > (1LL << 30)) return fail(MX_ERR_ARG, "too many bodies");
@@ -947,8 +969,17 @@ mx_status mx_step(mx_system* s, int n_steps) {
   MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
   MX_CUDA(slot_done(s, false, untimed));
   for (int k = 0; k < n_steps; ++k) {
-    MX_CUDA(cudaGraphLaunch(k + 1 == n_steps ? s->g_last : s->g_mid, s->st));
+    const bool test = eject_after(s, s->step + k + 1);
+    MX_CUDA(cudaGraphLaunch((k + 1 == n_steps || test) ? s->g_last : s->g_mid, s->st));
+    if (test) {
+      mx::launch_eject(s->d, 1, s->st);
+      MX_CUDA(cudaGetLastError());
+    }
     MX_CUDA(slot_done(s, true, untimed));
+    if (test && k + 1 < n_steps) {   // the next step starts with its own half kick
+      MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
+      MX_CUDA(slot_done(s, false, untimed));
+    }
   }
   s->step += n_steps;
   return sync_status(s);
@@ -1008,8 +1039,14 @@ mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_byte
     if (e == cudaSuccess) e = slot_done(s, false, timed3);
   }
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
-    const bool last_step = (k + 1 == n_steps);
+    const bool test = eject_after(s, s->step + k + 1);
+    const bool last_step = (k + 1 == n_steps) || test;
     if (k > 0) e = step_open(k);
+    if (e == cudaSuccess && k > 0 && eject_after(s, s->step + k)) {   // after a test: a fresh half kick
+      e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
+      if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
+      if (e == cudaSuccess) e = slot_done(s, false, timed3);
+    }
     if (e == cudaSuccess) e = timed(MX_K_JUMP_DRIFT, [&] { mx::launch_jump_drift(s->d, 0.5, st); });
     if (e == cudaSuccess)
       e = timed(MX_K_DETECT, [&] {
@@ -1020,6 +1057,7 @@ mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_byte
     if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, last_step ? 1 : 2, st); });
     if (e == cudaSuccess)
       e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last_step ? 1 : 2, st); });
+    if (e == cudaSuccess && test) e = timed(MX_K_EJECT, [&] { mx::launch_eject(s->d, 1, st); });
     if (e == cudaSuccess) e = slot_done(s, true, timed3);
     if (e == cudaSuccess) e = step_close();
   }
@@ -1110,17 +1148,21 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
   float ms = 0.f;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+    // a call's first step, and a step after an ejection test, start with a half kick
+    const bool head = (k == 0) || eject_after(s, s->step + k);
+    const bool test = eject_after(s, s->step + k + 1);
     if (flush_bytes > 0) e = cudaMemsetAsync(flush, k & 0xff, flush_bytes, st);
-    if (e == cudaSuccess && k == 0) {
+    if (e == cudaSuccess && head) {
       e = cudaGraphLaunch(s->gt_head, st);
       if (e == cudaSuccess) e = slot_done(s, false, timed3);
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch(k + 1 == n_steps ? s->gt_last : s->gt_mid, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch((k + 1 == n_steps || test) ? s->gt_last : s->gt_mid, st);
+    if (e == cudaSuccess && test) e = timed3(MX_K_EJECT, st, [&] { mx::launch_eject(s->d, 1, st); });
     if (e == cudaSuccess) e = slot_done(s, true, timed3);
     if (e == cudaSuccess) e = cudaEventRecord(e_end, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e_end);
     if (e != cudaSuccess) break;
-    if (k == 0)
+    if (head)
       for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
         e = cudaEventElapsedTime(&ms, s->mk_head[q], s->mk_head[q + 1]);
         sum[kHeadKind[q]] += ms;
@@ -1139,7 +1181,7 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
       cudaEventDestroy(sp.b);
     }
     spans.clear();
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, k == 0 ? s->mk_head[0] : s->mk_step[0], e_end);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, head ? s->mk_head[0] : s->mk_step[0], e_end);
     tot += ms;
   }
   for (auto& sp : spans) {
@@ -1330,6 +1372,46 @@ mx_status mx_set_state_device(mx_system* s, const double* dev_xv) {
   return MX_OK;
 }
 
+mx_status mx_check_ejections(mx_system* s, int* n_removed) {
+  if (!s) return fail(MX_ERR_ARG, "NULL system");
+  MX_TRY(set_device(s));
+  MX_TRY(settle(s));
+  MX_CUDA(cudaMemsetAsync(s->d.ej_new, 0, sizeof(int), s->st));
+  mx::launch_prep(s->d, 0.0, 0, s->st);   // P of the current state
+  mx::launch_eject(s->d, 0, s->st);
+  MX_CUDA(cudaMemcpyAsync(s->h_count, s->d.ej_new, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  MX_TRY(sync_status(s));
+  if (*s->h_count > 0) s->removed_any = true;
+  if (n_removed) *n_removed = *s->h_count;
+  return MX_OK;
+}
+
+mx_status mx_body_status(mx_system* s, signed char* host_stat, int* n_removed) {
+  if (!s) return fail(MX_ERR_ARG, "NULL system");
+  MX_TRY(set_device(s));
+  MX_TRY(settle(s));
+  if (host_stat)
+    MX_CUDA(cudaMemcpyAsync(host_stat, s->d.stat, s->N, cudaMemcpyDeviceToHost, s->st));
+  const int nsys = (int)s->h_sys.size();
+  std::vector<int> counts(nsys, 0);
+  if (n_removed) {
+    mx::launch_stat_count(s->d, s->d_counts, s->st);
+    MX_CUDA(cudaMemcpyAsync(counts.data(), s->d_counts, nsys * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+  }
+  MX_TRY(sync_status(s));
+  if (n_removed) std::copy(counts.begin(), counts.end(), n_removed);
+  return MX_OK;
+}
+
+mx_status mx_elements(mx_system* s, double* dev_el) {
+  if (!s || !dev_el) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_TRY(settle(s));
+  mx::launch_prep(s->d, 0.0, 0, s->st);
+  mx::launch_elements(s->d, dev_el, s->st);
+  return sync_status(s);
+}
+
 mx_status mx_fp64_peak(void* cuda_stream, double ms_target, double* tflops) {
   if (!tflops || !(ms_target > 0)) return fail(MX_ERR_ARG, "invalid arguments");
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -1510,6 +1592,8 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
     return fail(MX_ERR_ARG, "invalid arguments");
   for (auto& y : s->h_sys)
     if (y.dg_on) return fail(MX_ERR_ARG, "disk gravity is not differentiated by the adjoint");
+  if (s->eject_every > 0 || s->removed_any)
+    return fail(MX_ERR_ARG, "the adjoint does not follow bodies removed by ejection");
   MX_TRY(set_device(s));
   MX_TRY(settle(s));
   MX_TRY(ensure_adjoint(s));

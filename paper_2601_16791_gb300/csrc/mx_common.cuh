@@ -29,6 +29,8 @@ constexpr int kMaxBigPairs = 512; // big-big encounter pairs handled per step
 // the direct path's order), so with many big bodies a replay costs more than
 // the encounter it moves off the step.
 constexpr int kDeferMaxBig = 64;
+// Status of a body removed from the integration as ejected (Sec. 3.5).
+constexpr signed char kStatEjected = -3;
 
 // Device status bits, OR-ed by kernels and turned into mx_status on the host.
 enum : unsigned {
@@ -102,6 +104,11 @@ struct Dev {
   int kwords;      // 32-bit words per half kick
   int kcap;        // half kicks the bit array holds
   unsigned* status;
+  // Ejection (Sec. 3.5): a body with stat != 0 is out of the integration; it
+  // keeps its state and every kernel of the step passes it by.  A removed
+  // big body has mu = 0.
+  signed char* stat;   // [N] 0, or kStatEjected
+  int* ej_new;         // bodies removed by ejection tests since the host last cleared it
   const SysDev* sys;
   const Tile* tiles;
   int N, NB, nsys, ntiles;
@@ -126,6 +133,8 @@ struct Dev {
   double* h_b0;        // [hist_cap][6][NB] big bodies after jump 1 (pre-drift)
   double* h_b1;        // [hist_cap][6][NB] big bodies after the drift (detection endpoint)
   double* h_bx;        // [hist_cap][3][NB] big positions after jump 2 (kick sources)
+  double* h_mu;        // [hist_cap][NB] big mu during the slot, -1 for a removed body
+  int* h_ej;           // [hist_cap] 1: the ejection test follows the slot
   int* h_comp;         // [hist_cap][NB] big group of each big body, -1 for none
   int* h_nkick;        // [hist_cap] half kicks ending the slot; -1: a call's leading half kick
   int* d_rec;          // [3][dcap][kRecInts] records: bank 0 deferred in this window,
@@ -196,6 +205,12 @@ __device__ __forceinline__ double rcp_d(double x) {
 }
 
 __device__ __forceinline__ bool finite_d(double a) { return isfinite(a); }
+
+// A body removed from the integration (Sec. 3.5).  Detection also runs on
+// a Dev without bodies' status (the no-alloc entry), where nobody is removed.
+__device__ __forceinline__ bool removed(const Dev& d, int j) {
+  return d.stat != nullptr && d.stat[j] != 0;
+}
 
 // Jump displacement (h/2) P / m0 of the step's democratic-heliocentric split
 // (Sec. 2.1.3: momentum of massive bodies only).  Every kernel that applies

@@ -12,6 +12,7 @@ void configure_drift();
 void configure_detect();
 void configure_kick();
 void configure_bs();
+void configure_orbit();
 
 // k_init.cu / k_misc.cu
 void launch_init_sys(const Dev& d, int do_rcrit, double rcrit_hill, cudaStream_t st);
@@ -49,6 +50,11 @@ void launch_bs(const Dev& d, int nblocks, cudaStream_t st);
 void launch_catchup(const Dev& d, int nblocks, int mode, int bank_a, int bank_b, int bank_out,
                     int t_end, int tl, int next_slot, int t_next, cudaStream_t st);
 
+// k_orbit.cu (Sec. 3.5): ejection test (scheduled = 1 after a step), elements
+// (6 x N), removed bodies per system
+void launch_eject(const Dev& d, int scheduled, cudaStream_t st);
+void launch_elements(const Dev& d, double* out, cudaStream_t st);
+void launch_stat_count(const Dev& d, int* out, cudaStream_t st);
 
 // k_adjoint.cu
 void launch_adjoint_step(const Dev& d, const Adj& a, cudaStream_t st);

@@ -39,7 +39,8 @@ class MxGas(ctypes.Structure):
 
 class MxParams(ctypes.Structure):
     _fields_ = [("G", _D), ("m_star", _D), ("dt", _D), ("rcrit_hill", _D), ("bs_tol", _D),
-                ("kepler_max_iter", _I), ("bs_max_sub", _I), ("pair_cap", _I), ("gas", MxGas)]
+                ("kepler_max_iter", _I), ("bs_max_sub", _I), ("pair_cap", _I),
+                ("eject_every", _I), ("gas", MxGas)]
 
 
 class MxError(RuntimeError):
@@ -86,6 +87,9 @@ _SIGS = {
     "mx_loss_semimajor": (_I, [_P, _P, _P, _P, _P, _P]),
     "mx_adjoint_step": (_I, [_P, _P, ctypes.c_longlong, _P, _P]),
     "mx_adjoint_init": (_I, [_P, _P, _P]),
+    "mx_check_ejections": (_I, [_P, _P]),
+    "mx_body_status": (_I, [_P, _P, _P]),
+    "mx_elements": (_I, [_P, _P]),
 }
 
 
@@ -141,7 +145,8 @@ def make_params(cfg) -> MxParams:
                 g["gamma_c"], g["mu_mol"], g["sigma_mol_cm2"], g["cd_scale"], int(g["enabled"]),
                 int(g["cd_mode"]), int(g.get("disk_gravity", False)), 0)
     return MxParams(cfg["G"], cfg["m_star"], cfg["dt"], cfg["rcrit_hill"], cfg["bs_tol"],
-                    int(cfg["kepler_max_iter"]), int(cfg["bs_max_sub"]), int(cfg["pair_cap"]), gas)
+                    int(cfg["kepler_max_iter"]), int(cfg["bs_max_sub"]), int(cfg["pair_cap"]),
+                    int(cfg.get("eject_every", 0)), gas)
 
 
 # ------------------------------------------------------------ C-named calls
@@ -168,7 +173,7 @@ def mx_step(sys, n_steps):
 
 
 KERNELS = ("k_prep", "k_jump_kick", "k_jump_drift", "k_detect", "k_sort_keys", "k_groups", "k_bs",
-           "k_catchup", "k_catchup_side")
+           "k_catchup", "k_catchup_side", "k_eject")
 
 
 def mx_step_profiled(sys, n_steps):
@@ -323,6 +328,30 @@ def mx_defer_stats(sys):
     _check(load().mx_defer_stats(sys, ctypes.byref(w), ctypes.byref(mw), ctypes.byref(n),
                                  ctypes.byref(c)), "mx_defer_stats")
     return w.value, mw.value, n.value, c.value
+
+
+MX_STAT_EJECTED = -3
+
+
+def mx_check_ejections(sys):
+    """Runs the ejection test (Sec. 3.5) now; returns the bodies it removed."""
+    k = ctypes.c_int(0)
+    _check(load().mx_check_ejections(sys, ctypes.byref(k)), "mx_check_ejections")
+    return k.value
+
+
+def mx_body_status(sys, n, n_sys=1):
+    """(stat [n] int8: 0 or MX_STAT_EJECTED, removed bodies per system [n_sys])."""
+    stat = np.zeros(n, dtype=np.int8)
+    cnt = np.zeros(n_sys, dtype=np.int32)
+    _check(load().mx_body_status(sys, _hptr(stat), _hptr(cnt)), "mx_body_status")
+    return stat, cnt
+
+
+def mx_elements(sys, dev_el):
+    """Osculating heliocentric elements into dev_el (6 x N CUDA float64 tensor):
+    q, e, i, longitude of pericentre, node, mean anomaly."""
+    _check(load().mx_elements(sys, _dptr(dev_el)), "mx_elements")
 
 
 class Batch:

@@ -47,3 +47,18 @@ def test_kernels_are_sm_103a_native_source():
     src = " ".join(open(p).read() for p in glob.glob(os.path.join(ROOT, "paper_2601_16791_gb300", "*.py")))
     for banned in ("import triton", "torch.compile", "import oracle", "from oracle"):
         assert banned not in src
+
+
+def test_ejection_schedule_is_checked_on_the_host():
+    """A negative eject_every, or a batch whose systems disagree on it, is
+    refused before any device work (MX_ERR_ARG)."""
+    from paper_2601_16791_gb300 import mx, workloads as W
+    w = W.scatter_2giant(nsmall=10, eject_every=5)
+    bad = mx.make_params(dict(w.params, eject_every=-1))
+    with pytest.raises(mx.MxError) as e:
+        mx.mx_init_system(bad, w.nbig, w.nsmall, w.m_big, w.xv_helio)
+    assert e.value.status == "MX_ERR_ARG"
+    w0 = W.scatter_2giant(nsmall=10, eject_every=0)
+    with pytest.raises(mx.MxError) as e:
+        mx.mx_init_batch([w, w0])
+    assert e.value.status == "MX_ERR_ARG" and "eject_every" in str(e.value)
