@@ -363,6 +363,50 @@ def adjoint_leg(nsteps=200, every=50):
             "forward_step_ms": f_ms, "adjoint_over_forward_step": a_ms / f_ms}
 
 
+def eject_leg(steps=200):
+    """The ejection test of Sec. 3.5 on the gas disk (4 cores + 100,000
+    planetesimals): step time with the test after every step and without it,
+    the test's own launch time against the bytes it must read (the 6 state
+    doubles and 2 status bytes of every body), and one element conversion of
+    every body (mx_elements: momentum + k_elements)."""
+    import torch
+    from paper_2601_16791_gb300 import mx, workloads as W
+    st = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {"workload": WORKLOAD_TEXT, "steps": steps}
+    for every in (0, 1):
+        w = W.make(WORKLOAD)
+        w.params = dict(w.params, eject_every=every)
+        s = mx.System(w, stream=st.cuda_stream)
+        mx.mx_step_timed(s.h, 5, flush)
+        mx.mx_step_timed(s.h, 0, flush)
+        ms, cnt, tot = mx.mx_step_timed(s.h, steps, flush)
+        _, _, tot0 = mx.mx_step_timed(s.h, 0, flush)
+        key = "every_step" if every else "none"
+        out[f"ms_per_step_{key}"] = (tot + tot0) / steps
+        if every:
+            n_launch = max(1, cnt["k_eject"])
+            t = ms["k_eject"] / n_launch
+            out["k_eject_launches"] = cnt["k_eject"]
+            out["k_eject_us"] = 1e3 * t
+            out["k_eject_gbs"] = 50.0 * w.n / (t * 1e-3) / 1e9
+            out["removed"] = int(mx.mx_body_status(s.h, w.n)[1][0])
+            el = torch.empty((6, w.n), dtype=torch.float64, device="cuda")
+            mx.mx_elements(s.h, el)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                mx.mx_elements(s.h, el)
+            e1.record()
+            torch.cuda.synchronize()
+            out["elements_us"] = 1e3 * e0.elapsed_time(e1) / 20
+        s.close()
+    out["test_overhead_per_step"] = out["ms_per_step_every_step"] / out["ms_per_step_none"] - 1.0
+    out["timing"] = ("mx_step_timed (graphs, CUDA events, L2 flushed before every step); "
+                     "mx_elements: CUDA events around 20 calls (each ends with a status read)")
+    return out
+
+
 # ------------------------------------------------------------------- main
 def run_mx(args):
     import torch
@@ -488,6 +532,10 @@ def run_mx(args):
             line["adjoint"] = adjoint_leg()
         except Exception as exc:
             line["adjoint"] = {"error": str(exc)[:300]}
+        try:
+            line["ejection"] = eject_leg()
+        except Exception as exc:
+            line["ejection"] = {"error": str(exc)[:300]}
     if not args.no_cpu_baseline:
         cb, _, _ = oracle_rate(w, 12.0)
         line["cpu_baseline"] = cb
