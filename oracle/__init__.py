@@ -34,6 +34,24 @@ class OrcParams(ctypes.Structure):
                 ("eject_every", _I), ("gas", OrcGas)]
 
 
+class OrcGrowth(ctypes.Structure):
+    _fields_ = [("m0", _D), ("mc", _D), ("mf", _D), ("tau_c", _D), ("tau_g", _D),
+                ("delta_r", _D), ("grows", _I), ("reserved", _I)]
+
+
+def make_growth(g, nbig):
+    """OrcGrowth[nbig] from a dict of per-big arrays (m0, mc, mf, tau_c, tau_g,
+    delta_r, grows), or None."""
+    if g is None:
+        return None
+    arr = (OrcGrowth * nbig)()
+    for i in range(nbig):
+        arr[i] = OrcGrowth(float(g["m0"][i]), float(g["mc"][i]), float(g["mf"][i]),
+                           float(g["tau_c"][i]), float(g["tau_g"][i]), float(g["delta_r"][i]),
+                           int(g["grows"][i]), 0)
+    return arr
+
+
 ERRORS = {0: "ok", 1: "bad argument", 2: "Kepler solve did not converge",
           3: "Bulirsch-Stoer did not converge", 4: "pair list overflow", 5: "non-finite state"}
 
@@ -73,7 +91,9 @@ def lib():
             "orc_bs_group": (_I, [_P, _I, _P, _P, _P, _D, _P]),
             "orc_step": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _P, _P]),
             "orc_step_ex": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, ctypes.c_longlong, _P, _P,
-                                 _P]),
+                                 _D, _P, _P]),
+            "orc_gas_drag_gap": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P]),
+            "orc_grow_state": (_I, [_P, _I, _I, _P, _P, _P, _P, _D, _D, _P, _P, _P, _P, _P]),
             "orc_eject": (_I, [_P, _I, _I, _P, _P, _P, _P]),
             "orc_elements": (_I, [_I, _P, _P, _P]),
             "orc_energy": (_I, [_P, _I, _I, _P, _P, _P, _P]),
@@ -174,6 +194,17 @@ def gas_drag(p, nbig, xv, mu, rp_km, rhop):
 GAS_STATE_KEYS = ("sigma", "rho_g", "H_au", "cs", "vk", "eta", "vg", "hr")
 
 
+def gas_drag_gap(p, nbig, xv, mu, rp_km, rhop, gap_w, gap_f):
+    """Drag on the small bodies (3 x nsmall) with gaps around the massive ones."""
+    xv, mu, rp_km, rhop = _f64(xv), _f64(mu), _f64(rp_km), _f64(rhop)
+    gap_w, gap_f = _f64(gap_w), _f64(gap_f)
+    nsmall = xv.shape[1] - nbig
+    acc = np.empty((3, nsmall))
+    _check(lib().orc_gas_drag_gap(ctypes.byref(p), nbig, nsmall, _ptr(xv), _ptr(mu), _ptr(rp_km),
+                                  _ptr(rhop), _ptr(gap_w), _ptr(gap_f), _ptr(acc)), "gas_drag_gap")
+    return acc
+
+
 def gas_state(p, R):
     out = np.empty(8)
     _check(lib().orc_gas_state(ctypes.byref(p), float(R), _ptr(out)), "gas_state")
@@ -262,23 +293,38 @@ def step(p, nbig, xv, mu, rcrit, rp_km, rhop, nsteps, log_cap=0):
     return xv, ever, log[:min(lc.value, log_cap)].copy(), stats
 
 
-def step_ex(p, nbig, xv, mu, rcrit, rp_km, rhop, nsteps, stat=None, step0=0):
+def step_ex(p, nbig, xv, mu, rcrit, rp_km, rhop, nsteps, stat=None, step0=0, growth=None,
+            gap_c=4.0):
     """nsteps hybrid steps with the ejection test of Sec. 3.5 on the schedule
-    p.eject_every, from global step index step0.  Returns (xv, mu, stat, ever):
-    stat is int8, 0 for bodies in the integration and -3 for removed ones;
-    removed massive bodies have mu 0."""
+    p.eject_every and, with growth (a dict of per-big arrays, see make_growth),
+    the growth tracks and gaps of Secs. 3.1 and 3.3, from global step index
+    step0.  Returns (xv, mu, stat, ever, rcrit): stat is int8, 0 for bodies in
+    the integration and -3 for removed ones; removed massive bodies have mu 0."""
     xv = _f64(xv).copy()
     n = xv.shape[1]
     mu = _f64(mu).copy()
-    rcrit = _f64(rcrit)
+    rcrit = _f64(rcrit).copy()
+    gr = make_growth(growth, nbig)
     stat = np.zeros(n, dtype=np.int8) if stat is None else np.ascontiguousarray(stat, np.int8).copy()
     rp = None if rp_km is None else _f64(rp_km)
     rh = None if rhop is None else _f64(rhop)
     ever = np.zeros(n, dtype=np.uint8)
     _check(lib().orc_step_ex(ctypes.byref(p), nbig, n - nbig, _ptr(xv), _ptr(mu), _ptr(rcrit),
-                             _ptr(rp), _ptr(rh), int(nsteps), int(step0), _ptr(stat), _ptr(ever),
-                             None), "step_ex")
-    return xv, mu, stat, ever
+                             _ptr(rp), _ptr(rh), int(nsteps), int(step0), _ptr(stat), gr,
+                             float(gap_c), _ptr(ever), None), "step_ex")
+    return xv, mu, stat, ever, rcrit
+
+
+def grow_state(p, nbig, xv, mu, rcrit, growth, t, gap_c=4.0):
+    """Growth quantities at time t (orc_grow_state): dict of per-big arrays
+    mu, rcrit, gap_w, gap_f, radius."""
+    xv, mu, rcrit = _f64(xv), _f64(mu), _f64(rcrit)
+    out = {k: np.zeros(nbig) for k in ("mu", "rcrit", "gap_w", "gap_f", "radius")}
+    _check(lib().orc_grow_state(ctypes.byref(p), nbig, xv.shape[1], _ptr(xv), _ptr(mu),
+                                _ptr(rcrit), make_growth(growth, nbig), float(gap_c), float(t),
+                                _ptr(out["mu"]), _ptr(out["rcrit"]), _ptr(out["gap_w"]),
+                                _ptr(out["gap_f"]), _ptr(out["radius"])), "grow_state")
+    return out
 
 
 def eject(p, nbig, xv, mu, stat=None):

@@ -105,6 +105,9 @@ struct Bodies {
   // the kick, jump, drift or encounter search; a removed massive body has mu 0.
   std::vector<signed char> stat;
   bool gone(int j) const { return !stat.empty() && stat[j] != 0; }
+  // per massive body: gap half-width (0: no gap) and gas density factor in it
+  // (Sec. 3.1, Eqs. 8-9); empty: no gaps
+  std::vector<double> gap_w, gap_f;
 };
 
 template <class T>
@@ -267,15 +270,17 @@ DiskAt<T> disk_at(const GasT<T>& g, double mu0, const T& R) {
 // v_th = sqrt(8/pi) c_s and lambda = mu_mol m_H / (sigma_mol rho_g).
 // rho_g is the midplane value (Eq. 4) for every height.  Inside R_in the
 // density factor is zero (Sec. 3.1.1), so the drag vanishes.
+// dfac multiplies the gas density (the listing's dens_factor: a gap).
 template <class T>
 void drag_one(const GasT<T>& g, double mu0, const T* x, const T* vh, double rp_km,
-              double rhop, T* acc, double* re_ma) {
+              double rhop, T* acc, double* re_ma, double dfac = 1.0) {
   acc[0] = acc[1] = acc[2] = T(0.0);
   if (re_ma) re_ma[0] = re_ma[1] = 0.0;
   if (!g.raw.enabled) return;
   T R = sqrt(x[0] * x[0] + x[1] * x[1]);
   if (val(R) < g.raw.r_in_au) return;
   DiskAt<T> d = disk_at(g, mu0, R);
+  d.rho_g = d.rho_g * dfac;
   T ux = -x[1] / R, uy = x[0] / R;  // azimuthal unit vector
   T dvx = vh[0] - d.vg * ux;
   T dvy = vh[1] - d.vg * uy;
@@ -352,6 +357,21 @@ void disk_gravity_one(const GasT<T>& g, double mu0, const T* x, T* acc) {
   acc[1] = acc[1] + F * x[1] / R;
 }
 
+// The gas density factor of the Sec. 3.1 listing at cylindrical distance R:
+// 1, or the factor of the last massive body (ascending index) with a gap whose
+// band |R - r_i| < W_i holds R, r_i the body's cylindrical distance now.
+template <class T>
+double gap_factor(const Bodies& b, const State<T>& s, double R) {
+  double f = 1.0;
+  for (int i = 0; i < (int)b.gap_w.size(); ++i) {
+    if (!(b.gap_w[i] > 0.0)) continue;
+    const double xi = val(s.q[0][i]), yi = val(s.q[1][i]);
+    const double ri = std::sqrt(xi * xi + yi * yi);
+    if (R < ri + b.gap_w[i] && R > ri - b.gap_w[i]) f = b.gap_f[i];
+  }
+  return f;
+}
+
 // Drag on every small body, plus the disk's gravity when enabled.  The body's
 // heliocentric velocity is its DH (barycentric) velocity plus P/m0, P the
 // massive-body momentum at kick time.
@@ -369,7 +389,12 @@ void accel_drag(const GasT<T>& g, const Bodies& b, const State<T>& s, const T P[
     T vh[3];
     for (int k = 0; k < 3; ++k) vh[k] = s.q[3 + k][j] + P[k] / b.mu0;
     T acc[3];
-    drag_one(g, b.mu0, x, vh, b.rp_km[j - nb], b.rhop[j - nb], acc, nullptr);
+    double dfac = 1.0;
+    if (!b.gap_w.empty()) {
+      const double xj = val(x[0]), yj = val(x[1]);
+      dfac = gap_factor(b, s, std::sqrt(xj * xj + yj * yj));
+    }
+    drag_one(g, b.mu0, x, vh, b.rp_km[j - nb], b.rhop[j - nb], acc, nullptr, dfac);
     disk_gravity_one(g, b.mu0, x, acc);
     for (int k = 0; k < 3; ++k) a[k][j] = acc[k];
   }
@@ -939,6 +964,78 @@ int eject_check(Bodies& b, const State<double>& s) {
   return removed;
 }
 
+// ------------------------------------------ planet growth (Secs. 3.1, 3.3)
+// Eq. 13 (core phase, t <= tau_c) and Eq. 15 (runaway gas accretion after
+// it); the two meet at M_c, since (e/(e - 1))(1 - 1/e) = 1.
+constexpr double kEuler = 2.718281828459045235360287;
+
+double growth_mass(const orc_growth& g, double t) {
+  if (t <= g.tau_c)
+    return g.m0 + (kEuler / (kEuler - 1.0)) * (g.mc - g.m0) * (1.0 - std::exp(-t / g.tau_c));
+  return g.mc + (g.mf - g.mc) * (1.0 - std::exp(-(t - g.tau_c) / g.tau_g));
+}
+
+// Eq. 14 with k1 = 1 and k2 = 1/4: R_p = G M / (c_s^2/k1 + G M/(k2 R_H)).
+double inflated_radius(double gm, double cs, double rh) {
+  return gm / (cs * cs / 1.0 + gm / (0.25 * rh));
+}
+
+struct GrowOut {
+  double mu, rcrit, gap_w, gap_f, radius;
+};
+
+// Growth quantities of massive body i at time t (see orc_grow_state).  P is
+// the momentum of the state with the masses it has now.
+GrowOut grow_one(const orc_params& p, double mu0, const orc_growth& g, const double* x,
+                 const double* vb, const double P[3], double t, double gap_c) {
+  GrowOut o;
+  const double M = growth_mass(g, t);
+  o.mu = p.G * M;
+  double vh[3];
+  for (int k = 0; k < 3; ++k) vh[k] = vb[k] + P[k] / mu0;
+  const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  const double v2 = vh[0] * vh[0] + vh[1] * vh[1] + vh[2] * vh[2];
+  double a = 1.0 / (2.0 / r - v2 / (mu0 + o.mu));
+  if (!(a > 0.0)) a = r;
+  const double rh = a * std::cbrt(o.mu / (3.0 * mu0));
+  o.rcrit = p.rcrit_hill * rh;
+  const bool runaway = t > g.tau_c;
+  o.gap_w = runaway ? gap_c * rh : 0.0;
+  o.gap_f = runaway ? std::exp(-(t - g.tau_c) / g.tau_g) : 1.0;
+  // sound speed at the body's cylindrical distance (the disk of Sec. 3.1)
+  const double R = std::sqrt(x[0] * x[0] + x[1] * x[1]);
+  const double cs = p.gas.hr_1au * std::pow(R, p.gas.flare) * std::sqrt(mu0 / R);
+  if (!runaway) {
+    o.radius = inflated_radius(o.mu, cs, rh);
+  } else {   // R_c: Eq. 14 as it stood at tau_c, the mass M_c, on the current orbit
+    const double muc = p.G * g.mc;
+    double ac = 1.0 / (2.0 / r - v2 / (mu0 + muc));
+    if (!(ac > 0.0)) ac = r;
+    const double rc = inflated_radius(muc, cs, ac * std::cbrt(muc / (3.0 * mu0)));
+    o.radius = rc - g.delta_r * (1.0 - std::exp(-(t - g.tau_c) / g.tau_g));
+  }
+  return o;
+}
+
+// Applies the growth tracks at time t to the bodies (mu, rcrit, gaps).
+void grow_bodies(const orc_params& p, Bodies& b, const State<double>& s, const orc_growth* g,
+                 double gap_c, double t) {
+  double P[3];
+  momentum(b, s, P);
+  b.gap_w.assign(b.nbig, 0.0);
+  b.gap_f.assign(b.nbig, 1.0);
+  for (int i = 0; i < b.nbig; ++i) {
+    if (!g[i].grows || b.gone(i)) continue;
+    const double x[3] = {s.q[0][i], s.q[1][i], s.q[2][i]};
+    const double v[3] = {s.q[3][i], s.q[4][i], s.q[5][i]};
+    const GrowOut o = grow_one(p, b.mu0, g[i], x, v, P, t, gap_c);
+    b.mu[i] = o.mu;
+    b.rcrit[i] = o.rcrit;
+    b.gap_w[i] = o.gap_w;
+    b.gap_f[i] = o.gap_f;
+  }
+}
+
 // ------------------------------------------------------ set-up and readout
 double semimajor_of(double gm, const double* x, const double* v) {
   const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
@@ -1110,11 +1207,21 @@ int orc_drag_one(const orc_params* p, const double* x3, const double* vh3, doubl
 
 int orc_gas_drag(const orc_params* p, int nbig, int nsmall, const double* xv, const double* mu,
                  const double* rp_km, const double* rhop, double* acc_small) {
-  if (!p || !xv || !mu || !rp_km || !rhop || !acc_small) return ORC_ERR_ARG;
+  return orc_gas_drag_gap(p, nbig, nsmall, xv, mu, rp_km, rhop, nullptr, nullptr, acc_small);
+}
+
+int orc_gas_drag_gap(const orc_params* p, int nbig, int nsmall, const double* xv,
+                     const double* mu, const double* rp_km, const double* rhop,
+                     const double* gap_w, const double* gap_f, double* acc_small) {
+  if (!p || !xv || !mu || !rp_km || !rhop || !acc_small || (!gap_w != !gap_f)) return ORC_ERR_ARG;
   const int n = nbig + nsmall;
   std::vector<double> zero(n, 0.0);
   Bodies b;
   make_bodies(p, nbig, nsmall, mu, zero.data(), rp_km, rhop, b);
+  if (gap_w) {
+    b.gap_w.assign(gap_w, gap_w + nbig);
+    b.gap_f.assign(gap_f, gap_f + nbig);
+  }
   State<double> s;
   load_state(s, n, xv);
   GasT<double> g = make_gas<double>(p->gas, p->G);
@@ -1203,8 +1310,9 @@ int orc_step(const orc_params* p, int nbig, int nsmall, double* xv, const double
 }
 
 int orc_step_ex(const orc_params* p, int nbig, int nsmall, double* xv, double* mu,
-                const double* rcrit, const double* rp_km, const double* rhop, int nsteps,
-                long long step0, signed char* stat, unsigned char* ever_flag, long long* stats) {
+                double* rcrit, const double* rp_km, const double* rhop, int nsteps,
+                long long step0, signed char* stat, const orc_growth* growth, double gap_c,
+                unsigned char* ever_flag, long long* stats) {
   Bodies b;
   if (!xv || !mu || !rcrit || !stat || nsteps < 0 || step0 < 0 || p->eject_every < 0 ||
       !make_bodies(p, nbig, nsmall, mu, rcrit, rp_km, rhop, b))
@@ -1218,16 +1326,49 @@ int orc_step_ex(const orc_params* p, int nbig, int nsmall, double* xv, double* m
   int lc = 0;
   int err = ORC_OK;
   for (int k = 0; k < nsteps && !err; ++k) {
+    if (growth) grow_bodies(*p, b, s, growth, gap_c, (double)(step0 + k) * p->dt);
     err = hybrid_step(*p, g, b, s, ever_flag, k, nullptr, 0, &lc, st);
     if (!err && p->eject_every > 0 && (step0 + k + 1) % p->eject_every == 0) eject_check(b, s);
   }
   store_state(s, xv);
   std::copy(b.mu.begin(), b.mu.end(), mu);
+  std::copy(b.rcrit.begin(), b.rcrit.end(), rcrit);
   std::copy(b.stat.begin(), b.stat.end(), stat);
   if (stats) {
     stats[0] = st.pairs; stats[1] = st.groups; stats[2] = st.max_bs_sub; stats[3] = st.max_kep_iter;
   }
   return err;
+}
+
+int orc_grow_state(const orc_params* p, int nbig, int n, const double* xv, const double* mu,
+                   const double* rcrit, const orc_growth* g, double gap_c, double t,
+                   double* mu_out, double* rcrit_out, double* gap_w, double* gap_f,
+                   double* radius) {
+  if (!p || !xv || !mu || !rcrit || !g || nbig < 0 || n < nbig) return ORC_ERR_ARG;
+  Bodies b;
+  b.nbig = nbig;
+  b.nsmall = n - nbig;
+  b.n = n;
+  b.mu0 = p->G * p->m_star;
+  b.mu.assign(mu, mu + n);
+  State<double> s;
+  load_state(s, n, xv);
+  double P[3];
+  momentum(b, s, P);
+  for (int i = 0; i < nbig; ++i) {
+    GrowOut o{mu[i], rcrit[i], 0.0, 1.0, 0.0};
+    if (g[i].grows) {
+      const double x[3] = {s.q[0][i], s.q[1][i], s.q[2][i]};
+      const double v[3] = {s.q[3][i], s.q[4][i], s.q[5][i]};
+      o = grow_one(*p, b.mu0, g[i], x, v, P, t, gap_c);
+    }
+    if (mu_out) mu_out[i] = o.mu;
+    if (rcrit_out) rcrit_out[i] = o.rcrit;
+    if (gap_w) gap_w[i] = o.gap_w;
+    if (gap_f) gap_f[i] = o.gap_f;
+    if (radius) radius[i] = o.radius;
+  }
+  return ORC_OK;
 }
 
 int orc_eject(const orc_params* p, int nbig, int n, const double* xv, double* mu,

@@ -62,6 +62,17 @@ typedef struct {
   orc_gas gas;
 } orc_params;
 
+/* Growth track of one massive body (Sec. 3.3): core growth to mc at t =
+ * tau_c (Eq. 13), runaway gas accretion towards mf with e-folding time tau_g
+ * (Eq. 15); the radius of Eq. 14 before tau_c and Eq. 16 after it. */
+typedef struct {
+  double m0, mc, mf;    /* masses [Msun] at t = 0, t = tau_c, t -> inf */
+  double tau_c, tau_g;  /* [d] */
+  double delta_r;       /* radius lost in the collapse after tau_c (Eq. 16) [AU] */
+  int grows;            /* 0: the body keeps its mass */
+  int reserved;
+} orc_growth;
+
 void orc_set_threads(int n);
 
 /* Changeover function K(s) for changeover radius rc (Sec. 2.1.3 listing). */
@@ -88,6 +99,12 @@ int orc_momentum(int nbig, int n, const double* xv, const double* mu, double* P3
 int orc_gas_drag(const orc_params* p, int nbig, int nsmall, const double* xv,
                  const double* mu, const double* rp_km, const double* rhop,
                  double* acc_small);
+/* As orc_gas_drag with gaps (Sec. 3.1 listing, Eqs. 8-9): gap_w [nbig]
+ * half-widths (0: none) and gap_f [nbig] density factors, centred on each
+ * massive body's cylindrical distance in xv (both NULL: no gaps). */
+int orc_gas_drag_gap(const orc_params* p, int nbig, int nsmall, const double* xv,
+                     const double* mu, const double* rp_km, const double* rhop,
+                     const double* gap_w, const double* gap_f, double* acc_small);
 /* Disk quantities at cylindrical radius R [AU]:
  * out = {Sigma [g/cm^2], rho_g [g/cm^3], H [AU], c_s [AU/d], v_k [AU/d],
  *        eta, v_g [AU/d], H/r}. */
@@ -127,7 +144,8 @@ int orc_bs_group(const orc_params* p, int nb, const double* mu,
 
 /* nsteps hybrid steps of the full system, in place (DH state), the first
  * one with global index 0 (with p->eject_every > 0 the ejection test of
- * orc_step_ex runs on its schedule; removals are not returned).
+ * orc_step_ex runs on its schedule; removals are not returned).  Masses are
+ * fixed (orc_step_ex follows growth tracks).
  * ever_flag[n] (may be NULL) is OR-ed with 1 for every body flagged in any
  * step.  pair_log (may be NULL) receives (step, i, j) triples, up to
  * log_cap of them; log_count receives how many were found in total.
@@ -138,15 +156,36 @@ int orc_step(const orc_params* p, int nbig, int nsmall, double* xv,
              const double* rhop, int nsteps, unsigned char* ever_flag,
              int* pair_log, int log_cap, int* log_count, long long* stats);
 
-/* As orc_step, with bodies that can be removed (Sec. 3.5).  stat[n] (in/out):
+/* As orc_step, with bodies that can be removed (Sec. 3.5) and masses that can
+ * grow (Sec. 3.3; growth may be NULL).  With growth, every step k (global index
+ * step0 + k) starts by taking mu, rcrit and the gaps from orc_grow_state at
+ * t = (step0 + k) h; the planetesimals' drag then sees Sigma times the gap
+ * factor of the last growing body (ascending index) whose gap, centred on its
+ * cylindrical distance at kick time, holds the planetesimal's cylindrical
+ * distance strictly inside (the Sec. 3.1 listing).  rcrit[n] is in/out.  stat[n] (in/out):
  * 0 for a body in the integration, -3 for one removed as ejected; a removed
  * body keeps its state and takes no further part in the step.  mu[n] (in/out):
  * an ejected massive body's mu becomes 0.  step0 is the global index of the
  * first step (the ejection test follows steps with (step0 + k + 1) a multiple
  * of p->eject_every). */
 int orc_step_ex(const orc_params* p, int nbig, int nsmall, double* xv, double* mu,
-                const double* rcrit, const double* rp_km, const double* rhop, int nsteps,
-                long long step0, signed char* stat, unsigned char* ever_flag, long long* stats);
+                double* rcrit, const double* rp_km, const double* rhop, int nsteps,
+                long long step0, signed char* stat, const orc_growth* growth, double gap_c,
+                unsigned char* ever_flag, long long* stats);
+
+/* What the growth tracks give at time t (Sec. 3.3 and the gap of Sec. 3.1),
+ * from the DH state xv (6 x n) whose momentum is taken with the masses mu:
+ * for every growing massive body i < nbig, mu_out = G M_p(t), rcrit_out =
+ * rcrit_hill R_H with R_H = a (M_p / 3 m0)^(1/3) from the osculating a
+ * (gm = G (m0 + M_p)), the gap half-width gap_c R_H and density factor
+ * exp(-(t - tau_c)/tau_g) once t > tau_c (else half-width 0 and factor 1),
+ * and the radius (Eq. 14 with c_s at the body's cylindrical distance, or
+ * Eq. 16 with R_c = Eq. 14 at M_p = mc).  Bodies that do not grow keep mu and
+ * rcrit and get no gap and radius 0.  Any output may be NULL. */
+int orc_grow_state(const orc_params* p, int nbig, int n, const double* xv, const double* mu,
+                   const double* rcrit, const orc_growth* g, double gap_c, double t,
+                   double* mu_out, double* rcrit_out, double* gap_w, double* gap_f,
+                   double* radius);
 
 /* The ejection test of Sec. 3.5 on a DH state: every body still in the
  * integration whose heliocentric osculating eccentricity (gm = G(m0 + m) for

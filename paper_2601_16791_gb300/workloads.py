@@ -71,6 +71,10 @@ class Workload:
     rhop: np.ndarray           # [nsmall] g/cm^3
     nsteps: int
     checkpoint_every: int = 0
+    # growth tracks of the massive bodies (Sec. 3.3), per-big arrays m0, mc,
+    # mf [Msun], tau_c, tau_g [d], delta_r [AU], grows; None: fixed masses
+    growth: dict = None
+    gap_c: float = 4.0         # gap half-width in Hill radii (Eq. 8)
 
     @property
     def n(self):
@@ -247,6 +251,34 @@ def scatter_2giant(seed=5, nsmall=4000, nsteps=500, eject_every=10):
     return _assemble("scatter_2giant", params, m, xb, xs, rp, rho, nsteps)
 
 
+YEAR = 365.25                        # days
+
+
+def growth_2giant(seed=6, nsmall=24_000, nsteps=1000, tau_c_days=5.0e3 * YEAR,
+                  tau_g_days=1.0e3 * YEAR):
+    """Two forming giants in a gas disk (the paper's first use case, Sec. 4.1):
+    lunar-mass embryos (0.01 M_earth) at 10 and 20 AU grow to 15 M_earth cores
+    in tau_c (Eq. 13), then accrete gas towards 300 and 100 M_earth with
+    e-folding time tau_g (Eq. 15) and open gaps (Eqs. 8-9); planetesimals from
+    1 to 25 AU, 1,000 per AU, r_p log-uniform 1-100 km, rho ~ U[1, 3] g/cm^3.
+    dt = 10 d."""
+    rng = np.random.default_rng(seed)
+    m0 = np.full(2, 0.01 * M_EARTH)
+    node, peri, M = _angles(rng, 2)
+    xb = elements_to_xv(G * (1.0 + m0), np.array([10.0, 20.0]), 0.01, math.radians(0.5), node,
+                        peri, M)
+    xs = _smalls(rng, nsmall, 1.0, 25.0, 0.01, 0.005, G)
+    rp = np.exp(rng.uniform(math.log(1.0), math.log(100.0), nsmall))
+    rho = rng.uniform(1.0, 3.0, nsmall)
+    params = default_params(10.0, default_gas(True))
+    w = _assemble("growth_2giant", params, m0, xb, xs, rp, rho, nsteps)
+    w.growth = dict(m0=m0.copy(), mc=np.full(2, 15.0 * M_EARTH),
+                    mf=np.array([300.0, 100.0]) * M_EARTH, tau_c=np.full(2, float(tau_c_days)),
+                    tau_g=np.full(2, float(tau_g_days)), delta_r=np.full(2, 0.01),
+                    grows=np.ones(2, dtype=np.int32))
+    return w
+
+
 def adjoint_4core_50k(seed=4, nbig=4, nsmall=50_000, nsteps=2000, checkpoint_every=50):
     rng = np.random.default_rng(seed)
     m, xb = _cores(rng, nbig)
@@ -280,6 +312,7 @@ WORKLOADS = {
     "semiactive_2000big_200k": semiactive_2000big_200k,
     "adjoint_4core_50k": adjoint_4core_50k,
     "scatter_2giant": scatter_2giant,
+    "growth_2giant": growth_2giant,
 }
 
 

@@ -120,7 +120,7 @@ def _run_vs_oracle(w, calls, xv_helio=None, m_big=None, nbig=None):
     s.close()
     p = orc.make_params(wl.params)
     xv, mu, rc = orc.init(p, nbig, wl.nsmall, m_big, xh)
-    ref, mu_ref, st_ref, ever_ref = orc.step_ex(p, nbig, xv, mu, rc, wl.rp_km, wl.rhop, sum(calls))
+    ref, mu_ref, st_ref, ever_ref, _ = orc.step_ex(p, nbig, xv, mu, rc, wl.rp_km, wl.rhop, sum(calls))
     e_end = orc.elements(gm_of(wl, p, mu_ref), orc.readout(p, nbig, wl.nsmall, mu_ref, ref))[1]
     quiet = (ever_ref == 0) & (ever.cpu().numpy() == 0)
     differ = stat != st_ref

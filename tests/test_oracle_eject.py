@@ -223,12 +223,12 @@ def test_eject_schedule_and_frozen_state():
     removed after step 5 keeps its step-5 state; the bodies left move exactly
     as in a run without the test (removed planetesimals are massless)."""
     w, p, xv, mu, rc = _scatter(eject_every=5)
-    x4, mu4, st4, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 4)
+    x4, mu4, st4, _, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 4)
     assert not st4.any()
-    x5, mu5, st5, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 5)
+    x5, mu5, st5, _, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 5)
     gone = st5 == -3
     assert gone.sum() > w.nsmall // 4 and not gone[:w.nbig].any()
-    x12, _, st12, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 12)
+    x12, _, st12, _, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 12)
     assert np.array_equal(x12[:, gone], x5[:, gone])
     assert np.all(st12[gone] == -3)
     p0 = params(eject_every=0)
@@ -241,8 +241,8 @@ def test_step_index_sets_the_schedule():
     """The test follows steps whose global index is a multiple of eject_every:
     from step0 = 3, the first test comes after 2 steps."""
     w, p, xv, mu, rc = _scatter(eject_every=5)
-    _, _, st1, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 1, step0=3)
-    _, _, st2, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 2, step0=3)
+    _, _, st1, _, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 1, step0=3)
+    _, _, st2, _, _ = orc.step_ex(p, w.nbig, xv, mu, rc, None, None, 2, step0=3)
     assert not st1.any() and (st2 == -3).sum() > w.nsmall // 4
 
 
@@ -256,13 +256,13 @@ def test_removed_massive_body_takes_no_part():
     xh = np.concatenate([w.xv_helio[:, :2], xb[:, None], w.xv_helio[:, 2:]], axis=1)
     mb = np.concatenate([w.m_big, [m3]])
     x0, mu0, rc0 = orc.init(p, 3, w.nsmall, mb, xh)
-    x1, mu1, st1, _ = orc.step_ex(p, 3, x0, mu0, rc0, None, None, 1)
+    x1, mu1, st1, _, _ = orc.step_ex(p, 3, x0, mu0, rc0, None, None, 1)
     assert st1[2] == -3 and mu1[2] == 0.0
-    x9, mu9, st9, _ = orc.step_ex(p, 3, x1, mu1, rc0, None, None, 8, stat=st1, step0=1)
+    x9, mu9, st9, _, _ = orc.step_ex(p, 3, x1, mu1, rc0, None, None, 8, stat=st1, step0=1)
     # the same state without the removed body, as a 2-giant system
     keep = np.ones(x1.shape[1], dtype=bool)
     keep[2] = False
-    y9, _, sty, _ = orc.step_ex(p, 2, x1[:, keep], mu1[keep], rc0[keep], None, None, 8,
+    y9, _, sty, _, _ = orc.step_ex(p, 2, x1[:, keep], mu1[keep], rc0[keep], None, None, 8,
                                 stat=st1[keep], step0=1)
     assert np.array_equal(x9[:, keep], y9)
     assert np.array_equal(st9[keep], sty)
