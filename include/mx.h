@@ -187,7 +187,7 @@ void mx_destroy(mx_system* s);
 mx_status mx_step(mx_system* s, int n_steps);
 
 /* Kernels of one step, in launch order, for mx_step_profiled. */
-#define MX_NKERN 10
+#define MX_NKERN 11
 #define MX_K_PREP 0       /* momentum + staged big positions */
 #define MX_K_JUMP_KICK 1  /* jump + half kick(s): gravity and drag */
 #define MX_K_JUMP_DRIFT 2 /* jump + Kepler drift */
@@ -198,6 +198,7 @@ mx_status mx_step(mx_system* s, int n_steps);
 #define MX_K_CATCHUP 7    /* deferred planetesimals: window-end and settling catch-ups */
 #define MX_K_CATCHUP_SIDE 8 /* carried planetesimals on the side stream (overlaps the steps) */
 #define MX_K_EJECT 9      /* ejection test (steps on the eject_every schedule) */
+#define MX_K_GROW 10      /* growth tracks: masses, changeover radii, gaps (mx_set_growth) */
 
 /*
  * mx_step_profiled -- the same n_steps as mx_step, launched kernel by kernel
@@ -396,6 +397,42 @@ mx_status mx_body_status(mx_system* s, signed char* host_stat, int* n_removed);
  * tangent of half the true anomaly).  Node 0 for an orbit in the reference
  * plane; angles in [0, 2 pi). */
 mx_status mx_elements(mx_system* s, double* dev_el);
+
+/* ------------------------------------------------------------------------
+ * Planet growth and gas gaps (Sec. 3.3, Eqs. 13-16; Sec. 3.1, Eqs. 8-9 and
+ * the dens_factor listing).  A growing massive body follows
+ *   M(t) = m0 + (e/(e-1)) (mc - m0) (1 - exp(-t/tau_c))      t <= tau_c (Eq. 13)
+ *   M(t) = mc + (mf - mc) (1 - exp(-(t - tau_c)/tau_g))      t >  tau_c (Eq. 15)
+ * with t = (global step index) x dt at the start of each step; the mass is
+ * held for the step.  Its changeover radius follows the mass (rcrit_hill Hill
+ * radii, R_H = a (M/3 m0)^(1/3) from the osculating a), and once t > tau_c it
+ * opens a gap: planetesimals whose cylindrical distance lies strictly within
+ * gap_c R_H of the body's cylindrical distance (at kick time) see the gas
+ * density times exp(-(t - tau_c)/tau_g); with overlapping gaps the body with
+ * the highest index wins.  The radius (Eq. 14 before tau_c with c_s at the
+ * body's cylindrical distance, k1 = 1, k2 = 1/4; Eq. 16 after it, R_c from
+ * Eq. 14 at mass mc) is reported by mx_planets and not used by the step.
+ * With growth on, every step ends with its own half kick (the next one starts
+ * with the new masses), deferral is off, and there is no adjoint.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double m0, mc, mf;    /* Msun: at t = 0, at t = tau_c, for t -> inf */
+  double tau_c, tau_g;  /* days, > 0 */
+  double delta_r;       /* AU: radius lost after tau_c (Eq. 16) */
+  int grows;            /* 0: the body keeps its mass (and has no gap) */
+  int reserved;         /* 0 */
+} mx_growth;
+
+/* Growth tracks of system sys (0 for a single system): g [n_big of that
+ * system] (host, copied), gap_c the gap half-width in Hill radii (Eq. 8: 4).
+ * Takes effect at the next step.  MX_ERR_ARG for a bad index, non-positive
+ * times, negative masses, dt <= 0 with a growing body, or gap_c < 0. */
+mx_status mx_set_growth(mx_system* s, int sys, const mx_growth* g, double gap_c);
+
+/* Masses [Msun] and radii [AU] of the massive bodies of every system, in
+ * system order (host arrays of the total number of massive bodies, may be
+ * NULL).  Radius 0 for a body that does not grow. */
+mx_status mx_planets(mx_system* s, double* m_host, double* r_host);
 
 /* Sizes of the system. */
 mx_status mx_sizes(mx_system* s, int* n_big, int* n_small);

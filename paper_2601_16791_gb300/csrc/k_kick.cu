@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int 
     d.bx[S.boff + i] = bx;
     d.by[S.boff + i] = by;
     d.bz[S.boff + i] = bz;
+    if (S.grow_on) d.gap_r[S.boff + i] = sqrt(bx * bx + by * by);   // gap centre (Sec. 3.1)
     if (rec) {
       const size_t o = (size_t)slot * 3 * d.NB + S.boff + i;
       d.h_bx[o] = bx;
@@ -164,7 +165,8 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
   const double rp = drag ? d.rp_cm[j] : 0.0, kd = drag ? d.kdrag[j] : 0.0;
   const int kbase = d.kmode ? d.kick_ctr[1] : 0;
   // the gas at the (fixed) position, shared by the launch's half kicks
-  const GasAt gq = drag ? gas_at(S, x, y) : GasAt{false, 0.0, 0.0, 0.0};
+  GasAt gq = drag ? gas_at(S, x, y) : GasAt{false, 0.0, 0.0, 0.0};
+  if (drag && S.grow_on) gq.rho *= gap_factor(d, S, x, y);
   if (drag && S.dg_on) {   // disk gravity: fixed over the launch, like the big bodies' gravity
     ax += gq.adg[0];
     ay += gq.adg[1];
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_accel(Dev d, double* acc, int drag
   if (drag) {
     int kout = 0;
     gas_drag(S, x, y, z, u + P[0] * S.inv_mu0, v + P[1] * S.inv_mu0, w + P[2] * S.inv_mu0,
-             d.rp_cm[j], d.kdrag[j], a, -1, &kout);
+             d.rp_cm[j], d.kdrag[j], a, -1, &kout, S.grow_on ? gap_factor(d, S, x, y) : 1.0);
   }
   if (drag_only) {
     if (jl < S.nbig) return;

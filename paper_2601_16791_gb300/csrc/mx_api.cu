@@ -129,6 +129,10 @@ mx::SysDev make_sysdev(const mx_params& p, int off, int nbig, int n, int boff) {
   s.dg_edge = (g.gamma == 1.0) ? 1 : 0;
   const double two_pi_g = 2.0 * kPi * p.G * (kAuCm * kAuCm / kMsunG);
   s.c_dg = s.dg_on ? two_pi_g * (s.dg_edge ? g.r_in_au : disk_gravity_series(g.gamma)) : 0.0;
+  s.grow_on = 0;                 // mx_set_growth
+  s.G = p.G;
+  s.rcrit_hill = p.rcrit_hill;
+  s.gap_c = 4.0;
   return s;
 }
 
@@ -157,6 +161,8 @@ struct mx_system {
   long long step = 0;
   int eject_every = 0;            // ejection test schedule (Sec. 3.5), 0: none
   bool removed_any = false;       // a test outside the schedule removed bodies
+  bool grow_any = false;          // some system follows growth tracks (mx_set_growth)
+  mx::Growth* d_grow = nullptr;   // [NB]
   int* d_counts = nullptr;        // [nsys] removed bodies per system
   int bs_blocks = 0;
   int catch_blocks = 0;
@@ -275,9 +281,17 @@ bool eject_after(const mx_system* s, long long gstep) {
   return s->eject_every > 0 && gstep % s->eject_every == 0;
 }
 
-// Deferral is on for forward runs with a window; recording or replaying the
+// With growth tracks every step ends with its own half kick, and the next one
+// starts with the masses of its own start time (k_grow before its first kick).
+bool split_after(const mx_system* s, long long gstep) {
+  return s->grow_any || eject_after(s, gstep);
+}
+
+// Deferral is on for forward runs with a window (no growth); recording or replaying the
 // drag branches (kmode != 0) keeps every body on the direct path.
-void update_defer(mx_system* s) { s->d.defer = (s->window > 0 && s->d.kmode == 0) ? 1 : 0; }
+void update_defer(mx_system* s) {
+  s->d.defer = (s->window > 0 && s->d.kmode == 0 && !s->grow_any) ? 1 : 0;
+}
 
 // The end of a window of history slots [wbase, wbase + window).  On the main
 // stream, after the side stream's pass over the last window: bodies deferred
@@ -671,6 +685,12 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   }
   MX_TRY(dalloc(s, &d.status, 1));
   MX_TRY(dalloc(s, &d.stat, N));
+  MX_TRY(dalloc(s, &s->d_grow, NB));
+  MX_TRY(dalloc(s, &d.gap_r, NB));
+  MX_TRY(dalloc(s, &d.gap_w, NB));
+  MX_TRY(dalloc(s, &d.gap_f, NB));
+  MX_TRY(dalloc(s, &d.brad, NB));
+  d.grow = s->d_grow;
   MX_TRY(dalloc(s, &d.ej_new, 1));
   MX_TRY(dalloc(s, &s->d_counts, nsys));
   MX_TRY(dalloc(s, &s->d_sys, nsys));
@@ -698,6 +718,11 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemsetAsync(d.pair_count, 0, 2 * sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.flags, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.stat, 0, N, st));
+  MX_CUDA(cudaMemsetAsync(s->d_grow, 0, std::max(NB, 1) * sizeof(mx::Growth), st));
+  MX_CUDA(cudaMemsetAsync(d.gap_r, 0, std::max(NB, 1) * sizeof(double), st));
+  MX_CUDA(cudaMemsetAsync(d.gap_w, 0, std::max(NB, 1) * sizeof(double), st));
+  MX_CUDA(cudaMemsetAsync(d.gap_f, 0, std::max(NB, 1) * sizeof(double), st));
+  MX_CUDA(cudaMemsetAsync(d.brad, 0, std::max(NB, 1) * sizeof(double), st));
   MX_CUDA(cudaMemsetAsync(d.ej_new, 0, sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.ever, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.bb_count, 0, sizeof(unsigned long long), st));
@@ -966,17 +991,18 @@ mx_status mx_step(mx_system* s, int n_steps) {
     return sync_status(s);
   }
   MX_TRY(ensure_graphs(s));
+  if (s->grow_any) mx::launch_grow(s->d, s->step, s->st);
   MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
   MX_CUDA(slot_done(s, false, untimed));
   for (int k = 0; k < n_steps; ++k) {
     const bool test = eject_after(s, s->step + k + 1);
-    MX_CUDA(cudaGraphLaunch((k + 1 == n_steps || test) ? s->g_last : s->g_mid, s->st));
-    if (test) {
-      mx::launch_eject(s->d, 1, s->st);
-      MX_CUDA(cudaGetLastError());
-    }
+    const bool split = split_after(s, s->step + k + 1);
+    MX_CUDA(cudaGraphLaunch((k + 1 == n_steps || split) ? s->g_last : s->g_mid, s->st));
+    if (test) mx::launch_eject(s->d, 1, s->st);
+    MX_CUDA(cudaGetLastError());
     MX_CUDA(slot_done(s, true, untimed));
-    if (test && k + 1 < n_steps) {   // the next step starts with its own half kick
+    if (split && k + 1 < n_steps) {   // the next step starts with its own half kick
+      if (s->grow_any) mx::launch_grow(s->d, s->step + k + 1, s->st);
       MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
       MX_CUDA(slot_done(s, false, untimed));
     }
@@ -1034,16 +1060,19 @@ mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_byte
     if (e == cudaSuccess) e = step_close();
   } else {
     e = step_open(0);
+    if (e == cudaSuccess && s->grow_any)
+      e = timed(MX_K_GROW, [&] { mx::launch_grow(s->d, s->step, st); });
     if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
     if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
     if (e == cudaSuccess) e = slot_done(s, false, timed3);
   }
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
     const bool test = eject_after(s, s->step + k + 1);
-    const bool last_step = (k + 1 == n_steps) || test;
+    const bool last_step = (k + 1 == n_steps) || split_after(s, s->step + k + 1);
     if (k > 0) e = step_open(k);
-    if (e == cudaSuccess && k > 0 && eject_after(s, s->step + k)) {   // after a test: a fresh half kick
-      e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
+    if (e == cudaSuccess && k > 0 && split_after(s, s->step + k)) {   // a fresh half kick
+      if (s->grow_any) e = timed(MX_K_GROW, [&] { mx::launch_grow(s->d, s->step + k, st); });
+      if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
       if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
       if (e == cudaSuccess) e = slot_done(s, false, timed3);
     }
@@ -1149,14 +1178,17 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
     // a call's first step, and a step after an ejection test, start with a half kick
-    const bool head = (k == 0) || eject_after(s, s->step + k);
+    const bool head = (k == 0) || split_after(s, s->step + k);
     const bool test = eject_after(s, s->step + k + 1);
+    const bool split = split_after(s, s->step + k + 1);
     if (flush_bytes > 0) e = cudaMemsetAsync(flush, k & 0xff, flush_bytes, st);
+    if (e == cudaSuccess && head && s->grow_any)
+      e = timed3(MX_K_GROW, st, [&] { mx::launch_grow(s->d, s->step + k, st); });
     if (e == cudaSuccess && head) {
       e = cudaGraphLaunch(s->gt_head, st);
       if (e == cudaSuccess) e = slot_done(s, false, timed3);
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch((k + 1 == n_steps || test) ? s->gt_last : s->gt_mid, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch((k + 1 == n_steps || split) ? s->gt_last : s->gt_mid, st);
     if (e == cudaSuccess && test) e = timed3(MX_K_EJECT, st, [&] { mx::launch_eject(s->d, 1, st); });
     if (e == cudaSuccess) e = slot_done(s, true, timed3);
     if (e == cudaSuccess) e = cudaEventRecord(e_end, st);
@@ -1403,6 +1435,62 @@ mx_status mx_body_status(mx_system* s, signed char* host_stat, int* n_removed) {
   return MX_OK;
 }
 
+mx_status mx_set_growth(mx_system* s, int sys, const mx_growth* g, double gap_c) {
+  if (!s || !g || sys < 0 || sys >= (int)s->h_sys.size() || !(gap_c >= 0.0))
+    return fail(MX_ERR_ARG, "invalid arguments");
+  const int nb = s->nbig[sys];
+  std::vector<mx::Growth> gr(nb);
+  bool any = false;
+  for (int i = 0; i < nb; ++i) {
+    const mx_growth& q = g[i];
+    gr[i] = mx::Growth{q.m0, q.mc, q.mf, q.tau_c, q.tau_g, q.delta_r, q.grows ? 1 : 0, 0};
+    if (!q.grows) continue;
+    any = true;
+    if (!(q.m0 >= 0.0 && q.mc >= 0.0 && q.mf >= 0.0 && q.tau_c > 0.0 && q.tau_g > 0.0 &&
+          std::isfinite(q.delta_r) && std::isfinite(q.mf) && std::isfinite(q.tau_c) &&
+          std::isfinite(q.tau_g)))
+      return fail(MX_ERR_ARG, "invalid growth track of body " + std::to_string(i));
+  }
+  if (any && !(s->params[sys].dt > 0.0)) return fail(MX_ERR_ARG, "growth needs dt > 0");
+  MX_TRY(set_device(s));
+  MX_TRY(settle(s));
+  mx::SysDev& S = s->h_sys[sys];
+  if (nb > 0)
+    MX_CUDA(cudaMemcpyAsync(s->d_grow + S.boff, gr.data(), nb * sizeof(mx::Growth),
+                            cudaMemcpyHostToDevice, s->st));
+  S.grow_on = any ? 1 : 0;
+  S.gap_c = gap_c;
+  MX_CUDA(cudaMemcpyAsync(s->d_sys + sys, &S, sizeof(mx::SysDev), cudaMemcpyHostToDevice, s->st));
+  // no gap until the first step with the track
+  if (nb > 0) MX_CUDA(cudaMemsetAsync(s->d.gap_w + S.boff, 0, nb * sizeof(double), s->st));
+  s->grow_any = false;
+  for (auto& y : s->h_sys) s->grow_any = s->grow_any || y.grow_on;
+  update_defer(s);
+  drop_graphs(s);
+  return sync_status(s);
+}
+
+mx_status mx_planets(mx_system* s, double* m_host, double* r_host) {
+  if (!s) return fail(MX_ERR_ARG, "NULL system");
+  MX_TRY(set_device(s));
+  MX_TRY(settle(s));
+  const int NB = s->NB;
+  std::vector<double> mu(NB), rad(NB);
+  if (NB > 0) {
+    MX_CUDA(cudaMemcpyAsync(mu.data(), s->d.bmu, NB * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    MX_CUDA(cudaMemcpyAsync(rad.data(), s->d.brad, NB * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  }
+  MX_TRY(sync_status(s));
+  for (size_t k = 0; k < s->h_sys.size(); ++k) {
+    const mx::SysDev& S = s->h_sys[k];
+    for (int i = 0; i < S.nbig; ++i) {
+      if (m_host) m_host[S.boff + i] = mu[S.boff + i] / s->params[k].G;
+      if (r_host) r_host[S.boff + i] = rad[S.boff + i];
+    }
+  }
+  return MX_OK;
+}
+
 mx_status mx_elements(mx_system* s, double* dev_el) {
   if (!s || !dev_el) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
@@ -1594,6 +1682,7 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
     if (y.dg_on) return fail(MX_ERR_ARG, "disk gravity is not differentiated by the adjoint");
   if (s->eject_every > 0 || s->removed_any)
     return fail(MX_ERR_ARG, "the adjoint does not follow bodies removed by ejection");
+  if (s->grow_any) return fail(MX_ERR_ARG, "the adjoint does not follow growing masses");
   MX_TRY(set_device(s));
   MX_TRY(settle(s));
   MX_TRY(ensure_adjoint(s));

@@ -68,6 +68,17 @@ struct SysDev {
   // times 1/R for gamma = 1 (dg_edge), outward positive
   int dg_on, dg_edge;
   double c_dg;
+  // planet growth (Sec. 3.3) and gaps (Sec. 3.1, Eqs. 8-9)
+  int grow_on, pad1;
+  double G, rcrit_hill, gap_c;
+};
+
+// Growth track of one big body (Eqs. 13, 15; radius Eqs. 14, 16).
+struct Growth {
+  double m0, mc, mf;   // Msun
+  double tc, tg;       // d
+  double dr;           // AU
+  int grows, pad;
 };
 
 // A block's worth of targets, never spanning two systems.
@@ -109,6 +120,11 @@ struct Dev {
   // big body has mu = 0.
   signed char* stat;   // [N] 0, or kStatEjected
   int* ej_new;         // bodies removed by ejection tests since the host last cleared it
+  // Growth (Sec. 3.3): tracks, and per big body the gap's centre (cylindrical
+  // distance at kick time, k_prep), half-width (0: none) and density factor,
+  // and the radius (k_grow).
+  const Growth* grow;  // [NB]
+  double *gap_r, *gap_w, *gap_f, *brad;   // [NB]
   const SysDev* sys;
   const Tile* tiles;
   int N, NB, nsys, ntiles;

@@ -98,16 +98,36 @@ __device__ __forceinline__ void gas_drag_at(const SysDev& S, const GasAt& q, dou
   a[2] = -coef * dw;
 }
 
+// The gas density factor of a planetesimal at (x, y, .) (the dens_factor
+// listing of Sec. 3.1): 1, or the factor of the last big body (ascending
+// index) whose open gap (Eqs. 8-9) holds the planetesimal's cylindrical
+// distance R strictly inside |R - r_i| < W_i.  r_i (the big body's cylindrical
+// distance at kick time) comes from k_prep, W_i and the factor from k_grow.
+__device__ __forceinline__ double gap_factor(const Dev& d, const SysDev& S, double x, double y) {
+  const double R = sqrt(x * x + y * y);
+  double f = 1.0;
+  for (int i = 0; i < S.nbig; ++i) {
+    const int b = S.boff + i;
+    const double w = d.gap_w[b];
+    if (w > 0.0) {
+      const double r = d.gap_r[b];
+      if (R < r + w && R > r - w) f = d.gap_f[b];
+    }
+  }
+  return f;
+}
+
 // The gas's acceleration on one planetesimal at heliocentric position
 // (x, y, z) moving with heliocentric velocity (u, v, w): the drag (gas_at,
 // then gas_drag_at) plus, when enabled, the disk's gravity.  Quantities follow
 // Sec. 3.1: Sigma (Eq. 1, normalised at 1 AU), rho_g (Eq. 4) at the midplane,
-// v_g (Eqs. 5, 6), C_D (Eq. 7).
+// v_g (Eqs. 5, 6), C_D (Eq. 7).  dfac multiplies the gas density (a gap).
 __device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, double z, double u,
                                          double v, double w, double rp_cm, double kd, double* a,
-                                         int kb_in, int* kb_out) {
+                                         int kb_in, int* kb_out, double dfac = 1.0) {
   (void)z;
-  const GasAt q = gas_at(S, x, y);
+  GasAt q = gas_at(S, x, y);
+  q.rho *= dfac;
   gas_drag_at(S, q, x, y, u, v, w, rp_cm, kd, a, kb_in, kb_out);
   a[0] += q.adg[0];
   a[1] += q.adg[1];

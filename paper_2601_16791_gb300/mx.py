@@ -43,6 +43,11 @@ class MxParams(ctypes.Structure):
                 ("eject_every", _I), ("gas", MxGas)]
 
 
+class MxGrowth(ctypes.Structure):
+    _fields_ = [("m0", _D), ("mc", _D), ("mf", _D), ("tau_c", _D), ("tau_g", _D),
+                ("delta_r", _D), ("grows", _I), ("reserved", _I)]
+
+
 class MxError(RuntimeError):
     def __init__(self, code, where, msg=""):
         super().__init__(f"{where}: {STATUS.get(code, code)} {msg}".strip())
@@ -90,6 +95,8 @@ _SIGS = {
     "mx_check_ejections": (_I, [_P, _P]),
     "mx_body_status": (_I, [_P, _P, _P]),
     "mx_elements": (_I, [_P, _P]),
+    "mx_set_growth": (_I, [_P, _I, _P, _D]),
+    "mx_planets": (_I, [_P, _P, _P]),
 }
 
 
@@ -173,7 +180,7 @@ def mx_step(sys, n_steps):
 
 
 KERNELS = ("k_prep", "k_jump_kick", "k_jump_drift", "k_detect", "k_sort_keys", "k_groups", "k_bs",
-           "k_catchup", "k_catchup_side", "k_eject")
+           "k_catchup", "k_catchup_side", "k_eject", "k_grow")
 
 
 def mx_step_profiled(sys, n_steps):
@@ -354,6 +361,25 @@ def mx_elements(sys, dev_el):
     _check(load().mx_elements(sys, _dptr(dev_el)), "mx_elements")
 
 
+def mx_set_growth(sys, k, growth, n_big, gap_c=4.0):
+    """Growth tracks of system k from a dict of per-big arrays (m0, mc, mf
+    [Msun], tau_c, tau_g [d], delta_r [AU], grows)."""
+    arr = (MxGrowth * max(1, n_big))()
+    for i in range(n_big):
+        arr[i] = MxGrowth(float(growth["m0"][i]), float(growth["mc"][i]), float(growth["mf"][i]),
+                          float(growth["tau_c"][i]), float(growth["tau_g"][i]),
+                          float(growth["delta_r"][i]), int(growth["grows"][i]), 0)
+    _check(load().mx_set_growth(sys, int(k), arr, float(gap_c)), "mx_set_growth")
+
+
+def mx_planets(sys, nb_total):
+    """(masses [Msun], radii [AU]) of all massive bodies."""
+    m = np.zeros(nb_total)
+    r = np.zeros(nb_total)
+    _check(load().mx_planets(sys, _hptr(m), _hptr(r)), "mx_planets")
+    return m, r
+
+
 class Batch:
     """Owns one mx_system with many systems (mx_init_batch)."""
 
@@ -395,6 +421,8 @@ class System:
         self.n = workload.n
         self.h = mx_init_system(self.params, self.nbig, self.nsmall, workload.m_big,
                                 workload.xv_helio, workload.rp_km, workload.rhop, stream)
+        if getattr(workload, "growth", None) is not None:
+            mx_set_growth(self.h, 0, workload.growth, self.nbig, workload.gap_c)
 
     def step(self, n):
         mx_step(self.h, n)

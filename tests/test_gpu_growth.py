@@ -1,0 +1,131 @@
+"""Planet growth (Sec. 3.3) and gas gaps (Sec. 3.1) on the GPU against the oracle.
+
+Tolerances: masses relative <= 1e-14 (the track is two exponentials);
+radii relative <= 1e-12; drag with gaps relative <= 1e-12 per body; positions
+after a run, for bodies never flagged, relative <= 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2601_16791_gb300 import mx, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+TC, TG = 400.0, 200.0      # days: 40 steps of core growth, then runaway
+
+
+def workload(nsmall=3000):
+    return W.growth_2giant(nsmall=nsmall, tau_c_days=TC, tau_g_days=TG)
+
+
+@pytest.mark.parametrize("k", [0, 17, 40, 41, 75])
+def test_track_masses_and_radii(k):
+    """After one step from global step k the masses are the track's at t = k h
+    and the radii Eqs. 14 / 16 of that state."""
+    w = workload(200)
+    s = mx.System(w)
+    p = orc.make_params(w.params)
+    xv, mu, rc = orc.init(p, w.nbig, w.nsmall, w.m_big, w.xv_helio)
+    s.set_state(xv, mx.MX_COORD_DH, k)
+    ref = orc.grow_state(p, w.nbig, xv, mu, rc, w.growth, k * 10.0, w.gap_c)
+    s.step(1)
+    m, r = mx.mx_planets(s.h, w.nbig)
+    s.close()
+    assert np.max(np.abs(m * p.G - ref["mu"]) / ref["mu"]) <= 1e-14
+    assert np.max(np.abs(r - ref["radius"]) / np.abs(ref["radius"])) <= 1e-12
+    assert (ref["gap_w"] > 0).all() == (k * 10.0 > TC)
+
+
+def test_drag_with_open_gaps():
+    """In the runaway phase the drag of every planetesimal (mx_gas_drag) matches
+    the oracle's with the gaps orc.grow_state gives; some planetesimals are in
+    a gap and their drag differs from the gap-free one."""
+    w = workload(20_000)
+    s = mx.System(w)
+    p = orc.make_params(w.params)
+    xv, mu, rc = orc.init(p, w.nbig, w.nsmall, w.m_big, w.xv_helio)
+    k = 70
+    s.set_state(xv, mx.MX_COORD_DH, k)
+    g = orc.grow_state(p, w.nbig, xv, mu, rc, w.growth, k * 10.0, w.gap_c)
+    s.step(1)
+    s.set_state(xv, mx.MX_COORD_DH, k + 1)       # same state, masses and gaps of step k
+    mu2 = mu.copy()
+    mu2[:w.nbig] = g["mu"]
+    acc = torch.zeros((3, w.nsmall), dtype=torch.float64, device="cuda")
+    mx.mx_gas_drag(s.h, acc)
+    s.close()
+    ref = orc.gas_drag_gap(p, w.nbig, xv, mu2, w.rp_km, w.rhop, g["gap_w"], g["gap_f"])
+    plain = orc.gas_drag(p, w.nbig, xv, mu2, w.rp_km, w.rhop)
+    got = acc.cpu().numpy()
+    num = np.linalg.norm(got - ref, axis=0)
+    den = np.linalg.norm(ref, axis=0)
+    ok = den > 0
+    assert np.max(num[ok] / den[ok]) <= 1e-12
+    in_gap = np.linalg.norm(ref - plain, axis=0) > 1e-3 * np.linalg.norm(plain, axis=0)
+    assert in_gap.sum() > 100
+
+
+def test_growth_run_parity():
+    """120 steps through core growth (40 steps), the onset of runaway accretion
+    and open gaps, across call boundaries."""
+    w = workload(3000)
+    s = mx.System(w)
+    for n in (33, 7, 80):
+        s.step(n)
+    out = s.state(mx.MX_COORD_DH)
+    m, r = mx.mx_planets(s.h, w.nbig)
+    ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(s.h, ever)
+    assert mx.mx_defer_stats(s.h)[0] == 0          # no deferral with growth
+    s.close()
+    p = orc.make_params(w.params)
+    xv, mu, rc = orc.init(p, w.nbig, w.nsmall, w.m_big, w.xv_helio)
+    ref, mu_ref, _, ever_ref, _ = orc.step_ex(p, w.nbig, xv, mu, rc, w.rp_km, w.rhop, 120,
+                                              growth=w.growth, gap_c=w.gap_c)
+    assert np.max(np.abs(m * p.G - mu_ref[:w.nbig]) / mu_ref[:w.nbig]) <= 1e-12
+    assert m[0] > 50 * W.M_EARTH
+    keep = (ever_ref == 0) & (ever.cpu().numpy() == 0)
+    err = np.linalg.norm(out[:3] - ref[:3], axis=0) / np.linalg.norm(ref[:3], axis=0)
+    assert keep.sum() > 1500 and err[keep].max() <= 1e-9, err[keep].max()
+
+
+def test_runners_agree_and_count_growth_launches():
+    w = workload(2000)
+    ref = mx.System(w)
+    for n in (5, 9):
+        ref.step(n)
+    want = ref.state(mx.MX_COORD_DH)
+    ref.close()
+    s = mx.System(w)
+    _, c1, _ = mx.mx_step_profiled(s.h, 5)
+    _, c2, _ = mx.mx_step_profiled(s.h, 9)
+    assert c1["k_grow"] == 5 and c2["k_grow"] == 9 and c2["k_jump_kick"] == 18
+    assert np.array_equal(s.state(mx.MX_COORD_DH), want)
+    s.close()
+    s = mx.System(w)
+    flush = torch.empty(32 << 20, dtype=torch.uint8, device="cuda")
+    _, c1, _ = mx.mx_step_timed(s.h, 5, flush)
+    _, c2, _ = mx.mx_step_timed(s.h, 9, flush)
+    assert c1["k_grow"] == 5 and c2["k_grow"] == 9
+    assert np.array_equal(s.state(mx.MX_COORD_DH), want)
+    s.close()
+
+
+def test_growth_arguments_and_adjoint():
+    w = workload(100)
+    s = mx.System(w)
+    bad = dict(w.growth, tau_g=np.zeros(2))
+    with pytest.raises(mx.MxError) as e:
+        mx.mx_set_growth(s.h, 0, bad, w.nbig)
+    assert e.value.status == "MX_ERR_ARG"
+    z = torch.tensor(s.state(mx.MX_COORD_DH), device="cuda")
+    with pytest.raises(mx.MxError) as e:
+        mx.mx_adjoint_step(s.h, z, 0, torch.zeros_like(z),
+                           torch.zeros(3, dtype=torch.float64, device="cuda"))
+    assert e.value.status == "MX_ERR_ARG"
+    s.close()
