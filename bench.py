@@ -407,6 +407,51 @@ def eject_leg(steps=200):
     return out
 
 
+def growth_leg(steps=200):
+    """Planet growth and gaps (Secs. 3.1, 3.3) on the two-giant disk (2
+    embryos + 24,000 planetesimals with gas; tracks compressed to tau_c =
+    400 d, tau_g = 200 d so that the gaps are open in the timed steps 60-259):
+    step time with the tracks, against the same system with the masses fixed
+    at the tracks' values at step 60 (same encounters, no growth, no gaps),
+    with the per-kernel split of both."""
+    import torch
+    from paper_2601_16791_gb300 import mx, workloads as W
+    st = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {"workload": "growth_2giant: 2 embryos (0.01 -> 15 -> 300/100 M_earth) + 24,000 "
+                       "planetesimals, gas, tau_c = 400 d, tau_g = 200 d, steps 60-259",
+           "steps": steps}
+    m60 = None
+    for grow in (True, False):
+        w = W.growth_2giant(tau_c_days=400.0, tau_g_days=200.0)
+        s = mx.System(w, stream=st.cuda_stream)
+        if grow:
+            mx.mx_step_timed(s.h, 60, flush)
+            mx.mx_step_timed(s.h, 0, flush)
+            m60 = mx.mx_planets(s.h, w.nbig)[0]
+        else:   # same start state, masses fixed at step 60's
+            s.close()
+            w.growth = None
+            w.m_big = m60
+            s = mx.System(w, stream=st.cuda_stream)
+            mx.mx_step_timed(s.h, 60, flush)
+            mx.mx_step_timed(s.h, 0, flush)
+        ms, cnt, tot = mx.mx_step_timed(s.h, steps, flush)
+        ms0, cnt0, tot0 = mx.mx_step_timed(s.h, 0, flush)
+        key = "growth" if grow else "fixed_masses"
+        out[f"ms_per_step_{key}"] = (tot + tot0) / steps
+        out[f"kernels_ms_per_step_{key}"] = {k: (ms[k] + ms0[k]) / steps for k in mx.KERNELS
+                                             if ms[k] + ms0[k] > 0}
+        if grow:
+            out["k_prep_us"] = 1e3 * ms["k_prep"] / max(1, cnt["k_prep"])
+            out["masses_msun_end"] = mx.mx_planets(s.h, w.nbig)[0].tolist()
+        out[f"defer_window_{key}"] = mx.mx_defer_stats(s.h)[0]
+        s.close()
+    out["masses_msun_fixed"] = [float(v) for v in m60]
+    out["timing"] = "mx_step_timed (graphs, CUDA events, L2 flushed before every step)"
+    return out
+
+
 # ------------------------------------------------------------------- main
 def run_mx(args):
     import torch
@@ -536,6 +581,10 @@ def run_mx(args):
             line["ejection"] = eject_leg()
         except Exception as exc:
             line["ejection"] = {"error": str(exc)[:300]}
+        try:
+            line["growth"] = growth_leg()
+        except Exception as exc:
+            line["growth"] = {"error": str(exc)[:300]}
     if not args.no_cpu_baseline:
         cb, _, _ = oracle_rate(w, 12.0)
         line["cpu_baseline"] = cb

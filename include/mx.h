@@ -187,7 +187,7 @@ void mx_destroy(mx_system* s);
 mx_status mx_step(mx_system* s, int n_steps);
 
 /* Kernels of one step, in launch order, for mx_step_profiled. */
-#define MX_NKERN 11
+#define MX_NKERN 10
 #define MX_K_PREP 0       /* momentum + staged big positions */
 #define MX_K_JUMP_KICK 1  /* jump + half kick(s): gravity and drag */
 #define MX_K_JUMP_DRIFT 2 /* jump + Kepler drift */
@@ -198,7 +198,6 @@ mx_status mx_step(mx_system* s, int n_steps);
 #define MX_K_CATCHUP 7    /* deferred planetesimals: window-end and settling catch-ups */
 #define MX_K_CATCHUP_SIDE 8 /* carried planetesimals on the side stream (overlaps the steps) */
 #define MX_K_EJECT 9      /* ejection test (steps on the eject_every schedule) */
-#define MX_K_GROW 10      /* growth tracks: masses, changeover radii, gaps (mx_set_growth) */
 
 /*
  * mx_step_profiled -- the same n_steps as mx_step, launched kernel by kernel
@@ -403,17 +402,19 @@ mx_status mx_elements(mx_system* s, double* dev_el);
  * the dens_factor listing).  A growing massive body follows
  *   M(t) = m0 + (e/(e-1)) (mc - m0) (1 - exp(-t/tau_c))      t <= tau_c (Eq. 13)
  *   M(t) = mc + (mf - mc) (1 - exp(-(t - tau_c)/tau_g))      t >  tau_c (Eq. 15)
- * with t = (global step index) x dt at the start of each step; the mass is
- * held for the step.  Its changeover radius follows the mass (rcrit_hill Hill
+ * with t = (global step index) x dt at the start of each step (applied by
+ * the step's first kick launch, MX_K_PREP); the mass is held for the step.  Its changeover radius follows the mass (rcrit_hill Hill
  * radii, R_H = a (M/3 m0)^(1/3) from the osculating a), and once t > tau_c it
  * opens a gap: planetesimals whose cylindrical distance lies strictly within
  * gap_c R_H of the body's cylindrical distance (at kick time) see the gas
  * density times exp(-(t - tau_c)/tau_g); with overlapping gaps the body with
  * the highest index wins.  The radius (Eq. 14 before tau_c with c_s at the
  * body's cylindrical distance, k1 = 1, k2 = 1/4; Eq. 16 after it, R_c from
- * Eq. 14 at mass mc) is reported by mx_planets and not used by the step.
+ * Eq. 14 at mass mc on the current orbit) is not used by the step; mx_planets
+ * computes it for the current state at t = (steps taken) x dt.
  * With growth on, every step ends with its own half kick (the next one starts
- * with the new masses), deferral is off, and there is no adjoint.
+ * with the new masses), and there is no adjoint.  Deferred planetesimals
+ * replay each step with the masses, changeover radii and gaps it had.
  * ------------------------------------------------------------------------ */
 typedef struct {
   double m0, mc, mf;    /* Msun: at t = 0, at t = tau_c, for t -> inf */

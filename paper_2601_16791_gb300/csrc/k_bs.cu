@@ -1190,15 +1190,17 @@ struct CatchArgs {
   int t_next;           // where the next range starts: a body that reached t_end is kept there
 };
 
-// hmu: the system's big-body mu during the group's slot (the history's,
-// as a big body can be removed after the slot).
+// Big-body mu and changeover radius during slot t (the history's: masses
+// and radii can change after the slot, by growth or removal).
 template <int NB>
 __device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, const int* gid,
-                                               const double* hmu, double* mu, MemberK* K) {
+                                               int t, double* mu, MemberK* K) {
+  const double* hmu = d.h_mu + (size_t)t * d.NB + S.boff;
+  const double* hrc = d.h_rc + (size_t)t * d.NB + S.boff;
 #pragma unroll
   for (int m = 0; m < NB; ++m) {
     const int l = gid[m] - S.off;
-    const double rc = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
+    const double rc = (l < S.nbig) ? hrc[l] : 0.0;
     mu[m] = (l < S.nbig) ? hmu[l] : 0.0;
     K[m].rc = rc;
     K[m].rc2 = rc * rc;
@@ -1228,11 +1230,11 @@ struct CatchGroup {
 // Three or four bodies: the lane integrator of k_bs_spread on one warp, run
 // to the end of the step.
 template <int NB>
-__device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const CatchGroup& G,
-                                     const double* hmu, int lane, double* s6) {
+__device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const CatchGroup& G, int t,
+                                     int lane, double* s6) {
   double mu[NB];
   MemberK K[NB];
-  load_members_g<NB>(d, S, G.gid, hmu, mu, K);
+  load_members_g<NB>(d, S, G.gid, t, mu, K);
   GroupRun<NB> g;
 #pragma unroll
   for (int m = 0; m < NB; ++m)
@@ -1252,12 +1254,12 @@ __device__ __noinline__ int catch_bs(const Dev& d, const SysDev& S, const CatchG
 // lanes, one candidate per warp; three or four: to the end of the step on
 // warp 0, then broadcast).  Returns 1 (done, body state in s6), 0 (rounds ran
 // out, G updated) or -1 (sub-step cap).
-__device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, const double* hmu,
+__device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, int t,
                             int max_rounds, const CatchBlk& B, double* s6) {
   if (G.nb == 2) {
     double mu[2];
     MemberK K[2];
-    load_members_g<2>(d, S, G.gid, hmu, mu, K);
+    load_members_g<2>(d, S, G.gid, t, mu, K);
     const Bs2Term t = bs2_term(B.lane & 3, S.mu0, mu, K);
     GroupRun<2> g;
 #pragma unroll
@@ -1281,8 +1283,8 @@ __device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, const 
     return r;
   }
   if (B.wq == 0) {
-    const int r = (G.nb == 3) ? catch_bs<3>(d, S, G, hmu, B.lane, s6)
-                              : catch_bs<4>(d, S, G, hmu, B.lane, s6);
+    const int r = (G.nb == 3) ? catch_bs<3>(d, S, G, t, B.lane, s6)
+                              : catch_bs<4>(d, S, G, t, B.lane, s6);
     if (B.lane == 0) {
       for (int q = 0; q < 6; ++q) B.s_bc[q] = s6[q];
       *B.s_r = r;
@@ -1303,13 +1305,14 @@ __device__ __noinline__ void catch_bs_thread(const Dev& d, const SysDev& S, cons
   const double* B0 = d.h_b0 + (size_t)t * 6 * NBs + S.boff;
   const int nb = cnt + 1;
   const double* hmu = d.h_mu + (size_t)t * NBs + S.boff;
+  const double* hrc = d.h_rc + (size_t)t * NBs + S.boff;
   GroupState G;
   G.nb = nb;
   double Y[6][kMaxGroup];
   for (int m = 0; m < nb; ++m) {
     const bool big = m < cnt;
     G.mu[m] = big ? hmu[mem[m]] : 0.0;
-    G.rc[m] = big ? d.brc[S.boff + mem[m]] : 0.0;
+    G.rc[m] = big ? hrc[mem[m]] : 0.0;
     for (int q = 0; q < 6; ++q) Y[q][m] = big ? B0[(size_t)q * NBs + mem[m]] : a0[q];
   }
   int nsub = 0;
@@ -1344,6 +1347,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
   const double* B0 = d.h_b0 + (size_t)t * 6 * NBs + S.boff;
   const double* B1 = d.h_b1 + (size_t)t * 6 * NBs + S.boff;
   const double* hmu = d.h_mu + (size_t)t * NBs + S.boff;
+  const double* hrc = d.h_rc + (size_t)t * NBs + S.boff;
   const float hf = (float)S.h;
   // flagged big bodies, ascending
   int fl[kMaxGroup];
@@ -1353,7 +1357,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
     const int l = c0 + lane;
     bool hit = false;
     if (l < S.nbig && hmu[l] >= 0.0) {   // a body removed by then meets nothing
-      const double rcb = d.brc[S.boff + l];
+      const double rcb = hrc[l];
       const float rcf = fmaxf((float)rcb, (float)0.0);
       float bf[12];
       double b0[6], b1[6];
@@ -1461,9 +1465,10 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
   double u = s6[3], v = s6[4], w = s6[5];
   const double* BX = d.h_bx + (size_t)t * 3 * d.NB + S.boff;
   const double* hmu = d.h_mu + (size_t)t * d.NB + S.boff;
+  const double* hrc = d.h_rc + (size_t)t * d.NB + S.boff;
   double ax = 0, ay = 0, az = 0;
   for (int l = 0; l < S.nbig; ++l) {
-    const double rc = d.brc[S.boff + l];
+    const double rc = hrc[l];
     pair_acc(x - BX[l], y - BX[d.NB + l], z - BX[2 * (size_t)d.NB + l], fmax(hmu[l], 0.0),
              rc * rc, 0.01 * (rc * rc), 0.1 * rc, (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0, ax, ay, az);
   }
@@ -1471,7 +1476,11 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
   const double kick_h = 0.5 * S.h;
   const double hp0 = P2[0] * S.inv_mu0, hp1 = P2[1] * S.inv_mu0, hp2 = P2[2] * S.inv_mu0;
   const double rp = S.gas_on ? d.rp_cm[j] : 0.0, kd = S.gas_on ? d.kdrag[j] : 0.0;
-  const GasAt gq = S.gas_on ? gas_at(S, x, y) : GasAt{false, 0.0, 0.0, 0.0};
+  GasAt gq = S.gas_on ? gas_at(S, x, y) : GasAt{false, 0.0, 0.0, 0.0};
+  if (S.gas_on && S.grow_on) {   // the slot's gaps, as in k_jump_kick
+    const double* hg = d.h_gap + (size_t)t * 3 * d.NB + S.boff;
+    gq.rho *= gap_factor(hg, hg + d.NB, hg + 2 * (size_t)d.NB, S.nbig, x, y);
+  }
   if (S.gas_on && S.dg_on) {   // as in k_jump_kick
     ax += gq.adg[0];
     ay += gq.adg[1];
@@ -1569,7 +1578,7 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
   };
   for (;;) {
     if (G.nb >= 2) {
-      const int r = catch_bs_any(d, S, G, d.h_mu + (size_t)t * d.NB + S.boff, budget, B, s6);
+      const int r = catch_bs_any(d, S, G, t, budget, B, s6);
       if (r == 0) {
         carried = true;
         break;

@@ -8,6 +8,7 @@
 // Each target sums its sources in ascending order (the gather form of the
 // parallel loop), so results do not depend on the launch shape.
 #include "mx_common.cuh"
+#include "mx_growth.cuh"
 #include "mx_kernels.h"
 #include "mx_physics.cuh"
 
@@ -61,14 +62,26 @@ __device__ __forceinline__ void gravity_all(const Dev& d, const SysDev& S, BigSm
 // One block per system; a fixed partition and tree keep the sum deterministic.
 // nkick > 0: the kernel that follows makes nkick half kicks; the kick counter
 // (for recording or replaying the k branch of Eq. 7) advances here.
+// The first launch of a step (jump_frac = 0, nkick > 0) first applies the
+// growth tracks (Sec. 3.3) of a system that has them, at t = gstep x h; the
+// launch that ends a step (jump_frac != 0) counts it in gstep.
 __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int nkick) {
   const SysDev& S = d.sys[blockIdx.x];
+  __shared__ double red[3][kThreads];
+  if (S.grow_on && nkick > 0 && jump_frac == 0.0)
+    grow_update(d, S, (double)d.gstep[0] * S.h, red);
   if (nkick > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
     d.kick_ctr[1] = d.kick_ctr[0];
     d.kick_ctr[0] += nkick;
+    if (jump_frac != 0.0) d.gstep[0] += 1;   // no block reads it in this launch
   }
-  __shared__ double red[3][kThreads];
   const int N = d.N;
+  // With at most 32 big bodies (one per lane of warp 0) the tree below adds
+  // only zeros above its last five levels, so warp 0 alone takes those five
+  // levels with shuffles, in the same order (the same sum, bit for bit),
+  // without block barriers; the other warps have nothing to stage.
+  const bool one_warp = S.nbig <= 32;
+  if (one_warp && threadIdx.x >= 32) return;
   double p[3] = {0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
     const int g = S.off + i;
@@ -77,17 +90,24 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int 
     p[1] = fma(m, d.xv[4 * (size_t)N + g], p[1]);
     p[2] = fma(m, d.xv[5 * (size_t)N + g], p[2]);
   }
-  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = p[c];
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+  double Ps[3];
+  if (one_warp) {
+    for (int s = 16; s > 0; s >>= 1)
+      for (int c = 0; c < 3; ++c) p[c] += __shfl_down_sync(0xffffffffu, p[c], s);
+    for (int c = 0; c < 3; ++c) Ps[c] = __shfl_sync(0xffffffffu, p[c], 0);
+  } else {
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = p[c];
     __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s)
+        for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+      __syncthreads();
+    }
+    for (int c = 0; c < 3; ++c) Ps[c] = red[c][0];
   }
   double* P = d.P + 3 * blockIdx.x;
   if (threadIdx.x == 0)
-    for (int c = 0; c < 3; ++c) P[c] = red[c][0];
-  double Ps[3] = {red[0][0], red[1][0], red[2][0]};
+    for (int c = 0; c < 3; ++c) P[c] = Ps[c];
   double dj[3];
   jump_vec(Ps, S, jump_frac, dj);
   // the kicks of a history slot (the end of a step, or the leading half kick
@@ -116,6 +136,13 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int 
       d.h_bx[o + d.NB] = by;
       d.h_bx[o + 2 * (size_t)d.NB] = bz;
       d.h_mu[(size_t)slot * d.NB + S.boff + i] = removed(d, g) ? -1.0 : d.bmu[S.boff + i];
+      d.h_rc[(size_t)slot * d.NB + S.boff + i] = d.brc[S.boff + i];
+      if (S.grow_on) {
+        const size_t q = (size_t)slot * 3 * d.NB + S.boff + i;
+        d.h_gap[q] = d.gap_r[S.boff + i];
+        d.h_gap[q + d.NB] = d.gap_w[S.boff + i];
+        d.h_gap[q + 2 * (size_t)d.NB] = d.gap_f[S.boff + i];
+      }
     }
   }
 }

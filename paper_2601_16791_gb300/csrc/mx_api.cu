@@ -282,16 +282,14 @@ bool eject_after(const mx_system* s, long long gstep) {
 }
 
 // With growth tracks every step ends with its own half kick, and the next one
-// starts with the masses of its own start time (k_grow before its first kick).
+// starts with the masses of its own start time (k_prep applies them).
 bool split_after(const mx_system* s, long long gstep) {
   return s->grow_any || eject_after(s, gstep);
 }
 
-// Deferral is on for forward runs with a window (no growth); recording or replaying the
+// Deferral is on for forward runs with a window; recording or replaying the
 // drag branches (kmode != 0) keeps every body on the direct path.
-void update_defer(mx_system* s) {
-  s->d.defer = (s->window > 0 && s->d.kmode == 0 && !s->grow_any) ? 1 : 0;
-}
+void update_defer(mx_system* s) { s->d.defer = (s->window > 0 && s->d.kmode == 0) ? 1 : 0; }
 
 // The end of a window of history slots [wbase, wbase + window).  On the main
 // stream, after the side stream's pass over the last window: bodies deferred
@@ -565,6 +563,7 @@ mx_status trial_ms(mx_system* s, double* ms) {
   MX_CUDA(cudaMemsetAsync(s->d.bb_count, 0, sizeof(unsigned long long), s->st));
   MX_CUDA(cudaMemsetAsync(s->d.defer_total, 0, sizeof(unsigned long long), s->st));
   MX_CUDA(cudaMemsetAsync(s->d.kick_ctr, 0, 2 * sizeof(int), s->st));
+  MX_CUDA(cudaMemsetAsync(s->d.gstep, 0, sizeof(long long), s->st));
   MX_CUDA(cudaStreamSynchronize(s->st));
   *ms = t;
   return MX_OK;
@@ -661,7 +660,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_TRY(dalloc(s, &d.cont_state, (size_t)d.cont_cap * 27));
   // deferred planetesimals: per-step history of the big bodies, records
   {
-    const size_t per_step = (size_t)16 * NB * sizeof(double) + (size_t)NB * sizeof(int) +
+    const size_t per_step = (size_t)20 * NB * sizeof(double) + (size_t)NB * sizeof(int) +
                             (size_t)6 * nsys * sizeof(double) + 2 * sizeof(int);
     int hc = kMaxWindow;
     while (hc > 1 && (size_t)hc * per_step > kHistBudget) hc >>= 1;
@@ -676,6 +675,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
     MX_TRY(dalloc(s, &d.h_b1, (size_t)hc * 6 * NB));
     MX_TRY(dalloc(s, &d.h_bx, (size_t)hc * 3 * NB));
     MX_TRY(dalloc(s, &d.h_mu, (size_t)hc * NB));
+    MX_TRY(dalloc(s, &d.h_rc, (size_t)hc * NB));
+    MX_TRY(dalloc(s, &d.h_gap, (size_t)hc * 3 * NB));
     MX_TRY(dalloc(s, &d.h_ej, hc));
     MX_TRY(dalloc(s, &d.h_comp, (size_t)hc * NB));
     MX_TRY(dalloc(s, &d.h_nkick, hc));
@@ -690,6 +691,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_TRY(dalloc(s, &d.gap_w, NB));
   MX_TRY(dalloc(s, &d.gap_f, NB));
   MX_TRY(dalloc(s, &d.brad, NB));
+  MX_TRY(dalloc(s, &d.gstep, 1));
   d.grow = s->d_grow;
   MX_TRY(dalloc(s, &d.ej_new, 1));
   MX_TRY(dalloc(s, &s->d_counts, nsys));
@@ -723,6 +725,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemsetAsync(d.gap_w, 0, std::max(NB, 1) * sizeof(double), st));
   MX_CUDA(cudaMemsetAsync(d.gap_f, 0, std::max(NB, 1) * sizeof(double), st));
   MX_CUDA(cudaMemsetAsync(d.brad, 0, std::max(NB, 1) * sizeof(double), st));
+  MX_CUDA(cudaMemsetAsync(d.gstep, 0, sizeof(long long), st));
   MX_CUDA(cudaMemsetAsync(d.ej_new, 0, sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.ever, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.bb_count, 0, sizeof(unsigned long long), st));
@@ -991,7 +994,6 @@ mx_status mx_step(mx_system* s, int n_steps) {
     return sync_status(s);
   }
   MX_TRY(ensure_graphs(s));
-  if (s->grow_any) mx::launch_grow(s->d, s->step, s->st);
   MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
   MX_CUDA(slot_done(s, false, untimed));
   for (int k = 0; k < n_steps; ++k) {
@@ -1002,7 +1004,6 @@ mx_status mx_step(mx_system* s, int n_steps) {
     MX_CUDA(cudaGetLastError());
     MX_CUDA(slot_done(s, true, untimed));
     if (split && k + 1 < n_steps) {   // the next step starts with its own half kick
-      if (s->grow_any) mx::launch_grow(s->d, s->step + k + 1, s->st);
       MX_CUDA(cudaGraphLaunch(s->g_head, s->st));
       MX_CUDA(slot_done(s, false, untimed));
     }
@@ -1060,8 +1061,6 @@ mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_byte
     if (e == cudaSuccess) e = step_close();
   } else {
     e = step_open(0);
-    if (e == cudaSuccess && s->grow_any)
-      e = timed(MX_K_GROW, [&] { mx::launch_grow(s->d, s->step, st); });
     if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
     if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
     if (e == cudaSuccess) e = slot_done(s, false, timed3);
@@ -1071,8 +1070,7 @@ mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_byte
     const bool last_step = (k + 1 == n_steps) || split_after(s, s->step + k + 1);
     if (k > 0) e = step_open(k);
     if (e == cudaSuccess && k > 0 && split_after(s, s->step + k)) {   // a fresh half kick
-      if (s->grow_any) e = timed(MX_K_GROW, [&] { mx::launch_grow(s->d, s->step + k, st); });
-      if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
+      e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.0, 1, st); });
       if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.0, 0.5, 1, st); });
       if (e == cudaSuccess) e = slot_done(s, false, timed3);
     }
@@ -1182,8 +1180,6 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
     const bool test = eject_after(s, s->step + k + 1);
     const bool split = split_after(s, s->step + k + 1);
     if (flush_bytes > 0) e = cudaMemsetAsync(flush, k & 0xff, flush_bytes, st);
-    if (e == cudaSuccess && head && s->grow_any)
-      e = timed3(MX_K_GROW, st, [&] { mx::launch_grow(s->d, s->step + k, st); });
     if (e == cudaSuccess && head) {
       e = cudaGraphLaunch(s->gt_head, st);
       if (e == cudaSuccess) e = slot_done(s, false, timed3);
@@ -1383,6 +1379,7 @@ mx_status mx_set_state(mx_system* s, const double* xv_host, int coords, long lon
   }
   const int ctr[2] = {(int)(2 * step), (int)(2 * step)};
   MX_CUDA(cudaMemcpyAsync(s->d.kick_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s->st));
+  MX_CUDA(cudaMemcpyAsync(s->d.gstep, &step, sizeof(long long), cudaMemcpyHostToDevice, s->st));
   MX_TRY(sync_status(s));
   s->step = step;
   return MX_OK;
@@ -1476,6 +1473,7 @@ mx_status mx_planets(mx_system* s, double* m_host, double* r_host) {
   MX_TRY(settle(s));
   const int NB = s->NB;
   std::vector<double> mu(NB), rad(NB);
+  if (r_host) mx::launch_radius(s->d, s->st);
   if (NB > 0) {
     MX_CUDA(cudaMemcpyAsync(mu.data(), s->d.bmu, NB * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     MX_CUDA(cudaMemcpyAsync(rad.data(), s->d.brad, NB * sizeof(double), cudaMemcpyDeviceToHost, s->st));
@@ -1647,6 +1645,7 @@ mx_status mx_set_step_index(mx_system* s, long long step) {
   MX_TRY(set_device(s));
   const int ctr[2] = {(int)(2 * step), (int)(2 * step)};
   MX_CUDA(cudaMemcpyAsync(s->d.kick_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s->st));
+  MX_CUDA(cudaMemcpyAsync(s->d.gstep, &step, sizeof(long long), cudaMemcpyHostToDevice, s->st));
   MX_CUDA(cudaStreamSynchronize(s->st));
   s->step = step;
   return MX_OK;

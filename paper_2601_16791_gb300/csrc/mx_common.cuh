@@ -124,6 +124,7 @@ struct Dev {
   // distance at kick time, k_prep), half-width (0: none) and density factor,
   // and the radius (k_grow).
   const Growth* grow;  // [NB]
+  long long* gstep;    // [0] global index of the step under way (its first k_prep reads it)
   double *gap_r, *gap_w, *gap_f, *brad;   // [NB]
   const SysDev* sys;
   const Tile* tiles;
@@ -150,6 +151,8 @@ struct Dev {
   double* h_b1;        // [hist_cap][6][NB] big bodies after the drift (detection endpoint)
   double* h_bx;        // [hist_cap][3][NB] big positions after jump 2 (kick sources)
   double* h_mu;        // [hist_cap][NB] big mu during the slot, -1 for a removed body
+  double* h_rc;        // [hist_cap][NB] big changeover radius during the slot
+  double* h_gap;       // [hist_cap][3][NB] gaps during the slot: centre, half-width, factor
   int* h_ej;           // [hist_cap] 1: the ejection test follows the slot
   int* h_comp;         // [hist_cap][NB] big group of each big body, -1 for none
   int* h_nkick;        // [hist_cap] half kicks ending the slot; -1: a call's leading half kick

@@ -56,9 +56,8 @@ void launch_eject(const Dev& d, int scheduled, cudaStream_t st);
 void launch_elements(const Dev& d, double* out, cudaStream_t st);
 void launch_stat_count(const Dev& d, int* out, cudaStream_t st);
 
-// k_grow.cu (Sec. 3.3): masses, changeover radii, gaps and radii at the start
-// of global step `step` (systems with growth on)
-void launch_grow(const Dev& d, long long step, cudaStream_t st);
+// k_grow.cu (Sec. 3.3): radii of the growing planets now (mx_planets)
+void launch_radius(const Dev& d, cudaStream_t st);
 
 // k_adjoint.cu
 void launch_adjoint_step(const Dev& d, const Adj& a, cudaStream_t st);

@@ -99,22 +99,28 @@ __device__ __forceinline__ void gas_drag_at(const SysDev& S, const GasAt& q, dou
 }
 
 // The gas density factor of a planetesimal at (x, y, .) (the dens_factor
-// listing of Sec. 3.1): 1, or the factor of the last big body (ascending
+// listing of Sec. 3.1): 1, or the factor gf[i] of the last big body (ascending
 // index) whose open gap (Eqs. 8-9) holds the planetesimal's cylindrical
-// distance R strictly inside |R - r_i| < W_i.  r_i (the big body's cylindrical
-// distance at kick time) comes from k_prep, W_i and the factor from k_grow.
-__device__ __forceinline__ double gap_factor(const Dev& d, const SysDev& S, double x, double y) {
+// distance R strictly inside |R - gr[i]| < gw[i].  gr (the big bodies'
+// cylindrical distances at kick time) comes from k_prep, gw and gf from
+// k_grow; the arrays start at the system's first big body.  Not inlined, so
+// that the kick and the catch-up of deferred planetesimals decide alike.
+static __device__ __noinline__ double gap_factor(const double* gr, const double* gw,
+                                                 const double* gf, int nbig, double x, double y) {
   const double R = sqrt(x * x + y * y);
   double f = 1.0;
-  for (int i = 0; i < S.nbig; ++i) {
-    const int b = S.boff + i;
-    const double w = d.gap_w[b];
+  for (int i = 0; i < nbig; ++i) {
+    const double w = gw[i];
     if (w > 0.0) {
-      const double r = d.gap_r[b];
-      if (R < r + w && R > r - w) f = d.gap_f[b];
+      const double r = gr[i];
+      if (R < r + w && R > r - w) f = gf[i];
     }
   }
   return f;
+}
+
+__device__ __forceinline__ double gap_factor(const Dev& d, const SysDev& S, double x, double y) {
+  return gap_factor(d.gap_r + S.boff, d.gap_w + S.boff, d.gap_f + S.boff, S.nbig, x, y);
 }
 
 // The gas's acceleration on one planetesimal at heliocentric position

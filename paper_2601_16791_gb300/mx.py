@@ -180,7 +180,7 @@ def mx_step(sys, n_steps):
 
 
 KERNELS = ("k_prep", "k_jump_kick", "k_jump_drift", "k_detect", "k_sort_keys", "k_groups", "k_bs",
-           "k_catchup", "k_catchup_side", "k_eject", "k_grow")
+           "k_catchup", "k_catchup_side", "k_eject")
 
 
 def mx_step_profiled(sys, n_steps):

@@ -25,16 +25,17 @@ def workload(nsmall=3000):
 
 @pytest.mark.parametrize("k", [0, 17, 40, 41, 75])
 def test_track_masses_and_radii(k):
-    """After one step from global step k the masses are the track's at t = k h
-    and the radii Eqs. 14 / 16 of that state."""
+    """At global step k the radii (Eqs. 14 / 16) are those of the state at
+    t = k h; after one step the masses are the track's at t = k h."""
     w = workload(200)
     s = mx.System(w)
     p = orc.make_params(w.params)
     xv, mu, rc = orc.init(p, w.nbig, w.nsmall, w.m_big, w.xv_helio)
     s.set_state(xv, mx.MX_COORD_DH, k)
     ref = orc.grow_state(p, w.nbig, xv, mu, rc, w.growth, k * 10.0, w.gap_c)
+    _, r = mx.mx_planets(s.h, w.nbig)
     s.step(1)
-    m, r = mx.mx_planets(s.h, w.nbig)
+    m, _ = mx.mx_planets(s.h, w.nbig)
     s.close()
     assert np.max(np.abs(m * p.G - ref["mu"]) / ref["mu"]) <= 1e-14
     assert np.max(np.abs(r - ref["radius"]) / np.abs(ref["radius"])) <= 1e-12
@@ -81,7 +82,6 @@ def test_growth_run_parity():
     m, r = mx.mx_planets(s.h, w.nbig)
     ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
     mx.mx_encounter_log(s.h, ever)
-    assert mx.mx_defer_stats(s.h)[0] == 0          # no deferral with growth
     s.close()
     p = orc.make_params(w.params)
     xv, mu, rc = orc.init(p, w.nbig, w.nsmall, w.m_big, w.xv_helio)
@@ -94,7 +94,28 @@ def test_growth_run_parity():
     assert keep.sum() > 1500 and err[keep].max() <= 1e-9, err[keep].max()
 
 
-def test_runners_agree_and_count_growth_launches():
+def test_growth_with_deferral_is_bit_identical():
+    """Deferred planetesimals replay each step with that step's masses,
+    changeover radii and gaps (recorded per history slot); the result is the
+    direct path's, bit for bit, through core growth and open gaps."""
+    w = workload(30_000)
+    out = []
+    for window in (0, 8):
+        s = mx.System(w)
+        mx.mx_set_defer_window(s.h, window)
+        n0 = mx.mx_defer_stats(s.h)[2]
+        for n in (35, 10, 45):
+            s.step(n)
+        out.append((s.state(mx.MX_COORD_DH), mx.mx_planets(s.h, w.nbig)[0], s.energy()[0],
+                    mx.mx_defer_stats(s.h)[2] - n0))
+        s.close()
+    assert out[0][3] == 0 and out[1][3] > 0, "no body was deferred: the test is vacuous"
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+def test_runners_agree_and_split_every_step():
     w = workload(2000)
     ref = mx.System(w)
     for n in (5, 9):
@@ -104,14 +125,15 @@ def test_runners_agree_and_count_growth_launches():
     s = mx.System(w)
     _, c1, _ = mx.mx_step_profiled(s.h, 5)
     _, c2, _ = mx.mx_step_profiled(s.h, 9)
-    assert c1["k_grow"] == 5 and c2["k_grow"] == 9 and c2["k_jump_kick"] == 18
+    # every step: a first launch (with the growth update) and a last one
+    assert c1["k_prep"] == 10 and c2["k_prep"] == 18 and c2["k_jump_kick"] == 18
     assert np.array_equal(s.state(mx.MX_COORD_DH), want)
     s.close()
     s = mx.System(w)
     flush = torch.empty(32 << 20, dtype=torch.uint8, device="cuda")
     _, c1, _ = mx.mx_step_timed(s.h, 5, flush)
     _, c2, _ = mx.mx_step_timed(s.h, 9, flush)
-    assert c1["k_grow"] == 5 and c2["k_grow"] == 9
+    assert c1["k_prep"] == 10 and c2["k_prep"] == 18
     assert np.array_equal(s.state(mx.MX_COORD_DH), want)
     s.close()
 
