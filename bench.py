@@ -235,7 +235,7 @@ def source_hash(names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"k_jump_kick": ["k_kick.cu", "mx_common.cuh", "mx_physics.cuh"],
+KERNEL_SOURCES = {"k_jump_kick": ["k_kick.cu", "mx_common.cuh", "mx_physics.cuh", "mx_growth.cuh"],
                   "k_jump_drift": ["k_drift.cu", "mx_common.cuh", "mx_kepler.cuh"],
                   "k_detect": ["k_detect.cu", "mx_common.cuh", "mx_encounter.cuh"]}
 
