@@ -350,17 +350,30 @@ def adjoint_leg(nsteps=200, every=50):
         mx.mx_step(traj.h, 1)
     e[1].record()
     e[2].record()
+    mx._check(mx.load().mx_adjoint_encounters(traj.h, 0), "mx_adjoint_encounters")
     for _ in range(reps):
         mx.mx_adjoint_step(traj.h, z, 0, lam, dpar)
     e[3].record()
+    # the same step differentiated through its encounter groups
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mx._check(mx.load().mx_adjoint_encounters(traj.h, 1), "mx_adjoint_encounters")
+    e4.record()
+    for _ in range(reps):
+        mx.mx_adjoint_step(traj.h, z, 0, lam, dpar)
+    e5.record()
     torch.cuda.synchronize()
     f_ms = e[0].elapsed_time(e[1]) / reps
     a_ms = e[2].elapsed_time(e[3]) / reps
+    g_ms = e4.elapsed_time(e5) / reps
     traj.close()
     return {"workload": "adjoint_4core_50k: 4 cores + 50,000 planetesimals, gas, loss on final a",
             "steps": nsteps, "checkpoint_every": every, "forward_s": t_fwd, "backward_s": t_bwd,
             "backward_over_forward": t_bwd / t_fwd, "adjoint_step_ms": a_ms,
-            "forward_step_ms": f_ms, "adjoint_over_forward_step": a_ms / f_ms}
+            "forward_step_ms": f_ms, "adjoint_over_forward_step": a_ms / f_ms,
+            "adjoint_step_ms_through_groups": g_ms,
+            "through_groups_over_forward_step": g_ms / f_ms,
+            "note": ("adjoint_step: encountered planetesimals out of the loss (groups skipped); "
+                     "through_groups: every encounter group recorded and reversed")}
 
 
 def eject_leg(steps=200):

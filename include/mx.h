@@ -358,9 +358,20 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
 /* Reverse of one hybrid step.  dev_state_k: 6xN DH state at the start of
  * step step_k (device); dev_lambda: 6xN cotangent of the state at the end of
  * the step, replaced by the cotangent at its start; dev_dparams [3 n_sys]
- * (device) accumulates d/d(sigma1, gamma, cd_scale) of each system. */
+ * (device) accumulates d/d(sigma1, gamma, cd_scale) of each system.
+ * With encounter groups on (mx_adjoint_encounters), a planetesimal that meets
+ * a big body in the step is differentiated through its Bulirsch-Stoer
+ * integration (Sec. 2: the recomputed group's accepted sub-steps and
+ * extrapolation rows held fixed); with them off it is differentiated as if
+ * drifted, which is exact when its cotangent is zero (a loss that leaves it
+ * out; it is massless, so nothing else depends on it).  A big-big encounter
+ * gives MX_ERR_ENCOUNTER_IN_ADJOINT either way. */
 mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long step_k,
                           double* dev_lambda, double* dev_dparams);
+
+/* on = 1 (the default): mx_adjoint_step integrates and differentiates the
+ * step's encounter groups; 0: it skips them (see mx_adjoint_step). */
+mx_status mx_adjoint_encounters(mx_system* s, int on);
 
 /* Reverse of the set-up transform: cotangent of the initial DH state ->
  * cotangent of the initial heliocentric state (6xN device buffers). */

@@ -5,11 +5,15 @@ reverse sweep.
 
 The loss is the weighted squared change of semimajor axes,
     L = sum_j w_j (a_final,j - a_initial,j)^2,
-with a from the heliocentric state (mx_loss_semimajor).  Bodies flagged for an
-encounter in any step of the forward run get weight 0 (they are massless, so
-nothing else depends on them, and their Bulirsch-Stoer steps are not
-differentiated).  An encounter between two big bodies makes the backward
-raise MX_ERR_ENCOUNTER_IN_ADJOINT.  The k switch of the drag coefficient is
+with a from the heliocentric state (mx_loss_semimajor).  A planetesimal's
+close encounters are differentiated through the Bulirsch-Stoer groups of the
+step, with the accepted sub-steps and extrapolation rows held fixed (the
+adjoint's k_adj_bs.cu).  With mask_encounters=True (the default), planetesimals
+flagged for an encounter in any step get weight 0 instead, and the adjoint
+skips the groups (mx_adjoint_encounters): the derivative is exact for that
+loss and costs about as much as the forward step, where differentiating the
+groups costs their recorded Bulirsch-Stoer integration and its reverse.  An encounter between two big
+bodies makes the backward raise MX_ERR_ENCOUNTER_IN_ADJOINT.  The k switch of the drag coefficient is
 recorded in the forward run and replayed in the recomputation, so the
 reverse sweep sees the branches the forward run took.
 
@@ -75,9 +79,10 @@ class Trajectory:
 
 class SemimajorLoss(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, xv_helio0, gas, traj, w, nsteps, every):
+    def forward(ctx, xv_helio0, gas, traj, w, nsteps, every, mask_encounters):
         ckpts, ever, nbb = traj.run(xv_helio0, gas, nsteps, every, record=True)
-        w_eff = w * (1.0 - ever.to(torch.float64))
+        w_eff = w * (1.0 - ever.to(torch.float64)) if mask_encounters else w
+        ctx.groups = 0 if mask_encounters else 1
         L, seed_f, seed_i = traj.loss(xv_helio0, w_eff)
         ctx.traj, ctx.nsteps, ctx.every, ctx.nbb = traj, nsteps, every, nbb
         ctx.ckpts = ckpts
@@ -95,6 +100,7 @@ class SemimajorLoss(torch.autograd.Function):
         g = float(gL)
         h = traj.h
         mx.mx_kick_branches(h, 2)
+        mx._check(mx.load().mx_adjoint_encounters(h, ctx.groups), "mx_adjoint_encounters")
         lam = (seed_f * g).contiguous()
         dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
         seg = torch.empty((ctx.every, 6, traj.n), dtype=torch.float64, device="cuda")
@@ -111,9 +117,10 @@ class SemimajorLoss(torch.autograd.Function):
         grad0 = torch.empty((6, traj.n), dtype=torch.float64, device="cuda")
         mx.mx_adjoint_init(h, lam, grad0)
         grad0 += g * seed_i
-        return grad0, dpar, None, None, None, None
+        return grad0, dpar, None, None, None, None, None
 
 
-def semimajor_loss(traj, xv_helio0, gas, w, nsteps, every):
+def semimajor_loss(traj, xv_helio0, gas, w, nsteps, every, mask_encounters=True):
     """Differentiable loss of a run of nsteps steps checkpointed every `every`."""
-    return SemimajorLoss.apply(xv_helio0, gas, traj, w, int(nsteps), int(every))
+    return SemimajorLoss.apply(xv_helio0, gas, traj, w, int(nsteps), int(every),
+                               bool(mask_encounters))

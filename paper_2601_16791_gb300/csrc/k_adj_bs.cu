@@ -1,0 +1,405 @@
+// k_adj_bs.cu -- reverse mode through the Bulirsch-Stoer groups of one step
+// (arXiv 2601.16791, Sec. 2: a planetesimal in a close encounter leaves the
+// Kepler drift and is integrated by mdt_bs2 with the big bodies it meets).
+//
+// The adjoint recomputes the step from its start.  After the drift it runs
+// the encounter detection on the recomputed endpoints, groups each flagged
+// planetesimal with the big bodies it meets (pairs sorted by planetesimal,
+// so the groups come in a fixed order), and integrates every group again with
+// the step's thread integrator (mx_bs.cuh).  That integration is done twice:
+// once to count the accepted macro sub-steps, then, with space reserved on a
+// tape, to record each accepted sub-step's length, extrapolation row and
+// starting state.  The planetesimal's result replaces its drifted state.
+//
+// The reverse sweep treats that sequence as fixed (a discrete adjoint of the
+// Gragg-Bulirsch-Stoer map with its accepted steps and rows frozen, as a
+// forward-mode derivative that follows the primal's control flow gives):
+// every accepted sub-step is a fixed linear combination of Stoermer runs
+// (the Aitken-Neville weights of its row), and each Stoermer run is reversed
+// from its recomputed positions with the Jacobian of the group's forces (the
+// star and the (1 - K)-weighted pair forces).  The planetesimal's cotangent
+// at its pre-drift state replaces the drift's; the big bodies' shares are
+// added to theirs by a per-system fold in group order.  Big-big encounters
+// stay refused (ST_ADJ_ENC): a big body's own state never comes from a group.
+#include "mx_bs.cuh"
+#include "mx_common.cuh"
+#include "mx_kernels.h"
+
+namespace mx {
+
+namespace {
+
+__device__ __forceinline__ int pkey_j(unsigned long long k) { return (int)((k >> 32) & 0x7fffffffull); }
+__device__ __forceinline__ int pkey_i(unsigned long long k) { return (int)(k & 0xffffffffull); }
+__device__ __forceinline__ bool pkey_small(unsigned long long k) { return (k >> 63) != 0; }
+
+__device__ int sys_of_body(const Dev& d, int g) {
+  int lo = 0, hi = d.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d.sys[mid].off <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Tape record of one accepted macro sub-step: H, row, then the 6 x nb state.
+__device__ __forceinline__ int tape_stride(int nb) { return 2 + 6 * nb; }
+
+}  // namespace
+
+// One block: the group list from the sorted pair keys.  A group is a
+// planetesimal and the big bodies it meets (keys (1, j, i) ascending: one run
+// per j, its bigs ascending).  A big-big key refuses the adjoint.
+__global__ void __launch_bounds__(1024) k_adj_groups(Dev d, Adj a) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  const int cnt = *d.pair_count;
+  const int n = min(cnt, d.pair_cap);
+  if (threadIdx.x == 0) {
+    s_base = 0;
+    if (cnt > d.pair_cap) atomicOr(d.status, ST_PAIR_OVF);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int p = base + threadIdx.x;
+    bool start = false;
+    unsigned long long key = 0;
+    if (p < n) {
+      key = d.keys[p];
+      if (!pkey_small(key)) atomicOr(d.status, ST_ADJ_ENC);
+      start = pkey_small(key) && (p == 0 || !pkey_small(d.keys[p - 1]) ||
+                                  pkey_j(d.keys[p - 1]) != pkey_j(key));
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, start);
+    if (lane == 0) s_warp[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = s_base;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const int c = s_warp[w];
+        s_warp[w] = run;
+        run += c;
+      }
+      s_base = run;
+    }
+    __syncthreads();
+    if (start) {
+      const int gi = s_warp[warp] + __popc(m & ((1u << lane) - 1u));
+      const int j = pkey_j(key);
+      int q = p + 1;
+      while (q < n && pkey_small(d.keys[q]) && pkey_j(d.keys[q]) == j) ++q;
+      if (gi < a.g_cap) {
+        a.g_small[gi] = j;
+        a.g_key[gi] = p;
+        a.g_nb[gi] = q - p;
+        if (q - p + 1 > kMaxGroup) atomicOr(d.status, ST_GROUP);
+      } else {
+        atomicOr(d.status, ST_WORK_OVF);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.g_count = min(s_base, a.g_cap);
+}
+
+// The group's members (big bodies ascending, then the planetesimal), their
+// constants and their pre-drift states (x2, v1).
+__device__ bool load_adj_group(const Dev& d, const Adj& a, int g, GroupState& G,
+                               double (*Y)[kMaxGroup], int* big, int* jj, int* sys) {
+  const int j = a.g_small[g], p = a.g_key[g], nbb = a.g_nb[g];
+  if (nbb + 1 > kMaxGroup) return false;
+  const int sy = sys_of_body(d, j);
+  const SysDev& S = d.sys[sy];
+  const int N = d.N;
+  G.nb = nbb + 1;
+  for (int m = 0; m <= nbb; ++m) {
+    const int gi = (m < nbb) ? pkey_i(d.keys[p + m]) : j;
+    if (m < nbb) big[m] = gi - S.off;
+    G.mu[m] = (m < nbb) ? d.bmu[S.boff + (gi - S.off)] : 0.0;
+    G.rc[m] = (m < nbb) ? d.brc[S.boff + (gi - S.off)] : 0.0;
+    for (int c = 0; c < 3; ++c) {
+      Y[c][m] = a.x2[(size_t)c * N + gi];
+      Y[3 + c][m] = a.v1[(size_t)c * N + gi];
+    }
+  }
+  *jj = j;
+  *sys = sy;
+  return true;
+}
+
+// Forward: integrate every group (count, reserve, record); the planetesimal's
+// result replaces its drifted state in xv3.
+__global__ void __launch_bounds__(32) k_adj_bs_fwd(Dev d, Adj a) {
+  const int ng = *a.g_count;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    GroupState G;
+    double Y[6][kMaxGroup], Y0[6][kMaxGroup];
+    int big[kMaxGroup], j, sy;
+    a.g_M[g] = -1;
+    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) continue;
+    const SysDev& S = d.sys[sy];
+    for (int c = 0; c < 6; ++c)
+      for (int m = 0; m < G.nb; ++m) Y[c][m] = Y0[c][m];
+    int M = 0, nsub = 0;
+    auto count = [&](double, int, const double (*)[kMaxGroup]) { ++M; };
+    if (!bs_integrate_rec(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub, count)) {
+      atomicOr(d.status, ST_BS);
+      continue;
+    }
+    const int stride = tape_stride(G.nb);
+    const unsigned long long need = (unsigned long long)M * stride;
+    const unsigned long long off = atomicAdd(a.tape_top, need);
+    if (off + need > a.tape_cap) {
+      atomicOr(d.status, ST_WORK_OVF);
+      continue;
+    }
+    double* T = a.tape + off;
+    int rec_m = 0;
+    auto record = [&](double H, int kacc, const double (*Ys)[kMaxGroup]) {
+      double* r = T + (size_t)rec_m * stride;
+      r[0] = H;
+      r[1] = (double)kacc;
+      for (int c = 0; c < 6; ++c)
+        for (int m = 0; m < G.nb; ++m) r[2 + c * G.nb + m] = Ys[c][m];
+      ++rec_m;
+    };
+    for (int c = 0; c < 6; ++c)
+      for (int m = 0; m < G.nb; ++m) Y[c][m] = Y0[c][m];
+    bs_integrate_rec(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub, record);
+    a.g_off[g] = off;
+    a.g_M[g] = M;
+    const int N = d.N, s = G.nb - 1;
+    for (int c = 0; c < 6; ++c) a.xv3[(size_t)c * N + j] = Y[c][s];
+  }
+}
+
+// gX += J_a(X)^T lA for the group's accelerations a(X) (star plus the
+// (1 - K)-weighted pair forces of the massive members, as bs_accel).  For a
+// pair at separation s with weight w(s^2) = mu_i (1 - K(s))/s^3, the force on
+// b is -w dx (dx = x_b - x_i), whose Jacobian in dx is -w I - 2 w' dx dx^T,
+// w' = dw/d(s^2) = mu_i g'(s)/(2s), g = (1 - K)/s^3 (g = 1/s^3 inside 0.1 rc),
+// K' = 30 q^2 (1 - q)^2 / (0.9 rc).
+__device__ void accel_vjp(const GroupState& G, double mu0, const double (*X)[kMaxGroup],
+                          const double (*lA)[kMaxGroup], double (*gX)[kMaxGroup]) {
+  for (int b = 0; b < G.nb; ++b) {
+    const double x = X[0][b], y = X[1][b], z = X[2][b];
+    const double lx = lA[0][b], ly = lA[1][b], lz = lA[2][b];
+    const double r2 = x * x + y * y + z * z;
+    const double r = sqrt(r2);
+    const double ir3 = 1.0 / (r2 * r);
+    const double ir5 = ir3 / r2;
+    const double xl = x * lx + y * ly + z * lz;
+    gX[0][b] += -mu0 * (lx * ir3 - 3.0 * xl * x * ir5);
+    gX[1][b] += -mu0 * (ly * ir3 - 3.0 * xl * y * ir5);
+    gX[2][b] += -mu0 * (lz * ir3 - 3.0 * xl * z * ir5);
+    for (int i = 0; i < G.nb; ++i) {
+      if (i == b || G.mu[i] == 0.0) continue;
+      const double dx = x - X[0][i], dy = y - X[1][i], dz = z - X[2][i];
+      const double s2 = dx * dx + dy * dy + dz * dz;
+      const double rc = fmax(G.rc[b], G.rc[i]);
+      if (s2 >= rc * rc) continue;
+      const double s = sqrt(s2);
+      double gval, dg;
+      if (s2 <= 0.01 * rc * rc) {
+        gval = 1.0 / (s2 * s);
+        dg = -3.0 / (s2 * s2);
+      } else {
+        const double q = (s - 0.1 * rc) / (0.9 * rc);
+        const double K = q * q * q * (10.0 + q * (-15.0 + 6.0 * q));
+        const double Kp = 30.0 * q * q * (1.0 - q) * (1.0 - q) / (0.9 * rc);
+        gval = (1.0 - K) / (s2 * s);
+        dg = -Kp / (s2 * s) - 3.0 * (1.0 - K) / (s2 * s2);
+      }
+      const double w = G.mu[i] * gval;
+      const double wp = G.mu[i] * dg / (2.0 * s);
+      const double dl = dx * lx + dy * ly + dz * lz;
+      const double cx = -w * lx - 2.0 * wp * dl * dx;
+      const double cy = -w * ly - 2.0 * wp * dl * dy;
+      const double cz = -w * lz - 2.0 * wp * dl * dz;
+      gX[0][b] += cx;
+      gX[1][b] += cy;
+      gX[2][b] += cz;
+      gX[0][i] -= cx;
+      gX[1][i] -= cy;
+      gX[2][i] -= cz;
+    }
+  }
+}
+
+// Reverse of one Stoermer run (n sub-steps of length H/n from Y): adds
+// J^T (lO) to lY, with the positions X_0..X_n recomputed here.
+constexpr int kMaxSub = 2 * kBsRows;
+
+__device__ void stoermer_vjp(const GroupState& G, double mu0, const double (*Y)[kMaxGroup],
+                             double H, int n, const double (*lO)[kMaxGroup],
+                             double (*lY)[kMaxGroup], double scale) {
+  double X[kMaxSub + 1][3][kMaxGroup];
+  double A[3][kMaxGroup], D[3][kMaxGroup];
+  const double dd = H / n, d2 = dd * dd;
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < G.nb; ++b) X[0][c][b] = Y[c][b];
+  bs_accel(G, mu0, X[0], A);
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < G.nb; ++b) {
+      D[c][b] = dd * fma(0.5 * dd, A[c][b], Y[3 + c][b]);
+      X[1][c][b] = X[0][c][b] + D[c][b];
+    }
+  for (int s = 1; s < n; ++s) {
+    bs_accel(G, mu0, X[s], A);
+    for (int c = 0; c < 3; ++c)
+      for (int b = 0; b < G.nb; ++b) {
+        D[c][b] = fma(d2, A[c][b], D[c][b]);
+        X[s + 1][c][b] = X[s][c][b] + D[c][b];
+      }
+  }
+  // reverse: O_x = X_n, O_v = D_n/dd + (dd/2) A(X_n)
+  double lX[3][kMaxGroup], lD[3][kMaxGroup], lA[3][kMaxGroup];
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < G.nb; ++b) {
+      lX[c][b] = scale * lO[c][b];
+      lD[c][b] = scale * lO[3 + c][b] / dd;
+      lA[c][b] = scale * 0.5 * dd * lO[3 + c][b];
+    }
+  accel_vjp(G, mu0, X[n], lA, lX);
+  for (int s = n - 1; s >= 1; --s) {
+    // X_{s+1} = X_s + D_{s+1};  D_{s+1} = D_s + d2 A(X_s)
+    for (int c = 0; c < 3; ++c)
+      for (int b = 0; b < G.nb; ++b) {
+        lD[c][b] += lX[c][b];
+        lA[c][b] = d2 * lD[c][b];
+      }
+    accel_vjp(G, mu0, X[s], lA, lX);
+  }
+  // X_1 = X_0 + D_1;  D_1 = dd V_0 + (dd^2/2) A(X_0)
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < G.nb; ++b) {
+      lD[c][b] += lX[c][b];
+      lY[3 + c][b] += dd * lD[c][b];
+      lA[c][b] = 0.5 * d2 * lD[c][b];
+    }
+  accel_vjp(G, mu0, X[0], lA, lX);
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < G.nb; ++b) lY[c][b] += lX[c][b];
+}
+
+// The Aitken-Neville result of row K is sum_i c_i S_i over the Stoermer runs
+// S_0..S_K (the recurrence of bs_integrate is linear in them); c_i is the
+// recurrence applied to the unit vector e_i.
+__device__ void neville_weights(int K, double* c) {
+  for (int l = 0; l <= K; ++l) {
+    double row[kBsRows] = {0.0};
+    for (int k = 0; k <= K; ++k) {
+      double prev = row[0];
+      row[0] = (k == l) ? 1.0 : 0.0;
+      for (int jj = 1; jj <= k; ++jj) {
+        const double t = row[jj];
+        row[jj] = fma(row[jj - 1] - prev, inv_den(k, jj), row[jj - 1]);
+        prev = t;
+      }
+    }
+    c[l] = row[K];
+  }
+}
+
+// Reverse: the planetesimal's cotangent at its BS result (in lam) goes back
+// through the recorded sub-steps; its pre-drift cotangent replaces lam's, the
+// big members' shares go to g_contrib.
+__global__ void __launch_bounds__(32) k_adj_bs_vjp(Dev d, Adj a) {
+  const int ng = *a.g_count;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    const int M = a.g_M[g];
+    if (M < 0) continue;
+    GroupState G;
+    double Y0[6][kMaxGroup];
+    int big[kMaxGroup], j, sy;
+    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) continue;
+    const SysDev& S = d.sys[sy];
+    const int N = d.N, nb = G.nb, s = nb - 1;
+    double lY[6][kMaxGroup], lO[6][kMaxGroup];
+    for (int c = 0; c < 6; ++c)
+      for (int m = 0; m < nb; ++m) lO[c][m] = 0.0;
+    for (int c = 0; c < 6; ++c) lO[c][s] = a.lam[(size_t)c * N + j];
+    const int stride = tape_stride(nb);
+    for (int k = M - 1; k >= 0; --k) {
+      const double* r = a.tape + a.g_off[g] + (size_t)k * stride;
+      const double H = r[0];
+      const int K = (int)r[1];
+      double Ys[6][kMaxGroup];
+      for (int c = 0; c < 6; ++c)
+        for (int m = 0; m < nb; ++m) Ys[c][m] = r[2 + c * nb + m];
+      double cw[kBsRows];
+      neville_weights(K, cw);
+      for (int c = 0; c < 6; ++c)
+        for (int m = 0; m < nb; ++m) lY[c][m] = 0.0;
+      for (int i = 0; i <= K; ++i)
+        stoermer_vjp(G, S.mu0, Ys, H, 2 * (i + 1), lO, lY, cw[i]);
+      for (int c = 0; c < 6; ++c)
+        for (int m = 0; m < nb; ++m) lO[c][m] = lY[c][m];
+    }
+    for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + j] = lO[c][s];
+    double* out = a.g_contrib + (size_t)g * 6 * kMaxGroup;
+    for (int m = 0; m < s; ++m)
+      for (int c = 0; c < 6; ++c) out[6 * m + c] = lO[c][m];
+  }
+}
+
+// Per system: the big bodies' shares, added in group order (groups are sorted
+// by planetesimal, so a system's groups are contiguous), and the sum of the
+// position shares for jump 1's momentum term.
+__global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
+  const int sys = blockIdx.x;
+  const SysDev& S = d.sys[sys];
+  const int N = d.N;
+  const int ng = *a.g_count;
+  for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int g = 0; g < ng; ++g) {
+      const int j = a.g_small[g];
+      if (j < S.off || j >= S.off + S.n || a.g_M[g] < 0) continue;
+      const int p = a.g_key[g], nbb = a.g_nb[g];
+      for (int m = 0; m < nbb; ++m) {
+        if (pkey_i(d.keys[p + m]) - S.off != i) continue;
+        const double* c6 = a.g_contrib + (size_t)g * 6 * kMaxGroup + 6 * m;
+        for (int c = 0; c < 6; ++c) acc[c] += c6[c];
+      }
+    }
+    const int gi = S.off + i;
+    for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + gi] += acc[c];
+  }
+  if (threadIdx.x < 3) {
+    double sx = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      const int j = a.g_small[g];
+      if (j < S.off || j >= S.off + S.n || a.g_M[g] < 0) continue;
+      const int nbb = a.g_nb[g];
+      for (int m = 0; m < nbb; ++m) sx += a.g_contrib[(size_t)g * 6 * kMaxGroup + 6 * m + threadIdx.x];
+    }
+    a.bs_xsum[3 * sys + threadIdx.x] = sx;
+  }
+}
+
+void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
+  // detection on the recomputed endpoints, without touching the step's log
+  Dev dd = d;
+  dd.ever = nullptr;
+  dd.defer = 0;
+  cudaMemsetAsync(d.flags, 0, d.N, st);
+  cudaMemsetAsync(d.pair_count, 0, sizeof(int), st);
+  cudaMemsetAsync(a.tape_top, 0, sizeof(unsigned long long), st);
+  launch_detect(dd, a.x2, a.xv3, d.flags, d.keys, d.pair_count, d.pair_cap, 1, st);
+  launch_sort_keys(d.keys, d.pair_count, d.pair_cap, 0, st);
+  k_adj_groups<<<1, 1024, 0, st>>>(d, a);
+  k_adj_bs_fwd<<<nblocks, 32, 0, st>>>(d, a);
+}
+
+void launch_adjoint_bs_vjp(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
+  k_adj_bs_vjp<<<nblocks, 32, 0, st>>>(d, a);
+}
+
+void launch_adjoint_bs_fold(const Dev& d, const Adj& a, cudaStream_t st) {
+  k_adj_bs_fold<<<d.nsys, kThreads, 0, st>>>(d, a);
+}
+
+}  // namespace mx

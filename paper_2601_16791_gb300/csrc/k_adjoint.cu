@@ -4,10 +4,10 @@
 //
 // mx_adjoint_step receives the state z0 at the start of a step and the
 // cotangent of the state at its end, recomputes the step's intermediate
-// states from z0 (no Bulirsch-Stoer: bodies that met an encounter carry a
-// zero cotangent, because they are massless and left out of the loss, and a
-// big-big encounter makes the adjoint refuse), then sweeps back:
-//   kick 2 -> jump 2 -> drift -> jump 1 -> kick 1.
+// states from z0 (a planetesimal that meets a big body is integrated by
+// Bulirsch-Stoer from its pre-drift state, k_adj_bs.cu; a big-big encounter
+// makes the adjoint refuse), then sweeps back:
+//   kick 2 -> jump 2 -> drift or Bulirsch-Stoer -> jump 1 -> kick 1.
 // Couplings of all bodies to the few big bodies -- the big sources of the
 // gravity Jacobian, the momentum P inside both jumps and inside the drag's
 // heliocentric velocity -- are summed per tile in a fixed order and then per
@@ -564,7 +564,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_drift_vjp(Dev d, Adj a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
   double own[3] = {0, 0, 0};
-  if (act) {
+  // a planetesimal in an encounter group already holds its cotangent at the
+  // pre-drift state (k_adj_bs_vjp); it only enters the jump's sum
+  const bool in_group = a.groups && act && j - S.off >= S.nbig && d.flags[j];
+  if (in_group)
+    for (int c = 0; c < 3; ++c) own[c] = a.lam[(size_t)c * N + j];
+  if (act && !in_group) {
     const double x[3] = {a.x2[j], a.x2[(size_t)N + j], a.x2[2 * (size_t)N + j]};
     const double v[3] = {a.v1[j], a.v1[(size_t)N + j], a.v1[2 * (size_t)N + j]};
     double l1[3], m1[3], l0[3], m0[3];
@@ -603,6 +608,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_jump1(Dev d, Adj a) {
     double sum = 0;
     for (int tt = 0; tt < d.ntiles; ++tt)
       if (d.tiles[tt].sys == sys) sum += a.part[a.poff[tt] + threadIdx.x];
+    if (a.groups) sum += a.bs_xsum[3 * sys + threadIdx.x];   // the big bodies' BS shares
     lP[threadIdx.x] = 0.5 * S.h * S.inv_mu0 * sum;
   }
   __syncthreads();
@@ -621,13 +627,16 @@ void launch_adjoint_step(const Dev& d, const Adj& a, cudaStream_t st) {
   k_adj_kick1_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a);
   k_adj_momentum<<<d.nsys, kThreads, 0, st>>>(d, a.v1, a.v1 + N, a.v1 + 2 * (size_t)N, a.P, 1);
   k_adj_move_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a, 1);
+  if (a.groups) launch_adjoint_bs_fwd(d, a, a.bs_blocks, st);
   k_adj_momentum<<<d.nsys, kThreads, 0, st>>>(d, a.xv3 + 3 * (size_t)N, a.xv3 + 4 * (size_t)N,
                                                a.xv3 + 5 * (size_t)N, a.P, 2);
   k_adj_move_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a, 2);
   // reverse sweep: kick 2 (at x4, v3, P3), jump 2, drift, jump 1, kick 1 (at x0, v0, P0)
   k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, a.x4, a.xv3 + 3 * (size_t)N, 2, 2 * a.step + 1);
   k_adj_fold_kick<<<d.nsys, kThreads, 0, st>>>(d, a, 2);
+  if (a.groups) launch_adjoint_bs_vjp(d, a, a.bs_blocks, st);
   k_adj_drift_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a);
+  if (a.groups) launch_adjoint_bs_fold(d, a, st);
   k_adj_fold_jump1<<<d.nsys, kThreads, 0, st>>>(d, a);
   k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, a.z0, a.z0 + 3 * (size_t)N, 0, 2 * a.step);
   k_adj_fold_kick<<<d.nsys, kThreads, 0, st>>>(d, a, 1);

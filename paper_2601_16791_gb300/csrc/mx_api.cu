@@ -189,6 +189,13 @@ struct mx_system {
   // adjoint scratch (allocated on first use)
   double *a_v1 = nullptr, *a_x2 = nullptr, *a_xv3 = nullptr, *a_x4 = nullptr;
   double *a_part = nullptr, *a_P = nullptr, *a_L = nullptr;
+  // adjoint through the encounter groups (k_adj_bs.cu)
+  int a_gcap = 0;
+  int *a_gsmall = nullptr, *a_gkey = nullptr, *a_gnb = nullptr, *a_gM = nullptr, *a_gcount = nullptr;
+  unsigned long long *a_goff = nullptr, *a_tape_top = nullptr;
+  double *a_gcontrib = nullptr, *a_tape = nullptr, *a_bsx = nullptr;
+  unsigned long long a_tape_cap = 0;
+  int a_groups = 1;               // mx_adjoint_encounters
   int* a_poff = nullptr;
   size_t a_part_cap = 0;
   int a_poff_tiles = -1;          // tile count a_poff was built for
@@ -1537,11 +1544,29 @@ namespace {
 
 // Per-tile partial records for the adjoint and the loss: 3 doubles per big
 // body of the tile's system plus 9.
+// Encounter groups per adjoint step, and the doubles of their recorded
+// Bulirsch-Stoer sub-steps (a two-body group's sub-step takes 14).
+constexpr int kAdjGroups = 1 << 14;
+constexpr size_t kAdjTape = (size_t)1 << 23;
+
 mx_status ensure_adjoint(mx_system* s) {
   const int N = s->N;
   if (!s->a_v1) {
-    MX_TRY(dalloc(s, &s->a_v1, (size_t)3 * N));
-    MX_TRY(dalloc(s, &s->a_x2, (size_t)3 * N));
+    MX_TRY(dalloc(s, &s->a_x2, (size_t)6 * N));   // x2 and v1: one 6 x N pre-drift state
+    s->a_v1 = s->a_x2 + 3 * (size_t)N;
+    const int gcap = std::min(s->d.pair_cap, kAdjGroups);
+    s->a_gcap = gcap;
+    MX_TRY(dalloc(s, &s->a_gsmall, gcap));
+    MX_TRY(dalloc(s, &s->a_gkey, gcap));
+    MX_TRY(dalloc(s, &s->a_gnb, gcap));
+    MX_TRY(dalloc(s, &s->a_gM, gcap));
+    MX_TRY(dalloc(s, &s->a_gcount, 1));
+    MX_TRY(dalloc(s, &s->a_goff, gcap));
+    MX_TRY(dalloc(s, &s->a_gcontrib, (size_t)gcap * mx::kMaxGroup * 6));
+    MX_TRY(dalloc(s, &s->a_tape, kAdjTape));
+    MX_TRY(dalloc(s, &s->a_tape_top, 1));
+    MX_TRY(dalloc(s, &s->a_bsx, 3 * s->h_sys.size()));
+    s->a_tape_cap = kAdjTape;
     MX_TRY(dalloc(s, &s->a_xv3, (size_t)6 * N));
     MX_TRY(dalloc(s, &s->a_x4, (size_t)3 * N));
     MX_TRY(dalloc(s, &s->a_P, 9 * s->h_sys.size()));
@@ -1665,6 +1690,12 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
   return sync_status(s);
 }
 
+mx_status mx_adjoint_encounters(mx_system* s, int on) {
+  if (!s || (on != 0 && on != 1)) return fail(MX_ERR_ARG, "invalid arguments");
+  s->a_groups = on;
+  return MX_OK;
+}
+
 mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_grad_helio) {
   if (!s || !dev_lambda || !dev_grad_helio) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
@@ -1698,6 +1729,20 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   a.P = s->a_P;
   a.dpar = dev_dparams;
   a.step = (int)step_k;
+  a.groups = s->a_groups;
+  a.g_cap = s->a_gcap;
+  a.bs_blocks = s->bs_blocks;
+  a.g_small = s->a_gsmall;
+  a.g_key = s->a_gkey;
+  a.g_nb = s->a_gnb;
+  a.g_M = s->a_gM;
+  a.g_count = s->a_gcount;
+  a.g_off = s->a_goff;
+  a.g_contrib = s->a_gcontrib;
+  a.tape = s->a_tape;
+  a.tape_top = s->a_tape_top;
+  a.tape_cap = s->a_tape_cap;
+  a.bs_xsum = s->a_bsx;
   (void)N;
   mx::launch_adjoint_step(s->d, a, s->st);
   return sync_status(s);

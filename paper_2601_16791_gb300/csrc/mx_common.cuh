@@ -182,6 +182,17 @@ struct Adj {
   double* P;          // 9 per system: P0, P1, P3
   double* dpar;       // 3 per system, accumulated
   int step;           // index of the step (recorded k branches)
+  // Bulirsch-Stoer groups (k_adj_bs.cu): x2 and v1 are the two halves of one
+  // 6 x N pre-drift state; groups sorted by planetesimal
+  int groups;                    // 0: no encounter groups (bodies in them carry no cotangent)
+  int g_cap, bs_blocks;
+  int *g_small, *g_key, *g_nb, *g_M, *g_count;
+  unsigned long long* g_off;     // tape offset of each group
+  double* g_contrib;             // [g_cap][kMaxGroup][6] big members' cotangents
+  double* tape;                  // accepted sub-steps: H, row, 6 x nb start state
+  unsigned long long* tape_top;
+  unsigned long long tape_cap;
+  double* bs_xsum;               // 3 per system: sum of the big shares' position parts
 };
 
 // ------------------------------------------------------------------ helpers

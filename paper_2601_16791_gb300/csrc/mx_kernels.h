@@ -61,6 +61,11 @@ void launch_radius(const Dev& d, cudaStream_t st);
 
 // k_adjoint.cu
 void launch_adjoint_step(const Dev& d, const Adj& a, cudaStream_t st);
+// k_adj_bs.cu: the step's encounter groups inside the adjoint (forward with a
+// tape, reverse, per-system fold of the big bodies' shares)
+void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t st);
+void launch_adjoint_bs_vjp(const Dev& d, const Adj& a, int nblocks, cudaStream_t st);
+void launch_adjoint_bs_fold(const Dev& d, const Adj& a, cudaStream_t st);
 void launch_loss(const Dev& d, const double* xvh0, const double* w, double* seed_f, double* seed_i,
                  double* part, const int* poff, double* Lsys, cudaStream_t st);
 void launch_init_vjp(const Dev& d, const double* lam, double* grad, cudaStream_t st);

@@ -96,6 +96,7 @@ _SIGS = {
     "mx_body_status": (_I, [_P, _P, _P]),
     "mx_elements": (_I, [_P, _P]),
     "mx_set_growth": (_I, [_P, _I, _P, _D]),
+    "mx_adjoint_encounters": (_I, [_P, _I]),
     "mx_planets": (_I, [_P, _P, _P]),
 }
 

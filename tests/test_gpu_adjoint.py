@@ -5,9 +5,15 @@ Loss: weighted squared change of the planetesimals' semimajor axes after a
 checkpointed run (4 giant cores + planetesimals with gas drag, the shape of
 the adjoint workload).  Gradients w.r.t. the initial heliocentric state and
 (Sigma1, gamma, C_D factor) are checked along random directions:
-  * against the oracle's dual-number JVP: relative error <= 1e-8;
-  * against central differences of the GPU loss (recorded C_D branches
-    replayed): relative error <= 1e-5 at a step on the plateau.
+  * planetesimals that met a core masked out of the loss: against the
+    oracle's dual-number JVP, relative error <= 1e-8, and against central
+    differences of the GPU loss (recorded C_D branches replayed), <= 1e-5 at
+    a step on the plateau;
+  * every planetesimal in the loss, so the derivative runs through the
+    Bulirsch-Stoer groups (accepted sub-steps held fixed): against the
+    oracle's JVP, whose dual numbers follow its own integrator's steps,
+    relative error <= 1e-6 (the two integrators' sequences agree only to the
+    Bulirsch-Stoer tolerance).
 """
 import numpy as np
 import pytest
@@ -47,10 +53,10 @@ def _directions(w, k, rng):
     return out
 
 
-def _grad(traj, xv0, gas, wts, nsteps, every):
+def _grad(traj, xv0, gas, wts, nsteps, every, mask=True):
     x = xv0.clone().requires_grad_(True)
     p = gas.clone().requires_grad_(True)
-    L = semimajor_loss(traj, x, p, wts, nsteps, every)
+    L = semimajor_loss(traj, x, p, wts, nsteps, every, mask_encounters=mask)
     L.backward()
     return float(L.detach()), x.grad.detach().cpu().numpy(), p.grad.detach().cpu().numpy()
 
@@ -77,6 +83,28 @@ def test_adjoint_vs_oracle_jvp():
     traj.close()
 
 
+def test_adjoint_through_encounters_vs_oracle_jvp():
+    w, traj, xv0, gas, wts = _setup()
+    L, gx, gp = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every, mask=False)
+    _, gxm, gpm = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every, mask=True)
+    ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(traj.h, ever)
+    met = ever.cpu().numpy()[w.nbig:].astype(bool)
+    assert met.sum() > 0
+    # the bodies that met a core now carry a gradient
+    assert np.abs(gx[:, w.nbig:][:, met]).max() > 0 and not np.abs(gxm[:, w.nbig:][:, met]).any()
+    p = orc.make_params(w.params)
+    w_small = np.full(w.nsmall, 1.0 / w.nsmall)
+    rng = np.random.default_rng(13)
+    for dxv, dpar in _directions(w, 4, rng):
+        Lo, jvp = orc.jvp_loss(p, w.nbig, w.m_big, w.xv_helio, w.rp_km, w.rhop, w_small,
+                               w.nsteps, dxv, dpar)
+        ours = float((gx * dxv).sum() + (gp * dpar).sum())
+        assert abs(Lo - L) <= 1e-9 * abs(Lo)
+        assert abs(ours - jvp) <= 1e-6 * abs(jvp), (ours, jvp)
+    traj.close()
+
+
 def test_adjoint_vs_central_differences():
     w, traj, xv0, gas, wts = _setup(nsmall=200, nsteps=30)
     L, gx, gp = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every)
@@ -100,7 +128,7 @@ def test_adjoint_vs_central_differences():
 
 def test_adjoint_is_deterministic():
     w, traj, xv0, gas, wts = _setup(nsmall=150, nsteps=20)
-    a = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every)
-    b = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every)
+    a = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every, mask=False)
+    b = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every, mask=False)
     assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
     traj.close()
