@@ -6,10 +6,12 @@
 // the encounter detection on the recomputed endpoints, groups each flagged
 // planetesimal with the big bodies it meets (pairs sorted by planetesimal,
 // so the groups come in a fixed order), and integrates every group again with
-// the step's thread integrator (mx_bs.cuh).  That integration is done twice:
-// once to count the accepted macro sub-steps, then, with space reserved on a
-// tape, to record each accepted sub-step's length, extrapolation row and
-// starting state.  The planetesimal's result replaces its drifted state.
+// the arithmetic of the step's thread integrator (mx_bs.cuh), one warp per
+// group: lane r runs the Stoermer row with 2(r+1) sub-steps, lane 0 builds
+// the Aitken-Neville table and takes the first converged row, as the
+// sequential search does.  Each accepted macro sub-step's length,
+// extrapolation row and starting state go to the group's region of a tape.
+// The planetesimal's result replaces its drifted state.
 //
 // The reverse sweep treats that sequence as fixed (a discrete adjoint of the
 // Gragg-Bulirsch-Stoer map with its accepted steps and rows frozen, as a
@@ -17,7 +19,8 @@
 // every accepted sub-step is a fixed linear combination of Stoermer runs
 // (the Aitken-Neville weights of its row), and each Stoermer run is reversed
 // from its recomputed positions with the Jacobian of the group's forces (the
-// star and the (1 - K)-weighted pair forces).  The planetesimal's cotangent
+// star and the (1 - K)-weighted pair forces), one row per lane, the lanes'
+// shares summed in a fixed butterfly.  The planetesimal's cotangent
 // at its pre-drift state replaces the drift's; the big bodies' shares are
 // added to theirs by a per-system fold in group order.  Big-big encounters
 // stay refused (ST_ADJ_ENC): a big body's own state never comes from a group.
@@ -43,8 +46,10 @@ __device__ int sys_of_body(const Dev& d, int g) {
   return lo;
 }
 
-// Tape record of one accepted macro sub-step: H, row, then the 6 x nb state.
+// Tape record of one accepted macro sub-step: H, row, then the 6 x nb state;
+// each group has room for kAdjMaxSteps of them.
 __device__ __forceinline__ int tape_stride(int nb) { return 2 + 6 * nb; }
+constexpr int kAdjMaxSteps = 128;
 
 }  // namespace
 
@@ -101,7 +106,37 @@ __global__ void __launch_bounds__(1024) k_adj_groups(Dev d, Adj a) {
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *a.g_count = min(s_base, a.g_cap);
+  const int ng = min(s_base, a.g_cap);
+  if (threadIdx.x == 0) *a.g_count = ng;
+  // tape regions: an exclusive scan of kAdjMaxSteps records per group
+  __shared__ unsigned long long s_wsum[32];
+  __shared__ unsigned long long s_run;
+  if (threadIdx.x == 0) s_run = 0;
+  __syncthreads();
+  for (int base = 0; base < ng; base += blockDim.x) {
+    const int g = base + threadIdx.x;
+    unsigned long long v = 0;
+    if (g < ng) v = (unsigned long long)kAdjMaxSteps * tape_stride(min(a.g_nb[g], kMaxGroup - 1) + 1);
+    unsigned long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long run = s_run;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const unsigned long long c = s_wsum[w];
+        s_wsum[w] = run;
+        run += c;
+      }
+      s_run = run;
+    }
+    __syncthreads();
+    if (g < ng) a.g_off[g] = s_wsum[warp] + inc - v;
+    __syncthreads();
+  }
 }
 
 // The group's members (big bodies ascending, then the planetesimal), their
@@ -129,49 +164,121 @@ __device__ bool load_adj_group(const Dev& d, const Adj& a, int g, GroupState& G,
   return true;
 }
 
-// Forward: integrate every group (count, reserve, record); the planetesimal's
-// result replaces its drifted state in xv3.
+// Forward, one warp per group: lane r < kBsRows runs Stoermer row r from the
+// macro sub-step's start; lane 0 extrapolates, checks and (on acceptance)
+// records the sub-step and passes the new state to the other lanes through
+// shared memory.  The arithmetic and the decisions are bs_integrate's.  The
+// planetesimal's result replaces its drifted state in xv3.
 __global__ void __launch_bounds__(32) k_adj_bs_fwd(Dev d, Adj a) {
+  __shared__ double sraw[kBsRows][6][kMaxGroup];
+  __shared__ double sY[6][kMaxGroup];
+  const int lane = threadIdx.x;
   const int ng = *a.g_count;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+  for (int g = blockIdx.x; g < ng; g += gridDim.x) {
     GroupState G;
-    double Y[6][kMaxGroup], Y0[6][kMaxGroup];
+    double Y[6][kMaxGroup];
     int big[kMaxGroup], j, sy;
-    a.g_M[g] = -1;
-    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) continue;
-    const SysDev& S = d.sys[sy];
-    for (int c = 0; c < 6; ++c)
-      for (int m = 0; m < G.nb; ++m) Y[c][m] = Y0[c][m];
-    int M = 0, nsub = 0;
-    auto count = [&](double, int, const double (*)[kMaxGroup]) { ++M; };
-    if (!bs_integrate_rec(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub, count)) {
-      atomicOr(d.status, ST_BS);
+    if (!load_adj_group(d, a, g, G, Y, big, &j, &sy)) {
+      if (lane == 0) a.g_M[g] = -1;
       continue;
     }
-    const int stride = tape_stride(G.nb);
-    const unsigned long long need = (unsigned long long)M * stride;
-    const unsigned long long off = atomicAdd(a.tape_top, need);
-    if (off + need > a.tape_cap) {
-      atomicOr(d.status, ST_WORK_OVF);
+    const SysDev& S = d.sys[sy];
+    const int nb = G.nb, stride = tape_stride(nb);
+    const unsigned long long off = a.g_off[g];
+    if (off + (unsigned long long)kAdjMaxSteps * stride > a.tape_cap) {
+      if (lane == 0) {
+        a.g_M[g] = -1;
+        atomicOr(d.status, ST_WORK_OVF);
+      }
       continue;
     }
     double* T = a.tape + off;
-    int rec_m = 0;
-    auto record = [&](double H, int kacc, const double (*Ys)[kMaxGroup]) {
-      double* r = T + (size_t)rec_m * stride;
-      r[0] = H;
-      r[1] = (double)kacc;
-      for (int c = 0; c < 6; ++c)
-        for (int m = 0; m < G.nb; ++m) r[2 + c * G.nb + m] = Ys[c][m];
-      ++rec_m;
-    };
-    for (int c = 0; c < 6; ++c)
-      for (int m = 0; m < G.nb; ++m) Y[c][m] = Y0[c][m];
-    bs_integrate_rec(G, S.mu0, S.h, d.bs_tol, d.bs_max_sub, Y, &nsub, record);
-    a.g_off[g] = off;
-    a.g_M[g] = M;
-    const int N = d.N, s = G.nb - 1;
-    for (int c = 0; c < 6; ++c) a.xv3[(size_t)c * N + j] = Y[c][s];
+    const double tol2 = d.bs_tol * d.bs_tol;
+    double rem = S.h, H = S.h;
+    int nsub = 0, M = 0;
+    bool ok = true;
+    while (rem != 0.0) {
+      if (nsub >= d.bs_max_sub || M >= kAdjMaxSteps) {
+        ok = false;
+        break;
+      }
+      ++nsub;
+      if (fabs(H) > fabs(rem)) H = rem;
+      if (lane < kBsRows) {
+        double raw[6][kMaxGroup];
+        stoermer(G, S.mu0, Y, H, 2 * (lane + 1), raw);
+        for (int c = 0; c < 6; ++c)
+          for (int b = 0; b < nb; ++b) sraw[lane][c][b] = raw[c][b];
+      }
+      __syncwarp();
+      int kacc = -1;
+      if (lane == 0) {
+        double row[kBsRows][6][kMaxGroup];
+        double xscal[kMaxGroup], vscal[kMaxGroup];
+        for (int b = 0; b < nb; ++b) {
+          xscal[b] = 1.0 / fma(Y[0][b], Y[0][b], fma(Y[1][b], Y[1][b], Y[2][b] * Y[2][b]));
+          vscal[b] = 1.0 / fma(Y[3][b], Y[3][b], fma(Y[4][b], Y[4][b], Y[5][b] * Y[5][b]));
+        }
+        for (int k = 0; k < kBsRows && kacc < 0; ++k) {
+          for (int c = 0; c < 6; ++c)
+            for (int b = 0; b < nb; ++b) {
+              double prev = row[0][c][b];
+              row[0][c][b] = sraw[k][c][b];
+              for (int jj = 1; jj <= k; ++jj) {
+                const double t = row[jj][c][b];
+                row[jj][c][b] = fma(row[jj - 1][c][b] - prev, inv_den(k, jj), row[jj - 1][c][b]);
+                prev = t;
+              }
+            }
+          if (k >= 1) {
+            double err = 0.0;
+            for (int b = 0; b < nb; ++b) {
+              double ex = 0.0, ev = 0.0;
+              for (int c = 0; c < 3; ++c) {
+                const double dx = row[k][c][b] - row[k - 1][c][b];
+                const double dv = row[k][3 + c][b] - row[k - 1][3 + c][b];
+                ex = fma(dx, dx, ex);
+                ev = fma(dv, dv, ev);
+              }
+              err = fmax(err, fmax(ex * xscal[b], ev * vscal[b]));
+            }
+            if (err <= tol2) kacc = k;
+          }
+        }
+        if (kacc >= 0) {
+          double* r = T + (size_t)M * stride;
+          r[0] = H;
+          r[1] = (double)kacc;
+          for (int c = 0; c < 6; ++c)
+            for (int b = 0; b < nb; ++b) {
+              r[2 + c * nb + b] = Y[c][b];
+              sY[c][b] = row[kacc][c][b];
+            }
+        }
+      }
+      kacc = __shfl_sync(0xffffffffu, kacc, 0);
+      __syncwarp();
+      if (kacc >= 0) {
+        for (int c = 0; c < 6; ++c)
+          for (int b = 0; b < nb; ++b) Y[c][b] = sY[c][b];
+        rem -= H;
+        H *= 1.3;
+        ++M;
+      } else {
+        H *= 0.5;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      if (!ok) {
+        atomicOr(d.status, M >= kAdjMaxSteps ? ST_WORK_OVF : ST_BS);
+        a.g_M[g] = -1;
+      } else {
+        a.g_M[g] = M;
+        const int N = d.N, s = nb - 1;
+        for (int c = 0; c < 6; ++c) a.xv3[(size_t)c * N + j] = Y[c][s];
+      }
+    }
   }
 }
 
@@ -303,12 +410,15 @@ __device__ void neville_weights(int K, double* c) {
   }
 }
 
-// Reverse: the planetesimal's cotangent at its BS result (in lam) goes back
-// through the recorded sub-steps; its pre-drift cotangent replaces lam's, the
-// big members' shares go to g_contrib.
+// Reverse, one warp per group: the planetesimal's cotangent at its BS result
+// (in lam) goes back through the recorded sub-steps, lane r <= K reversing
+// Stoermer row r with its Aitken-Neville weight and the lanes' shares summed
+// by a butterfly (every lane ends with the same sum).  The planetesimal's
+// pre-drift cotangent replaces lam's; the big members' shares go to g_contrib.
 __global__ void __launch_bounds__(32) k_adj_bs_vjp(Dev d, Adj a) {
+  const int lane = threadIdx.x;
   const int ng = *a.g_count;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+  for (int g = blockIdx.x; g < ng; g += gridDim.x) {
     const int M = a.g_M[g];
     if (M < 0) continue;
     GroupState G;
@@ -326,22 +436,29 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp(Dev d, Adj a) {
       const double* r = a.tape + a.g_off[g] + (size_t)k * stride;
       const double H = r[0];
       const int K = (int)r[1];
-      double Ys[6][kMaxGroup];
-      for (int c = 0; c < 6; ++c)
-        for (int m = 0; m < nb; ++m) Ys[c][m] = r[2 + c * nb + m];
-      double cw[kBsRows];
-      neville_weights(K, cw);
       for (int c = 0; c < 6; ++c)
         for (int m = 0; m < nb; ++m) lY[c][m] = 0.0;
-      for (int i = 0; i <= K; ++i)
-        stoermer_vjp(G, S.mu0, Ys, H, 2 * (i + 1), lO, lY, cw[i]);
+      if (lane <= K) {
+        double Ys[6][kMaxGroup];
+        for (int c = 0; c < 6; ++c)
+          for (int m = 0; m < nb; ++m) Ys[c][m] = r[2 + c * nb + m];
+        double cw[kBsRows];
+        neville_weights(K, cw);
+        stoermer_vjp(G, S.mu0, Ys, H, 2 * (lane + 1), lO, lY, cw[lane]);
+      }
       for (int c = 0; c < 6; ++c)
-        for (int m = 0; m < nb; ++m) lO[c][m] = lY[c][m];
+        for (int m = 0; m < nb; ++m) {
+          double v = lY[c][m];
+          for (int o = 1; o < kBsRows; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          lO[c][m] = v;
+        }
     }
-    for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + j] = lO[c][s];
-    double* out = a.g_contrib + (size_t)g * 6 * kMaxGroup;
-    for (int m = 0; m < s; ++m)
-      for (int c = 0; c < 6; ++c) out[6 * m + c] = lO[c][m];
+    if (lane == 0) {
+      for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + j] = lO[c][s];
+      double* out = a.g_contrib + (size_t)g * 6 * kMaxGroup;
+      for (int m = 0; m < s; ++m)
+        for (int c = 0; c < 6; ++c) out[6 * m + c] = lO[c][m];
+    }
   }
 }
 
@@ -387,7 +504,6 @@ void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t
   dd.defer = 0;
   cudaMemsetAsync(d.flags, 0, d.N, st);
   cudaMemsetAsync(d.pair_count, 0, sizeof(int), st);
-  cudaMemsetAsync(a.tape_top, 0, sizeof(unsigned long long), st);
   launch_detect(dd, a.x2, a.xv3, d.flags, d.keys, d.pair_count, d.pair_cap, 1, st);
   launch_sort_keys(d.keys, d.pair_count, d.pair_cap, 0, st);
   k_adj_groups<<<1, 1024, 0, st>>>(d, a);

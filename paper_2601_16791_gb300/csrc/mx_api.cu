@@ -192,7 +192,7 @@ struct mx_system {
   // adjoint through the encounter groups (k_adj_bs.cu)
   int a_gcap = 0;
   int *a_gsmall = nullptr, *a_gkey = nullptr, *a_gnb = nullptr, *a_gM = nullptr, *a_gcount = nullptr;
-  unsigned long long *a_goff = nullptr, *a_tape_top = nullptr;
+  unsigned long long* a_goff = nullptr;
   double *a_gcontrib = nullptr, *a_tape = nullptr, *a_bsx = nullptr;
   unsigned long long a_tape_cap = 0;
   int a_groups = 1;               // mx_adjoint_encounters
@@ -1545,7 +1545,8 @@ namespace {
 // Per-tile partial records for the adjoint and the loss: 3 doubles per big
 // body of the tile's system plus 9.
 // Encounter groups per adjoint step, and the doubles of their recorded
-// Bulirsch-Stoer sub-steps (a two-body group's sub-step takes 14).
+// Bulirsch-Stoer sub-steps (each group has room for 128 sub-steps; a
+// two-body group's sub-step takes 14 doubles).
 constexpr int kAdjGroups = 1 << 14;
 constexpr size_t kAdjTape = (size_t)1 << 23;
 
@@ -1564,7 +1565,6 @@ mx_status ensure_adjoint(mx_system* s) {
     MX_TRY(dalloc(s, &s->a_goff, gcap));
     MX_TRY(dalloc(s, &s->a_gcontrib, (size_t)gcap * mx::kMaxGroup * 6));
     MX_TRY(dalloc(s, &s->a_tape, kAdjTape));
-    MX_TRY(dalloc(s, &s->a_tape_top, 1));
     MX_TRY(dalloc(s, &s->a_bsx, 3 * s->h_sys.size()));
     s->a_tape_cap = kAdjTape;
     MX_TRY(dalloc(s, &s->a_xv3, (size_t)6 * N));
@@ -1740,7 +1740,6 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   a.g_off = s->a_goff;
   a.g_contrib = s->a_gcontrib;
   a.tape = s->a_tape;
-  a.tape_top = s->a_tape_top;
   a.tape_cap = s->a_tape_cap;
   a.bs_xsum = s->a_bsx;
   (void)N;

@@ -190,8 +190,7 @@ struct Adj {
   unsigned long long* g_off;     // tape offset of each group
   double* g_contrib;             // [g_cap][kMaxGroup][6] big members' cotangents
   double* tape;                  // accepted sub-steps: H, row, 6 x nb start state
-  unsigned long long* tape_top;
-  unsigned long long tape_cap;
+  unsigned long long tape_cap;   // doubles
   double* bs_xsum;               // 3 per system: sum of the big shares' position parts
 };
 
