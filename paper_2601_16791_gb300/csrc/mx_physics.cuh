@@ -147,7 +147,9 @@ __device__ __forceinline__ void pair_acc(double dx, double dy, double dz, double
   const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
   const double yy = rsqrt_d(s2);
   double f = yy * yy * yy;
-  if (s2 < rc2) {
+  // s2 < rc2 decided on the bit patterns: for non-negative doubles the integer
+  // order is the value order, and the compare leaves the FP64 pipe free
+  if (__double_as_longlong(s2) < __double_as_longlong(rc2)) {
     if (s2 <= rc2lo) {
       f = 0.0;
     } else {
