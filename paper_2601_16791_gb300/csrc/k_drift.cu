@@ -5,9 +5,10 @@
 // One thread per body.  The Kepler equation in the universal anomaly s,
 //   F(s) = r0 s + eta G2(s) + zeta G3(s) - h = 0,   G_k = s^k c_k(beta s^2),
 // with r0 = |x|, eta = x.v, beta = 2 mu/r0 - v^2, zeta = mu - beta r0, is
-// solved by Halley's method from a second-order starting guess.  Once a
-// Halley correction is below 1e-7 of s, the next error is below the FP64
-// resolution (cubic convergence), so the stepped s is final; the G functions
+// solved by Halley's method from a third-order starting guess.  Once a
+// Halley correction is small enough (1e-5 of s on short steps, 1e-7 on long
+// ones; mx_kepler.cuh), the next error is below the FP64 resolution (cubic
+// convergence), so the stepped s is final; the G functions
 // are carried to it by a second-order Taylor step (dG_k/ds = G_{k-1}) instead
 // of a fresh series evaluation.  The state then moves with the Gauss f and g
 // functions.

@@ -27,6 +27,24 @@ __device__ __forceinline__ void stumpff_series(double z, double& c2, double& c3)
   c3 = fma(-z, c3, 1.0 / 6.0);
 }
 
+// The same series with six terms, for |z| <= 0.03 (a step of up to about
+// 0.17 rad of mean motion): the first term left out, z^6/14!, is below 1e-20
+// of c2 there.
+__device__ __forceinline__ void stumpff_series6(double z, double& c2, double& c3) {
+  c2 = 1.0 / 479001600.0;           // 1/12!
+  c3 = 1.0 / 6227020800.0;          // 1/13!
+  c2 = fma(-z, c2, 1.0 / 3628800.0);
+  c3 = fma(-z, c3, 1.0 / 39916800.0);
+  c2 = fma(-z, c2, 1.0 / 40320.0);
+  c3 = fma(-z, c3, 1.0 / 362880.0);
+  c2 = fma(-z, c2, 1.0 / 720.0);
+  c3 = fma(-z, c3, 1.0 / 5040.0);
+  c2 = fma(-z, c2, 1.0 / 24.0);
+  c3 = fma(-z, c3, 1.0 / 120.0);
+  c2 = fma(-z, c2, 0.5);
+  c3 = fma(-z, c3, 1.0 / 6.0);
+}
+
 // c0..c3 for any z: quarter the argument into the series range, then apply
 // c0(4z) = 2c0^2 - 1, c1(4z) = c0 c1, c2(4z) = c1^2/2, c3(4z) = (c2 + c0 c3)/4.
 static __device__ __noinline__ void stumpff_reduced(double z, double& c0, double& c1, double& c2,
@@ -52,7 +70,9 @@ __device__ __forceinline__ void gfuns(double s, double beta, double* G) {
   const double s2 = s * s;
   const double z = beta * s2;
   double c2, c3;
-  if (fabs(z) <= 0.3) {
+  if (fabs(z) <= 0.03) {
+    stumpff_series6(z, c2, c3);
+  } else if (fabs(z) <= 0.3) {
     stumpff_series(z, c2, c3);
   } else {
     double c0, c1;
@@ -75,8 +95,19 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, int maxit, dou
   const double eta = fma(x, u, fma(y, v, z * w));
   const double beta = fma(2.0 * mu, ir0, -v2);
   const double zeta = fma(-beta, r0, mu);
-  // second-order guess s = (h/r0)(1 - eta h / (2 r0^2))
-  double s = h * ir0 * fma(-0.5 * eta * h, ir0 * ir0, 1.0);
+  // Short steps (|beta| (h/r0)^2 <= 0.1, n h below about 0.3): third-order
+  // guess from inverting h = r0 s + eta s^2/2 + zeta s^3/6, s = h/r0
+  // - eta h^2/(2 r0^3) + h^3 (eta^2/(2 r0^5) - zeta/(6 r0^4)), error O((n h)^4).
+  // Halley's error after a correction of relative size e is about
+  // (zeta/(6 r0) - eta^2/(4 r0^2)) s^2 e^3 ~ ((n h)^2/6) e^3 in relative terms,
+  // below 2e-17 for e <= 1e-5 on a short step, so a correction that small
+  // ends the solve there (1e-7 otherwise).  Longer steps, where the series
+  // says little, start from its second-order part.
+  const double hi = h * ir0;
+  const bool short_step = fabs(beta) * hi * hi <= 0.1;
+  const double t1 = short_step ? fma(0.5 * eta * eta, ir0, -zeta * (1.0 / 6.0)) : 0.0;
+  const double stop = short_step ? 1e-5 : 1e-7;
+  double s = hi * fma(h * ir0 * ir0, fma(hi, t1, -0.5 * eta), 1.0);
   double G[4];
   bool done = false;
   double ds = 0.0;
@@ -87,7 +118,7 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, int maxit, dou
     const double Fpp = fma(eta, G[0], zeta * G[1]);
     ds = -F * Fp * rcp_d(fma(Fp, Fp, -0.5 * F * Fpp));
     s += ds;
-    if (fabs(ds) <= 1e-7 * fabs(s)) {
+    if (fabs(ds) <= stop * fabs(s)) {
       done = true;
       break;
     }
