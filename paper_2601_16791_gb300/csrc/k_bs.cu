@@ -1348,11 +1348,12 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
     ax += gq.adg[0];
     ay += gq.adg[1];
   }
+  const DragConst dc = S.gas_on ? drag_const(S, gq, x, y, hp0, hp1, hp2, rp, kd) : DragConst{};
   for (int kk = 0; kk < nk; ++kk) {
     double a[3] = {0.0, 0.0, 0.0};
     if (S.gas_on) {
       int kout = 0;
-      gas_drag_at(S, gq, x, y, u + hp0, v + hp1, w + hp2, rp, kd, a, -1, &kout);
+      gas_drag_at(S, dc, u, v, w, a, -1, &kout);
     }
     u = fma(kick_h, ax + a[0], u);
     v = fma(kick_h, ay + a[1], v);

@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
     ax += gq.adg[0];
     ay += gq.adg[1];
   }
+  const DragConst dc = drag ? drag_const(S, gq, x, y, hp0, hp1, hp2, rp, kd) : DragConst{};
 #pragma unroll
   for (int kk = 0; kk < NKICK; ++kk) {
     double a[3] = {0.0, 0.0, 0.0};
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
       const size_t word = (size_t)kidx * d.kwords + (j >> 5);
       int kin = -1, kout = 0;
       if (kuse && d.kmode == 2) kin = (d.kbits[word] >> (j & 31)) & 1u;
-      gas_drag_at(S, gq, x, y, u + hp0, v + hp1, w + hp2, rp, kd, a, kin, &kout);
+      gas_drag_at(S, dc, u, v, w, a, kin, &kout);
       if (kuse && d.kmode == 1 && kout) atomicOr(&d.kbits[word], 1u << (j & 31));
     }
     u = fma(kick_h, ax + a[0], u);

@@ -60,27 +60,54 @@ __device__ __forceinline__ GasAt gas_at(const SysDev& S, double x, double y) {
   return q;
 }
 
-// Drag acceleration (Eq. 3) of one planetesimal at heliocentric position
-// (x, y, .) with the gas there (gas_at), moving with heliocentric velocity
-// (u, v, w).  C_D (Eq. 7) from Re and Ma.
-// kd = 3 / (8 r_p[AU] rho_p); rp_cm = r_p in cm.
-// kb_in: -1 takes the k of Eq. 7 from Re; 0 or 1 forces k = 0.4 or 0.2 (a
-// recorded branch being replayed).  *kb_out receives the branch used.
-__device__ __forceinline__ void gas_drag_at(const SysDev& S, const GasAt& q, double x, double y,
-                                            double u, double v, double w, double rp_cm, double kd,
-                                            double* a, int kb_in, int* kb_out) {
+// The drag's terms of one planetesimal that do not depend on its velocity,
+// for the half kicks of one launch (the position, the gas there and the
+// momentum P are fixed over them): the gas's velocity minus P/m0 along x and
+// y (so that dv = v_b + off), and the factors of Re and of the drag magnitude.
+struct DragConst {
+  bool in_gas;
+  double offu, offv, offw;   // dv = (u + offu, v + offv, w + offw), u barycentric
+  double inv_cs;
+  double re_k;               // Re = re_k |dv|
+  double coef_k;             // |a| = C_D coef_k |dv|^2
+};
+
+// kd = 3 / (8 r_p[AU] rho_p); rp_cm = r_p in cm; (hp0, hp1, hp2) = P/m0.
+__device__ __forceinline__ DragConst drag_const(const SysDev& S, const GasAt& q, double x,
+                                                double y, double hp0, double hp1, double hp2,
+                                                double rp_cm, double kd) {
+  DragConst c;
+  c.in_gas = q.in_gas;
+  c.offu = fma(q.g, y, hp0);
+  c.offv = fma(-q.g, x, hp1);
+  c.offw = hp2;
+  c.inv_cs = q.inv_cs;
+  c.re_k = (S.c_re * rp_cm) * (q.rho * q.inv_cs);
+  c.coef_k = (S.cd_scale * kd) * q.rho;
+  return c;
+}
+
+// Drag acceleration (Eq. 3) of one planetesimal with barycentric velocity
+// (u, v, w), from its velocity-free terms (drag_const).  C_D (Eq. 7) from Re
+// and Ma.  kb_in: -1 takes the k of Eq. 7 from Re; 0 or 1 forces k = 0.4 or
+// 0.2 (a recorded branch being replayed).  *kb_out receives the branch used.
+__device__ __forceinline__ void gas_drag_at(const SysDev& S, const DragConst& c, double u,
+                                            double v, double w, double* a, int kb_in,
+                                            int* kb_out) {
   a[0] = a[1] = a[2] = 0.0;
   *kb_out = 0;
-  if (!q.in_gas) return;
-  const double du = fma(q.g, y, u);
-  const double dv = fma(-q.g, x, v);
-  const double dw = w;
+  if (!c.in_gas) return;
+  const double du = u + c.offu;
+  const double dv = v + c.offv;
+  const double dw = w + c.offw;
   const double dv2 = fma(du, du, fma(dv, dv, dw * dw));
   if (dv2 == 0.0) return;
   const double dvm = dv2 * rsqrt_d(dv2);
-  const double Ma = dvm * q.inv_cs;
-  const double Re = S.c_re * rp_cm * Ma * q.rho;
-  const int kb = (kb_in >= 0) ? kb_in : (Re < 1e5 ? 0 : 1);
+  const double Ma = dvm * c.inv_cs;
+  const double Re = c.re_k * dvm;
+  // Re < 1e5 on the bit patterns (both positive): off the FP64 pipe
+  const int kb = (kb_in >= 0) ? kb_in
+                              : (__double_as_longlong(Re) < __double_as_longlong(1e5) ? 0 : 1);
   *kb_out = kb;
   const double k = kb ? 0.2 : 0.4;
   // Eq. 7 with one reciprocal: [(24/Re + 40/(10+Re))^-1 + 0.23 Ma]^-1 = D/den1
@@ -92,7 +119,7 @@ __device__ __forceinline__ void gas_drag_at(const SysDev& S, const GasAt& q, dou
   const double first = D * A * r;           // = D / den1
   const double second = fma(2.0, Ma, 1.6 * k) * den1 * r;
   const double cd = (S.cd_mode == 1) ? fma(first, first, second) : first + second;
-  const double coef = S.cd_scale * cd * kd * q.rho * dvm;
+  const double coef = cd * c.coef_k * dvm;
   a[0] = -coef * du;
   a[1] = -coef * dv;
   a[2] = -coef * dw;
@@ -128,13 +155,14 @@ __device__ __forceinline__ double gap_factor(const Dev& d, const SysDev& S, doub
 // then gas_drag_at) plus, when enabled, the disk's gravity.  Quantities follow
 // Sec. 3.1: Sigma (Eq. 1, normalised at 1 AU), rho_g (Eq. 4) at the midplane,
 // v_g (Eqs. 5, 6), C_D (Eq. 7).  dfac multiplies the gas density (a gap).
+// (u, v, w) is the heliocentric velocity here.
 __device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, double z, double u,
                                          double v, double w, double rp_cm, double kd, double* a,
                                          int kb_in, int* kb_out, double dfac = 1.0) {
   (void)z;
   GasAt q = gas_at(S, x, y);
   q.rho *= dfac;
-  gas_drag_at(S, q, x, y, u, v, w, rp_cm, kd, a, kb_in, kb_out);
+  gas_drag_at(S, drag_const(S, q, x, y, 0.0, 0.0, 0.0, rp_cm, kd), u, v, w, a, kb_in, kb_out);
   a[0] += q.adg[0];
   a[1] += q.adg[1];
 }
