@@ -77,3 +77,54 @@ def test_batch_member_vs_oracle():
         err = np.linalg.norm(got[:3] - ref[:3], axis=0) / np.linalg.norm(ref[:3], axis=0)
         assert err[keep].max() <= 1e-9, (k, err[keep].max())
     b.close()
+
+
+def test_batch_with_ejection_schedule():
+    """Two scattering swarms on the same ejection schedule: in a batch and
+    alone they take the same steps, so states and removals agree bit for bit,
+    and the per-system removal counts are each system's own."""
+    ws = [W.scatter_2giant(seed=s, nsmall=600, eject_every=5) for s in (5, 7)]
+    b = mx.Batch(ws)
+    b.step(23)
+    stat_b, cnt_b = mx.mx_body_status(b.h, b.n, len(ws))
+    for k, w in enumerate(ws):
+        alone = mx.System(w)
+        alone.step(23)
+        assert np.array_equal(b.system_state(k, mx.MX_COORD_DH), alone.state(mx.MX_COORD_DH))
+        stat, cnt = mx.mx_body_status(alone.h, w.n)
+        alone.close()
+        lo, hi = b.offsets[k], b.offsets[k + 1]
+        assert np.array_equal(stat_b[lo:hi], stat) and cnt_b[k] == cnt[0] > 100
+    b.close()
+
+
+def test_batch_with_one_growing_system():
+    """Growth tracks on system 0 only (mx_set_growth with its index): system 0
+    matches its run alone bit for bit (both end every step with their own half
+    kick), system 1 runs the same map with split kicks (positions of bodies
+    that met no planet within 1e-12), and the masses are the growing system's."""
+    g = W.growth_2giant(nsmall=500, tau_c_days=400.0, tau_g_days=200.0)
+    p = W.plain_2big_1k(nsmall=300)
+    p.params = dict(p.params, dt=10.0)
+    b = mx.Batch([g, p])
+    mx.mx_set_growth(b.h, 0, g.growth, g.nbig, g.gap_c)
+    b.step(60)
+    alone = mx.System(g)
+    alone.step(60)
+    assert np.array_equal(b.system_state(0, mx.MX_COORD_DH), alone.state(mx.MX_COORD_DH))
+    m_alone, _ = mx.mx_planets(alone.h, g.nbig)
+    alone.close()
+    m_b, _ = mx.mx_planets(b.h, g.nbig + p.nbig)
+    assert np.array_equal(m_b[:g.nbig], m_alone) and m_b[0] > 10 * g.m_big[0]
+    assert np.allclose(m_b[g.nbig:], p.m_big, rtol=1e-15, atol=0)
+    other = mx.System(p)
+    other.step(60)
+    ref = other.state(mx.MX_COORD_DH)
+    ever = torch.zeros(p.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(other.h, ever)
+    other.close()
+    got = b.system_state(1, mx.MX_COORD_DH)
+    err = np.linalg.norm(got[:3] - ref[:3], axis=0) / np.linalg.norm(ref[:3], axis=0)
+    quiet = ever.cpu().numpy() == 0
+    assert quiet.sum() > 200 and err[quiet].max() <= 1e-12
+    b.close()
