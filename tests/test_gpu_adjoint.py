@@ -132,3 +132,58 @@ def test_adjoint_is_deterministic():
     b = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every, mask=False)
     assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
     traj.close()
+
+
+def test_full_size_adjoint_workload():
+    """The adjoint workload at its full size: 4 cores + 50,000 planetesimals,
+    2,000 steps checkpointed every 50.
+      * The mean over every planetesimal that met no core: the gradient along
+        16 random directions against central differences of the GPU loss
+        (recorded C_D branches replayed), <= 1e-5.
+      * A loss on 200 sampled planetesimals (weight 1/N on them, 0 elsewhere;
+        the GPU still integrates all 50,000): against the oracle's JVP over
+        the cores and that sample, which, being massless, moves as inside the
+        full disk, <= 1e-8.  The other planetesimals get a zero gradient."""
+    w, traj, xv0, gas, wts = _setup(nsmall=50_000, nsteps=2000, every=50)
+    L, gx, gp = _grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every)
+    ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(traj.h, ever)
+    ev = ever.cpu().numpy()[w.nbig:].astype(bool)
+    assert 0 < ev.sum() < w.nsmall // 4
+    w_eff = wts * (1.0 - ever.to(torch.float64))
+    rng = np.random.default_rng(21)
+    for dxv, dpar in _directions(w, 16, rng):
+        ours = float((gx * dxv).sum() + (gp * dpar).sum())
+        dx_t = torch.tensor(dxv, dtype=torch.float64, device="cuda")
+        dp_t = torch.tensor(dpar, dtype=torch.float64, device="cuda")
+        best = np.inf
+        for t in (1e-2, 3e-2, 3e-3, 1e-1):
+            Lp = traj.loss_at(xv0 + t * dx_t, gas + t * dp_t, w_eff, w.nsteps, w.checkpoint_every)
+            Lm = traj.loss_at(xv0 - t * dx_t, gas - t * dp_t, w_eff, w.nsteps, w.checkpoint_every)
+            best = min(best, abs((Lp - Lm) / (2 * t) - ours) / abs(ours))
+            if best <= 1e-5:
+                break
+        assert best <= 1e-5, best
+    # the sampled loss against the oracle
+    quiet = np.flatnonzero(~ev)
+    sel = np.sort(rng.choice(quiet, 200, replace=False))
+    cols = np.concatenate([np.arange(w.nbig), w.nbig + sel])
+    p = orc.make_params(w.params)
+    xh = w.xv_helio[:, cols].copy()
+    xv, mu, rc = orc.init(p, w.nbig, len(sel), w.m_big, xh)
+    _, ever_o, _, _ = orc.step(p, w.nbig, xv, mu, rc, w.rp_km[sel], w.rhop[sel], w.nsteps)
+    w_o = np.where(ever_o[w.nbig:] == 0, 1.0 / w.nsmall, 0.0)
+    assert (w_o > 0).sum() >= 190
+    w_s = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    w_s[torch.as_tensor(w.nbig + sel, device="cuda")] = torch.as_tensor(w_o, device="cuda")
+    L2, gx2, gp2 = _grad(traj, xv0, gas, w_s, w.nsteps, w.checkpoint_every)
+    rest = np.ones(w.n, dtype=bool)
+    rest[cols] = False
+    assert not gx2[:, rest].any()
+    for dxv, dpar in _directions(w, 4, rng):
+        Lo, jvp = orc.jvp_loss(p, w.nbig, w.m_big, xh, w.rp_km[sel], w.rhop[sel], w_o, w.nsteps,
+                               dxv[:, cols], dpar)
+        ours = float((gx2[:, cols] * dxv[:, cols]).sum() + (gp2 * dpar).sum())
+        assert abs(Lo - L2) <= 1e-9 * abs(Lo)
+        assert abs(ours - jvp) <= 1e-8 * abs(jvp), (ours, jvp)
+    traj.close()

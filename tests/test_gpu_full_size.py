@@ -1,0 +1,103 @@
+"""The semi-active disk and the 256-system ensemble at their full sizes, in the
+launch configuration the benchmark times, against the oracle on sampled
+planetesimals.
+
+Planetesimals are massless, so a sample of them moves exactly as inside the
+full disk: the oracle integrates every big body with the sample, the GPU the
+whole system, and the sampled columns are compared.
+
+Tolerances: positions of bodies that neither side flagged for an encounter,
+relative <= 1e-9; big bodies that went through Bulirsch-Stoer groups, relative
+<= 1e-8 (each group step agrees to the Bulirsch-Stoer tolerance, 1e-12, and
+the differences pass to the other big bodies through their mutual gravity).
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2601_16791_gb300 import mx, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _sample(w, k, rng):
+    """Columns of all big bodies plus k sampled planetesimals (all if fewer)."""
+    k = min(k, w.nsmall)
+    sel = np.sort(rng.choice(w.nsmall, k, replace=False))
+    cols = np.concatenate([np.arange(w.nbig), w.nbig + sel])
+    return sel, cols
+
+
+def _oracle_on_sample(w, sel, cols, nsteps):
+    sub = W.Workload(f"{w.name} sample", w.params, w.nbig, len(sel), w.m_big,
+                     w.xv_helio[:, cols].copy(), w.rp_km[sel].copy(), w.rhop[sel].copy(), nsteps)
+    p = orc.make_params(sub.params)
+    xv, mu, rc = orc.init(p, sub.nbig, sub.nsmall, sub.m_big, sub.xv_helio)
+    ref, ever, _, st = orc.step(p, sub.nbig, xv, mu, rc, sub.rp_km, sub.rhop, nsteps)
+    return ref, ever, st
+
+
+def _rel(a, b):
+    return np.linalg.norm(a[:3] - b[:3], axis=0) / np.linalg.norm(b[:3], axis=0)
+
+
+def test_semiactive_full_size_sampled():
+    """2,000 embryos + 200,000 planetesimals, 20 steps: every embryo and 400
+    sampled planetesimals against the oracle."""
+    w = W.semiactive_2000big_200k()
+    nsteps = 20
+    g = mx.System(w)
+    g.step(nsteps)
+    out = g.state(mx.MX_COORD_DH)
+    ever_g = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(g.h, ever_g)
+    ever_g = ever_g.cpu().numpy().astype(bool)
+    g.close()
+    sel, cols = _sample(w, 400, np.random.default_rng(31))
+    ref, ever_o, st = _oracle_on_sample(w, sel, cols, nsteps)
+    got = out[:, cols]
+    err = _rel(got, ref)
+    quiet = (ever_o == 0) & ~ever_g[cols]
+    big = np.arange(len(cols)) < w.nbig
+    assert st[1] > 100 and (~quiet[big]).sum() > 50, "no big-body groups: the test is vacuous"
+    assert quiet[~big].sum() > 350
+    assert err[quiet].max() <= 1e-9, err[quiet].max()
+    assert err[big].max() <= 1e-8, err[big].max()
+
+
+def test_ensemble_full_size_sampled():
+    """The 256-system ensemble (8.47 million bodies) in one batch, 20 steps:
+    five members (the largest, the smallest, one with 50 embryos and two drawn
+    at random) against the oracle on their embryos and 200 sampled
+    planetesimals each."""
+    ws = W.ensemble_256()
+    nsteps = 20
+    b = mx.Batch(ws)
+    b.step(nsteps)
+    xv = b.state(mx.MX_COORD_DH)
+    ever_g = torch.zeros(b.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(b.h, ever_g)
+    ever_g = ever_g.cpu().numpy().astype(bool)
+    off = np.asarray(b.offsets)
+    b.close()
+    assert b.n > 8_000_000
+    rng = np.random.default_rng(41)
+    sizes = np.array([w.n for w in ws])
+    picks = [int(np.argmax(sizes)), int(np.argmin(sizes)),
+             int(np.argmax([w.nbig for w in ws]))]
+    picks += [int(k) for k in rng.choice(len(ws), 2, replace=False)]
+    checked = 0
+    for k in picks:
+        w = ws[k]
+        sel, cols = _sample(w, 200, rng)
+        ref, ever_o, _ = _oracle_on_sample(w, sel, cols, nsteps)
+        got = xv[:, off[k] + cols]
+        quiet = (ever_o == 0) & ~ever_g[off[k] + cols]
+        err = _rel(got, ref)
+        assert err[quiet].max() <= 1e-9, (k, err[quiet].max())
+        checked += int(quiet.sum())
+    assert checked > 800
