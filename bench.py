@@ -549,21 +549,21 @@ def run_mx(args):
 
     # end to end through the public API with host buffers: per step the state
     # goes host->device from pinned memory, one step runs, the state comes back
+    # into the other pinned buffer, which feeds the next step
     L = mx.load()
-    pin_in = torch.empty((6, w.n), dtype=torch.float64, pin_memory=True)
-    pin_out = torch.empty((6, w.n), dtype=torch.float64, pin_memory=True)
-    pin_in.copy_(torch.from_numpy(sysm.state(mx.MX_COORD_DH)))
+    pins = [torch.empty((6, w.n), dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    pins[0].copy_(torch.from_numpy(sysm.state(mx.MX_COORD_DH)))
     stepc = ctypes.c_longlong(0)
     ne = max(1, args.e2e_steps)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(ne):
-        mx._check(L.mx_set_state(sysm.h, ctypes.c_void_p(pin_in.data_ptr()), mx.MX_COORD_DH, 0),
+    for k in range(ne):
+        src, dst = pins[k & 1], pins[(k + 1) & 1]
+        mx._check(L.mx_set_state(sysm.h, ctypes.c_void_p(src.data_ptr()), mx.MX_COORD_DH, k),
                   "mx_set_state")
         mx._check(L.mx_step(sysm.h, 1), "mx_step")
-        mx._check(L.mx_get_state(sysm.h, ctypes.c_void_p(pin_out.data_ptr()), mx.MX_COORD_DH,
+        mx._check(L.mx_get_state(sysm.h, ctypes.c_void_p(dst.data_ptr()), mx.MX_COORD_DH,
                                  ctypes.byref(stepc)), "mx_get_state")
-        pin_in.copy_(pin_out)
     e2e_s = reduce_max(time.perf_counter() - t0, "cuda")
     e2e_value = whole_job_rate(w.n, ne, world, e2e_s)
 

@@ -17,12 +17,33 @@
 
 namespace mx {
 
+// Big bodies staged per pass, in the block's dynamic shared memory: `chunk`
+// = min(threads per block, most big bodies of a system) entries of each
+// array (a disk with a few big bodies leaves the SM its shared memory).
+__host__ __device__ __forceinline__ int det_chunk(int tile, int big_max) {
+  const int c = big_max < tile ? big_max : tile;
+  return c < 1 ? 1 : c;
+}
+
+__host__ __device__ __forceinline__ size_t det_smem_bytes(int chunk) {
+  return (size_t)chunk * (13 * sizeof(double) + 13 * sizeof(float) + 1);
+}
+
 struct DetSmem {
-  double s[12][kThreads];   // x0 y0 z0 u0 v0 w0 x1 y1 z1 u1 v1 w1
-  float f[12][kThreads];
-  double rc[kThreads];
-  float rcf[kThreads];
-  unsigned char out[kThreads];   // big body removed from the integration (Sec. 3.5)
+  double* s[12];   // x0 y0 z0 u0 v0 w0 x1 y1 z1 u1 v1 w1
+  float* f[12];
+  double* rc;
+  float* rcf;
+  unsigned char* out;   // big body removed from the integration (Sec. 3.5)
+  __device__ DetSmem(unsigned char* base, int n) {
+    double* db = reinterpret_cast<double*>(base);
+    for (int q = 0; q < 12; ++q) s[q] = db + q * n;
+    rc = db + 12 * n;
+    float* fb = reinterpret_cast<float*>(db + 13 * n);
+    for (int q = 0; q < 12; ++q) f[q] = fb + q * n;
+    rcf = fb + 12 * n;
+    out = reinterpret_cast<unsigned char*>(fb + 13 * n);
+  }
 };
 
 // xv0, xv1: 6 x N endpoint states; keys/count/cap: pair output.
@@ -32,7 +53,9 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
                                                      unsigned char* flags,
                                                      unsigned long long* keys, int* count,
                                                      int cap, int runs) {
-  __shared__ DetSmem sm;
+  extern __shared__ __align__(16) unsigned char dsm_det[];
+  const int chunk = det_chunk(blockDim.x, d.big_max);
+  DetSmem sm(dsm_det, chunk);
   const Tile t = d.tiles[blockIdx.x];
   const SysDev& S = d.sys[t.sys];
   const int N = d.N;
@@ -80,8 +103,8 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
       if (start + e < cap) keys[start + e] = tag | (unsigned)(S.off + hits[e]);
     if (mine) nh = 0;
   };
-  for (int c0 = 0; c0 < S.nbig; c0 += blockDim.x) {
-    const int cn = min((int)blockDim.x, S.nbig - c0);
+  for (int c0 = 0; c0 < S.nbig; c0 += chunk) {
+    const int cn = min(chunk, S.nbig - c0);
     __syncthreads();
     if (threadIdx.x < cn) {
       const int g = S.off + c0 + threadIdx.x;
@@ -211,7 +234,8 @@ void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int 
 
 void launch_detect(const Dev& d, const double* xv0, const double* xv1, unsigned char* flags,
                    unsigned long long* keys, int* count, int cap, int runs, cudaStream_t st) {
-  k_detect<<<d.ntiles, d.tile, 0, st>>>(d, xv0, xv1, flags, keys, count, cap, runs);
+  const size_t sm = det_smem_bytes(det_chunk(d.tile, d.big_max));
+  k_detect<<<d.ntiles, d.tile, sm, st>>>(d, xv0, xv1, flags, keys, count, cap, runs);
 }
 
 void launch_sort_keys(unsigned long long* keys, const int* count, int cap, int swap_ij,

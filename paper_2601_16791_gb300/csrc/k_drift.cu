@@ -50,12 +50,16 @@ __global__ void __launch_bounds__(kThreads) k_jump_drift(Dev d, double jump_frac
   }
   double dj[3];
   jump_vec(d.P + 3 * t.sys, S, jump_frac, dj);
-  double x = d.xv[j] + dj[0];
-  double y = d.xv[(size_t)N + j] + dj[1];
-  double z = d.xv[2 * (size_t)N + j] + dj[2];
-  double u = d.xv[3 * (size_t)N + j];
-  double v = d.xv[4 * (size_t)N + j];
-  double w = d.xv[5 * (size_t)N + j];
+  // a big body comes from the kick's output (d.bk): the kick of an interior
+  // step leaves it there only
+  const double* src = (jl < S.nbig) ? d.bk + S.boff + jl : d.xv + j;
+  const size_t ld = (jl < S.nbig) ? (size_t)d.NB : (size_t)N;
+  double x = src[0] + dj[0];
+  double y = src[ld] + dj[1];
+  double z = src[2 * ld] + dj[2];
+  double u = src[3 * ld];
+  double v = src[4 * ld];
+  double w = src[5 * ld];
   d.xv0[j] = x;
   d.xv0[(size_t)N + j] = y;
   d.xv0[2 * (size_t)N + j] = z;

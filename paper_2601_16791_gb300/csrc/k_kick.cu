@@ -14,14 +14,23 @@
 
 namespace mx {
 
+// Big positions come from k_prep's copy (d.bx), or, with `dj` (a kick that
+// makes its own prep), from the state plus the jump.
 __device__ __forceinline__ void stage_bigs(const Dev& d, const SysDev& S, int c0, int cn,
-                                           BigSmem& sb) {
+                                           BigSmem& sb, const double* dj) {
   for (int k = threadIdx.x; k < cn; k += blockDim.x) {
     const int b = S.boff + c0 + k;
     const double rc = d.brc[b];
-    sb.x[k] = d.bx[b];
-    sb.y[k] = d.by[b];
-    sb.z[k] = d.bz[b];
+    if (dj) {
+      const size_t g = (size_t)S.off + c0 + k;
+      sb.x[k] = d.xv[g] + dj[0];
+      sb.y[k] = d.xv[(size_t)d.N + g] + dj[1];
+      sb.z[k] = d.xv[2 * (size_t)d.N + g] + dj[2];
+    } else {
+      sb.x[k] = d.bx[b];
+      sb.y[k] = d.by[b];
+      sb.z[k] = d.bz[b];
+    }
     sb.mu[k] = d.bmu[b];
     sb.rc[k] = rc;
     sb.rc2[k] = rc * rc;
@@ -35,12 +44,13 @@ __device__ __forceinline__ void stage_bigs(const Dev& d, const SysDev& S, int c0
 // bodies of its system; every thread of the block must call it.
 __device__ __forceinline__ void gravity_all(const Dev& d, const SysDev& S, BigSmem& sb, bool act,
                                             int jl, double rcj, double x, double y, double z,
-                                            double& ax, double& ay, double& az) {
+                                            double& ax, double& ay, double& az,
+                                            const double* dj = nullptr) {
   const bool jbig = jl < S.nbig;
-  for (int c0 = 0; c0 < S.nbig; c0 += kBigChunk) {
-    const int cn = min(kBigChunk, S.nbig - c0);
+  for (int c0 = 0; c0 < S.nbig; c0 += sb.chunk) {
+    const int cn = min(sb.chunk, S.nbig - c0);
     __syncthreads();
-    stage_bigs(d, S, c0, cn, sb);
+    stage_bigs(d, S, c0, cn, sb, dj);
     __syncthreads();
     if (!act) continue;
     if (!jbig) {
@@ -58,8 +68,56 @@ __device__ __forceinline__ void gravity_all(const Dev& d, const SysDev& S, BigSm
   }
 }
 
+// P = sum of mu_i v_i over the big bodies of system S, in out[0..2] (shared)
+// for every thread of the block.  The sum has one fixed partition and tree,
+// whatever the block size: kThreads partial sums, partial t over the bodies
+// i = t (mod kThreads) in ascending order, then a pairwise tree over the
+// partials.  With at most 32 big bodies every partial past the first 32 is
+// zero, so the tree adds only zeros above its last five levels, and warp 0
+// takes those five levels with shuffles (the same sum, bit for bit).
+// red: kThreads x 3 shared scratch.  Every thread of the block must call it.
+__device__ __forceinline__ void system_momentum(const Dev& d, const SysDev& S,
+                                                double (*red)[kThreads], double* out) {
+  const int N = d.N;
+  auto partial = [&](int t, double* p) {
+    p[0] = p[1] = p[2] = 0.0;
+    for (int i = t; i < S.nbig; i += kThreads) {
+      const int g = S.off + i;
+      const double m = d.bmu[S.boff + i];
+      p[0] = fma(m, d.xv[3 * (size_t)N + g], p[0]);
+      p[1] = fma(m, d.xv[4 * (size_t)N + g], p[1]);
+      p[2] = fma(m, d.xv[5 * (size_t)N + g], p[2]);
+    }
+  };
+  if (S.nbig <= 32) {
+    if (threadIdx.x < 32) {
+      double p[3];
+      partial(threadIdx.x, p);
+      for (int s = 16; s > 0; s >>= 1)
+        for (int c = 0; c < 3; ++c) p[c] += __shfl_down_sync(0xffffffffu, p[c], s);
+      if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) out[c] = p[c];
+    }
+  } else {
+    for (int t = threadIdx.x; t < kThreads; t += blockDim.x) {
+      double p[3];
+      partial(t, p);
+      for (int c = 0; c < 3; ++c) red[c][t] = p[c];
+    }
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+      for (int t = threadIdx.x; t < s; t += blockDim.x)
+        for (int c = 0; c < 3; ++c) red[c][t] += red[c][t + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 3; ++c) out[c] = red[c][0];
+  }
+  __syncthreads();
+}
+
 // Momentum of each system's massive bodies and the staged big positions.
-// One block per system; a fixed partition and tree keep the sum deterministic.
+// One block per system (system_momentum fixes the sum's order).
 // nkick > 0: the kernel that follows makes nkick half kicks; the kick counter
 // (for recording or replaying the k branch of Eq. 7) advances here.
 // The first launch of a step (jump_frac = 0, nkick > 0) first applies the
@@ -68,6 +126,7 @@ __device__ __forceinline__ void gravity_all(const Dev& d, const SysDev& S, BigSm
 __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int nkick) {
   const SysDev& S = d.sys[blockIdx.x];
   __shared__ double red[3][kThreads];
+  __shared__ double s_P[3];
   if (S.grow_on && nkick > 0 && jump_frac == 0.0)
     grow_update(d, S, (double)d.gstep[0] * S.h, red);
   if (nkick > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -76,35 +135,8 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int 
     if (jump_frac != 0.0) d.gstep[0] += 1;   // no block reads it in this launch
   }
   const int N = d.N;
-  // With at most 32 big bodies (one per lane of warp 0) the tree below adds
-  // only zeros above its last five levels, so warp 0 alone takes those five
-  // levels with shuffles, in the same order (the same sum, bit for bit),
-  // without block barriers; the other warps have nothing to stage.
-  const bool one_warp = S.nbig <= 32;
-  if (one_warp && threadIdx.x >= 32) return;
-  double p[3] = {0.0, 0.0, 0.0};
-  for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
-    const int g = S.off + i;
-    const double m = d.bmu[S.boff + i];
-    p[0] = fma(m, d.xv[3 * (size_t)N + g], p[0]);
-    p[1] = fma(m, d.xv[4 * (size_t)N + g], p[1]);
-    p[2] = fma(m, d.xv[5 * (size_t)N + g], p[2]);
-  }
-  double Ps[3];
-  if (one_warp) {
-    for (int s = 16; s > 0; s >>= 1)
-      for (int c = 0; c < 3; ++c) p[c] += __shfl_down_sync(0xffffffffu, p[c], s);
-    for (int c = 0; c < 3; ++c) Ps[c] = __shfl_sync(0xffffffffu, p[c], 0);
-  } else {
-    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = p[c];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s)
-        for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
-      __syncthreads();
-    }
-    for (int c = 0; c < 3; ++c) Ps[c] = red[c][0];
-  }
+  system_momentum(d, S, red, s_P);
+  const double Ps[3] = {s_P[0], s_P[1], s_P[2]};
   double* P = d.P + 3 * blockIdx.x;
   if (threadIdx.x == 0)
     for (int c = 0; c < 3; ++c) P[c] = Ps[c];
@@ -147,27 +179,107 @@ __global__ void __launch_bounds__(kThreads) k_prep(Dev d, double jump_frac, int 
   }
 }
 
+// The prep of a kick made inside it (the FUSED kick of an interior step):
+// each block computes its system's P (system_momentum: the sum k_prep makes,
+// bit for bit) and stages the big bodies from the state plus the jump.  The
+// big bodies' own results go to d.bk only, so that no block of the launch
+// overwrites a big body's state that another block still reads; the drift
+// that follows reads them there.  The block of each system's first tile
+// stores P and the history record k_prep would, and system 0's advances the
+// counters.  Those blocks read the history slot before they arrive, and the
+// last of them to arrive moves the slot on (no block waits for another).
+struct FusedPrep {
+  double P[3];
+};
+
+__device__ __forceinline__ FusedPrep fused_prep(const Dev& d, const SysDev& S, const Tile& t,
+                                                int nkick, double (*red)[kThreads]) {
+  __shared__ double s_P[3];
+  __shared__ int s_slot;
+  const bool head = t.start == S.off;
+  if (head && threadIdx.x == 0) s_slot = d.defer ? *(volatile int*)d.hstep : 0;
+  system_momentum(d, S, red, s_P);   // ends with a block barrier
+  FusedPrep f;
+  for (int c = 0; c < 3; ++c) f.P[c] = s_P[c];
+  if (!head) return f;
+  const int slot = s_slot;
+  const int sysi = t.sys;
+  if (threadIdx.x == 0) {
+    if (sysi == 0) {
+      d.kick_ctr[1] = d.kick_ctr[0];
+      d.kick_ctr[0] += nkick;
+      d.gstep[0] += 1;
+    }
+    if (d.defer) {
+      __threadfence();
+      if (atomicAdd(d.arrive, 1) == d.nsys - 1) {
+        *d.arrive = 0;
+        *d.hstep = slot + 1;
+      }
+    }
+  }
+  const bool rec = d.defer && slot < d.hist_cap;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 3; ++c) d.P[3 * sysi + c] = f.P[c];
+    if (rec) {
+      for (int c = 0; c < 3; ++c)
+        d.h_P[(size_t)slot * 6 * d.nsys + 3 * d.nsys + 3 * sysi + c] = f.P[c];
+      if (sysi == 0) {
+        d.h_nkick[slot] = nkick;
+        d.h_ej[slot] = 0;
+      }
+    }
+  }
+  if (rec) {
+    double dj[3];
+    jump_vec(f.P, S, 0.5, dj);
+    const int N = d.N;
+    for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
+      const int g = S.off + i;
+      const size_t o = (size_t)slot * 3 * d.NB + S.boff + i;
+      d.h_bx[o] = d.xv[g] + dj[0];
+      d.h_bx[o + d.NB] = d.xv[(size_t)N + g] + dj[1];
+      d.h_bx[o + 2 * (size_t)d.NB] = d.xv[2 * (size_t)N + g] + dj[2];
+      d.h_mu[(size_t)slot * d.NB + S.boff + i] = removed(d, g) ? -1.0 : d.bmu[S.boff + i];
+      d.h_rc[(size_t)slot * d.NB + S.boff + i] = d.brc[S.boff + i];
+    }
+  }
+  return f;
+}
+
 // Jump then kick (nkick half kicks of kick_frac * h each, gravity evaluated once; the
 // drag is re-evaluated before each with the updated velocity).  The momentum
-// P read here is the one k_prep just computed; it stays valid across the
-// kicks because the K-weighted pair forces are antisymmetric and the drag acts
-// on massless bodies only.
-template <int NKICK>
-__global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac, double kick_frac) {
-  __shared__ BigSmem sb;
+// P read here is the one k_prep just computed (FUSED: the one the kernel
+// computes itself, for a step's end, jump_frac = 1/2, with nkick = 2); it
+// stays valid across the kicks because the K-weighted pair forces are
+// antisymmetric and the drag acts on massless bodies only.  Every kick also
+// leaves the big bodies' results in d.bk, where the drift reads them.
+// Dynamic shared memory: kick_smem_bytes(d, FUSED) (the staging; FUSED with
+// more than 32 big bodies also the momentum tree, in the same space, before
+// the staging).
+template <int NKICK, bool FUSED>
+__global__ void __launch_bounds__(kThreads, FUSED ? 3 : 1) k_jump_kick(Dev d, double jump_frac,
+                                                                      double kick_frac) {
+  extern __shared__ double dsm[];
+  BigSmem sb(dsm, big_chunk(d.big_max));
   const Tile t = d.tiles[blockIdx.x];
   const SysDev& S = d.sys[t.sys];
-  const double* P = d.P + 3 * t.sys;
   const int N = d.N;
-  double dj[3];
-  jump_vec(P, S, jump_frac, dj);
+  double Pv[3], dj[3];
+  if constexpr (FUSED) {
+    const FusedPrep f = fused_prep(d, S, t, NKICK, reinterpret_cast<double(*)[kThreads]>(dsm));
+    for (int c = 0; c < 3; ++c) Pv[c] = f.P[c];
+  } else {
+    for (int c = 0; c < 3; ++c) Pv[c] = d.P[3 * t.sys + c];
+    // the last kernel of a history slot moves on to the next one
+    if (d.defer && blockIdx.x == 0 && threadIdx.x == 0) *d.hstep += 1;
+  }
+  jump_vec(Pv, S, jump_frac, dj);
   const double kick_h = kick_frac * S.h;
   const int j = t.start + threadIdx.x;
   // a deferred planetesimal is kicked by the window's catch-up instead; a
   // removed body is not kicked
   const bool act = threadIdx.x < t.count && !(d.defer && d.lag[j]) && !removed(d, j);
-  // the last kernel of a history slot moves on to the next one
-  if (d.defer && blockIdx.x == 0 && threadIdx.x == 0) *d.hstep += 1;
   const int jl = j - S.off;
   double x = 0, y = 0, z = 0, u = 0, v = 0, w = 0, rcj = 0.0;
   if (act) {
@@ -180,15 +292,16 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
     if (jl < S.nbig) rcj = d.brc[S.boff + jl];
   }
   double ax = 0, ay = 0, az = 0;
-  gravity_all(d, S, sb, act, jl, rcj, x, y, z, ax, ay, az);
+  gravity_all(d, S, sb, act, jl, rcj, x, y, z, ax, ay, az, FUSED ? dj : nullptr);
   if (!act) return;
-  if (jump_frac != 0.0) {
+  const bool big = jl < S.nbig;
+  if (jump_frac != 0.0 && !(FUSED && big)) {
     d.xv[j] = x;
     d.xv[(size_t)N + j] = y;
     d.xv[2 * (size_t)N + j] = z;
   }
-  const bool drag = S.gas_on && jl >= S.nbig;
-  const double hp0 = P[0] * S.inv_mu0, hp1 = P[1] * S.inv_mu0, hp2 = P[2] * S.inv_mu0;
+  const bool drag = S.gas_on && !big;
+  const double hp0 = Pv[0] * S.inv_mu0, hp1 = Pv[1] * S.inv_mu0, hp2 = Pv[2] * S.inv_mu0;
   const double rp = drag ? d.rp_cm[j] : 0.0, kd = drag ? d.kdrag[j] : 0.0;
   const int kbase = d.kmode ? d.kick_ctr[1] : 0;
   // the gas at the (fixed) position, shared by the launch's half kicks
@@ -215,9 +328,21 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
     v = fma(kick_h, ay + a[1], v);
     w = fma(kick_h, az + a[2], w);
   }
-  d.xv[3 * (size_t)N + j] = u;
-  d.xv[4 * (size_t)N + j] = v;
-  d.xv[5 * (size_t)N + j] = w;
+  if (big) {
+    double* q = d.bk + S.boff + jl;
+    const size_t NB = d.NB;
+    q[0] = x;
+    q[NB] = y;
+    q[2 * NB] = z;
+    q[3 * NB] = u;
+    q[4 * NB] = v;
+    q[5 * NB] = w;
+  }
+  if (!(FUSED && big)) {
+    d.xv[3 * (size_t)N + j] = u;
+    d.xv[4 * (size_t)N + j] = v;
+    d.xv[5 * (size_t)N + j] = w;
+  }
   if (!(finite_d(x) && finite_d(y) && finite_d(z) && finite_d(u) && finite_d(v) && finite_d(w)))
     atomicOr(d.status, ST_NONFINITE);
 }
@@ -225,7 +350,8 @@ __global__ void __launch_bounds__(kThreads) k_jump_kick(Dev d, double jump_frac,
 // Kick acceleration (gravity + drag) without changing the state: 3 x N.
 __global__ void __launch_bounds__(kThreads) k_accel(Dev d, double* acc, int drag_only,
                                                     int acc_stride, int acc_base) {
-  __shared__ BigSmem sb;
+  extern __shared__ double dsm[];
+  BigSmem sb(dsm, big_chunk(d.big_max));
   const Tile t = d.tiles[blockIdx.x];
   const SysDev& S = d.sys[t.sys];
   const double* P = d.P + 3 * t.sys;
@@ -271,15 +397,30 @@ void launch_prep(const Dev& d, double jump_frac, int nkick, cudaStream_t st) {
   k_prep<<<d.nsys, kThreads, 0, st>>>(d, jump_frac, nkick);
 }
 
+static size_t kick_smem_bytes(const Dev& d, bool fused) {
+  size_t n = 9 * (size_t)big_chunk(d.big_max);
+  if (fused && d.big_max > 32 && n < 3 * (size_t)kThreads) n = 3 * (size_t)kThreads;
+  return n * sizeof(double);
+}
+
 void launch_jump_kick(const Dev& d, double jump_frac, double kick_frac, int nkick,
                       cudaStream_t st) {
-  if (nkick == 2) k_jump_kick<2><<<d.ntiles, d.tile, 0, st>>>(d, jump_frac, kick_frac);
-  else k_jump_kick<1><<<d.ntiles, d.tile, 0, st>>>(d, jump_frac, kick_frac);
+  const size_t sm = kick_smem_bytes(d, false);
+  if (nkick == 2) k_jump_kick<2, false><<<d.ntiles, d.tile, sm, st>>>(d, jump_frac, kick_frac);
+  else k_jump_kick<1, false><<<d.ntiles, d.tile, sm, st>>>(d, jump_frac, kick_frac);
+}
+
+// The interior steps' kick with its own prep (no k_prep launch before it):
+// jump 1/2, two half kicks; for forward runs without growth tracks or k
+// branches recorded or replayed.
+void launch_jump_kick_fused(const Dev& d, cudaStream_t st) {
+  k_jump_kick<2, true><<<d.ntiles, d.tile, kick_smem_bytes(d, true), st>>>(d, 0.5, 0.5);
 }
 
 void launch_accel(const Dev& d, double* acc, int drag_only, int acc_stride, int acc_base,
                   cudaStream_t st) {
-  k_accel<<<d.ntiles, d.tile, 0, st>>>(d, acc, drag_only, acc_stride, acc_base);
+  k_accel<<<d.ntiles, d.tile, kick_smem_bytes(d, false), st>>>(d, acc, drag_only, acc_stride,
+                                                              acc_base);
 }
 
 // The kernels of a step share one shared-memory carveout (the largest), so
@@ -288,8 +429,9 @@ void launch_accel(const Dev& d, double* acc, int drag_only, int acc_stride, int 
 void configure_kick() {
   const int c = cudaSharedmemCarveoutMaxShared;
   cudaFuncSetAttribute(k_prep, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_jump_kick<1>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_jump_kick<2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_jump_kick<1, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_jump_kick<2, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_jump_kick<2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
 }
 
 }  // namespace mx

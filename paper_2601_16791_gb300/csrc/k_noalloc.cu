@@ -101,6 +101,7 @@ extern "C" mx_status mx_detect_encounters_noalloc(const mx_params* p, int n_big,
   d.nsys = 1;
   d.ntiles = (n + mx::kThreads - 1) / mx::kThreads;
   d.tile = mx::kThreads;
+  d.big_max = n_big;
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(scratch + kOffKeys);
   int* count = reinterpret_cast<int*>(scratch + kOffCount);
   if (cudaMemsetAsync(dev_flags, 0, (size_t)n, st) != cudaSuccess) return MX_ERR_CUDA;

@@ -256,6 +256,11 @@ void enqueue_head(mx_system* s, cudaStream_t st, cudaEvent_t* marks) {
   if (marks) mark_event(marks[2], st);
 }
 
+// An interior step's kick makes its own prep (k_jump_kick<2, true>) in forward
+// runs without growth tracks (their update sits in k_prep) and without k
+// branches recorded or replayed (the kick counter k_prep advances).
+bool fuse_prep(const mx_system* s) { return s->d.kmode == 0 && !s->grow_any; }
+
 void enqueue_step(mx_system* s, int last, cudaStream_t st, cudaEvent_t* marks) {
   int m = 0;
   auto mark = [&] {
@@ -271,9 +276,14 @@ void enqueue_step(mx_system* s, int last, cudaStream_t st, cudaEvent_t* marks) {
   mark();
   mx::launch_bs(s->d, s->bs_blocks, st);
   mark();
-  mx::launch_prep(s->d, 0.5, last ? 1 : 2, st);
-  mark();
-  mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st);
+  if (!last && fuse_prep(s)) {
+    mark();   // no k_prep: an empty span keeps the timed graphs' layout
+    mx::launch_jump_kick_fused(s->d, st);
+  } else {
+    mx::launch_prep(s->d, 0.5, last ? 1 : 2, st);
+    mark();
+    mx::launch_jump_kick(s->d, 0.5, 0.5, last ? 1 : 2, st);
+  }
   mark();
 }
 
@@ -643,6 +653,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_TRY(dalloc(s, &d.bmu, NB));
   MX_TRY(dalloc(s, &d.brc, NB));
   MX_TRY(dalloc(s, &d.P, 3 * (size_t)nsys));
+  MX_TRY(dalloc(s, &d.bk, 6 * (size_t)NB));
+  MX_TRY(dalloc(s, &d.arrive, 1));
   MX_TRY(dalloc(s, &d.flags, N));
   MX_TRY(dalloc(s, &d.keys, cap2));
   MX_TRY(dalloc(s, &d.pair_count, 2));
@@ -713,6 +725,8 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   d.nsys = nsys;
   d.ntiles = (int)tiles.size();
   d.tile = s->tile;
+  d.big_max = 0;
+  for (auto& q : sys) d.big_max = std::max(d.big_max, q.nbig);
   d.pair_cap = cap;
   d.work_cap = work_cap;
   d.mem_cap = mem_cap;
@@ -737,6 +751,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemsetAsync(d.ever, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.bb_count, 0, sizeof(unsigned long long), st));
   MX_CUDA(cudaMemsetAsync(d.kick_ctr, 0, 2 * sizeof(int), st));
+  MX_CUDA(cudaMemsetAsync(d.arrive, 0, sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.lag, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.hstep, 0, sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.rcount, 0, 3 * sizeof(int), st));
@@ -1088,9 +1103,13 @@ mx_status profiled_run(mx_system* s, int n_steps, void* flush, size_t flush_byte
       });
     if (e == cudaSuccess) e = timed(MX_K_GROUPS, [&] { mx::launch_groups(s->d, st); });
     if (e == cudaSuccess) e = timed(MX_K_BS, [&] { mx::launch_bs(s->d, s->bs_blocks, st); });
-    if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, last_step ? 1 : 2, st); });
-    if (e == cudaSuccess)
-      e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last_step ? 1 : 2, st); });
+    if (!last_step && fuse_prep(s)) {
+      if (e == cudaSuccess) e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick_fused(s->d, st); });
+    } else {
+      if (e == cudaSuccess) e = timed(MX_K_PREP, [&] { mx::launch_prep(s->d, 0.5, last_step ? 1 : 2, st); });
+      if (e == cudaSuccess)
+        e = timed(MX_K_JUMP_KICK, [&] { mx::launch_jump_kick(s->d, 0.5, 0.5, last_step ? 1 : 2, st); });
+    }
     if (e == cudaSuccess && test) e = timed(MX_K_EJECT, [&] { mx::launch_eject(s->d, 1, st); });
     if (e == cudaSuccess) e = slot_done(s, true, timed3);
     if (e == cudaSuccess) e = step_close();
@@ -1203,8 +1222,11 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
         sum[kHeadKind[q]] += ms;
         cnt[kHeadKind[q]]++;
       }
+    // a fused interior kick has no k_prep: its span (empty) is not counted
+    const bool fused = !(k + 1 == n_steps || split) && fuse_prep(s);
     for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
       e = cudaEventElapsedTime(&ms, s->mk_step[q], s->mk_step[q + 1]);
+      if (fused && kStepKind[q] == MX_K_PREP) continue;
       sum[kStepKind[q]] += ms;
       cnt[kStepKind[q]]++;
     }

@@ -94,6 +94,8 @@ struct Dev {
   double* kdrag;   // N
   double *bx, *by, *bz, *bmu, *brc;   // NB
   double* P;       // 3 x nsys
+  double* bk;      // 6 x NB: big bodies after the latest kick, the drift's source for them
+  int* arrive;     // [1] blocks of a kick with its own prep that have read the history slot
   unsigned char* flags;               // N
   unsigned long long* keys;           // pair keys [pair_cap]
   int* pair_count;
@@ -130,6 +132,7 @@ struct Dev {
   const Tile* tiles;
   int N, NB, nsys, ntiles;
   int tile;        // targets per tile = threads per block of the per-body kernels
+  int big_max;     // most big bodies of any system (sizes the kernels' shared staging)
   int pair_cap, work_cap, mem_cap;
   int kepler_max_iter, bs_max_sub;
   double bs_tol;

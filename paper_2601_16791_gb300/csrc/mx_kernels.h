@@ -25,6 +25,7 @@ void launch_dfma(double* sink, int blocks, int iters, cudaStream_t st);
 // k_kick.cu
 void launch_prep(const Dev& d, double jump_frac, int nkick, cudaStream_t st);
 void launch_jump_kick(const Dev& d, double jump_frac, double kick_frac, int nkick, cudaStream_t st);
+void launch_jump_kick_fused(const Dev& d, cudaStream_t st);
 void launch_accel(const Dev& d, double* acc, int drag_only, int acc_stride, int acc_base,
                   cudaStream_t st);
 

@@ -191,10 +191,21 @@ __device__ __forceinline__ void pair_acc(double dx, double dy, double dz, double
   az = fma(-f, dz, az);
 }
 
-// Shared-memory staging of one chunk of big bodies.
+// Shared-memory staging of one chunk of big bodies: nine arrays of `chunk`
+// doubles in the block's dynamic shared memory, chunk = min(most big bodies
+// of a system, kBigChunk), so that a disk with a few big bodies leaves the SM
+// its shared memory (the number of resident blocks is then set by registers).
+__host__ __device__ __forceinline__ int big_chunk(int big_max) {
+  return big_max < 1 ? 1 : (big_max < kBigChunk ? big_max : kBigChunk);
+}
+
 struct BigSmem {
-  double x[kBigChunk], y[kBigChunk], z[kBigChunk], mu[kBigChunk];
-  double rc[kBigChunk], rc2[kBigChunk], rc2lo[kBigChunk], rc01[kBigChunk], i09rc[kBigChunk];
+  double *x, *y, *z, *mu, *rc, *rc2, *rc2lo, *rc01, *i09rc;
+  int chunk;
+  __device__ BigSmem(double* base, int n)
+      : x(base), y(base + n), z(base + 2 * n), mu(base + 3 * n), rc(base + 4 * n),
+        rc2(base + 5 * n), rc2lo(base + 6 * n), rc01(base + 7 * n), i09rc(base + 8 * n),
+        chunk(n) {}
 };
 
 }  // namespace mx
