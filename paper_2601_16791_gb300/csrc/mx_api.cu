@@ -198,8 +198,11 @@ struct mx_system {
   int a_groups = 1;               // mx_adjoint_encounters
   int* a_poff = nullptr;
   size_t a_part_cap = 0;
-  int a_poff_tiles = -1;          // tile count a_poff was built for
-  int a_poff_tile = -1, a_poff_order = -1;
+  // the adjoint's own tiling (kThreads targets, system order), whatever the
+  // forward step's autotuner picked: its kernels are faster on full blocks,
+  // and its per-tile partial sums then do not depend on the forward tiling
+  mx::Tile* a_tiles = nullptr;
+  int a_ntiles = 0;
   long long kbits_cap = 0;
 };
 
@@ -1572,9 +1575,18 @@ namespace {
 constexpr int kAdjGroups = 1 << 14;
 constexpr size_t kAdjTape = (size_t)1 << 23;
 
+// The step's device view with the adjoint's tiling.
+mx::Dev adjoint_dev(const mx_system* s) {
+  mx::Dev d = s->d;
+  d.tiles = s->a_tiles;
+  d.ntiles = s->a_ntiles;
+  d.tile = mx::kThreads;
+  return d;
+}
+
 mx_status ensure_adjoint(mx_system* s) {
   const int N = s->N;
-  if (!s->a_v1) {
+  if (!s->a_tiles) {
     MX_TRY(dalloc(s, &s->a_x2, (size_t)6 * N));   // x2 and v1: one 6 x N pre-drift state
     s->a_v1 = s->a_x2 + 3 * (size_t)N;
     const int gcap = std::min(s->d.pair_cap, kAdjGroups);
@@ -1593,25 +1605,24 @@ mx_status ensure_adjoint(mx_system* s) {
     MX_TRY(dalloc(s, &s->a_x4, (size_t)3 * N));
     MX_TRY(dalloc(s, &s->a_P, 9 * s->h_sys.size()));
     MX_TRY(dalloc(s, &s->a_L, s->h_sys.size()));
-    MX_TRY(dalloc(s, &s->a_poff, s->tiles_cap));
-  }
-  if (s->a_poff_tile == s->tile && s->a_poff_order == s->order) return MX_OK;
-  std::vector<mx::Tile> tiles = make_tiles(s->h_sys, s->tile, s->order);
-  std::vector<int> poff(tiles.size());
-  size_t off = 0;
-  for (size_t t = 0; t < tiles.size(); ++t) {
-    poff[t] = (int)off;
-    off += 3 * (size_t)s->h_sys[tiles[t].sys].nbig + 9;
-  }
-  if (off > (size_t)INT32_MAX) return fail(MX_ERR_ARG, "adjoint partials too large");
-  if (off > s->a_part_cap) {
+    std::vector<mx::Tile> tiles = make_tiles(s->h_sys, mx::kThreads, 0);
+    std::vector<int> poff(tiles.size());
+    size_t off = 0;
+    for (size_t t = 0; t < tiles.size(); ++t) {
+      poff[t] = (int)off;
+      off += 3 * (size_t)s->h_sys[tiles[t].sys].nbig + 9;
+    }
+    if (off > (size_t)INT32_MAX) return fail(MX_ERR_ARG, "adjoint partials too large");
     MX_TRY(dalloc(s, &s->a_part, off));
     s->a_part_cap = off;
+    MX_TRY(dalloc(s, &s->a_poff, tiles.size()));
+    MX_TRY(dalloc(s, &s->a_tiles, tiles.size()));
+    s->a_ntiles = (int)tiles.size();
+    MX_CUDA(cudaMemcpyAsync(s->a_poff, poff.data(), poff.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
+    MX_CUDA(cudaMemcpyAsync(s->a_tiles, tiles.data(), tiles.size() * sizeof(mx::Tile),
+                            cudaMemcpyHostToDevice, s->st));
+    MX_CUDA(cudaStreamSynchronize(s->st));
   }
-  MX_CUDA(cudaMemcpyAsync(s->a_poff, poff.data(), poff.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
-  MX_CUDA(cudaStreamSynchronize(s->st));
-  s->a_poff_tile = s->tile;
-  s->a_poff_order = s->order;
   return MX_OK;
 }
 
@@ -1706,8 +1717,8 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
   MX_TRY(settle(s));
   MX_TRY(ensure_adjoint(s));
   mx::launch_prep(s->d, 0.0, 0, s->st);
-  mx::launch_loss(s->d, dev_xv_helio0, dev_w, dev_seed_final, dev_seed_init, s->a_part, s->a_poff,
-                  s->a_L, s->st);
+  mx::launch_loss(adjoint_dev(s), dev_xv_helio0, dev_w, dev_seed_final, dev_seed_init, s->a_part,
+                  s->a_poff, s->a_L, s->st);
   MX_CUDA(cudaMemcpyAsync(L, s->a_L, s->h_sys.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
   return sync_status(s);
 }
@@ -1765,7 +1776,7 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   a.tape_cap = s->a_tape_cap;
   a.bs_xsum = s->a_bsx;
   (void)N;
-  mx::launch_adjoint_step(s->d, a, s->st);
+  mx::launch_adjoint_step(adjoint_dev(s), a, s->st);
   return sync_status(s);
 }
 
