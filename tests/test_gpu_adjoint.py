@@ -187,3 +187,17 @@ def test_full_size_adjoint_workload():
         assert abs(Lo - L2) <= 1e-9 * abs(Lo)
         assert abs(ours - jvp) <= 1e-8 * abs(jvp), (ours, jvp)
     traj.close()
+
+
+def test_adjoint_does_not_depend_on_the_forward_tiling():
+    """The forward step gives the same bits for any tiling, and the adjoint
+    runs on its own tiling, so the loss and gradient are bit-identical
+    whatever tile size the forward autotuner picked."""
+    w, traj, xv0, gas, wts = _setup(nsmall=700, nsteps=20, every=10)
+    out = []
+    for tile in (64, 256, 128):
+        mx.mx_set_tiling(traj.h, tile, 0)
+        out.append(_grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every))
+    for o in out[1:]:
+        assert o[0] == out[0][0] and np.array_equal(o[1], out[0][1]) and np.array_equal(o[2], out[0][2])
+    traj.close()
