@@ -561,9 +561,12 @@ __device__ __forceinline__ void bs2_accel(const Bs2Term& t, const double (&X)[3]
   const double s2 = fma(dv[0], dv[0], fma(dv[1], dv[1], dv[2] * dv[2]));
   const double yy = rsqrt_d(s2);
   double wgt = (yy * yy) * (yy * t.musrc);
-  if (s2 >= t.rc2) {
+  // the changeover tests on the bit patterns (s2 and the radii are
+  // non-negative, the star's +infinity): off the FP64 pipe
+  const long long b2 = __double_as_longlong(s2);
+  if (b2 >= __double_as_longlong(t.rc2)) {
     wgt = 0.0;
-  } else if (s2 > t.rc2lo) {
+  } else if (b2 > __double_as_longlong(t.rc2lo)) {
     const double q = fma(s2, yy, -t.rc01) * t.i09;
     wgt *= fma(-q * q * q, fma(q, fma(6.0, q, -15.0), 10.0), 1.0);
   }
@@ -601,9 +604,12 @@ __device__ __forceinline__ int bs2_check(int K, int row, double sc, double tol2,
     e = fma(dx, dx, e);
   }
   e *= sc;
-  e = fmax(e, __shfl_xor_sync(0xffffffffu, e, 1));
-  e = fmax(e, __shfl_xor_sync(0xffffffffu, e, 2));
-  const bool conv = row >= 1 && row <= K && e <= tol2;
+  // max and test of non-negative errors on their bit patterns (integer order
+  // is value order there), off the FP64 pipe
+  long long eb = __double_as_longlong(e);
+  eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 1));
+  eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 2));
+  const bool conv = row >= 1 && row <= K && eb <= __double_as_longlong(tol2);
   const unsigned v = __ballot_sync(0xffffffffu, conv);
   return v ? ((__ffs(v) - 1) >> 2) : -1;
 }
