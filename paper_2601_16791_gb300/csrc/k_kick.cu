@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_jump_kick(Dev d, double jump
   gravity_all(d, S, sb, act, jl, rcj, x, y, z, ax, ay, az, FUSED ? dj : nullptr);
   if (!act) return;
   const bool big = jl < S.nbig;
-  if (jump_frac != 0.0 && !(FUSED && big)) {
+  if (__double_as_longlong(jump_frac) != 0 && !(FUSED && big)) {   // jump_frac is +0 or 1/2
     d.xv[j] = x;
     d.xv[(size_t)N + j] = y;
     d.xv[2 * (size_t)N + j] = z;

@@ -236,7 +236,11 @@ __device__ __forceinline__ double rcp_d(double x) {
   return fma(y, fma(e, e, e), y);
 }
 
-__device__ __forceinline__ bool finite_d(double a) { return isfinite(a); }
+// A double is finite when its exponent field is not all ones: tested on the
+// high word with integer instructions, off the FP64 pipe.
+__device__ __forceinline__ bool finite_d(double a) {
+  return (__double2hiint(a) & 0x7ff00000) != 0x7ff00000;
+}
 
 // A body removed from the integration (Sec. 3.5).  Detection also runs on
 // a Dev without bodies' status (the no-alloc entry), where nobody is removed.

@@ -65,14 +65,21 @@ static __device__ __noinline__ void stumpff_reduced(double z, double& c0, double
   }
 }
 
+// |a| <= c for a constant c > 0, on the bit patterns (integer order is value
+// order for non-negative doubles; a NaN compares false, as in FP64), so the
+// test leaves the FP64 pipe free.
+__device__ __forceinline__ bool abs_le(double a, double c) {
+  return (__double_as_longlong(a) & 0x7fffffffffffffffLL) <= __double_as_longlong(c);
+}
+
 // G0..G3 at s for beta.
 __device__ __forceinline__ void gfuns(double s, double beta, double* G) {
   const double s2 = s * s;
   const double z = beta * s2;
   double c2, c3;
-  if (fabs(z) <= 0.03) {
+  if (abs_le(z, 0.03)) {
     stumpff_series6(z, c2, c3);
-  } else if (fabs(z) <= 0.3) {
+  } else if (abs_le(z, 0.3)) {
     stumpff_series(z, c2, c3);
   } else {
     double c0, c1;
@@ -87,7 +94,7 @@ __device__ __forceinline__ void gfuns(double s, double beta, double* G) {
 // Returns false when the iteration cap is reached.
 __device__ __forceinline__ bool kepler_drift(double mu, double h, int maxit, double& x, double& y,
                                              double& z, double& u, double& v, double& w) {
-  if (h == 0.0) return true;
+  if ((__double_as_longlong(h) << 1) == 0) return true;   // h = +-0
   const double r02 = fma(x, x, fma(y, y, z * z));
   const double ir0 = rsqrt_d(r02);
   const double r0 = r02 * ir0;
@@ -104,7 +111,7 @@ __device__ __forceinline__ bool kepler_drift(double mu, double h, int maxit, dou
   // ends the solve there (1e-7 otherwise).  Longer steps, where the series
   // says little, start from its second-order part.
   const double hi = h * ir0;
-  const bool short_step = fabs(beta) * hi * hi <= 0.1;
+  const bool short_step = abs_le(beta * hi * hi, 0.1);
   const double t1 = short_step ? fma(0.5 * eta * eta, ir0, -zeta * (1.0 / 6.0)) : 0.0;
   const double stop = short_step ? 1e-5 : 1e-7;
   double s = hi * fma(h * ir0 * ir0, fma(hi, t1, -0.5 * eta), 1.0);

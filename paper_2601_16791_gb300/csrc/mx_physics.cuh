@@ -26,7 +26,9 @@ __device__ __forceinline__ GasAt gas_at(const SysDev& S, double x, double y) {
   const double R2 = fma(x, x, y * y);
   const double iR = rsqrt_d(R2);             // 1/R
   const double R = R2 * iR;
-  if (R < S.r_in) return q;                  // no gas inside the inner edge (Sec. 3.1.1)
+  // no gas inside the inner edge (Sec. 3.1.1); R >= 0, so the test on the bit
+  // patterns is the value test, off the FP64 pipe
+  if (__double_as_longlong(R) < __double_as_longlong(S.r_in)) return q;
   double sigma, rmh, rcs, reta, inv_cs;      // Sigma, R^-(1+f), R^(f-1/2), R^(2f), 1/c_s
   const double ih = rsqrt_d(R);              // R^-1/2
   if (S.flare_quarter) {
@@ -101,7 +103,7 @@ __device__ __forceinline__ void gas_drag_at(const SysDev& S, const DragConst& c,
   const double dv = v + c.offv;
   const double dw = w + c.offw;
   const double dv2 = fma(du, du, fma(dv, dv, dw * dw));
-  if (dv2 == 0.0) return;
+  if (__double_as_longlong(dv2) == 0) return;   // dv2 is +0 or positive
   const double dvm = dv2 * rsqrt_d(dv2);
   const double Ma = dvm * c.inv_cs;
   const double Re = c.re_k * dvm;
