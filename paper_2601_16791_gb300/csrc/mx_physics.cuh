@@ -111,7 +111,7 @@ __device__ __forceinline__ void gas_drag_at(const SysDev& S, const DragConst& c,
   const int kb = (kb_in >= 0) ? kb_in
                               : (__double_as_longlong(Re) < __double_as_longlong(1e5) ? 0 : 1);
   *kb_out = kb;
-  const double k = kb ? 0.2 : 0.4;
+  const double k16 = kb ? 1.6 * 0.2 : 1.6 * 0.4;   // 1.6 k, both products made by the compiler
   // Eq. 7 with one reciprocal: [(24/Re + 40/(10+Re))^-1 + 0.23 Ma]^-1 = D/den1
   // where D = 240 + 64 Re and den1 = Re (10 + Re) + 0.23 Ma D.
   const double D = fma(64.0, Re, 240.0);
@@ -119,7 +119,7 @@ __device__ __forceinline__ void gas_drag_at(const SysDev& S, const DragConst& c,
   const double A = 1.6 + Ma;
   const double r = rcp_d(den1 * A);
   const double first = D * A * r;           // = D / den1
-  const double second = fma(2.0, Ma, 1.6 * k) * den1 * r;
+  const double second = fma(2.0, Ma, k16) * den1 * r;
   const double cd = (S.cd_mode == 1) ? fma(first, first, second) : first + second;
   const double coef = cd * c.coef_k * dvm;
   a[0] = -coef * du;
