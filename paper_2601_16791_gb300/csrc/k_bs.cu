@@ -46,22 +46,46 @@ __device__ __forceinline__ int key_j(unsigned long long k) { return (int)((k >> 
 __device__ __forceinline__ int key_i(unsigned long long k) { return (int)(k & 0xffffffffull); }
 __device__ __forceinline__ bool key_small(unsigned long long k) { return (k >> 63) != 0; }
 
-// Inclusive block scan of two ints (blockDim.x = 1024).
+// Inclusive block scan of two ints (blockDim.x a multiple of 32, at most
+// 1024): shuffles within each warp, then one warp scans the warps' totals
+// (sa, sb: 32 ints each of shared scratch).  Two block barriers.
 __device__ __forceinline__ void block_scan2(int& a, int& b, int* sa, int* sb) {
-  const int t = threadIdx.x;
-  sa[t] = a;
-  sb[t] = b;
-  __syncthreads();
-  for (int off = 1; off < blockDim.x; off <<= 1) {
-    const int xa = (t >= off) ? sa[t - off] : 0;
-    const int xb = (t >= off) ? sb[t - off] : 0;
-    __syncthreads();
-    sa[t] += xa;
-    sb[t] += xb;
-    __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int xa = __shfl_up_sync(0xffffffffu, a, o);
+    const int xb = __shfl_up_sync(0xffffffffu, b, o);
+    if (lane >= o) {
+      a += xa;
+      b += xb;
+    }
   }
-  a = sa[t];
-  b = sb[t];
+  if (lane == 31) {
+    sa[warp] = a;
+    sb[warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    int ta = (lane < nw) ? sa[lane] : 0;
+    int tb = (lane < nw) ? sb[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int xa = __shfl_up_sync(0xffffffffu, ta, o);
+      const int xb = __shfl_up_sync(0xffffffffu, tb, o);
+      if (lane >= o) {
+        ta += xa;
+        tb += xb;
+      }
+    }
+    sa[lane] = ta;
+    sb[lane] = tb;
+  }
+  __syncthreads();
+  if (warp > 0) {
+    a += sa[warp - 1];
+    b += sb[warp - 1];
+  }
 }
 
 // Members of the test-particle group of the run of pairs starting at p
