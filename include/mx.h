@@ -188,7 +188,10 @@ mx_status mx_step(mx_system* s, int n_steps);
 
 /* Kernels of one step, in launch order, for mx_step_profiled. */
 #define MX_NKERN 10
-#define MX_K_PREP 0       /* momentum + staged big positions */
+#define MX_K_PREP 0       /* momentum + staged big positions: before a call's first and
+                             last half kick, and before every kick of runs with growth
+                             tracks or recorded/replayed k branches; the other kicks
+                             compute them themselves */
 #define MX_K_JUMP_KICK 1  /* jump + half kick(s): gravity and drag */
 #define MX_K_JUMP_DRIFT 2 /* jump + Kepler drift */
 #define MX_K_DETECT 3     /* encounter detection + compaction */

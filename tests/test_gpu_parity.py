@@ -340,3 +340,26 @@ def test_checkpoint_resume_bitwise():
     b = g.state(mx.MX_COORD_DH)
     g.close()
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("nbig,window", [(4, 8), (40, 8), (200, 0)])
+def test_call_boundaries_bitwise(nbig, window):
+    """An interior step's kick computes the momentum itself (warp shuffles up
+    to 32 big bodies, a fixed tree above), while a call's last half kick
+    follows k_prep: the same sum either way, so one call of 24 steps and calls
+    of 5, 1, 11 and 7 steps give the same bits, deferred planetesimals
+    included."""
+    if nbig == 4:
+        w = W.gas_4core_100k(nsmall=6000)
+    else:
+        w = W.semiactive_2000big_200k(nbig=nbig, nsmall=4000)
+    outs = []
+    for calls in ([24], [5, 1, 11, 7]):
+        g = mx.System(w)
+        mx.mx_set_defer_window(g.h, window)
+        for n in calls:
+            g.step(n)
+        outs.append((g.state(mx.MX_COORD_DH), g.energy()[0]))
+        g.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
