@@ -435,6 +435,7 @@ def semiactive_leg(steps=20):
     mx.mx_step_timed(s.h, 0, flush)
     ms, cnt, tot = mx.mx_step_timed(s.h, steps, flush)
     ms0, cnt0, tot0 = mx.mx_step_timed(s.h, 0, flush)
+    tile, order = mx.mx_tiling(s.h)
     s.close()
     out = {"workload": "semiactive_2000big_200k: 2,000 embryos (lunar to Mars mass) + 200,000 "
                        "planetesimals, 0.5-4 AU, no gas, dt = 6 d",
@@ -450,6 +451,7 @@ def semiactive_leg(steps=20):
             tf = f / (ms[k] * 1e-3) / 1e12
             out[f"{k}_tflops"] = tf
             out[f"{k}_frac_of_peak"] = tf / peak
+    out["tile"], out["tile_order"] = tile, order
     out["timing"] = "mx_step_timed (graphs, CUDA events, L2 flushed before every step)"
     return out
 
