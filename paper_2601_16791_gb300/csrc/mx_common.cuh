@@ -20,7 +20,7 @@
 namespace mx {
 
 constexpr int kThreads = 256;     // threads per block of the per-body kernels (= tile)
-constexpr int kBigChunk = 512;    // big bodies staged in shared memory per pass
+constexpr int kBigChunk = 256;    // big bodies staged in shared memory per pass
 constexpr int kMaxGroup = 16;     // bodies per Bulirsch-Stoer group (MX_MAX_GROUP)
 constexpr int kBsRows = 8;        // extrapolation rows: n_k = 2, 4, ..., 16
 constexpr int kMaxBigPairs = 512; // big-big encounter pairs handled per step
