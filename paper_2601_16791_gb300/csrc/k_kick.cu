@@ -257,12 +257,13 @@ __device__ __forceinline__ FusedPrep fused_prep(const Dev& d, const SysDev& S, c
 // Dynamic shared memory: kick_smem_bytes(d, FUSED) (the staging; FUSED with
 // more than 32 big bodies also the momentum tree, in the same space, before
 // the staging).
-// MINB: resident blocks the register allocation must allow (3 caps the kick
-// with its own prep at 80 registers, as the others; with many big bodies,
-// where the pair loop dominates, it runs uncapped instead, without spills).
-template <int NKICK, bool FUSED, int MINB = 1>
-__global__ void __launch_bounds__(kThreads, MINB) k_jump_kick(Dev d, double jump_frac,
-                                                             double kick_frac) {
+// Register use is capped at 80 (three resident blocks of 256 threads): with
+// the big bodies staged in chunks of at most 256, registers set residency,
+// and the extra warps outweigh the few spills (measured on the gas disk and
+// the semi-active disk).
+template <int NKICK, bool FUSED>
+__global__ void __launch_bounds__(kThreads, 3) k_jump_kick(Dev d, double jump_frac,
+                                                          double kick_frac) {
   extern __shared__ double dsm[];
   BigSmem sb(dsm, big_chunk(d.big_max));
   const Tile t = d.tiles[blockIdx.x];
@@ -417,9 +418,7 @@ void launch_jump_kick(const Dev& d, double jump_frac, double kick_frac, int nkic
 // jump 1/2, two half kicks; for forward runs without growth tracks or k
 // branches recorded or replayed.
 void launch_jump_kick_fused(const Dev& d, cudaStream_t st) {
-  const size_t sm = kick_smem_bytes(d, true);
-  if (d.big_max > 32) k_jump_kick<2, true, 1><<<d.ntiles, d.tile, sm, st>>>(d, 0.5, 0.5);
-  else k_jump_kick<2, true, 3><<<d.ntiles, d.tile, sm, st>>>(d, 0.5, 0.5);
+  k_jump_kick<2, true><<<d.ntiles, d.tile, kick_smem_bytes(d, true), st>>>(d, 0.5, 0.5);
 }
 
 void launch_accel(const Dev& d, double* acc, int drag_only, int acc_stride, int acc_base,
@@ -436,8 +435,7 @@ void configure_kick() {
   cudaFuncSetAttribute(k_prep, cudaFuncAttributePreferredSharedMemoryCarveout, c);
   cudaFuncSetAttribute(k_jump_kick<1, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
   cudaFuncSetAttribute(k_jump_kick<2, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_jump_kick<2, true, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-  cudaFuncSetAttribute(k_jump_kick<2, true, 3>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_jump_kick<2, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
 }
 
 }  // namespace mx
