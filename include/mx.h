@@ -316,12 +316,14 @@ mx_status mx_set_state_device(mx_system* s, const double* dev_xv);
 
 /* ------------------------------------------------------------------------
  * Differentiation: a hand-written adjoint (reverse mode) of the hybrid step.
- * The spec loss is the squared change of the planetesimals' semimajor
- * axes; its gradient is taken with respect to the initial heliocentric state
- * and to the gas parameters (Sigma normalisation, Sigma slope, C_D factor).
- * Bodies that met an encounter are massless and are left out of the loss
- * (weight 0), so Bulirsch-Stoer is never differentiated; an encounter
- * between two big bodies makes the adjoint inapplicable (the caller checks
+ * The loss provided (mx_loss_semimajor) is the weighted squared change of the
+ * planetesimals' semimajor axes; its gradient is taken with respect to the
+ * initial heliocentric state and to the gas parameters (Sigma normalisation,
+ * Sigma slope, C_D factor).  Planetesimals that met a big body either carry
+ * weight 0 (they are massless, so nothing else depends on them and the
+ * encounter groups are skipped), or are differentiated through their
+ * Bulirsch-Stoer groups (mx_adjoint_encounters).  An encounter between two
+ * big bodies makes the adjoint inapplicable (the caller checks
  * mx_encounter_log).  The Python layer (paper_2601_16791_gb300.autograd)
  * drives checkpointing: the state is stored every k steps and each segment is
  * recomputed before its reverse sweep.
