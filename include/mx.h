@@ -225,7 +225,10 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
  * caller-owned) is overwritten on the system's stream, outside the steps'
  * timed spans; after every step the host waits for it and reads its events.
  * Outputs as mx_step_profiled.  flush_bytes = 0 means no flush; n_steps = 0
- * runs the pending catch-up, timed.
+ * runs the pending catch-up, timed.  With kernel_ms and launches both NULL
+ * the production graphs run unchanged, with events only around each step
+ * (the event nodes between kernels add about 7% to a step), and only
+ * total_ms is written.
  */
 mx_status mx_step_timed(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
                         double* kernel_ms, int* launches, double* total_ms);

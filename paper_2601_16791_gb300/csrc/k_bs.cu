@@ -129,15 +129,19 @@ __device__ int run_members(const unsigned long long* keys, int p, int n, const i
   return cnt;
 }
 
+constexpr int kGroupKeysSmem = 2048;   // 16 KB of static shared memory
+
 __global__ void __launch_bounds__(1024) k_groups(Dev d) {
   __shared__ int nodes[2 * kMaxBigPairs];
   __shared__ int parent[2 * kMaxBigPairs];
   __shared__ int comp_of[2 * kMaxBigPairs];
   __shared__ int comp_start[2 * kMaxBigPairs + 1];
   __shared__ int comp_nodes[2 * kMaxBigPairs];
-  __shared__ int sa[1024], sb[1024];
-  __shared__ int s_nbb, s_nnodes, s_ncomp, s_bw, s_bm, s_bad;
+  __shared__ int sa[32], sb[32];
+  __shared__ int s_nbb, s_nnodes, s_ncomp, s_bw, s_bm, s_bad, s_slot;
   __shared__ unsigned long long bbk[kMaxBigPairs];   // the big-big pairs
+  // the step's keys, read once from global memory when they fit
+  __shared__ unsigned long long skeys[kGroupKeysSmem];
   const int count = *d.pair_count;
   if (count > d.pair_cap) {
     if (threadIdx.x == 0) atomicOr(d.status, ST_PAIR_OVF);
@@ -145,14 +149,17 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
   }
   const int n = count;
   if (n == 0) return;
-  const unsigned long long* keys = d.keys;
+  const bool staged = n <= kGroupKeysSmem;
+  const unsigned long long* keys = staged ? skeys : d.keys;
   if (threadIdx.x == 0) {
     s_nbb = 0;
     s_bad = 0;
+    s_slot = d.defer ? *d.hstep : 0;   // read early, used by thread 0 below
   }
   __syncthreads();
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const unsigned long long k = keys[p];
+    const unsigned long long k = d.keys[p];
+    if (staged) skeys[p] = k;
     if (!key_small(k)) {
       const int q = atomicAdd(&s_nbb, 1);
       if (q < kMaxBigPairs) bbk[q] = k;
@@ -232,7 +239,7 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
       for (int b = comp_start[c]; b < comp_start[c + 1]; ++b) d.work_mem[m++] = nodes[comp_nodes[b]];
     }
     // big groups of this step, for the catch-up of deferred planetesimals
-    const int slot = d.defer ? *d.hstep : 0;
+    const int slot = s_slot;
     if (d.defer && slot < d.hist_cap)
       for (int e = 0; e < nn; ++e) {
         const SysDev& Sg = d.sys[sys_of(d, nodes[e])];

@@ -1181,7 +1181,13 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
   if (n_steps == 0) return profiled_run(s, 0, flush, flush_bytes, kernel_ms, launches, total_ms);
   MX_TRY(set_device(s));
   MX_TRY(ensure_graphs(s));
-  MX_TRY(ensure_timed_graphs(s));
+  // with no per-kernel output asked for, the production graphs run as they
+  // are, with events only around each step
+  const bool per_kernel = kernel_ms || launches;
+  if (per_kernel) MX_TRY(ensure_timed_graphs(s));
+  cudaGraphExec_t gh = per_kernel ? s->gt_head : s->g_head;
+  cudaGraphExec_t gm = per_kernel ? s->gt_mid : s->g_mid;
+  cudaGraphExec_t gl = per_kernel ? s->gt_last : s->g_last;
   cudaStream_t st = s->st;
   double sum[MX_NKERN] = {0};
   int cnt[MX_NKERN] = {0};
@@ -1202,8 +1208,9 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
   static const int kHeadKind[2] = {MX_K_PREP, MX_K_JUMP_KICK};
   static const int kStepKind[6] = {MX_K_JUMP_DRIFT, MX_K_DETECT, MX_K_GROUPS, MX_K_BS, MX_K_PREP,
                                    MX_K_JUMP_KICK};
-  cudaEvent_t e_end = nullptr;
+  cudaEvent_t e_end = nullptr, e_start = nullptr;
   MX_CUDA(cudaEventCreate(&e_end));
+  MX_CUDA(cudaEventCreate(&e_start));
   double tot = 0.0;
   float ms = 0.f;
   cudaError_t e = cudaSuccess;
@@ -1213,17 +1220,18 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
     const bool test = eject_after(s, s->step + k + 1);
     const bool split = split_after(s, s->step + k + 1);
     if (flush_bytes > 0) e = cudaMemsetAsync(flush, k & 0xff, flush_bytes, st);
+    if (e == cudaSuccess && !per_kernel) e = cudaEventRecord(e_start, st);
     if (e == cudaSuccess && head) {
-      e = cudaGraphLaunch(s->gt_head, st);
+      e = cudaGraphLaunch(gh, st);
       if (e == cudaSuccess) e = slot_done(s, false, timed3);
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch((k + 1 == n_steps || split) ? s->gt_last : s->gt_mid, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch((k + 1 == n_steps || split) ? gl : gm, st);
     if (e == cudaSuccess && test) e = timed3(MX_K_EJECT, st, [&] { mx::launch_eject(s->d, 1, st); });
     if (e == cudaSuccess) e = slot_done(s, true, timed3);
     if (e == cudaSuccess) e = cudaEventRecord(e_end, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e_end);
     if (e != cudaSuccess) break;
-    if (head)
+    if (head && per_kernel)
       for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
         e = cudaEventElapsedTime(&ms, s->mk_head[q], s->mk_head[q + 1]);
         sum[kHeadKind[q]] += ms;
@@ -1231,7 +1239,7 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
       }
     // a fused interior kick has no k_prep: its span (empty) is not counted
     const bool fused = !(k + 1 == n_steps || split) && fuse_prep(s);
-    for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
+    for (int q = 0; q < 6 && per_kernel && e == cudaSuccess; ++q) {
       e = cudaEventElapsedTime(&ms, s->mk_step[q], s->mk_step[q + 1]);
       if (fused && kStepKind[q] == MX_K_PREP) continue;
       sum[kStepKind[q]] += ms;
@@ -1245,7 +1253,9 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
       cudaEventDestroy(sp.b);
     }
     spans.clear();
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, head ? s->mk_head[0] : s->mk_step[0], e_end);
+    if (e == cudaSuccess)
+      e = cudaEventElapsedTime(&ms, !per_kernel ? e_start : head ? s->mk_head[0] : s->mk_step[0],
+                               e_end);
     tot += ms;
   }
   for (auto& sp : spans) {
@@ -1253,6 +1263,7 @@ mx_status timed_graph_run(mx_system* s, int n_steps, void* flush, size_t flush_b
     cudaEventDestroy(sp.b);
   }
   cudaEventDestroy(e_end);
+  cudaEventDestroy(e_start);
   // side-stream launches that have completed
   std::vector<mx_system::Span> keep;
   for (auto& sp : s->side_spans) {

@@ -194,15 +194,21 @@ def mx_step_profiled(sys, n_steps):
     return dict(zip(KERNELS, ms.tolist())), dict(zip(KERNELS, cnt.tolist())), tot.value
 
 
-def mx_step_timed(sys, n_steps, dev_flush=None):
+def mx_step_timed(sys, n_steps, dev_flush=None, per_kernel=True):
     """mx_step_profiled with dev_flush (a CUDA tensor, e.g. larger than L2)
-    overwritten before every step, outside the timed spans."""
+    overwritten before every step, outside the timed spans.  per_kernel=False
+    runs the production graphs with events only around each step (the
+    per-kernel dicts come back empty)."""
     ms = np.zeros(len(KERNELS))
     cnt = np.zeros(len(KERNELS), dtype=np.int32)
     tot = ctypes.c_double(0.0)
     nbytes = 0 if dev_flush is None else dev_flush.numel() * dev_flush.element_size()
-    _check(load().mx_step_timed(sys, int(n_steps), _dptr(dev_flush), nbytes, _hptr(ms), _hptr(cnt),
+    _check(load().mx_step_timed(sys, int(n_steps), _dptr(dev_flush), nbytes,
+                                _hptr(ms) if per_kernel else None,
+                                _hptr(cnt) if per_kernel else None,
                                 ctypes.byref(tot)), "mx_step_timed")
+    if not per_kernel:
+        return {}, {}, tot.value
     return dict(zip(KERNELS, ms.tolist())), dict(zip(KERNELS, cnt.tolist())), tot.value
 
 

@@ -158,3 +158,17 @@ def test_timed_path_with_flush_matches_step():
     s.close()
     assert tot > 0 and cnt["k_jump_drift"] == 25 and cnt["k_jump_kick"] == 26
     assert np.array_equal(a, _run(w, 32, [25])[0])
+
+
+def test_production_graph_spans_match_step():
+    """mx_step_timed with no per-kernel outputs runs the production graphs
+    with events only around each step: the same states as mx_step."""
+    w = W.gas_4core_100k(nsmall=30_000)
+    flush = torch.empty(8 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    s = mx.System(w)
+    ms, cnt, tot = mx.mx_step_timed(s.h, 25, flush, per_kernel=False)
+    _, _, tot0 = mx.mx_step_timed(s.h, 0, flush, per_kernel=False)
+    a = s.state(mx.MX_COORD_DH)
+    s.close()
+    assert tot > 0 and ms == {} and cnt == {}
+    assert np.array_equal(a, _run(w, 32, [25])[0])
