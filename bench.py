@@ -132,11 +132,12 @@ class Clocks:
 
 
 # --------------------------------------------------------------- baselines
-def oracle_rate(workload, target_s, warm_steps=1):
-    """Oracle particle-steps/s on the host cores over a bounded sample of the
-    workload: every big body plus a prefix of the planetesimals."""
+def oracle_rate(workload, target_s, warm_steps=1, threads=None):
+    """Oracle particle-steps/s on the host cores (all, or `threads`) over a
+    bounded sample of the workload: every big body plus a prefix of the
+    planetesimals."""
     import oracle as orc
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     orc.set_threads(cores)
     w = workload
 
@@ -164,8 +165,23 @@ def oracle_rate(workload, target_s, warm_steps=1):
     el = time.perf_counter() - t0
     n = w.nbig + ns
     return {"value": n * nsteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": f"{w.nbig} cores + first {ns} of {w.nsmall} planetesimals, {nsteps} steps "
                       f"({el:.1f} s wall)"}, n, el / nsteps
+
+
+def cpu_model():
+    """The host CPU's name as the kernel reports it (best effort)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -205,7 +221,7 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "n_bodies": w.n,
                        "reference": "CPU FP64 oracle (oracle/mx_oracle.cpp), OpenMP over targets"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -653,7 +669,9 @@ def run_mx(args):
         except Exception as exc:
             line["semiactive"] = {"error": str(exc)[:300]}
     if not args.no_cpu_baseline:
+        one, _, _ = oracle_rate(w, 3.0, threads=1)
         cb, _, _ = oracle_rate(w, 12.0)
+        cb["single_thread"] = {"value": one["value"], "sample": one["sample"]}
         line["cpu_baseline"] = cb
     if world > 1:
         torch.distributed.destroy_process_group()
