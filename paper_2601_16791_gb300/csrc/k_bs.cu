@@ -1386,15 +1386,17 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
     ay += gq.adg[1];
   }
   const DragConst dc = S.gas_on ? drag_const(S, gq, x, y, hp0, hp1, hp2, rp, kd) : DragConst{};
-  for (int kk = 0; kk < nk; ++kk) {
-    double a[3] = {0.0, 0.0, 0.0};
+  for (int kk = 0; kk < nk; ++kk) {   // as in k_jump_kick
     if (S.gas_on) {
       int kout = 0;
-      gas_drag_at(S, dc, u, v, w, a, -1, &kout);
+      double dvec[3];
+      const double coef = gas_drag_coef(S, dc, u, v, w, dvec, -1, &kout);
+      kick_with_drag(kick_h, ax, ay, az, coef, dvec, u, v, w);
+    } else {
+      u = fma(kick_h, ax, u);
+      v = fma(kick_h, ay, v);
+      w = fma(kick_h, az, w);
     }
-    u = fma(kick_h, ax + a[0], u);
-    v = fma(kick_h, ay + a[1], v);
-    w = fma(kick_h, az + a[2], w);
   }
   if (!(finite_d(x) && finite_d(y) && finite_d(z) && finite_d(u) && finite_d(v) && finite_d(w)) &&
       lead)

@@ -318,19 +318,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_jump_kick(Dev d, double jump_fr
   const DragConst dc = drag ? drag_const(S, gq, x, y, hp0, hp1, hp2, rp, kd) : DragConst{};
 #pragma unroll
   for (int kk = 0; kk < NKICK; ++kk) {
-    double a[3] = {0.0, 0.0, 0.0};
     if (drag) {
       const int kidx = kbase + kk;
       const bool kuse = d.kmode != 0 && kidx < d.kcap;
       const size_t word = (size_t)kidx * d.kwords + (j >> 5);
       int kin = -1, kout = 0;
       if (kuse && d.kmode == 2) kin = (d.kbits[word] >> (j & 31)) & 1u;
-      gas_drag_at(S, dc, u, v, w, a, kin, &kout);
+      double dvec[3];
+      const double coef = gas_drag_coef(S, dc, u, v, w, dvec, kin, &kout);
       if (kuse && d.kmode == 1 && kout) atomicOr(&d.kbits[word], 1u << (j & 31));
+      kick_with_drag(kick_h, ax, ay, az, coef, dvec, u, v, w);
+    } else {
+      u = fma(kick_h, ax, u);
+      v = fma(kick_h, ay, v);
+      w = fma(kick_h, az, w);
     }
-    u = fma(kick_h, ax + a[0], u);
-    v = fma(kick_h, ay + a[1], v);
-    w = fma(kick_h, az + a[2], w);
   }
   if (big) {
     double* q = d.bk + S.boff + jl;

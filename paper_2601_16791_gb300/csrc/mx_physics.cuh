@@ -89,21 +89,26 @@ __device__ __forceinline__ DragConst drag_const(const SysDev& S, const GasAt& q,
   return c;
 }
 
-// Drag acceleration (Eq. 3) of one planetesimal with barycentric velocity
-// (u, v, w), from its velocity-free terms (drag_const).  C_D (Eq. 7) from Re
-// and Ma.  kb_in: -1 takes the k of Eq. 7 from Re; 0 or 1 forces k = 0.4 or
-// 0.2 (a recorded branch being replayed).  *kb_out receives the branch used.
-__device__ __forceinline__ void gas_drag_at(const SysDev& S, const DragConst& c, double u,
-                                            double v, double w, double* a, int kb_in,
-                                            int* kb_out) {
-  a[0] = a[1] = a[2] = 0.0;
+// Drag (Eq. 3) of one planetesimal with barycentric velocity (u, v, w), from
+// its velocity-free terms (drag_const): returns coef >= 0 with the
+// acceleration -coef (du, dv, dw), the velocity relative to the gas, written
+// to dvec.  C_D (Eq. 7) from Re and Ma.  kb_in: -1 takes the k of Eq. 7 from
+// Re; 0 or 1 forces k = 0.4 or 0.2 (a recorded branch being replayed).
+// *kb_out receives the branch used.
+__device__ __forceinline__ double gas_drag_coef(const SysDev& S, const DragConst& c, double u,
+                                                double v, double w, double* dvec, int kb_in,
+                                                int* kb_out) {
+  dvec[0] = dvec[1] = dvec[2] = 0.0;
   *kb_out = 0;
-  if (!c.in_gas) return;
+  if (!c.in_gas) return 0.0;
   const double du = u + c.offu;
   const double dv = v + c.offv;
   const double dw = w + c.offw;
+  dvec[0] = du;
+  dvec[1] = dv;
+  dvec[2] = dw;
   const double dv2 = fma(du, du, fma(dv, dv, dw * dw));
-  if (__double_as_longlong(dv2) == 0) return;   // dv2 is +0 or positive
+  if (__double_as_longlong(dv2) == 0) return 0.0;   // dv2 is +0 or positive
   const double dvm = dv2 * rsqrt_d(dv2);
   const double Ma = dvm * c.inv_cs;
   const double Re = c.re_k * dvm;
@@ -113,18 +118,45 @@ __device__ __forceinline__ void gas_drag_at(const SysDev& S, const DragConst& c,
   *kb_out = kb;
   const double k16 = kb ? 1.6 * 0.2 : 1.6 * 0.4;   // 1.6 k, both products made by the compiler
   // Eq. 7 with one reciprocal: [(24/Re + 40/(10+Re))^-1 + 0.23 Ma]^-1 = D/den1
-  // where D = 240 + 64 Re and den1 = Re (10 + Re) + 0.23 Ma D.
+  // where D = 240 + 64 Re and den1 = Re (10 + Re) + 0.23 Ma D, and the second
+  // term (2 Ma + 1.6 k)/(1.6 + Ma); over the common denominator den1 A:
+  // C_D = [D A + (2 Ma + 1.6 k) den1] / (den1 A).
   const double D = fma(64.0, Re, 240.0);
   const double den1 = fma(0.23 * Ma, D, Re * (10.0 + Re));
   const double A = 1.6 + Ma;
   const double r = rcp_d(den1 * A);
-  const double first = D * A * r;           // = D / den1
-  const double second = fma(2.0, Ma, k16) * den1 * r;
-  const double cd = (S.cd_mode == 1) ? fma(first, first, second) : first + second;
-  const double coef = cd * c.coef_k * dvm;
-  a[0] = -coef * du;
-  a[1] = -coef * dv;
-  a[2] = -coef * dw;
+  const double t2 = fma(2.0, Ma, k16);
+  double cd;
+  if (S.cd_mode == 1) {   // the first term squared
+    const double first = D * A * r;
+    cd = fma(first, first, t2 * den1 * r);
+  } else {
+    cd = fma(t2, den1, D * A) * r;
+  }
+  return cd * c.coef_k * dvm;
+}
+
+// The drag acceleration itself (gas_drag_coef), into a[3].
+__device__ __forceinline__ void gas_drag_at(const SysDev& S, const DragConst& c, double u,
+                                            double v, double w, double* a, int kb_in,
+                                            int* kb_out) {
+  double d[3];
+  const double coef = gas_drag_coef(S, c, u, v, w, d, kb_in, kb_out);
+  a[0] = -coef * d[0];
+  a[1] = -coef * d[1];
+  a[2] = -coef * d[2];
+}
+
+// One half kick of a planetesimal's velocity with the gravity (ax, ay, az)
+// and the drag coefficient and relative velocity of gas_drag_coef:
+// v + h (a_grav - coef dv), as (v + h a_grav) - (h coef) dv.
+__device__ __forceinline__ void kick_with_drag(double h, double ax, double ay, double az,
+                                               double coef, const double* dvec, double& u,
+                                               double& v, double& w) {
+  const double hc = h * coef;
+  u = fma(-hc, dvec[0], fma(h, ax, u));
+  v = fma(-hc, dvec[1], fma(h, ay, v));
+  w = fma(-hc, dvec[2], fma(h, az, w));
 }
 
 // The gas density factor of a planetesimal at (x, y, .) (the dens_factor
