@@ -171,16 +171,23 @@ def oracle_rate(workload, target_s, warm_steps=1, threads=None):
 
 
 def cpu_model():
-    """The host CPU's name as the kernel reports it (best effort)."""
+    """The host CPU's name as the kernel reports it (best effort; on Arm the
+    implementer and part numbers)."""
+    import platform
+    arm = {}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 key = line.split(":")[0].strip().lower()
                 if key in ("model name", "cpu model", "hardware"):
                     return line.split(":", 1)[1].strip()
+                if key in ("cpu implementer", "cpu part") and key not in arm:
+                    arm[key] = line.split(":", 1)[1].strip()
     except OSError:
         pass
-    import platform
+    if arm:
+        return (f"{platform.machine()} (CPU implementer {arm.get('cpu implementer', '?')}, "
+                f"part {arm.get('cpu part', '?')})")
     return platform.processor() or platform.machine()
 
 
