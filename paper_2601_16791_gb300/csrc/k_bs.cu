@@ -1366,11 +1366,28 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
   const double* BX = d.h_bx + (size_t)t * 3 * d.NB + S.boff;
   const double* hmu = d.h_mu + (size_t)t * d.NB + S.boff;
   const double* hrc = d.h_rc + (size_t)t * d.NB + S.boff;
+  // the pairs' weights on the lanes (lane l: big body c0 + l), then the sum
+  // in ascending order, as the kick's loop makes it (the same bits)
   double ax = 0, ay = 0, az = 0;
-  for (int l = 0; l < S.nbig; ++l) {
-    const double rc = hrc[l];
-    pair_acc(x - BX[l], y - BX[d.NB + l], z - BX[2 * (size_t)d.NB + l], fmax(hmu[l], 0.0),
-             rc * rc, 0.01 * (rc * rc), 0.1 * rc, (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0, ax, ay, az);
+  const int lane = threadIdx.x & 31;
+  for (int c0 = 0; c0 < S.nbig; c0 += 32) {
+    const int l = c0 + lane;
+    double f = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    if (l < S.nbig) {
+      const double rc = hrc[l];
+      ex = x - BX[l];
+      ey = y - BX[d.NB + l];
+      ez = z - BX[2 * (size_t)d.NB + l];
+      f = pair_weight(ex, ey, ez, fmax(hmu[l], 0.0), rc * rc, 0.01 * (rc * rc), 0.1 * rc,
+                      (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0);
+    }
+    const int cn = min(32, S.nbig - c0);
+    for (int k = 0; k < cn; ++k) {
+      const double fk = __shfl_sync(0xffffffffu, f, k);
+      ax = fma(-fk, __shfl_sync(0xffffffffu, ex, k), ax);
+      ay = fma(-fk, __shfl_sync(0xffffffffu, ey, k), ay);
+      az = fma(-fk, __shfl_sync(0xffffffffu, ez, k), az);
+    }
   }
   const int nk = head ? -hk : hk;
   const double kick_h = 0.5 * S.h;

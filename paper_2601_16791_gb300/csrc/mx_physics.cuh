@@ -201,11 +201,11 @@ __device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, do
   a[1] += q.adg[1];
 }
 
-// K(s)/s^3 times mu for one pair, accumulated into (ax, ay, az) as -f * d
-// (Sec. 2.1.3: K = 1 for s^2 >= rc^2, 0 for s^2 <= 0.01 rc^2, quintic between).
-__device__ __forceinline__ void pair_acc(double dx, double dy, double dz, double mu, double rc2,
-                                         double rc2lo, double rc01, double i09rc, double& ax,
-                                         double& ay, double& az) {
+// f = mu K(s)/s^3 for one pair at separation d (Sec. 2.1.3: K = 1 for
+// s^2 >= rc^2, 0 for s^2 <= 0.01 rc^2, quintic between).
+__device__ __forceinline__ double pair_weight(double dx, double dy, double dz, double mu,
+                                              double rc2, double rc2lo, double rc01,
+                                              double i09rc) {
   const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
   const double yy = rsqrt_d(s2);
   double f = yy * yy * yy;
@@ -219,7 +219,14 @@ __device__ __forceinline__ void pair_acc(double dx, double dy, double dz, double
       f *= q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
     }
   }
-  f *= mu;
+  return f * mu;
+}
+
+// The pair's acceleration -f d accumulated into (ax, ay, az).
+__device__ __forceinline__ void pair_acc(double dx, double dy, double dz, double mu, double rc2,
+                                         double rc2lo, double rc01, double i09rc, double& ax,
+                                         double& ay, double& az) {
+  const double f = pair_weight(dx, dy, dz, mu, rc2, rc2lo, rc01, i09rc);
   ax = fma(-f, dx, ax);
   ay = fma(-f, dy, ay);
   az = fma(-f, dz, az);
