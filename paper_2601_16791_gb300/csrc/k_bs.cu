@@ -1241,14 +1241,14 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
   const double a1[6] = {x, y, z, u, v, w};
   float af[12];
   for (int k = 0; k < 6; ++k) {
-    af[k] = (float)a0[k];
-    af[6 + k] = (float)a1[k];
+    af[k] = to_float_bits(a0[k]);
+    af[6 + k] = to_float_bits(a1[k]);
   }
   const double* B0 = d.h_b0 + (size_t)t * 6 * NBs + S.boff;
   const double* B1 = d.h_b1 + (size_t)t * 6 * NBs + S.boff;
   const double* hmu = d.h_mu + (size_t)t * NBs + S.boff;
   const double* hrc = d.h_rc + (size_t)t * NBs + S.boff;
-  const float hf = (float)S.h;
+  const float hf = to_float_bits(S.h);
   // flagged big bodies, ascending
   int fl[kMaxGroup];
   int nf = 0;
@@ -1258,14 +1258,14 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
     bool hit = false;
     if (l < S.nbig && hmu[l] >= 0.0) {   // a body removed by then meets nothing
       const double rcb = hrc[l];
-      const float rcf = fmaxf((float)rcb, (float)0.0);
+      const float rcf = fmaxf(to_float_bits(rcb), 0.0f);
       float bf[12];
       double b0[6], b1[6];
       for (int q = 0; q < 6; ++q) {
         b0[q] = B0[(size_t)q * NBs + l];
         b1[q] = B1[(size_t)q * NBs + l];
-        bf[q] = (float)b0[q];
-        bf[6 + q] = (float)b1[q];
+        bf[q] = to_float_bits(b0[q]);
+        bf[6 + q] = to_float_bits(b1[q]);
       }
       if (encounter_screen(af, bf, rcf * rcf, hf)) {
         const double rc = fmax(rcb, 0.0);

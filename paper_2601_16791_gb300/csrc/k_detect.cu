@@ -67,18 +67,18 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
   const bool jbig = jl < S.nbig;
   const int lane = threadIdx.x & 31;
   const double h = S.h;
-  const float hf = (float)h;
+  const float hf = to_float_bits(h);
   double a0[6], a1[6];
   float af[12];
   double rcj = 0.0;
   for (int k = 0; k < 6; ++k) {
     a0[k] = act ? xv0[(size_t)k * N + j] : 0.0;
     a1[k] = act ? xv1[(size_t)k * N + j] : 0.0;
-    af[k] = (float)a0[k];
-    af[6 + k] = (float)a1[k];
+    af[k] = to_float_bits(a0[k]);
+    af[6 + k] = to_float_bits(a1[k]);
   }
   if (act && jbig) rcj = d.brc[S.boff + jl];
-  const float rcjf = (float)rcj;
+  const float rcjf = to_float_bits(rcj);
   int hits[kMaxGroup];
   int nh = 0;
   const unsigned long long tag = ((unsigned long long)(jbig ? 0u : 1u) << 63) |
@@ -112,12 +112,12 @@ __global__ void __launch_bounds__(kThreads) k_detect(Dev d, const double* xv0, c
         const double p0 = xv0[(size_t)k * N + g], p1 = xv1[(size_t)k * N + g];
         sm.s[k][threadIdx.x] = p0;
         sm.s[6 + k][threadIdx.x] = p1;
-        sm.f[k][threadIdx.x] = (float)p0;
-        sm.f[6 + k][threadIdx.x] = (float)p1;
+        sm.f[k][threadIdx.x] = to_float_bits(p0);
+        sm.f[6 + k][threadIdx.x] = to_float_bits(p1);
       }
       const double rcb = d.brc[S.boff + c0 + threadIdx.x];
       sm.rc[threadIdx.x] = rcb;
-      sm.rcf[threadIdx.x] = (float)rcb;
+      sm.rcf[threadIdx.x] = to_float_bits(rcb);
       sm.out[threadIdx.x] = removed(d, g);
     }
     __syncthreads();

@@ -210,6 +210,18 @@ __device__ __forceinline__ float abs_to_float_bits(double x) {
   return __uint_as_float((hi - ((1023u - 127u) << 20)) << 3);
 }
 
+// x as a float for the FP32 encounter screen, read off the binary64 bit
+// pattern like abs_to_float_bits (20 mantissa bits kept, relative error
+// < 2^-20, far inside the screen's margin), sign kept; zero for
+// |x| < 2^-126.  Valid for |x| < 2^128.  Integer instructions only, where a
+// conversion would take an FP64 issue slot.
+__device__ __forceinline__ float to_float_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned a = hi & 0x7fffffffu;
+  const unsigned f = (a < (897u << 20)) ? 0u : ((a - ((1023u - 127u) << 20)) << 3);
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
 // A positive normal float as a double, exactly, by moving its bits.
 __device__ __forceinline__ double float_to_double_bits(float f) {
   const unsigned u = __float_as_uint(f);
