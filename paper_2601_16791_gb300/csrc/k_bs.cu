@@ -42,6 +42,9 @@ __device__ __forceinline__ int sys_of(const Dev& d, int g) {
   return lo;
 }
 
+// 2^-c for 0 <= c <= 1022, exactly, from its bit pattern (no FP64 division).
+__device__ __forceinline__ double pow2_neg(int c) { return __hiloint2double((1023 - c) << 20, 0); }
+
 __device__ __forceinline__ int key_j(unsigned long long k) { return (int)((k >> 32) & 0x7fffffffull); }
 __device__ __forceinline__ int key_i(unsigned long long k) { return (int)(k & 0xffffffffull); }
 __device__ __forceinline__ bool key_small(unsigned long long k) { return (k >> 63) != 0; }
@@ -387,7 +390,7 @@ __device__ int bs_rounds(unsigned gmask, int base, int lane, double mu0, const d
   }
   const int n = 2 * (row + 1);
   const double inv_n = 1.0 / n;
-  const double cscale = 1.0 / (double)(1 << cand);
+  const double cscale = pow2_neg(cand);   // 2^-cand, exact
   for (int round = 0; round < max_rounds; ++round) {
     if (g.rem == 0.0) return 1;
     if (g.nsub >= max_sub) return -1;
@@ -477,7 +480,7 @@ __device__ int bs_rounds(unsigned gmask, int base, int lane, double mu0, const d
       for (int c = 0; c < 6; ++c)
 #pragma unroll
         for (int b = 0; b < NB; ++b) g.Y[c][b] = __shfl_sync(gmask, T[c][b], src);
-      const double Hacc = g.H / (double)(1 << c_acc);
+      const double Hacc = g.H * pow2_neg(c_acc);   // exact: a power of two
       g.rem -= Hacc;
       g.H = 1.3 * Hacc;
     } else {
@@ -657,7 +660,7 @@ __device__ int bs2_rounds(int cand, int lane, const Bs2Term& t, double tol, int 
   const bool vel = q >= 2;
   const int n = 2 * (row + 1);
   const double tol2 = tol * tol;
-  const double cscale = 1.0 / (double)(1 << cand);
+  const double cscale = pow2_neg(cand);   // 2^-cand, exact
   for (int round = 0; round < max_rounds; ++round) {
     if (g.rem == 0.0) return 1;
     if (g.nsub >= max_sub) return -1;
@@ -750,7 +753,7 @@ __device__ int bs2_rounds(int cand, int lane, const Bs2Term& t, double tol, int 
       }
       g.nsub += acc_c + 1;                   // attempts a one-at-a-time search makes
       if (g.nsub > max_sub) return -1;
-      const double Hacc = g.H * (1.0 / (double)(1 << acc_c));
+      const double Hacc = g.H * pow2_neg(acc_c);   // exact: a power of two
       g.rem -= Hacc;
       g.H = 1.3 * Hacc;
     } else {
