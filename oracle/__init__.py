@@ -89,6 +89,7 @@ def lib():
             "orc_hermite_d2min": (_D, [_D, _D, _D, _D, _D]),
             "orc_detect": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P]),
             "orc_bs_group": (_I, [_P, _I, _P, _P, _P, _D, _P]),
+            "orc_build_groups": (_I, [_I, _I, _I, _P, _I, _I, _P, _P, _P, _P]),
             "orc_step": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _P, _P]),
             "orc_step_ex": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I, ctypes.c_longlong, _P, _P,
                                  _D, _P, _P]),
@@ -272,6 +273,23 @@ def bs_group(p, mu, rcrit, xv, h):
     _check(lib().orc_bs_group(ctypes.byref(p), xv.shape[1], _ptr(mu), _ptr(rcrit), _ptr(xv),
                               float(h), ctypes.byref(nsub)), "bs_group")
     return xv, nsub.value
+
+
+def build_groups(nbig, nsmall, pairs):
+    """Encounter groups of one step from its flagged (i, j) pairs.  Returns a
+    list of (members, write_from): members bigs ascending then the
+    planetesimal, write_from the index of the first member written back."""
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    ng = ctypes.c_int(0)
+    cap_g = max(1, nbig + nsmall)
+    cap_m = max(1, len(pr) * (nbig + 1) + nbig)
+    mem = np.empty(cap_m, dtype=np.int32)
+    off = np.empty(cap_g + 1, dtype=np.int32)
+    wf = np.empty(cap_g, dtype=np.int32)
+    _check(lib().orc_build_groups(int(nbig), int(nsmall), len(pr), _ptr(pr), cap_g, cap_m,
+                                  _ptr(mem), _ptr(off), _ptr(wf), ctypes.byref(ng)),
+           "build_groups")
+    return [(mem[off[g]:off[g + 1]].tolist(), int(wf[g])) for g in range(ng.value)]
 
 
 def step(p, nbig, xv, mu, rcrit, rp_km, rhop, nsteps, log_cap=0):

@@ -1273,6 +1273,41 @@ int orc_detect(const orc_params* p, int nbig, int n, const double* xv0, const do
   return (int)pr.size() > cap ? ORC_ERR_PAIR_OVERFLOW : ORC_OK;
 }
 
+// Encounter groups of one step from its flagged pairs (big index first, each
+// pair once, as orc_detect lists them).  Writes each group's members, bigs
+// ascending then the planetesimal, back to back in members[], the start of
+// group g at offsets[g] (offsets[ngroups] = total) and the first member that
+// receives the group's result at write_from[g].  Big groups come first (root
+// order), then the planetesimals' groups in planetesimal order.
+int orc_build_groups(int nbig, int nsmall, int npairs, const int* pairs, int cap_groups,
+                     int cap_members, int* members, int* offsets, int* write_from,
+                     int* ngroups) {
+  if (nbig < 0 || nsmall < 0 || npairs < 0 || (npairs > 0 && !pairs) || !ngroups)
+    return ORC_ERR_ARG;
+  Bodies b;
+  b.nbig = nbig; b.nsmall = nsmall; b.n = nbig + nsmall;
+  std::vector<std::pair<int, int>> pr((size_t)npairs);
+  for (int k = 0; k < npairs; ++k) {
+    const int i = pairs[2 * k], j = pairs[2 * k + 1];
+    if (i < 0 || i >= nbig || j <= i || j >= b.n) return ORC_ERR_ARG;
+    pr[k] = {i, j};
+  }
+  std::vector<Group> g = build_groups(b, pr);
+  *ngroups = (int)g.size();
+  size_t tot = 0;
+  for (auto& q : g) tot += q.members.size();
+  if ((int)g.size() > cap_groups || (long long)tot > cap_members) return ORC_ERR_PAIR_OVERFLOW;
+  if (!members || !offsets || !write_from) return ORC_ERR_ARG;
+  int o = 0;
+  for (size_t k = 0; k < g.size(); ++k) {
+    offsets[k] = o;
+    write_from[k] = g[k].write_from;
+    for (int m : g[k].members) members[o++] = m;
+  }
+  offsets[g.size()] = o;
+  return ORC_OK;
+}
+
 int orc_bs_group(const orc_params* p, int nb, const double* mu, const double* rcrit, double* xv,
                  double h, int* nsub) {
   if (!p || nb <= 0 || !mu || !rcrit || !xv) return ORC_ERR_ARG;

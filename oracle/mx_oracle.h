@@ -136,6 +136,20 @@ int orc_detect(const orc_params* p, int nbig, int n, const double* xv0,
                const double* xv1, const double* rcrit, unsigned char* flags,
                int* pairs, int cap, int* npairs);
 
+/* Encounter groups of one step (reading of Sec. 2's single BS call over the
+ * encounter bodies): bigs joined by flagged big-big pairs form big groups;
+ * each flagged planetesimal forms a group of the whole big groups of the
+ * bigs it meets, then itself, and only it is written back.  pairs: npairs
+ * (i, j) with i < nbig, i < j < nbig + nsmall.  Output: members[] back to
+ * back (bigs ascending, then the planetesimal), offsets[ngroups + 1],
+ * write_from[ngroups] (index within the group of the first member written).
+ * Big groups (two or more bigs) come first, then the planetesimals' groups
+ * in planetesimal order.  ORC_ERR_PAIR_OVERFLOW if the groups exceed
+ * cap_groups or cap_members (ngroups still set). */
+int orc_build_groups(int nbig, int nsmall, int npairs, const int* pairs,
+                     int cap_groups, int cap_members, int* members,
+                     int* offsets, int* write_from, int* ngroups);
+
 /* Bulirsch-Stoer integration over h of a group of nb bodies (6 x nb SoA
  * state, modified in place) under the star plus (1-K)-weighted pair forces
  * from the group's massive members. nsub receives the macro sub-steps. */
