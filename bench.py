@@ -7,15 +7,15 @@ gas disk Sigma = 1700 (r/AU)^-1 g/cm^2, H/r = 0.05 (r/AU)^0.25, dt = 10 days;
 seeded synthetic inputs (paper_2601_16791_gb300.workloads.gas_4core_100k).
 
 A timed step is one full hybrid step (half kick with drag, jump, Kepler drift,
-encounter detection, Bulirsch-Stoer of the flagged groups, jump, half kick),
-run kernel by kernel with CUDA events on the system's stream: all K steps in
-one mx_step_timed call, the production launch sequence (a step's closing half
-kick and the next step's opening one share a launch).  L2 is flushed (256 MiB
-write) before every step, outside the steps' timed spans.  Planetesimals whose
-encounter outlasts one Bulirsch-Stoer macro sub-step are deferred and
-replayed by the catch-up kernel at window ends (long encounters continue on a
-side stream while the next window runs); the timed region ends with the last
-catch-up, so every timed step is complete.
+encounter detection, Bulirsch-Stoer of the flagged groups, jump, half kick).
+The K steps run through the production CUDA graphs of mx_step, enqueued back to
+back with an L2 flush (201 MB write) before every step, followed by the
+catch-up that brings every deferred planetesimal to the last step
+(planetesimals whose encounter outlasts one Bulirsch-Stoer macro sub-step are
+replayed from the big bodies' recorded history; long encounters continue on a
+side stream while the next window runs).  The value is N K over that span's
+device time minus the K flushes, timed alone right after.  Per-kernel times
+come from a second pass of K steps with events between kernels.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -52,6 +52,13 @@ FLOPS_KICK_UPDATE = 9      # v += (h/2)(a_grav + a_drag)
 FLOPS_JUMP = 3             # x += (h/2) P/m0
 FLOPS_DRIFT = 340          # universal-variable solve: ~60 x 5 iterations + Stumpff ~40
 FLOPS_DETECT_PAIR = 30     # endpoint distances and slopes, per (target, big) pair
+# one force evaluation of a two-body Bulirsch-Stoer group (a planetesimal and
+# a big body) with the Stoermer update: two star terms (12 each), the big
+# body's (1-K)-weighted pull on the planetesimal (20), their sum (3), and the
+# update D += d^2 A, X += D of both bodies (18); the massless body's pull on
+# the big body is zero and not counted
+FLOPS_BS2_FEVAL = 65
+FLUSH_BYTES = 192 << 20    # L2 flush between steps: 201 MB written, 1.56x the 129 MB L2
 
 
 def parse():
@@ -64,8 +71,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and adjoint legs")
     ap.add_argument("--ensemble-steps", type=int, default=10)
+    ap.add_argument("--budget-s", type=float, default=120.0,
+                    help="reference arm: host seconds the warm-up and timed steps may take")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="another named workload (informational; the metric is quoted on the default)")
+    ap.add_argument("--window", type=int, default=None,
+                    help="deferral window in steps (default: the library's)")
     ap.add_argument("--tiling", default=None,
                     help="tile,order to override the autotuner (order 2: tiles per SM)")
     return ap.parse_args()
@@ -166,8 +177,8 @@ def oracle_rate(workload, target_s, warm_steps=1, threads=None):
     n = w.nbig + ns
     return {"value": n * nsteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "cpu": cpu_model(),
-            "sample": f"{w.nbig} cores + first {ns} of {w.nsmall} planetesimals, {nsteps} steps "
-                      f"({el:.1f} s wall)"}, n, el / nsteps
+            "sample": f"{w.nbig} bigs + {ns} of {w.nsmall} planetesimals, {nsteps} steps, "
+                      f"{el:.1f} s"}, n, el / nsteps
 
 
 def cpu_model():
@@ -200,8 +211,8 @@ def run_reference(args):
     w = W.make(WORKLOAD)
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
-    # bound the sample so W + K steps take about two minutes
-    budget_s = 120.0
+    # bound the sample so W + K steps take about --budget-s seconds
+    budget_s = args.budget_s
     per_step_target = budget_s / max(1, args.steps + args.warmup)
     ns = 256
     p = orc.make_params(w.params)
@@ -225,12 +236,12 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "n_bodies": w.n,
-                       "reference": "CPU FP64 oracle (oracle/mx_oracle.cpp), OpenMP over targets"},
+            "config": bench_config(w),
+            "reference": "CPU FP64 oracle (oracle/mx_oracle.cpp), OpenMP over targets",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(r4(line), separators=(",", ":")), flush=True)
 
 
 # ---------------------------------------------------------------- roofline
@@ -249,6 +260,19 @@ def kernel_flops(kname, w, launches, nsteps):
     if kname == "k_detect":
         return FLOPS_DETECT_PAIR * (ns * nb + nb * (nb - 1) // 2) * launches
     return None
+
+
+def catchup_flops(w, ops):
+    """Algorithmic FP64 flops of catch-up work counted on the device
+    (mx_catchup_work): body-slots through jump + drift + encounter test, half
+    kicks of one body (gravity of every big body, drag, update), two-body
+    Bulirsch-Stoer force evaluations of the one-try-at-a-time search."""
+    slots, kicks, fevals = ops
+    nb = w.nbig
+    drag = FLOPS_DRAG if w.params["gas"]["enabled"] else 0
+    return (slots * (FLOPS_JUMP + FLOPS_DRIFT + nb * FLOPS_DETECT_PAIR)
+            + kicks * (nb * FLOPS_PAIR_KICK + drag + FLOPS_KICK_UPDATE)
+            + fevals * FLOPS_BS2_FEVAL)
 
 
 def source_hash(names):
@@ -328,12 +352,9 @@ def ensemble_leg(steps, nsys=256):
     t_loop = time.perf_counter() - t0
     for s in systems:
         s.close()
-    return {"workload": "ensemble_256: 256 systems, 2-50 embryos and 1e3-2e5 planetesimals each, "
-                        "gas Sigma x U[0.3,3], dt=10 d",
-            "n_systems": nsys, "n_bodies": n_tot, "steps": steps,
+    return {"n_systems": nsys, "n_bodies": n_tot, "steps": steps,
             "batched_value": n_tot * steps / t_batch, "loop_value": n_tot * steps / t_loop,
-            "unit": UNIT, "speedup": t_loop / t_batch, "tile": tile, "tile_order": order,
-            "timing": "host wall clock around mx_step with device synchronisation"}
+            "speedup": t_loop / t_batch, "tile": [tile, order]}
 
 
 def adjoint_leg(nsteps=200, every=50):
@@ -389,14 +410,11 @@ def adjoint_leg(nsteps=200, every=50):
     a_ms = e[2].elapsed_time(e[3]) / reps
     g_ms = e4.elapsed_time(e5) / reps
     traj.close()
-    return {"workload": "adjoint_4core_50k: 4 cores + 50,000 planetesimals, gas, loss on final a",
-            "steps": nsteps, "checkpoint_every": every, "forward_s": t_fwd, "backward_s": t_bwd,
-            "backward_over_forward": t_bwd / t_fwd, "adjoint_step_ms": a_ms,
-            "forward_step_ms": f_ms, "adjoint_over_forward_step": a_ms / f_ms,
+    return {"steps": nsteps, "checkpoint_every": every,
+            "backward_over_forward": t_bwd / t_fwd, "forward_step_ms": f_ms,
+            "adjoint_step_ms": a_ms, "adjoint_over_forward_step": a_ms / f_ms,
             "adjoint_step_ms_through_groups": g_ms,
-            "through_groups_over_forward_step": g_ms / f_ms,
-            "note": ("adjoint_step: encountered planetesimals out of the loss (groups skipped); "
-                     "through_groups: every encounter group recorded and reversed")}
+            "through_groups_over_forward_step": g_ms / f_ms}
 
 
 def eject_leg(steps=200):
@@ -409,7 +427,7 @@ def eject_leg(steps=200):
     from paper_2601_16791_gb300 import mx, workloads as W
     st = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    out = {"workload": WORKLOAD_TEXT, "steps": steps}
+    out = {"steps": steps}
     for every in (0, 1):
         w = W.make(WORKLOAD)
         w.params = dict(w.params, eject_every=every)
@@ -423,9 +441,7 @@ def eject_leg(steps=200):
         if every:
             n_launch = max(1, cnt["k_eject"])
             t = ms["k_eject"] / n_launch
-            out["k_eject_launches"] = cnt["k_eject"]
             out["k_eject_us"] = 1e3 * t
-            out["k_eject_gbs"] = 50.0 * w.n / (t * 1e-3) / 1e9
             out["removed"] = int(mx.mx_body_status(s.h, w.n)[1][0])
             el = torch.empty((6, w.n), dtype=torch.float64, device="cuda")
             mx.mx_elements(s.h, el)
@@ -438,8 +454,6 @@ def eject_leg(steps=200):
             out["elements_us"] = 1e3 * e0.elapsed_time(e1) / 20
         s.close()
     out["test_overhead_per_step"] = out["ms_per_step_every_step"] / out["ms_per_step_none"] - 1.0
-    out["timing"] = ("mx_step_timed (graphs, CUDA events, L2 flushed before every step); "
-                     "mx_elements: CUDA events around 20 calls (each ends with a status read)")
     return out
 
 
@@ -460,22 +474,15 @@ def semiactive_leg(steps=20):
     ms0, cnt0, tot0 = mx.mx_step_timed(s.h, 0, flush)
     tile, order = mx.mx_tiling(s.h)
     s.close()
-    out = {"workload": "semiactive_2000big_200k: 2,000 embryos (lunar to Mars mass) + 200,000 "
-                       "planetesimals, 0.5-4 AU, no gas, dt = 6 d",
-           "n_bodies": w.n, "steps": steps, "ms_per_step": (tot + tot0) / steps,
-           "value": w.n * steps / ((tot + tot0) * 1e-3), "unit": UNIT, "fp64_peak_tflops": peak,
-           "kernels_ms_per_step": {k: (ms[k] + ms0[k]) / steps for k in mx.KERNELS
-                                   if ms[k] + ms0[k] > 0}}
+    out = {"n_bodies": w.n, "steps": steps, "ms_per_step": (tot + tot0) / steps,
+           "value": w.n * steps / ((tot + tot0) * 1e-3)}
     # (detection's count is per pair; its FP32 screen skips most of them, so
     # it is not a rate against the FP64 peak)
-    for k in ("k_jump_kick", "k_jump_drift"):
+    for k, key in (("k_jump_kick", "kick_frac_of_peak"), ("k_jump_drift", "drift_frac_of_peak")):
         f = kernel_flops(k, w, cnt[k], steps)
         if f and ms[k] > 0:
-            tf = f / (ms[k] * 1e-3) / 1e12
-            out[f"{k}_tflops"] = tf
-            out[f"{k}_frac_of_peak"] = tf / peak
-    out["tile"], out["tile_order"] = tile, order
-    out["timing"] = "mx_step_timed (graphs, CUDA events, L2 flushed before every step)"
+            out[key] = f / (ms[k] * 1e-3) / 1e12 / peak
+    out["tile"] = [tile, order]
     return out
 
 
@@ -490,9 +497,7 @@ def growth_leg(steps=200):
     from paper_2601_16791_gb300 import mx, workloads as W
     st = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    out = {"workload": "growth_2giant: 2 embryos (0.01 -> 15 -> 300/100 M_earth) + 24,000 "
-                       "planetesimals, gas, tau_c = 400 d, tau_g = 200 d, steps 60-259",
-           "steps": steps}
+    out = {"steps": steps}
     m60 = None
     for grow in (True, False):
         w = W.growth_2giant(tau_c_days=400.0, tau_g_days=200.0)
@@ -512,19 +517,31 @@ def growth_leg(steps=200):
         ms0, cnt0, tot0 = mx.mx_step_timed(s.h, 0, flush)
         key = "growth" if grow else "fixed_masses"
         out[f"ms_per_step_{key}"] = (tot + tot0) / steps
-        out[f"kernels_ms_per_step_{key}"] = {k: (ms[k] + ms0[k]) / steps for k in mx.KERNELS
-                                             if ms[k] + ms0[k] > 0}
         if grow:
             out["k_prep_us"] = 1e3 * ms["k_prep"] / max(1, cnt["k_prep"])
-            out["masses_msun_end"] = mx.mx_planets(s.h, w.nbig)[0].tolist()
-        out[f"defer_window_{key}"] = mx.mx_defer_stats(s.h)[0]
         s.close()
-    out["masses_msun_fixed"] = [float(v) for v in m60]
-    out["timing"] = "mx_step_timed (graphs, CUDA events, L2 flushed before every step)"
     return out
 
 
 # ------------------------------------------------------------------- main
+def r4(x):
+    """Rounds floats to 4 significant digits, recursively (a short JSON line)."""
+    if isinstance(x, float):
+        return float(f"{x:.4g}")
+    if isinstance(x, dict):
+        return {k: r4(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [r4(v) for v in x]
+    return x
+
+
+def bench_config(w, name=WORKLOAD):
+    """The `config` of both arms (the same dict)."""
+    return {"workload": name, "n_bodies": w.n,
+            "description": WORKLOAD_TEXT if name == WORKLOAD else name,
+            "l2": "GPU arm: 201 MB written before every timed step (outside the value); CPU arm: n/a"}
+
+
 def run_mx(args):
     import torch
     from paper_2601_16791_gb300 import mx, workloads as W
@@ -539,7 +556,9 @@ def run_mx(args):
     sysm = mx.System(w, stream=st.cuda_stream)
     if args.tiling:
         mx.mx_set_tiling(sysm.h, *[int(v) for v in args.tiling.split(",")])
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB
+    if args.window is not None:
+        mx.mx_set_defer_window(sysm.h, args.window)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
         if world > 1:
@@ -552,25 +571,24 @@ def run_mx(args):
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    total_ms = 0.0
-    # all K steps in one call, through the production step graphs of mx_step
-    # (a step's two half kicks in one launch), with CUDA events only around
-    # each step; L2 flushed before every step outside the steps' spans; the
-    # second call brings deferred planetesimals up to date, inside the region
-    for n in (args.steps, 0):
-        _, _, tot = mx.mx_step_timed(sysm.h, n, flush, per_kernel=False)
-        total_ms += tot
+    # The timed region: K steps through the production step graphs, enqueued
+    # back to back, each preceded by an L2 flush, then the catch-up that
+    # brings every deferred planetesimal to the last step (side stream joined),
+    # as one span of device time; the K flushes are then timed alone and
+    # subtracted.
+    wall_ms, flush_ms = mx.mx_step_wall(sysm.h, args.steps, flush)
     torch.cuda.synchronize()
     dwin, dmax, _, _ = mx.mx_defer_stats(sysm.h)
     tiling = mx.mx_tiling(sysm.h)
     barrier()
     clk = clocks.stop()
-    t_max = reduce_max(total_ms, "cuda")
+    t_max = reduce_max(wall_ms - flush_ms, "cuda")
     value = whole_job_rate(w.n, args.steps, world, t_max * 1e-3)
     # the same K steps again (from where the region ended), through the step
-    # graphs' variants with an event between kernels: the per-kernel times and
-    # launch counts (event nodes add about 7% to a step, so this pass is not
-    # the value)
+    # graphs' variants with an event between kernels: each kernel's time and
+    # launch count, and the catch-ups' device-counted work (event nodes add
+    # about 7% to a step, so this pass is not the value)
+    mx.mx_catchup_work(sysm.h, reset=True)
     kms = {k: 0.0 for k in mx.KERNELS}
     kcnt = {k: 0 for k in mx.KERNELS}
     kernel_total_ms = 0.0
@@ -581,6 +599,7 @@ def run_mx(args):
             kcnt[k] += cnt[k]
         kernel_total_ms += tot
     torch.cuda.synchronize()
+    ops_main, ops_side = mx.mx_catchup_work(sysm.h)
 
     # end to end through the public API with host buffers: per step the state
     # goes host->device from pinned memory, one step runs, the state comes back
@@ -607,82 +626,61 @@ def run_mx(args):
         if world > 1:
             torch.distributed.destroy_process_group()
         return
+
+    def flops_of(k):
+        if k == "k_catchup":
+            return catchup_flops(w, ops_main)
+        if k == "k_catchup_side":
+            return catchup_flops(w, ops_side)
+        return kernel_flops(k, w, kcnt[k], args.steps)
+
     # dominant kernel on the step's critical path (the side-stream catch-up
     # overlaps the steps) and its roofline
     dom = max((k for k in kms if k != "k_catchup_side"), key=lambda k: kms[k])
-    flops = kernel_flops(dom, w, kcnt[dom], args.steps)
+    flops = flops_of(dom)
     avg_ms = kms[dom] / max(1, kcnt[dom])
-    achieved = (flops / kcnt[dom]) / (avg_ms * 1e-3) / 1e12 if flops else None
-    traffic = dram_traffic(dom)
+    achieved = (flops / max(1, kcnt[dom])) / (avg_ms * 1e-3) / 1e12 if flops and avg_ms > 0 else None
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "peak_source": "FP64 FMA-chain probe (mx_fp64_peak, all SMs) in this run",
-            "avg_launch_ms": avg_ms,
-            "share_of_step": kms[dom] / max(1e-12, kernel_total_ms),
-            "timing": ("the kernel's CUDA-event spans in a second pass of the same K steps through "
-                       "the step graphs' variants with an event between kernels")}
-    per_kernel = {}
+            "frac": (achieved / peak) if achieved else None, "traffic": dram_traffic(dom),
+            "peak_source": "measured FP64 FMA-chain peak (mx_fp64_peak, all SMs, this run)",
+            "avg_launch_ms": avg_ms, "share_of_step": kms[dom] / max(1e-12, kernel_total_ms)}
+    kern = {}
     for k in mx.KERNELS:
-        per_kernel[k] = {"ms_per_step": kms[k] / args.steps, "launches": kcnt[k]}
-        fk = kernel_flops(k, w, kcnt[k], args.steps)
+        if kcnt[k] == 0:
+            continue
+        row = [kms[k] / args.steps, kcnt[k]]
+        fk = flops_of(k)
         if fk and kms[k] > 0:
-            per_kernel[k]["tflops"] = fk / (kms[k] * 1e-3) / 1e12
-            per_kernel[k]["frac_of_peak"] = per_kernel[k]["tflops"] / peak
-    per_kernel["k_catchup_side"]["note"] = "side stream, overlaps the steps"
+            row.append(fk / (kms[k] * 1e-3) / 1e12 / peak)
+        kern[k] = row
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload,
-                       "description": WORKLOAD_TEXT if args.workload == WORKLOAD else args.workload,
-                       "n_bodies": w.n,
-                       "per_rank_seed": "1 + rank",
-                       "l2": "flushed before every timed step (256 MiB write, outside the step spans)",
-                       "path": ("mx_step_timed: all steps in one call through the production step "
-                                "graphs, CUDA events around each step; per-kernel times from a second "
-                                "pass of K steps with events between kernels"),
-                       "defer_window": dwin,
-                       "tiling": {"tile": tiling[0], "order": tiling[1],
-                                  "meaning": "order 2: tiles per SM (balanced); else targets per block"},
-                       "deferred": ("planetesimals whose encounter outlasts one Bulirsch-Stoer macro "
-                                    "sub-step are replayed by k_catchup at the end of each window of "
-                                    f"{dwin} steps; bodies still in a long encounter continue on a "
-                                    "side stream (k_catchup_side) while the next window runs; the "
-                                    "timed region ends with the last catch-up")},
-            "roofline": roof, "kernels": per_kernel, "clocks": clk,
+            "config": bench_config(w, args.workload),
+            "timing": {"wall_ms": wall_ms, "flush_ms": flush_ms, "defer_window": dwin,
+                       "tile": list(tiling)},
+            "roofline": roof, "clocks": clk,
+            "kernels": kern,
             "gpu_launches": int(sum(kcnt.values())),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 48 * w.n,
-                    "d2h_bytes_per_step": 48 * w.n, "steps": ne,
-                    "api": "mx_set_state + mx_step + mx_get_state (pinned host buffers)"}}
+                    "d2h_bytes_per_step": 48 * w.n, "steps": ne}}
     sysm.close()
     if not args.no_extra:
-        try:
-            line["batched"] = ensemble_leg(args.ensemble_steps)
-        except Exception as exc:  # reported, not hidden
-            line["batched"] = {"error": str(exc)[:300]}
-        try:
-            line["adjoint"] = adjoint_leg()
-        except Exception as exc:
-            line["adjoint"] = {"error": str(exc)[:300]}
-        try:
-            line["ejection"] = eject_leg()
-        except Exception as exc:
-            line["ejection"] = {"error": str(exc)[:300]}
-        try:
-            line["growth"] = growth_leg()
-        except Exception as exc:
-            line["growth"] = {"error": str(exc)[:300]}
-        try:
-            line["semiactive"] = semiactive_leg()
-        except Exception as exc:
-            line["semiactive"] = {"error": str(exc)[:300]}
+        for key, fn in (("batched", lambda: ensemble_leg(args.ensemble_steps)),
+                        ("adjoint", adjoint_leg), ("ejection", eject_leg),
+                        ("growth", growth_leg), ("semiactive", semiactive_leg)):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # reported, not hidden
+                line[key] = {"error": str(exc)[:120]}
     if not args.no_cpu_baseline:
         one, _, _ = oracle_rate(w, 3.0, threads=1)
         cb, _, _ = oracle_rate(w, 12.0)
-        cb["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+        cb["single_thread"] = one["value"]
         line["cpu_baseline"] = cb
     if world > 1:
         torch.distributed.destroy_process_group()
-    print(json.dumps(line), flush=True)
+    print(json.dumps(r4(line), separators=(",", ":")), flush=True)
 
 
 def main():

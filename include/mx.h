@@ -168,6 +168,17 @@ mx_status mx_set_tiling(mx_system* s, int tile, int order);
  * be NULL).
  */
 mx_status mx_set_defer_window(mx_system* s, int window);
+/* mx_catchup_work -- work the catch-ups have done since creation or the last
+ * reset, in units of fixed algorithmic cost (host ops6[6]): [0] body-slots
+ * replayed through jump, drift and the encounter test, [1] half kicks of one
+ * body, [2] force evaluations of two-body Bulirsch-Stoer groups as the
+ * one-try-at-a-time step search makes them (every row of each failed try,
+ * rows up to the accepted one of the accepted try); [0..2] by the main
+ * stream's catch-ups (MX_K_CATCHUP), [3..5] by the side stream's
+ * (MX_K_CATCHUP_SIDE).  Waits for the side stream's last pass.  Groups of
+ * three or more bodies are not counted.  reset != 0 zeroes the counters
+ * after reading. */
+mx_status mx_catchup_work(mx_system* s, long long* ops6, int reset);
 mx_status mx_defer_stats(mx_system* s, int* window, int* max_window, long long* deferred,
                          long long* catchups);
 
@@ -233,6 +244,22 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
 mx_status mx_step_timed(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
                         double* kernel_ms, int* launches, double* total_ms);
 
+/*
+ * mx_step_wall -- n_steps steps through the production CUDA graphs of
+ * mx_step, then the catch-up that brings every deferred planetesimal to the
+ * last step, all enqueued with no host wait in between; before every step the
+ * device buffer dev_flush (flush_bytes bytes, caller-owned; 0 = no flush) is
+ * overwritten on the system's stream.
+ *  wall_ms   device time from before the first flush to after the catch-up
+ *            (the side stream's work is joined into it), host, required
+ *  flush_ms  if not NULL: the same n_steps flushes enqueued alone after the
+ *            span, with nothing else in flight, timed the same way
+ * Anything pending from earlier calls is settled before the span starts.
+ * Synchronises before returning.  n_steps >= 1.
+ */
+mx_status mx_step_wall(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
+                       double* wall_ms, double* flush_ms);
+
 /* Encounter pairs found by the last step (sorted by (i, j), i big, body
  * indices), copied to host_pairs [2*cap]; *n_pairs gets the full count. */
 mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pairs);
@@ -286,11 +313,18 @@ mx_status mx_detect_encounters(mx_system* s, const double* dev_xv0, const double
  *  cuda_stream  stream to run on (NULL: legacy default stream).
  * The first call on a device, made with that device current, looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call shares the one array, which keeps the last
- * call's contents; the call clears what must start at zero.  Calls that
- * overlap on the GPU (other threads or streams) race on the array.
- * Errors: MX_ERR_ARG (including n above the limit), MX_ERR_CUDA,
- * MX_ERR_PAIR_OVERFLOW when more than cap or MX_NOALLOC_MAX_PAIRS pairs.
+ * any stream capture.  The address is kept for the life of the process: a
+ * cudaDeviceReset (or any reset of the device's primary context) unloads the
+ * array, and the kept address is then stale, so after such a reset this
+ * entry point must not be called again on that device in the same process.
+ * Every call shares the one array, which keeps the last call's contents; the
+ * call clears what must start at zero.  Calls that overlap on the GPU (other
+ * threads or streams) race on the array.
+ * Errors: MX_ERR_ARG (including n above the limit), MX_ERR_CUDA (also when a
+ * CUDA error was already pending at entry: it is left pending and nothing
+ * runs), MX_ERR_PAIR_OVERFLOW when more than cap or MX_NOALLOC_MAX_PAIRS
+ * pairs (n_pairs still receives the full count, and with at most
+ * MX_NOALLOC_MAX_PAIRS pairs the first cap of the sorted list are written).
  * Synchronises the stream before returning.
  */
 #define MX_NOALLOC_MAX_BODIES (1 << 21)

@@ -655,7 +655,8 @@ __device__ __forceinline__ int bs2_check(int K, int row, double sc, double tol2,
 // and warp before and after.
 template <int NCAND>
 __device__ int bs2_rounds(int cand, int lane, const Bs2Term& t, double tol, int max_sub,
-                          int max_rounds, GroupRun<2>& g, int* s_row, double* s_y) {
+                          int max_rounds, GroupRun<2>& g, int* s_row, double* s_y,
+                          unsigned long long* fevals = nullptr) {
   const int row = lane >> 2, q = lane & 3, ob = q & 1;
   const bool vel = q >= 2;
   const int n = 2 * (row + 1);
@@ -752,11 +753,16 @@ __device__ int bs2_rounds(int cand, int lane, const Bs2Term& t, double tol, int 
         __syncthreads();
       }
       g.nsub += acc_c + 1;                   // attempts a one-at-a-time search makes
+      // force evaluations of that search: every row of each failed try, rows
+      // 0..acc_r of the accepted one (row r: 2(r + 1) sub-steps + 1)
+      if (fevals && cand == 0 && lane == 0)
+        atomicAdd(fevals, (unsigned long long)(80 * acc_c + (acc_r + 1) * (acc_r + 3)));
       if (g.nsub > max_sub) return -1;
       const double Hacc = g.H * pow2_neg(acc_c);   // exact: a power of two
       g.rem -= Hacc;
       g.H = 1.3 * Hacc;
     } else {
+      if (fevals && cand == 0 && lane == 0) atomicAdd(fevals, (unsigned long long)(80 * NCAND));
       g.nsub += NCAND;
       g.H *= 1.0 / (double)(1 << NCAND);
     }
@@ -1115,6 +1121,7 @@ __device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, co
 
 struct CatchBlk {
   int lane, wq;
+  unsigned long long* ops;   // work counters of this pass (main or side stream)
   int* s_row;     // [4]
   double* s_y;    // [12]
   double* s_bc;   // [6] broadcast of a body state
@@ -1173,7 +1180,7 @@ __device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, int t,
     g.H = G.H;
     g.nsub = G.nsub;
     const int r = bs2_rounds<4>(B.wq, B.lane, t, d.bs_tol, d.bs_max_sub, max_rounds, g, B.s_row,
-                                B.s_y);
+                                B.s_y, B.ops + 2);
 #pragma unroll
     for (int m = 0; m < 2; ++m)
 #pragma unroll
@@ -1234,6 +1241,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
   const int lane = B.lane;
   const bool w0 = B.wq == 0;
   const size_t NBs = (size_t)d.NB;
+  if (w0 && lane == 0) atomicAdd(B.ops + 0, 1ull);
   double dj[3];
   jump_vec(d.h_P + (size_t)t * 6 * d.nsys + 3 * sys, S, 0.5, dj);
   double x = s6[0] + dj[0], y = s6[1] + dj[1], z = s6[2] + dj[2];
@@ -1358,7 +1366,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
 // Jump 2 and the half kick(s) that end step t, or (head) the leading half
 // kick of a call, which has no jump and keeps the positions as they are.
 __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t, bool lead,
-                           double* s6) {
+                           double* s6, unsigned long long* ops) {
   const double* P2 = d.h_P + (size_t)t * 6 * d.nsys + 3 * d.nsys + 3 * sys;
   const int hk = d.h_nkick[t];
   const bool head = hk < 0;
@@ -1393,6 +1401,7 @@ __device__ void catch_back(const Dev& d, const SysDev& S, int sys, int j, int t,
     }
   }
   const int nk = head ? -hk : hk;
+  if (lead) atomicAdd(ops + 1, (unsigned long long)nk);
   const double kick_h = 0.5 * S.h;
   const double hp0 = P2[0] * S.inv_mu0, hp1 = P2[1] * S.inv_mu0, hp2 = P2[2] * S.inv_mu0;
   const double rp = S.gas_on ? d.rp_cm[j] : 0.0, kd = S.gas_on ? d.kdrag[j] : 0.0;
@@ -1508,7 +1517,7 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
       }
       if (r < 0 && lead) atomicOr(d.status, ST_BS);
       G.nb = 0;
-      catch_back(d, S, sys, j, t, lead, s6);
+      catch_back(d, S, sys, j, t, lead, s6, B.ops);
       ejected = eject_after(t);
       ++t;
       if (ejected) break;
@@ -1524,7 +1533,7 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
       }
       if (nb >= 2) continue;   // the group runs at the top of the loop
     }
-    catch_back(d, S, sys, j, t, lead, s6);
+    catch_back(d, S, sys, j, t, lead, s6, B.ops);
     ejected = eject_after(t);
     ++t;
     if (ejected) break;
@@ -1579,7 +1588,8 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
 __global__ void __launch_bounds__(128) k_catchup(Dev d, CatchArgs a) {
   __shared__ int s_row[4], s_r;
   __shared__ double s_y[12], s_bc[6];
-  const CatchBlk B{(int)(threadIdx.x & 31), (int)(threadIdx.x >> 5), s_row, s_y, s_bc, &s_r};
+  const CatchBlk B{(int)(threadIdx.x & 31), (int)(threadIdx.x >> 5),
+                   d.work_ops + (a.mode == 1 ? 4 : 0), s_row, s_y, s_bc, &s_r};
   const int na = (a.bank_a >= 0) ? min(d.rcount[a.bank_a], d.dcap) : 0;
   const int nb = (a.bank_b >= 0) ? min(d.rcount[a.bank_b], d.dcap) : 0;
   if (a.next_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) d.hstep[0] = a.next_slot;

@@ -28,6 +28,12 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 constexpr int kNaMaxTiles = MX_NOALLOC_MAX_BODIES / mx::kThreads;
+// The key sort pads the keys up to the next power of two of the pair count;
+// with a power-of-two capacity the padding stays inside the key region.
+static_assert((MX_NOALLOC_MAX_PAIRS & (MX_NOALLOC_MAX_PAIRS - 1)) == 0,
+              "the pair capacity must be a power of two");
+static_assert(MX_NOALLOC_MAX_BODIES % mx::kThreads == 0,
+              "the body limit must be a whole number of tiles");
 
 // Byte offsets of the pieces inside the scratch array.
 constexpr size_t kOffKeys = 0;
@@ -69,6 +75,9 @@ extern "C" mx_status mx_detect_encounters_noalloc(const mx_params* p, int n_big,
       (cap > 0 && !dev_pairs) || n_big < 0 || n < n_big || n <= 0 || !std::isfinite(p->dt))
     return MX_ERR_ARG;
   if (n > MX_NOALLOC_MAX_BODIES) return MX_ERR_ARG;   // beyond the static scratch
+  // An error left pending by earlier work is the caller's: report it before
+  // launching anything, rather than as this call's launch failure.
+  if (cudaPeekAtLastError() != cudaSuccess) return MX_ERR_CUDA;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MX_ERR_CUDA;
   unsigned char* scratch = nullptr;
@@ -106,12 +115,19 @@ extern "C" mx_status mx_detect_encounters_noalloc(const mx_params* p, int n_big,
   int* count = reinterpret_cast<int*>(scratch + kOffCount);
   if (cudaMemsetAsync(dev_flags, 0, (size_t)n, st) != cudaSuccess) return MX_ERR_CUDA;
   k_noalloc_setup<<<32, 256, 0, st>>>(scratch, sys, n);
+  if (cudaGetLastError() != cudaSuccess) return MX_ERR_CUDA;
   mx::launch_detect(d, dev_xv0, dev_xv1, dev_flags, keys, count, MX_NOALLOC_MAX_PAIRS, 0, st);
+  if (cudaGetLastError() != cudaSuccess) return MX_ERR_CUDA;
   mx::launch_sort_keys(keys, count, MX_NOALLOC_MAX_PAIRS, 1, st);
-  if (cap > 0) mx::launch_keys_to_pairs(keys, count, cap < MX_NOALLOC_MAX_PAIRS ? cap : MX_NOALLOC_MAX_PAIRS, dev_pairs, st);
+  if (cudaGetLastError() != cudaSuccess) return MX_ERR_CUDA;
+  if (cap > 0) {
+    mx::launch_keys_to_pairs(keys, count, cap < MX_NOALLOC_MAX_PAIRS ? cap : MX_NOALLOC_MAX_PAIRS,
+                             dev_pairs, st);
+    if (cudaGetLastError() != cudaSuccess) return MX_ERR_CUDA;
+  }
   int found = 0;
   if (cudaMemcpyAsync(&found, count, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      cudaStreamSynchronize(st) != cudaSuccess)
     return MX_ERR_CUDA;
   *n_pairs = found;
   if (found > MX_NOALLOC_MAX_PAIRS || found > cap) return MX_ERR_PAIR_OVERFLOW;

@@ -586,6 +586,7 @@ mx_status trial_ms(mx_system* s, double* ms) {
   MX_CUDA(cudaMemsetAsync(s->d.ever, 0, s->N, s->st));
   MX_CUDA(cudaMemsetAsync(s->d.bb_count, 0, sizeof(unsigned long long), s->st));
   MX_CUDA(cudaMemsetAsync(s->d.defer_total, 0, sizeof(unsigned long long), s->st));
+  MX_CUDA(cudaMemsetAsync(s->d.work_ops, 0, 8 * sizeof(unsigned long long), s->st));
   MX_CUDA(cudaMemsetAsync(s->d.kick_ctr, 0, 2 * sizeof(int), s->st));
   MX_CUDA(cudaMemsetAsync(s->d.gstep, 0, sizeof(long long), s->st));
   MX_CUDA(cudaStreamSynchronize(s->st));
@@ -696,6 +697,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
     MX_TRY(dalloc(s, &d.hstep, 1));
     MX_TRY(dalloc(s, &d.rcount, 3));
     MX_TRY(dalloc(s, &d.defer_total, 1));
+    MX_TRY(dalloc(s, &d.work_ops, 8));
     MX_TRY(dalloc(s, &d.h_P, (size_t)hc * 6 * nsys));
     MX_TRY(dalloc(s, &d.h_b0, (size_t)hc * 6 * NB));
     MX_TRY(dalloc(s, &d.h_b1, (size_t)hc * 6 * NB));
@@ -763,6 +765,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemsetAsync(d.hstep, 0, sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.rcount, 0, 3 * sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.defer_total, 0, sizeof(unsigned long long), st));
+  MX_CUDA(cudaMemsetAsync(d.work_ops, 0, 8 * sizeof(unsigned long long), st));
   update_defer(s);
   // host staging: state rows, masses as mu = G m, per-body drag inputs
   std::vector<double> xv((size_t)6 * N), bmu(NB, 0.0), rpb(N, 1.0), rhob(N, 1.0);
@@ -987,6 +990,22 @@ mx_status mx_defer_stats(mx_system* s, int* window, int* max_window, long long* 
   if (max_window) *max_window = s->d.hist_cap / 2;
   if (deferred) *deferred = (long long)n;
   if (catchups) *catchups = s->catchups;
+  return MX_OK;
+}
+
+mx_status mx_catchup_work(mx_system* s, long long* ops6, int reset) {
+  if (!s || !ops6) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  unsigned long long w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // after the side stream's last pass, so its counts are complete
+  if (s->side_busy) MX_CUDA(cudaStreamWaitEvent(s->st, s->ev_side, 0));
+  MX_CUDA(cudaMemcpyAsync(w, s->d.work_ops, sizeof(w), cudaMemcpyDeviceToHost, s->st));
+  if (reset) MX_CUDA(cudaMemsetAsync(s->d.work_ops, 0, sizeof(w), s->st));
+  MX_CUDA(cudaStreamSynchronize(s->st));
+  for (int k = 0; k < 3; ++k) {
+    ops6[k] = (long long)w[k];
+    ops6[3 + k] = (long long)w[4 + k];
+  }
   return MX_OK;
 }
 
@@ -1300,6 +1319,57 @@ mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* la
 mx_status mx_step_timed(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
                         double* kernel_ms, int* launches, double* total_ms) {
   return timed_graph_run(s, n_steps, dev_flush, flush_bytes, kernel_ms, launches, total_ms);
+}
+
+mx_status mx_step_wall(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
+                       double* wall_ms, double* flush_ms) {
+  if (!s || n_steps < 1 || (flush_bytes > 0 && !dev_flush) || !wall_ms)
+    return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_TRY(ensure_graphs(s));
+  MX_TRY(settle(s));   // nothing pending from earlier calls enters the span
+  cudaStream_t st = s->st;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (auto& e : ev) MX_CUDA(cudaEventCreate(&e));
+  cudaError_t e = cudaEventRecord(ev[0], st);
+  for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+    const bool head = (k == 0) || split_after(s, s->step + k);
+    const bool test = eject_after(s, s->step + k + 1);
+    const bool split = split_after(s, s->step + k + 1);
+    if (flush_bytes > 0) e = cudaMemsetAsync(dev_flush, k & 0xff, flush_bytes, st);
+    if (e == cudaSuccess && head) {
+      e = cudaGraphLaunch(s->g_head, st);
+      if (e == cudaSuccess) e = slot_done(s, false, untimed);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch((k + 1 == n_steps || split) ? s->g_last : s->g_mid, st);
+    if (e == cudaSuccess && test) {
+      mx::launch_eject(s->d, 1, st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = slot_done(s, true, untimed);
+  }
+  // the settle waits for the side stream on the main stream, so the end event
+  // follows every catch-up of the steps
+  if (e == cudaSuccess) e = settle_with(s, untimed);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess && flush_ms) {   // the flushes alone, nothing else in flight
+    e = cudaEventRecord(ev[2], st);
+    for (int k = 0; k < n_steps && e == cudaSuccess && flush_bytes > 0; ++k)
+      e = cudaMemsetAsync(dev_flush, (k + 1) & 0xff, flush_bytes, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(flush_ms ? ev[3] : ev[1]);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  *wall_ms = ms;
+  if (e == cudaSuccess && flush_ms) {
+    e = cudaEventElapsedTime(&ms, ev[2], ev[3]);
+    *flush_ms = ms;
+  }
+  for (auto& q : ev) cudaEventDestroy(q);
+  if (e != cudaSuccess) return fail(MX_ERR_CUDA, std::string("wall step: ") + cudaGetErrorString(e));
+  s->step += n_steps;
+  return sync_status(s);
 }
 
 mx_status mx_last_encounters(mx_system* s, int* host_pairs, int cap, int* n_pairs) {

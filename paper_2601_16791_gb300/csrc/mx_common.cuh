@@ -149,6 +149,13 @@ struct Dev {
   int* hstep;          // [0] history slot of the current step
   int* rcount;         // [3] records in each bank
   unsigned long long* defer_total;  // bodies deferred since creation
+  // Work done by catch-ups, in units with a fixed algorithmic cost: [0]
+  // body-slots drifted (jump + drift + encounter test), [1] half kicks of
+  // one body, [2] force evaluations of two-body Bulirsch-Stoer groups that
+  // the one-at-a-time step search makes (rows of the accepted try and of
+  // every failed try before it); [0..2] main-stream passes, [4..6] the side
+  // stream's.
+  unsigned long long* work_ops;   // [8]
   double* h_P;         // [hist_cap][2][3 nsys] P of jump 1, P of jump 2 and the kicks
   double* h_b0;        // [hist_cap][6][NB] big bodies after jump 1 (pre-drift)
   double* h_b1;        // [hist_cap][6][NB] big bodies after the drift (detection endpoint)

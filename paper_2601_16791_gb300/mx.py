@@ -63,6 +63,8 @@ _SIGS = {
     "mx_step": (_I, [_P, _I]),
     "mx_step_profiled": (_I, [_P, _I, _P, _P, _P]),
     "mx_step_timed": (_I, [_P, _I, _P, ctypes.c_size_t, _P, _P, _P]),
+    "mx_step_wall": (_I, [_P, _I, _P, ctypes.c_size_t, _P, _P]),
+    "mx_catchup_work": (_I, [_P, _P, _I]),
     "mx_last_encounters": (_I, [_P, _P, _I, _P]),
     "mx_accel": (_I, [_P, _P]),
     "mx_gas_drag": (_I, [_P, _P]),
@@ -210,6 +212,26 @@ def mx_step_timed(sys, n_steps, dev_flush=None, per_kernel=True):
     if not per_kernel:
         return {}, {}, tot.value
     return dict(zip(KERNELS, ms.tolist())), dict(zip(KERNELS, cnt.tolist())), tot.value
+
+
+def mx_step_wall(sys, n_steps, dev_flush=None):
+    """n_steps production steps plus the settling catch-up, enqueued without
+    host waits, dev_flush overwritten before every step.  Returns (wall_ms,
+    flush_ms): the span from the first flush to the end of the catch-up, and
+    the same flushes timed alone afterwards."""
+    wall, fl = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    nbytes = 0 if dev_flush is None else dev_flush.numel() * dev_flush.element_size()
+    _check(load().mx_step_wall(sys, int(n_steps), _dptr(dev_flush), nbytes, ctypes.byref(wall),
+                               ctypes.byref(fl)), "mx_step_wall")
+    return wall.value, fl.value
+
+
+def mx_catchup_work(sys, reset=False):
+    """Catch-up work counters: ((body-slots, half kicks, two-body BS force
+    evaluations) of the main-stream catch-ups, the same of the side stream's)."""
+    ops = np.zeros(6, dtype=np.int64)
+    _check(load().mx_catchup_work(sys, _hptr(ops), 1 if reset else 0), "mx_catchup_work")
+    return tuple(int(v) for v in ops[:3]), tuple(int(v) for v in ops[3:])
 
 
 def mx_last_encounters(sys, cap=1 << 16):

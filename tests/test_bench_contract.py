@@ -1,5 +1,6 @@
 """bench.py's reference arm (the CPU oracle) on the host: one JSON line with
-the keys the benchmark contract names.  CPU only, a few seconds."""
+the keys the benchmark contract names.  CPU only; the sample is sized for a
+5-second budget, so the test takes a few seconds."""
 import json
 import os
 import subprocess
@@ -10,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "1"],
+                        "--steps", "1", "--warmup", "1", "--budget-s", "5"],
                        capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]

@@ -6,9 +6,11 @@ allocation's implicit device synchronisation is not acceptable; they cannot
 call cudaMalloc.  mx_detect_encounters_noalloc serves them from a fixed array
 in the library's static device memory.  This test calls it through the C ABI
 twice in a row, on two different step states, and checks each result against
-mx_detect_encounters (the allocating entry point) on the same inputs: the
-same sorted pair list and the same flags, except pairs within 1e-9 relative of
-the changeover threshold (the tolerance of the detection parity tests).
+mx_detect_encounters (the allocating entry point) and against the CPU
+oracle's detection on the same inputs: the same sorted pair list and the same
+flags, except pairs within 1e-9 relative of the changeover threshold (the
+tolerance of the detection parity tests).  It also checks the overflow
+contract (a cap below the pair count) and that a call takes no device memory.
 """
 import ctypes
 
@@ -47,7 +49,14 @@ def _dev(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def _noalloc(w, xv0, xv1, rc, cap):
+def _same_up_to_threshold(p, xv0, xv1, rc, got, ref):
+    A, B = set(map(tuple, got.tolist())), set(map(tuple, ref.tolist()))
+    for (i, j) in A ^ B:
+        assert _near(p, xv0, xv1, rc, i, j), (i, j)
+    return A, B
+
+
+def _noalloc_raw(w, xv0, xv1, rc, cap):
     L = mx.load()
     params = mx.make_params(w.params)
     d0, d1, drc = _dev(xv0), _dev(xv1), _dev(rc)
@@ -60,8 +69,13 @@ def _noalloc(w, xv0, xv1, rc, cap):
         ctypes.c_void_p(d0.data_ptr()), ctypes.c_void_p(d1.data_ptr()),
         ctypes.c_void_p(flags.data_ptr()), ctypes.c_void_p(pairs.data_ptr()), cap,
         ctypes.byref(n), ctypes.c_void_p(st))
+    return code, n.value, pairs.cpu().numpy(), flags.cpu().numpy()
+
+
+def _noalloc(w, xv0, xv1, rc, cap):
+    code, n, pairs, flags = _noalloc_raw(w, xv0, xv1, rc, cap)
     assert code == mx.MX_OK, mx.STATUS.get(code, code)
-    return pairs.cpu().numpy()[:2 * n.value].reshape(-1, 2), flags.cpu().numpy()
+    return pairs[:2 * n].reshape(-1, 2), flags
 
 
 def _allocating(w, xv0, xv1, cap):
@@ -81,12 +95,54 @@ def test_noalloc_detection_matches_allocating_entry_point_twice():
         got, fg = _noalloc(w, xv0, xv1, rc, cap)
         ref, fr = _allocating(w, xv0, xv1, cap)
         assert len(ref) > 5
-        A, B = set(map(tuple, got.tolist())), set(map(tuple, ref.tolist()))
-        for (i, j) in A ^ B:
-            assert _near(p, xv0, xv1, rc, i, j), (i, j)
+        A, B = _same_up_to_threshold(p, xv0, xv1, rc, got, ref)
         assert np.array_equal(got, np.array(sorted(A)).reshape(-1, 2))
         if A == B:
             assert np.array_equal(fg, fr)
+        # and against the oracle's detection (the definition, on the CPU)
+        fo, po = orc.detect(p, w.nbig, xv0, xv1, rc)
+        A, C = _same_up_to_threshold(p, xv0, xv1, rc, got, po)
+        if A == C:
+            assert np.array_equal(fg, fo)
+
+
+def test_noalloc_overflow_returns_the_full_count_and_the_first_pairs():
+    w = W.semiactive_2000big_200k(nbig=400, nsmall=5000)
+    p, xv0, xv1, rc = _inputs(w)
+    full, _ = _noalloc(w, xv0, xv1, rc, 1 << 14)
+    assert len(full) > 3
+    cap = 2
+    code, n, pairs, _ = _noalloc_raw(w, xv0, xv1, rc, cap)
+    assert code == 6, mx.STATUS.get(code, code)    # MX_ERR_PAIR_OVERFLOW
+    assert n == len(full)
+    assert np.array_equal(pairs[:2 * cap].reshape(-1, 2), full[:cap])
+
+
+def test_noalloc_takes_no_device_memory():
+    w = W.plain_2big_1k()
+    p, xv0, xv1, rc = _inputs(w)
+    _noalloc(w, xv0, xv1, rc, 1 << 10)          # first call: address look-up
+    torch.cuda.synchronize()
+    # inputs and outputs allocated up front; the call itself must not move
+    # the device's free memory
+    L = mx.load()
+    params = mx.make_params(w.params)
+    d0, d1, drc = _dev(xv0), _dev(xv1), _dev(rc)
+    flags = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    pairs = torch.zeros(2 << 10, dtype=torch.int32, device="cuda")
+    n = ctypes.c_int(0)
+    st = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        code = L.mx_detect_encounters_noalloc(
+            ctypes.byref(params), w.nbig, w.n, ctypes.c_void_p(drc.data_ptr()),
+            ctypes.c_void_p(d0.data_ptr()), ctypes.c_void_p(d1.data_ptr()),
+            ctypes.c_void_p(flags.data_ptr()), ctypes.c_void_p(pairs.data_ptr()), 1 << 10,
+            ctypes.byref(n), ctypes.c_void_p(st))
+        assert code == mx.MX_OK
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
