@@ -161,7 +161,7 @@ mx_status mx_set_tiling(mx_system* s, int tile, int order);
  *
  * mx_set_defer_window: window = 0 keeps every body on the direct path;
  * 1 <= window <= the history length (*max_window of mx_defer_stats, at most
- * 64) sets the slots per catch-up.  Default: min(32, history length).
+ * 64) sets the slots per catch-up.  Default: min(10, history length).
  * MX_ERR_ARG for a window outside that range.
  * mx_defer_stats: window in effect (0 when off), history length, bodies
  * deferred since creation, catch-up launches made (host pointers, each may

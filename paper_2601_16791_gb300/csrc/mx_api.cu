@@ -326,13 +326,29 @@ cudaError_t window_end(mx_system* s, Timed&& timed) {
   const int next = (s->wbase == 0) ? s->window : 0;
   const int tl = (s->last_full >= s->wbase && s->last_full < t_end) ? s->last_full : -1;
   cudaError_t e = cudaSuccess;
-  if (s->side_busy) e = cudaStreamWaitEvent(s->st, s->ev_side, 0);
-  if (e == cudaSuccess)
+  if (s->side_busy) {
+    // Bodies deferred in this window (bank 0) do not depend on the side
+    // stream's pass (it works on the other carried bank and on the other half
+    // of the history ring), so they are replayed before the main stream waits
+    // for it; the carried bank follows once the side pass is done.
+    e = timed(MX_K_CATCHUP, s->st, [&] {
+      mx::launch_catchup(s->d, s->catch_blocks, 0, 0, -1, out, t_end, tl, next, next, s->st);
+    });
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->st, s->ev_side, 0);
+    if (e == cudaSuccess)
+      e = timed(MX_K_CATCHUP, s->st, [&] {
+        mx::launch_catchup(s->d, s->catch_blocks, 0, s->carried, -1, out, t_end, tl, next, next,
+                           s->st);
+        cudaMemsetAsync(s->d.rcount + s->carried, 0, sizeof(int), s->st);
+        cudaMemsetAsync(s->d.rcount, 0, sizeof(int), s->st);
+      });
+  } else {
     e = timed(MX_K_CATCHUP, s->st, [&] {
       mx::launch_catchup(s->d, s->catch_blocks, 0, s->carried, 0, out, t_end, tl, next, next, s->st);
       cudaMemsetAsync(s->d.rcount + s->carried, 0, sizeof(int), s->st);
       cudaMemsetAsync(s->d.rcount, 0, sizeof(int), s->st);
     });
+  }
   if (e == cudaSuccess) e = cudaEventRecord(s->ev_main, s->st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side_st, s->ev_main, 0);
   if (e == cudaSuccess)
@@ -371,13 +387,27 @@ template <class Timed>
 cudaError_t settle_with(mx_system* s, Timed&& timed) {
   if (!s->d.defer || (s->pending == 0 && !s->side_busy)) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  if (s->side_busy) e = cudaStreamWaitEvent(s->st, s->ev_side, 0);
-  if (e == cudaSuccess)
+  const int t_end = s->wbase + s->pending;
+  if (s->side_busy) {
+    // as at a window's end: the bodies deferred in this window first, while
+    // the side stream may still run; then, after it, the carried bank
     e = timed(MX_K_CATCHUP, s->st, [&] {
-      mx::launch_catchup(s->d, s->catch_blocks, 2, s->carried, 0, -1, s->wbase + s->pending,
-                         s->last_full, 0, 0, s->st);
+      mx::launch_catchup(s->d, s->catch_blocks, 2, 0, -1, -1, t_end, s->last_full, 0, 0, s->st);
+    });
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->st, s->ev_side, 0);
+    if (e == cudaSuccess)
+      e = timed(MX_K_CATCHUP, s->st, [&] {
+        mx::launch_catchup(s->d, s->catch_blocks, 2, s->carried, -1, -1, t_end, s->last_full, 0, 0,
+                           s->st);
+        cudaMemsetAsync(s->d.rcount, 0, 3 * sizeof(int), s->st);
+      });
+  } else {
+    e = timed(MX_K_CATCHUP, s->st, [&] {
+      mx::launch_catchup(s->d, s->catch_blocks, 2, s->carried, 0, -1, t_end, s->last_full, 0, 0,
+                         s->st);
       cudaMemsetAsync(s->d.rcount, 0, 3 * sizeof(int), s->st);
     });
+  }
   s->side_busy = false;
   s->pending = 0;
   s->wbase = 0;
@@ -427,7 +457,7 @@ mx_status ensure_timed_graphs(mx_system* s) {
 
 constexpr int kMinTile = 64;
 constexpr int kMaxWindow = 64;       // steps of big-body history kept for deferred planetesimals
-constexpr int kDefaultWindow = 32;
+constexpr int kDefaultWindow = 10;
 constexpr size_t kHistBudget = 256ull << 20;   // bytes the history may take
 
 // Tiles of `tile` targets per system; order 1 puts the costliest first (work

@@ -206,9 +206,14 @@ def test_gas_steps():
 
 
 def test_semiactive_steps_with_big_encounters():
+    """300 embryos + 3,000 planetesimals, 200 steps, big-big encounters on
+    the way: bodies never flagged agree to 1e-9 (the oracle's own spread under
+    a 1e-13 perturbation of the embryos' velocities is ~1e-11 at this length),
+    and so does every other body but the few in the deepest encounters."""
     w = W.semiactive_2000big_200k(nbig=300, nsmall=3000)
-    err, keep, st = _compare_run(w, 60, tol=1e-8)
+    err, keep, st = _compare_run(w, 200, tol=1e-9)
     assert st[0] > 0 and st[1] > 0
+    assert np.percentile(err[~keep], 90) <= 1e-9
 
 
 def test_full_size_sampled_gas_workload():
