@@ -324,8 +324,9 @@ def whole_job_rate(bodies_per_rank, steps, world, t_max_s):
 # ------------------------------------------------- ensemble and adjoint legs
 def ensemble_leg(steps, nsys=256):
     """256 systems (2-50 embryos, 1e3-2e5 planetesimals each, gas with Sigma
-    x U[0.3, 3]): one batched mx_system vs a host loop calling mx_step on one
-    mx_system per system.  Both advance every system by `steps` steps."""
+    x U[0.3, 3]): one batched mx_system (per-kernel step graphs, then one
+    persistent launch per interior step) vs a host loop calling mx_step on
+    one mx_system per system.  Each advances every system by `steps` steps."""
     import torch
     from paper_2601_16791_gb300 import mx, workloads as W
     ws = W.ensemble_256(nsys=nsys)
@@ -339,6 +340,14 @@ def ensemble_leg(steps, nsys=256):
     b.step(steps)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
+    # the same steps with every interior step as one persistent launch
+    mx.mx_set_persistent(b.h, True)
+    b.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    torch.cuda.synchronize()
+    t_persist = time.perf_counter() - t0
     b.close()
     systems = [mx.System(w, stream=st.cuda_stream) for w in ws]
     for s in systems:
@@ -354,7 +363,9 @@ def ensemble_leg(steps, nsys=256):
         s.close()
     return {"n_systems": nsys, "n_bodies": n_tot, "steps": steps,
             "batched_value": n_tot * steps / t_batch, "loop_value": n_tot * steps / t_loop,
-            "speedup": t_loop / t_batch, "tile": [tile, order]}
+            "persistent_value": n_tot * steps / t_persist,
+            "speedup": t_loop / t_batch, "speedup_persistent": t_loop / t_persist,
+            "tile": [tile, order]}
 
 
 def adjoint_leg(nsteps=200, every=50):

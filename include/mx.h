@@ -168,6 +168,27 @@ mx_status mx_set_tiling(mx_system* s, int tile, int order);
  * be NULL).
  */
 mx_status mx_set_defer_window(mx_system* s, int window);
+/*
+ * mx_set_persistent -- run each interior step of mx_step (every step of a
+ * call but its last; the leading half kick stays a launch of its own) as ONE
+ * cooperative launch over all systems of the handle, captured in the step's
+ * CUDA graph: the phases of the step (jump and drift, detection, groups,
+ * Bulirsch-Stoer of every group, the kick with its own momentum) run in
+ * turn, separated by grid barriers, on the same device functions and tiles
+ * as the per-kernel step, so the state is the same bit for bit (spec:
+ * the batched ensemble advances in one persistent launch per step; the
+ * paper has no counterpart).  Applies to forward runs with deferral on and
+ * no growth tracks, ejection schedule or recorded k branches; other steps
+ * keep the per-kernel graphs.  on = 1 switches the tiling to 256 targets per
+ * block if it was smaller (results do not depend on the tiling).
+ *  spin_limit  polls a grid barrier waits for the other blocks before it
+ *              gives up (< 0: the default, 2^24, about two seconds); a step
+ *              whose barrier gave up returns MX_ERR_BARRIER_TIMEOUT (the
+ *              launch still ends; the state is then that of a partial step).
+ * Errors: MX_ERR_ARG, MX_ERR_CUDA (no resident grid).  Settles first.
+ */
+mx_status mx_set_persistent(mx_system* s, int on, long long spin_limit);
+
 /* mx_catchup_work -- work the catch-ups have done since creation or the last
  * reset, in units of fixed algorithmic cost (host ops6[6]): [0] body-slots
  * replayed through jump, drift and the encounter test, [1] half kicks of one

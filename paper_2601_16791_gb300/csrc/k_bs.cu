@@ -27,6 +27,9 @@
 #include "mx_kepler.cuh"
 #include "mx_kernels.h"
 #include "mx_bs.cuh"
+#include "mx_detect_body.cuh"
+#include "mx_drift_body.cuh"
+#include "mx_kick_body.cuh"
 #include "mx_orbit.cuh"
 #include "mx_physics.cuh"
 
@@ -134,7 +137,11 @@ __device__ int run_members(const unsigned long long* keys, int p, int n, const i
 
 constexpr int kGroupKeysSmem = 2048;   // 16 KB of static shared memory
 
-__global__ void __launch_bounds__(1024) k_groups(Dev d) {
+// The encounter groups of the step from its pair keys, in one block of any
+// size (a multiple of 32, at most 1024): big groups by union-find over the
+// big-big pairs, then one test-particle group per run of keys with the same
+// planetesimal, in key order.
+__device__ __forceinline__ void groups_block(const Dev& d) {
   __shared__ int nodes[2 * kMaxBigPairs];
   __shared__ int parent[2 * kMaxBigPairs];
   __shared__ int comp_of[2 * kMaxBigPairs];
@@ -305,6 +312,8 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) {
     }
   }
 }
+
+__global__ void __launch_bounds__(1024) k_groups(Dev d) { groups_block(d); }
 
 // ------------------------------------------------- warp-cooperative groups
 // Groups of up to kLaneMaxNB bodies run on lanes: lane 8c + r of a group
@@ -886,10 +895,10 @@ __global__ void __launch_bounds__(32) k_bs_pack2(Dev d) {
 // Every group, one per warp, in one launch: two bodies on term lanes, three
 // or four on the lane integrator (eight lanes), more on one thread.  Used
 // with deferral on, where nothing is handed to a spread phase.
-__global__ void __launch_bounds__(32) k_bs_all(Dev d) {
+__device__ __forceinline__ void bs_all_warps(const Dev& d, int w0, int nw) {
   const int W = *d.work_count;
-  const int lane = threadIdx.x;
-  for (int w = blockIdx.x; w < W; w += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int w = w0; w < W; w += nw) {
     const int nb = d.work_off[w + 1] - d.work_off[w];
     if (nb == 2) pack_two(d, w, lane);
     else if (nb == 3) { if (lane < 8) pack_group<3>(d, w, 0xffu, 0, lane); }
@@ -898,6 +907,8 @@ __global__ void __launch_bounds__(32) k_bs_all(Dev d) {
     __syncwarp();
   }
 }
+
+__global__ void __launch_bounds__(32) k_bs_all(Dev d) { bs_all_warps(d, blockIdx.x, gridDim.x); }
 
 __device__ void pack_two(const Dev& d, int w, int lane) {
   const int o0 = d.work_off[w];
@@ -1600,6 +1611,117 @@ __global__ void __launch_bounds__(128) k_catchup(Dev d, CatchArgs a) {
   }
 }
 
+// ------------------------------------------------------ the persistent step
+// One interior step of every system of a batch as one cooperative launch
+// (all blocks resident): the phases of the per-kernel step -- jump and drift,
+// detection, groups, Bulirsch-Stoer of every group, the kick with its own
+// prep -- run the same device functions on the same tiles, separated by grid
+// barriers, so the result is the per-kernel step's, bit for bit.  Blocks take
+// tiles in turn (block b: tiles b, b + G, ...; the tiles are in the tiling's
+// order, costliest first when the autotuner picked that), warps take groups
+// in turn, and block 0 builds the groups.
+//
+// A barrier waits at most `spin` polls of its generation word; a block that
+// gives up sets ST_BARRIER and the abort flag, and every block leaves at the
+// next barrier it reaches (a wait never outlasts its limit, so the launch
+// ends whatever happens).  Returns false to every thread once that happened.
+__device__ bool grid_sync(unsigned* bar, long long spin, unsigned* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vb = bar;
+    int ok = vb[2] == 0;
+    if (ok) {
+      const unsigned gen = vb[1];
+      __threadfence();
+      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        vb[0] = 0;   // every block has arrived: ready for the next barrier
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        long long k = 0;
+        while (vb[1] == gen) {
+          if (vb[2] != 0) {
+            ok = 0;
+            break;
+          }
+          if (++k > spin) {
+            atomicOr(status, ST_BARRIER);
+            atomicExch(bar + 2, 1u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Dynamic shared memory: the larger of detection's and the fused kick's.
+__global__ void __launch_bounds__(kThreads, 2) k_step_persist(Dev d, long long spin) {
+  extern __shared__ __align__(16) unsigned char dsm_p[];
+  const int G = gridDim.x;
+  for (int t = blockIdx.x; t < d.ntiles; t += G) jump_drift_tile(d, 0.5, t);
+  if (!grid_sync(d.gbar, spin, d.status)) return;
+  for (int t = blockIdx.x; t < d.ntiles; t += G) {
+    __syncthreads();   // the last tile's staged bodies are no longer read
+    detect_tile(d, d.xv0, d.xv, d.flags, d.keys, d.pair_count, d.pair_cap, 1, t, dsm_p);
+  }
+  if (!grid_sync(d.gbar, spin, d.status)) return;
+  if (blockIdx.x == 0) groups_block(d);
+  if (!grid_sync(d.gbar, spin, d.status)) return;
+  const int wpb = blockDim.x >> 5;
+  bs_all_warps(d, blockIdx.x * wpb + (threadIdx.x >> 5), G * wpb);
+  __syncwarp();
+  if (!grid_sync(d.gbar, spin, d.status)) return;
+  for (int t = blockIdx.x; t < d.ntiles; t += G) {
+    // the momentum tree of a system with more than 32 big bodies shares the
+    // staging space: no thread may still read the last tile's staged bodies
+    __syncthreads();
+    jump_kick_tile<2, true>(d, 0.5, 0.5, t, reinterpret_cast<double*>(dsm_p));
+  }
+}
+
+static size_t persist_smem_bytes(const Dev& d) {
+  const size_t a = det_smem_bytes(det_chunk(d.tile, d.big_max));
+  const size_t b = kick_smem_bytes(d, true);
+  return a > b ? a : b;
+}
+
+int persist_grid(const Dev& d) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaFuncSetAttribute(k_step_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)persist_smem_bytes(d)) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persist, d.tile,
+                                                    persist_smem_bytes(d)) != cudaSuccess)
+    return 0;
+  const int g = per_sm * sms;
+  return g < d.ntiles ? g : d.ntiles;
+}
+
+cudaError_t launch_step_persist(const Dev& d, int grid, long long spin, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d.gbar, 0, 4 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(d.tile);
+  cfg.dynamicSmemBytes = persist_smem_bytes(d);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_step_persist, d, spin);
+}
+
 void launch_groups(const Dev& d, cudaStream_t st) { k_groups<<<1, 1024, 0, st>>>(d); }
 
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
@@ -1635,6 +1757,7 @@ void configure_bs() {
   cudaFuncSetAttribute(k_bs_spread2, cudaFuncAttributePreferredSharedMemoryCarveout, c);
   cudaFuncSetAttribute(k_bs_spread<3, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
   cudaFuncSetAttribute(k_catchup, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+  cudaFuncSetAttribute(k_step_persist, cudaFuncAttributePreferredSharedMemoryCarveout, c);
 }
 
 }  // namespace mx

@@ -182,6 +182,9 @@ struct mx_system {
     cudaEvent_t a, b;
   };
   std::vector<Span> side_spans;
+  int persist = 0;                // interior steps as one cooperative launch (k_step_persist)
+  long long persist_spin = 1ll << 24;   // polls a grid barrier waits before it gives up
+  int persist_grid = 0;           // blocks of that launch (all resident)
   int tile = mx::kThreads;        // targets per tile (autotuned)
   int order = 0;                  // 0: tiles in system order; 1: costliest first
   int tiles_cap = 0;
@@ -264,7 +267,17 @@ void enqueue_head(mx_system* s, cudaStream_t st, cudaEvent_t* marks) {
 // branches recorded or replayed (the kick counter k_prep advances).
 bool fuse_prep(const mx_system* s) { return s->d.kmode == 0 && !s->grow_any; }
 
+// The persistent form of an interior step (mx_set_persistent): with deferral
+// on, in forward runs whose interior kick makes its own prep.
+bool persist_step(const mx_system* s, int last) {
+  return s->persist && !last && fuse_prep(s) && s->d.defer && s->persist_grid > 0;
+}
+
 void enqueue_step(mx_system* s, int last, cudaStream_t st, cudaEvent_t* marks) {
+  if (!marks && persist_step(s, last)) {
+    mx::launch_step_persist(s->d, s->persist_grid, s->persist_spin, st);
+    return;
+  }
   int m = 0;
   auto mark = [&] {
     if (marks) mark_event(marks[m++], st);
@@ -505,6 +518,7 @@ mx_status set_tiling(mx_system* s, int tile, int order) {
   s->order = order;
   s->d.tile = tile;
   s->d.ntiles = (int)tiles.size();
+  if (s->persist) s->persist_grid = mx::persist_grid(s->d);
   drop_graphs(s);
   return MX_OK;
 }
@@ -743,6 +757,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
     s->window = std::min(kDefaultWindow, hc / 2);
   }
   MX_TRY(dalloc(s, &d.status, 1));
+  MX_TRY(dalloc(s, &d.gbar, 4));
   MX_TRY(dalloc(s, &d.stat, N));
   MX_TRY(dalloc(s, &s->d_grow, NB));
   MX_TRY(dalloc(s, &d.gap_r, NB));
@@ -777,6 +792,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemcpyAsync(s->d_tiles, tiles.data(), tiles.size() * sizeof(mx::Tile),
                           cudaMemcpyHostToDevice, st));
   MX_CUDA(cudaMemsetAsync(d.status, 0, sizeof(unsigned), st));
+  MX_CUDA(cudaMemsetAsync(d.gbar, 0, 4 * sizeof(unsigned), st));
   MX_CUDA(cudaMemsetAsync(d.pair_count, 0, 2 * sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.flags, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.stat, 0, N, st));
@@ -1020,6 +1036,22 @@ mx_status mx_defer_stats(mx_system* s, int* window, int* max_window, long long* 
   if (max_window) *max_window = s->d.hist_cap / 2;
   if (deferred) *deferred = (long long)n;
   if (catchups) *catchups = s->catchups;
+  return MX_OK;
+}
+
+mx_status mx_set_persistent(mx_system* s, int on, long long spin_limit) {
+  if (!s || on < 0 || on > 1) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  MX_TRY(settle(s));
+  if (on && s->tile < mx::kThreads) MX_TRY(set_tiling(s, mx::kThreads, s->order));
+  s->persist = on;
+  s->persist_spin = spin_limit < 0 ? (1ll << 24) : spin_limit;
+  s->persist_grid = on ? mx::persist_grid(s->d) : 0;
+  if (on && s->persist_grid <= 0) {
+    s->persist = 0;
+    return fail(MX_ERR_CUDA, "no resident grid for the persistent step");
+  }
+  drop_graphs(s);
   return MX_OK;
 }
 

@@ -156,6 +156,9 @@ struct Dev {
   // every failed try before it); [0..2] main-stream passes, [4..6] the side
   // stream's.
   unsigned long long* work_ops;   // [8]
+  // Grid barrier of the persistent step (k_step_persist): arrivals, the
+  // barrier's generation, and a flag set once any block gave up waiting.
+  unsigned* gbar;                   // [4]
   double* h_P;         // [hist_cap][2][3 nsys] P of jump 1, P of jump 2 and the kicks
   double* h_b0;        // [hist_cap][6][NB] big bodies after jump 1 (pre-drift)
   double* h_b1;        // [hist_cap][6][NB] big bodies after the drift (detection endpoint)

@@ -45,6 +45,12 @@ void launch_keys_to_pairs(const unsigned long long* keys, const int* count, int 
 // k_bs.cu
 void launch_groups(const Dev& d, cudaStream_t st);
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st);
+// The persistent interior step (one cooperative launch, grid barriers with
+// at most `spin` polls each): its largest resident grid for the current
+// tiling (0 if the occupancy query failed), and the launch (barrier words
+// zeroed first).
+int persist_grid(const Dev& d);
+cudaError_t launch_step_persist(const Dev& d, int grid, long long spin, cudaStream_t st);
 // mode 0: window end (budgeted, carried bodies to bank_out); 1: side stream
 // (bank_a in place); 2: settle (everything rejoins).  Slots up to t_end; a
 // body kept at t_end is stored at slot t_next (the next range's start).

@@ -65,6 +65,7 @@ _SIGS = {
     "mx_step_timed": (_I, [_P, _I, _P, ctypes.c_size_t, _P, _P, _P]),
     "mx_step_wall": (_I, [_P, _I, _P, ctypes.c_size_t, _P, _P]),
     "mx_catchup_work": (_I, [_P, _P, _I]),
+    "mx_set_persistent": (_I, [_P, _I, ctypes.c_longlong]),
     "mx_last_encounters": (_I, [_P, _P, _I, _P]),
     "mx_accel": (_I, [_P, _P]),
     "mx_gas_drag": (_I, [_P, _P]),
@@ -224,6 +225,12 @@ def mx_step_wall(sys, n_steps, dev_flush=None):
     _check(load().mx_step_wall(sys, int(n_steps), _dptr(dev_flush), nbytes, ctypes.byref(wall),
                                ctypes.byref(fl)), "mx_step_wall")
     return wall.value, fl.value
+
+
+def mx_set_persistent(sys, on=True, spin_limit=-1):
+    """Interior steps as one cooperative launch per step (grid barriers
+    between the phases); spin_limit < 0 keeps the default barrier patience."""
+    _check(load().mx_set_persistent(sys, 1 if on else 0, int(spin_limit)), "mx_set_persistent")
 
 
 def mx_catchup_work(sys, reset=False):
