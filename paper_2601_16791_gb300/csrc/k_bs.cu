@@ -1616,10 +1616,9 @@ __global__ void __launch_bounds__(128) k_catchup(Dev d, CatchArgs a) {
 // (all blocks resident): the phases of the per-kernel step -- jump and drift,
 // detection, groups, Bulirsch-Stoer of every group, the kick with its own
 // prep -- run the same device functions on the same tiles, separated by grid
-// barriers, so the result is the per-kernel step's, bit for bit.  Blocks take
-// tiles in turn (block b: tiles b, b + G, ...; the tiles are in the tiling's
-// order, costliest first when the autotuner picked that), warps take groups
-// in turn, and block 0 builds the groups.
+// barriers, so the result is the per-kernel step's, bit for bit.  Blocks
+// claim tiles from a counter per phase, warps take groups in turn, and block
+// 0 builds the groups.
 //
 // A barrier waits at most `spin` polls of its generation word; a block that
 // gives up sets ST_BARRIER and the abort flag, and every block leaves at the
@@ -1662,29 +1661,36 @@ __device__ bool grid_sync(unsigned* bar, long long spin, unsigned* status) {
   return s_ok != 0;
 }
 
+// The next tile of a phase for this block, claimed from the phase's counter
+// (tiles come in the tiling's order, costliest first when the autotuner
+// picked that, and each block takes the next one when it is free).  The
+// barrier also ends every read of the last tile's shared staging (a fused
+// kick's momentum tree shares that space).
+__device__ __forceinline__ int next_tile(unsigned* ctr) {
+  __shared__ int s_t;
+  __syncthreads();
+  if (threadIdx.x == 0) s_t = (int)atomicAdd(ctr, 1u);
+  __syncthreads();
+  return s_t;
+}
+
 // Dynamic shared memory: the larger of detection's and the fused kick's.
-__global__ void __launch_bounds__(kThreads, 2) k_step_persist(Dev d, long long spin) {
+__global__ void __launch_bounds__(kThreads, 3) k_step_persist(Dev d, long long spin) {
   extern __shared__ __align__(16) unsigned char dsm_p[];
-  const int G = gridDim.x;
-  for (int t = blockIdx.x; t < d.ntiles; t += G) jump_drift_tile(d, 0.5, t);
+  unsigned* ctr = d.gbar + 4;   // tile counters of the three per-body phases
+  for (int t = next_tile(ctr); t < d.ntiles; t = next_tile(ctr)) jump_drift_tile(d, 0.5, t);
   if (!grid_sync(d.gbar, spin, d.status)) return;
-  for (int t = blockIdx.x; t < d.ntiles; t += G) {
-    __syncthreads();   // the last tile's staged bodies are no longer read
+  for (int t = next_tile(ctr + 1); t < d.ntiles; t = next_tile(ctr + 1))
     detect_tile(d, d.xv0, d.xv, d.flags, d.keys, d.pair_count, d.pair_cap, 1, t, dsm_p);
-  }
   if (!grid_sync(d.gbar, spin, d.status)) return;
   if (blockIdx.x == 0) groups_block(d);
   if (!grid_sync(d.gbar, spin, d.status)) return;
   const int wpb = blockDim.x >> 5;
-  bs_all_warps(d, blockIdx.x * wpb + (threadIdx.x >> 5), G * wpb);
+  bs_all_warps(d, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb);
   __syncwarp();
   if (!grid_sync(d.gbar, spin, d.status)) return;
-  for (int t = blockIdx.x; t < d.ntiles; t += G) {
-    // the momentum tree of a system with more than 32 big bodies shares the
-    // staging space: no thread may still read the last tile's staged bodies
-    __syncthreads();
+  for (int t = next_tile(ctr + 2); t < d.ntiles; t = next_tile(ctr + 2))
     jump_kick_tile<2, true>(d, 0.5, 0.5, t, reinterpret_cast<double*>(dsm_p));
-  }
 }
 
 static size_t persist_smem_bytes(const Dev& d) {
@@ -1707,7 +1713,7 @@ int persist_grid(const Dev& d) {
 }
 
 cudaError_t launch_step_persist(const Dev& d, int grid, long long spin, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(d.gbar, 0, 4 * sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(d.gbar, 0, 8 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);

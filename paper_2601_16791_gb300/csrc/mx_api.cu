@@ -757,7 +757,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
     s->window = std::min(kDefaultWindow, hc / 2);
   }
   MX_TRY(dalloc(s, &d.status, 1));
-  MX_TRY(dalloc(s, &d.gbar, 4));
+  MX_TRY(dalloc(s, &d.gbar, 8));
   MX_TRY(dalloc(s, &d.stat, N));
   MX_TRY(dalloc(s, &s->d_grow, NB));
   MX_TRY(dalloc(s, &d.gap_r, NB));
@@ -792,7 +792,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_CUDA(cudaMemcpyAsync(s->d_tiles, tiles.data(), tiles.size() * sizeof(mx::Tile),
                           cudaMemcpyHostToDevice, st));
   MX_CUDA(cudaMemsetAsync(d.status, 0, sizeof(unsigned), st));
-  MX_CUDA(cudaMemsetAsync(d.gbar, 0, 4 * sizeof(unsigned), st));
+  MX_CUDA(cudaMemsetAsync(d.gbar, 0, 8 * sizeof(unsigned), st));
   MX_CUDA(cudaMemsetAsync(d.pair_count, 0, 2 * sizeof(int), st));
   MX_CUDA(cudaMemsetAsync(d.flags, 0, N, st));
   MX_CUDA(cudaMemsetAsync(d.stat, 0, N, st));

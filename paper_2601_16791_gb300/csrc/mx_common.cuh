@@ -157,8 +157,9 @@ struct Dev {
   // stream's.
   unsigned long long* work_ops;   // [8]
   // Grid barrier of the persistent step (k_step_persist): arrivals, the
-  // barrier's generation, and a flag set once any block gave up waiting.
-  unsigned* gbar;                   // [4]
+  // barrier's generation, a flag set once any block gave up waiting, and
+  // (from [4]) the tile counters of its per-body phases.
+  unsigned* gbar;                   // [8]
   double* h_P;         // [hist_cap][2][3 nsys] P of jump 1, P of jump 2 and the kicks
   double* h_b0;        // [hist_cap][6][NB] big bodies after jump 1 (pre-drift)
   double* h_b1;        // [hist_cap][6][NB] big bodies after the drift (detection endpoint)
