@@ -334,6 +334,9 @@ __global__ void __launch_bounds__(1024) k_groups(Dev d) { groups_block(d); }
 // SM's FP64 pipe.
 constexpr int kLaneMaxNB = 4;
 constexpr int kPackRounds = 3;
+// With deferral on, the one round of a two-body group in the packed phase
+// stops at the check after this row when nothing has converged yet.
+constexpr int kDeferRow = 3;
 
 // Changeover constants of one member: rc^2, 0.01 rc^2, 0.1 rc, 1/(0.9 rc).
 struct MemberK {
@@ -665,7 +668,7 @@ __device__ __forceinline__ int bs2_check(int K, int row, double sc, double tol2,
 template <int NCAND>
 __device__ int bs2_rounds(int cand, int lane, const Bs2Term& t, double tol, int max_sub,
                           int max_rounds, GroupRun<2>& g, int* s_row, double* s_y,
-                          unsigned long long* fevals = nullptr) {
+                          unsigned long long* fevals = nullptr, int stop_row = kBsRows - 1) {
   const int row = lane >> 2, q = lane & 3, ob = q & 1;
   const bool vel = q >= 2;
   const int n = 2 * (row + 1);
@@ -716,6 +719,8 @@ __device__ int bs2_rounds(int cand, int lane, const Bs2Term& t, double tol, int 
           acc_c = 0;
           acc_r = r;
           decided = true;
+        } else if (K >= stop_row && K < kBsRows - 1) {
+          return 0;   // handed over before the round is decided: g is as it was
         } else if (K == kBsRows - 1) {
           decided = true;
         }
@@ -925,8 +930,11 @@ __device__ void pack_two(const Dev& d, int w, int lane) {
   g.rem = S.h;
   g.H = S.h;
   g.nsub = 0;
+  // with deferral on, a group whose first try has not converged by row
+  // kDeferRow goes to the catch-up, which runs that macro sub-step again
+  // from the start with four candidates (the same steps are accepted)
   const int r = bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, d.defer ? 1 : kPackRounds, g,
-                              nullptr, nullptr);
+                              nullptr, nullptr, nullptr, d.defer ? kDeferRow : kBsRows - 1);
   pack_tail<2>(d, w, 0xffffffffu, 0, lane, o0, r, g, [&](GroupRun<2>& gg) {
     return bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, 1 << 30, gg, nullptr, nullptr);
   });
