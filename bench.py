@@ -282,9 +282,14 @@ def source_hash(names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"k_jump_kick": ["k_kick.cu", "mx_common.cuh", "mx_physics.cuh", "mx_growth.cuh"],
-                  "k_jump_drift": ["k_drift.cu", "mx_common.cuh", "mx_kepler.cuh"],
-                  "k_detect": ["k_detect.cu", "mx_common.cuh", "mx_encounter.cuh"]}
+KERNEL_SOURCES = {"k_jump_kick": ["k_kick.cu", "mx_kick_body.cuh", "mx_common.cuh", "mx_physics.cuh",
+                                  "mx_growth.cuh"],
+                  "k_jump_drift": ["k_drift.cu", "mx_drift_body.cuh", "mx_common.cuh", "mx_kepler.cuh"],
+                  "k_detect": ["k_detect.cu", "mx_detect_body.cuh", "mx_common.cuh",
+                               "mx_encounter.cuh"],
+                  "k_bs": ["k_bs.cu", "mx_bs.cuh", "mx_common.cuh", "mx_physics.cuh"],
+                  "k_catchup": ["k_bs.cu", "mx_bs.cuh", "mx_common.cuh", "mx_physics.cuh",
+                                "mx_kepler.cuh", "mx_encounter.cuh"]}
 
 
 def dram_traffic(kname):
