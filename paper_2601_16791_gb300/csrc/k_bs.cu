@@ -784,6 +784,160 @@ __device__ int bs2_rounds(int cand, int lane, const Bs2Term& t, double tol, int 
   return (g.rem == 0.0) ? 1 : 0;
 }
 
+// ------------------------------------------------ two bodies on three warps
+// The catch-up's integrator for two-body groups.  A group's macro sub-steps
+// form one serial chain, and a warp scheduler issues one FP64 instruction
+// about every 69 cycles, so the chain's length in FP64 instructions per warp
+// sets its time.  Here warp c (c = 0, 1, 2) keeps coordinate c of every lane
+// of bs2_rounds' layout (lane 4r + q: Stoermer row r, force term q), so the
+// per-coordinate work (differences, accelerations, the Stoermer update, the
+// Aitken-Neville table) is a third of bs2_rounds'; the squared separation
+// and the error, which need all three coordinates, exchange them through
+// shared memory and sum them in bs2_rounds' order.  Every floating-point
+// operation is bs2_rounds' own, so each try gives its bits and the step
+// search, one try per round (H, then H/2 after a failure, ...), accepts what
+// it accepts.  Warps 0-2 only (named barrier 1, 96 threads); g is the same
+// on every lane of the three warps before and after.
+struct Bs2cSmem {
+  double* d;   // [2][3][32] the pair separations, by sub-step parity
+  double* e;   // [3][32] the coordinates' error differences
+  double* y;   // [12] the accepted state: x0, x1, v0, v1
+};
+
+__device__ __forceinline__ void bs2c_bar() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
+
+__device__ __forceinline__ double bs2c_accel(const Bs2Term& t, int c, int lane, double X,
+                                             const Bs2cSmem& sm, int& buf) {
+  const double xo = __shfl_xor_sync(0xffffffffu, X, 1);
+  const double dv = X - (t.pair ? xo : 0.0);
+  double* sd = sm.d + buf * 96;
+  sd[c * 32 + lane] = dv;
+  bs2c_bar();
+  const double d0 = sd[lane], d1 = sd[32 + lane], d2 = sd[64 + lane];
+  buf ^= 1;
+  const double s2 = fma(d0, d0, fma(d1, d1, d2 * d2));
+  const double yy = rsqrt_d(s2);
+  double wgt = (yy * yy) * (yy * t.musrc);
+  const long long b2 = __double_as_longlong(s2);
+  if (b2 >= __double_as_longlong(t.rc2)) {
+    wgt = 0.0;
+  } else if (b2 > __double_as_longlong(t.rc2lo)) {
+    const double qv = fma(s2, yy, -t.rc01) * t.i09;
+    wgt *= fma(-qv * qv * qv, fma(qv, fma(6.0, qv, -15.0), 10.0), 1.0);
+  }
+  const double a = -wgt * dv;
+  return a + __shfl_xor_sync(0xffffffffu, a, 2);
+}
+
+// bs2_check on one coordinate: the Neville table of rows 0..K, then the error
+// summed over the three coordinates in bs2_rounds' order.
+__device__ __forceinline__ int bs2c_check(int K, int row, int c, int lane, double sc, double tol2,
+                                          double Traw, double& T, const Bs2cSmem& sm) {
+  double Tp = Traw;
+  T = Traw;
+#pragma unroll
+  for (int j = 1; j < kBsRows; ++j) {
+    if (j > K) break;
+    const double up = __shfl_up_sync(0xffffffffu, T, 4);
+    if (row >= j && row <= K) {
+      if (row == j) Tp = T;
+      T = fma(T - up, c_bs_inv_den[row][j], T);
+    }
+  }
+  sm.e[c * 32 + lane] = T - Tp;
+  bs2c_bar();
+  const double x0 = sm.e[lane], x1 = sm.e[32 + lane], x2 = sm.e[64 + lane];
+  double e = 0.0;
+  e = fma(x0, x0, e);
+  e = fma(x1, x1, e);
+  e = fma(x2, x2, e);
+  e *= sc;
+  long long eb = __double_as_longlong(e);
+  eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 1));
+  eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 2));
+  const bool conv = row >= 1 && row <= K && eb <= __double_as_longlong(tol2);
+  const unsigned v = __ballot_sync(0xffffffffu, conv);
+  return v ? ((__ffs(v) - 1) >> 2) : -1;
+}
+
+// Up to max_rounds tries (one per round); returns 1 when the step is done, 0
+// when rounds ran out, -1 at the sub-step cap, as bs2_rounds does.
+__device__ int bs2c_rounds(int c, int lane, const Bs2Term& t, double tol, int max_sub,
+                           int max_rounds, GroupRun<2>& g, const Bs2cSmem& sm,
+                           unsigned long long* fevals) {
+  const int row = lane >> 2, q = lane & 3, ob = q & 1;
+  const bool vel = q >= 2;
+  const int n = 2 * (row + 1);
+  const double tol2 = tol * tol;
+  int buf = 0;
+  for (int round = 0; round < max_rounds; ++round) {
+    if (g.rem == 0.0) return 1;
+    if (g.nsub >= max_sub) return -1;
+    if (fabs(g.H) > fabs(g.rem)) g.H = g.rem;
+    const double Hc = g.H * pow2_neg(0);
+    double X = ob ? g.Y[c][1] : g.Y[c][0];
+    const double V = ob ? g.Y[3 + c][1] : g.Y[3 + c][0];
+    const int so = vel ? 3 : 0;
+    const double s0 = ob ? g.Y[so][1] : g.Y[so][0];
+    const double s1 = ob ? g.Y[so + 1][1] : g.Y[so + 1][0];
+    const double s2v = ob ? g.Y[so + 2][1] : g.Y[so + 2][0];
+    const double sc = rcp_d(fma(s0, s0, fma(s1, s1, s2v * s2v)));
+    const double dd = Hc * c_bs_inv_n[row];
+    const double d2 = dd * dd;
+    double A = bs2c_accel(t, c, lane, X, sm, buf);
+    double D = dd * fma(0.5 * dd, A, V);
+    X += D;
+    double Traw = 0.0, T = 0.0;
+    int acc_r = -1;
+    bool decided = false;
+    for (int st = 1; st <= 2 * kBsRows && !decided; ++st) {
+      A = bs2c_accel(t, c, lane, X, sm, buf);
+      if (st < n) {
+        D = fma(d2, A, D);
+        X += D;
+      } else if (st == n) {
+        const double idd = n * rcp_d(Hc);
+        Traw = vel ? fma(D, idd, 0.5 * dd * A) : X;
+      }
+      const int K = (st >> 1) - 1;   // the row that completed at this sub-step
+      if ((st & 1) || !((kBs2Checks >> K) & 1u)) continue;
+      const int r = bs2c_check(K, row, c, lane, sc, tol2, Traw, T, sm);
+      if (r >= 0) {
+        acc_r = r;
+        decided = true;
+      } else if (K == kBsRows - 1) {
+        decided = true;
+      }
+    }
+    if (acc_r >= 0) {
+      // the accepted row's lanes hold coordinate c of x0, x1 (q = 0, 1) and
+      // v0, v1 (q = 2, 3)
+      if (row == acc_r) sm.y[3 * q + c] = T;
+      bs2c_bar();
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        g.Y[k][0] = sm.y[k];
+        g.Y[k][1] = sm.y[3 + k];
+        g.Y[3 + k][0] = sm.y[6 + k];
+        g.Y[3 + k][1] = sm.y[9 + k];
+      }
+      bs2c_bar();
+      g.nsub += 1;
+      if (fevals && c == 0 && lane == 0)
+        atomicAdd(fevals, (unsigned long long)((acc_r + 1) * (acc_r + 3)));
+      if (g.nsub > max_sub) return -1;
+      const double Hacc = g.H * pow2_neg(0);
+      g.rem -= Hacc;
+      g.H = 1.3 * Hacc;
+    } else {
+      if (fevals && c == 0 && lane == 0) atomicAdd(fevals, 80ull);
+      g.nsub += 1;
+      g.H *= 1.0 / (double)(1 << 1);
+    }
+  }
+  return (g.rem == 0.0) ? 1 : 0;
+}
+
 // Continuation record: rem, H, nsub, then Y.
 constexpr int kContDoubles = 3 + 6 * kLaneMaxNB;
 
@@ -1141,6 +1295,8 @@ __device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, co
 struct CatchBlk {
   int lane, wq;
   unsigned long long* ops;   // work counters of this pass (main or side stream)
+  Bs2cSmem b2;               // two-body groups on three warps (bs2c_rounds)
+  double* s_g;               // [15] a group's run state, broadcast to the block
   int* s_row;     // [4]
   double* s_y;    // [12]
   double* s_bc;   // [6] broadcast of a body state
@@ -1198,17 +1354,33 @@ __device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, int t,
     g.rem = G.rem;
     g.H = G.H;
     g.nsub = G.nsub;
-    const int r = bs2_rounds<4>(B.wq, B.lane, t, d.bs_tol, d.bs_max_sub, max_rounds, g, B.s_row,
-                                B.s_y, B.ops + 2);
+    // warps 0-2 integrate; the result reaches warp 3 through shared memory
+    int r = 0;
+    if (B.wq < 3) r = bs2c_rounds(B.wq, B.lane, t, d.bs_tol, d.bs_max_sub, max_rounds, g, B.b2,
+                                  B.ops + 2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *B.s_r = r;
+      B.s_g[0] = g.rem;
+      B.s_g[1] = g.H;
+      B.s_g[2] = (double)g.nsub;
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) B.s_g[3 + 6 * m + q] = g.Y[q][m];
+    }
+    __syncthreads();
+    r = *B.s_r;
+    G.rem = B.s_g[0];
+    G.H = B.s_g[1];
+    G.nsub = (int)B.s_g[2];
 #pragma unroll
     for (int m = 0; m < 2; ++m)
 #pragma unroll
-      for (int q = 0; q < 6; ++q) G.Y[q][m] = g.Y[q][m];
-    G.rem = g.rem;
-    G.H = g.H;
-    G.nsub = g.nsub;
+      for (int q = 0; q < 6; ++q) G.Y[q][m] = B.s_g[3 + 6 * m + q];
+    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 6; ++q) s6[q] = g.Y[q][1];
+    for (int q = 0; q < 6; ++q) s6[q] = G.Y[q][1];
     return r;
   }
   if (B.wq == 0) {
@@ -1606,9 +1778,11 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
 
 __global__ void __launch_bounds__(128) k_catchup(Dev d, CatchArgs a) {
   __shared__ int s_row[4], s_r;
-  __shared__ double s_y[12], s_bc[6];
+  __shared__ double s_y[12], s_bc[6], s_g[15];
+  __shared__ double s_b2d[2 * 3 * 32], s_b2e[3 * 32], s_b2y[12];
   const CatchBlk B{(int)(threadIdx.x & 31), (int)(threadIdx.x >> 5),
-                   d.work_ops + (a.mode == 1 ? 4 : 0), s_row, s_y, s_bc, &s_r};
+                   d.work_ops + (a.mode == 1 ? 4 : 0), Bs2cSmem{s_b2d, s_b2e, s_b2y}, s_g,
+                   s_row, s_y, s_bc, &s_r};
   const int na = (a.bank_a >= 0) ? min(d.rcount[a.bank_a], d.dcap) : 0;
   const int nb = (a.bank_b >= 0) ? min(d.rcount[a.bank_b], d.dcap) : 0;
   if (a.next_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) d.hstep[0] = a.next_slot;
