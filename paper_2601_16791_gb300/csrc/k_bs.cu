@@ -22,6 +22,8 @@
 // ~67-cycle latency and costs the same for 1 or 32 active lanes, so a group's
 // serial chain, not its arithmetic, sets the time: the rows and step
 // candidates of a macro sub-step go on separate lanes to shorten it.
+#include <cooperative_groups.h>
+
 #include "mx_common.cuh"
 #include "mx_encounter.cuh"
 #include "mx_kepler.cuh"
@@ -860,21 +862,103 @@ __device__ __forceinline__ int bs2c_check(int K, int row, int c, int lane, doubl
   return v ? ((__ffs(v) - 1) >> 2) : -1;
 }
 
-// Up to max_rounds tries (one per round); returns 1 when the step is done, 0
-// when rounds ran out, -1 at the sub-step cap, as bs2_rounds does.
+// The two CTAs of a catch-up cluster try H (rank 0) and H/2 (rank 1) in the
+// same round, as the first two candidates of bs2_rounds.  Each CTA's mailbox
+// receives the other's message: rank 0's the H/2 try (its lowest converged
+// row, or -1, and that row's state), rank 1's the round's outcome (the
+// accepted candidate and row, or -1, and the new state).  A message is
+// written, then fenced at cluster scope, then its round number is stored in
+// `seq`; the reader polls `seq` (at most kMailSpin polls).
+struct ClusterMail {
+  double* y;          // [12] state in the message
+  volatile int* hdr;  // [2] candidate, row
+  volatile int* seq;  // [1] round number of the message
+  volatile int* ack;  // [1] rank 0's: the last outcome rank 1 has read
+  int* round;         // [1] rounds run by this CTA's catch-up so far (both CTAs alike)
+  int* flag;          // [1] scratch: a word one thread read, for the three warps
+  int cta;            // 0 or 1
+  unsigned* status;
+};
+constexpr long long kMailSpin = 1ll << 26;   // about a second of polls
+
+// Writes this CTA's message into the other CTA's mailbox: lanes of row
+// `row_sel` hold coordinate c of the state's four vectors (x0, x1, v0, v1).
+__device__ __forceinline__ void mail_send(const ClusterMail& mb, int c, int lane, int row,
+                                          int row_sel, int cand, int r, double T, int seq) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned other = (unsigned)(1 - mb.cta);
+  double* ry = cl.map_shared_rank(mb.y, other);
+  int* rh = cl.map_shared_rank(const_cast<int*>(mb.hdr), other);
+  int* rs = cl.map_shared_rank(const_cast<int*>(mb.seq), other);
+  if (r >= 0 && row == row_sel) ry[3 * (lane & 3) + c] = T;
+  if (c == 0 && lane == 0) {
+    rh[0] = cand;
+    rh[1] = r;
+  }
+  bs2c_bar();
+  if (c == 0 && lane == 0) {
+    asm volatile("fence.acq_rel.cluster;" ::: "memory");
+    *reinterpret_cast<volatile int*>(rs) = seq;
+  }
+}
+
+// Waits until *w >= v (one thread polls, the three warps get its answer);
+// false if that did not happen within kMailSpin polls (ST_BARRIER).
+__device__ __forceinline__ bool mail_wait_word(const ClusterMail& mb, volatile int* w, int v,
+                                               int c, int lane) {
+  if (c == 0 && lane == 0) {
+    long long k = 0;
+    int ok = 1;
+    while (*w < v) {   // a shared-memory word: a poll costs tens of cycles
+      if (++k > kMailSpin) {
+        atomicOr(mb.status, ST_BARRIER);
+        ok = 0;
+        break;
+      }
+    }
+    asm volatile("fence.acq_rel.cluster;" ::: "memory");
+    *mb.flag = ok;
+  }
+  bs2c_bar();
+  const bool ok = *mb.flag != 0;
+  bs2c_bar();
+  return ok;
+}
+
+// The message of round `seq` in this CTA's mailbox.  Round numbers only grow,
+// and the other CTA sends the message of a round only after this CTA's
+// message of the round before has been read, so the word reaches `seq` and
+// stays there while this CTA waits.
+__device__ __forceinline__ bool mail_wait(const ClusterMail& mb, int seq, int c, int lane) {
+  return mail_wait_word(mb, mb.seq, seq, c, lane);
+}
+
+// Up to max_rounds tries per CTA (one per round); returns 1 when the step is
+// done, 0 when rounds ran out, -1 at the sub-step cap, as bs2_rounds does.
+// With `mb` the CTA is one of a cluster pair (above); without, it tries one
+// candidate per round alone.
 __device__ int bs2c_rounds(int c, int lane, const Bs2Term& t, double tol, int max_sub,
                            int max_rounds, GroupRun<2>& g, const Bs2cSmem& sm,
-                           unsigned long long* fevals) {
+                           unsigned long long* fevals, const ClusterMail* mb = nullptr) {
   const int row = lane >> 2, q = lane & 3, ob = q & 1;
   const bool vel = q >= 2;
   const int n = 2 * (row + 1);
   const double tol2 = tol * tol;
+  const int cand = mb ? mb->cta : 0;
+  const int ncand = mb ? 2 : 1;
   int buf = 0;
   for (int round = 0; round < max_rounds; ++round) {
     if (g.rem == 0.0) return 1;
     if (g.nsub >= max_sub) return -1;
     if (fabs(g.H) > fabs(g.rem)) g.H = g.rem;
-    const double Hc = g.H * pow2_neg(0);
+    int seq = 0;
+    if (mb) {
+      seq = *mb->round + 1;
+      bs2c_bar();   // every warp has read the round number
+      if (c == 0 && lane == 0) *mb->round = seq;
+    }
+    const double Hc = g.H * pow2_neg(cand);
     double X = ob ? g.Y[c][1] : g.Y[c][0];
     const double V = ob ? g.Y[3 + c][1] : g.Y[3 + c][0];
     const int so = vel ? 3 : 0;
@@ -889,7 +973,7 @@ __device__ int bs2c_rounds(int c, int lane, const Bs2Term& t, double tol, int ma
     X += D;
     double Traw = 0.0, T = 0.0;
     int acc_r = -1;
-    bool decided = false;
+    bool decided = false, moot = false;
     for (int st = 1; st <= 2 * kBsRows && !decided; ++st) {
       A = bs2c_accel(t, c, lane, X, sm, buf);
       if (st < n) {
@@ -907,7 +991,71 @@ __device__ int bs2c_rounds(int c, int lane, const Bs2Term& t, double tol, int ma
         decided = true;
       } else if (K == kBsRows - 1) {
         decided = true;
+      } else if (mb && cand == 1) {
+        // rank 0 has already decided the round: this try no longer matters
+        if (c == 0 && lane == 0) *mb->flag = (*mb->seq >= seq) ? 1 : 0;
+        bs2c_bar();
+        moot = *mb->flag != 0;
+        bs2c_bar();
+        decided = moot;
       }
+    }
+    int acc_c = (acc_r >= 0) ? cand : -1;
+    if (mb) {
+      bool ok = true;
+      if (cand == 1) {
+        if (!moot) mail_send(*mb, c, lane, row, acc_r, 1, acc_r, T, seq);
+        ok = mail_wait(*mb, seq, c, lane);
+        acc_c = ok ? mb->hdr[0] : -1;
+        acc_r = ok ? mb->hdr[1] : -1;
+        if (ok && acc_c >= 0 && row == acc_r) T = mb->y[3 * q + c];
+        bs2c_bar();   // every warp has read the outcome: rank 0 may send the next one
+        if (c == 0 && lane == 0) {
+          namespace cg = cooperative_groups;
+          int* rack = cg::this_cluster().map_shared_rank(const_cast<int*>(mb->ack), 0u);
+          asm volatile("fence.acq_rel.cluster;" ::: "memory");
+          *reinterpret_cast<volatile int*>(rack) = seq;
+        }
+      } else {
+        if (acc_c < 0) {   // H failed: the round is H/2's try
+          ok = mail_wait(*mb, seq, c, lane);
+          acc_r = ok ? mb->hdr[1] : -1;
+          acc_c = (acc_r >= 0) ? 1 : -1;
+          if (acc_c == 1 && row == acc_r) T = mb->y[3 * q + c];
+        }
+        // rank 1 has read the last round's outcome before this one replaces it
+        ok = ok && mail_wait_word(*mb, mb->ack, seq - 1, c, lane);
+        mail_send(*mb, c, lane, row, acc_r, acc_c, acc_r, T, seq);
+      }
+      bs2c_bar();
+      if (!ok) return -1;
+      if (acc_c >= 0) {
+        // the accepted state: both ranks hold it on the lanes of row acc_r
+        // (the own try's, or the other's copied in from the mailbox)
+        if (row == acc_r) sm.y[3 * q + c] = T;
+        bs2c_bar();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          g.Y[k][0] = sm.y[k];
+          g.Y[k][1] = sm.y[3 + k];
+          g.Y[3 + k][0] = sm.y[6 + k];
+          g.Y[3 + k][1] = sm.y[9 + k];
+        }
+        bs2c_bar();
+        g.nsub += acc_c + 1;
+        if (fevals && cand == 0 && c == 0 && lane == 0)
+          atomicAdd(fevals, (unsigned long long)(80 * acc_c + (acc_r + 1) * (acc_r + 3)));
+        if (g.nsub > max_sub) return -1;
+        const double Hacc = g.H * pow2_neg(acc_c);
+        g.rem -= Hacc;
+        g.H = 1.3 * Hacc;
+      } else {
+        if (fevals && cand == 0 && c == 0 && lane == 0)
+          atomicAdd(fevals, (unsigned long long)(80 * ncand));
+        g.nsub += ncand;
+        g.H *= 1.0 / (double)(1 << 2);
+      }
+      continue;
     }
     if (acc_r >= 0) {
       // the accepted row's lanes hold coordinate c of x0, x1 (q = 0, 1) and
@@ -1239,10 +1387,12 @@ __global__ void __launch_bounds__(32) k_bs(Dev d) {
 // states (the integrators of the packed and spread phases, which accept the
 // same sub-steps), jump (P of jump 2), gravity of the staged big positions in
 // ascending order and the half kick(s) with drag.  So a deferred body ends
-// where the direct path would have put it, bit for bit.  The four warps take
-// the same path (each on its own scheduler, so the repeated work costs no
-// time); they differ only in the step candidate of a two-body group, and only
-// warp 0 writes.
+// where the direct path would have put it, bit for bit.  Each body has a
+// cluster of two CTAs of four warps, on two SMs.  Both CTAs and all their
+// warps take the same path (each warp on its own scheduler, so the repeated
+// work costs no time); in a two-body group's Bulirsch-Stoer rounds warps 0-2
+// of each CTA split the coordinates and the CTAs try H and H/2
+// (bs2c_rounds); only warp 0 of rank 0 writes.
 //
 // Modes (CatchArgs::mode):
 //  0  window end, main stream: every body deferred in the window and every
@@ -1294,8 +1444,10 @@ __device__ __forceinline__ void load_members_g(const Dev& d, const SysDev& S, co
 
 struct CatchBlk {
   int lane, wq;
+  int cta;                   // rank in the cluster pair (only rank 0 writes)
   unsigned long long* ops;   // work counters of this pass (main or side stream)
   Bs2cSmem b2;               // two-body groups on three warps (bs2c_rounds)
+  const ClusterMail* mail;   // the pair's mailboxes
   double* s_g;               // [15] a group's run state, broadcast to the block
   int* s_row;     // [4]
   double* s_y;    // [12]
@@ -1357,7 +1509,7 @@ __device__ int catch_bs_any(const Dev& d, const SysDev& S, CatchGroup& G, int t,
     // warps 0-2 integrate; the result reaches warp 3 through shared memory
     int r = 0;
     if (B.wq < 3) r = bs2c_rounds(B.wq, B.lane, t, d.bs_tol, d.bs_max_sub, max_rounds, g, B.b2,
-                                  B.ops + 2);
+                                  B.cta == 0 ? B.ops + 2 : nullptr, B.mail);
     __syncthreads();
     if (threadIdx.x == 0) {
       *B.s_r = r;
@@ -1431,14 +1583,15 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
                            const CatchBlk& B, double* s6, CatchGroup& G, int* kn, int* kl) {
   const int lane = B.lane;
   const bool w0 = B.wq == 0;
+  const bool wr = w0 && B.cta == 0;   // the warp that writes (rank 1 replays alike, silently)
   const size_t NBs = (size_t)d.NB;
-  if (w0 && lane == 0) atomicAdd(B.ops + 0, 1ull);
+  if (wr && lane == 0) atomicAdd(B.ops + 0, 1ull);
   double dj[3];
   jump_vec(d.h_P + (size_t)t * 6 * d.nsys + 3 * sys, S, 0.5, dj);
   double x = s6[0] + dj[0], y = s6[1] + dj[1], z = s6[2] + dj[2];
   double u = s6[3], v = s6[4], w = s6[5];
   const double a0[6] = {x, y, z, u, v, w};
-  if (!kepler_drift(S.mu0, S.h, d.kepler_max_iter, x, y, z, u, v, w) && w0 && lane == 0)
+  if (!kepler_drift(S.mu0, S.h, d.kepler_max_iter, x, y, z, u, v, w) && wr && lane == 0)
     atomicOr(d.status, ST_KEPLER);
   const double a1[6] = {x, y, z, u, v, w};
   float af[12];
@@ -1475,7 +1628,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
       }
     }
     unsigned m = __ballot_sync(0xffffffffu, hit);
-    if (hit && w0) {
+    if (hit && wr) {
       const int gi = S.off + l;
       if (d.ever) {
         d.ever[gi] = 1;
@@ -1495,7 +1648,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
       else over = true;
     }
   }
-  if (keys == 1 && w0 && lane == 0) d.flags[j] = nf > 0 ? 1 : 0;
+  if (keys == 1 && wr && lane == 0) d.flags[j] = nf > 0 ? 1 : 0;
   if (keys == 2) {
     *kn = nf;
     for (int e = 0; e < nf; ++e) kl[e] = fl[e];
@@ -1530,7 +1683,7 @@ __device__ int catch_front(const Dev& d, const SysDev& S, int sys, int j, int t,
     }
   }
   if (bad) {   // the direct path skips the step's Bulirsch-Stoer and reports it
-    if (w0 && lane == 0) atomicOr(d.status, ST_GROUP);
+    if (wr && lane == 0) atomicOr(d.status, ST_GROUP);
     return 0;
   }
   const int nb = cnt + 1;
@@ -1642,7 +1795,7 @@ __device__ __forceinline__ double* rec_state(const Dev& d, int bank, int idx) {
 // group outruns the budget).
 __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx,
                              const CatchBlk& B) {
-  const bool lead = threadIdx.x == 0;
+  const bool lead = threadIdx.x == 0 && B.cta == 0;
   const int* R = rec_ints(d, bank, idx);
   const double* Cs = rec_state(d, bank, idx);
   const int j = R[0];
@@ -1776,21 +1929,36 @@ __device__ void catch_record(const Dev& d, const CatchArgs& a, int bank, int idx
   }
 }
 
-__global__ void __launch_bounds__(128) k_catchup(Dev d, CatchArgs a) {
+// A cluster of two CTAs per deferred body, on two SMs: both replay the body
+// alike (only rank 0 writes), and in a two-body group's Bulirsch-Stoer rounds
+// rank 0 tries H and rank 1 tries H/2 (bs2c_rounds with a ClusterMail).
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128) k_catchup(Dev d, CatchArgs a) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
   __shared__ int s_row[4], s_r;
   __shared__ double s_y[12], s_bc[6], s_g[15];
   __shared__ double s_b2d[2 * 3 * 32], s_b2e[3 * 32], s_b2y[12];
-  const CatchBlk B{(int)(threadIdx.x & 31), (int)(threadIdx.x >> 5),
-                   d.work_ops + (a.mode == 1 ? 4 : 0), Bs2cSmem{s_b2d, s_b2e, s_b2y}, s_g,
+  __shared__ double s_my[12];
+  __shared__ int s_mw[6];   // header (2), seq, ack, round, scratch flag
+  const int cta = (int)cl.block_rank();
+  if (threadIdx.x < 6) s_mw[threadIdx.x] = 0;
+  const ClusterMail mail{s_my, s_mw, s_mw + 2, s_mw + 3, s_mw + 4, s_mw + 5, cta, d.status};
+  const CatchBlk B{(int)(threadIdx.x & 31), (int)(threadIdx.x >> 5), cta,
+                   d.work_ops + (a.mode == 1 ? 4 : 0), Bs2cSmem{s_b2d, s_b2e, s_b2y}, &mail, s_g,
                    s_row, s_y, s_bc, &s_r};
+  // both mailboxes are zeroed before either CTA can write into the other's
+  cl.sync();
   const int na = (a.bank_a >= 0) ? min(d.rcount[a.bank_a], d.dcap) : 0;
   const int nb = (a.bank_b >= 0) ? min(d.rcount[a.bank_b], d.dcap) : 0;
   if (a.next_slot >= 0 && blockIdx.x == 0 && threadIdx.x == 0) d.hstep[0] = a.next_slot;
-  for (int r = blockIdx.x; r < na + nb; r += gridDim.x) {
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  for (int r = pair; r < na + nb; r += npairs) {
     if (r < na) catch_record(d, a, a.bank_a, r, B);
     else catch_record(d, a, a.bank_b, r - na, B);
     __syncthreads();
   }
+  // no CTA leaves while the other may still write into its shared memory
+  cl.sync();
 }
 
 // ------------------------------------------------------ the persistent step
@@ -1929,7 +2097,7 @@ void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
 void launch_catchup(const Dev& d, int nblocks, int mode, int bank_a, int bank_b, int bank_out,
                     int t_end, int tl, int next_slot, int t_next, cudaStream_t st) {
   const CatchArgs a{mode, bank_a, bank_b, bank_out, t_end, tl, next_slot, t_next};
-  k_catchup<<<nblocks, 128, 0, st>>>(d, a);
+  k_catchup<<<(nblocks + 1) & ~1, 128, 0, st>>>(d, a);   // whole cluster pairs
 }
 
 // The kernels of a step share one shared-memory carveout (the largest), so
