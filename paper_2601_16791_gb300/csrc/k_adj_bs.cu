@@ -25,6 +25,7 @@
 // added to theirs by a per-system fold in group order.  Big-big encounters
 // stay refused (ST_ADJ_ENC): a big body's own state never comes from a group.
 #include "mx_bs.cuh"
+#include "mx_bs2.cuh"
 #include "mx_common.cuh"
 #include "mx_kernels.h"
 
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(32) k_adj_bs_fwd(Dev d, Adj a) {
       if (lane == 0) a.g_M[g] = -1;
       continue;
     }
+    if (G.nb == 2) continue;   // k_adj_bs_fwd2
     const SysDev& S = d.sys[sy];
     const int nb = G.nb, stride = tape_stride(nb);
     const unsigned long long off = a.g_off[g];
@@ -277,6 +279,143 @@ __global__ void __launch_bounds__(32) k_adj_bs_fwd(Dev d, Adj a) {
         a.g_M[g] = M;
         const int N = d.N, s = nb - 1;
         for (int c = 0; c < 6; ++c) a.xv3[(size_t)c * N + j] = Y[c][s];
+      }
+    }
+  }
+}
+
+// Forward of a two-body group (a big body and the planetesimal), one block
+// of four warps per group: warps 0-2 run the catch-up's integrator with one
+// coordinate each (bs2c arithmetic, the same tries and accepted sub-steps as
+// the step's own two-body integrator), one try per round, and record every
+// accepted macro sub-step (H, row, starting state) in the group's tape.
+__global__ void __launch_bounds__(128) k_adj_bs_fwd2(Dev d, Adj a) {
+  __shared__ double s_d[2 * 3 * 32], s_e[3 * 32], s_y[12];
+  const Bs2cSmem sm{s_d, s_e, s_y};
+  const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const int row = lane >> 2, q = lane & 3, ob = q & 1;
+  const bool vel = q >= 2;
+  const int n = 2 * (row + 1);
+  const int ng = *a.g_count;
+  for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+    if (a.g_nb[g] != 1) continue;   // two bodies: one big body and the planetesimal
+    if (c == 3) continue;           // warps 0-2 only (named barrier 1)
+    GroupState G;
+    double Y0[6][kMaxGroup];
+    int big[kMaxGroup], j, sy;
+    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) {
+      if (threadIdx.x == 0) a.g_M[g] = -1;
+      continue;
+    }
+    const SysDev& S = d.sys[sy];
+    const int stride = tape_stride(2);
+    const unsigned long long off = a.g_off[g];
+    if (off + (unsigned long long)kAdjMaxSteps * stride > a.tape_cap) {
+      if (threadIdx.x == 0) {
+        a.g_M[g] = -1;
+        atomicOr(d.status, ST_WORK_OVF);
+      }
+      continue;
+    }
+    double* T = a.tape + off;
+    double mu[2];
+    MemberK K[2];
+    for (int m = 0; m < 2; ++m) {
+      const double rc = G.rc[m];
+      mu[m] = G.mu[m];
+      K[m].rc = rc;
+      K[m].rc2 = rc * rc;
+      K[m].rc2lo = 0.01 * (rc * rc);
+      K[m].rc01 = 0.1 * rc;
+      K[m].i09 = (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
+    }
+    const Bs2Term tm = bs2_term(q, S.mu0, mu, K);
+    GroupRun<2> gr;
+    for (int k = 0; k < 6; ++k) {
+      gr.Y[k][0] = Y0[k][0];
+      gr.Y[k][1] = Y0[k][1];
+    }
+    gr.rem = S.h;
+    gr.H = S.h;
+    gr.nsub = 0;
+    const double tol2 = d.bs_tol * d.bs_tol;
+    int buf = 0, M = 0;
+    bool ok = true;
+    while (gr.rem != 0.0) {
+      if (gr.nsub >= d.bs_max_sub || M >= kAdjMaxSteps) {
+        ok = false;
+        break;
+      }
+      if (fabs(gr.H) > fabs(gr.rem)) gr.H = gr.rem;
+      const double Hc = gr.H;
+      double X = ob ? gr.Y[c][1] : gr.Y[c][0];
+      const double V = ob ? gr.Y[3 + c][1] : gr.Y[3 + c][0];
+      const int so = vel ? 3 : 0;
+      const double s0 = ob ? gr.Y[so][1] : gr.Y[so][0];
+      const double s1 = ob ? gr.Y[so + 1][1] : gr.Y[so + 1][0];
+      const double s2v = ob ? gr.Y[so + 2][1] : gr.Y[so + 2][0];
+      const double sc = rcp_d(fma(s0, s0, fma(s1, s1, s2v * s2v)));
+      const double dd = Hc * c_bs_inv_n[row];
+      const double d2 = dd * dd;
+      double A = bs2c_accel(tm, c, lane, X, sm, buf);
+      double D = dd * fma(0.5 * dd, A, V);
+      X += D;
+      double Traw = 0.0, Tv = 0.0;
+      int acc_r = -1;
+      bool decided = false;
+      for (int st = 1; st <= 2 * kBsRows && !decided; ++st) {
+        A = bs2c_accel(tm, c, lane, X, sm, buf);
+        if (st < n) {
+          D = fma(d2, A, D);
+          X += D;
+        } else if (st == n) {
+          const double idd = n * rcp_d(Hc);
+          Traw = vel ? fma(D, idd, 0.5 * dd * A) : X;
+        }
+        const int Kr = (st >> 1) - 1;
+        if ((st & 1) || !((kBs2Checks >> Kr) & 1u)) continue;
+        const int r = bs2c_check(Kr, row, c, lane, sc, tol2, Traw, Tv, sm);
+        if (r >= 0) {
+          acc_r = r;
+          decided = true;
+        } else if (Kr == kBsRows - 1) {
+          decided = true;
+        }
+      }
+      gr.nsub += 1;
+      if (acc_r >= 0) {
+        if (c == 0 && lane == 0) {   // the sub-step's record: H, row, starting state
+          double* rr = T + (size_t)M * stride;
+          rr[0] = Hc;
+          rr[1] = (double)acc_r;
+          for (int k = 0; k < 6; ++k) {
+            rr[2 + 2 * k] = gr.Y[k][0];
+            rr[3 + 2 * k] = gr.Y[k][1];
+          }
+        }
+        if (row == acc_r) sm.y[3 * q + c] = Tv;
+        bs2c_bar();
+        for (int k = 0; k < 3; ++k) {
+          gr.Y[k][0] = sm.y[k];
+          gr.Y[k][1] = sm.y[3 + k];
+          gr.Y[3 + k][0] = sm.y[6 + k];
+          gr.Y[3 + k][1] = sm.y[9 + k];
+        }
+        bs2c_bar();
+        gr.rem -= Hc;
+        gr.H = 1.3 * Hc;
+        ++M;
+      } else {
+        gr.H *= 0.5;
+      }
+    }
+    if (c == 0 && lane == 0) {
+      if (!ok) {
+        atomicOr(d.status, M >= kAdjMaxSteps ? ST_WORK_OVF : ST_BS);
+        a.g_M[g] = -1;
+      } else {
+        a.g_M[g] = M;
+        for (int k = 0; k < 6; ++k) a.xv3[(size_t)k * d.N + j] = gr.Y[k][1];
       }
     }
   }
@@ -425,6 +564,7 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp(Dev d, Adj a) {
     double Y0[6][kMaxGroup];
     int big[kMaxGroup], j, sy;
     if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) continue;
+    if (G.nb == 2) continue;   // k_adj_bs_vjp2
     const SysDev& S = d.sys[sy];
     const int N = d.N, nb = G.nb, s = nb - 1;
     double lY[6][kMaxGroup], lO[6][kMaxGroup];
@@ -462,39 +602,278 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp(Dev d, Adj a) {
   }
 }
 
-// Per system: the big bodies' shares, added in group order (groups are sorted
-// by planetesimal, so a system's groups are contiguous), and the sum of the
-// position shares for jump 1's momentum term.
+// Reverse of a two-body group, one warp per group, on term lanes: lane 4r + q
+// reverses Stoermer row r for force term q (the layout of bs2_rounds: 0 and 1
+// the star on body 0 and 1, 2 body 1 on body 0, 3 body 0 on body 1), so a
+// lane evaluates one term's Jacobian product instead of all of them.  Every
+// term is written as a pair term (the star is a source at the origin with
+// weight 1 - K = 1): with d = x_b - x_src, s = |d|, w = mu (1 - K)/s^3 and
+// w' = dw/d(s^2), the force -w d has the product
+//   c = -w lA - 2 w' (d . lA) d,
+// added to body b's cotangent; a pair term also takes c from its source.
+// A body's total is its two terms' c plus the other body's pair reaction,
+// gathered with shuffles in a fixed order (both lanes of a body get the same
+// bits).  The rows' results are weighted by the Aitken-Neville coefficients
+// of the recorded row and summed over rows by a fixed butterfly.
+struct AdjTerm {
+  double mu, rc2, rc2lo, rc01, i09;
+  bool pair;
+};
+
+// The weight w = mu (1 - K(s))/s^3 of the lane's term at separation vector
+// dx, and (with `deriv`) w' = dw/d(s^2):
+//   w' = -1.5 w / s^2 - mu K'(s) / (2 s^4),  K' = 30 q^2 (1 - q)^2 / (0.9 rc).
+__device__ __forceinline__ void adj_weight(const AdjTerm& t, const double (&dx)[3], double& w,
+                                           double& wp) {
+  const double s2 = fma(dx[0], dx[0], fma(dx[1], dx[1], dx[2] * dx[2]));
+  const double yy = rsqrt_d(s2);          // 1/s
+  const double y3 = (yy * yy) * yy;       // 1/s^3
+  w = t.mu * y3;
+  wp = -1.5 * w * (yy * yy);
+  const long long b2 = __double_as_longlong(s2);
+  if (b2 >= __double_as_longlong(t.rc2)) {
+    w = 0.0;
+    wp = 0.0;
+  } else if (b2 > __double_as_longlong(t.rc2lo)) {
+    const double q = fma(s2, yy, -t.rc01) * t.i09;
+    const double omk = fma(-q * q * q, fma(q, fma(6.0, q, -15.0), 10.0), 1.0);
+    const double om = 1.0 - q;
+    const double kp = 30.0 * (q * q) * (om * om) * t.i09;
+    wp = fma(wp, omk, -0.5 * (t.mu * y3) * kp * yy);
+    w *= omk;
+  }
+}
+
+constexpr int kAdjSub = 2 * kBsRows;
+
+__global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
+  const int lane = threadIdx.x;
+  const int row = lane >> 2, q = lane & 3, ob = q & 1;
+  const int src_r = (lane & ~3) + 3 - ob;   // the row's lane of the other body's pair term
+  const int ng = *a.g_count;
+  for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+    if (a.g_nb[g] != 1) continue;
+    const int M = a.g_M[g];
+    if (M < 0) continue;
+    GroupState G;
+    double Y0[6][kMaxGroup];
+    int big[kMaxGroup], j, sy;
+    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) continue;
+    const SysDev& S = d.sys[sy];
+    const int N = d.N;
+    AdjTerm tm;
+    tm.pair = q >= 2;
+    {
+      const double rc = fmax(G.rc[0], G.rc[1]);   // the pair's changeover radius
+      tm.mu = tm.pair ? G.mu[1 - ob] : S.mu0;
+      tm.rc2 = tm.pair ? rc * rc : INFINITY;
+      tm.rc2lo = tm.pair ? 0.01 * (rc * rc) : INFINITY;
+      tm.rc01 = tm.pair ? 0.1 * rc : 0.0;
+      tm.i09 = (tm.pair && rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
+    }
+    // the force of the lane's body at X (both of its terms, summed)
+    auto accel = [&](const double (&X)[3], double (&A)[3]) {
+      double dx[3], w, wp;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double xo = __shfl_xor_sync(0xffffffffu, X[c], 1);
+        dx[c] = X[c] - (tm.pair ? xo : 0.0);
+      }
+      adj_weight(tm, dx, w, wp);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double av = -w * dx[c];
+        A[c] = av + __shfl_xor_sync(0xffffffffu, av, 2);
+      }
+    };
+    // lX += J^T lA at positions X: the lane's term's product, the body's
+    // other term (lane q ^ 2) and the other body's pair reaction
+    auto vjp = [&](const double (&X)[3], const double (&lA)[3], double (&lX)[3]) {
+      double dx[3], w, wp;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double xo = __shfl_xor_sync(0xffffffffu, X[c], 1);
+        dx[c] = X[c] - (tm.pair ? xo : 0.0);
+      }
+      adj_weight(tm, dx, w, wp);
+      const double f = -2.0 * wp * fma(dx[0], lA[0], fma(dx[1], lA[1], dx[2] * lA[2]));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double cs = fma(f, dx[c], -w * lA[c]);
+        const double cr = tm.pair ? -cs : 0.0;
+        const double other = __shfl_xor_sync(0xffffffffu, cs, 2);
+        const double react = __shfl_sync(0xffffffffu, cr, src_r);
+        lX[c] += (cs + other) + react;
+      }
+    };
+    // the cotangent of the group's output: the planetesimal's (body 1)
+    double lO[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) lO[k] = ob ? a.lam[(size_t)k * N + j] : 0.0;
+    const int stride = tape_stride(2);
+    for (int k = M - 1; k >= 0; --k) {
+      const double* r = a.tape + a.g_off[g] + (size_t)k * stride;
+      const double H = r[0];
+      const int K = (int)r[1];
+      double cw[kBsRows];
+      neville_weights(K, cw);
+      const bool act = row <= K;
+      const int n = 2 * (row + 1), nmax = 2 * (K + 1);
+      const double dd = H / n, d2 = dd * dd;
+      const double scale = act ? cw[row] : 0.0;
+      // forward: positions X_0..X_min(n, nmax) of this lane's body
+      double Xs[kAdjSub + 1][3];
+      double X[3], D[3], A[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        X[c] = r[2 + 2 * c + ob];
+        Xs[0][c] = X[c];
+      }
+      accel(X, A);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        D[c] = dd * fma(0.5 * dd, A[c], r[2 + 2 * (3 + c) + ob]);
+        X[c] += D[c];
+        Xs[1][c] = X[c];
+      }
+      for (int st = 1; st < nmax; ++st) {
+        accel(X, A);
+        if (st < n) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            D[c] = fma(d2, A[c], D[c]);
+            X[c] += D[c];
+            Xs[st + 1][c] = X[c];
+          }
+        }
+      }
+      // reverse, the rows in lockstep from the longest accepted row down; a
+      // lane's own sweep starts at its n (a lane with nothing to do carries
+      // zero cotangents at valid positions, which add nothing)
+      double lX[3], lD[3], lA[3], lYv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        lX[c] = scale * lO[c];
+        lD[c] = scale * lO[3 + c] / dd;
+        lA[c] = scale * 0.5 * dd * lO[3 + c];   // O_v = D_n/dd + (dd/2) A(X_n)
+        lYv[c] = 0.0;
+      }
+      const int top = min(n, nmax);
+      for (int st = nmax; st >= 0; --st) {
+        double la[3], Xp[3];
+        if (st > top) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) la[c] = 0.0;
+        } else if (st == n) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) la[c] = lA[c];
+        } else if (st >= 1) {   // X_{s+1} = X_s + D_{s+1}, D_{s+1} = D_s + d2 A(X_s)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            lD[c] += lX[c];
+            la[c] = d2 * lD[c];
+          }
+        } else {                // X_1 = X_0 + D_1, D_1 = dd V_0 + (dd^2/2) A(X_0)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            lD[c] += lX[c];
+            lYv[c] = dd * lD[c];
+            la[c] = 0.5 * d2 * lD[c];
+          }
+        }
+        const int sp = min(st, top);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Xp[c] = Xs[sp][c];
+        vjp(Xp, la, lX);
+      }
+      // this row's share of the input cotangent, weighted; summed over rows
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        double v = act ? (c < 3 ? lX[c] : lYv[c - 3]) : 0.0;
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        lO[c] = v;
+      }
+    }
+    if (lane == 1)   // body 1: the planetesimal's cotangent at its pre-drift state
+      for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + j] = lO[c];
+    if (lane == 0) {   // body 0: the big body's share
+      double* out = a.g_contrib + (size_t)g * 6 * kMaxGroup;
+      for (int c = 0; c < 6; ++c) out[c] = lO[c];
+    }
+  }
+}
+
+// Per system: the big bodies' shares and the sum of the position shares for
+// jump 1's momentum term.  With up to 64 big bodies a system's sums run over
+// the groups on all threads of the block (thread t takes groups t, t + 256,
+// ... in order) and end in a fixed pairwise tree; with more, one thread per
+// big body adds its shares in group order.  Either way the order is fixed.
 __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
+  __shared__ double red[6][kThreads];
   const int sys = blockIdx.x;
   const SysDev& S = d.sys[sys];
   const int N = d.N;
   const int ng = *a.g_count;
-  for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int g = 0; g < ng; ++g) {
-      const int j = a.g_small[g];
-      if (j < S.off || j >= S.off + S.n || a.g_M[g] < 0) continue;
-      const int p = a.g_key[g], nbb = a.g_nb[g];
-      for (int m = 0; m < nbb; ++m) {
-        if (pkey_i(d.keys[p + m]) - S.off != i) continue;
-        const double* c6 = a.g_contrib + (size_t)g * 6 * kMaxGroup + 6 * m;
-        for (int c = 0; c < 6; ++c) acc[c] += c6[c];
+  const int t = threadIdx.x;
+  auto in_sys = [&](int g) {
+    const int j = a.g_small[g];
+    return j >= S.off && j < S.off + S.n && a.g_M[g] >= 0;
+  };
+  // block-wide sum of v[0..nv) into red[.][0] (every thread must call it)
+  auto tree = [&](const double* v, int nv) {
+    for (int c = 0; c < nv; ++c) red[c][t] = v[c];
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if (t < w)
+        for (int c = 0; c < nv; ++c) red[c][t] += red[c][t + w];
+      __syncthreads();
+    }
+  };
+  if (S.nbig <= 64) {
+    for (int i = 0; i < S.nbig; ++i) {
+      double acc[6] = {0, 0, 0, 0, 0, 0};
+      for (int g = t; g < ng; g += kThreads) {
+        if (!in_sys(g)) continue;
+        const int p = a.g_key[g], nbb = a.g_nb[g];
+        for (int m = 0; m < nbb; ++m) {
+          if (pkey_i(d.keys[p + m]) - S.off != i) continue;
+          const double* c6 = a.g_contrib + (size_t)g * 6 * kMaxGroup + 6 * m;
+          for (int c = 0; c < 6; ++c) acc[c] += c6[c];
+        }
       }
+      tree(acc, 6);
+      if (t == 0)
+        for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + S.off + i] += red[c][0];
+      __syncthreads();
     }
-    const int gi = S.off + i;
-    for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + gi] += acc[c];
-  }
-  if (threadIdx.x < 3) {
-    double sx = 0.0;
-    for (int g = 0; g < ng; ++g) {
-      const int j = a.g_small[g];
-      if (j < S.off || j >= S.off + S.n || a.g_M[g] < 0) continue;
-      const int nbb = a.g_nb[g];
-      for (int m = 0; m < nbb; ++m) sx += a.g_contrib[(size_t)g * 6 * kMaxGroup + 6 * m + threadIdx.x];
+  } else {
+    for (int i = t; i < S.nbig; i += blockDim.x) {
+      double acc[6] = {0, 0, 0, 0, 0, 0};
+      for (int g = 0; g < ng; ++g) {
+        if (!in_sys(g)) continue;
+        const int p = a.g_key[g], nbb = a.g_nb[g];
+        for (int m = 0; m < nbb; ++m) {
+          if (pkey_i(d.keys[p + m]) - S.off != i) continue;
+          const double* c6 = a.g_contrib + (size_t)g * 6 * kMaxGroup + 6 * m;
+          for (int c = 0; c < 6; ++c) acc[c] += c6[c];
+        }
+      }
+      const int gi = S.off + i;
+      for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + gi] += acc[c];
     }
-    a.bs_xsum[3 * sys + threadIdx.x] = sx;
+    __syncthreads();
   }
+  double sx[3] = {0, 0, 0};
+  for (int g = t; g < ng; g += kThreads) {
+    if (!in_sys(g)) continue;
+    const int nbb = a.g_nb[g];
+    for (int m = 0; m < nbb; ++m)
+      for (int c = 0; c < 3; ++c) sx[c] += a.g_contrib[(size_t)g * 6 * kMaxGroup + 6 * m + c];
+  }
+  tree(sx, 3);
+  if (t < 3) a.bs_xsum[3 * sys + t] = red[t][0];
 }
 
 void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
@@ -507,11 +886,13 @@ void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t
   launch_detect(dd, a.x2, a.xv3, d.flags, d.keys, d.pair_count, d.pair_cap, 1, st);
   launch_sort_keys(d.keys, d.pair_count, d.pair_cap, 0, st);
   k_adj_groups<<<1, 1024, 0, st>>>(d, a);
-  k_adj_bs_fwd<<<nblocks, 32, 0, st>>>(d, a);
+  k_adj_bs_fwd<<<nblocks, 32, 0, st>>>(d, a);    // groups of three or more bodies
+  k_adj_bs_fwd2<<<nblocks, 128, 0, st>>>(d, a);  // two-body groups
 }
 
 void launch_adjoint_bs_vjp(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
-  k_adj_bs_vjp<<<nblocks, 32, 0, st>>>(d, a);
+  k_adj_bs_vjp<<<nblocks, 32, 0, st>>>(d, a);    // groups of three or more bodies
+  k_adj_bs_vjp2<<<nblocks, 32, 0, st>>>(d, a);   // two-body groups
 }
 
 void launch_adjoint_bs_fold(const Dev& d, const Adj& a, cudaStream_t st) {
