@@ -651,6 +651,24 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
   const int row = lane >> 2, q = lane & 3, ob = q & 1;
   const int src_r = (lane & ~3) + 3 - ob;   // the row's lane of the other body's pair term
   const int ng = *a.g_count;
+  // Aitken-Neville weights of every row K (neville_weights, with the
+  // constants the two-body integrator extrapolates with), once per block
+  __shared__ double s_nw[kBsRows][kBsRows];
+  for (int e = lane; e < kBsRows * kBsRows; e += 32) {
+    const int K = e / kBsRows, l = e % kBsRows;
+    double rw[kBsRows] = {0.0};
+    for (int k = 0; k <= K; ++k) {
+      double prev = rw[0];
+      rw[0] = (k == l) ? 1.0 : 0.0;
+      for (int jj = 1; jj <= k; ++jj) {
+        const double t = rw[jj];
+        rw[jj] = fma(rw[jj - 1] - prev, c_bs_inv_den[k][jj], rw[jj - 1]);
+        prev = t;
+      }
+    }
+    s_nw[K][l] = (l <= K) ? rw[K] : 0.0;
+  }
+  __syncwarp();
   for (int g = blockIdx.x; g < ng; g += gridDim.x) {
     if (a.g_nb[g] != 1) continue;
     const int M = a.g_M[g];
@@ -671,9 +689,10 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
       tm.rc01 = tm.pair ? 0.1 * rc : 0.0;
       tm.i09 = (tm.pair && rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
     }
-    // the force of the lane's body at X (both of its terms, summed)
-    auto accel = [&](const double (&X)[3], double (&A)[3]) {
-      double dx[3], w, wp;
+    // the force of the lane's body at X (both of its terms, summed); the
+    // term's separation and weights are kept for the reverse sweep
+    auto accel = [&](const double (&X)[3], double (&A)[3], double (&dx)[3], double& w,
+                     double& wp) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double xo = __shfl_xor_sync(0xffffffffu, X[c], 1);
@@ -686,16 +705,11 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
         A[c] = av + __shfl_xor_sync(0xffffffffu, av, 2);
       }
     };
-    // lX += J^T lA at positions X: the lane's term's product, the body's
-    // other term (lane q ^ 2) and the other body's pair reaction
-    auto vjp = [&](const double (&X)[3], const double (&lA)[3], double (&lX)[3]) {
-      double dx[3], w, wp;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double xo = __shfl_xor_sync(0xffffffffu, X[c], 1);
-        dx[c] = X[c] - (tm.pair ? xo : 0.0);
-      }
-      adj_weight(tm, dx, w, wp);
+    // lX += J^T lA at a position kept by the forward sweep (separation dx,
+    // weights w, wp): the lane's term's product, the body's other term (lane
+    // q ^ 2) and the other body's pair reaction
+    auto vjp = [&](const double (&dx)[3], double w, double wp, const double (&lA)[3],
+                   double (&lX)[3]) {
       const double f = -2.0 * wp * fma(dx[0], lA[0], fma(dx[1], lA[1], dx[2] * lA[2]));
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -715,35 +729,37 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
       const double* r = a.tape + a.g_off[g] + (size_t)k * stride;
       const double H = r[0];
       const int K = (int)r[1];
-      double cw[kBsRows];
-      neville_weights(K, cw);
       const bool act = row <= K;
       const int n = 2 * (row + 1), nmax = 2 * (K + 1);
       const double dd = H / n, d2 = dd * dd;
-      const double scale = act ? cw[row] : 0.0;
-      // forward: positions X_0..X_min(n, nmax) of this lane's body
-      double Xs[kAdjSub + 1][3];
+      const double scale = act ? s_nw[K][row] : 0.0;
+      // forward: the term's separation and weights at the positions X_s,
+      // s = 0..min(n, nmax), of this lane's body
+      const int top = min(n, nmax);
+      double dxs[kAdjSub + 1][3], ws[kAdjSub + 1], wps[kAdjSub + 1];
       double X[3], D[3], A[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        X[c] = r[2 + 2 * c + ob];
-        Xs[0][c] = X[c];
-      }
-      accel(X, A);
+      for (int c = 0; c < 3; ++c) X[c] = r[2 + 2 * c + ob];
+      accel(X, A, dxs[0], ws[0], wps[0]);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         D[c] = dd * fma(0.5 * dd, A[c], r[2 + 2 * (3 + c) + ob]);
         X[c] += D[c];
-        Xs[1][c] = X[c];
       }
-      for (int st = 1; st < nmax; ++st) {
-        accel(X, A);
+      for (int st = 1; st <= nmax; ++st) {   // at X_st (a shorter row stays at its X_n)
+        double dxt[3], wt, wpt;
+        accel(X, A, dxt, wt, wpt);
+        if (st <= top) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) dxs[st][c] = dxt[c];
+          ws[st] = wt;
+          wps[st] = wpt;
+        }
         if (st < n) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             D[c] = fma(d2, A[c], D[c]);
             X[c] += D[c];
-            Xs[st + 1][c] = X[c];
           }
         }
       }
@@ -758,9 +774,8 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
         lA[c] = scale * 0.5 * dd * lO[3 + c];   // O_v = D_n/dd + (dd/2) A(X_n)
         lYv[c] = 0.0;
       }
-      const int top = min(n, nmax);
       for (int st = nmax; st >= 0; --st) {
-        double la[3], Xp[3];
+        double la[3];
         if (st > top) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) la[c] = 0.0;
@@ -782,9 +797,7 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
           }
         }
         const int sp = min(st, top);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Xp[c] = Xs[sp][c];
-        vjp(Xp, la, lX);
+        vjp(dxs[sp], ws[sp], wps[sp], la, lX);
       }
       // this row's share of the input cotangent, weighted; summed over rows
 #pragma unroll
