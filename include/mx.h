@@ -436,6 +436,16 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
  * step's encounter groups; 0: it skips them (see mx_adjoint_step). */
 mx_status mx_adjoint_encounters(mx_system* s, int on);
 
+/* Memory for the reverse of two-body encounter groups.  The adjoint's
+ * recomputation keeps the Stoermer sub-steps of each accepted macro sub-step
+ * of a two-body group (26,112 bytes a slot; default 16,384 slots, 428 MB,
+ * allocated at the first mx_adjoint_step), so that the reverse reads them
+ * back instead of integrating the sub-step again.  Records beyond the pool
+ * are recomputed; the result is the same to the bit either way.  slots = 0
+ * keeps none; at most 2^20.  The pool in place is freed (after the stream's
+ * work) and the new one allocated at the next adjoint step. */
+mx_status mx_adjoint_store(mx_system* s, long long slots);
+
 /* Reverse of the set-up transform: cotangent of the initial DH state ->
  * cotangent of the initial heliocentric state (6xN device buffers). */
 mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_grad_helio);

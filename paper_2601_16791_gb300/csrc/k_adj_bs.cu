@@ -47,10 +47,25 @@ __device__ int sys_of_body(const Dev& d, int g) {
   return lo;
 }
 
-// Tape record of one accepted macro sub-step: H, row, then the 6 x nb state;
-// each group has room for kAdjMaxSteps of them.
-__device__ __forceinline__ int tape_stride(int nb) { return 2 + 6 * nb; }
+// Tape record of one accepted macro sub-step: H, row, the 6 x nb state, then
+// (two-body groups) the slot of its kept Stoermer sub-steps or -1; each group
+// has room for kAdjMaxSteps of them.
+__device__ __forceinline__ int tape_stride(int nb) { return 3 + 6 * nb; }
 constexpr int kAdjMaxSteps = 128;
+
+// Slots of kept sub-steps are handed to a group kSubChunk at a time (one
+// atomic per kSubChunk records); -1 when the pool is used up or absent.
+constexpr int kSubChunk = 8;
+constexpr int kSubStride = kAdjSubVals * 32;   // doubles of one sub-step in a slot
+static_assert(kAdjSubRec == (2 * kBsRows + 1) * kSubStride, "a slot holds sub-steps 0..2 kBsRows");
+static_assert((kAdjSubRec * sizeof(double)) % 16 == 0 && (kSubStride * sizeof(double)) % 16 == 0,
+              "slots and sub-steps are whole 16-byte chunks");
+
+__device__ __forceinline__ int take_slots(const Adj& a) {
+  if (a.sub == nullptr) return -1;
+  const unsigned s0 = atomicAdd(a.sub_count, (unsigned)kSubChunk);
+  return (s0 <= a.sub_cap && a.sub_cap - s0 >= (unsigned)kSubChunk) ? (int)s0 : -1;
+}
 
 }  // namespace
 
@@ -108,7 +123,10 @@ __global__ void __launch_bounds__(1024) k_adj_groups(Dev d, Adj a) {
     __syncthreads();
   }
   const int ng = min(s_base, a.g_cap);
-  if (threadIdx.x == 0) *a.g_count = ng;
+  if (threadIdx.x == 0) {
+    *a.g_count = ng;
+    if (a.sub_count) *a.sub_count = 0;
+  }
   // tape regions: an exclusive scan of kAdjMaxSteps records per group
   __shared__ unsigned long long s_wsum[32];
   __shared__ unsigned long long s_run;
@@ -288,9 +306,13 @@ __global__ void __launch_bounds__(32) k_adj_bs_fwd(Dev d, Adj a) {
 // of four warps per group: warps 0-2 run the catch-up's integrator with one
 // coordinate each (bs2c arithmetic, the same tries and accepted sub-steps as
 // the step's own two-body integrator), one try per round, and record every
-// accepted macro sub-step (H, row, starting state) in the group's tape.
+// accepted macro sub-step (H, row, starting state) in the group's tape.  Each
+// try also keeps its Stoermer sub-steps (every lane's term at every position
+// up to its row's last) in the slot of the record it tries for; a rejected
+// try's slot is rewritten by the next try, so the accepted one stays.
 __global__ void __launch_bounds__(128) k_adj_bs_fwd2(Dev d, Adj a) {
   __shared__ double s_d[2 * 3 * 32], s_e[3 * 32], s_y[12];
+  __shared__ int s_slot;
   const Bs2cSmem sm{s_d, s_e, s_y};
   const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
   const int row = lane >> 2, q = lane & 3, ob = q & 1;
@@ -341,6 +363,9 @@ __global__ void __launch_bounds__(128) k_adj_bs_fwd2(Dev d, Adj a) {
     const double tol2 = d.bs_tol * d.bs_tol;
     int buf = 0, M = 0;
     bool ok = true;
+    if (threadIdx.x == 0) s_slot = take_slots(a);
+    bs2c_bar();
+    int slot0 = s_slot, m0 = 0;   // the group's current chunk of slots, from record m0
     while (gr.rem != 0.0) {
       if (gr.nsub >= d.bs_max_sub || M >= kAdjMaxSteps) {
         ok = false;
@@ -348,6 +373,8 @@ __global__ void __launch_bounds__(128) k_adj_bs_fwd2(Dev d, Adj a) {
       }
       if (fabs(gr.H) > fabs(gr.rem)) gr.H = gr.rem;
       const double Hc = gr.H;
+      const int slot = (slot0 >= 0) ? slot0 + (M - m0) : -1;
+      double* keep = (slot >= 0) ? a.sub + (size_t)slot * kAdjSubRec : nullptr;
       double X = ob ? gr.Y[c][1] : gr.Y[c][0];
       const double V = ob ? gr.Y[3 + c][1] : gr.Y[3 + c][0];
       const int so = vel ? 3 : 0;
@@ -357,14 +384,15 @@ __global__ void __launch_bounds__(128) k_adj_bs_fwd2(Dev d, Adj a) {
       const double sc = rcp_d(fma(s0, s0, fma(s1, s1, s2v * s2v)));
       const double dd = Hc * c_bs_inv_n[row];
       const double d2 = dd * dd;
-      double A = bs2c_accel(tm, c, lane, X, sm, buf);
+      double A = bs2c_accel(tm, c, lane, X, sm, buf, keep);
       double D = dd * fma(0.5 * dd, A, V);
       X += D;
       double Traw = 0.0, Tv = 0.0;
       int acc_r = -1;
       bool decided = false;
       for (int st = 1; st <= 2 * kBsRows && !decided; ++st) {
-        A = bs2c_accel(tm, c, lane, X, sm, buf);
+        A = bs2c_accel(tm, c, lane, X, sm, buf,
+                       (keep && st <= n) ? keep + (size_t)st * kSubStride : nullptr);
         if (st < n) {
           D = fma(d2, A, D);
           X += D;
@@ -392,9 +420,16 @@ __global__ void __launch_bounds__(128) k_adj_bs_fwd2(Dev d, Adj a) {
             rr[2 + 2 * k] = gr.Y[k][0];
             rr[3 + 2 * k] = gr.Y[k][1];
           }
+          rr[14] = (double)slot;
         }
+        const bool chunk_done = slot0 >= 0 && M + 1 - m0 == kSubChunk;
+        if (chunk_done && threadIdx.x == 0) s_slot = take_slots(a);
         if (row == acc_r) sm.y[3 * q + c] = Tv;
         bs2c_bar();
+        if (chunk_done) {
+          slot0 = s_slot;
+          m0 = M + 1;
+        }
         for (int k = 0; k < 3; ++k) {
           gr.Y[k][0] = sm.y[k];
           gr.Y[k][1] = sm.y[3 + k];
@@ -602,59 +637,72 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp(Dev d, Adj a) {
   }
 }
 
-// Reverse of a two-body group, one warp per group, on term lanes: lane 4r + q
-// reverses Stoermer row r for force term q (the layout of bs2_rounds: 0 and 1
-// the star on body 0 and 1, 2 body 1 on body 0, 3 body 0 on body 1), so a
-// lane evaluates one term's Jacobian product instead of all of them.  Every
-// term is written as a pair term (the star is a source at the origin with
-// weight 1 - K = 1): with d = x_b - x_src, s = |d|, w = mu (1 - K)/s^3 and
-// w' = dw/d(s^2), the force -w d has the product
+// Reverse of a two-body group, one block of three warps per group, in the
+// forward's layout (lane 4r + q: Stoermer row r, force term q, as in
+// bs2_rounds: 0 and 1 the star on body 0 and 1, 2 body 1 on body 0, 3 body 0
+// on body 1; warp c: coordinate c).  Every term is written as a pair term
+// (the star is a source at the origin): with d = x_b - x_src, s = |d|,
+// w = mu (1 - K)/s^3 and w' = dw/d(s^2), the force -w d has the product
 //   c = -w lA - 2 w' (d . lA) d,
-// added to body b's cotangent; a pair term also takes c from its source.
-// A body's total is its two terms' c plus the other body's pair reaction,
-// gathered with shuffles in a fixed order (both lanes of a body get the same
-// bits).  The rows' results are weighted by the Aitken-Neville coefficients
-// of the recorded row and summed over rows by a fixed butterfly.
-struct AdjTerm {
-  double mu, rc2, rc2lo, rc01, i09;
-  bool pair;
-};
+// added to body b's cotangent; a pair term also gives -c to its source.  The
+// dot product takes lA's three coordinates from shared memory; a body's total
+// is its two terms' c plus the other body's pair reaction, gathered with
+// shuffles in a fixed order (both lanes of a body get the same bits).  The
+// rows' results are weighted by the Aitken-Neville coefficients of the
+// recorded row and summed over rows by a fixed butterfly.
+//
+// The Stoermer positions of a record come from the slot the forward kept
+// (copied to shared memory with cp.async one record ahead of the sweep), or,
+// for a record without a slot, are recomputed with the forward's own
+// arithmetic into the same layout: both give the same bits.
 
-// The weight w = mu (1 - K(s))/s^3 of the lane's term at separation vector
-// dx, and (with `deriv`) w' = dw/d(s^2):
-//   w' = -1.5 w / s^2 - mu K'(s) / (2 s^4),  K' = 30 q^2 (1 - q)^2 / (0.9 rc).
-__device__ __forceinline__ void adj_weight(const AdjTerm& t, const double (&dx)[3], double& w,
-                                           double& wp) {
-  const double s2 = fma(dx[0], dx[0], fma(dx[1], dx[1], dx[2] * dx[2]));
-  const double yy = rsqrt_d(s2);          // 1/s
-  const double y3 = (yy * yy) * yy;       // 1/s^3
-  w = t.mu * y3;
-  wp = -1.5 * w * (yy * yy);
+// -2 dw/d(s^2) of a term from its kept weight w, 1/s and s^2:
+//   w' = -1.5 w / s^2 - mu K'(s) / (2 s^4),  K' = 30 q^2 (1 - q)^2 / (0.9 rc),
+// the second part inside the changeover shell (0.1 rc < s < rc) only.
+__device__ __forceinline__ double adj_wpm2(const Bs2Term& t, double s2, double yy, double w) {
   const long long b2 = __double_as_longlong(s2);
-  if (b2 >= __double_as_longlong(t.rc2)) {
-    w = 0.0;
-    wp = 0.0;
-  } else if (b2 > __double_as_longlong(t.rc2lo)) {
+  if (b2 >= __double_as_longlong(t.rc2)) return 0.0;
+  const double y2 = yy * yy;
+  double r = 3.0 * w * y2;
+  if (b2 > __double_as_longlong(t.rc2lo)) {
+    const double w0 = y2 * (yy * t.musrc);   // the weight before the changeover factor
     const double q = fma(s2, yy, -t.rc01) * t.i09;
-    const double omk = fma(-q * q * q, fma(q, fma(6.0, q, -15.0), 10.0), 1.0);
     const double om = 1.0 - q;
     const double kp = 30.0 * (q * q) * (om * om) * t.i09;
-    wp = fma(wp, omk, -0.5 * (t.mu * y3) * kp * yy);
-    w *= omk;
+    r = fma(w0 * kp, yy, r);
   }
+  return r;
 }
 
-constexpr int kAdjSub = 2 * kBsRows;
+__device__ __forceinline__ void cp_async16(double* dst, const double* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
 
-__global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
-  const int lane = threadIdx.x;
+// Dynamic shared memory of k_adj_bs_vjp2: two records' sub-steps, the
+// cotangent exchange (two buffers) and bs2c_accel's exchange.
+constexpr int kVjp2Smem = (2 * kAdjSubRec + 2 * 96 + 2 * 96 + 96 + 12) * (int)sizeof(double);
+
+__global__ void __launch_bounds__(96) k_adj_bs_vjp2(Dev d, Adj a) {
+  extern __shared__ __align__(16) double s_v2[];
+  double* s_rec = s_v2;                      // [2][kAdjSubRec]
+  double* s_la = s_v2 + 2 * kAdjSubRec;      // [2][3][32]
+  const Bs2cSmem sm{s_la + 2 * 96, s_la + 4 * 96, s_la + 5 * 96};
+  __shared__ double s_nw[kBsRows][kBsRows];
+  const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
   const int row = lane >> 2, q = lane & 3, ob = q & 1;
-  const int src_r = (lane & ~3) + 3 - ob;   // the row's lane of the other body's pair term
+  const int src_r = (lane & ~3) + 3 - ob;    // the row's lane of the other body's pair term
+  const int n = 2 * (row + 1);
   const int ng = *a.g_count;
   // Aitken-Neville weights of every row K (neville_weights, with the
-  // constants the two-body integrator extrapolates with), once per block
-  __shared__ double s_nw[kBsRows][kBsRows];
-  for (int e = lane; e < kBsRows * kBsRows; e += 32) {
+  // constants the two-body integrator extrapolates with)
+  for (int e = threadIdx.x; e < kBsRows * kBsRows; e += blockDim.x) {
     const int K = e / kBsRows, l = e % kBsRows;
     double rw[kBsRows] = {0.0};
     for (int k = 0; k <= K; ++k) {
@@ -668,7 +716,8 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
     }
     s_nw[K][l] = (l <= K) ? rw[K] : 0.0;
   }
-  __syncwarp();
+  bs2c_bar();
+  const int stride = tape_stride(2);
   for (int g = blockIdx.x; g < ng; g += gridDim.x) {
     if (a.g_nb[g] != 1) continue;
     const int M = a.g_M[g];
@@ -679,141 +728,125 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp2(Dev d, Adj a) {
     if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) continue;
     const SysDev& S = d.sys[sy];
     const int N = d.N;
-    AdjTerm tm;
-    tm.pair = q >= 2;
+    Bs2Term tm;
     {
-      const double rc = fmax(G.rc[0], G.rc[1]);   // the pair's changeover radius
-      tm.mu = tm.pair ? G.mu[1 - ob] : S.mu0;
-      tm.rc2 = tm.pair ? rc * rc : INFINITY;
-      tm.rc2lo = tm.pair ? 0.01 * (rc * rc) : INFINITY;
-      tm.rc01 = tm.pair ? 0.1 * rc : 0.0;
-      tm.i09 = (tm.pair && rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
+      double mu[2];
+      MemberK K[2];
+      for (int m = 0; m < 2; ++m) {
+        const double rc = G.rc[m];
+        mu[m] = G.mu[m];
+        K[m].rc = rc;
+        K[m].rc2 = rc * rc;
+        K[m].rc2lo = 0.01 * (rc * rc);
+        K[m].rc01 = 0.1 * rc;
+        K[m].i09 = (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
+      }
+      tm = bs2_term(q, S.mu0, mu, K);
     }
-    // the force of the lane's body at X (both of its terms, summed); the
-    // term's separation and weights are kept for the reverse sweep
-    auto accel = [&](const double (&X)[3], double (&A)[3], double (&dx)[3], double& w,
-                     double& wp) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double xo = __shfl_xor_sync(0xffffffffu, X[c], 1);
-        dx[c] = X[c] - (tm.pair ? xo : 0.0);
+    const double* tape = a.tape + a.g_off[g];
+    // the copy of record k's kept sub-steps 0..2(K + 1), if it has a slot
+    auto fetch = [&](int k) {
+      const double* r = tape + (size_t)k * stride;
+      const int slot = (int)r[14];
+      if (slot >= 0) {
+        const double* src = a.sub + (size_t)slot * kAdjSubRec;
+        double* dst = s_rec + (k & 1) * kAdjSubRec;
+        const int chunks = (2 * (int)r[1] + 3) * (kSubStride / 2);
+        for (int i = threadIdx.x; i < chunks; i += 96) cp_async16(dst + 2 * i, src + 2 * i);
       }
-      adj_weight(tm, dx, w, wp);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double av = -w * dx[c];
-        A[c] = av + __shfl_xor_sync(0xffffffffu, av, 2);
-      }
-    };
-    // lX += J^T lA at a position kept by the forward sweep (separation dx,
-    // weights w, wp): the lane's term's product, the body's other term (lane
-    // q ^ 2) and the other body's pair reaction
-    auto vjp = [&](const double (&dx)[3], double w, double wp, const double (&lA)[3],
-                   double (&lX)[3]) {
-      const double f = -2.0 * wp * fma(dx[0], lA[0], fma(dx[1], lA[1], dx[2] * lA[2]));
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double cs = fma(f, dx[c], -w * lA[c]);
-        const double cr = tm.pair ? -cs : 0.0;
-        const double other = __shfl_xor_sync(0xffffffffu, cs, 2);
-        const double react = __shfl_sync(0xffffffffu, cr, src_r);
-        lX[c] += (cs + other) + react;
-      }
+      cp_async_commit();
     };
     // the cotangent of the group's output: the planetesimal's (body 1)
-    double lO[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) lO[k] = ob ? a.lam[(size_t)k * N + j] : 0.0;
-    const int stride = tape_stride(2);
+    double lOp = ob ? a.lam[(size_t)c * N + j] : 0.0;
+    double lOv = ob ? a.lam[(size_t)(3 + c) * N + j] : 0.0;
+    if (M > 0) fetch(M - 1);
     for (int k = M - 1; k >= 0; --k) {
-      const double* r = a.tape + a.g_off[g] + (size_t)k * stride;
+      if (k > 0) fetch(k - 1);
+      else cp_async_commit();
+      cp_async_wait1();   // record k's copy (all but the newest group) has landed
+      bs2c_bar();
+      double* B = s_rec + (k & 1) * kAdjSubRec;
+      const double* r = tape + (size_t)k * stride;
       const double H = r[0];
       const int K = (int)r[1];
-      const bool act = row <= K;
-      const int n = 2 * (row + 1), nmax = 2 * (K + 1);
-      const double dd = H / n, d2 = dd * dd;
-      const double scale = act ? s_nw[K][row] : 0.0;
-      // forward: the term's separation and weights at the positions X_s,
-      // s = 0..min(n, nmax), of this lane's body
-      const int top = min(n, nmax);
-      double dxs[kAdjSub + 1][3], ws[kAdjSub + 1], wps[kAdjSub + 1];
-      double X[3], D[3], A[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) X[c] = r[2 + 2 * c + ob];
-      accel(X, A, dxs[0], ws[0], wps[0]);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        D[c] = dd * fma(0.5 * dd, A[c], r[2 + 2 * (3 + c) + ob]);
-        X[c] += D[c];
-      }
-      for (int st = 1; st <= nmax; ++st) {   // at X_st (a shorter row stays at its X_n)
-        double dxt[3], wt, wpt;
-        accel(X, A, dxt, wt, wpt);
-        if (st <= top) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) dxs[st][c] = dxt[c];
-          ws[st] = wt;
-          wps[st] = wpt;
-        }
-        if (st < n) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            D[c] = fma(d2, A[c], D[c]);
-            X[c] += D[c];
+      const int nmax = 2 * (K + 1);
+      const double dd = H * c_bs_inv_n[row], d2 = dd * dd;
+      if ((int)r[14] < 0) {   // no slot: the forward's sub-steps again, into B
+        double X = r[2 + 2 * c + ob];
+        const double V = r[2 + 2 * (3 + c) + ob];
+        int buf = 0;
+        double A = bs2c_accel(tm, c, lane, X, sm, buf, B);
+        double D = dd * fma(0.5 * dd, A, V);
+        X += D;
+        for (int st = 1; st <= nmax; ++st) {
+          A = bs2c_accel(tm, c, lane, X, sm, buf, (st <= n) ? B + (size_t)st * kSubStride : nullptr);
+          if (st < n) {
+            D = fma(d2, A, D);
+            X += D;
           }
         }
+        bs2c_bar();
       }
       // reverse, the rows in lockstep from the longest accepted row down; a
       // lane's own sweep starts at its n (a lane with nothing to do carries
-      // zero cotangents at valid positions, which add nothing)
-      double lX[3], lD[3], lA[3], lYv[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        lX[c] = scale * lO[c];
-        lD[c] = scale * lO[3 + c] / dd;
-        lA[c] = scale * 0.5 * dd * lO[3 + c];   // O_v = D_n/dd + (dd/2) A(X_n)
-        lYv[c] = 0.0;
-      }
+      // zero cotangents at kept positions, which add nothing)
+      const bool act = row <= K;
+      const double scale = act ? s_nw[K][row] : 0.0;
+      const int top = min(n, nmax);
+      double lX = scale * lOp, lD = scale * lOv / dd, lYv = 0.0;
+      const double lA = scale * 0.5 * dd * lOv;   // O_v = D_n/dd + (dd/2) A(X_n)
+      int par = 0;
       for (int st = nmax; st >= 0; --st) {
-        double la[3];
+        double la;
         if (st > top) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) la[c] = 0.0;
+          la = 0.0;
         } else if (st == n) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) la[c] = lA[c];
+          la = lA;
         } else if (st >= 1) {   // X_{s+1} = X_s + D_{s+1}, D_{s+1} = D_s + d2 A(X_s)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            lD[c] += lX[c];
-            la[c] = d2 * lD[c];
-          }
+          lD += lX;
+          la = d2 * lD;
         } else {                // X_1 = X_0 + D_1, D_1 = dd V_0 + (dd^2/2) A(X_0)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            lD[c] += lX[c];
-            lYv[c] = dd * lD[c];
-            la[c] = 0.5 * d2 * lD[c];
-          }
+          lD += lX;
+          lYv = dd * lD;
+          la = 0.5 * d2 * lD;
         }
-        const int sp = min(st, top);
-        vjp(dxs[sp], ws[sp], wps[sp], la, lX);
+        double* xl = s_la + par * 96;
+        xl[c * 32 + lane] = la;
+        bs2c_bar();
+        const double l0 = xl[lane], l1 = xl[32 + lane], l2 = xl[64 + lane];
+        par ^= 1;
+        const double* e = B + (size_t)min(st, top) * kSubStride;
+        const double x0 = e[lane], x1 = e[32 + lane], x2 = e[64 + lane];
+        const double w = e[96 + lane];
+        const double f = adj_wpm2(tm, e[160 + lane], e[128 + lane], w) *
+                         fma(x0, l0, fma(x1, l1, x2 * l2));
+        const double xc = (c == 0) ? x0 : ((c == 1) ? x1 : x2);
+        const double cs = fma(f, xc, -w * la);
+        const double cr = tm.pair ? -cs : 0.0;
+        const double other = __shfl_xor_sync(0xffffffffu, cs, 2);
+        const double react = __shfl_sync(0xffffffffu, cr, src_r);
+        lX += (cs + other) + react;
       }
       // this row's share of the input cotangent, weighted; summed over rows
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        double v = act ? (c < 3 ? lX[c] : lYv[c - 3]) : 0.0;
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        lO[c] = v;
-      }
+      double vp = act ? lX : 0.0, vv = act ? lYv : 0.0;
+      vp += __shfl_xor_sync(0xffffffffu, vp, 4);
+      vv += __shfl_xor_sync(0xffffffffu, vv, 4);
+      vp += __shfl_xor_sync(0xffffffffu, vp, 8);
+      vv += __shfl_xor_sync(0xffffffffu, vv, 8);
+      vp += __shfl_xor_sync(0xffffffffu, vp, 16);
+      vv += __shfl_xor_sync(0xffffffffu, vv, 16);
+      lOp = vp;
+      lOv = vv;
+      bs2c_bar();   // B is read by every warp before the copy of record k - 2 lands in it
     }
-    if (lane == 1)   // body 1: the planetesimal's cotangent at its pre-drift state
-      for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + j] = lO[c];
+    if (lane == 1) {   // body 1: the planetesimal's cotangent at its pre-drift state
+      a.lam[(size_t)c * N + j] = lOp;
+      a.lam[(size_t)(3 + c) * N + j] = lOv;
+    }
     if (lane == 0) {   // body 0: the big body's share
       double* out = a.g_contrib + (size_t)g * 6 * kMaxGroup;
-      for (int c = 0; c < 6; ++c) out[c] = lO[c];
+      out[c] = lOp;
+      out[3 + c] = lOv;
     }
   }
 }
@@ -905,7 +938,8 @@ void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t
 
 void launch_adjoint_bs_vjp(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
   k_adj_bs_vjp<<<nblocks, 32, 0, st>>>(d, a);    // groups of three or more bodies
-  k_adj_bs_vjp2<<<nblocks, 32, 0, st>>>(d, a);   // two-body groups
+  cudaFuncSetAttribute(k_adj_bs_vjp2, cudaFuncAttributeMaxDynamicSharedMemorySize, kVjp2Smem);
+  k_adj_bs_vjp2<<<nblocks, 96, kVjp2Smem, st>>>(d, a);   // two-body groups
 }
 
 void launch_adjoint_bs_fold(const Dev& d, const Adj& a, cudaStream_t st) {

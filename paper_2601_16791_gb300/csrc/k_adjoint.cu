@@ -493,6 +493,27 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
   }
 }
 
+// Sums over a system's tiles of values v < V of their partial records (the
+// system's tiles are consecutive, so record k sits at p0 + k R), into out[v]
+// (shared memory), on a block of kThreads threads.  Each value's tiles are
+// split into P interleaved strands (strand s adds tiles s, s + P, ... in
+// order; P the largest power of two <= 32 with P V <= kThreads), and the
+// strands are added by a fixed butterfly, so the chain of dependent adds is
+// T / P long and the order depends on nothing but V.  Every thread calls it.
+__device__ void fold_tiles(const double* p0, int R, int T, int V, double* out) {
+  int P = 1;
+  while (2 * P <= 32 && 2 * P * V <= kThreads) P *= 2;
+  const int v = threadIdx.x / P, s = threadIdx.x & (P - 1);
+  double acc = 0.0;
+  if (v < V) {
+#pragma unroll 4
+    for (int k = s; k < T; k += P) acc += p0[(size_t)k * R + v];
+  }
+  for (int o = P >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (v < V && s == 0) out[v] = acc;
+  __syncthreads();
+}
+
 // Per system: fold the tile partials of a kick's reverse (fixed order).
 //  kick 2: lam_x(big) += G; lam_P3 = dP_drag + (h/2)/m0 (sum_j lam_x4_j);
 //          lam_v(big) += mu lam_P3.
@@ -501,50 +522,62 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_kick(Dev d, Adj a, int wh
   const int sys = blockIdx.x;
   const SysDev& S = d.sys[sys];
   const int N = d.N;
+  const int t0 = a.sys_tiles[sys], T = a.sys_tiles[sys + 1] - t0;
+  const int nb = S.nbig, R = 3 * nb + 9;
+  const double* p0 = a.part + (T > 0 ? a.poff[t0] : 0);
   __shared__ double tot[9];
   __shared__ double gsum_sh[3];
-  // big position cotangents: for each big, sum over the system's tiles in order
-  double gs[3] = {0, 0, 0};
-  for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
-    double g0 = 0, g1 = 0, g2 = 0;
-    for (int tt = 0; tt < d.ntiles; ++tt) {
-      if (d.tiles[tt].sys != sys) continue;
-      const double* rec = a.part + a.poff[tt];
-      g0 += rec[3 * i];
-      g1 += rec[3 * i + 1];
-      g2 += rec[3 * i + 2];
+  __shared__ double fold[kThreads];
+  if (R <= kThreads) {
+    fold_tiles(p0, R, T, R, fold);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      const int g = S.off + i;
+      for (int c = 0; c < 3; ++c) a.lam[(size_t)c * N + g] += fold[3 * i + c];
     }
-    const int g = S.off + i;
-    a.lam[g] += g0;
-    a.lam[(size_t)N + g] += g1;
-    a.lam[2 * (size_t)N + g] += g2;
-    gs[0] += g0;
-    gs[1] += g1;
-    gs[2] += g2;
-  }
-  if (threadIdx.x < 9) {
-    double sum = 0;
-    for (int tt = 0; tt < d.ntiles; ++tt)
-      if (d.tiles[tt].sys == sys) sum += a.part[a.poff[tt] + 3 * S.nbig + threadIdx.x];
-    tot[threadIdx.x] = sum;
-  }
-  // the bigs' extra position cotangent also enters sum_j lam_x4_j
-  __shared__ double red[3][kThreads];
-  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = gs[c];
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+    if (threadIdx.x < 3) {   // the bigs' extra position cotangent, summed in big order
+      double sum = 0.0;
+      for (int i = 0; i < nb; ++i) sum += fold[3 * i + threadIdx.x];
+      gsum_sh[threadIdx.x] = sum;
+    }
+    if (threadIdx.x < 9) tot[threadIdx.x] = fold[3 * nb + threadIdx.x];
+  } else {
+    // many big bodies: one thread per big body adds its shares in tile order
+    double gs[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      double g0 = 0, g1 = 0, g2 = 0;
+      for (int k = 0; k < T; ++k) {
+        const double* rec = p0 + (size_t)k * R;
+        g0 += rec[3 * i];
+        g1 += rec[3 * i + 1];
+        g2 += rec[3 * i + 2];
+      }
+      const int g = S.off + i;
+      a.lam[g] += g0;
+      a.lam[(size_t)N + g] += g1;
+      a.lam[2 * (size_t)N + g] += g2;
+      gs[0] += g0;
+      gs[1] += g1;
+      gs[2] += g2;
+    }
+    fold_tiles(p0 + 3 * nb, R, T, 9, tot);
+    // the bigs' extra position cotangent also enters sum_j lam_x4_j
+    __shared__ double red[3][kThreads];
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = gs[c];
     __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w)
+        for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x < 3) gsum_sh[threadIdx.x] = red[threadIdx.x][0];
   }
-  if (threadIdx.x < 3) gsum_sh[threadIdx.x] = red[threadIdx.x][0];
   __syncthreads();
   double lP[3];
   for (int c = 0; c < 3; ++c) {
     lP[c] = tot[c];
     if (which == 2) lP[c] += 0.5 * S.h * S.inv_mu0 * (tot[3 + c] + gsum_sh[c]);
   }
-  for (int i = threadIdx.x; i < S.nbig; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     const int g = S.off + i;
     const double m = d.bmu[S.boff + i];
     for (int c = 0; c < 3; ++c) a.lam[(size_t)(3 + c) * N + g] += m * lP[c];
@@ -604,10 +637,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_jump1(Dev d, Adj a) {
   const SysDev& S = d.sys[sys];
   const int N = d.N;
   __shared__ double lP[3];
+  const int t0 = a.sys_tiles[sys], T = a.sys_tiles[sys + 1] - t0;
+  fold_tiles(a.part + (T > 0 ? a.poff[t0] : 0), 3 * S.nbig + 9, T, 3, lP);
   if (threadIdx.x < 3) {
-    double sum = 0;
-    for (int tt = 0; tt < d.ntiles; ++tt)
-      if (d.tiles[tt].sys == sys) sum += a.part[a.poff[tt] + threadIdx.x];
+    double sum = lP[threadIdx.x];
     if (a.groups) sum += a.bs_xsum[3 * sys + threadIdx.x];   // the big bodies' BS shares
     lP[threadIdx.x] = 0.5 * S.h * S.inv_mu0 * sum;
   }

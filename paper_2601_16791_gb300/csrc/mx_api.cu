@@ -198,8 +198,13 @@ struct mx_system {
   unsigned long long* a_goff = nullptr;
   double *a_gcontrib = nullptr, *a_tape = nullptr, *a_bsx = nullptr;
   unsigned long long a_tape_cap = 0;
+  // kept Stoermer sub-steps of two-body records (mx_adjoint_store)
+  double* a_sub = nullptr;
+  unsigned* a_subn = nullptr;
+  unsigned a_sub_cap = 0, a_sub_want = 1u << 14;
   int a_groups = 1;               // mx_adjoint_encounters
   int* a_poff = nullptr;
+  int* a_systiles = nullptr;
   size_t a_part_cap = 0;
   // the adjoint's own tiling (kThreads targets, system order), whatever the
   // forward step's autotuner picked: its kernels are faster on full blocks,
@@ -1718,7 +1723,7 @@ namespace {
 // body of the tile's system plus 9.
 // Encounter groups per adjoint step, and the doubles of their recorded
 // Bulirsch-Stoer sub-steps (each group has room for 128 sub-steps; a
-// two-body group's sub-step takes 14 doubles).
+// two-body group's sub-step takes 15 doubles).
 constexpr int kAdjGroups = 1 << 14;
 constexpr size_t kAdjTape = (size_t)1 << 23;
 
@@ -1731,7 +1736,15 @@ mx::Dev adjoint_dev(const mx_system* s) {
   return d;
 }
 
+mx_status ensure_adjoint_store(mx_system* s) {
+  if (s->a_sub_want == 0 || s->a_sub) return MX_OK;
+  MX_TRY(dalloc(s, &s->a_sub, (size_t)s->a_sub_want * mx::kAdjSubRec));
+  s->a_sub_cap = s->a_sub_want;
+  return MX_OK;
+}
+
 mx_status ensure_adjoint(mx_system* s) {
+  MX_TRY(ensure_adjoint_store(s));
   const int N = s->N;
   if (!s->a_tiles) {
     MX_TRY(dalloc(s, &s->a_x2, (size_t)6 * N));   // x2 and v1: one 6 x N pre-drift state
@@ -1746,6 +1759,7 @@ mx_status ensure_adjoint(mx_system* s) {
     MX_TRY(dalloc(s, &s->a_goff, gcap));
     MX_TRY(dalloc(s, &s->a_gcontrib, (size_t)gcap * mx::kMaxGroup * 6));
     MX_TRY(dalloc(s, &s->a_tape, kAdjTape));
+    MX_TRY(dalloc(s, &s->a_subn, 1));
     MX_TRY(dalloc(s, &s->a_bsx, 3 * s->h_sys.size()));
     s->a_tape_cap = kAdjTape;
     MX_TRY(dalloc(s, &s->a_xv3, (size_t)6 * N));
@@ -1763,6 +1777,12 @@ mx_status ensure_adjoint(mx_system* s) {
     MX_TRY(dalloc(s, &s->a_part, off));
     s->a_part_cap = off;
     MX_TRY(dalloc(s, &s->a_poff, tiles.size()));
+    std::vector<int> systiles(s->h_sys.size() + 1, 0);   // tiles come in system order
+    for (const mx::Tile& t : tiles) systiles[t.sys + 1] += 1;
+    for (size_t k = 1; k < systiles.size(); ++k) systiles[k] += systiles[k - 1];
+    MX_TRY(dalloc(s, &s->a_systiles, systiles.size()));
+    MX_CUDA(cudaMemcpyAsync(s->a_systiles, systiles.data(), systiles.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s->st));
     MX_TRY(dalloc(s, &s->a_tiles, tiles.size()));
     s->a_ntiles = (int)tiles.size();
     MX_CUDA(cudaMemcpyAsync(s->a_poff, poff.data(), poff.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
@@ -1876,6 +1896,20 @@ mx_status mx_adjoint_encounters(mx_system* s, int on) {
   return MX_OK;
 }
 
+mx_status mx_adjoint_store(mx_system* s, long long slots) {
+  if (!s || slots < 0 || slots > (1ll << 20)) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  if (s->a_sub) {   // the pool is replaced at the next adjoint step
+    MX_CUDA(cudaStreamSynchronize(s->st));
+    MX_CUDA(cudaFree(s->a_sub));
+    s->allocs.erase(std::remove(s->allocs.begin(), s->allocs.end(), (void*)s->a_sub), s->allocs.end());
+    s->a_sub = nullptr;
+    s->a_sub_cap = 0;
+  }
+  s->a_sub_want = (unsigned)slots;
+  return MX_OK;
+}
+
 mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_grad_helio) {
   if (!s || !dev_lambda || !dev_grad_helio) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
@@ -1906,6 +1940,7 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   a.lam = dev_lambda;
   a.part = s->a_part;
   a.poff = s->a_poff;
+  a.sys_tiles = s->a_systiles;
   a.P = s->a_P;
   a.dpar = dev_dparams;
   a.step = (int)step_k;
@@ -1922,6 +1957,9 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   a.tape = s->a_tape;
   a.tape_cap = s->a_tape_cap;
   a.bs_xsum = s->a_bsx;
+  a.sub = s->a_sub;
+  a.sub_count = s->a_subn;
+  a.sub_cap = s->a_sub_cap;
   (void)N;
   mx::launch_adjoint_step(adjoint_dev(s), a, s->st);
   return sync_status(s);

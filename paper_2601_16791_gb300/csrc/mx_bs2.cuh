@@ -166,8 +166,12 @@ struct Bs2cSmem {
 
 __device__ __forceinline__ void bs2c_bar() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
 
+// With `rec`, the lane's term at this sub-step is also kept: its separation
+// (coordinate c) in row c and, in row 3 + c, its weight (c = 0), 1/s (c = 1)
+// or s^2 (c = 2), rows of 32 lanes.
 __device__ __forceinline__ double bs2c_accel(const Bs2Term& t, int c, int lane, double X,
-                                             const Bs2cSmem& sm, int& buf) {
+                                             const Bs2cSmem& sm, int& buf,
+                                             double* rec = nullptr) {
   const double xo = __shfl_xor_sync(0xffffffffu, X, 1);
   const double dv = X - (t.pair ? xo : 0.0);
   double* sd = sm.d + buf * 96;
@@ -184,6 +188,10 @@ __device__ __forceinline__ double bs2c_accel(const Bs2Term& t, int c, int lane, 
   } else if (b2 > __double_as_longlong(t.rc2lo)) {
     const double qv = fma(s2, yy, -t.rc01) * t.i09;
     wgt *= fma(-qv * qv * qv, fma(qv, fma(6.0, qv, -15.0), 10.0), 1.0);
+  }
+  if (rec) {
+    rec[c * 32 + lane] = dv;
+    rec[(3 + c) * 32 + lane] = (c == 0) ? wgt : ((c == 1) ? yy : s2);
   }
   const double a = -wgt * dv;
   return a + __shfl_xor_sync(0xffffffffu, a, 2);

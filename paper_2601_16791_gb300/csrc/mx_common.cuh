@@ -193,6 +193,7 @@ struct Adj {
   double* lam;        // 6 x N cotangent, in/out
   double* part;       // per-tile partial sums
   const int* poff;    // [ntiles] offset of each tile's partial record
+  const int* sys_tiles;   // [nsys + 1] first tile of each system (tiles in system order)
   double* P;          // 9 per system: P0, P1, P3
   double* dpar;       // 3 per system, accumulated
   int step;           // index of the step (recorded k branches)
@@ -203,10 +204,20 @@ struct Adj {
   int *g_small, *g_key, *g_nb, *g_M, *g_count;
   unsigned long long* g_off;     // tape offset of each group
   double* g_contrib;             // [g_cap][kMaxGroup][6] big members' cotangents
-  double* tape;                  // accepted sub-steps: H, row, 6 x nb start state
+  double* tape;                  // accepted sub-steps: H, row, 6 x nb start state, slot
   unsigned long long tape_cap;   // doubles
   double* bs_xsum;               // 3 per system: sum of the big shares' position parts
+  // two-body groups: the Stoermer sub-steps of each accepted macro sub-step,
+  // kAdjSubRec doubles a slot (null: none are kept, the reverse recomputes)
+  double* sub;
+  unsigned* sub_count;           // slots handed out in this step
+  unsigned sub_cap;              // slots
 };
+
+// One slot of kept Stoermer sub-steps: sub-steps 0..16, each six rows of 32
+// lanes (separation x, y, z, force weight, 1/s, s^2 of the lane's term).
+constexpr int kAdjSubVals = 6;
+constexpr int kAdjSubRec = 17 * kAdjSubVals * 32;
 
 // ------------------------------------------------------------------ helpers
 // On this part FP64 instructions (conversions included) issue at ~1/60 of the

@@ -100,6 +100,7 @@ _SIGS = {
     "mx_elements": (_I, [_P, _P]),
     "mx_set_growth": (_I, [_P, _I, _P, _D]),
     "mx_adjoint_encounters": (_I, [_P, _I]),
+    "mx_adjoint_store": (_I, [_P, ctypes.c_longlong]),
     "mx_planets": (_I, [_P, _P, _P]),
 }
 

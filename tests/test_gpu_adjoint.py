@@ -201,3 +201,23 @@ def test_adjoint_does_not_depend_on_the_forward_tiling():
     for o in out[1:]:
         assert o[0] == out[0][0] and np.array_equal(o[1], out[0][1]) and np.array_equal(o[2], out[0][2])
     traj.close()
+
+
+def test_adjoint_kept_and_recomputed_substeps_agree_bitwise():
+    """The reverse of a two-body group reads the Stoermer sub-steps the
+    forward kept, or recomputes them when the pool is used up: with the
+    default pool, a pool of one chunk (8 slots: the first records kept, the
+    rest recomputed) and no pool, the loss and gradient through the groups are
+    the same to the bit."""
+    w, traj, xv0, gas, wts = _setup(nsmall=300, nsteps=40, every=10)
+    out = []
+    for slots in (1 << 14, 8, 0):
+        mx._check(mx.load().mx_adjoint_store(traj.h, slots), "mx_adjoint_store")
+        out.append(_grad(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every, mask=False))
+    ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(traj.h, ever)
+    assert ever.cpu().numpy()[w.nbig:].sum() > 0
+    for o in out[1:]:
+        assert o[0] == out[0][0] and np.array_equal(o[1], out[0][1]) and np.array_equal(o[2], out[0][2])
+    assert np.abs(out[0][1]).max() > 0
+    traj.close()
