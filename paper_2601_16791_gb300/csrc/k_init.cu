@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kThreads) k_init_sys(Dev d, int do_rcrit, doub
       const double r = sqrt(x * x + y * y + z * z);
       double a = 1.0 / (2.0 / r - (u * u + v * v + w * w) / (S.mu0 + mu));
       if (!(a > 0.0)) a = r;
-      d.brc[S.boff + i] = rcrit_hill * a * cbrt(mu / (3.0 * S.mu0));
+      set_rcrit(d, S.boff + i, rcrit_hill * a * cbrt(mu / (3.0 * S.mu0)));
     }
   }
   for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];

@@ -709,6 +709,7 @@ mx_status build(mx_system* s, const std::vector<const double*>& m_big,
   MX_TRY(dalloc(s, &d.bz, NB));
   MX_TRY(dalloc(s, &d.bmu, NB));
   MX_TRY(dalloc(s, &d.brc, NB));
+  MX_TRY(dalloc(s, &d.brc4, 4 * (size_t)NB));
   MX_TRY(dalloc(s, &d.P, 3 * (size_t)nsys));
   MX_TRY(dalloc(s, &d.bk, 6 * (size_t)NB));
   MX_TRY(dalloc(s, &d.arrive, 1));

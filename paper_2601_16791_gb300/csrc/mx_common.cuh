@@ -93,6 +93,7 @@ struct Dev {
   double* rp_cm;   // N
   double* kdrag;   // N
   double *bx, *by, *bz, *bmu, *brc;   // NB
+  double* brc4;    // 4 x NB: rc^2, 0.01 rc^2, 0.1 rc, 1/(0.9 rc) of each big body (set_rcrit)
   double* P;       // 3 x nsys
   double* bk;      // 6 x NB: big bodies after the latest kick, the drift's source for them
   int* arrive;     // [1] blocks of a kick with its own prep that have read the history slot
@@ -274,6 +275,17 @@ __device__ __forceinline__ double rcp_d(double x) {
 // high word with integer instructions, off the FP64 pipe.
 __device__ __forceinline__ bool finite_d(double a) {
   return (__double2hiint(a) & 0x7ff00000) != 0x7ff00000;
+}
+
+// A big body's changeover radius and the constants the pair weight takes
+// from it (rc^2, 0.01 rc^2, 0.1 rc, 1/(0.9 rc), as the kick's staging had
+// computed them per block), so that the kick only loads them.
+__device__ __forceinline__ void set_rcrit(const Dev& d, int b, double rc) {
+  d.brc[b] = rc;
+  d.brc4[b] = rc * rc;
+  d.brc4[(size_t)d.NB + b] = 0.01 * (rc * rc);
+  d.brc4[2 * (size_t)d.NB + b] = 0.1 * rc;
+  d.brc4[3 * (size_t)d.NB + b] = (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
 }
 
 // A body removed from the integration (Sec. 3.5).  Detection also runs on

@@ -85,7 +85,7 @@ __device__ __forceinline__ void grow_update(const Dev& d, const SysDev& S, doubl
     big_rv2(d, S, i, P, &r, &v2, &R);
     const double rh = semimajor_or_r(S.mu0 + mu, r, v2) * cbrt(mu / (3.0 * S.mu0));
     d.bmu[b] = mu;
-    d.brc[b] = S.rcrit_hill * rh;
+    set_rcrit(d, b, S.rcrit_hill * rh);
     const bool runaway = t > G.tc;
     d.gap_w[b] = runaway ? S.gap_c * rh : 0.0;
     d.gap_f[b] = runaway ? exp(-(t - G.tc) / G.tg) : 1.0;

@@ -10,12 +10,18 @@ namespace mx {
 
 
 // Big positions come from k_prep's copy (d.bx), or, with `dj` (a kick that
-// makes its own prep), from the state plus the jump.
+// makes its own prep), from the state plus the jump.  The block's last warp
+// takes the first bodies: warp 0 makes the momentum sum of a fused kick, and
+// the warps of a block share the four warp schedulers in order, so the two
+// pieces of per-block work land on different schedulers.
 __device__ __forceinline__ void stage_bigs(const Dev& d, const SysDev& S, int c0, int cn,
                                            BigSmem& sb, const double* dj) {
-  for (int k = threadIdx.x; k < cn; k += blockDim.x) {
+  const int first = (blockDim.x > 32) ? (int)blockDim.x - 32 : 0;
+  for (int r = threadIdx.x; r < cn + first; r += blockDim.x) {
+    const int k = r - first;   // threads [first, blockDim) take k = 0, 1, ...
+    if (k < 0) continue;
     const int b = S.boff + c0 + k;
-    const double rc = d.brc[b];
+    const size_t NB = d.NB;
     if (dj) {
       const size_t g = (size_t)S.off + c0 + k;
       sb.x[k] = d.xv[g] + dj[0];
@@ -27,11 +33,11 @@ __device__ __forceinline__ void stage_bigs(const Dev& d, const SysDev& S, int c0
       sb.z[k] = d.bz[b];
     }
     sb.mu[k] = d.bmu[b];
-    sb.rc[k] = rc;
-    sb.rc2[k] = rc * rc;
-    sb.rc2lo[k] = 0.01 * (rc * rc);
-    sb.rc01[k] = 0.1 * rc;
-    sb.i09rc[k] = (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
+    sb.rc[k] = d.brc[b];
+    sb.rc2[k] = d.brc4[b];
+    sb.rc2lo[k] = d.brc4[NB + b];
+    sb.rc01[k] = d.brc4[2 * NB + b];
+    sb.i09rc[k] = d.brc4[3 * NB + b];
   }
 }
 
@@ -88,8 +94,12 @@ __device__ __forceinline__ void system_momentum(const Dev& d, const SysDev& S,
     if (threadIdx.x < 32) {
       double p[3];
       partial(threadIdx.x, p);
+      // a level whose offset s >= nbig adds lanes holding +0 to every lane
+      // below s (a partial is never -0: it starts at +0), which changes no
+      // bit, so it is skipped
       for (int s = 16; s > 0; s >>= 1)
-        for (int c = 0; c < 3; ++c) p[c] += __shfl_down_sync(0xffffffffu, p[c], s);
+        if (s < S.nbig)
+          for (int c = 0; c < 3; ++c) p[c] += __shfl_down_sync(0xffffffffu, p[c], s);
       if (threadIdx.x == 0)
         for (int c = 0; c < 3; ++c) out[c] = p[c];
     }
@@ -184,18 +194,59 @@ __device__ __forceinline__ void prep_system(const Dev& d, double jump_frac, int 
 // counters.  Those blocks read the history slot before they arrive, and the
 // last of them to arrive moves the slot on (no block waits for another).
 struct FusedPrep {
-  double P[3];
+  double P[3], dj[3], hp[3];   // P, the jump (jump_vec at jump_frac), P/m0
 };
 
+// P of a fused kick, its jump (jump_vec) and P/m0, into shared memory.  With
+// at most 32 big bodies, component c is summed by warp c mod (warps) with
+// system_momentum's partials and tree (the same bits), and the same warp
+// forms its jump and P/m0 component: the block's few per-block instructions
+// are spread over its warps, which sit on different warp schedulers.  With
+// more, system_momentum.  Every thread of the block must call it; ends with a
+// block barrier.
+__device__ __forceinline__ void fused_momentum(const Dev& d, const SysDev& S, double jump_frac,
+                                               double (*red)[kThreads], double* sP, double* sdj,
+                                               double* shp) {
+  const int N = d.N;
+  const double cj = (jump_frac * S.h) * S.inv_mu0;
+  if (S.nbig <= 32) {
+    const int nw = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (int c = warp; c < 3; c += nw) {
+      double p = 0.0;
+      if (lane < S.nbig) p = fma(d.bmu[S.boff + lane], d.xv[(size_t)(3 + c) * N + S.off + lane], p);
+      for (int s = 16; s > 0; s >>= 1)
+        if (s < S.nbig) p += __shfl_down_sync(0xffffffffu, p, s);
+      if (lane == 0) {
+        sP[c] = p;
+        sdj[c] = cj * p;
+        shp[c] = p * S.inv_mu0;
+      }
+    }
+  } else {
+    system_momentum(d, S, red, sP);
+    if (threadIdx.x < 3) {
+      sdj[threadIdx.x] = cj * sP[threadIdx.x];
+      shp[threadIdx.x] = sP[threadIdx.x] * S.inv_mu0;
+    }
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ FusedPrep fused_prep(const Dev& d, const SysDev& S, const Tile& t,
-                                                int nkick, double (*red)[kThreads]) {
-  __shared__ double s_P[3];
+                                                int nkick, double jump_frac,
+                                                double (*red)[kThreads]) {
+  __shared__ double s_P[3], s_dj[3], s_hp[3];
   __shared__ int s_slot;
   const bool head = t.start == S.off;
   if (head && threadIdx.x == 0) s_slot = d.defer ? *(volatile int*)d.hstep : 0;
-  system_momentum(d, S, red, s_P);   // ends with a block barrier
+  fused_momentum(d, S, jump_frac, red, s_P, s_dj, s_hp);   // ends with a block barrier
   FusedPrep f;
-  for (int c = 0; c < 3; ++c) f.P[c] = s_P[c];
+  for (int c = 0; c < 3; ++c) {
+    f.P[c] = s_P[c];
+    f.dj[c] = s_dj[c];
+    f.hp[c] = s_hp[c];
+  }
   if (!head) return f;
   const int slot = s_slot;
   const int sysi = t.sys;
@@ -264,16 +315,21 @@ __device__ __forceinline__ void jump_kick_tile(const Dev& d, double jump_frac, d
   const Tile t = d.tiles[bid];
   const SysDev& S = d.sys[t.sys];
   const int N = d.N;
-  double Pv[3], dj[3];
+  double dj[3], hp[3];
   if constexpr (FUSED) {
-    const FusedPrep f = fused_prep(d, S, t, NKICK, reinterpret_cast<double(*)[kThreads]>(dsm));
-    for (int c = 0; c < 3; ++c) Pv[c] = f.P[c];
+    const FusedPrep f =
+        fused_prep(d, S, t, NKICK, jump_frac, reinterpret_cast<double(*)[kThreads]>(dsm));
+    for (int c = 0; c < 3; ++c) {
+      dj[c] = f.dj[c];
+      hp[c] = f.hp[c];
+    }
   } else {
-    for (int c = 0; c < 3; ++c) Pv[c] = d.P[3 * t.sys + c];
+    const double* Pv = d.P + 3 * t.sys;
     // the last kernel of a history slot moves on to the next one
     if (d.defer && bid == 0 && threadIdx.x == 0) *d.hstep += 1;
+    jump_vec(Pv, S, jump_frac, dj);
+    for (int c = 0; c < 3; ++c) hp[c] = Pv[c] * S.inv_mu0;
   }
-  jump_vec(Pv, S, jump_frac, dj);
   const double kick_h = kick_frac * S.h;
   const int j = t.start + threadIdx.x;
   // a deferred planetesimal is kicked by the window's catch-up instead; a
@@ -300,7 +356,7 @@ __device__ __forceinline__ void jump_kick_tile(const Dev& d, double jump_frac, d
     d.xv[2 * (size_t)N + j] = z;
   }
   const bool drag = S.gas_on && !big;
-  const double hp0 = Pv[0] * S.inv_mu0, hp1 = Pv[1] * S.inv_mu0, hp2 = Pv[2] * S.inv_mu0;
+  const double hp0 = hp[0], hp1 = hp[1], hp2 = hp[2];
   const double rp = drag ? d.rp_cm[j] : 0.0, kd = drag ? d.kdrag[j] : 0.0;
   const int kbase = d.kmode ? d.kick_ctr[1] : 0;
   // the gas at the (fixed) position, shared by the launch's half kicks

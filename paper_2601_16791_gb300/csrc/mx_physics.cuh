@@ -203,23 +203,31 @@ __device__ __forceinline__ void gas_drag(const SysDev& S, double x, double y, do
 
 // f = mu K(s)/s^3 for one pair at separation d (Sec. 2.1.3: K = 1 for
 // s^2 >= rc^2, 0 for s^2 <= 0.01 rc^2, quintic between).
+// mu/s^3 comes straight from the single-precision estimate y of 1/s (relative
+// error ~1e-6, as in rsqrt_d): with e = 1 - s^2 y^2 (y^2 is exact, y having
+// 24 significant bits), 1/s^3 = y^3 (1 - e)^(-3/2) = y^3 (1 + 3e/2 + 15e^2/8),
+// the dropped terms ~2 e^3 below the FP64 rounding; 1/s itself (for the
+// changeover shell only) is y (1 + e/2 + 3e^2/8), as rsqrt_d makes it.
 __device__ __forceinline__ double pair_weight(double dx, double dy, double dz, double mu,
                                               double rc2, double rc2lo, double rc01,
                                               double i09rc) {
   const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
-  const double yy = rsqrt_d(s2);
-  double f = yy * yy * yy;
+  const double y = float_to_double_bits(rsqrtf(abs_to_float_bits(s2)));
+  const double y2 = y * y;
+  const double e = fma(-s2, y2, 1.0);
+  double f = ((mu * y) * y2) * fma(e, fma(1.875, e, 1.5), 1.0);
   // s2 < rc2 decided on the bit patterns: for non-negative doubles the integer
   // order is the value order, and the compare leaves the FP64 pipe free
   if (__double_as_longlong(s2) < __double_as_longlong(rc2)) {
     if (s2 <= rc2lo) {
       f = 0.0;
     } else {
+      const double yy = fma(y * e, fma(0.375, e, 0.5), y);
       const double q = (s2 * yy - rc01) * i09rc;
       f *= q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
     }
   }
-  return f * mu;
+  return f;
 }
 
 // The pair's acceleration -f d accumulated into (ax, ay, az).
