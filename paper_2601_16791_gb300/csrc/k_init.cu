@@ -81,6 +81,17 @@ __global__ void __launch_bounds__(kThreads) k_readout(Dev d, double* out) {
   }
 }
 
+// The step counter and the half-kick counters at step `step` (kernel
+// arguments, so that setting them takes no host-to-device copy).
+__global__ void k_set_step(Dev d, long long step) {
+  d.kick_ctr[0] = d.kick_ctr[1] = (int)(2 * step);
+  d.gstep[0] = step;
+}
+
+void launch_set_step(const Dev& d, long long step, cudaStream_t st) {
+  k_set_step<<<1, 1, 0, st>>>(d, step);
+}
+
 void launch_init_sys(const Dev& d, int do_rcrit, double rcrit_hill, cudaStream_t st) {
   k_init_sys<<<d.nsys, kThreads, 0, st>>>(d, do_rcrit, rcrit_hill);
 }

@@ -1562,9 +1562,7 @@ mx_status mx_set_state(mx_system* s, const double* xv_host, int coords, long lon
     mx::launch_init_sys(s->d, 0, 0.0, s->st);
     mx::launch_init_bodies(s->d, nullptr, nullptr, 0, s->st);
   }
-  const int ctr[2] = {(int)(2 * step), (int)(2 * step)};
-  MX_CUDA(cudaMemcpyAsync(s->d.kick_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s->st));
-  MX_CUDA(cudaMemcpyAsync(s->d.gstep, &step, sizeof(long long), cudaMemcpyHostToDevice, s->st));
+  mx::launch_set_step(s->d, step, s->st);
   MX_TRY(sync_status(s));
   s->step = step;
   return MX_OK;
@@ -1869,9 +1867,7 @@ mx_status mx_encounter_log(mx_system* s, unsigned char* dev_ever, long long* n_b
 mx_status mx_set_step_index(mx_system* s, long long step) {
   if (!s || step < 0 || step > (1LL << 29)) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
-  const int ctr[2] = {(int)(2 * step), (int)(2 * step)};
-  MX_CUDA(cudaMemcpyAsync(s->d.kick_ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s->st));
-  MX_CUDA(cudaMemcpyAsync(s->d.gstep, &step, sizeof(long long), cudaMemcpyHostToDevice, s->st));
+  mx::launch_set_step(s->d, step, s->st);
   MX_CUDA(cudaStreamSynchronize(s->st));
   s->step = step;
   return MX_OK;

@@ -16,6 +16,7 @@ void configure_orbit();
 
 // k_init.cu / k_misc.cu
 void launch_init_sys(const Dev& d, int do_rcrit, double rcrit_hill, cudaStream_t st);
+void launch_set_step(const Dev& d, long long step, cudaStream_t st);
 void launch_init_bodies(const Dev& d, const double* rp_km, const double* rho, int set_drag,
                         cudaStream_t st);
 void launch_readout(const Dev& d, double* out, cudaStream_t st);
