@@ -493,6 +493,8 @@ __device__ int bs_rounds(unsigned gmask, int base, int lane, double mu0, const d
   return (g.rem == 0.0) ? 1 : 0;
 }
 
+// The members' masses and changeover constants (a big body's from set_rcrit's
+// table, the same bits as computed here from r_c; a planetesimal has none).
 template <int NB>
 __device__ __forceinline__ void load_members(const Dev& d, const SysDev& S, int o0, double* mu,
                                              MemberK* K) {
@@ -500,13 +502,14 @@ __device__ __forceinline__ void load_members(const Dev& d, const SysDev& S, int 
   for (int m = 0; m < NB; ++m) {
     const int g = d.work_mem[o0 + m];
     const int l = g - S.off;
-    const double rc = (l < S.nbig) ? d.brc[S.boff + l] : 0.0;
-    mu[m] = (l < S.nbig) ? d.bmu[S.boff + l] : 0.0;
-    K[m].rc = rc;
-    K[m].rc2 = rc * rc;
-    K[m].rc2lo = 0.01 * (rc * rc);
-    K[m].rc01 = 0.1 * rc;
-    K[m].i09 = (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0;
+    const bool big = l < S.nbig;
+    const size_t b = (size_t)S.boff + (big ? l : 0);
+    mu[m] = big ? d.bmu[b] : 0.0;
+    K[m].rc = big ? d.brc[b] : 0.0;
+    K[m].rc2 = big ? d.brc4[b] : 0.0;
+    K[m].rc2lo = big ? d.brc4[d.NB + b] : 0.0;
+    K[m].rc01 = big ? d.brc4[2 * (size_t)d.NB + b] : 0.0;
+    K[m].i09 = big ? d.brc4[3 * (size_t)d.NB + b] : 0.0;
   }
 }
 
@@ -933,6 +936,7 @@ __device__ void pack_tail(const Dev& d, int w, unsigned gmask, int base, int lan
   }
   if (slot >= d.cont_cap) {   // list full or no spread phase: finish here
     const int r2 = finish_here(g);
+    if (r2 == 2) return;   // the caller finishes the group itself
     if (lane == base) {
       if (r2 < 0) atomicOr(d.status, ST_BS);
       d.work_nsub[w] = g.nsub;
@@ -977,6 +981,7 @@ __device__ __noinline__ void pack_group(const Dev& d, int w, unsigned gmask, int
 }
 
 __device__ void pack_two(const Dev& d, int w, int lane);
+__device__ void pack_two_pair(const Dev& d, int a, int b, int lane);
 __device__ __noinline__ void thread_group(const Dev& d, int w);
 
 // Two-body groups, one per warp (term lanes, one candidate).
@@ -989,16 +994,37 @@ __global__ void __launch_bounds__(32) k_bs_pack2(Dev d) {
 // Every group, one per warp, in one launch: two bodies on term lanes, three
 // or four on the lane integrator (eight lanes), more on one thread.  Used
 // with deferral on, where nothing is handed to a spread phase.
+__device__ __forceinline__ void bs_one_warp(const Dev& d, int w, int lane) {
+  const int nb = d.work_off[w + 1] - d.work_off[w];
+  if (nb == 2) pack_two(d, w, lane);
+  else if (nb == 3) { if (lane < 8) pack_group<3>(d, w, 0xffu, 0, lane); }
+  else if (nb == 4) { if (lane < 8) pack_group<4>(d, w, 0xffu, 0, lane); }
+  else if (nb > kLaneMaxNB && lane == 0) thread_group(d, w);
+  __syncwarp();
+}
+
+// A two-body group whose planetesimal may be deferred: with deferral on,
+// pack_two makes one try and gives it up at row kDeferRow, so only rows
+// 0..kDeferRow of its lanes ever count.
+__device__ __forceinline__ bool two_deferrable(const Dev& d, int w) {
+  return d.defer && d.work_off[w + 1] - d.work_off[w] == 2 && d.work_wfrom[w] == 1 &&
+         d.sys[d.work_sys[w]].nbig <= kDeferMaxBig;
+}
+
+// The work items go to the warps in pairs (2s, 2s + 1).  A pair of deferrable
+// two-body groups shares the warp (pack_two_pair, 16 lanes each); any other
+// pair is taken one item after the other.
 __device__ __forceinline__ void bs_all_warps(const Dev& d, int w0, int nw) {
   const int W = *d.work_count;
   const int lane = threadIdx.x & 31;
-  for (int w = w0; w < W; w += nw) {
-    const int nb = d.work_off[w + 1] - d.work_off[w];
-    if (nb == 2) pack_two(d, w, lane);
-    else if (nb == 3) { if (lane < 8) pack_group<3>(d, w, 0xffu, 0, lane); }
-    else if (nb == 4) { if (lane < 8) pack_group<4>(d, w, 0xffu, 0, lane); }
-    else if (nb > kLaneMaxNB && lane == 0) thread_group(d, w);
-    __syncwarp();
+  for (int sp = w0; 2 * sp < W; sp += nw) {
+    const int a = 2 * sp, b = 2 * sp + 1;
+    if (b < W && two_deferrable(d, a) && two_deferrable(d, b)) {
+      pack_two_pair(d, a, b, lane);
+    } else {
+      bs_one_warp(d, a, lane);
+      if (b < W) bs_one_warp(d, b, lane);
+    }
   }
 }
 
@@ -1027,6 +1053,185 @@ __device__ void pack_two(const Dev& d, int w, int lane) {
   pack_tail<2>(d, w, 0xffffffffu, 0, lane, o0, r, g, [&](GroupRun<2>& gg) {
     return bs2_rounds<1>(0, lane, t, d.bs_tol, d.bs_max_sub, 1 << 30, gg, nullptr, nullptr);
   });
+}
+
+// bs2_check on the 16 lanes of half `hs` (0 or 16) of the warp: the lowest
+// converged row of that half.  Every lane of the warp calls it.
+__device__ __forceinline__ int bs2_check_half(int K, int row, int hs, double sc, double tol2,
+                                              const double (&Traw)[3], double (&T)[3]) {
+  double Tp[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) T[c] = Tp[c] = Traw[c];
+#pragma unroll
+  for (int j = 1; j <= kDeferRow; ++j) {
+    if (j > K) break;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double up = __shfl_up_sync(0xffffffffu, T[c], 4);
+      if (row >= j && row <= K) {
+        if (row == j) Tp[c] = T[c];
+        T[c] = fma(T[c] - up, c_bs_inv_den[row][j], T[c]);
+      }
+    }
+  }
+  double e = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double dx = T[c] - Tp[c];
+    e = fma(dx, dx, e);
+  }
+  e *= sc;
+  long long eb = __double_as_longlong(e);
+  eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 1));
+  eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 2));
+  const bool conv = row >= 1 && row <= K && eb <= __double_as_longlong(tol2);
+  const unsigned v = (__ballot_sync(0xffffffffu, conv) >> hs) & 0xffffu;
+  return v ? ((__ffs(v) - 1) >> 2) : -1;
+}
+
+// One round of bs2_rounds<1> (max_rounds 1, stop_row kDeferRow) on the 16
+// lanes of this lane's half of the warp: lane 16h + 4r + q holds row r <=
+// kDeferRow and force term q of the half's group.  The arithmetic of every
+// row and check is bs2_rounds' own, so the round returns what bs2_rounds
+// returns and leaves g as it leaves it.  The halves run in lockstep (every
+// shuffle and vote takes the whole warp) until both have decided.
+__device__ int bs2_half_round(int lane, const Bs2Term& t, double tol, int max_sub,
+                              GroupRun<2>& g) {
+  const int hs = lane & 16, row = (lane >> 2) & 3, q = lane & 3, ob = q & 1;
+  const bool vel = q >= 2;
+  const int n = 2 * (row + 1);
+  const double tol2 = tol * tol;
+  int res = 2;   // 2: the try decides
+  if (g.rem == 0.0) res = 1;
+  else if (g.nsub >= max_sub) res = -1;
+  if (res == 2 && fabs(g.H) > fabs(g.rem)) g.H = g.rem;
+  const double Hc = g.H * pow2_neg(0);
+  double X[3], V[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    X[c] = ob ? g.Y[c][1] : g.Y[c][0];
+    V[c] = ob ? g.Y[3 + c][1] : g.Y[3 + c][0];
+  }
+  const double s0 = vel ? V[0] : X[0], s1 = vel ? V[1] : X[1], s2v = vel ? V[2] : X[2];
+  const double sc = rcp_d(fma(s0, s0, fma(s1, s1, s2v * s2v)));
+  const double dd = Hc * c_bs_inv_n[row];
+  const double d2 = dd * dd;
+  double A[3], D[3], Traw[3] = {0.0, 0.0, 0.0}, T[3], Tacc[3] = {0.0, 0.0, 0.0};
+  bs2_accel(t, X, A);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    D[c] = dd * fma(0.5 * dd, A[c], V[c]);
+    X[c] += D[c];
+  }
+  int acc_r = -1;
+  bool done = res != 2;
+  for (int s = 1; s <= 2 * (kDeferRow + 1); ++s) {
+    if (__all_sync(0xffffffffu, done)) break;
+    bs2_accel(t, X, A);
+    if (s < n) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        D[c] = fma(d2, A[c], D[c]);
+        X[c] += D[c];
+      }
+    } else if (s == n) {
+      const double idd = n * rcp_d(Hc);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Traw[c] = vel ? fma(D[c], idd, 0.5 * dd * A[c]) : X[c];
+    }
+    const int K = (s >> 1) - 1;   // the row that completed at this sub-step
+    if ((s & 1) || !((kBs2Checks >> K) & 1u)) continue;
+    const int r = bs2_check_half(K, row, hs, sc, tol2, Traw, T);
+    if (!done) {
+      if (r >= 0) {
+        acc_r = r;
+        done = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Tacc[c] = T[c];
+      } else if (K >= kDeferRow) {
+        done = true;   // handed over before the round is decided: g is as it was
+      }
+    }
+  }
+  // the accepted row's lanes hold x0, x1 (q = 0, 1) and v0, v1 (q = 2, 3)
+  const int src = hs + 4 * (acc_r >= 0 ? acc_r : 0);
+  double Yn[6][2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Yn[c][0] = __shfl_sync(0xffffffffu, Tacc[c], src + 0);
+    Yn[c][1] = __shfl_sync(0xffffffffu, Tacc[c], src + 1);
+    Yn[3 + c][0] = __shfl_sync(0xffffffffu, Tacc[c], src + 2);
+    Yn[3 + c][1] = __shfl_sync(0xffffffffu, Tacc[c], src + 3);
+  }
+  if (res != 2) return res;
+  if (acc_r < 0) return 0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    g.Y[c][0] = Yn[c][0];
+    g.Y[c][1] = Yn[c][1];
+  }
+  g.nsub += 1;
+  if (g.nsub > max_sub) return -1;
+  const double Hacc = g.H * pow2_neg(0);
+  g.rem -= Hacc;
+  g.H = 1.3 * Hacc;
+  return (g.rem == 0.0) ? 1 : 0;
+}
+
+// Two deferrable two-body groups a and b on one warp, 16 lanes each (lanes
+// 0-15: a, 16-31: b): pack_two's round on the half (bs2_half_round), then
+// pack_tail.  A group pack_tail would finish in the step (the record banks
+// full) is finished afterwards by the whole warp from where its half left it,
+// as pack_two finishes it.
+__device__ void pack_two_pair(const Dev& d, int a, int b, int lane) {
+  const int hs = lane & 16;
+  const int w = hs ? b : a;
+  const int o0 = d.work_off[w];
+  const SysDev& S = d.sys[d.work_sys[w]];
+  double mu[2];
+  MemberK K[2];
+  load_members<2>(d, S, o0, mu, K);
+  const Bs2Term t = bs2_term(lane & 3, S.mu0, mu, K);
+  GroupRun<2> g;
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g.Y[c][m] = d.xv0[(size_t)c * d.N + d.work_mem[o0 + m]];
+  g.rem = S.h;
+  g.H = S.h;
+  g.nsub = 0;
+  const int r = bs2_half_round(lane, t, d.bs_tol, d.bs_max_sub, g);
+  bool fin = false;
+  pack_tail<2>(d, w, 0xffffu << hs, hs, lane, o0, r, g, [&](GroupRun<2>&) {
+    fin = true;
+    return 2;
+  });
+  const unsigned fins = __ballot_sync(0xffffffffu, fin && (lane & 15) == 0);
+  for (int h = 0; h < 32; h += 16) {
+    if (!(fins & (1u << h))) continue;
+    const int wf = h ? b : a;
+    const int of = d.work_off[wf];
+    const SysDev& Sf = d.sys[d.work_sys[wf]];
+    double muf[2];
+    MemberK Kf[2];
+    load_members<2>(d, Sf, of, muf, Kf);
+    const Bs2Term tf = bs2_term(lane & 3, Sf.mu0, muf, Kf);
+    GroupRun<2> gf;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) gf.Y[c][m] = __shfl_sync(0xffffffffu, g.Y[c][m], h);
+    gf.rem = __shfl_sync(0xffffffffu, g.rem, h);
+    gf.H = __shfl_sync(0xffffffffu, g.H, h);
+    gf.nsub = __shfl_sync(0xffffffffu, g.nsub, h);
+    const int r2 = bs2_rounds<1>(0, lane, tf, d.bs_tol, d.bs_max_sub, 1 << 30, gf, nullptr, nullptr);
+    if (lane == 0) {
+      if (r2 < 0) atomicOr(d.status, ST_BS);
+      d.work_nsub[wf] = gf.nsub;
+    }
+    write_members<2>(d, wf, of, lane, gf);
+  }
+  __syncwarp();
 }
 
 // Two-body groups handed over by k_bs_pack2: one per block of four warps,
@@ -1870,7 +2075,7 @@ void launch_groups(const Dev& d, cudaStream_t st) { k_groups<<<1, 1024, 0, st>>>
 void launch_bs(const Dev& d, int nblocks, cudaStream_t st) {
   // (a group has at least two members: one big body and the body it meets)
   if (d.defer) {   // no spread phase: one launch
-    k_bs_all<<<4 * nblocks, 32, 0, st>>>(d);
+    k_bs_all<<<nblocks, 32, 0, st>>>(d);   // one wave; pairs of groups per warp
     return;
   }
   cudaMemsetAsync(d.cont_count, 0, sizeof(int), st);
