@@ -82,6 +82,7 @@ def lib():
             "orc_gas_state": (_I, [_P, _D, _P]),
             "orc_drag_cd": (_D, [_D, _D, _I]),
             "orc_dg_series": (_D, [_D]),
+            "orc_dg_series_dgamma": (_D, [_D]),
             "orc_disk_gravity": (_I, [_P, _P, _P]),
             "orc_drag_one": (_I, [_P, _P, _P, _D, _D, _P, _P]),
             "orc_stumpff": (None, [_D, _P]),
@@ -219,6 +220,11 @@ def drag_cd(Re, Ma, mode=0):
 def dg_series(gamma):
     """S(gamma) of Eq. 10: F_DG = 2 pi G Sigma(r) S(gamma) for gamma != 1."""
     return lib().orc_dg_series(float(gamma))
+
+
+def dg_series_dgamma(gamma):
+    """dS/dgamma of the disk-gravity series S(gamma) of Eq. 10, summed term by term."""
+    return lib().orc_dg_series_dgamma(float(gamma))
 
 
 def disk_gravity(p, x3):

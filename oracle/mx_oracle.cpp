@@ -314,7 +314,11 @@ void drag_one(const GasT<T>& g, double mu0, const T* x, const T* vh, double rp_k
 // (eight levels).  Reading: F_DG is the signed radial force per unit mass in the
 // midplane (positive outward), applied along the cylindrical radius; it acts
 // on planetesimals only, where there is gas (r >= R_in).
-double dg_series(double gamma) {
+// With deriv = 1 the same sums give dS/dgamma, term by term: with
+// a = 2n + 2 - gamma and b = 2n - 1 + gamma, d/dgamma [(1 - gamma)/(a b)] =
+// [-a b + (1 - gamma)(b - a)]/(a b)^2; those terms fall off as -1/(pi n^2),
+// so the same extrapolation applies.
+double dg_series_sum(double gamma, int deriv) {
   const int levels = 8;
   double S[levels];
   double sum = 0.0, comp = 0.0;      // compensated (Kahan) sum of the terms
@@ -325,8 +329,14 @@ double dg_series(double gamma) {
     for (; n < N; ++n) {
       if (n > 0) An_root *= (2.0 * n - 1.0) / (2.0 * n);
       const double An = An_root * An_root;
-      const double t = An * (1.0 - gamma) * (4.0 * n + 1.0) /
-                       ((2.0 * n + 2.0 - gamma) * (2.0 * n - 1.0 + gamma));
+      double t;
+      if (!deriv) {
+        t = An * (1.0 - gamma) * (4.0 * n + 1.0) /
+            ((2.0 * n + 2.0 - gamma) * (2.0 * n - 1.0 + gamma));
+      } else {
+        const double a = 2.0 * n + 2.0 - gamma, b = 2.0 * n - 1.0 + gamma;
+        t = An * (4.0 * n + 1.0) * (-(a * b) + (1.0 - gamma) * (b - a)) / ((a * b) * (a * b));
+      }
       const double y = t - comp;
       const double nxt = sum + y;
       comp = (nxt - sum) - y;
@@ -343,6 +353,16 @@ double dg_series(double gamma) {
   return S[levels - 1];
 }
 
+double dg_series(double gamma) { return dg_series_sum(gamma, 0); }
+double dg_series_dgamma(double gamma) { return dg_series_sum(gamma, 1); }
+
+// S(gamma) as a function of the (possibly dual) parameter gamma: the forward
+// derivative carries dS/dgamma.
+inline double dg_factor(double gamma) { return dg_series(gamma); }
+inline Dual dg_factor(const Dual& gamma) {
+  return Dual(dg_series(gamma.v), dg_series_dgamma(gamma.v) * gamma.d);
+}
+
 template <class T>
 void disk_gravity_one(const GasT<T>& g, double mu0, const T* x, T* acc) {
   if (!g.raw.enabled || !g.raw.disk_gravity) return;
@@ -352,7 +372,7 @@ void disk_gravity_one(const GasT<T>& g, double mu0, const T* x, T* acc) {
   const double to_code = kAuCm * kAuCm / kMsunG;   // g/cm^2 -> Msun/AU^2
   T F = T(2.0 * kPi * g.G * to_code) * d.sigma;
   if (g.raw.gamma == 1.0) F = F * (g.raw.r_in_au / R);
-  else F = F * dg_series(g.raw.gamma);
+  else F = F * dg_factor(g.gamma);
   acc[0] = acc[0] + F * x[0] / R;
   acc[1] = acc[1] + F * x[1] / R;
 }
@@ -1188,6 +1208,7 @@ int orc_gas_state(const orc_params* p, double R, double* out8) {
 double orc_drag_cd(double Re, double Ma, int cd_mode) { return drag_cd(Re, Ma, cd_mode); }
 
 double orc_dg_series(double gamma) { return dg_series(gamma); }
+double orc_dg_series_dgamma(double gamma) { return dg_series_dgamma(gamma); }
 
 int orc_disk_gravity(const orc_params* p, const double* x3, double* acc3) {
   if (!p || !x3 || !acc3) return ORC_ERR_ARG;

@@ -111,6 +111,9 @@ int orc_gas_drag_gap(const orc_params* p, int nbig, int nsmall, const double* xv
 int orc_gas_state(const orc_params* p, double R, double* out8);
 /* The series S(gamma) of Eq. 10 (gamma != 1): F_DG = 2 pi G Sigma(r) S(gamma). */
 double orc_dg_series(double gamma);
+/* dS/dgamma of the same series (the forward derivative of the disk's gravity
+ * with respect to gamma). */
+double orc_dg_series_dgamma(double gamma);
 /* Disk-gravity acceleration (Eqs. 10-12) on a planetesimal at x3 (AU/d^2). */
 int orc_disk_gravity(const orc_params* p, const double* x3, double* acc3);
 /* Drag coefficient of Eq. 7 (k = 0.4 below Re = 1e5, 0.2 from 1e5 up). */

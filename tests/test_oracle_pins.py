@@ -49,6 +49,22 @@ def test_disk_gravity_series_vs_mpmath(gamma):
     assert abs(orc.dg_series(gamma) - ref) <= 2e-15 * abs(ref)
 
 
+@pytest.mark.parametrize("gamma", [0.3, 0.8, 1.5, 1.9])
+def test_disk_gravity_series_derivative_vs_mpmath(gamma):
+    """dS/dgamma, which the oracle's forward derivative carries through the
+    disk's gravity, against mpmath's numerical derivative of its own sum of
+    Eq. 10's series."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+
+    def S(g):
+        term = lambda n: ((mp.binomial(2 * n, n) / mp.mpf(4) ** n) ** 2 * (1 - g) * (4 * n + 1)
+                          / ((2 * n + 2 - g) * (2 * n - 1 + g)))
+        return mp.nsum(term, [0, mp.inf])
+    ref = float(mp.diff(S, mp.mpf(gamma)))
+    assert abs(orc.dg_series_dgamma(gamma) - ref) <= 1e-12 * abs(ref)
+
+
 def test_disk_gravity_units_against_cgs():
     """2 pi G Sigma for Sigma = 1700 g/cm^2 at 1 AU, gamma = 1.5 (force = that x S),
     computed in CGS (G = 6.6743e-8) and converted to AU/day^2: the Gaussian units
@@ -576,3 +592,35 @@ def test_jvp_matches_central_difference():
     fd = (loss_at(eps) - loss_at(-eps)) / (2 * eps)
     assert abs(fd - dL) <= 1e-5 * abs(dL)
     assert L > 0
+
+
+@pytest.mark.parametrize("gamma,r_in,dpar", [(1.5, 1.0, (0.0, 0.02, 0.0)),
+                                              (1.5, 1.0, (17.0, 0.0, 0.0)),
+                                              (1.0, 1.5, (17.0, 0.0, 0.0))])
+def test_jvp_with_disk_gravity_matches_central_difference(gamma, r_in, dpar):
+    """With the disk's gravity on (Eqs. 10-12): the derivative along gamma
+    runs through Sigma and through S(gamma) (for gamma != 1; dropping dS/dgamma
+    puts it 85% off here), the one along sigma1 through Sigma.  At gamma = 1 the
+    force is the edge form of Eq. 12, a branch in gamma, so only sigma1 is
+    checked there.  The loss runs its bodies' encounters through BS, whose
+    step choices leave ~1e-6 of noise in the differences."""
+    w = W.gas_4core_100k(nsmall=24, nsteps=6)
+    w.params = dict(w.params, gas=dict(w.params["gas"], gamma=gamma, r_in_au=r_in,
+                                       disk_gravity=True))
+    p = orc.make_params(w.params)
+    wts = np.full(w.nsmall, 1.0 / w.nsmall)
+    dxv = np.zeros((6, w.n))
+    dpar = np.array(dpar)
+    L, dL = orc.jvp_loss(p, w.nbig, w.m_big, w.xv_helio, w.rp_km, w.rhop, wts, w.nsteps, dxv, dpar)
+
+    def loss_at(t):
+        gas = dict(w.params["gas"])
+        gas["sigma1_gcm2"] += t * dpar[0]
+        gas["gamma"] += t * dpar[1]
+        pp = orc.make_params(dict(w.params, gas=gas))
+        Lt, _ = orc.jvp_loss(pp, w.nbig, w.m_big, w.xv_helio, w.rp_km, w.rhop, wts, w.nsteps,
+                             dxv, np.zeros(3))
+        return Lt
+    eps = 1e-2
+    fd = (loss_at(eps) - loss_at(-eps)) / (2 * eps)
+    assert abs(fd - dL) <= 1e-5 * abs(dL), (fd, dL)
