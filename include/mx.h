@@ -382,9 +382,14 @@ mx_status mx_set_state_device(mx_system* s, const double* dev_xv);
  * encounter groups are skipped), or are differentiated through their
  * Bulirsch-Stoer groups (mx_adjoint_encounters).  An encounter between two
  * big bodies makes the adjoint inapplicable (the caller checks
- * mx_encounter_log).  The Python layer (paper_2601_16791_gb300.autograd)
- * drives checkpointing: the state is stored every k steps and each segment is
- * recomputed before its reverse sweep.
+ * mx_encounter_log).  The disk's gravity (Eqs. 10-12), when on, is
+ * differentiated too: with respect to position, sigma1 and gamma (through
+ * Sigma and, for gamma != 1, through the series S(gamma)); at gamma = 1 the
+ * force is the edge form of Eq. 12, and its gamma derivative is the one of
+ * that form.  Systems with growth or the ejection test have no adjoint.
+ * The Python layer (paper_2601_16791_gb300.autograd) drives checkpointing:
+ * the state is stored every k steps and each segment is recomputed before
+ * its reverse sweep.
  * ------------------------------------------------------------------------ */
 
 /* Gas parameters of system k (Sec. 3.1): Sigma at 1 AU, slope gamma (Eq. 1),

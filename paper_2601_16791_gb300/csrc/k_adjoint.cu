@@ -125,6 +125,38 @@ __device__ void drag_vjp(const SysDev& S, double x, double y, double u, double v
   gx[1] += ly;
 }
 
+// Reverse of the disk's gravity on a planetesimal (Eqs. 10-12), in the form
+// the kick applies it: a = g(R) (x, y, 0), g = c_dg Sigma(R) R^-m, m = 2 for
+// the gamma = 1 edge form (F = 2 pi G Sigma r_in / R) and m = 1 otherwise
+// (F = 2 pi G Sigma S(gamma)), Sigma = sigma1 R^-gamma E(R, gamma), and no
+// force inside r_in.  la is the cotangent of the acceleration.  Adds
+// la . da/d(x, y) to gx and la . da/d(sigma1, gamma) to gp[0], gp[1]:
+//   da/dx = g e_x + (x, y) g'(R) x / R,  g'/g = dln Sigma/dR - m/R,
+//   dln g/dgamma = -ln R + dln E/dgamma + dln S/dgamma (0 for the edge form).
+__device__ void disk_gravity_vjp(const SysDev& S, double x, double y, const double* la, double* gx,
+                                 double* gp) {
+  const double R2 = x * x + y * y;
+  const double R = sqrt(R2);
+  if (!(R >= S.r_in) || R2 == 0.0) return;
+  const double lnR = log(R);
+  double E = 1.0, dlnE_dR = 0.0, dlnE_dg = 0.0;
+  if (!S.rc_inf) {
+    const double lr = log(R * S.inv_rc);
+    const double p = exp((2.0 - S.gamma) * lr);
+    E = exp(-p);
+    dlnE_dR = -(2.0 - S.gamma) * p / R;
+    dlnE_dg = p * lr;
+  }
+  const double m = S.dg_edge ? 2.0 : 1.0;
+  const double g = S.c_dg * S.sigma1 * exp(-(S.gamma + m) * lnR) * E;
+  const double lr = la[0] * x + la[1] * y;
+  const double c = lr * g * (-S.gamma / R + dlnE_dR - m / R) / R;
+  gx[0] += g * la[0] + c * x;
+  gx[1] += g * la[1] + c * y;
+  gp[0] += lr * g / S.sigma1;
+  gp[1] += lr * g * (-lnR + dlnE_dg + S.dlnS_dgamma);
+}
+
 // ------------------------------------------------ Kepler-drift derivative
 // G4, G5 at (s, beta): series for |beta s^2| <= 0.3, else from
 // G_{k+2} = (s^k/k! - G_k)/beta.
@@ -461,6 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
         gas_drag(S, x, y, z, u, v, w, d.rp_cm[j], d.kdrag[j], ad, -1, &kb);
       }
       drag_vjp(S, x, y, u, v, w, d.rp_cm[j], d.kdrag[j], kb, la, dx3, dv3, own + 6);
+      if (S.dg_on) disk_gravity_vjp(S, x, y, la, dx3, own + 6);
       gx += dx3[0];
       gy += dx3[1];
       gz += dx3[2];

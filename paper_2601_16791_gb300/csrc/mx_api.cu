@@ -60,6 +60,31 @@ double disk_gravity_series(double gamma) {
   return S;
 }
 
+// dS/dgamma (gamma != 1), for the adjoint: each term's logarithmic
+// derivative is -1/(1-gamma) + 1/(2n+2-gamma) - 1/(2n-1+gamma), summed as
+// S is; the tail's derivative is -(1/pi)(1/N + 1/(4N^2)).  Cached per gamma.
+double disk_gravity_series_dgamma(double gamma) {
+  static std::vector<std::pair<double, double>> cache;
+  for (auto& kv : cache)
+    if (kv.first == gamma) return kv.second;
+  const int N = 1 << 20;
+  double sum = 0.0, comp = 0.0, b = 1.0;
+  for (int n = 0; n < N; ++n) {
+    if (n > 0) b *= (2.0 * n - 1.0) / (2.0 * n);
+    const double p = 2.0 * n + 2.0 - gamma, q = 2.0 * n - 1.0 + gamma;
+    const double t = b * b * (1.0 - gamma) * (4.0 * n + 1.0) / (p * q);
+    const double dt = t * (-1.0 / (1.0 - gamma) + 1.0 / p - 1.0 / q);
+    const double y = dt - comp;
+    const double nx = sum + y;
+    comp = (nx - sum) - y;
+    sum = nx;
+  }
+  const double Nd = (double)N;
+  const double dS = sum - (1.0 / kPi) * (1.0 / Nd + 0.25 / (Nd * Nd));
+  cache.push_back({gamma, dS});
+  return dS;
+}
+
 #define MX_CUDA(call)                                                                     \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \
@@ -129,6 +154,9 @@ mx::SysDev make_sysdev(const mx_params& p, int off, int nbig, int n, int boff) {
   s.dg_edge = (g.gamma == 1.0) ? 1 : 0;
   const double two_pi_g = 2.0 * kPi * p.G * (kAuCm * kAuCm / kMsunG);
   s.c_dg = s.dg_on ? two_pi_g * (s.dg_edge ? g.r_in_au : disk_gravity_series(g.gamma)) : 0.0;
+  s.dlnS_dgamma = (s.dg_on && !s.dg_edge)
+                      ? disk_gravity_series_dgamma(g.gamma) / disk_gravity_series(g.gamma)
+                      : 0.0;
   s.grow_on = 0;                 // mx_set_growth
   s.G = p.G;
   s.rcrit_hill = p.rcrit_hill;
@@ -1919,8 +1947,6 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
                           double* dev_lambda, double* dev_dparams) {
   if (!s || !dev_state_k || !dev_lambda || !dev_dparams || step_k < 0 || step_k > (1LL << 29))
     return fail(MX_ERR_ARG, "invalid arguments");
-  for (auto& y : s->h_sys)
-    if (y.dg_on) return fail(MX_ERR_ARG, "disk gravity is not differentiated by the adjoint");
   if (s->eject_every > 0 || s->removed_any)
     return fail(MX_ERR_ARG, "the adjoint does not follow bodies removed by ejection");
   if (s->grow_any) return fail(MX_ERR_ARG, "the adjoint does not follow growing masses");

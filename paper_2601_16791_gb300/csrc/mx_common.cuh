@@ -68,6 +68,7 @@ struct SysDev {
   // times 1/R for gamma = 1 (dg_edge), outward positive
   int dg_on, dg_edge;
   double c_dg;
+  double dlnS_dgamma;   // d ln S / d gamma of the series (0 for the edge form), for the adjoint
   // planet growth (Sec. 3.3) and gaps (Sec. 3.1, Eqs. 8-9)
   int grow_on, pad1;
   double G, rcrit_hill, gap_c;

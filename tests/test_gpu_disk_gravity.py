@@ -4,7 +4,7 @@ The kick adds the disk's radial force on planetesimals to the big bodies'
 gravity.  Checked: the acceleration of mx_accel / mx_gas_drag at 1e-12 for the
 gamma = 1 edge form and for gamma != 1 (the series S(gamma), which the library
 and the oracle sum by different methods); positions after a run; the deferred
-path bit for bit; and the adjoint's refusal.
+path bit for bit; and the adjoint through the disk's gravity.
 """
 import numpy as np
 import pytest
@@ -84,13 +84,40 @@ def test_deferred_path_with_disk_gravity_is_bit_identical():
     assert np.array_equal(out[0][0], out[1][0])
 
 
-def test_adjoint_refuses_disk_gravity():
-    w = _workload(1.0, 1.5, nsmall=200)
-    g = mx.System(w)
-    z = torch.tensor(g.state(mx.MX_COORD_DH), dtype=torch.float64, device="cuda")
-    lam = torch.zeros_like(z)
-    dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
-    with pytest.raises(mx.MxError) as e:
-        mx.mx_adjoint_step(g.h, z, 0, lam, dpar)
-    assert e.value.status == "MX_ERR_ARG"
-    g.close()
+@pytest.mark.parametrize("gamma,r_in", [(1.5, 1.0), (1.0, 1.5)])
+def test_adjoint_with_disk_gravity_vs_oracle_jvp(gamma, r_in):
+    """The adjoint through the disk's gravity (a radial force on planetesimals
+    in the gas: position and, through Sigma and S(gamma), sigma1 and gamma)
+    against the oracle's dual-number JVP, encountered planetesimals masked as
+    in the plain adjoint test; relative <= 1e-8.  At gamma = 1 the force is the
+    edge form of Eq. 12, a branch in gamma, so gamma is not perturbed there."""
+    from paper_2601_16791_gb300.autograd import Trajectory, semimajor_loss
+    w = W.adjoint_4core_50k(nsmall=300, nsteps=40, checkpoint_every=10)
+    w.params = dict(w.params, gas=dict(w.params["gas"], gamma=gamma, r_in_au=r_in,
+                                       disk_gravity=True))
+    traj = Trajectory(w)
+    g = w.params["gas"]
+    xv0 = torch.tensor(w.xv_helio, dtype=torch.float64, device="cuda", requires_grad=True)
+    gas = torch.tensor([g["sigma1_gcm2"], g["gamma"], g["cd_scale"]], dtype=torch.float64,
+                       device="cuda", requires_grad=True)
+    wts = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    wts[w.nbig:] = 1.0 / w.nsmall
+    L = semimajor_loss(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every, mask_encounters=True)
+    L.backward()
+    gx, gp = xv0.grad.cpu().numpy(), gas.grad.cpu().numpy()
+    ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    mx.mx_encounter_log(traj.h, ever)
+    traj.close()
+    w_small = (1.0 / w.nsmall) * (1 - ever.cpu().numpy()[w.nbig:].astype(float))
+    p = orc.make_params(w.params)
+    rng = np.random.default_rng(21)
+    for _ in range(3):
+        dxv = np.zeros((6, w.n))
+        dxv[:3] = rng.normal(0, 1e-4, (3, w.n))
+        dxv[3:] = rng.normal(0, 1e-6, (3, w.n))
+        dpar = np.array([17.0, 0.01 if gamma != 1.0 else 0.0, 0.01]) * rng.normal(0, 1, 3)
+        Lo, jvp = orc.jvp_loss(p, w.nbig, w.m_big, w.xv_helio, w.rp_km, w.rhop, w_small,
+                               w.nsteps, dxv, dpar)
+        ours = float((gx * dxv).sum() + (gp * dpar).sum())
+        assert abs(Lo - float(L.detach())) <= 1e-9 * abs(Lo)
+        assert abs(ours - jvp) <= 1e-8 * abs(jvp), (ours, jvp)
