@@ -6,10 +6,10 @@ Planetesimals are massless, so a sample of them moves exactly as inside the
 full disk: the oracle integrates every big body with the sample, the GPU the
 whole system, and the sampled columns are compared.
 
-Tolerances: positions of bodies that neither side flagged for an encounter,
-relative <= 1e-9; big bodies that went through Bulirsch-Stoer groups, relative
-<= 1e-8 (each group step agrees to the Bulirsch-Stoer tolerance, 1e-12, and
-the differences pass to the other big bodies through their mutual gravity).
+Tolerances: positions relative <= 1e-9, for bodies that neither side
+flagged for an encounter and (in the semi-active disk, over its 20 steps) for
+every big body, those that went through Bulirsch-Stoer groups included
+(measured 4e-12 at most for those, 1e-15 for the rest).
 """
 import numpy as np
 import pytest
@@ -66,7 +66,7 @@ def test_semiactive_full_size_sampled():
     assert st[1] > 100 and (~quiet[big]).sum() > 50, "no big-body groups: the test is vacuous"
     assert quiet[~big].sum() > 350
     assert err[quiet].max() <= 1e-9, err[quiet].max()
-    assert err[big].max() <= 1e-8, err[big].max()
+    assert err[big].max() <= 1e-9, err[big].max()
 
 
 def test_ensemble_full_size_sampled():
