@@ -42,7 +42,8 @@ typedef enum {
   MX_ERR_PAIR_OVERFLOW = 6,       /* more encounter pairs than pair_cap */
   MX_ERR_NONFINITE = 7,           /* a non-finite position or velocity */
   MX_ERR_BARRIER_TIMEOUT = 8,     /* a bounded device-side wait gave up */
-  MX_ERR_ENCOUNTER_IN_ADJOINT = 9,/* the adjoint met a big-big encounter */
+  MX_ERR_ENCOUNTER_IN_ADJOINT = 9,/* reserved (the adjoint now follows big-big
+                                     encounters through their groups) */
   MX_ERR_GROUP_TOO_LARGE = 10     /* an encounter group exceeds MX_MAX_GROUP */
 } mx_status;
 
@@ -380,9 +381,9 @@ mx_status mx_set_state_device(mx_system* s, const double* dev_xv);
  * Sigma slope, C_D factor).  Planetesimals that met a big body either carry
  * weight 0 (they are massless, so nothing else depends on them and the
  * encounter groups are skipped), or are differentiated through their
- * Bulirsch-Stoer groups (mx_adjoint_encounters).  An encounter between two
- * big bodies makes the adjoint inapplicable (the caller checks
- * mx_encounter_log).  The disk's gravity (Eqs. 10-12), when on, is
+ * Bulirsch-Stoer groups (mx_adjoint_encounters).  Big bodies that meet form
+ * groups of their own, which the adjoint always differentiates when asked to
+ * (modes 1 and 2 of mx_adjoint_encounters).  The disk's gravity (Eqs. 10-12), when on, is
  * differentiated too: with respect to position, sigma1 and gamma (through
  * Sigma and, for gamma != 1, through the series S(gamma)); at gamma = 1 the
  * force is the edge form of Eq. 12, and its gamma derivative is the one of
@@ -432,13 +433,22 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
  * integration (Sec. 2: the recomputed group's accepted sub-steps and
  * extrapolation rows held fixed); with them off it is differentiated as if
  * drifted, which is exact when its cotangent is zero (a loss that leaves it
- * out; it is massless, so nothing else depends on it).  A big-big encounter
- * gives MX_ERR_ENCOUNTER_IN_ADJOINT either way. */
+ * out; it is massless, so nothing else depends on it).  Big bodies that meet
+ * are differentiated through their own groups in modes 1 and 2. */
 mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long step_k,
                           double* dev_lambda, double* dev_dparams);
 
-/* on = 1 (the default): mx_adjoint_step integrates and differentiates the
- * step's encounter groups; 0: it skips them (see mx_adjoint_step). */
+/* Which of the step's encounter groups mx_adjoint_step integrates and
+ * differentiates.  The groups are the step's own (rebuilt from the
+ * recomputed endpoints): groups of big bodies joined by big-big encounters,
+ * and test-particle groups, a planetesimal with the whole big groups of the
+ * big bodies it meets.
+ *   on = 1 (the default): every group;
+ *   on = 2: the groups of big bodies only, for a loss that gives the
+ *           planetesimals that met a big body weight 0 (they are massless,
+ *           so nothing else depends on them);
+ *   on = 0: none; the caller asserts that no big bodies met in the step
+ *           (mx_encounter_log), or the big bodies' derivative is wrong. */
 mx_status mx_adjoint_encounters(mx_system* s, int on);
 
 /* Memory for the reverse of two-body encounter groups.  The adjoint's

@@ -8,12 +8,14 @@ The loss is the weighted squared change of semimajor axes,
 with a from the heliocentric state (mx_loss_semimajor).  A planetesimal's
 close encounters are differentiated through the Bulirsch-Stoer groups of the
 step, with the accepted sub-steps and extrapolation rows held fixed (the
-adjoint's k_adj_bs.cu).  With mask_encounters=True (the default), planetesimals
+adjoint's k_adj_bs.cu).  With mask_encounters=True (the default), bodies
 flagged for an encounter in any step get weight 0 instead, and the adjoint
-skips the groups (mx_adjoint_encounters): the derivative is exact for that
-loss and costs about as much as the forward step, where differentiating the
-groups costs their recorded Bulirsch-Stoer integration and its reverse.  An encounter between two big
-bodies makes the backward raise MX_ERR_ENCOUNTER_IN_ADJOINT.  The k switch of the drag coefficient is
+skips the test-particle groups (mx_adjoint_encounters): the derivative is
+exact for that loss, since those planetesimals are massless, and costs about
+as much as the forward step, where differentiating the groups costs their
+recorded Bulirsch-Stoer integration and its reverse.  Groups of big bodies
+(big-big encounters) are always differentiated: every body feels them.  The
+k switch of the drag coefficient is
 recorded in the forward run and replayed in the recomputation, so the
 reverse sweep sees the branches the forward run took.
 
@@ -82,7 +84,8 @@ class SemimajorLoss(torch.autograd.Function):
     def forward(ctx, xv_helio0, gas, traj, w, nsteps, every, mask_encounters):
         ckpts, ever, nbb = traj.run(xv_helio0, gas, nsteps, every, record=True)
         w_eff = w * (1.0 - ever.to(torch.float64)) if mask_encounters else w
-        ctx.groups = 0 if mask_encounters else 1
+        # masked: the groups of big bodies only, and none when no big bodies met
+        ctx.groups = (2 if nbb > 0 else 0) if mask_encounters else 1
         L, seed_f, seed_i = traj.loss(xv_helio0, w_eff)
         ctx.traj, ctx.nsteps, ctx.every, ctx.nbb = traj, nsteps, every, nbb
         ctx.ckpts = ckpts
@@ -93,9 +96,6 @@ class SemimajorLoss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gL):
         traj = ctx.traj
-        if ctx.nbb > 0:
-            raise mx.MxError(9, "SemimajorLoss.backward",
-                             f"{ctx.nbb} big-big encounter pairs in the forward run")
         seed_f, seed_i = ctx.saved_tensors
         g = float(gL)
         h = traj.h

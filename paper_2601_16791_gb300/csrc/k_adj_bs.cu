@@ -1,17 +1,21 @@
 // k_adj_bs.cu -- reverse mode through the Bulirsch-Stoer groups of one step
-// (arXiv 2601.16791, Sec. 2: a planetesimal in a close encounter leaves the
-// Kepler drift and is integrated by mdt_bs2 with the big bodies it meets).
+// (arXiv 2601.16791, Sec. 2: bodies in a close encounter leave the Kepler
+// drift and are integrated by mdt_bs2 together).
 //
 // The adjoint recomputes the step from its start.  After the drift it runs
-// the encounter detection on the recomputed endpoints, groups each flagged
-// planetesimal with the big bodies it meets (pairs sorted by planetesimal,
-// so the groups come in a fixed order), and integrates every group again with
-// the arithmetic of the step's thread integrator (mx_bs.cuh), one warp per
-// group: lane r runs the Stoermer row with 2(r+1) sub-steps, lane 0 builds
-// the Aitken-Neville table and takes the first converged row, as the
-// sequential search does.  Each accepted macro sub-step's length,
-// extrapolation row and starting state go to the group's region of a tape.
-// The planetesimal's result replaces its drifted state.
+// the encounter detection on the recomputed endpoints and builds the step's
+// own groups from them (k_groups on the sorted pairs, so the items come in a
+// fixed order): groups of big bodies joined by big-big encounters, every
+// member written back, and test-particle groups, a planetesimal with the
+// whole big groups of the big bodies it meets, only the planetesimal written
+// back.  Every group is integrated again and each accepted macro sub-step's
+// length, extrapolation row and starting state go to the group's region of a
+// tape: test-particle pairs on three warps with the catch-up's two-body
+// arithmetic (mx_bs2.cuh), other groups on one warp with the arithmetic of
+// the step's thread integrator (mx_bs.cuh; lane r runs the Stoermer row with
+// 2(r+1) sub-steps, lane 0 builds the Aitken-Neville table and takes the
+// first converged row, as the sequential search does).  The members'
+// results replace their drifted states.
 //
 // The reverse sweep treats that sequence as fixed (a discrete adjoint of the
 // Gragg-Bulirsch-Stoer map with its accepted steps and rows frozen, as a
@@ -19,11 +23,10 @@
 // every accepted sub-step is a fixed linear combination of Stoermer runs
 // (the Aitken-Neville weights of its row), and each Stoermer run is reversed
 // from its recomputed positions with the Jacobian of the group's forces (the
-// star and the (1 - K)-weighted pair forces), one row per lane, the lanes'
-// shares summed in a fixed butterfly.  The planetesimal's cotangent
-// at its pre-drift state replaces the drift's; the big bodies' shares are
-// added to theirs by a per-system fold in group order.  Big-big encounters
-// stay refused (ST_ADJ_ENC): a big body's own state never comes from a group.
+// star and the (1 - K)-weighted pair forces), the rows' shares summed in a
+// fixed butterfly.  A member written back gets its cotangent at its
+// pre-drift state in place of the drift's; the big bodies of a test-particle
+// group get shares, added to theirs by a per-system fold in item order.
 #include "mx_bs.cuh"
 #include "mx_bs2.cuh"
 #include "mx_common.cuh"
@@ -32,20 +35,6 @@
 namespace mx {
 
 namespace {
-
-__device__ __forceinline__ int pkey_j(unsigned long long k) { return (int)((k >> 32) & 0x7fffffffull); }
-__device__ __forceinline__ int pkey_i(unsigned long long k) { return (int)(k & 0xffffffffull); }
-__device__ __forceinline__ bool pkey_small(unsigned long long k) { return (k >> 63) != 0; }
-
-__device__ int sys_of_body(const Dev& d, int g) {
-  int lo = 0, hi = d.nsys - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (d.sys[mid].off <= g) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 
 // Tape record of one accepted macro sub-step: H, row, the 6 x nb state, then
 // (two-body groups) the slot of its kept Stoermer sub-steps or -1; each group
@@ -69,73 +58,38 @@ __device__ __forceinline__ int take_slots(const Adj& a) {
 
 }  // namespace
 
-// One block: the group list from the sorted pair keys.  A group is a
-// planetesimal and the big bodies it meets (keys (1, j, i) ascending: one run
-// per j, its bigs ascending).  A big-big key refuses the adjoint.
-__global__ void __launch_bounds__(1024) k_adj_groups(Dev d, Adj a) {
-  __shared__ int s_warp[32];
-  __shared__ int s_base;
-  const int cnt = *d.pair_count;
-  const int n = min(cnt, d.pair_cap);
-  if (threadIdx.x == 0) {
-    s_base = 0;
-    if (cnt > d.pair_cap) atomicOr(d.status, ST_PAIR_OVF);
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int p = base + threadIdx.x;
-    bool start = false;
-    unsigned long long key = 0;
-    if (p < n) {
-      key = d.keys[p];
-      if (!pkey_small(key)) atomicOr(d.status, ST_ADJ_ENC);
-      start = pkey_small(key) && (p == 0 || !pkey_small(d.keys[p - 1]) ||
-                                  pkey_j(d.keys[p - 1]) != pkey_j(key));
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, start);
-    if (lane == 0) s_warp[warp] = __popc(m);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int run = s_base;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        const int c = s_warp[w];
-        s_warp[w] = run;
-        run += c;
-      }
-      s_base = run;
-    }
-    __syncthreads();
-    if (start) {
-      const int gi = s_warp[warp] + __popc(m & ((1u << lane) - 1u));
-      const int j = pkey_j(key);
-      int q = p + 1;
-      while (q < n && pkey_small(d.keys[q]) && pkey_j(d.keys[q]) == j) ++q;
-      if (gi < a.g_cap) {
-        a.g_small[gi] = j;
-        a.g_key[gi] = p;
-        a.g_nb[gi] = q - p;
-        if (q - p + 1 > kMaxGroup) atomicOr(d.status, ST_GROUP);
-      } else {
-        atomicOr(d.status, ST_WORK_OVF);
-      }
-    }
-    __syncthreads();
-  }
-  const int ng = min(s_base, a.g_cap);
-  if (threadIdx.x == 0) {
-    *a.g_count = ng;
-    if (a.sub_count) *a.sub_count = 0;
-  }
-  // tape regions: an exclusive scan of kAdjMaxSteps records per group
+// The items of the step's work list the adjoint takes: every one (groups 1),
+// or the groups of big bodies only (groups 2: every member written back).
+__device__ __forceinline__ bool adj_takes(const Dev& d, const Adj& a, int w) {
+  return a.groups == 1 || (a.groups == 2 && d.work_wfrom[w] == 0);
+}
+
+// One block, after k_groups: the tape region of every item the adjoint takes
+// (an exclusive scan of kAdjMaxSteps records of its size, in item order), and
+// the mark flags = 2 on the members it writes back, whose drift the reverse
+// then leaves to the group.  Every item starts with g_M = -1 (not processed);
+// the forward kernels set it.
+__global__ void __launch_bounds__(1024) k_adj_tape(Dev d, Adj a) {
   __shared__ unsigned long long s_wsum[32];
   __shared__ unsigned long long s_run;
-  if (threadIdx.x == 0) s_run = 0;
+  const int W = min(*d.work_count, a.g_cap);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    s_run = 0;
+    if (a.sub_count) *a.sub_count = 0;
+  }
   __syncthreads();
-  for (int base = 0; base < ng; base += blockDim.x) {
-    const int g = base + threadIdx.x;
+  for (int base = 0; base < W; base += blockDim.x) {
+    const int w = base + threadIdx.x;
     unsigned long long v = 0;
-    if (g < ng) v = (unsigned long long)kAdjMaxSteps * tape_stride(min(a.g_nb[g], kMaxGroup - 1) + 1);
+    if (w < W) {
+      a.g_M[w] = -1;
+      if (adj_takes(d, a, w)) {
+        const int o = d.work_off[w], nb = d.work_off[w + 1] - o;
+        v = (unsigned long long)kAdjMaxSteps * tape_stride(min(nb, kMaxGroup));
+        for (int m = d.work_wfrom[w]; m < nb; ++m) d.flags[d.work_mem[o + m]] = 2;
+      }
+    }
     unsigned long long inc = v;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long t = __shfl_up_sync(0xffffffffu, inc, o);
@@ -145,63 +99,72 @@ __global__ void __launch_bounds__(1024) k_adj_groups(Dev d, Adj a) {
     __syncthreads();
     if (threadIdx.x == 0) {
       unsigned long long run = s_run;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        const unsigned long long c = s_wsum[w];
-        s_wsum[w] = run;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+        const unsigned long long c = s_wsum[q];
+        s_wsum[q] = run;
         run += c;
       }
       s_run = run;
     }
     __syncthreads();
-    if (g < ng) a.g_off[g] = s_wsum[warp] + inc - v;
+    if (w < W) a.g_off[w] = s_wsum[warp] + inc - v;
     __syncthreads();
   }
 }
 
-// The group's members (big bodies ascending, then the planetesimal), their
-// constants and their pre-drift states (x2, v1).
-__device__ bool load_adj_group(const Dev& d, const Adj& a, int g, GroupState& G,
-                               double (*Y)[kMaxGroup], int* big, int* jj, int* sys) {
-  const int j = a.g_small[g], p = a.g_key[g], nbb = a.g_nb[g];
-  if (nbb + 1 > kMaxGroup) return false;
-  const int sy = sys_of_body(d, j);
+// Item w's members in the step's order (big bodies ascending, then the
+// planetesimal of a test-particle group), their constants and their
+// pre-drift states (x2, v1); *jj the last member, *wf the first written back.
+__device__ bool load_adj_group(const Dev& d, const Adj& a, int w, GroupState& G,
+                               double (*Y)[kMaxGroup], int* big, int* jj, int* sys, int* wf) {
+  const int o = d.work_off[w], nb = d.work_off[w + 1] - o;
+  if (nb < 2 || nb > kMaxGroup) return false;
+  const int sy = d.work_sys[w];
   const SysDev& S = d.sys[sy];
   const int N = d.N;
-  G.nb = nbb + 1;
-  for (int m = 0; m <= nbb; ++m) {
-    const int gi = (m < nbb) ? pkey_i(d.keys[p + m]) : j;
-    if (m < nbb) big[m] = gi - S.off;
-    G.mu[m] = (m < nbb) ? d.bmu[S.boff + (gi - S.off)] : 0.0;
-    G.rc[m] = (m < nbb) ? d.brc[S.boff + (gi - S.off)] : 0.0;
+  G.nb = nb;
+  for (int m = 0; m < nb; ++m) {
+    const int gi = d.work_mem[o + m];
+    const int l = gi - S.off;
+    const bool bm = l < S.nbig;
+    big[m] = bm ? l : -1;
+    G.mu[m] = bm ? d.bmu[S.boff + l] : 0.0;
+    G.rc[m] = bm ? d.brc[S.boff + l] : 0.0;
     for (int c = 0; c < 3; ++c) {
       Y[c][m] = a.x2[(size_t)c * N + gi];
       Y[3 + c][m] = a.v1[(size_t)c * N + gi];
     }
   }
-  *jj = j;
+  *jj = d.work_mem[o + nb - 1];
   *sys = sy;
+  *wf = d.work_wfrom[w];
   return true;
+}
+
+// A test-particle pair (a big body and the planetesimal): k_adj_bs_fwd2 and
+// k_adj_bs_vjp2 take it; every other item goes to the general kernels.
+__device__ __forceinline__ bool adj_pair(const Dev& d, int w) {
+  return d.work_off[w + 1] - d.work_off[w] == 2 && d.work_wfrom[w] == 1;
 }
 
 // Forward, one warp per group: lane r < kBsRows runs Stoermer row r from the
 // macro sub-step's start; lane 0 extrapolates, checks and (on acceptance)
 // records the sub-step and passes the new state to the other lanes through
 // shared memory.  The arithmetic and the decisions are bs_integrate's.  The
-// planetesimal's result replaces its drifted state in xv3.
+// results of the members written back (the planetesimal of a test-particle
+// group, every member of a group of big bodies) replace their drifted states
+// in xv3.
 __global__ void __launch_bounds__(32) k_adj_bs_fwd(Dev d, Adj a) {
   __shared__ double sraw[kBsRows][6][kMaxGroup];
   __shared__ double sY[6][kMaxGroup];
   const int lane = threadIdx.x;
-  const int ng = *a.g_count;
+  const int ng = min(*d.work_count, a.g_cap);
   for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+    if (!adj_takes(d, a, g) || adj_pair(d, g)) continue;   // pairs: k_adj_bs_fwd2
     GroupState G;
     double Y[6][kMaxGroup];
-    int big[kMaxGroup], j, sy;
-    if (!load_adj_group(d, a, g, G, Y, big, &j, &sy)) {
-      if (lane == 0) a.g_M[g] = -1;
-      continue;
-    }
-    if (G.nb == 2) continue;   // k_adj_bs_fwd2
+    int big[kMaxGroup], j, sy, wf;
+    if (!load_adj_group(d, a, g, G, Y, big, &j, &sy, &wf)) continue;
     const SysDev& S = d.sys[sy];
     const int nb = G.nb, stride = tape_stride(nb);
     const unsigned long long off = a.g_off[g];
@@ -295,8 +258,9 @@ __global__ void __launch_bounds__(32) k_adj_bs_fwd(Dev d, Adj a) {
         a.g_M[g] = -1;
       } else {
         a.g_M[g] = M;
-        const int N = d.N, s = nb - 1;
-        for (int c = 0; c < 6; ++c) a.xv3[(size_t)c * N + j] = Y[c][s];
+        const int N = d.N, o = d.work_off[g];
+        for (int m = wf; m < nb; ++m)
+          for (int c = 0; c < 6; ++c) a.xv3[(size_t)c * N + d.work_mem[o + m]] = Y[c][m];
       }
     }
   }
@@ -318,17 +282,14 @@ __global__ void __launch_bounds__(128) k_adj_bs_fwd2(Dev d, Adj a) {
   const int row = lane >> 2, q = lane & 3, ob = q & 1;
   const bool vel = q >= 2;
   const int n = 2 * (row + 1);
-  const int ng = *a.g_count;
+  const int ng = min(*d.work_count, a.g_cap);
   for (int g = blockIdx.x; g < ng; g += gridDim.x) {
-    if (a.g_nb[g] != 1) continue;   // two bodies: one big body and the planetesimal
+    if (!adj_takes(d, a, g) || !adj_pair(d, g)) continue;   // a big body and the planetesimal
     if (c == 3) continue;           // warps 0-2 only (named barrier 1)
     GroupState G;
     double Y0[6][kMaxGroup];
-    int big[kMaxGroup], j, sy;
-    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) {
-      if (threadIdx.x == 0) a.g_M[g] = -1;
-      continue;
-    }
+    int big[kMaxGroup], j, sy, wf;
+    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy, &wf)) continue;
     const SysDev& S = d.sys[sy];
     const int stride = tape_stride(2);
     const unsigned long long off = a.g_off[g];
@@ -591,21 +552,21 @@ __device__ void neville_weights(int K, double* c) {
 // pre-drift cotangent replaces lam's; the big members' shares go to g_contrib.
 __global__ void __launch_bounds__(32) k_adj_bs_vjp(Dev d, Adj a) {
   const int lane = threadIdx.x;
-  const int ng = *a.g_count;
+  const int ng = min(*d.work_count, a.g_cap);
   for (int g = blockIdx.x; g < ng; g += gridDim.x) {
     const int M = a.g_M[g];
-    if (M < 0) continue;
+    if (M < 0 || adj_pair(d, g)) continue;   // pairs: k_adj_bs_vjp2
     GroupState G;
     double Y0[6][kMaxGroup];
-    int big[kMaxGroup], j, sy;
-    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) continue;
-    if (G.nb == 2) continue;   // k_adj_bs_vjp2
+    int big[kMaxGroup], j, sy, wf;
+    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy, &wf)) continue;
     const SysDev& S = d.sys[sy];
-    const int N = d.N, nb = G.nb, s = nb - 1;
+    const int N = d.N, nb = G.nb, o = d.work_off[g];
+    // the cotangents of the outputs: the members written back carry theirs
     double lY[6][kMaxGroup], lO[6][kMaxGroup];
     for (int c = 0; c < 6; ++c)
-      for (int m = 0; m < nb; ++m) lO[c][m] = 0.0;
-    for (int c = 0; c < 6; ++c) lO[c][s] = a.lam[(size_t)c * N + j];
+      for (int m = 0; m < nb; ++m)
+        lO[c][m] = (m >= wf) ? a.lam[(size_t)c * N + d.work_mem[o + m]] : 0.0;
     const int stride = tape_stride(nb);
     for (int k = M - 1; k >= 0; --k) {
       const double* r = a.tape + a.g_off[g] + (size_t)k * stride;
@@ -628,11 +589,15 @@ __global__ void __launch_bounds__(32) k_adj_bs_vjp(Dev d, Adj a) {
           lO[c][m] = v;
         }
     }
+    // a member written back gets its cotangent at its pre-drift state; any
+    // other (a big body of a test-particle group) a share, folded per system
     if (lane == 0) {
-      for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + j] = lO[c][s];
       double* out = a.g_contrib + (size_t)g * 6 * kMaxGroup;
-      for (int m = 0; m < s; ++m)
-        for (int c = 0; c < 6; ++c) out[6 * m + c] = lO[c][m];
+      for (int m = 0; m < nb; ++m)
+        for (int c = 0; c < 6; ++c) {
+          if (m >= wf) a.lam[(size_t)c * N + d.work_mem[o + m]] = lO[c][m];
+          else out[6 * m + c] = lO[c][m];
+        }
     }
   }
 }
@@ -699,7 +664,7 @@ __global__ void __launch_bounds__(96) k_adj_bs_vjp2(Dev d, Adj a) {
   const int row = lane >> 2, q = lane & 3, ob = q & 1;
   const int src_r = (lane & ~3) + 3 - ob;    // the row's lane of the other body's pair term
   const int n = 2 * (row + 1);
-  const int ng = *a.g_count;
+  const int ng = min(*d.work_count, a.g_cap);
   // Aitken-Neville weights of every row K (neville_weights, with the
   // constants the two-body integrator extrapolates with)
   for (int e = threadIdx.x; e < kBsRows * kBsRows; e += blockDim.x) {
@@ -719,13 +684,13 @@ __global__ void __launch_bounds__(96) k_adj_bs_vjp2(Dev d, Adj a) {
   bs2c_bar();
   const int stride = tape_stride(2);
   for (int g = blockIdx.x; g < ng; g += gridDim.x) {
-    if (a.g_nb[g] != 1) continue;
+    if (!adj_pair(d, g)) continue;
     const int M = a.g_M[g];
     if (M < 0) continue;
     GroupState G;
     double Y0[6][kMaxGroup];
-    int big[kMaxGroup], j, sy;
-    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy)) continue;
+    int big[kMaxGroup], j, sy, wf;
+    if (!load_adj_group(d, a, g, G, Y0, big, &j, &sy, &wf)) continue;
     const SysDev& S = d.sys[sy];
     const int N = d.N;
     Bs2Term tm;
@@ -851,22 +816,20 @@ __global__ void __launch_bounds__(96) k_adj_bs_vjp2(Dev d, Adj a) {
   }
 }
 
-// Per system: the big bodies' shares and the sum of the position shares for
+// Per system: the shares of the members a group does not write back (big
+// bodies of test-particle groups) and the sum of their position parts for
 // jump 1's momentum term.  With up to 64 big bodies a system's sums run over
-// the groups on all threads of the block (thread t takes groups t, t + 256,
-// ... in order) and end in a fixed pairwise tree; with more, one thread per
-// big body adds its shares in group order.  Either way the order is fixed.
+// the items on all threads of the block (thread t takes items t, t + 256, ...
+// in order) and end in a fixed pairwise tree; with more, one thread per big
+// body adds its shares in item order.  Either way the order is fixed.
 __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
   __shared__ double red[6][kThreads];
   const int sys = blockIdx.x;
   const SysDev& S = d.sys[sys];
   const int N = d.N;
-  const int ng = *a.g_count;
+  const int ng = min(*d.work_count, a.g_cap);
   const int t = threadIdx.x;
-  auto in_sys = [&](int g) {
-    const int j = a.g_small[g];
-    return j >= S.off && j < S.off + S.n && a.g_M[g] >= 0;
-  };
+  auto in_sys = [&](int g) { return d.work_sys[g] == sys && a.g_M[g] >= 0; };
   // block-wide sum of v[0..nv) into red[.][0] (every thread must call it)
   auto tree = [&](const double* v, int nv) {
     for (int c = 0; c < nv; ++c) red[c][t] = v[c];
@@ -877,18 +840,20 @@ __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
       __syncthreads();
     }
   };
+  // item g's share for big body i (local index), added to acc
+  auto add_share = [&](int g, int i, double* acc) {
+    const int o = d.work_off[g], wf = d.work_wfrom[g];
+    for (int m = 0; m < wf; ++m) {
+      if (d.work_mem[o + m] - S.off != i) continue;
+      const double* c6 = a.g_contrib + (size_t)g * 6 * kMaxGroup + 6 * m;
+      for (int c = 0; c < 6; ++c) acc[c] += c6[c];
+    }
+  };
   if (S.nbig <= 64) {
     for (int i = 0; i < S.nbig; ++i) {
       double acc[6] = {0, 0, 0, 0, 0, 0};
-      for (int g = t; g < ng; g += kThreads) {
-        if (!in_sys(g)) continue;
-        const int p = a.g_key[g], nbb = a.g_nb[g];
-        for (int m = 0; m < nbb; ++m) {
-          if (pkey_i(d.keys[p + m]) - S.off != i) continue;
-          const double* c6 = a.g_contrib + (size_t)g * 6 * kMaxGroup + 6 * m;
-          for (int c = 0; c < 6; ++c) acc[c] += c6[c];
-        }
-      }
+      for (int g = t; g < ng; g += kThreads)
+        if (in_sys(g)) add_share(g, i, acc);
       tree(acc, 6);
       if (t == 0)
         for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + S.off + i] += red[c][0];
@@ -897,15 +862,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
   } else {
     for (int i = t; i < S.nbig; i += blockDim.x) {
       double acc[6] = {0, 0, 0, 0, 0, 0};
-      for (int g = 0; g < ng; ++g) {
-        if (!in_sys(g)) continue;
-        const int p = a.g_key[g], nbb = a.g_nb[g];
-        for (int m = 0; m < nbb; ++m) {
-          if (pkey_i(d.keys[p + m]) - S.off != i) continue;
-          const double* c6 = a.g_contrib + (size_t)g * 6 * kMaxGroup + 6 * m;
-          for (int c = 0; c < 6; ++c) acc[c] += c6[c];
-        }
-      }
+      for (int g = 0; g < ng; ++g)
+        if (in_sys(g)) add_share(g, i, acc);
       const int gi = S.off + i;
       for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + gi] += acc[c];
     }
@@ -914,8 +872,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
   double sx[3] = {0, 0, 0};
   for (int g = t; g < ng; g += kThreads) {
     if (!in_sys(g)) continue;
-    const int nbb = a.g_nb[g];
-    for (int m = 0; m < nbb; ++m)
+    const int wf = d.work_wfrom[g];
+    for (int m = 0; m < wf; ++m)
       for (int c = 0; c < 3; ++c) sx[c] += a.g_contrib[(size_t)g * 6 * kMaxGroup + 6 * m + c];
   }
   tree(sx, 3);
@@ -924,22 +882,26 @@ __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
 
 void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
   // detection on the recomputed endpoints, without touching the step's log
+  // (encounter flags, big-big count, deferral history)
   Dev dd = d;
   dd.ever = nullptr;
+  dd.bb_count = nullptr;
   dd.defer = 0;
   cudaMemsetAsync(d.flags, 0, d.N, st);
   cudaMemsetAsync(d.pair_count, 0, sizeof(int), st);
   launch_detect(dd, a.x2, a.xv3, d.flags, d.keys, d.pair_count, d.pair_cap, 1, st);
+  // sorted keys give the work items a fixed order (the shares' fold follows it)
   launch_sort_keys(d.keys, d.pair_count, d.pair_cap, 0, st);
-  k_adj_groups<<<1, 1024, 0, st>>>(d, a);
-  k_adj_bs_fwd<<<nblocks, 32, 0, st>>>(d, a);    // groups of three or more bodies
-  k_adj_bs_fwd2<<<nblocks, 128, 0, st>>>(d, a);  // two-body groups
+  launch_groups(dd, st);   // the step's own groups: big groups, then test-particle groups
+  k_adj_tape<<<1, 1024, 0, st>>>(dd, a);
+  k_adj_bs_fwd<<<nblocks, 32, 0, st>>>(d, a);    // every item but the test-particle pairs
+  k_adj_bs_fwd2<<<nblocks, 128, 0, st>>>(d, a);  // test-particle pairs
 }
 
 void launch_adjoint_bs_vjp(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
-  k_adj_bs_vjp<<<nblocks, 32, 0, st>>>(d, a);    // groups of three or more bodies
+  k_adj_bs_vjp<<<nblocks, 32, 0, st>>>(d, a);    // every item but the test-particle pairs
   cudaFuncSetAttribute(k_adj_bs_vjp2, cudaFuncAttributeMaxDynamicSharedMemorySize, kVjp2Smem);
-  k_adj_bs_vjp2<<<nblocks, 96, kVjp2Smem, st>>>(d, a);   // two-body groups
+  k_adj_bs_vjp2<<<nblocks, 96, kVjp2Smem, st>>>(d, a);   // test-particle pairs
 }
 
 void launch_adjoint_bs_fold(const Dev& d, const Adj& a, cudaStream_t st) {

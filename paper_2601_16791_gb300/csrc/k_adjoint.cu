@@ -630,9 +630,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_drift_vjp(Dev d, Adj a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
   double own[3] = {0, 0, 0};
-  // a planetesimal in an encounter group already holds its cotangent at the
-  // pre-drift state (k_adj_bs_vjp); it only enters the jump's sum
-  const bool in_group = a.groups && act && j - S.off >= S.nbig && d.flags[j];
+  // a body an encounter group writes back (marked 2 by k_adj_tape) already
+  // holds its cotangent at the pre-drift state (k_adj_bs_vjp); it only enters
+  // the jump's sum
+  const bool in_group = a.groups && act && d.flags[j] == 2;
   if (in_group)
     for (int c = 0; c < 3; ++c) own[c] = a.lam[(size_t)c * N + j];
   if (act && !in_group) {

@@ -102,8 +102,6 @@ mx_status status_to_code(unsigned st) {
   if (st & mx::ST_WORK_OVF) return fail(MX_ERR_PAIR_OVERFLOW, "encounter work list overflow");
   if (st & mx::ST_BS) return fail(MX_ERR_BS_NOCONV, "Bulirsch-Stoer hit its sub-step cap");
   if (st & mx::ST_BARRIER) return fail(MX_ERR_BARRIER_TIMEOUT, "device wait gave up");
-  if (st & mx::ST_ADJ_ENC)
-    return fail(MX_ERR_ENCOUNTER_IN_ADJOINT, "big-big encounter inside the adjoint");
   if (st & mx::ST_WINDOW) return fail(MX_ERR_CUDA, "deferral window longer than its history");
   return MX_OK;
 }
@@ -222,7 +220,7 @@ struct mx_system {
   double *a_part = nullptr, *a_P = nullptr, *a_L = nullptr;
   // adjoint through the encounter groups (k_adj_bs.cu)
   int a_gcap = 0;
-  int *a_gsmall = nullptr, *a_gkey = nullptr, *a_gnb = nullptr, *a_gM = nullptr, *a_gcount = nullptr;
+  int* a_gM = nullptr;
   unsigned long long* a_goff = nullptr;
   double *a_gcontrib = nullptr, *a_tape = nullptr, *a_bsx = nullptr;
   unsigned long long a_tape_cap = 0;
@@ -1748,10 +1746,8 @@ namespace {
 
 // Per-tile partial records for the adjoint and the loss: 3 doubles per big
 // body of the tile's system plus 9.
-// Encounter groups per adjoint step, and the doubles of their recorded
-// Bulirsch-Stoer sub-steps (each group has room for 128 sub-steps; a
-// two-body group's sub-step takes 15 doubles).
-constexpr int kAdjGroups = 1 << 14;
+// The doubles of the adjoint's recorded Bulirsch-Stoer sub-steps (each group
+// has room for 128 sub-steps; a two-body group's sub-step takes 15 doubles).
 constexpr size_t kAdjTape = (size_t)1 << 23;
 
 // The step's device view with the adjoint's tiling.
@@ -1776,13 +1772,9 @@ mx_status ensure_adjoint(mx_system* s) {
   if (!s->a_tiles) {
     MX_TRY(dalloc(s, &s->a_x2, (size_t)6 * N));   // x2 and v1: one 6 x N pre-drift state
     s->a_v1 = s->a_x2 + 3 * (size_t)N;
-    const int gcap = std::min(s->d.pair_cap, kAdjGroups);
+    const int gcap = s->d.work_cap;   // one entry per item of the step's work list
     s->a_gcap = gcap;
-    MX_TRY(dalloc(s, &s->a_gsmall, gcap));
-    MX_TRY(dalloc(s, &s->a_gkey, gcap));
-    MX_TRY(dalloc(s, &s->a_gnb, gcap));
     MX_TRY(dalloc(s, &s->a_gM, gcap));
-    MX_TRY(dalloc(s, &s->a_gcount, 1));
     MX_TRY(dalloc(s, &s->a_goff, gcap));
     MX_TRY(dalloc(s, &s->a_gcontrib, (size_t)gcap * mx::kMaxGroup * 6));
     MX_TRY(dalloc(s, &s->a_tape, kAdjTape));
@@ -1916,7 +1908,7 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
 }
 
 mx_status mx_adjoint_encounters(mx_system* s, int on) {
-  if (!s || (on != 0 && on != 1)) return fail(MX_ERR_ARG, "invalid arguments");
+  if (!s || on < 0 || on > 2) return fail(MX_ERR_ARG, "invalid arguments");
   s->a_groups = on;
   return MX_OK;
 }
@@ -1970,11 +1962,7 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   a.groups = s->a_groups;
   a.g_cap = s->a_gcap;
   a.bs_blocks = s->bs_blocks;
-  a.g_small = s->a_gsmall;
-  a.g_key = s->a_gkey;
-  a.g_nb = s->a_gnb;
   a.g_M = s->a_gM;
-  a.g_count = s->a_gcount;
   a.g_off = s->a_goff;
   a.g_contrib = s->a_gcontrib;
   a.tape = s->a_tape;

@@ -41,7 +41,6 @@ enum : unsigned {
   ST_BARRIER = 1u << 4,
   ST_GROUP = 1u << 5,
   ST_WORK_OVF = 1u << 6,
-  ST_ADJ_ENC = 1u << 7,
   ST_WINDOW = 1u << 8
 };
 
@@ -200,12 +199,16 @@ struct Adj {
   double* dpar;       // 3 per system, accumulated
   int step;           // index of the step (recorded k branches)
   // Bulirsch-Stoer groups (k_adj_bs.cu): x2 and v1 are the two halves of one
-  // 6 x N pre-drift state; groups sorted by planetesimal
-  int groups;                    // 0: no encounter groups (bodies in them carry no cotangent)
-  int g_cap, bs_blocks;
-  int *g_small, *g_key, *g_nb, *g_M, *g_count;
-  unsigned long long* g_off;     // tape offset of each group
-  double* g_contrib;             // [g_cap][kMaxGroup][6] big members' cotangents
+  // 6 x N pre-drift state.  The groups are the step's own work list (d.work_*,
+  // built by k_groups from the recomputed endpoints), item by item.
+  // groups: 0 none (the caller asserts no big-big encounter: bodies in groups
+  // carry no cotangent); 1 every group; 2 groups of big bodies only (a loss
+  // that leaves out the planetesimals that met a big body)
+  int groups;
+  int g_cap, bs_blocks;          // g_cap: work items (d.work_cap)
+  int* g_M;                      // accepted sub-steps recorded per item, -1: not processed
+  unsigned long long* g_off;     // tape offset of each item
+  double* g_contrib;             // [g_cap][kMaxGroup][6] shares of members not written back
   double* tape;                  // accepted sub-steps: H, row, 6 x nb start state, slot
   unsigned long long tape_cap;   // doubles
   double* bs_xsum;               // 3 per system: sum of the big shares' position parts

@@ -221,3 +221,46 @@ def test_adjoint_kept_and_recomputed_substeps_agree_bitwise():
         assert o[0] == out[0][0] and np.array_equal(o[1], out[0][1]) and np.array_equal(o[2], out[0][2])
     assert np.abs(out[0][1]).max() > 0
     traj.close()
+
+
+@pytest.mark.parametrize("mask", [False, True])
+def test_adjoint_through_big_body_encounters_vs_oracle_jvp(mask):
+    """A swarm of 1,000 embryos with 1,000 planetesimals over 30 steps, where
+    embryos meet each other (groups of big bodies, every member's state from
+    the group) and planetesimals meet embryos (test-particle groups with the
+    whole big groups).  The gradient of the planetesimals' loss against the
+    oracle's dual-number JVP, which follows its own integrator's steps:
+    relative <= 1e-6.  mask=True leaves out the planetesimals that met a big
+    body (mode 2: the big groups only); mask=False takes every group."""
+    from paper_2601_16791_gb300.autograd import Trajectory, semimajor_loss
+    w = W.semiactive_2000big_200k(nbig=1000, nsmall=1000, nsteps=30)
+    w.checkpoint_every = 10
+    traj = Trajectory(w)
+    g = w.params["gas"]
+    xv0 = torch.tensor(w.xv_helio, dtype=torch.float64, device="cuda", requires_grad=True)
+    gas = torch.tensor([g["sigma1_gcm2"], g["gamma"], g["cd_scale"]], dtype=torch.float64,
+                       device="cuda", requires_grad=True)
+    wts = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    wts[w.nbig:] = 1.0 / w.nsmall
+    L = semimajor_loss(traj, xv0, gas, wts, w.nsteps, w.checkpoint_every, mask_encounters=mask)
+    L.backward()
+    gx = xv0.grad.cpu().numpy()
+    ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    nbb = mx.mx_encounter_log(traj.h, ever)
+    traj.close()
+    ever = ever.cpu().numpy().astype(bool)
+    assert nbb > 20 and ever[:w.nbig].sum() > 20, "no big-body groups: the test is vacuous"
+    w_small = np.full(w.nsmall, 1.0 / w.nsmall)
+    if mask:
+        w_small = w_small * (1 - ever[w.nbig:].astype(float))
+    p = orc.make_params(w.params)
+    rng = np.random.default_rng(17)
+    for _ in range(3):
+        dxv = np.zeros((6, w.n))
+        dxv[:3] = rng.normal(0, 1e-4, (3, w.n))
+        dxv[3:] = rng.normal(0, 1e-6, (3, w.n))
+        Lo, jvp = orc.jvp_loss(p, w.nbig, w.m_big, w.xv_helio, w.rp_km, w.rhop, w_small,
+                               w.nsteps, dxv, np.zeros(3))
+        ours = float((gx * dxv).sum())
+        assert abs(Lo - float(L.detach())) <= 1e-9 * abs(Lo)
+        assert abs(ours - jvp) <= 1e-6 * abs(jvp), (ours, jvp)
