@@ -264,3 +264,54 @@ def test_adjoint_through_big_body_encounters_vs_oracle_jvp(mask):
         ours = float((gx * dxv).sum())
         assert abs(Lo - float(L.detach())) <= 1e-9 * abs(Lo)
         assert abs(ours - jvp) <= 1e-6 * abs(jvp), (ours, jvp)
+
+
+def test_semiactive_full_size_adjoint_sampled():
+    """The semi-active disk at full size (2,000 embryos, which meet each other
+    every step, + 200,000 planetesimals), 20 steps checkpointed every 10, with
+    the masked loss on 300 sampled planetesimals that met no embryo (mode 2:
+    the groups of big bodies only).  Being massless, the sample moves as
+    inside the full disk, so the oracle's JVP over the embryos and the sample
+    is the reference: relative <= 1e-6 (the embryos' groups run on each
+    side's own integrator).  The other planetesimals get a zero gradient."""
+    from paper_2601_16791_gb300.autograd import Trajectory, semimajor_loss
+    w = W.semiactive_2000big_200k(nsteps=20)
+    w.checkpoint_every = 10
+    rng = np.random.default_rng(23)
+    p = orc.make_params(w.params)
+    cand = np.sort(rng.choice(w.nsmall, 400, replace=False))
+    cols0 = np.concatenate([np.arange(w.nbig), w.nbig + cand])
+    xv, mu, rc = orc.init(p, w.nbig, len(cand), w.m_big, w.xv_helio[:, cols0].copy())
+    _, ever_o, _, _ = orc.step(p, w.nbig, xv, mu, rc, w.rp_km[cand], w.rhop[cand], w.nsteps)
+    assert ever_o[:w.nbig].sum() > 100, "no big-body groups: the test is vacuous"
+    sel = cand[ever_o[w.nbig:] == 0][:300]
+    assert len(sel) == 300
+    cols = np.concatenate([np.arange(w.nbig), w.nbig + sel])
+    traj = Trajectory(w)
+    g = w.params["gas"]
+    xv0 = torch.tensor(w.xv_helio, dtype=torch.float64, device="cuda", requires_grad=True)
+    gas = torch.tensor([g["sigma1_gcm2"], g["gamma"], g["cd_scale"]], dtype=torch.float64,
+                       device="cuda", requires_grad=True)
+    w_s = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    w_s[torch.as_tensor(w.nbig + sel, device="cuda")] = 1.0 / len(sel)
+    L = semimajor_loss(traj, xv0, gas, w_s, w.nsteps, w.checkpoint_every, mask_encounters=True)
+    L.backward()
+    gx = xv0.grad.cpu().numpy()
+    ever = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    nbb = mx.mx_encounter_log(traj.h, ever)
+    traj.close()
+    assert nbb > 100 and not ever.cpu().numpy()[w.nbig + sel].any()
+    rest = np.ones(w.n, dtype=bool)
+    rest[cols] = False
+    assert not gx[:, rest].any()
+    w_o = np.full(len(sel), 1.0 / len(sel))
+    xh = w.xv_helio[:, cols].copy()
+    for _ in range(3):
+        dxv = np.zeros((6, len(cols)))
+        dxv[:3] = rng.normal(0, 1e-4, (3, len(cols)))
+        dxv[3:] = rng.normal(0, 1e-6, (3, len(cols)))
+        Lo, jvp = orc.jvp_loss(p, w.nbig, w.m_big, xh, w.rp_km[sel], w.rhop[sel], w_o, w.nsteps,
+                               dxv, np.zeros(3))
+        ours = float((gx[:, cols] * dxv).sum())
+        assert abs(Lo - float(L.detach())) <= 1e-9 * abs(Lo)
+        assert abs(ours - jvp) <= 1e-6 * abs(jvp), (ours, jvp)
