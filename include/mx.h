@@ -434,7 +434,14 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
  * extrapolation rows held fixed); with them off it is differentiated as if
  * drifted, which is exact when its cotangent is zero (a loss that leaves it
  * out; it is massless, so nothing else depends on it).  Big bodies that meet
- * are differentiated through their own groups in modes 1 and 2. */
+ * are differentiated through their own groups in modes 1 and 2.
+ * The groups' record (128 accepted sub-steps reserved per group) grows to
+ * what the step needs; the step waits once on the device to size it.
+ * Errors: MX_ERR_ARG; MX_ERR_OOM when the record cannot grow;
+ * MX_ERR_BS_NOCONV when a group needs more than 128 accepted sub-steps or
+ * hits the sub-step cap; the step's own errors (MX_ERR_PAIR_OVERFLOW,
+ * MX_ERR_GROUP_TOO_LARGE, ...).  On an error in the recomputation up to the
+ * groups' plan, dev_lambda and dev_dparams are unchanged. */
 mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long step_k,
                           double* dev_lambda, double* dev_dparams);
 

@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(1024) k_adj_tape(Dev d, Adj a) {
     if (w < W) a.g_off[w] = s_wsum[warp] + inc - v;
     __syncthreads();
   }
+  if (threadIdx.x == 0) *a.tape_need = s_run;
 }
 
 // Item w's members in the step's order (big bodies ascending, then the
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(32) k_adj_bs_fwd(Dev d, Adj a) {
     }
     if (lane == 0) {
       if (!ok) {
-        atomicOr(d.status, M >= kAdjMaxSteps ? ST_WORK_OVF : ST_BS);
+        atomicOr(d.status, M >= kAdjMaxSteps ? ST_TAPE : ST_BS);
         a.g_M[g] = -1;
       } else {
         a.g_M[g] = M;
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(128) k_adj_bs_fwd2(Dev d, Adj a) {
     }
     if (c == 0 && lane == 0) {
       if (!ok) {
-        atomicOr(d.status, M >= kAdjMaxSteps ? ST_WORK_OVF : ST_BS);
+        atomicOr(d.status, M >= kAdjMaxSteps ? ST_TAPE : ST_BS);
         a.g_M[g] = -1;
       } else {
         a.g_M[g] = M;
@@ -880,7 +881,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
   if (t < 3) a.bs_xsum[3 * sys + t] = red[t][0];
 }
 
-void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
+void launch_adjoint_bs_plan(const Dev& d, const Adj& a, cudaStream_t st) {
   // detection on the recomputed endpoints, without touching the step's log
   // (encounter flags, big-big count, deferral history)
   Dev dd = d;
@@ -894,6 +895,9 @@ void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t
   launch_sort_keys(d.keys, d.pair_count, d.pair_cap, 0, st);
   launch_groups(dd, st);   // the step's own groups: big groups, then test-particle groups
   k_adj_tape<<<1, 1024, 0, st>>>(dd, a);
+}
+
+void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
   k_adj_bs_fwd<<<nblocks, 32, 0, st>>>(d, a);    // every item but the test-particle pairs
   k_adj_bs_fwd2<<<nblocks, 128, 0, st>>>(d, a);  // test-particle pairs
 }

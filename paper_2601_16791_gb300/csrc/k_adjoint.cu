@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_jump1(Dev d, Adj a) {
   }
 }
 
-void launch_adjoint_step(const Dev& d, const Adj& a, cudaStream_t st) {
+void launch_adjoint_step_a(const Dev& d, const Adj& a, cudaStream_t st) {
   const int N = d.N;
   // forward recomputation
   k_adj_momentum<<<d.nsys, kThreads, 0, st>>>(d, a.z0 + 3 * (size_t)N, a.z0 + 4 * (size_t)N,
@@ -694,6 +694,11 @@ void launch_adjoint_step(const Dev& d, const Adj& a, cudaStream_t st) {
   k_adj_kick1_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a);
   k_adj_momentum<<<d.nsys, kThreads, 0, st>>>(d, a.v1, a.v1 + N, a.v1 + 2 * (size_t)N, a.P, 1);
   k_adj_move_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a, 1);
+  if (a.groups) launch_adjoint_bs_plan(d, a, st);
+}
+
+void launch_adjoint_step_b(const Dev& d, const Adj& a, cudaStream_t st) {
+  const int N = d.N;
   if (a.groups) launch_adjoint_bs_fwd(d, a, a.bs_blocks, st);
   k_adj_momentum<<<d.nsys, kThreads, 0, st>>>(d, a.xv3 + 3 * (size_t)N, a.xv3 + 4 * (size_t)N,
                                                a.xv3 + 5 * (size_t)N, a.P, 2);

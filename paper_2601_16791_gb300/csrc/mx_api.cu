@@ -101,6 +101,8 @@ mx_status status_to_code(unsigned st) {
     return fail(MX_ERR_GROUP_TOO_LARGE, "encounter group larger than MX_MAX_GROUP bodies");
   if (st & mx::ST_WORK_OVF) return fail(MX_ERR_PAIR_OVERFLOW, "encounter work list overflow");
   if (st & mx::ST_BS) return fail(MX_ERR_BS_NOCONV, "Bulirsch-Stoer hit its sub-step cap");
+  if (st & mx::ST_TAPE)
+    return fail(MX_ERR_BS_NOCONV, "an adjoint encounter group took more than 128 accepted sub-steps");
   if (st & mx::ST_BARRIER) return fail(MX_ERR_BARRIER_TIMEOUT, "device wait gave up");
   if (st & mx::ST_WINDOW) return fail(MX_ERR_CUDA, "deferral window longer than its history");
   return MX_OK;
@@ -224,6 +226,8 @@ struct mx_system {
   unsigned long long* a_goff = nullptr;
   double *a_gcontrib = nullptr, *a_tape = nullptr, *a_bsx = nullptr;
   unsigned long long a_tape_cap = 0;
+  unsigned long long* a_need = nullptr;   // device: doubles the step's groups reserve
+  unsigned long long* h_need = nullptr;   // pinned copy
   // kept Stoermer sub-steps of two-body records (mx_adjoint_store)
   double* a_sub = nullptr;
   unsigned* a_subn = nullptr;
@@ -892,6 +896,7 @@ void destroy_impl(mx_system* s) {
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_status) cudaFreeHost(s->h_status);
   if (s->h_count) cudaFreeHost(s->h_count);
+  if (s->h_need) cudaFreeHost(s->h_need);
   if (s->side_st) {
     cudaStreamSynchronize(s->side_st);
     cudaStreamDestroy(s->side_st);
@@ -1746,9 +1751,24 @@ namespace {
 
 // Per-tile partial records for the adjoint and the loss: 3 doubles per big
 // body of the tile's system plus 9.
-// The doubles of the adjoint's recorded Bulirsch-Stoer sub-steps (each group
-// has room for 128 sub-steps; a two-body group's sub-step takes 15 doubles).
+// The doubles of the adjoint's recorded Bulirsch-Stoer sub-steps to start
+// with (each group reserves room for 128 sub-steps; a two-body group's
+// sub-step takes 15 doubles).  The tape grows to what a step's groups reserve.
 constexpr size_t kAdjTape = (size_t)1 << 23;
+
+// Makes the tape hold `need` doubles, with a quarter to spare (the stream is
+// idle: the caller has synchronised it).
+mx_status grow_tape(mx_system* s, unsigned long long need) {
+  if (need <= s->a_tape_cap) return MX_OK;
+  const unsigned long long cap = std::max(need + need / 4, 2 * s->a_tape_cap);
+  MX_CUDA(cudaFree(s->a_tape));
+  s->allocs.erase(std::remove(s->allocs.begin(), s->allocs.end(), (void*)s->a_tape), s->allocs.end());
+  s->a_tape = nullptr;
+  s->a_tape_cap = 0;
+  MX_TRY(dalloc(s, &s->a_tape, (size_t)cap));
+  s->a_tape_cap = cap;
+  return MX_OK;
+}
 
 // The step's device view with the adjoint's tiling.
 mx::Dev adjoint_dev(const mx_system* s) {
@@ -1778,6 +1798,9 @@ mx_status ensure_adjoint(mx_system* s) {
     MX_TRY(dalloc(s, &s->a_goff, gcap));
     MX_TRY(dalloc(s, &s->a_gcontrib, (size_t)gcap * mx::kMaxGroup * 6));
     MX_TRY(dalloc(s, &s->a_tape, kAdjTape));
+    MX_TRY(dalloc(s, &s->a_need, 1));
+    if (cudaMallocHost(&s->h_need, sizeof(unsigned long long)) != cudaSuccess)
+      return fail(MX_ERR_OOM, "cudaMallocHost");
     MX_TRY(dalloc(s, &s->a_subn, 1));
     MX_TRY(dalloc(s, &s->a_bsx, 3 * s->h_sys.size()));
     s->a_tape_cap = kAdjTape;
@@ -1967,12 +1990,23 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   a.g_contrib = s->a_gcontrib;
   a.tape = s->a_tape;
   a.tape_cap = s->a_tape_cap;
+  a.tape_need = s->a_need;
   a.bs_xsum = s->a_bsx;
   a.sub = s->a_sub;
   a.sub_count = s->a_subn;
   a.sub_cap = s->a_sub_cap;
   (void)N;
-  mx::launch_adjoint_step(adjoint_dev(s), a, s->st);
+  const mx::Dev d = adjoint_dev(s);
+  mx::launch_adjoint_step_a(d, a, s->st);
+  if (a.groups) {   // the groups' tape, sized from their plan
+    MX_CUDA(cudaMemcpyAsync(s->h_need, s->a_need, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            s->st));
+    MX_TRY(sync_status(s));
+    MX_TRY(grow_tape(s, *s->h_need));
+    a.tape = s->a_tape;
+    a.tape_cap = s->a_tape_cap;
+  }
+  mx::launch_adjoint_step_b(d, a, s->st);
   return sync_status(s);
 }
 

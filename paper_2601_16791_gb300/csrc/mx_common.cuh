@@ -41,6 +41,7 @@ enum : unsigned {
   ST_BARRIER = 1u << 4,
   ST_GROUP = 1u << 5,
   ST_WORK_OVF = 1u << 6,
+  ST_TAPE = 1u << 7,     // an adjoint group needed more sub-steps than its tape holds
   ST_WINDOW = 1u << 8
 };
 
@@ -211,6 +212,7 @@ struct Adj {
   double* g_contrib;             // [g_cap][kMaxGroup][6] shares of members not written back
   double* tape;                  // accepted sub-steps: H, row, 6 x nb start state, slot
   unsigned long long tape_cap;   // doubles
+  unsigned long long* tape_need; // doubles the step's groups reserve (k_adj_tape)
   double* bs_xsum;               // 3 per system: sum of the big shares' position parts
   // two-body groups: the Stoermer sub-steps of each accepted macro sub-step,
   // kAdjSubRec doubles a slot (null: none are kept, the reverse recomputes)

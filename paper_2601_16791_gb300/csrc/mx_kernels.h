@@ -68,9 +68,14 @@ void launch_stat_count(const Dev& d, int* out, cudaStream_t st);
 void launch_radius(const Dev& d, cudaStream_t st);
 
 // k_adjoint.cu
-void launch_adjoint_step(const Dev& d, const Adj& a, cudaStream_t st);
+// The adjoint step in two parts: the forward recomputation up to the drift,
+// with the encounter groups' tape plan (its size in doubles in *a.tape_need)
+// when a.groups; then the groups' integration and the reverse sweep.
+void launch_adjoint_step_a(const Dev& d, const Adj& a, cudaStream_t st);
+void launch_adjoint_step_b(const Dev& d, const Adj& a, cudaStream_t st);
 // k_adj_bs.cu: the step's encounter groups inside the adjoint (forward with a
 // tape, reverse, per-system fold of the big bodies' shares)
+void launch_adjoint_bs_plan(const Dev& d, const Adj& a, cudaStream_t st);
 void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t st);
 void launch_adjoint_bs_vjp(const Dev& d, const Adj& a, int nblocks, cudaStream_t st);
 void launch_adjoint_bs_fold(const Dev& d, const Adj& a, cudaStream_t st);
