@@ -71,11 +71,12 @@ __device__ __forceinline__ bool adj_takes(const Dev& d, const Adj& a, int w) {
 // the forward kernels set it.
 __global__ void __launch_bounds__(1024) k_adj_tape(Dev d, Adj a) {
   __shared__ unsigned long long s_wsum[32];
-  __shared__ unsigned long long s_run;
+  __shared__ unsigned long long s_run, s_ent;
   const int W = min(*d.work_count, a.g_cap);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     s_run = 0;
+    s_ent = 0;
     if (a.sub_count) *a.sub_count = 0;
   }
   __syncthreads();
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(1024) k_adj_tape(Dev d, Adj a) {
         const int o = d.work_off[w], nb = d.work_off[w + 1] - o;
         v = (unsigned long long)kAdjMaxSteps * tape_stride(min(nb, kMaxGroup));
         for (int m = d.work_wfrom[w]; m < nb; ++m) d.flags[d.work_mem[o + m]] = 2;
+        if (d.work_wfrom[w] > 0) atomicAdd(&s_ent, (unsigned long long)d.work_wfrom[w]);
       }
     }
     unsigned long long inc = v;
@@ -110,7 +112,10 @@ __global__ void __launch_bounds__(1024) k_adj_tape(Dev d, Adj a) {
     if (w < W) a.g_off[w] = s_wsum[warp] + inc - v;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *a.tape_need = s_run;
+  if (threadIdx.x == 0) {
+    a.tape_need[0] = s_run;
+    a.tape_need[1] = s_ent;
+  }
 }
 
 // Item w's members in the step's order (big bodies ascending, then the
@@ -817,12 +822,52 @@ __global__ void __launch_bounds__(96) k_adj_bs_vjp2(Dev d, Adj a) {
   }
 }
 
+// Many big bodies: one key per share of a member that a group does not write
+// back, (body << 32 | item kMaxGroup + member), for k_sort_keys; the order of
+// the sorted keys does not depend on the order they are written in.
+__global__ void __launch_bounds__(kThreads) k_adj_share_keys(Dev d, Adj a) {
+  const int W = min(*d.work_count, a.g_cap);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < W; g += gridDim.x * blockDim.x) {
+    const int wf = d.work_wfrom[g];
+    if (wf == 0 || !adj_takes(d, a, g)) continue;
+    const int o = d.work_off[g];
+    const int e0 = atomicAdd(a.scount, wf);
+    for (int m = 0; m < wf; ++m) {
+      if (e0 + m >= a.skeys_cap) {
+        atomicOr(d.status, ST_WORK_OVF);
+        break;
+      }
+      a.skeys[e0 + m] = ((unsigned long long)d.work_mem[o + m] << 32) |
+                        (unsigned long long)(g * kMaxGroup + m);
+    }
+  }
+}
+
+// Each run of sorted keys of one body: its shares added in item order.
+__global__ void __launch_bounds__(kThreads) k_adj_share_sum(Dev d, Adj a) {
+  const int n = min(*a.scount, a.skeys_cap);
+  const int N = d.N;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const unsigned body = (unsigned)(a.skeys[p] >> 32);
+    if (p > 0 && (unsigned)(a.skeys[p - 1] >> 32) == body) continue;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = p; q < n && (unsigned)(a.skeys[q] >> 32) == body; ++q) {
+      const unsigned e = (unsigned)(a.skeys[q] & 0xffffffffull);
+      if (a.g_M[e / kMaxGroup] < 0) continue;
+      const double* c6 = a.g_contrib + (size_t)e * 6;
+      for (int c = 0; c < 6; ++c) acc[c] += c6[c];
+    }
+    for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + body] += acc[c];
+  }
+}
+
 // Per system: the shares of the members a group does not write back (big
 // bodies of test-particle groups) and the sum of their position parts for
 // jump 1's momentum term.  With up to 64 big bodies a system's sums run over
 // the items on all threads of the block (thread t takes items t, t + 256, ...
-// in order) and end in a fixed pairwise tree; with more, one thread per big
-// body adds its shares in item order.  Either way the order is fixed.
+// in order) and end in a fixed pairwise tree; with more (sorted_shares, for
+// every system), k_adj_share_sum has added each body's shares in item order.
+// Either way the order is fixed.
 __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
   __shared__ double red[6][kThreads];
   const int sys = blockIdx.x;
@@ -850,7 +895,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
       for (int c = 0; c < 6; ++c) acc[c] += c6[c];
     }
   };
-  if (S.nbig <= 64) {
+  if (a.sorted_shares) {
+    // the shares were added by k_adj_share_sum
+  } else if (S.nbig <= 64) {
     for (int i = 0; i < S.nbig; ++i) {
       double acc[6] = {0, 0, 0, 0, 0, 0};
       for (int g = t; g < ng; g += kThreads)
@@ -860,15 +907,6 @@ __global__ void __launch_bounds__(kThreads) k_adj_bs_fold(Dev d, Adj a) {
         for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + S.off + i] += red[c][0];
       __syncthreads();
     }
-  } else {
-    for (int i = t; i < S.nbig; i += blockDim.x) {
-      double acc[6] = {0, 0, 0, 0, 0, 0};
-      for (int g = 0; g < ng; ++g)
-        if (in_sys(g)) add_share(g, i, acc);
-      const int gi = S.off + i;
-      for (int c = 0; c < 6; ++c) a.lam[(size_t)c * N + gi] += acc[c];
-    }
-    __syncthreads();
   }
   double sx[3] = {0, 0, 0};
   for (int g = t; g < ng; g += kThreads) {
@@ -898,6 +936,11 @@ void launch_adjoint_bs_plan(const Dev& d, const Adj& a, cudaStream_t st) {
 }
 
 void launch_adjoint_bs_fwd(const Dev& d, const Adj& a, int nblocks, cudaStream_t st) {
+  if (a.sorted_shares) {
+    cudaMemsetAsync(a.scount, 0, sizeof(int), st);
+    k_adj_share_keys<<<a.bs_blocks, kThreads, 0, st>>>(d, a);
+    launch_sort_keys(a.skeys, a.scount, a.skeys_cap, 0, st);
+  }
   k_adj_bs_fwd<<<nblocks, 32, 0, st>>>(d, a);    // every item but the test-particle pairs
   k_adj_bs_fwd2<<<nblocks, 128, 0, st>>>(d, a);  // test-particle pairs
 }
@@ -909,6 +952,7 @@ void launch_adjoint_bs_vjp(const Dev& d, const Adj& a, int nblocks, cudaStream_t
 }
 
 void launch_adjoint_bs_fold(const Dev& d, const Adj& a, cudaStream_t st) {
+  if (a.sorted_shares) k_adj_share_sum<<<a.bs_blocks, kThreads, 0, st>>>(d, a);
   k_adj_bs_fold<<<d.nsys, kThreads, 0, st>>>(d, a);
 }
 

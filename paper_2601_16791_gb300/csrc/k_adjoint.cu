@@ -309,9 +309,52 @@ __device__ __forceinline__ int kick_branch(const Dev& d, int kick, int j) {
   return (d.kbits[(size_t)kick * d.kwords + (j >> 5)] >> (j & 31)) & 1u;
 }
 
+// Big bodies staged in shared memory per pass of the adjoint's kicks.
+constexpr int kAdjChunk = 128;
+
+// The changeover constants of a pair (rc^2, 0.01 rc^2, 0.1 rc, 1/(0.9 rc)
+// with rc = max(rc_i, rc_j), Sec. 2.1.3): the big body's, or the target's
+// own when the target is a big body with the larger radius.  They grow with
+// rc, so comparing rc^2 picks the larger radius.
+struct PairRc {
+  double rc2, lo, r01, i09;
+};
+__device__ __forceinline__ PairRc pair_rc(const double (*sc)[kAdjChunk], int k, const PairRc& own) {
+  PairRc c{sc[0][k], sc[1][k], sc[2][k], sc[3][k]};
+  // compared on the bit patterns (non-negative doubles), off the FP64 pipe
+  if (__double_as_longlong(own.rc2) > __double_as_longlong(c.rc2)) c = own;
+  return c;
+}
+
+// A target's own changeover constants (zero for a planetesimal).
+__device__ __forceinline__ PairRc target_rc(const Dev& d, const SysDev& S, int jl) {
+  PairRc c{0.0, 0.0, 0.0, 0.0};
+  if (jl < S.nbig) {
+    const size_t b = S.boff + jl;
+    c = PairRc{d.brc4[b], d.brc4[(size_t)d.NB + b], d.brc4[2 * (size_t)d.NB + b],
+               d.brc4[3 * (size_t)d.NB + b]};
+  }
+  return c;
+}
+
+// Positions, masses and changeover constants of a chunk of big bodies.
+__device__ __forceinline__ void stage_chunk(const Dev& d, const SysDev& S, const double* X, int c0,
+                                            int cn, double* sx, double* sy, double* sz, double* sm,
+                                            double (*sc)[kAdjChunk]) {
+  const int N = d.N;
+  for (int k = threadIdx.x; k < cn; k += blockDim.x) {
+    const int g = S.off + c0 + k;
+    const size_t b = S.boff + c0 + k;
+    sx[k] = X[g]; sy[k] = X[(size_t)N + g]; sz[k] = X[2 * (size_t)N + g];
+    sm[k] = d.bmu[b];
+    for (int q = 0; q < 4; ++q) sc[q][k] = d.brc4[(size_t)q * d.NB + b];
+  }
+}
+
 // Kick 1 forward: v1 = v0 + (h/2)(a_grav(x0) + a_drag(x0, v0 + P0/m0)).
 __global__ void __launch_bounds__(kThreads) k_adj_kick1_fwd(Dev d, Adj a) {
-  __shared__ double sx[kBigChunk], sy[kBigChunk], sz[kBigChunk], sm[kBigChunk], sr[kBigChunk];
+  __shared__ double sx[kAdjChunk], sy[kAdjChunk], sz[kAdjChunk], sm[kAdjChunk];
+  __shared__ double sc[4][kAdjChunk];
   const Tile t = d.tiles[blockIdx.x];
   const SysDev& S = d.sys[t.sys];
   const int N = d.N;
@@ -319,28 +362,23 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick1_fwd(Dev d, Adj a) {
   const int j = t.start + threadIdx.x;
   const int jl = j - S.off;
   const double* P0 = a.P + 9 * t.sys;
-  double x = 0, y = 0, z = 0, u = 0, v = 0, w = 0, rcj = 0;
+  double x = 0, y = 0, z = 0, u = 0, v = 0, w = 0;
   if (act) {
     x = a.z0[j]; y = a.z0[(size_t)N + j]; z = a.z0[2 * (size_t)N + j];
     u = a.z0[3 * (size_t)N + j]; v = a.z0[4 * (size_t)N + j]; w = a.z0[5 * (size_t)N + j];
-    if (jl < S.nbig) rcj = d.brc[S.boff + jl];
   }
+  const PairRc trc = target_rc(d, S, act ? jl : S.nbig);
   double ax = 0, ay = 0, az = 0;
-  for (int c0 = 0; c0 < S.nbig; c0 += kBigChunk) {
-    const int cn = min(kBigChunk, S.nbig - c0);
+  for (int c0 = 0; c0 < S.nbig; c0 += kAdjChunk) {
+    const int cn = min(kAdjChunk, S.nbig - c0);
     __syncthreads();
-    for (int k = threadIdx.x; k < cn; k += blockDim.x) {
-      const int g = S.off + c0 + k;
-      sx[k] = a.z0[g]; sy[k] = a.z0[(size_t)N + g]; sz[k] = a.z0[2 * (size_t)N + g];
-      sm[k] = d.bmu[S.boff + c0 + k]; sr[k] = d.brc[S.boff + c0 + k];
-    }
+    stage_chunk(d, S, a.z0, c0, cn, sx, sy, sz, sm, sc);
     __syncthreads();
     if (!act) continue;
     for (int k = 0; k < cn; ++k) {
       if (c0 + k == jl) continue;
-      const double rc = fmax(sr[k], rcj);
-      pair_acc(x - sx[k], y - sy[k], z - sz[k], sm[k], rc * rc, 0.01 * (rc * rc), 0.1 * rc,
-               (rc > 0.0) ? 1.0 / (0.9 * rc) : 0.0, ax, ay, az);
+      const PairRc c = pair_rc(sc, k, trc);
+      pair_acc(x - sx[k], y - sy[k], z - sz[k], sm[k], c.rc2, c.lo, c.r01, c.i09, ax, ay, az);
     }
   }
   if (!act) return;
@@ -381,16 +419,54 @@ __global__ void __launch_bounds__(kThreads) k_adj_move_fwd(Dev d, Adj a, int sta
   }
 }
 
+// The cotangent a pair gives the target's position, mu J l with J the
+// Jacobian of the pair's acceleration -mu K(s) d/s^3 and l the cotangent of
+// the acceleration: J l = -(K/s^3 l + (K' s - 3K)/s^5 d (d.l)) (the big body's
+// position gets the opposite).  1/s from the single-precision estimate, as in
+// the forward's pair weight; zero inside 0.1 rc, where K = 0.
+__device__ __forceinline__ void pair_vjp(double dx, double dy, double dz, double mu,
+                                         const PairRc& c, double lax, double lay, double laz,
+                                         double& jx, double& jy, double& jz) {
+  const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
+  jx = jy = jz = 0.0;
+  if (__double_as_longlong(s2) <= __double_as_longlong(c.lo)) return;
+  const double y = float_to_double_bits(rsqrtf(abs_to_float_bits(s2)));
+  const double e = fma(-s2 * y, y, 1.0);
+  const double is = fma(y * e, fma(0.375, e, 0.5), y);   // 1/s
+  const double is2 = is * is;
+  const double mis3 = mu * (is2 * is);
+  double K = 1.0, t = -3.0;   // K and K' s - 3K
+  if (__double_as_longlong(s2) < __double_as_longlong(c.rc2)) {
+    const double sv = s2 * is;
+    const double q = (sv - c.r01) * c.i09;
+    const double omq = 1.0 - q;
+    K = q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
+    t = fma(30.0 * q * q * omq * omq * c.i09, sv, -3.0 * K);
+  }
+  const double dl = fma(dx, lax, fma(dy, lay, dz * laz));
+  const double A = mis3 * K, B = (mis3 * is2) * (t * dl);
+  jx = fma(A, lax, B * dx);
+  jy = fma(A, lay, B * dy);
+  jz = fma(A, laz, B * dz);
+}
+
 // Reverse of a half kick at positions X (3 x N), velocities V (3 x N) and
 // momentum Pk, with the cotangent in a.lam: lam_x += (h/2) J^T lam_v,
 // lam_v += (h/2) (d a_drag/d v)^T lam_v.  Per-tile partials: the cotangent
 // each big body's position receives from all targets, the drag's share of
 // the momentum cotangent, the sum of the targets' own position cotangents
 // (for the jump before this kick), and the parameter cotangents.
-constexpr int kAdjChunk = 128;
+//
+// A warp's sums for the big bodies go round its lanes: the chunk's bodies
+// are taken W at a time (W the largest power of two <= those left, at most
+// 32); in round r, lane l of each W-lane group takes body (l + r) mod W of
+// the batch and then passes its running sum for that body to the lane before
+// it, so each body's sum visits the group's targets in a fixed order with
+// one shuffle a pair, and the groups' sums are added at the end.
 __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const double* X,
                                                            const double* V, int pslot, int kick) {
-  __shared__ double sx[kAdjChunk], sy[kAdjChunk], sz[kAdjChunk], sm[kAdjChunk], sr[kAdjChunk];
+  __shared__ double sx[kAdjChunk], sy[kAdjChunk], sz[kAdjChunk], sm[kAdjChunk];
+  __shared__ double sc[4][kAdjChunk];
   __shared__ double wpart[kThreads / 32][kAdjChunk][3];
   __shared__ double wsum[kThreads / 32][9];
   const Tile t = d.tiles[blockIdx.x];
@@ -404,66 +480,57 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
   const double* Pk = a.P + 9 * t.sys + 3 * pslot;
   const double th = 0.5 * S.h;
   double* rec = a.part + a.poff[blockIdx.x];
-  double x = 0, y = 0, z = 0, lvx = 0, lvy = 0, lvz = 0, rcj = 0;
+  double x = 0, y = 0, z = 0, lvx = 0, lvy = 0, lvz = 0;
   if (act) {
     x = X[j]; y = X[(size_t)N + j]; z = X[2 * (size_t)N + j];
     lvx = a.lam[3 * (size_t)N + j]; lvy = a.lam[4 * (size_t)N + j]; lvz = a.lam[5 * (size_t)N + j];
-    if (jl < S.nbig) rcj = d.brc[S.boff + jl];
   }
+  const PairRc trc = target_rc(d, S, act ? jl : S.nbig);
   // cotangent of the kick's acceleration
   const double lax = th * lvx, lay = th * lvy, laz = th * lvz;
   double gx = 0, gy = 0, gz = 0;   // into lam_x of this target
   for (int c0 = 0; c0 < S.nbig; c0 += kAdjChunk) {
     const int cn = min(kAdjChunk, S.nbig - c0);
     __syncthreads();
-    for (int k = threadIdx.x; k < cn; k += blockDim.x) {
-      const int g = S.off + c0 + k;
-      sx[k] = X[g]; sy[k] = X[(size_t)N + g]; sz[k] = X[2 * (size_t)N + g];
-      sm[k] = d.bmu[S.boff + c0 + k]; sr[k] = d.brc[S.boff + c0 + k];
-    }
+    stage_chunk(d, S, X, c0, cn, sx, sy, sz, sm, sc);
     __syncthreads();
-    for (int k = 0; k < cn; ++k) {
-      double jx = 0, jy = 0, jz = 0;
-      if (act && c0 + k != jl) {
-        const double dx = x - sx[k], dy = y - sy[k], dz = z - sz[k];
-        const double rc = fmax(sr[k], rcj);
-        const double rc2 = rc * rc;
-        const double s2 = dx * dx + dy * dy + dz * dz;
-        if (s2 > 0.01 * rc2) {
-          const double is = 1.0 / sqrt(s2);
-          const double s = s2 * is;
-          const double is3 = is * is * is;
-          double K = 1.0, Kp = 0.0;
-          if (s2 < rc2) {
-            const double q = (s - 0.1 * rc) / (0.9 * rc);
-            K = q * q * q * (10.0 + q * (-15.0 + 6.0 * q));
-            Kp = 30.0 * q * q * (1.0 - q) * (1.0 - q) / (0.9 * rc);
-          }
-          // J l = K/s^3 l + (K' s - 3K)/s^5 d (d.l), l = cotangent of the acceleration
-          const double dl = dx * lax + dy * lay + dz * laz;
-          const double c1 = K * is3, c2 = (Kp * s - 3.0 * K) * is3 * is * is * dl;
-          jx = c1 * lax + c2 * dx;
-          jy = c1 * lay + c2 * dy;
-          jz = c1 * laz + c2 * dz;
-          gx -= sm[k] * jx;
-          gy -= sm[k] * jy;
-          gz -= sm[k] * jz;
-          jx *= sm[k];
-          jy *= sm[k];
-          jz *= sm[k];
+    for (int base = 0; base < cn;) {
+      const int left = cn - base;
+      const int W = left >= 32 ? 32 : 1 << (31 - __clz(left));
+      const int gl = lane & (W - 1);
+      double bx = 0, by = 0, bz = 0;   // the running sum of the body this lane holds
+      for (int r = 0; r < W; ++r) {
+        const int k = base + ((gl + r) & (W - 1));
+        if (act && c0 + k != jl) {
+          double jx, jy, jz;
+          pair_vjp(x - sx[k], y - sy[k], z - sz[k], sm[k], pair_rc(sc, k, trc), lax, lay, laz,
+                   jx, jy, jz);
+          gx -= jx;
+          gy -= jy;
+          gz -= jz;
+          bx += jx;
+          by += jy;
+          bz += jz;
+        }
+        if (r + 1 < W) {
+          const int src = (gl + 1) & (W - 1);
+          bx = __shfl_sync(0xffffffffu, bx, src, W);
+          by = __shfl_sync(0xffffffffu, by, src, W);
+          bz = __shfl_sync(0xffffffffu, bz, src, W);
         }
       }
-      // the big body's position gets +mu_i J l: sum over the warp in a fixed tree
-      for (int off = 16; off > 0; off >>= 1) {
-        jx += __shfl_down_sync(0xffffffffu, jx, off);
-        jy += __shfl_down_sync(0xffffffffu, jy, off);
-        jz += __shfl_down_sync(0xffffffffu, jz, off);
+      for (int off = W; off < 32; off <<= 1) {
+        bx += __shfl_down_sync(0xffffffffu, bx, off);
+        by += __shfl_down_sync(0xffffffffu, by, off);
+        bz += __shfl_down_sync(0xffffffffu, bz, off);
       }
-      if (lane == 0) {
-        wpart[warp][k][0] = jx;
-        wpart[warp][k][1] = jy;
-        wpart[warp][k][2] = jz;
+      if (lane < W) {
+        const int k = base + ((gl + W - 1) & (W - 1));
+        wpart[warp][k][0] = bx;
+        wpart[warp][k][1] = by;
+        wpart[warp][k][2] = bz;
       }
+      base += W;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < cn; k += blockDim.x) {
@@ -547,6 +614,31 @@ __device__ void fold_tiles(const double* p0, int R, int T, int V, double* out) {
   __syncthreads();
 }
 
+// Systems with more than (kThreads - 9) / 3 big bodies: block (sys, y) folds
+// the tile partials of the big bodies' position cotangents 3 per body, values
+// y kThreads .. (y + 1) kThreads - 1 of the system, one thread a value over
+// four interleaved strands of tiles added in a fixed order; adds them to
+// lam_x and keeps them for k_adj_fold_kick.
+__global__ void __launch_bounds__(kThreads) k_adj_fold_big(Dev d, Adj a) {
+  const int sys = blockIdx.x;
+  const SysDev& S = d.sys[sys];
+  const int nb = S.nbig, R = 3 * nb + 9;
+  if (R <= kThreads) return;
+  const int v = blockIdx.y * kThreads + threadIdx.x;
+  if (v >= 3 * nb) return;
+  const int t0 = a.sys_tiles[sys], T = a.sys_tiles[sys + 1] - t0;
+  const double* p0 = a.part + (T > 0 ? a.poff[t0] : 0) + v;
+  double acc[4] = {0, 0, 0, 0};
+  int k = 0;
+  for (; k + 4 <= T; k += 4)
+    for (int q = 0; q < 4; ++q) acc[q] += p0[(size_t)(k + q) * R];
+  for (int q = 0; k < T; ++k, ++q) acc[q] += p0[(size_t)k * R];
+  const double f = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  const int i = v / 3, c = v - 3 * i;
+  a.lam[(size_t)c * d.N + S.off + i] += f;
+  a.bfold[3 * (size_t)S.boff + v] = f;
+}
+
 // Per system: fold the tile partials of a kick's reverse (fixed order).
 //  kick 2: lam_x(big) += G; lam_P3 = dP_drag + (h/2)/m0 (sum_j lam_x4_j);
 //          lam_v(big) += mu lam_P3.
@@ -574,26 +666,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_kick(Dev d, Adj a, int wh
     }
     if (threadIdx.x < 9) tot[threadIdx.x] = fold[3 * nb + threadIdx.x];
   } else {
-    // many big bodies: one thread per big body adds its shares in tile order
+    // many big bodies: k_adj_fold_big has added their cotangents and left
+    // them in a.bfold; their sum in big order for sum_j lam_x4_j
     double gs[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-      double g0 = 0, g1 = 0, g2 = 0;
-      for (int k = 0; k < T; ++k) {
-        const double* rec = p0 + (size_t)k * R;
-        g0 += rec[3 * i];
-        g1 += rec[3 * i + 1];
-        g2 += rec[3 * i + 2];
-      }
-      const int g = S.off + i;
-      a.lam[g] += g0;
-      a.lam[(size_t)N + g] += g1;
-      a.lam[2 * (size_t)N + g] += g2;
-      gs[0] += g0;
-      gs[1] += g1;
-      gs[2] += g2;
-    }
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+      for (int c = 0; c < 3; ++c) gs[c] += a.bfold[3 * ((size_t)S.boff + i) + c];
     fold_tiles(p0 + 3 * nb, R, T, 9, tot);
-    // the bigs' extra position cotangent also enters sum_j lam_x4_j
     __shared__ double red[3][kThreads];
     for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = gs[c];
     __syncthreads();
@@ -686,6 +764,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_jump1(Dev d, Adj a) {
   }
 }
 
+void launch_fold_kick(const Dev& d, const Adj& a, int which, cudaStream_t st) {
+  if (3 * d.big_max + 9 > kThreads)
+    k_adj_fold_big<<<dim3(d.nsys, (3 * d.big_max + kThreads - 1) / kThreads), kThreads, 0, st>>>(d, a);
+  k_adj_fold_kick<<<d.nsys, kThreads, 0, st>>>(d, a, which);
+}
+
 void launch_adjoint_step_a(const Dev& d, const Adj& a, cudaStream_t st) {
   const int N = d.N;
   // forward recomputation
@@ -705,13 +789,13 @@ void launch_adjoint_step_b(const Dev& d, const Adj& a, cudaStream_t st) {
   k_adj_move_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a, 2);
   // reverse sweep: kick 2 (at x4, v3, P3), jump 2, drift, jump 1, kick 1 (at x0, v0, P0)
   k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, a.x4, a.xv3 + 3 * (size_t)N, 2, 2 * a.step + 1);
-  k_adj_fold_kick<<<d.nsys, kThreads, 0, st>>>(d, a, 2);
+  launch_fold_kick(d, a, 2, st);
   if (a.groups) launch_adjoint_bs_vjp(d, a, a.bs_blocks, st);
   k_adj_drift_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a);
   if (a.groups) launch_adjoint_bs_fold(d, a, st);
   k_adj_fold_jump1<<<d.nsys, kThreads, 0, st>>>(d, a);
   k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, a.z0, a.z0 + 3 * (size_t)N, 0, 2 * a.step);
-  k_adj_fold_kick<<<d.nsys, kThreads, 0, st>>>(d, a, 1);
+  launch_fold_kick(d, a, 1, st);
 }
 
 // ------------------------------------------------------ loss and set-up

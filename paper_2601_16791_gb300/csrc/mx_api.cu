@@ -226,8 +226,12 @@ struct mx_system {
   unsigned long long* a_goff = nullptr;
   double *a_gcontrib = nullptr, *a_tape = nullptr, *a_bsx = nullptr;
   unsigned long long a_tape_cap = 0;
-  unsigned long long* a_need = nullptr;   // device: doubles the step's groups reserve
+  unsigned long long* a_need = nullptr;   // device [2]: tape doubles, big bodies' shares
   unsigned long long* h_need = nullptr;   // pinned copy
+  unsigned long long* a_skeys = nullptr;  // sorted share keys (many big bodies)
+  int* a_scount = nullptr;
+  int a_skeys_cap = 0;
+  double* a_bfold = nullptr;              // 3 x NB
   // kept Stoermer sub-steps of two-body records (mx_adjoint_store)
   double* a_sub = nullptr;
   unsigned* a_subn = nullptr;
@@ -1756,6 +1760,24 @@ namespace {
 // sub-step takes 15 doubles).  The tape grows to what a step's groups reserve.
 constexpr size_t kAdjTape = (size_t)1 << 23;
 
+// Makes the share keys hold `n` (a power of two for the bitonic sort's
+// padding; the stream is idle).
+mx_status grow_share_keys(mx_system* s, unsigned long long n) {
+  if (n <= (unsigned long long)s->a_skeys_cap) return MX_OK;
+  unsigned long long cap = 1024;
+  while (cap < n) cap <<= 1;
+  if (cap > (1ull << 30)) return fail(MX_ERR_PAIR_OVERFLOW, "too many encounter shares");
+  if (s->a_skeys) {
+    MX_CUDA(cudaFree(s->a_skeys));
+    s->allocs.erase(std::remove(s->allocs.begin(), s->allocs.end(), (void*)s->a_skeys), s->allocs.end());
+    s->a_skeys = nullptr;
+    s->a_skeys_cap = 0;
+  }
+  MX_TRY(dalloc(s, &s->a_skeys, (size_t)cap));
+  s->a_skeys_cap = (int)cap;
+  return MX_OK;
+}
+
 // Makes the tape hold `need` doubles, with a quarter to spare (the stream is
 // idle: the caller has synchronised it).
 mx_status grow_tape(mx_system* s, unsigned long long need) {
@@ -1798,9 +1820,11 @@ mx_status ensure_adjoint(mx_system* s) {
     MX_TRY(dalloc(s, &s->a_goff, gcap));
     MX_TRY(dalloc(s, &s->a_gcontrib, (size_t)gcap * mx::kMaxGroup * 6));
     MX_TRY(dalloc(s, &s->a_tape, kAdjTape));
-    MX_TRY(dalloc(s, &s->a_need, 1));
-    if (cudaMallocHost(&s->h_need, sizeof(unsigned long long)) != cudaSuccess)
+    MX_TRY(dalloc(s, &s->a_need, 2));
+    if (cudaMallocHost(&s->h_need, 2 * sizeof(unsigned long long)) != cudaSuccess)
       return fail(MX_ERR_OOM, "cudaMallocHost");
+    MX_TRY(dalloc(s, &s->a_scount, 1));
+    MX_TRY(dalloc(s, &s->a_bfold, 3 * (size_t)s->NB));
     MX_TRY(dalloc(s, &s->a_subn, 1));
     MX_TRY(dalloc(s, &s->a_bsx, 3 * s->h_sys.size()));
     s->a_tape_cap = kAdjTape;
@@ -1991,6 +2015,11 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   a.tape = s->a_tape;
   a.tape_cap = s->a_tape_cap;
   a.tape_need = s->a_need;
+  a.sorted_shares = s->d.big_max > 64;
+  a.skeys = s->a_skeys;
+  a.scount = s->a_scount;
+  a.skeys_cap = s->a_skeys_cap;
+  a.bfold = s->a_bfold;
   a.bs_xsum = s->a_bsx;
   a.sub = s->a_sub;
   a.sub_count = s->a_subn;
@@ -1999,12 +2028,15 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   const mx::Dev d = adjoint_dev(s);
   mx::launch_adjoint_step_a(d, a, s->st);
   if (a.groups) {   // the groups' tape, sized from their plan
-    MX_CUDA(cudaMemcpyAsync(s->h_need, s->a_need, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                            s->st));
+    MX_CUDA(cudaMemcpyAsync(s->h_need, s->a_need, 2 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s->st));
     MX_TRY(sync_status(s));
-    MX_TRY(grow_tape(s, *s->h_need));
+    MX_TRY(grow_tape(s, s->h_need[0]));
+    if (a.sorted_shares) MX_TRY(grow_share_keys(s, s->h_need[1]));
     a.tape = s->a_tape;
     a.tape_cap = s->a_tape_cap;
+    a.skeys = s->a_skeys;
+    a.skeys_cap = s->a_skeys_cap;
   }
   mx::launch_adjoint_step_b(d, a, s->st);
   return sync_status(s);

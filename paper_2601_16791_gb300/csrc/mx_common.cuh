@@ -212,7 +212,15 @@ struct Adj {
   double* g_contrib;             // [g_cap][kMaxGroup][6] shares of members not written back
   double* tape;                  // accepted sub-steps: H, row, 6 x nb start state, slot
   unsigned long long tape_cap;   // doubles
-  unsigned long long* tape_need; // doubles the step's groups reserve (k_adj_tape)
+  unsigned long long* tape_need; // [2]: doubles the step's groups reserve, and the
+                                 // shares of big bodies not written back (k_adj_tape)
+  // many big bodies (sorted_shares): each big body's shares are added in the
+  // order of (body, item, member) keys sorted once, skeys_cap >= their count
+  int sorted_shares;
+  unsigned long long* skeys;
+  int* scount;
+  int skeys_cap;
+  double* bfold;                 // 3 per big body: its folded kick cotangent (many big bodies)
   double* bs_xsum;               // 3 per system: sum of the big shares' position parts
   // two-body groups: the Stoermer sub-steps of each accepted macro sub-step,
   // kAdjSubRec doubles a slot (null: none are kept, the reverse recomputes)
