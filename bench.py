@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and adjoint legs")
     ap.add_argument("--ensemble-steps", type=int, default=30)
+    ap.add_argument("--legs", default="batched,adjoint,ejection,growth,semiactive",
+                    help="comma-separated extra legs to run")
     ap.add_argument("--budget-s", type=float, default=120.0,
                     help="reference arm: host seconds the warm-up and timed steps may take")
     ap.add_argument("--workload", default=WORKLOAD,
@@ -451,10 +453,47 @@ def eject_leg(steps=200):
     return out
 
 
+def semiactive_adjoint(s, w, reps=3):
+    """One adjoint step against one forward step (mx_step(1): both half
+    kicks) from the same state of the semi-active disk: with the groups of
+    big bodies only (mode 2, the masked loss) and through every group."""
+    import torch
+    from paper_2601_16791_gb300 import mx
+    z = torch.empty((6, w.n), dtype=torch.float64, device="cuda")
+    mx.mx_get_state_device(s.h, z)
+    lam = torch.randn((6, w.n), dtype=torch.float64, device="cuda",
+                      generator=torch.Generator(device="cuda").manual_seed(5))
+    dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    mx.mx_set_state_device(s.h, z)
+    mx.mx_step(s.h, 1)
+    ev[0].record()
+    for _ in range(reps):
+        mx.mx_set_state_device(s.h, z)
+        mx.mx_step(s.h, 1)
+    ev[1].record()
+    for mode, (a, b) in ((2, (2, 3)), (1, (4, 5))):
+        mx._check(mx.load().mx_adjoint_encounters(s.h, mode), "mx_adjoint_encounters")
+        mx.mx_adjoint_step(s.h, z, 0, lam, dpar)
+        ev[a].record()
+        for _ in range(reps):
+            mx.mx_adjoint_step(s.h, z, 0, lam, dpar)
+        ev[b].record()
+    torch.cuda.synchronize()
+    f_ms = ev[0].elapsed_time(ev[1]) / reps
+    a_ms = ev[2].elapsed_time(ev[3]) / reps
+    g_ms = ev[4].elapsed_time(ev[5]) / reps
+    return {"forward_step_ms": f_ms, "adjoint_step_ms": a_ms,
+            "adjoint_over_forward_step": a_ms / f_ms,
+            "adjoint_step_ms_through_groups": g_ms,
+            "through_groups_over_forward_step": g_ms / f_ms}
+
+
 def semiactive_leg(steps=20):
     """The O(N_big N) regime: 2,000 embryos + 200,000 planetesimals (no gas),
-    where the kick is gravity of 2,000 sources on every body.  Step time and
-    the kick's algorithmic FP64 rate against the measured peak."""
+    where the kick is gravity of 2,000 sources on every body.  Step time, the
+    kick's algorithmic FP64 rate against the measured peak, and the cost of
+    an adjoint step."""
     import torch
     from paper_2601_16791_gb300 import mx, workloads as W
     st = torch.cuda.current_stream()
@@ -467,9 +506,11 @@ def semiactive_leg(steps=20):
     ms, cnt, tot = mx.mx_step_timed(s.h, steps, flush)
     ms0, cnt0, tot0 = mx.mx_step_timed(s.h, 0, flush)
     tile, order = mx.mx_tiling(s.h)
+    adj = semiactive_adjoint(s, w)
     s.close()
     out = {"n_bodies": w.n, "steps": steps, "ms_per_step": (tot + tot0) / steps,
            "value": w.n * steps / ((tot + tot0) * 1e-3)}
+    out.update(adj)
     # (detection's count is per pair; its FP32 screen skips most of them, so
     # it is not a rate against the FP64 peak)
     for k, key in (("k_jump_kick", "kick_frac_of_peak"),):
@@ -662,6 +703,8 @@ def run_mx(args):
         for key, fn in (("batched", lambda: ensemble_leg(args.ensemble_steps)),
                         ("adjoint", adjoint_leg), ("ejection", eject_leg),
                         ("growth", growth_leg), ("semiactive", semiactive_leg)):
+            if key not in args.legs.split(","):
+                continue
             try:
                 line[key] = fn()
             except Exception as exc:  # reported, not hidden
