@@ -419,35 +419,45 @@ __global__ void __launch_bounds__(kThreads) k_adj_move_fwd(Dev d, Adj a, int sta
   }
 }
 
-// The cotangent a pair gives the target's position, mu J l with J the
-// Jacobian of the pair's acceleration -mu K(s) d/s^3 and l the cotangent of
-// the acceleration: J l = -(K/s^3 l + (K' s - 3K)/s^5 d (d.l)) (the big body's
-// position gets the opposite).  1/s from the single-precision estimate, as in
-// the forward's pair weight; zero inside 0.1 rc, where K = 0.
+// One pair's part of a half kick's reverse.  With J the Jacobian of the
+// pair's acceleration -mu K(s) d/s^3 and l the cotangent of the acceleration,
+// mu J l = -(A l + B d), A = mu K/s^3, B = mu (K' s - 3K)/s^5 (d.l); the big
+// body's position gets A l + B d, added to (bx, by, bz), and the target's
+// gets -(A l + B d), kept as the sums sa += A and sb += B d (the target adds
+// -(sa l + sb) once).  nl = -3 l, so that outside the changeover shell (K = 1,
+// K' = 0) B = mu/s^5 (d.nl).  1/s from the single-precision estimate with one
+// correction, as in the forward's pair weight; nothing inside 0.1 rc (K = 0).
 __device__ __forceinline__ void pair_vjp(double dx, double dy, double dz, double mu,
                                          const PairRc& c, double lax, double lay, double laz,
-                                         double& jx, double& jy, double& jz) {
+                                         double nlx, double nly, double nlz, double& bx,
+                                         double& by, double& bz, double& sa, double& sbx,
+                                         double& sby, double& sbz) {
   const double s2 = fma(dx, dx, fma(dy, dy, dz * dz));
-  jx = jy = jz = 0.0;
   if (__double_as_longlong(s2) <= __double_as_longlong(c.lo)) return;
   const double y = float_to_double_bits(rsqrtf(abs_to_float_bits(s2)));
   const double e = fma(-s2 * y, y, 1.0);
   const double is = fma(y * e, fma(0.375, e, 0.5), y);   // 1/s
   const double is2 = is * is;
   const double mis3 = mu * (is2 * is);
-  double K = 1.0, t = -3.0;   // K and K' s - 3K
+  const double dl3 = fma(dx, nlx, fma(dy, nly, dz * nlz));   // -3 d.l
+  double A = mis3, T = dl3;   // T = (K' s - 3K) d.l
   if (__double_as_longlong(s2) < __double_as_longlong(c.rc2)) {
     const double sv = s2 * is;
     const double q = (sv - c.r01) * c.i09;
     const double omq = 1.0 - q;
-    K = q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
-    t = fma(30.0 * q * q * omq * omq * c.i09, sv, -3.0 * K);
+    const double K = q * q * q * fma(q, fma(6.0, q, -15.0), 10.0);
+    const double Kp = 30.0 * q * q * omq * omq * c.i09;   // dK/ds
+    A = mis3 * K;
+    T = dl3 * fma(Kp * sv, -1.0 / 3.0, K);
   }
-  const double dl = fma(dx, lax, fma(dy, lay, dz * laz));
-  const double A = mis3 * K, B = (mis3 * is2) * (t * dl);
-  jx = fma(A, lax, B * dx);
-  jy = fma(A, lay, B * dy);
-  jz = fma(A, laz, B * dz);
+  const double B = (mis3 * is2) * T;
+  bx = fma(A, lax, fma(B, dx, bx));
+  by = fma(A, lay, fma(B, dy, by));
+  bz = fma(A, laz, fma(B, dz, bz));
+  sa += A;
+  sbx = fma(B, dx, sbx);
+  sby = fma(B, dy, sby);
+  sbz = fma(B, dz, sbz);
 }
 
 // Reverse of a half kick at positions X (3 x N), velocities V (3 x N) and
@@ -488,7 +498,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
   const PairRc trc = target_rc(d, S, act ? jl : S.nbig);
   // cotangent of the kick's acceleration
   const double lax = th * lvx, lay = th * lvy, laz = th * lvz;
-  double gx = 0, gy = 0, gz = 0;   // into lam_x of this target
+  const double nlx = -3.0 * lax, nly = -3.0 * lay, nlz = -3.0 * laz;
+  double sa = 0, sbx = 0, sby = 0, sbz = 0;   // the target's sums (pair_vjp)
   for (int c0 = 0; c0 < S.nbig; c0 += kAdjChunk) {
     const int cn = min(kAdjChunk, S.nbig - c0);
     __syncthreads();
@@ -501,17 +512,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
       double bx = 0, by = 0, bz = 0;   // the running sum of the body this lane holds
       for (int r = 0; r < W; ++r) {
         const int k = base + ((gl + r) & (W - 1));
-        if (act && c0 + k != jl) {
-          double jx, jy, jz;
+        if (act && c0 + k != jl)
           pair_vjp(x - sx[k], y - sy[k], z - sz[k], sm[k], pair_rc(sc, k, trc), lax, lay, laz,
-                   jx, jy, jz);
-          gx -= jx;
-          gy -= jy;
-          gz -= jz;
-          bx += jx;
-          by += jy;
-          bz += jz;
-        }
+                   nlx, nly, nlz, bx, by, bz, sa, sbx, sby, sbz);
         if (r + 1 < W) {
           const int src = (gl + 1) & (W - 1);
           bx = __shfl_sync(0xffffffffu, bx, src, W);
@@ -545,6 +548,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
       rec[3 * (c0 + k) + 2] = s2;
     }
   }
+  // into lam_x of this target
+  double gx = -fma(sa, lax, sbx), gy = -fma(sa, lay, sby), gz = -fma(sa, laz, sbz);
   // drag
   double own[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // dP (3), sum lam_x (3), dparams (3)
   if (act) {

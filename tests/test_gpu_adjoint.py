@@ -326,3 +326,91 @@ def test_semiactive_full_size_adjoint_sampled(mask):
         ours = float((gx[:, cols] * dxv).sum())
         assert abs(Lo - float(L.detach())) <= 1e-9 * abs(Lo)
         assert abs(ours - jvp) <= 1e-6 * abs(jvp), (ours, jvp)
+
+
+def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode):
+    """Forward run of nsteps from the heliocentric state xv_h0 (every state
+    kept), the loss of weights w_host (bodies that met a big body left out
+    when mode is 0), and its reverse through the C ABI: (L per system, the
+    gradient w.r.t. xv_h0, d/d(params) per system, the encounter log)."""
+    mx.mx_set_state(h, xv_h0, mx.MX_COORD_HELIO, 0)
+    mx.mx_encounter_log(h, None, reset=True)
+    mx.mx_kick_branches(h, 1, 2 * nsteps + 2)
+    seg = []
+    for _ in range(nsteps):
+        z = torch.empty((6, n), dtype=torch.float64, device="cuda")
+        mx.mx_get_state_device(h, z)
+        seg.append(z)
+        mx.mx_step(h, 1)
+    ever = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    nbb = mx.mx_encounter_log(h, ever)
+    wt = torch.tensor(w_host, dtype=torch.float64, device="cuda")
+    if mode == 0:
+        wt = wt * (1.0 - ever.to(torch.float64))
+    xv0 = torch.tensor(xv_h0, dtype=torch.float64, device="cuda")
+    seed_f = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    seed_i = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    L = mx.mx_loss_semimajor(h, xv0, wt, seed_f, seed_i, nsys)
+    mx.mx_kick_branches(h, 2)
+    mx._check(mx.load().mx_adjoint_encounters(h, mode), "mx_adjoint_encounters")
+    lam = seed_f.clone()
+    dpar = torch.zeros(3 * nsys, dtype=torch.float64, device="cuda")
+    for k in reversed(range(nsteps)):
+        mx.mx_adjoint_step(h, seg[k], k, lam, dpar)
+    grad = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    mx.mx_adjoint_init(h, lam, grad)
+    grad += seed_i
+    return L, grad.cpu().numpy(), dpar.cpu().numpy(), nbb, ever.cpu().numpy()
+
+
+def test_batched_adjoint_matches_each_system_alone():
+    """Three gas disks of different sizes and gas (gamma = 1; gamma = 1.5 with
+    a larger C_D factor; gamma = 1 with an inner edge at 1.5 AU and the disk's
+    gravity) differentiated as
+    one batched mx_system, against each differentiated alone over the same 8
+    steps.  The adjoint's tiles, partial records and folds are per system, so
+    with the encounter groups skipped (the masked loss) the loss, the
+    gradient and the parameter cotangents are the same bits.  Through every
+    group the groups' shares are summed over the batch's one work list, in
+    another order than alone: relative 1e-12."""
+    ws = []
+    for seed, nb, ns, gam, cds, rin in ((11, 4, 3000, 1.0, 1.0, None), (12, 3, 2000, 1.5, 1.3, None),
+                                         (13, 5, 2500, 1.0, 0.8, 1.5)):
+        w = W.gas_4core_100k(seed=seed, nbig=nb, nsmall=ns, nsteps=8)
+        w.params["gas"].update(gamma=gam, cd_scale=cds)
+        if rin is not None:   # the disk's gravity, the gamma = 1 edge form
+            w.params["gas"].update(r_in_au=rin, disk_gravity=True)
+        ws.append(w)
+    nsteps = 8
+    rng = np.random.default_rng(29)
+    b = mx.Batch(ws)
+    off = b.offsets
+    xv_all = np.concatenate([w.xv_helio for w in ws], axis=1)
+    w_all = rng.uniform(0.5, 1.5, b.n) / b.n
+    for i, w in enumerate(ws):   # the loss over the planetesimals only
+        w_all[off[i]:off[i] + w.nbig] = 0.0
+    out = {}
+    for mode in (0, 1):
+        out[mode] = _raw_adjoint(b.h, b.n, len(ws), xv_all, w_all, nsteps, mode)
+    b.close()
+    met = 0
+    for i, w in enumerate(ws):
+        s = mx.System(w)
+        sl = slice(off[i], off[i + 1])
+        for mode in (0, 1):
+            L, g, dp, nbb, ever = _raw_adjoint(s.h, w.n, 1, w.xv_helio, w_all[sl], nsteps, mode)
+            Lb, gb, dpb, _, everb = out[mode]
+            assert nbb == 0, "big bodies met: mode 0 does not apply"
+            assert np.array_equal(ever, everb[sl])
+            met += int(ever.sum())
+            if mode == 0:
+                assert Lb[i] == L[0]
+                assert np.array_equal(gb[:, sl], g)
+                assert np.array_equal(dpb[3 * i:3 * i + 3], dp)
+            else:
+                assert abs(Lb[i] - L[0]) <= 1e-15 * abs(L[0])
+                assert np.abs(gb[:, sl] - g).max() <= 1e-12 * np.abs(g).max()
+                assert np.allclose(dpb[3 * i:3 * i + 3], dp, rtol=1e-12, atol=0)
+            assert np.abs(g).max() > 0 and np.abs(dp).max() > 0
+        s.close()
+    assert met > 0, "no planetesimal met a core: the groups' case is vacuous"
