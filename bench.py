@@ -405,12 +405,14 @@ def adjoint_leg(nsteps=200, every=50):
     f_ms = e[0].elapsed_time(e[1]) / reps
     a_ms = e[2].elapsed_time(e[3]) / reps
     g_ms = e4.elapsed_time(e5) / reps
+    m_ms = merged_adjoint_ms(traj.h, w.n, z, 0)
     traj.close()
     return {"steps": nsteps, "checkpoint_every": every,
             "backward_over_forward": t_bwd / t_fwd, "forward_step_ms": f_ms,
             "adjoint_step_ms": a_ms, "adjoint_over_forward_step": a_ms / f_ms,
             "adjoint_step_ms_through_groups": g_ms,
-            "through_groups_over_forward_step": g_ms / f_ms}
+            "through_groups_over_forward_step": g_ms / f_ms,
+            "merged_adjoint_step_ms": m_ms, "merged_over_forward_step": m_ms / f_ms}
 
 
 def eject_leg(steps=200):
@@ -453,10 +455,42 @@ def eject_leg(steps=200):
     return out
 
 
+def merged_adjoint_ms(h, n, z, mode, k=4):
+    """Per-step time of the reverse of k consecutive steps from state z with
+    mx_adjoint_merge on (each step's first half kick shares its pair pass with
+    the previous step's last), the final pending pass included."""
+    import torch
+    from paper_2601_16791_gb300 import mx
+    seg = []
+    mx.mx_set_state_device(h, z)
+    for _ in range(k):
+        zi = torch.empty_like(z)
+        mx.mx_get_state_device(h, zi)
+        seg.append(zi)
+        mx.mx_step(h, 1)
+    lam = torch.randn(z.shape, dtype=torch.float64, device="cuda",
+                      generator=torch.Generator(device="cuda").manual_seed(6))
+    dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mx._check(mx.load().mx_adjoint_encounters(h, mode), "mx_adjoint_encounters")
+    mx.mx_adjoint_merge(h, True)
+    for rep in range(2):   # the first pass warms up
+        if rep == 1:
+            e0.record()
+        for i in reversed(range(k)):
+            mx.mx_adjoint_step(h, seg[i], i, lam, dpar)
+        mx.mx_adjoint_flush(h)
+    e1.record()
+    torch.cuda.synchronize()
+    mx.mx_adjoint_merge(h, False)
+    return e0.elapsed_time(e1) / k
+
+
 def semiactive_adjoint(s, w, reps=3):
     """One adjoint step against one forward step (mx_step(1): both half
     kicks) from the same state of the semi-active disk: with the groups of
-    big bodies only (mode 2, the masked loss) and through every group."""
+    big bodies only (mode 2, the masked loss) and through every group; and the
+    per-step cost of consecutive steps reversed with mx_adjoint_merge (mode 2)."""
     import torch
     from paper_2601_16791_gb300 import mx
     z = torch.empty((6, w.n), dtype=torch.float64, device="cuda")
@@ -483,10 +517,12 @@ def semiactive_adjoint(s, w, reps=3):
     f_ms = ev[0].elapsed_time(ev[1]) / reps
     a_ms = ev[2].elapsed_time(ev[3]) / reps
     g_ms = ev[4].elapsed_time(ev[5]) / reps
+    m_ms = merged_adjoint_ms(s.h, w.n, z, 2, k=8)
     return {"forward_step_ms": f_ms, "adjoint_step_ms": a_ms,
             "adjoint_over_forward_step": a_ms / f_ms,
             "adjoint_step_ms_through_groups": g_ms,
-            "through_groups_over_forward_step": g_ms / f_ms}
+            "through_groups_over_forward_step": g_ms / f_ms,
+            "merged_adjoint_step_ms": m_ms, "merged_over_forward_step": m_ms / f_ms}
 
 
 def semiactive_leg(steps=20):

@@ -70,8 +70,8 @@ typedef struct {
   int disk_gravity;     /* 1: the disk's gravity on planetesimals (Eqs. 10-12): a radial
                            force per unit mass 2 pi G Sigma(R) S(gamma) (gamma != 1) or
                            2 pi G Sigma(R) r_in / R (gamma = 1), outward positive, along the
-                           cylindrical radius, where R >= r_in; not differentiated by the
-                           adjoint (MX_ERR_ARG there) */
+                           cylindrical radius, where R >= r_in; the adjoint differentiates
+                           it (position, sigma1, gamma) */
   int reserved;         /* 0 */
 } mx_gas;
 
@@ -468,8 +468,35 @@ mx_status mx_adjoint_encounters(mx_system* s, int on);
  * work) and the new one allocated at the next adjoint step. */
 mx_status mx_adjoint_store(mx_system* s, long long slots);
 
+/* Merged reverse of consecutive steps.  Both half kicks of the hybrid step
+ * (Sec. 2.1) sit between a step's last drift and the next step's first at the
+ * same positions, and the gravity part of a half kick's reverse is linear in
+ * its cotangent.  With on = 1, mx_adjoint_step of step k takes the drag part
+ * of its first half kick's reverse and leaves the pair pass pending: its
+ * cotangent and positions (2 x 3 x N doubles) are kept in the system, and the
+ * next call, for step k - 1 on the same dev_lambda, takes it in the pass of
+ * that step's last half kick.  That saves one pass over the (target, big body)
+ * pairs a step, most of an adjoint step with many big bodies.  Until then,
+ * the position rows of that dev_lambda lack the pending term.
+ * mx_adjoint_init, mx_adjoint_flush, mx_adjoint_merge(s, 0), or an
+ * mx_adjoint_step of any other step or cotangent adds it first.  The shared
+ * pass runs at the recomputed positions of step k - 1's last half kick, which
+ * are step k's starting positions for every body the mode integrates
+ * faithfully: every body in mode 1; in mode 2 all but the planetesimals that
+ * met a big body, and in mode 0 all but the members of encounter groups,
+ * whose cotangents the mode's loss must leave at zero anyway
+ * (mx_adjoint_encounters).  The results then agree with the unmerged reverse
+ * to rounding; the order of every sum stays fixed.  Default 0. */
+mx_status mx_adjoint_merge(mx_system* s, int on);
+
+/* Adds a merged reverse's pending pair pass (mx_adjoint_merge) to the
+ * cotangent it belongs to, so that buffer holds the cotangent at the start
+ * of the step it was last given to.  No-op without one.  Synchronises. */
+mx_status mx_adjoint_flush(mx_system* s);
+
 /* Reverse of the set-up transform: cotangent of the initial DH state ->
- * cotangent of the initial heliocentric state (6xN device buffers). */
+ * cotangent of the initial heliocentric state (6xN device buffers).  Adds a
+ * pending pair pass (mx_adjoint_merge) to its cotangent first. */
 mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_grad_helio);
 
 /* ------------------------------------------------------------------------

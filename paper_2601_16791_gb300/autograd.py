@@ -17,7 +17,9 @@ recorded Bulirsch-Stoer integration and its reverse.  Groups of big bodies
 (big-big encounters) are always differentiated: every body feels them.  The
 k switch of the drag coefficient is
 recorded in the forward run and replayed in the recomputation, so the
-reverse sweep sees the branches the forward run took.
+reverse sweep sees the branches the forward run took.  Consecutive steps are
+reversed with mx_adjoint_merge on: the pair pass of a step's first half kick
+joins that of the previous step's last half kick, at the same positions.
 
 Inputs: the initial heliocentric state (6 x N float64 CUDA tensor) and the
 gas parameters (sigma1 [g/cm^2], gamma, cd_scale) as a 3-vector.
@@ -101,6 +103,9 @@ class SemimajorLoss(torch.autograd.Function):
         h = traj.h
         mx.mx_kick_branches(h, 2)
         mx._check(mx.load().mx_adjoint_encounters(h, ctx.groups), "mx_adjoint_encounters")
+        # consecutive steps share the pair pass of their adjoining half kicks;
+        # mx_adjoint_init adds the last pending one
+        mx.mx_adjoint_merge(h, True)
         lam = (seed_f * g).contiguous()
         dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
         seg = torch.empty((ctx.every, 6, traj.n), dtype=torch.float64, device="cuda")
@@ -116,6 +121,7 @@ class SemimajorLoss(torch.autograd.Function):
                 mx.mx_adjoint_step(h, seg[k], start + k, lam, dpar)
         grad0 = torch.empty((6, traj.n), dtype=torch.float64, device="cuda")
         mx.mx_adjoint_init(h, lam, grad0)
+        mx.mx_adjoint_merge(h, False)
         grad0 += g * seed_i
         return grad0, dpar, None, None, None, None, None
 

@@ -460,6 +460,23 @@ __device__ __forceinline__ void pair_vjp(double dx, double dy, double dz, double
   sbz = fma(B, dz, sbz);
 }
 
+// Which parts of a half kick's reverse a launch takes.  The gravity's part is
+// linear in the cotangent l of the acceleration and depends on the positions
+// only, so the reverse of a step's first half kick and of the previous step's
+// last one (the same positions) can share one pass over the pairs: the first
+// launch takes the drag and leaves its l in lout, the second adds it (lin) to
+// its own before the pair pass.
+//   grav: the pass over the (target, big body) pairs;
+//   drag: the drag's reverse (and the disk's gravity);
+//   own: l = (h/2) lam_v of this kick (0: none, a pass with lin alone);
+//   lin: 3 x N, added to l for the pair pass (or null);
+//   lout: 3 x N, receives this kick's own l (or null).
+struct KickRev {
+  int grav, drag, own;
+  const double* lin;
+  double* lout;
+};
+
 // Reverse of a half kick at positions X (3 x N), velocities V (3 x N) and
 // momentum Pk, with the cotangent in a.lam: lam_x += (h/2) J^T lam_v,
 // lam_v += (h/2) (d a_drag/d v)^T lam_v.  Per-tile partials: the cotangent
@@ -474,7 +491,8 @@ __device__ __forceinline__ void pair_vjp(double dx, double dy, double dz, double
 // it, so each body's sum visits the group's targets in a fixed order with
 // one shuffle a pair, and the groups' sums are added at the end.
 __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const double* X,
-                                                           const double* V, int pslot, int kick) {
+                                                           const double* V, int pslot, int kick,
+                                                           KickRev r) {
   __shared__ double sx[kAdjChunk], sy[kAdjChunk], sz[kAdjChunk], sm[kAdjChunk];
   __shared__ double sc[4][kAdjChunk];
   __shared__ double wpart[kThreads / 32][kAdjChunk][3];
@@ -496,11 +514,24 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
     lvx = a.lam[3 * (size_t)N + j]; lvy = a.lam[4 * (size_t)N + j]; lvz = a.lam[5 * (size_t)N + j];
   }
   const PairRc trc = target_rc(d, S, act ? jl : S.nbig);
-  // cotangent of the kick's acceleration
-  const double lax = th * lvx, lay = th * lvy, laz = th * lvz;
-  const double nlx = -3.0 * lax, nly = -3.0 * lay, nlz = -3.0 * laz;
+  // the cotangent of this kick's acceleration (the drag's too), and the
+  // gravity's: that plus the one a merged reverse carries in (r.lin)
+  const double lax = r.own ? th * lvx : 0.0, lay = r.own ? th * lvy : 0.0,
+               laz = r.own ? th * lvz : 0.0;
+  double gax = lax, gay = lay, gaz = laz;
+  if (act && r.lin) {
+    gax += r.lin[j];
+    gay += r.lin[(size_t)N + j];
+    gaz += r.lin[2 * (size_t)N + j];
+  }
+  if (act && r.lout) {
+    r.lout[j] = lax;
+    r.lout[(size_t)N + j] = lay;
+    r.lout[2 * (size_t)N + j] = laz;
+  }
+  const double nlx = -3.0 * gax, nly = -3.0 * gay, nlz = -3.0 * gaz;
   double sa = 0, sbx = 0, sby = 0, sbz = 0;   // the target's sums (pair_vjp)
-  for (int c0 = 0; c0 < S.nbig; c0 += kAdjChunk) {
+  for (int c0 = 0; r.grav && c0 < S.nbig; c0 += kAdjChunk) {
     const int cn = min(kAdjChunk, S.nbig - c0);
     __syncthreads();
     stage_chunk(d, S, X, c0, cn, sx, sy, sz, sm, sc);
@@ -513,7 +544,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
       for (int r = 0; r < W; ++r) {
         const int k = base + ((gl + r) & (W - 1));
         if (act && c0 + k != jl)
-          pair_vjp(x - sx[k], y - sy[k], z - sz[k], sm[k], pair_rc(sc, k, trc), lax, lay, laz,
+          pair_vjp(x - sx[k], y - sy[k], z - sz[k], sm[k], pair_rc(sc, k, trc), gax, gay, gaz,
                    nlx, nly, nlz, bx, by, bz, sa, sbx, sby, sbz);
         if (r + 1 < W) {
           const int src = (gl + 1) & (W - 1);
@@ -549,12 +580,12 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick_vjp(Dev d, Adj a, const d
     }
   }
   // into lam_x of this target
-  double gx = -fma(sa, lax, sbx), gy = -fma(sa, lay, sby), gz = -fma(sa, laz, sbz);
+  double gx = -fma(sa, gax, sbx), gy = -fma(sa, gay, sby), gz = -fma(sa, gaz, sbz);
   // drag
   double own[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // dP (3), sum lam_x (3), dparams (3)
   if (act) {
     double lvxn = lvx, lvyn = lvy, lvzn = lvz;
-    if (S.gas_on && jl >= S.nbig) {
+    if (r.drag && S.gas_on && jl >= S.nbig) {
       const double u = V[j] + Pk[0] * S.inv_mu0, v = V[(size_t)N + j] + Pk[1] * S.inv_mu0,
                    w = V[2 * (size_t)N + j] + Pk[2] * S.inv_mu0;
       const double la[3] = {lax, lay, laz};
@@ -648,7 +679,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_big(Dev d, Adj a) {
 //  kick 2: lam_x(big) += G; lam_P3 = dP_drag + (h/2)/m0 (sum_j lam_x4_j);
 //          lam_v(big) += mu lam_P3.
 //  kick 1: lam_x(big) += G; lam_v(big) += mu dP_drag.
-__global__ void __launch_bounds__(kThreads) k_adj_fold_kick(Dev d, Adj a, int which) {
+__global__ void __launch_bounds__(kThreads) k_adj_fold_kick(Dev d, Adj a, int which, int grav) {
   const int sys = blockIdx.x;
   const SysDev& S = d.sys[sys];
   const int N = d.N;
@@ -660,13 +691,15 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_kick(Dev d, Adj a, int wh
   __shared__ double fold[kThreads];
   if (R <= kThreads) {
     fold_tiles(p0, R, T, R, fold);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    // (without the pair pass, the records' big-body values are not this
+    // launch's and are left out)
+    for (int i = threadIdx.x; grav && i < nb; i += blockDim.x) {
       const int g = S.off + i;
       for (int c = 0; c < 3; ++c) a.lam[(size_t)c * N + g] += fold[3 * i + c];
     }
     if (threadIdx.x < 3) {   // the bigs' extra position cotangent, summed in big order
       double sum = 0.0;
-      for (int i = 0; i < nb; ++i) sum += fold[3 * i + threadIdx.x];
+      for (int i = 0; grav && i < nb; ++i) sum += fold[3 * i + threadIdx.x];
       gsum_sh[threadIdx.x] = sum;
     }
     if (threadIdx.x < 9) tot[threadIdx.x] = fold[3 * nb + threadIdx.x];
@@ -674,7 +707,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_kick(Dev d, Adj a, int wh
     // many big bodies: k_adj_fold_big has added their cotangents and left
     // them in a.bfold; their sum in big order for sum_j lam_x4_j
     double gs[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+    for (int i = threadIdx.x; grav && i < nb; i += blockDim.x)
       for (int c = 0; c < 3; ++c) gs[c] += a.bfold[3 * ((size_t)S.boff + i) + c];
     fold_tiles(p0 + 3 * nb, R, T, 9, tot);
     __shared__ double red[3][kThreads];
@@ -698,7 +731,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_kick(Dev d, Adj a, int wh
     const double m = d.bmu[S.boff + i];
     for (int c = 0; c < 3; ++c) a.lam[(size_t)(3 + c) * N + g] += m * lP[c];
   }
-  if (threadIdx.x < 3) a.dpar[3 * sys + threadIdx.x] += tot[6 + threadIdx.x];
+  if (a.dpar && threadIdx.x < 3) a.dpar[3 * sys + threadIdx.x] += tot[6 + threadIdx.x];
 }
 
 // Reverse of the drift: (lam_x2, lam_v1) = J^T (lam_x3, lam_v3) per body,
@@ -769,10 +802,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_jump1(Dev d, Adj a) {
   }
 }
 
-void launch_fold_kick(const Dev& d, const Adj& a, int which, cudaStream_t st) {
-  if (3 * d.big_max + 9 > kThreads)
+void launch_fold_kick(const Dev& d, const Adj& a, int which, int grav, cudaStream_t st) {
+  if (grav && 3 * d.big_max + 9 > kThreads)
     k_adj_fold_big<<<dim3(d.nsys, (3 * d.big_max + kThreads - 1) / kThreads), kThreads, 0, st>>>(d, a);
-  k_adj_fold_kick<<<d.nsys, kThreads, 0, st>>>(d, a, which);
+  k_adj_fold_kick<<<d.nsys, kThreads, 0, st>>>(d, a, which, grav);
 }
 
 void launch_adjoint_step_a(const Dev& d, const Adj& a, cudaStream_t st) {
@@ -793,14 +826,25 @@ void launch_adjoint_step_b(const Dev& d, const Adj& a, cudaStream_t st) {
                                                a.xv3 + 5 * (size_t)N, a.P, 2);
   k_adj_move_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a, 2);
   // reverse sweep: kick 2 (at x4, v3, P3), jump 2, drift, jump 1, kick 1 (at x0, v0, P0)
-  k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, a.x4, a.xv3 + 3 * (size_t)N, 2, 2 * a.step + 1);
-  launch_fold_kick(d, a, 2, st);
+  // (with a.lin, the pair pass also takes the next step's first half kick,
+  // left pending at the same positions)
+  k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, a.x4, a.xv3 + 3 * (size_t)N, 2, 2 * a.step + 1,
+                                              KickRev{1, 1, 1, a.lin, nullptr});
+  launch_fold_kick(d, a, 2, 1, st);
   if (a.groups) launch_adjoint_bs_vjp(d, a, a.bs_blocks, st);
   k_adj_drift_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a);
   if (a.groups) launch_adjoint_bs_fold(d, a, st);
   k_adj_fold_jump1<<<d.nsys, kThreads, 0, st>>>(d, a);
-  k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, a.z0, a.z0 + 3 * (size_t)N, 0, 2 * a.step);
-  launch_fold_kick(d, a, 1, st);
+  // merged: the drag now, the pair pass with the previous step's last half kick
+  const KickRev r1{a.defer_k1 ? 0 : 1, 1, 1, nullptr, a.defer_k1 ? a.lpend : nullptr};
+  k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, a.z0, a.z0 + 3 * (size_t)N, 0, 2 * a.step, r1);
+  launch_fold_kick(d, a, 1, r1.grav, st);
+}
+
+void launch_adjoint_flush(const Dev& d, const Adj& a, const double* xpos, cudaStream_t st) {
+  k_adj_kick_vjp<<<d.ntiles, d.tile, 0, st>>>(d, a, xpos, xpos, 0, 0,
+                                              KickRev{1, 0, 0, a.lpend, nullptr});
+  launch_fold_kick(d, a, 1, 1, st);
 }
 
 // ------------------------------------------------------ loss and set-up

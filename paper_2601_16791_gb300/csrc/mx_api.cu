@@ -232,6 +232,13 @@ struct mx_system {
   int* a_scount = nullptr;
   int a_skeys_cap = 0;
   double* a_bfold = nullptr;              // 3 x NB
+  // merged reverse of consecutive half kicks (mx_adjoint_merge): the pair
+  // pass of the last adjoint step's first half kick, pending with its
+  // cotangent (a_lpend) and positions (a_xpend), both 3 x N
+  int a_merge = 0, a_pend = 0;
+  long long a_pend_step = -1;
+  double* a_pend_lam = nullptr;
+  double *a_lpend = nullptr, *a_xpend = nullptr;
   // kept Stoermer sub-steps of two-body records (mx_adjoint_store)
   double* a_sub = nullptr;
   unsigned* a_subn = nullptr;
@@ -1825,6 +1832,8 @@ mx_status ensure_adjoint(mx_system* s) {
       return fail(MX_ERR_OOM, "cudaMallocHost");
     MX_TRY(dalloc(s, &s->a_scount, 1));
     MX_TRY(dalloc(s, &s->a_bfold, 3 * (size_t)s->NB));
+    MX_TRY(dalloc(s, &s->a_lpend, (size_t)6 * N));
+    s->a_xpend = s->a_lpend + 3 * (size_t)N;
     MX_TRY(dalloc(s, &s->a_subn, 1));
     MX_TRY(dalloc(s, &s->a_bsx, 3 * s->h_sys.size()));
     s->a_tape_cap = kAdjTape;
@@ -1856,6 +1865,54 @@ mx_status ensure_adjoint(mx_system* s) {
                             cudaMemcpyHostToDevice, s->st));
     MX_CUDA(cudaStreamSynchronize(s->st));
   }
+  return MX_OK;
+}
+
+// The adjoint's view of the system's buffers for one call on dev_lambda and
+// dev_dparams (the per-step fields are the caller's).
+mx::Adj make_adj(const mx_system* s, double* dev_lambda, double* dev_dparams) {
+  mx::Adj a{};
+  a.v1 = s->a_v1;
+  a.x2 = s->a_x2;
+  a.xv3 = s->a_xv3;
+  a.x4 = s->a_x4;
+  a.lam = dev_lambda;
+  a.part = s->a_part;
+  a.poff = s->a_poff;
+  a.sys_tiles = s->a_systiles;
+  a.P = s->a_P;
+  a.dpar = dev_dparams;
+  a.groups = s->a_groups;
+  a.g_cap = s->a_gcap;
+  a.bs_blocks = s->bs_blocks;
+  a.g_M = s->a_gM;
+  a.g_off = s->a_goff;
+  a.g_contrib = s->a_gcontrib;
+  a.tape = s->a_tape;
+  a.tape_cap = s->a_tape_cap;
+  a.tape_need = s->a_need;
+  a.sorted_shares = s->d.big_max > 64;
+  a.skeys = s->a_skeys;
+  a.scount = s->a_scount;
+  a.skeys_cap = s->a_skeys_cap;
+  a.bfold = s->a_bfold;
+  a.bs_xsum = s->a_bsx;
+  a.sub = s->a_sub;
+  a.sub_count = s->a_subn;
+  a.sub_cap = s->a_sub_cap;
+  a.lin = nullptr;
+  a.lpend = s->a_lpend;
+  a.defer_k1 = 0;
+  return a;
+}
+
+// The pending pair pass of a merged reverse, on its own, into the cotangent
+// it belongs to (enqueued; the caller reads the status).
+mx_status flush_adjoint(mx_system* s) {
+  if (!s->a_pend) return MX_OK;
+  mx::Adj a = make_adj(s, s->a_pend_lam, nullptr);
+  mx::launch_adjoint_flush(adjoint_dev(s), a, s->a_xpend, s->st);
+  s->a_pend = 0;
   return MX_OK;
 }
 
@@ -1978,6 +2035,7 @@ mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_gr
   if (!s || !dev_lambda || !dev_grad_helio) return fail(MX_ERR_ARG, "invalid arguments");
   MX_TRY(set_device(s));
   MX_TRY(settle(s));
+  MX_TRY(flush_adjoint(s));   // a merged reverse's pending pair pass first
   mx::launch_init_vjp(s->d, dev_lambda, dev_grad_helio, s->st);
   return sync_status(s);
 }
@@ -1992,39 +2050,16 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   MX_TRY(set_device(s));
   MX_TRY(settle(s));
   MX_TRY(ensure_adjoint(s));
-  const size_t N = s->N;
-  mx::Adj a;
+  // a pending pair pass joins this step's last half kick only when this is
+  // the step before it, on the same cotangent; otherwise it runs on its own
+  const bool merge_in = s->a_pend && s->a_merge && s->a_pend_step == step_k + 1 &&
+                        s->a_pend_lam == dev_lambda;
+  if (s->a_pend && !merge_in) MX_TRY(flush_adjoint(s));
+  mx::Adj a = make_adj(s, dev_lambda, dev_dparams);
   a.z0 = dev_state_k;
-  a.v1 = s->a_v1;
-  a.x2 = s->a_x2;
-  a.xv3 = s->a_xv3;
-  a.x4 = s->a_x4;
-  a.lam = dev_lambda;
-  a.part = s->a_part;
-  a.poff = s->a_poff;
-  a.sys_tiles = s->a_systiles;
-  a.P = s->a_P;
-  a.dpar = dev_dparams;
   a.step = (int)step_k;
-  a.groups = s->a_groups;
-  a.g_cap = s->a_gcap;
-  a.bs_blocks = s->bs_blocks;
-  a.g_M = s->a_gM;
-  a.g_off = s->a_goff;
-  a.g_contrib = s->a_gcontrib;
-  a.tape = s->a_tape;
-  a.tape_cap = s->a_tape_cap;
-  a.tape_need = s->a_need;
-  a.sorted_shares = s->d.big_max > 64;
-  a.skeys = s->a_skeys;
-  a.scount = s->a_scount;
-  a.skeys_cap = s->a_skeys_cap;
-  a.bfold = s->a_bfold;
-  a.bs_xsum = s->a_bsx;
-  a.sub = s->a_sub;
-  a.sub_count = s->a_subn;
-  a.sub_cap = s->a_sub_cap;
-  (void)N;
+  a.lin = merge_in ? s->a_lpend : nullptr;
+  a.defer_k1 = s->a_merge;
   const mx::Dev d = adjoint_dev(s);
   mx::launch_adjoint_step_a(d, a, s->st);
   if (a.groups) {   // the groups' tape, sized from their plan
@@ -2039,6 +2074,35 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
     a.skeys_cap = s->a_skeys_cap;
   }
   mx::launch_adjoint_step_b(d, a, s->st);
+  s->a_pend = 0;
+  if (s->a_merge) {   // this step's first half kick waits for its pair pass
+    MX_CUDA(cudaMemcpyAsync(s->a_xpend, dev_state_k, 3 * (size_t)s->N * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s->st));
+    s->a_pend = 1;
+    s->a_pend_step = step_k;
+    s->a_pend_lam = dev_lambda;
+  }
+  const mx_status r = sync_status(s);
+  if (r != MX_OK) s->a_pend = 0;
+  return r;
+}
+
+mx_status mx_adjoint_merge(mx_system* s, int on) {
+  if (!s || on < 0 || on > 1) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  if (!on && s->a_pend) {
+    MX_TRY(flush_adjoint(s));
+    MX_TRY(sync_status(s));
+  }
+  s->a_merge = on;
+  return MX_OK;
+}
+
+mx_status mx_adjoint_flush(mx_system* s) {
+  if (!s) return fail(MX_ERR_ARG, "invalid arguments");
+  MX_TRY(set_device(s));
+  if (!s->a_pend) return MX_OK;
+  MX_TRY(flush_adjoint(s));
   return sync_status(s);
 }
 

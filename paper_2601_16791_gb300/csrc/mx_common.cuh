@@ -221,6 +221,13 @@ struct Adj {
   int* scount;
   int skeys_cap;
   double* bfold;                 // 3 per big body: its folded kick cotangent (many big bodies)
+  // merged reverse of consecutive half kicks (k_adjoint.cu, KickRev): lin
+  // (or null) is the pending cotangent of the next step's first half kick,
+  // taken in this step's last-kick pair pass; with defer_k1 this step's first
+  // half kick leaves its own in lpend (3 x N) instead of a pair pass
+  const double* lin;
+  double* lpend;
+  int defer_k1;
   double* bs_xsum;               // 3 per system: sum of the big shares' position parts
   // two-body groups: the Stoermer sub-steps of each accepted macro sub-step,
   // kAdjSubRec doubles a slot (null: none are kept, the reverse recomputes)

@@ -73,6 +73,9 @@ void launch_radius(const Dev& d, cudaStream_t st);
 // when a.groups; then the groups' integration and the reverse sweep.
 void launch_adjoint_step_a(const Dev& d, const Adj& a, cudaStream_t st);
 void launch_adjoint_step_b(const Dev& d, const Adj& a, cudaStream_t st);
+// The pending pair pass of a merged reverse on its own (a.lpend at the
+// positions xpos, 3 x N), into a.lam.
+void launch_adjoint_flush(const Dev& d, const Adj& a, const double* xpos, cudaStream_t st);
 // k_adj_bs.cu: the step's encounter groups inside the adjoint (forward with a
 // tape, reverse, per-system fold of the big bodies' shares)
 void launch_adjoint_bs_plan(const Dev& d, const Adj& a, cudaStream_t st);

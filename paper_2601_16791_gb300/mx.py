@@ -101,6 +101,8 @@ _SIGS = {
     "mx_set_growth": (_I, [_P, _I, _P, _D]),
     "mx_adjoint_encounters": (_I, [_P, _I]),
     "mx_adjoint_store": (_I, [_P, ctypes.c_longlong]),
+    "mx_adjoint_merge": (_I, [_P, _I]),
+    "mx_adjoint_flush": (_I, [_P]),
     "mx_planets": (_I, [_P, _P, _P]),
 }
 
@@ -520,6 +522,14 @@ def mx_loss_semimajor(sys, dev_xv_helio0, dev_w, dev_seed_final, dev_seed_init, 
 def mx_adjoint_step(sys, dev_state_k, step_k, dev_lambda, dev_dparams):
     _check(load().mx_adjoint_step(sys, _dptr(dev_state_k), int(step_k), _dptr(dev_lambda),
                                   _dptr(dev_dparams)), "mx_adjoint_step")
+
+
+def mx_adjoint_merge(sys, on):
+    _check(load().mx_adjoint_merge(sys, int(bool(on))), "mx_adjoint_merge")
+
+
+def mx_adjoint_flush(sys):
+    _check(load().mx_adjoint_flush(sys), "mx_adjoint_flush")
 
 
 def mx_adjoint_init(sys, dev_lambda, dev_grad_helio):

@@ -328,11 +328,15 @@ def test_semiactive_full_size_adjoint_sampled(mask):
         assert abs(ours - jvp) <= 1e-6 * abs(jvp), (ours, jvp)
 
 
-def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode):
+def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode, merge=False, flush_at=None):
     """Forward run of nsteps from the heliocentric state xv_h0 (every state
     kept), the loss of weights w_host (bodies that met a big body left out
-    when mode is 0), and its reverse through the C ABI: (L per system, the
-    gradient w.r.t. xv_h0, d/d(params) per system, the encounter log)."""
+    in modes 0 and 2, whose reverse assumes it), and its reverse through the
+    C ABI: (L per system, the
+    gradient w.r.t. xv_h0, d/d(params) per system, the encounter log).  With
+    merge, consecutive steps are reversed with mx_adjoint_merge on; with
+    flush_at = k, the cotangent after step k's reverse is also returned (read
+    after mx_adjoint_flush)."""
     mx.mx_set_state(h, xv_h0, mx.MX_COORD_HELIO, 0)
     mx.mx_encounter_log(h, None, reset=True)
     mx.mx_kick_branches(h, 1, 2 * nsteps + 2)
@@ -345,7 +349,7 @@ def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode):
     ever = torch.zeros(n, dtype=torch.uint8, device="cuda")
     nbb = mx.mx_encounter_log(h, ever)
     wt = torch.tensor(w_host, dtype=torch.float64, device="cuda")
-    if mode == 0:
+    if mode in (0, 2):
         wt = wt * (1.0 - ever.to(torch.float64))
     xv0 = torch.tensor(xv_h0, dtype=torch.float64, device="cuda")
     seed_f = torch.empty((6, n), dtype=torch.float64, device="cuda")
@@ -355,12 +359,19 @@ def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode):
     mx._check(mx.load().mx_adjoint_encounters(h, mode), "mx_adjoint_encounters")
     lam = seed_f.clone()
     dpar = torch.zeros(3 * nsys, dtype=torch.float64, device="cuda")
+    mx.mx_adjoint_merge(h, merge)
+    mid = None
     for k in reversed(range(nsteps)):
         mx.mx_adjoint_step(h, seg[k], k, lam, dpar)
+        if k == flush_at:
+            mx.mx_adjoint_flush(h)
+            mid = lam.cpu().numpy()
     grad = torch.empty((6, n), dtype=torch.float64, device="cuda")
     mx.mx_adjoint_init(h, lam, grad)
+    mx.mx_adjoint_merge(h, False)
     grad += seed_i
-    return L, grad.cpu().numpy(), dpar.cpu().numpy(), nbb, ever.cpu().numpy()
+    out = (L, grad.cpu().numpy(), dpar.cpu().numpy(), nbb, ever.cpu().numpy())
+    return out if flush_at is None else out + (mid,)
 
 
 def test_batched_adjoint_matches_each_system_alone():
@@ -414,3 +425,41 @@ def test_batched_adjoint_matches_each_system_alone():
             assert np.abs(g).max() > 0 and np.abs(dp).max() > 0
         s.close()
     assert met > 0, "no planetesimal met a core: the groups' case is vacuous"
+
+
+@pytest.mark.parametrize("disk", ["gas", "semiactive"])
+def test_merged_reverse_matches_unmerged(disk):
+    """mx_adjoint_merge: the pair pass of each step's first half kick taken
+    with the previous step's last one (same positions, summed cotangents)
+    against separate passes, with the groups skipped or every group
+    differentiated.  The gas disk (4 cores + 3,000 planetesimals, 12 steps)
+    and 1,000 embryos + 2,000 planetesimals (20 steps), whose embryos meet
+    (mode 2 instead of 0).
+    The sums are the same terms grouped otherwise: relative 1e-12.  A flush
+    after step 6's reverse (mx_adjoint_flush) gives the unmerged cotangent
+    there, and the run goes on merged to the same gradient."""
+    if disk == "gas":
+        nsteps = 12
+        w = W.adjoint_4core_50k(seed=4, nsmall=3000, nsteps=nsteps)
+        modes = (0, 1)
+    else:
+        nsteps = 20
+        w = W.semiactive_2000big_200k(nbig=1000, nsmall=2000, nsteps=nsteps)
+        modes = (2, 1)
+    s = mx.System(w)
+    wts = np.zeros(w.n)
+    wts[w.nbig:] = 1.0 / w.nsmall
+    for mode in modes:
+        L0, g0, d0, nbb, _, mid0 = _raw_adjoint(s.h, w.n, 1, w.xv_helio, wts, nsteps, mode,
+                                                flush_at=6)
+        L1, g1, d1, _, _, mid1 = _raw_adjoint(s.h, w.n, 1, w.xv_helio, wts, nsteps, mode,
+                                              merge=True, flush_at=6)
+        assert (nbb == 0) == (disk == "gas")
+        assert L0[0] == L1[0]
+        assert np.abs(g1 - g0).max() <= 1e-12 * np.abs(g0).max()
+        assert np.allclose(d1, d0, rtol=1e-12, atol=0)
+        for r in range(6):
+            assert np.abs(mid1[r] - mid0[r]).max() <= 1e-12 * np.abs(mid0[r]).max()
+        assert np.abs(g0).max() > 0
+        assert (np.abs(d0).max() > 0) == (disk == "gas")   # no gas on the embryos' disk
+    s.close()
