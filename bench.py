@@ -456,18 +456,22 @@ def eject_leg(steps=200):
 
 
 def merged_adjoint_ms(h, n, z, mode, k=4):
-    """Per-step time of the reverse of k consecutive steps from state z with
-    mx_adjoint_merge on (each step's first half kick shares its pair pass with
-    the previous step's last), the final pending pass included."""
+    """Per-step time of the reverse of k consecutive steps from state z as
+    the autograd backward runs it: mx_adjoint_merge on (each step's first half
+    kick shares its pair pass with the previous step's last) and each step's
+    pre-drift state from the forward (mx_adjoint_step_predrift), the final
+    pending pass included."""
     import torch
     from paper_2601_16791_gb300 import mx
-    seg = []
+    seg, pre = [], []
     mx.mx_set_state_device(h, z)
     for _ in range(k):
         zi = torch.empty_like(z)
         mx.mx_get_state_device(h, zi)
         seg.append(zi)
         mx.mx_step(h, 1)
+        pre.append(torch.empty_like(z))
+        mx.mx_predrift_state(h, pre[-1])
     lam = torch.randn(z.shape, dtype=torch.float64, device="cuda",
                       generator=torch.Generator(device="cuda").manual_seed(6))
     dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
@@ -478,7 +482,7 @@ def merged_adjoint_ms(h, n, z, mode, k=4):
         if rep == 1:
             e0.record()
         for i in reversed(range(k)):
-            mx.mx_adjoint_step(h, seg[i], i, lam, dpar)
+            mx.mx_adjoint_step_predrift(h, seg[i], pre[i], i, lam, dpar)
         mx.mx_adjoint_flush(h)
     e1.record()
     torch.cuda.synchronize()

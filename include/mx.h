@@ -445,6 +445,26 @@ mx_status mx_loss_semimajor(mx_system* s, const double* dev_xv_helio0, const dou
 mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long step_k,
                           double* dev_lambda, double* dev_dparams);
 
+/* The pre-drift state of the last step mx_step took (Sec. 2.1: the state the
+ * Kepler drift starts from): heliocentric positions after the first jump and
+ * barycentric velocities after the first half kick, 6xN into dev_xv (device).
+ * MX_ERR_ARG when the last step-taking call was not mx_step, or deferral was
+ * on in it for a system that can defer (a deferred planetesimal is drifted by
+ * the catch-up instead; recording or replaying drag branches turns deferral
+ * off, and systems with more than 64 big bodies never defer, see
+ * mx_set_defer_window). */
+mx_status mx_predrift_state(mx_system* s, double* dev_xv);
+
+/* mx_adjoint_step with the step's pre-drift state from the forward run
+ * (mx_predrift_state after the mx_step(1) that started from dev_state_k),
+ * read only, instead of recomputing the first half kick and jump: one pass
+ * over the (target, big body) pairs less.  The same derivative; it follows
+ * the forward's values where the recomputation would differ from them by
+ * rounding. */
+mx_status mx_adjoint_step_predrift(mx_system* s, const double* dev_state_k,
+                                   const double* dev_predrift_k, long long step_k,
+                                   double* dev_lambda, double* dev_dparams);
+
 /* Which of the step's encounter groups mx_adjoint_step integrates and
  * differentiates.  The groups are the step's own (rebuilt from the
  * recomputed endpoints): groups of big bodies joined by big-big encounters,

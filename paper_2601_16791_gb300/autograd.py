@@ -19,7 +19,9 @@ k switch of the drag coefficient is
 recorded in the forward run and replayed in the recomputation, so the
 reverse sweep sees the branches the forward run took.  Consecutive steps are
 reversed with mx_adjoint_merge on: the pair pass of a step's first half kick
-joins that of the previous step's last half kick, at the same positions.
+joins that of the previous step's last half kick, at the same positions.  The
+recomputation keeps each step's pre-drift state (mx_predrift_state), so the
+adjoint does not recompute the first half kick (mx_adjoint_step_predrift).
 
 Inputs: the initial heliocentric state (6 x N float64 CUDA tensor) and the
 gas parameters (sigma1 [g/cm^2], gamma, cd_scale) as a 3-vector.
@@ -109,16 +111,19 @@ class SemimajorLoss(torch.autograd.Function):
         lam = (seed_f * g).contiguous()
         dpar = torch.zeros(3, dtype=torch.float64, device="cuda")
         seg = torch.empty((ctx.every, 6, traj.n), dtype=torch.float64, device="cuda")
+        pre = torch.empty((ctx.every, 6, traj.n), dtype=torch.float64, device="cuda")
         for start, ck in reversed(ctx.ckpts):
             length = min(ctx.every, ctx.nsteps - start)
             mx.mx_set_state_device(h, ck)
             mx.mx_set_step_index(h, start)
+            # each step's start and pre-drift state (the branch replay keeps
+            # deferral off, so the step leaves every body's)
             for k in range(length):
                 mx.mx_get_state_device(h, seg[k])
-                if k + 1 < length:
-                    mx.mx_step(h, 1)
+                mx.mx_step(h, 1)
+                mx.mx_predrift_state(h, pre[k])
             for k in reversed(range(length)):
-                mx.mx_adjoint_step(h, seg[k], start + k, lam, dpar)
+                mx.mx_adjoint_step_predrift(h, seg[k], pre[k], start + k, lam, dpar)
         grad0 = torch.empty((6, traj.n), dtype=torch.float64, device="cuda")
         mx.mx_adjoint_init(h, lam, grad0)
         mx.mx_adjoint_merge(h, False)

@@ -395,7 +395,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_kick1_fwd(Dev d, Adj a) {
 }
 
 // Jump 1 and drift forward: x2 = x0 + (h/2) P1/m0, (x3, v3) = drift(x2, v1);
-// or, with stage 2, jump 2: x4 = x3 + (h/2) P3/m0.
+// with stage 3 the drift alone, from the (x2, v1) the forward step left
+// (a.pd, read only); with stage 2, jump 2: x4 = x3 + (h/2) P3/m0.
 __global__ void __launch_bounds__(kThreads) k_adj_move_fwd(Dev d, Adj a, int stage) {
   const Tile t = d.tiles[blockIdx.x];
   if (threadIdx.x >= t.count) return;
@@ -403,12 +404,17 @@ __global__ void __launch_bounds__(kThreads) k_adj_move_fwd(Dev d, Adj a, int sta
   const int N = d.N;
   const int j = t.start + threadIdx.x;
   const double c = 0.5 * S.h * S.inv_mu0;
-  if (stage == 1) {
-    const double* P1 = a.P + 9 * t.sys + 3;
-    double x = a.z0[j] + c * P1[0];
-    double y = a.z0[(size_t)N + j] + c * P1[1];
-    double z = a.z0[2 * (size_t)N + j] + c * P1[2];
-    a.x2[j] = x; a.x2[(size_t)N + j] = y; a.x2[2 * (size_t)N + j] = z;
+  if (stage != 2) {
+    double x, y, z;
+    if (stage == 1) {
+      const double* P1 = a.P + 9 * t.sys + 3;
+      x = a.z0[j] + c * P1[0];
+      y = a.z0[(size_t)N + j] + c * P1[1];
+      z = a.z0[2 * (size_t)N + j] + c * P1[2];
+      a.x2[j] = x; a.x2[(size_t)N + j] = y; a.x2[2 * (size_t)N + j] = z;
+    } else {   // stage 3: the forward's own pre-drift state (a.pd)
+      x = a.x2[j]; y = a.x2[(size_t)N + j]; z = a.x2[2 * (size_t)N + j];
+    }
     double u = a.v1[j], v = a.v1[(size_t)N + j], w = a.v1[2 * (size_t)N + j];
     if (!kepler_drift(S.mu0, S.h, d.kepler_max_iter, x, y, z, u, v, w)) atomicOr(d.status, ST_KEPLER);
     a.xv3[j] = x; a.xv3[(size_t)N + j] = y; a.xv3[2 * (size_t)N + j] = z;
@@ -813,9 +819,10 @@ void launch_adjoint_step_a(const Dev& d, const Adj& a, cudaStream_t st) {
   // forward recomputation
   k_adj_momentum<<<d.nsys, kThreads, 0, st>>>(d, a.z0 + 3 * (size_t)N, a.z0 + 4 * (size_t)N,
                                                a.z0 + 5 * (size_t)N, a.P, 0);
-  k_adj_kick1_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a);
+  // (with a.pd, x2 and v1 are the forward's, and only the drift is redone)
+  if (!a.pd) k_adj_kick1_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a);
   k_adj_momentum<<<d.nsys, kThreads, 0, st>>>(d, a.v1, a.v1 + N, a.v1 + 2 * (size_t)N, a.P, 1);
-  k_adj_move_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a, 1);
+  k_adj_move_fwd<<<d.ntiles, d.tile, 0, st>>>(d, a, a.pd ? 3 : 1);
   if (a.groups) launch_adjoint_bs_plan(d, a, st);
 }
 

@@ -236,6 +236,7 @@ struct mx_system {
   // pass of the last adjoint step's first half kick, pending with its
   // cotangent (a_lpend) and positions (a_xpend), both 3 x N
   int a_merge = 0, a_pend = 0;
+  int pd_ok = 0;   // d.xv0 holds the pre-drift state of every body for the last mx_step
   long long a_pend_step = -1;
   double* a_pend_lam = nullptr;
   double *a_lpend = nullptr, *a_xpend = nullptr;
@@ -1167,6 +1168,12 @@ mx_status mx_step(mx_system* s, int n_steps) {
     }
   }
   s->step += n_steps;
+  // a deferred body's drift is the catch-up's; only planetesimals of systems
+  // with at most kDeferMaxBig big bodies are ever deferred
+  bool deferrable = false;
+  if (s->d.defer)
+    for (const auto& sy : s->h_sys) deferrable |= sy.nbig <= mx::kDeferMaxBig;
+  s->pd_ok = !deferrable;
   return sync_status(s);
 }
 
@@ -1423,11 +1430,13 @@ extern "C" {
 
 mx_status mx_step_profiled(mx_system* s, int n_steps, double* kernel_ms, int* launches,
                            double* total_ms) {
+  if (s) s->pd_ok = 0;
   return profiled_run(s, n_steps, nullptr, 0, kernel_ms, launches, total_ms);
 }
 
 mx_status mx_step_timed(mx_system* s, int n_steps, void* dev_flush, size_t flush_bytes,
                         double* kernel_ms, int* launches, double* total_ms) {
+  if (s) s->pd_ok = 0;
   return timed_graph_run(s, n_steps, dev_flush, flush_bytes, kernel_ms, launches, total_ms);
 }
 
@@ -1435,6 +1444,7 @@ mx_status mx_step_wall(mx_system* s, int n_steps, void* dev_flush, size_t flush_
                        double* wall_ms, double* flush_ms) {
   if (!s || n_steps < 1 || (flush_bytes > 0 && !dev_flush) || !wall_ms)
     return fail(MX_ERR_ARG, "invalid arguments");
+  s->pd_ok = 0;
   MX_TRY(set_device(s));
   MX_TRY(ensure_graphs(s));
   MX_TRY(settle(s));   // nothing pending from earlier calls enters the span
@@ -2040,8 +2050,8 @@ mx_status mx_adjoint_init(mx_system* s, const double* dev_lambda, double* dev_gr
   return sync_status(s);
 }
 
-mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long step_k,
-                          double* dev_lambda, double* dev_dparams) {
+static mx_status adjoint_step(mx_system* s, const double* dev_state_k, const double* dev_pd,
+                       long long step_k, double* dev_lambda, double* dev_dparams) {
   if (!s || !dev_state_k || !dev_lambda || !dev_dparams || step_k < 0 || step_k > (1LL << 29))
     return fail(MX_ERR_ARG, "invalid arguments");
   if (s->eject_every > 0 || s->removed_any)
@@ -2058,6 +2068,11 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   mx::Adj a = make_adj(s, dev_lambda, dev_dparams);
   a.z0 = dev_state_k;
   a.step = (int)step_k;
+  if (dev_pd) {   // read only: the kernels that write x2 and v1 do not run
+    a.pd = dev_pd;
+    a.x2 = const_cast<double*>(dev_pd);
+    a.v1 = a.x2 + 3 * (size_t)s->N;
+  }
   a.lin = merge_in ? s->a_lpend : nullptr;
   a.defer_k1 = s->a_merge;
   const mx::Dev d = adjoint_dev(s);
@@ -2085,6 +2100,28 @@ mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long ste
   const mx_status r = sync_status(s);
   if (r != MX_OK) s->a_pend = 0;
   return r;
+}
+
+mx_status mx_adjoint_step(mx_system* s, const double* dev_state_k, long long step_k,
+                          double* dev_lambda, double* dev_dparams) {
+  return adjoint_step(s, dev_state_k, nullptr, step_k, dev_lambda, dev_dparams);
+}
+
+mx_status mx_adjoint_step_predrift(mx_system* s, const double* dev_state_k,
+                                   const double* dev_predrift_k, long long step_k,
+                                   double* dev_lambda, double* dev_dparams) {
+  if (!dev_predrift_k) return fail(MX_ERR_ARG, "invalid arguments");
+  return adjoint_step(s, dev_state_k, dev_predrift_k, step_k, dev_lambda, dev_dparams);
+}
+
+mx_status mx_predrift_state(mx_system* s, double* dev_xv) {
+  if (!s || !dev_xv) return fail(MX_ERR_ARG, "invalid arguments");
+  if (!s->pd_ok)
+    return fail(MX_ERR_ARG, "no pre-drift state: the last mx_step had deferral on, or none ran");
+  MX_TRY(set_device(s));
+  MX_CUDA(cudaMemcpyAsync(dev_xv, s->d.xv0, 6 * (size_t)s->N * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s->st));
+  return sync_status(s);
 }
 
 mx_status mx_adjoint_merge(mx_system* s, int on) {

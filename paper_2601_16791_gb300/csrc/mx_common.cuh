@@ -228,6 +228,9 @@ struct Adj {
   const double* lin;
   double* lpend;
   int defer_k1;
+  // the forward step's pre-drift state (x2, v1), 6 x N (mx_predrift_state),
+  // or null: recomputed.  When set, x2 and v1 point into it and are only read
+  const double* pd;
   double* bs_xsum;               // 3 per system: sum of the big shares' position parts
   // two-body groups: the Stoermer sub-steps of each accepted macro sub-step,
   // kAdjSubRec doubles a slot (null: none are kept, the reverse recomputes)

@@ -102,6 +102,8 @@ _SIGS = {
     "mx_adjoint_encounters": (_I, [_P, _I]),
     "mx_adjoint_store": (_I, [_P, ctypes.c_longlong]),
     "mx_adjoint_merge": (_I, [_P, _I]),
+    "mx_predrift_state": (_I, [_P, _P]),
+    "mx_adjoint_step_predrift": (_I, [_P, _P, _P, ctypes.c_longlong, _P, _P]),
     "mx_adjoint_flush": (_I, [_P]),
     "mx_planets": (_I, [_P, _P, _P]),
 }
@@ -522,6 +524,16 @@ def mx_loss_semimajor(sys, dev_xv_helio0, dev_w, dev_seed_final, dev_seed_init, 
 def mx_adjoint_step(sys, dev_state_k, step_k, dev_lambda, dev_dparams):
     _check(load().mx_adjoint_step(sys, _dptr(dev_state_k), int(step_k), _dptr(dev_lambda),
                                   _dptr(dev_dparams)), "mx_adjoint_step")
+
+
+def mx_predrift_state(sys, dev_xv):
+    _check(load().mx_predrift_state(sys, _dptr(dev_xv)), "mx_predrift_state")
+
+
+def mx_adjoint_step_predrift(sys, dev_state_k, dev_predrift_k, step_k, dev_lambda, dev_dparams):
+    _check(load().mx_adjoint_step_predrift(sys, _dptr(dev_state_k), _dptr(dev_predrift_k),
+                                           int(step_k), _dptr(dev_lambda), _dptr(dev_dparams)),
+           "mx_adjoint_step_predrift")
 
 
 def mx_adjoint_merge(sys, on):

@@ -328,7 +328,8 @@ def test_semiactive_full_size_adjoint_sampled(mask):
         assert abs(ours - jvp) <= 1e-6 * abs(jvp), (ours, jvp)
 
 
-def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode, merge=False, flush_at=None):
+def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode, merge=False, flush_at=None,
+                 predrift=False):
     """Forward run of nsteps from the heliocentric state xv_h0 (every state
     kept), the loss of weights w_host (bodies that met a big body left out
     in modes 0 and 2, whose reverse assumes it), and its reverse through the
@@ -336,16 +337,20 @@ def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode, merge=False, flush_at=
     gradient w.r.t. xv_h0, d/d(params) per system, the encounter log).  With
     merge, consecutive steps are reversed with mx_adjoint_merge on; with
     flush_at = k, the cotangent after step k's reverse is also returned (read
-    after mx_adjoint_flush)."""
+    after mx_adjoint_flush).  With predrift, each step's pre-drift state from
+    the forward run replaces the adjoint's recomputation of it."""
     mx.mx_set_state(h, xv_h0, mx.MX_COORD_HELIO, 0)
     mx.mx_encounter_log(h, None, reset=True)
     mx.mx_kick_branches(h, 1, 2 * nsteps + 2)
-    seg = []
+    seg, pre = [], []
     for _ in range(nsteps):
         z = torch.empty((6, n), dtype=torch.float64, device="cuda")
         mx.mx_get_state_device(h, z)
         seg.append(z)
         mx.mx_step(h, 1)
+        if predrift:   # (recording branches keeps deferral off)
+            pre.append(torch.empty((6, n), dtype=torch.float64, device="cuda"))
+            mx.mx_predrift_state(h, pre[-1])
     ever = torch.zeros(n, dtype=torch.uint8, device="cuda")
     nbb = mx.mx_encounter_log(h, ever)
     wt = torch.tensor(w_host, dtype=torch.float64, device="cuda")
@@ -362,7 +367,10 @@ def _raw_adjoint(h, n, nsys, xv_h0, w_host, nsteps, mode, merge=False, flush_at=
     mx.mx_adjoint_merge(h, merge)
     mid = None
     for k in reversed(range(nsteps)):
-        mx.mx_adjoint_step(h, seg[k], k, lam, dpar)
+        if predrift:
+            mx.mx_adjoint_step_predrift(h, seg[k], pre[k], k, lam, dpar)
+        else:
+            mx.mx_adjoint_step(h, seg[k], k, lam, dpar)
         if k == flush_at:
             mx.mx_adjoint_flush(h)
             mid = lam.cpu().numpy()
@@ -462,4 +470,39 @@ def test_merged_reverse_matches_unmerged(disk):
             assert np.abs(mid1[r] - mid0[r]).max() <= 1e-12 * np.abs(mid0[r]).max()
         assert np.abs(g0).max() > 0
         assert (np.abs(d0).max() > 0) == (disk == "gas")   # no gas on the embryos' disk
+    s.close()
+
+
+@pytest.mark.parametrize("disk", ["gas", "semiactive"])
+def test_adjoint_from_the_forward_predrift_state(disk):
+    """mx_adjoint_step_predrift takes each step's pre-drift state (x2, v1)
+    from the forward run (mx_predrift_state) instead of recomputing the first
+    half kick and jump: the same gradient, with the groups skipped or every
+    group differentiated (relative 1e-12; the recomputation repeats the
+    forward's arithmetic).  mx_predrift_state refuses after a step with
+    deferral on, whose deferred bodies the catch-up drifts."""
+    if disk == "gas":
+        nsteps = 12
+        w = W.adjoint_4core_50k(seed=4, nsmall=3000, nsteps=nsteps)
+        modes = (0, 1)
+    else:
+        nsteps = 10
+        w = W.semiactive_2000big_200k(nbig=1000, nsmall=2000, nsteps=nsteps)
+        modes = (2, 1)
+    s = mx.System(w)
+    wts = np.zeros(w.n)
+    wts[w.nbig:] = 1.0 / w.nsmall
+    for mode in modes:
+        L0, g0, d0, _, _ = _raw_adjoint(s.h, w.n, 1, w.xv_helio, wts, nsteps, mode)
+        L1, g1, d1, _, _ = _raw_adjoint(s.h, w.n, 1, w.xv_helio, wts, nsteps, mode, predrift=True)
+        assert L0[0] == L1[0]
+        assert np.abs(g1 - g0).max() <= 1e-12 * np.abs(g0).max()
+        assert np.allclose(d1, d0, rtol=1e-12, atol=0)
+    if disk == "gas":   # deferral on (the default window, no branch recording)
+        mx.mx_kick_branches(s.h, 0)
+        mx.mx_set_state(s.h, w.xv_helio, mx.MX_COORD_HELIO, 0)
+        mx.mx_step(s.h, 1)
+        buf = torch.empty((6, w.n), dtype=torch.float64, device="cuda")
+        with pytest.raises(mx.MxError):
+            mx.mx_predrift_state(s.h, buf)
     s.close()
