@@ -354,8 +354,13 @@ def ensemble_leg(steps, nsys=256):
 
 
 def adjoint_leg(nsteps=200, every=50):
-    """Cost of one hand-written adjoint step against one forward step on the
-    adjoint workload (4 cores + 50,000 planetesimals with gas)."""
+    """Cost of the hand-written adjoint on the adjoint workload (4 cores +
+    50,000 planetesimals with gas): bwd_over_fwd, the autograd backward's wall
+    time over its forward run's; from one state, one adjoint step against one
+    forward step (fwd_ms, mx_step(1)) with the groups skipped (adjoint_step_ms,
+    adjoint_over_forward_step) and through every group (groups_ms,
+    groups_ratio); and consecutive steps as the backward runs them, merged and
+    from the forward's pre-drift states (run_ms, run_ratio)."""
     import torch
     from paper_2601_16791_gb300 import mx, workloads as W
     from paper_2601_16791_gb300.autograd import Trajectory, semimajor_loss
@@ -407,12 +412,9 @@ def adjoint_leg(nsteps=200, every=50):
     g_ms = e4.elapsed_time(e5) / reps
     m_ms = merged_adjoint_ms(traj.h, w.n, z, 0)
     traj.close()
-    return {"steps": nsteps, "checkpoint_every": every,
-            "backward_over_forward": t_bwd / t_fwd, "forward_step_ms": f_ms,
+    return {"steps": nsteps, "every": every, "bwd_over_fwd": t_bwd / t_fwd, "fwd_ms": f_ms,
             "adjoint_step_ms": a_ms, "adjoint_over_forward_step": a_ms / f_ms,
-            "adjoint_step_ms_through_groups": g_ms,
-            "through_groups_over_forward_step": g_ms / f_ms,
-            "merged_adjoint_step_ms": m_ms, "merged_over_forward_step": m_ms / f_ms}
+            "groups_ms": g_ms, "groups_ratio": g_ms / f_ms, "run_ms": m_ms, "run_ratio": m_ms / f_ms}
 
 
 def eject_leg(steps=200):
@@ -522,11 +524,8 @@ def semiactive_adjoint(s, w, reps=3):
     a_ms = ev[2].elapsed_time(ev[3]) / reps
     g_ms = ev[4].elapsed_time(ev[5]) / reps
     m_ms = merged_adjoint_ms(s.h, w.n, z, 2, k=8)
-    return {"forward_step_ms": f_ms, "adjoint_step_ms": a_ms,
-            "adjoint_over_forward_step": a_ms / f_ms,
-            "adjoint_step_ms_through_groups": g_ms,
-            "through_groups_over_forward_step": g_ms / f_ms,
-            "merged_adjoint_step_ms": m_ms, "merged_over_forward_step": m_ms / f_ms}
+    return {"fwd_ms": f_ms, "adjoint_step_ms": a_ms, "adjoint_over_forward_step": a_ms / f_ms,
+            "groups_ms": g_ms, "groups_ratio": g_ms / f_ms, "run_ms": m_ms, "run_ratio": m_ms / f_ms}
 
 
 def semiactive_leg(steps=20):
