@@ -497,7 +497,9 @@ mx_status mx_adjoint_store(mx_system* s, long long slots);
  * next call, for step k - 1 on the same dev_lambda, takes it in the pass of
  * that step's last half kick.  That saves one pass over the (target, big body)
  * pairs a step, most of an adjoint step with many big bodies.  Until then,
- * the position rows of that dev_lambda lack the pending term.
+ * the position rows of that dev_lambda lack the pending term, and the buffer
+ * must stay allocated: the term is added into it later (mx_destroy drops a
+ * pending term without touching it).
  * mx_adjoint_init, mx_adjoint_flush, mx_adjoint_merge(s, 0), or an
  * mx_adjoint_step of any other step or cotangent adds it first.  The shared
  * pass runs at the recomputed positions of step k - 1's last half kick, which
