@@ -808,6 +808,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_fold_jump1(Dev d, Adj a) {
   }
 }
 
+int adjoint_vjp_blocks_per_sm(int threads) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adj_kick_vjp, threads, 0) != cudaSuccess)
+    return 0;
+  return n;
+}
+
 void launch_fold_kick(const Dev& d, const Adj& a, int which, int grav, cudaStream_t st) {
   if (grav && 3 * d.big_max + 9 > kThreads)
     k_adj_fold_big<<<dim3(d.nsys, (3 * d.big_max + kThreads - 1) / kThreads), kThreads, 0, st>>>(d, a);

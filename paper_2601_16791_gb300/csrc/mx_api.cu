@@ -253,6 +253,7 @@ struct mx_system {
   // and its per-tile partial sums then do not depend on the forward tiling
   mx::Tile* a_tiles = nullptr;
   int a_ntiles = 0;
+  int a_tile = mx::kThreads;   // targets per block of the adjoint's per-target kernels
   long long kbits_cap = 0;
 };
 
@@ -1814,8 +1815,35 @@ mx::Dev adjoint_dev(const mx_system* s) {
   mx::Dev d = s->d;
   d.tiles = s->a_tiles;
   d.ntiles = s->a_ntiles;
-  d.tile = mx::kThreads;
+  d.tile = s->a_tile;
   return d;
+}
+
+// The adjoint's targets per block.  With few big bodies, 256 (the per-tile
+// partial records and their folds favour full blocks: 0.62 against 1.01 ms a
+// step with 64 on the 4-core disk).  With many, the kick's reverse is a long
+// pass over the pairs in which every block does the same work, so the block
+// count is chosen to fill whole waves of the resident blocks: of 160 to 256
+// targets (whole warps), the size whose waves come closest to a whole number
+// (902 blocks of 224 targets make 2.97 waves on 152 SMs, where 790 of 256
+// make 2.6 and a third of the SMs idle through the last).
+int adjoint_tile(const mx_system* s) {
+  if (s->d.big_max <= 64) return mx::kThreads;
+  const int nsm = s->bs_blocks / 4;
+  int best_tile = mx::kThreads;
+  double best = -1.0;
+  for (int w = mx::kThreads / 32; w >= 5; --w) {
+    const int t = 32 * w;
+    const int occ = mx::adjoint_vjp_blocks_per_sm(t);
+    if (occ <= 0 || nsm <= 0) continue;
+    const double waves = (double)make_tiles(s->h_sys, t, 0).size() / ((double)occ * nsm);
+    const double eff = waves / std::ceil(waves);
+    if (eff > best + 1e-9) {
+      best = eff;
+      best_tile = t;
+    }
+  }
+  return best_tile;
 }
 
 mx_status ensure_adjoint_store(mx_system* s) {
@@ -1851,7 +1879,8 @@ mx_status ensure_adjoint(mx_system* s) {
     MX_TRY(dalloc(s, &s->a_x4, (size_t)3 * N));
     MX_TRY(dalloc(s, &s->a_P, 9 * s->h_sys.size()));
     MX_TRY(dalloc(s, &s->a_L, s->h_sys.size()));
-    std::vector<mx::Tile> tiles = make_tiles(s->h_sys, mx::kThreads, 0);
+    s->a_tile = adjoint_tile(s);
+    std::vector<mx::Tile> tiles = make_tiles(s->h_sys, s->a_tile, 0);
     std::vector<int> poff(tiles.size());
     size_t off = 0;
     for (size_t t = 0; t < tiles.size(); ++t) {

@@ -76,6 +76,8 @@ void launch_adjoint_step_b(const Dev& d, const Adj& a, cudaStream_t st);
 // The pending pair pass of a merged reverse on its own (a.lpend at the
 // positions xpos, 3 x N), into a.lam.
 void launch_adjoint_flush(const Dev& d, const Adj& a, const double* xpos, cudaStream_t st);
+// Resident blocks per SM of the kick's reverse at `threads` threads a block.
+int adjoint_vjp_blocks_per_sm(int threads);
 // k_adj_bs.cu: the step's encounter groups inside the adjoint (forward with a
 // tape, reverse, per-system fold of the big bodies' shares)
 void launch_adjoint_bs_plan(const Dev& d, const Adj& a, cudaStream_t st);
