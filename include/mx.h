@@ -137,8 +137,9 @@ mx_status mx_batch_offsets(mx_system* s, int* offsets);
 mx_status mx_batch_size(mx_system* s, int* n_sys, int* n_total);
 /* Energy and angular momentum of every system: E [n_sys], L3 [3 n_sys]. */
 mx_status mx_energy_batch(mx_system* s, double* E, double* L3);
-/* Tile size (64, 128 or 256 targets per block) and order (0: system order,
- * 1: costliest tiles first) in use; mx_set_tiling overrides the autotuner. */
+/* Tile size (targets per block: a multiple of 32 from 64 to 256) and order
+ * (0: system order, 1: costliest tiles first) in use; mx_set_tiling overrides
+ * the autotuner.  MX_ERR_ARG for another size or order. */
 mx_status mx_tiling(mx_system* s, int* tile, int* order);
 mx_status mx_set_tiling(mx_system* s, int tile, int order);
 

@@ -686,6 +686,9 @@ mx_status trial_ms(mx_system* s, double* ms) {
   return MX_OK;
 }
 
+// A tile is whole warps, from 64 to 256 targets.
+bool valid_tile(int tile) { return tile >= 64 && tile <= mx::kThreads && tile % 32 == 0; }
+
 mx_status autotune(mx_system* s) {
   const char* env = std::getenv("MX_AUTOTUNE");
   if (env && std::strcmp(env, "0") == 0) return MX_OK;
@@ -693,12 +696,14 @@ mx_status autotune(mx_system* s) {
   for (auto& kv : tune_load())
     if (kv.first == key) {
       const int tile = kv.second.first, order = kv.second.second;
-      if ((tile == 64 || tile == 128 || tile == 256) && (order == 0 || order == 1))
-        return set_tiling(s, tile, order);
+      if (valid_tile(tile) && (order == 0 || order == 1)) return set_tiling(s, tile, order);
     }
   double best = 1e300;
   int bt = s->tile, bo = s->order;
-  for (int tile : {64, 128, 256})
+  // whole warps from 64 to 256 targets: besides the powers of two, sizes whose
+  // block count fills the resident slots' waves more evenly (a long kernel
+  // ends with its last, partly filled wave)
+  for (int tile : {64, 96, 128, 160, 192, 224, 256})
     for (int order : {0, 1}) {
       if (order == 1 && s->params.size() == 1) continue;   // one system: order is moot
       MX_TRY(set_tiling(s, tile, order));
@@ -1057,8 +1062,8 @@ mx_status mx_tiling(mx_system* s, int* tile, int* order) {
 }
 
 mx_status mx_set_tiling(mx_system* s, int tile, int order) {
-  if (!s || !(tile == 64 || tile == 128 || tile == 256) || !(order == 0 || order == 1))
-    return fail(MX_ERR_ARG, "tile must be 64, 128 or 256 and order 0 or 1");
+  if (!s || !valid_tile(tile) || !(order == 0 || order == 1))
+    return fail(MX_ERR_ARG, "tile must be a multiple of 32 from 64 to 256 and order 0 or 1");
   MX_TRY(set_device(s));
   return set_tiling(s, tile, order);
 }

@@ -50,7 +50,7 @@ def test_batch_equals_systems_run_alone():
 def test_tiling_does_not_change_results():
     ws = _members()
     outs = []
-    for tile in (64, 128, 256):
+    for tile in (64, 96, 128, 224, 256):
         for order in (0, 1):
             b = mx.Batch(ws)
             mx.mx_set_tiling(b.h, tile, order)
